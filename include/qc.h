@@ -1,0 +1,279 @@
+/*
+ * qc.h -- C ABI of a single-GPU (GB300, sm_103a) state-vector simulator for the
+ * computation defined in QCLAB (Keip, Camps, Van Beeumen, "QCLAB: A Matlab Toolbox
+ * for Quantum Computing", arXiv:2503.03016, 2025).
+ *
+ * Conventions used by every call (QCLAB Sec. 3.1, Sec. 3.2, Sec. 5.1):
+ *   - A state on n qubits is 2^n complex amplitudes, interleaved (re, im), either
+ *     complex64 (2 x float) or complex128 (2 x double), contiguous, in device memory.
+ *   - Qubit 0 is the leftmost Kronecker factor: amplitude index
+ *     i = sum_q b_q * 2^(n-1-q).  A bitstring's character j is qubit j, so '01' is
+ *     index 1 (Sec. 3.1: simulate('00') equals simulate([1;0;0;0])).
+ *   - A k-qubit gate U' on qubits (q_0, ..., q_{k-1}) acts as I_l (x) U' (x) I_r
+ *     (Sec. 3.2); the row/column index of U' has q_0 as its most significant bit.
+ *   - Gate matrices are passed from the host in FP64, row-major, as (re, im) pairs;
+ *     complex64 states round them to FP32.
+ *
+ * Errors: every call returns a qc_status.  Argument errors are reported before
+ * anything is launched and leave the state untouched.  CUDA errors surface as
+ * QC_ERR_CUDA at the call that observes them (asynchronous calls report launch
+ * errors; synchronising calls also report execution errors).  qc_last_error()
+ * returns a thread-local, human-readable message for the last failure of the
+ * calling thread.  No C++ exception and no process exit ever crosses this ABI.
+ *
+ * Streams: each state carries a CUDA stream (default: the legacy default stream).
+ * Calls are asynchronous on that stream unless documented as synchronising.
+ *
+ * Ownership: pointers passed in stay owned by the caller; the library owns only
+ * what qc_state_alloc allocates (amplitudes) and the per-state scratch it creates
+ * lazily, all released by qc_state_free.
+ */
+#ifndef QC_H_
+#define QC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QC_OK = 0,
+  QC_ERR_INVALID_ARG = 1, /* bad qubit index, size, pointer, dtype, ...        */
+  QC_ERR_OOM = 2,         /* device allocation failed                            */
+  QC_ERR_CUDA = 3,        /* a CUDA runtime error (message in qc_last_error)     */
+  QC_ERR_UNSUPPORTED = 4, /* valid request this build does not implement         */
+  QC_ERR_ZERO_PROB = 5,   /* collapse onto an outcome of (numerically) zero prob.*/
+  QC_ERR_TIMEOUT = 6      /* a bounded device wait ran out                       */
+} qc_status;
+
+typedef enum { QC_C64 = 0, QC_C128 = 1 } qc_dtype;
+
+/* Arithmetic of fused k-qubit blocks (qc_apply_fused_k, qc_run_circuit). */
+typedef enum {
+  QC_PREC_NATIVE = 0, /* FMA in the state's own precision on the CUDA cores        */
+  QC_PREC_TF32X3 = 1  /* complex64 only: tensor cores (tcgen05, kind::tf32), each
+                         product split as a_hi*b_hi + a_hi*b_lo + a_lo*b_hi with
+                         FP32 accumulation                                          */
+} qc_prec;
+
+typedef struct qc_state qc_state; /* opaque */
+
+/* Message describing the calling thread's last error ("" if none). */
+const char* qc_last_error(void);
+/* ABI version (incremented on incompatible changes). */
+int qc_abi_version(void);
+/* Number of CUDA kernels this library has launched in this process (all threads);
+ * a diagnostic for benchmarks. */
+uint64_t qc_launch_count(void);
+
+/* ---------------------------------------------------------------------------
+ * State handles (QCLAB Sec. 3.1 "Initialization")
+ * ------------------------------------------------------------------------- */
+
+/* Allocates a 2^n-amplitude state on the current device; 1 <= n <= 34.  `stream`
+ * is a cudaStream_t (NULL = legacy default stream).  The amplitudes are left
+ * uninitialised; call one of the qc_state_init_* functions. */
+qc_status qc_state_alloc(int n, qc_dtype dtype, void* stream, qc_state** out);
+
+/* Wraps caller-owned device memory (e.g. a torch tensor) of 2^n amplitudes, at
+ * least 16-byte aligned.  qc_state_free will not free it. */
+qc_status qc_state_wrap(int n, qc_dtype dtype, void* dev_amps, void* stream, qc_state** out);
+
+/* Releases the handle, its scratch and (if library-owned) its amplitudes.  NULL is
+ * accepted.  Synchronises the state's stream first. */
+qc_status qc_state_free(qc_state* s);
+
+/* n, dtype and the device address of the amplitudes. */
+qc_status qc_state_info(const qc_state* s, int* n, qc_dtype* dtype, void** dev_amps);
+
+/* Replaces the stream subsequent calls on `s` use. */
+qc_status qc_state_set_stream(qc_state* s, void* stream);
+
+/* Basis state |index>, index per the convention above (Sec. 3.1: bitstring start). */
+qc_status qc_state_init_basis(qc_state* s, uint64_t index);
+
+/* Copies 2^n amplitudes of dtype `src_dtype` from `amps` (device memory, or host
+ * memory if `src_on_host` is nonzero) into the state, converting precision
+ * (Sec. 3.1: vector start).  The vector is not normalised. */
+qc_status qc_state_init_vector(qc_state* s, const void* amps, qc_dtype src_dtype, int src_on_host);
+
+/* Normalised complex Gaussian state generated on the device: amplitude j uses the
+ * counter-based SplitMix64 stream (Steele, Lea, Flood, OOPSLA 2014) with uniforms
+ * u1 = U(2j), u2 = U(2j+1), U(c) = (mix(seed + (c+1)*0x9E3779B97F4A7C15) >> 11) * 2^-53,
+ * and the Box-Muller transform r = sqrt(-2 ln(1-u1)), (re, im) = r (cos, sin)(2 pi u2).
+ * The norm is accumulated in FP64 and the division done in FP64 before rounding
+ * to the state's precision.  Synchronising. */
+qc_status qc_state_init_gaussian(qc_state* s, uint64_t seed);
+
+/* dst <- src (same n and dtype); used to branch on measurement outcomes. */
+qc_status qc_state_copy(qc_state* dst, const qc_state* src);
+
+/* Copies the amplitudes to host memory `host_dst` (2^n amplitudes of the state's
+ * dtype).  Synchronising. */
+qc_status qc_state_download(const qc_state* s, void* host_dst);
+
+/* ---------------------------------------------------------------------------
+ * Gate application (QCLAB Sec. 3.2: U = I_l (x) U' (x) I_r applied to the state)
+ * ------------------------------------------------------------------------- */
+
+/* U' = U (2x2, 8 doubles) on qubit q. */
+qc_status qc_apply_1q(qc_state* s, int q, const double U[8]);
+
+/* U' = U (4x4, 32 doubles) on (qa, qb), row index 2*b_qa + b_qb; qa != qb, either
+ * order. */
+qc_status qc_apply_2q(qc_state* s, int qa, int qb, const double U[32]);
+
+/* U (2x2) on `target`, applied only where control j reads ctrl_states[j] (0 or 1;
+ * NULL = all 1).  Covers CNOT/CZ (Sec. 2, Sec. 5.3) and MCX with open controls
+ * (Sec. 5.4).  0 <= nctrl <= 6; all qubits distinct. */
+qc_status qc_apply_ctrl(qc_state* s, const int* ctrls, const int* ctrl_states, int nctrl, int target,
+                        const double U[8]);
+
+/* A dense 2^k x 2^k block on qubits[0..k-1] (qubits[0] = MSB of the block index),
+ * 1 <= k <= 7 (QC_PREC_TF32X3: 2 <= k <= 6).  The product of consecutive gates that
+ * act on at most k qubits (gate fusion). */
+qc_status qc_apply_fused_k(qc_state* s, const int* qubits, int k, const double* U, qc_prec prec);
+
+/* ---------------------------------------------------------------------------
+ * Measurement, probabilities, sampling (QCLAB Sec. 3.3)
+ * ------------------------------------------------------------------------- */
+
+/* Measures qubit q in the Z basis: P(o) = sum over indices whose bit for q is o of
+ * |psi_i|^2 (FP64).  With T = P(0) + P(1), the outcome is 1 iff u*T >= P(0) (u in
+ * [0,1), supplied by the caller).  The state is collapsed onto the outcome and
+ * divided by sqrt(P(outcome)) in FP64.  Returns the outcome and P(outcome)/T.
+ * Synchronising. */
+qc_status qc_measure(qc_state* s, int q, double u, int* outcome, double* prob);
+
+/* Forced branch: collapses onto `outcome` and renormalises, returning its
+ * probability P(outcome)/T; QC_ERR_ZERO_PROB (state untouched) if that probability
+ * is <= 1e-12 (complex128) or <= 1e-6 (complex64).  Synchronising. */
+qc_status qc_collapse(qc_state* s, int q, int outcome, double* prob);
+
+/* P(outcome) for qubit q without collapsing (host scalar, synchronising). */
+qc_status qc_outcome_prob(const qc_state* s, int q, int outcome, double* prob);
+
+/* dev_out[i] = re_i*re_i + im_i*im_i in FP64 (two rounded products, one rounded
+ * sum; complex64 amplitudes are widened exactly first).  2^n doubles. */
+qc_status qc_probs(const qc_state* s, double* dev_out);
+
+/* Draws `shots` outcomes: with cdf_k the FP64 number nearest the exact prefix sum of
+ * the p_i above and T = cdf_{N-1}, dev_out[s] = min{k : dev_u[s]*T < cdf_k} for
+ * caller-supplied uniforms dev_u in [0,1) (device memory).  Bit-exact given the
+ * same p_i and uniforms. */
+qc_status qc_sample(const qc_state* s, const double* dev_u, int64_t shots, uint64_t* dev_out);
+
+/* The same rule as qc_sample applied to a caller-supplied probability vector dev_p
+ * (device, 2^n nonnegative doubles, 16-byte aligned, sum below 2^10), e.g. a marginal
+ * distribution.  `s` supplies the stream and scratch; its amplitudes are not read. */
+qc_status qc_sample_probs(qc_state* s, const double* dev_p, int n, const double* dev_u, int64_t shots,
+                          uint64_t* dev_out);
+
+/* host_out[t] = coeffs[t] * <psi| P_t |psi> for Pauli strings P_t of n characters
+ * in {I,X,Y,Z}, character j acting on qubit j (coeffs NULL = all 1).  Reductions in
+ * FP64.  Synchronising.  (Sec. 5.2 builds a density-matrix estimate from such
+ * expectations.) */
+qc_status qc_expect_pauli(const qc_state* s, const char* const* strings, const double* coeffs, int nterms,
+                          double* host_out);
+
+/* ---------------------------------------------------------------------------
+ * Circuits (QCLAB Sec. 2: QCircuit / push_back; nested circuits are flattened by
+ * the caller)
+ * ------------------------------------------------------------------------- */
+
+#define QC_MAX_OP_QUBITS 8
+
+typedef enum {
+  QC_GATE_MATRIX1 = 0,      /* dense 2x2 at pool[matrix], qubits[0]                  */
+  QC_GATE_MATRIX2 = 1,      /* dense 4x4 at pool[matrix], (qubits[0], qubits[1])      */
+  QC_GATE_H = 2,
+  QC_GATE_X = 3,
+  QC_GATE_Y = 4,
+  QC_GATE_Z = 5,
+  QC_GATE_S = 6,
+  QC_GATE_SDG = 7,
+  QC_GATE_T = 8,
+  QC_GATE_TDG = 9,
+  QC_GATE_RX = 10,          /* exp(-i t X/2)                                          */
+  QC_GATE_RY = 11,          /* exp(-i t Y/2)                                          */
+  QC_GATE_RZ = 12,          /* exp(-i t Z/2) = diag(e^{-it/2}, e^{it/2})              */
+  QC_GATE_U3 = 13,          /* OpenQASM U3(theta, phi, lambda)                        */
+  QC_GATE_CNOT = 14,        /* qubits = (control, target)                             */
+  QC_GATE_CZ = 15,          /* qubits = (a, b)                                        */
+  QC_GATE_CP = 16,          /* diag(1,1,1,e^{i phi}) on (a, b)                        */
+  QC_GATE_SWAP = 17,
+  QC_GATE_MCX = 18,         /* qubits = (controls..., target), ctrl_states            */
+  QC_GATE_CTRL_MATRIX1 = 19 /* controlled dense 2x2 at pool[matrix]                   */
+} qc_gate_kind;
+
+typedef struct qc_op {
+  int32_t kind;                        /* qc_gate_kind                                  */
+  int32_t nq;                          /* entries used in qubits[]                      */
+  int32_t qubits[QC_MAX_OP_QUBITS];    /* controlled kinds: controls first, target last */
+  uint32_t ctrl_states;                /* bit j = required value of control j (MCX,
+                                          CTRL_MATRIX1); CNOT/CZ/CP use 1              */
+  int32_t param;                       /* >= 0: angles from params[param ...]; -1: angle[] */
+  int32_t adjoint;                     /* nonzero: apply U^dagger                        */
+  int32_t reserved;
+  double angle[3];
+  int64_t matrix;                      /* offset in doubles into pool, or -1             */
+} qc_op;
+
+typedef struct qc_circuit {
+  int32_t n;
+  int32_t nops;
+  const qc_op* ops;   /* host memory */
+  const double* pool; /* host FP64 (re,im) row-major matrices referenced by ops */
+  int64_t pool_len;   /* doubles in pool */
+} qc_circuit;
+
+typedef enum {
+  QC_RUN_PER_GATE = 0, /* one full sweep per gate: the paper's plain method (Sec. 3.2) */
+  QC_RUN_FUSED = 1     /* planner: gates grouped into shared-memory tile passes and
+                          fused k-qubit blocks; same result up to rounding            */
+} qc_run_mode;
+
+/* Applies every op of `c` (c->n must equal the state's n) in order.  `params`
+ * (host, may be NULL if no op uses it) supplies angles for ops with param >= 0.
+ * `prec` selects the arithmetic of fused blocks in QC_RUN_FUSED. */
+qc_status qc_run_circuit(qc_state* s, const qc_circuit* c, const double* params, qc_run_mode mode,
+                         qc_prec prec);
+
+/* ---------------------------------------------------------------------------
+ * Batched circuits and adjoint gradients (parameterised ansatz circuits)
+ * ------------------------------------------------------------------------- */
+
+/* Adjoint (reverse-sweep) gradient of E(theta) = <psi(theta)| H |psi(theta)>,
+ * psi(theta) = U_L ... U_1 |0...0>, H = sum_t coeffs[t] P_t (Pauli strings as in
+ * qc_expect_pauli).  Parameterised ops must be RX/RY/RZ with param >= 0 (each
+ * U = exp(-i t G/2)); dE/dt_l = Im <lambda_l| G_l |psi_l> summed over the ops that use
+ * parameter l, with psi_l the state after op l and lambda_l = U_{l+1}^dag ... U_L^dag H psi.
+ * `params` (host, nparams doubles).  Writes *host_energy and host_grad[nparams].
+ * Uses three state buffers of c->n qubits in `dtype`.  Synchronising. */
+qc_status qc_adjoint_grad(const qc_circuit* c, const double* params, int nparams, const char* const* strings,
+                          const double* coeffs, int nterms, qc_dtype dtype, void* stream, double* host_energy,
+                          double* host_grad);
+
+/* A batch of independent parameterised circuits of uneven qubit counts evaluated
+ * in one persistent launch (complex64).  Circuit b has n[b] qubits (2 <= n <= 20)
+ * and runs `layers` layers of [RY(t) then RZ(t) on every qubit, then CZ(i, i+1),
+ * i = 0..n-2], parameter index layer*2n + 2q + {0: RY, 1: RZ}, from |0...0>, reading
+ * its parameters from params + param_offset[b] (device memory).  dev_out[b] =
+ * <psi_b| sum_{i<n-1} Z_i Z_{i+1} |psi_b>, accumulated in FP64. */
+typedef struct qc_batch {
+  int32_t count;                /* number of circuits                                */
+  int32_t layers;
+  const int32_t* n;             /* host: qubit count per circuit                     */
+  const int64_t* param_offset;  /* host: offset of circuit b's parameters            */
+  const float* dev_params;      /* device: all parameters (FP32 angles)              */
+  int64_t nparams;              /* total number of parameters                        */
+} qc_batch;
+
+qc_status qc_run_batch(const qc_batch* b, void* stream, double* dev_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QC_H_ */

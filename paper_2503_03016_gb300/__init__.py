@@ -1,0 +1,9 @@
+"""GB300 (sm_103a) state-vector simulator for the computation defined in QCLAB
+(Keip, Camps, Van Beeumen, arXiv:2503.03016).
+
+All simulation work runs in the CUDA library behind include/qc.h; this package is
+its Python binding (argument marshalling) plus a torch-facing convenience layer.
+"""
+from ._binding import *  # noqa: F401,F403
+from ._binding import lib, QCError, Circuit  # noqa: F401
+from .state import State  # noqa: F401

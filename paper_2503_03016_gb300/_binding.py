@@ -1,0 +1,352 @@
+"""ctypes binding of the C ABI in include/qc.h (argument marshalling only).
+
+Every function keeps the C name.  Device buffers are passed as torch CUDA tensors
+(or raw integer addresses); streams default to torch's current stream.  A non-zero
+status raises :class:`QCError` carrying ``qc_last_error()``.  There is no CPU
+fallback: if the CUDA library is missing, :func:`lib` raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libqcgb.so")
+
+QC_C64, QC_C128 = 0, 1
+QC_PREC_NATIVE, QC_PREC_TF32X3 = 0, 1
+QC_RUN_PER_GATE, QC_RUN_FUSED = 0, 1
+STATUS = {0: "QC_OK", 1: "QC_ERR_INVALID_ARG", 2: "QC_ERR_OOM", 3: "QC_ERR_CUDA", 4: "QC_ERR_UNSUPPORTED",
+          5: "QC_ERR_ZERO_PROB", 6: "QC_ERR_TIMEOUT"}
+
+GATE = {"u1q": 0, "u2q": 1, "h": 2, "x": 3, "y": 4, "z": 5, "s": 6, "sdg": 7, "t": 8, "tdg": 9, "rx": 10,
+        "ry": 11, "rz": 12, "u3": 13, "cnot": 14, "cz": 15, "cp": 16, "swap": 17, "mcx": 18, "ctrl": 19}
+MAX_OP_QUBITS = 8
+
+
+class QCError(RuntimeError):
+    def __init__(self, func: str, status: int, msg: str):
+        super().__init__("%s failed: %s (%s)" % (func, STATUS.get(status, status), msg))
+        self.status = status
+
+
+class qc_op(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("nq", ctypes.c_int32), ("qubits", ctypes.c_int32 * MAX_OP_QUBITS),
+                ("ctrl_states", ctypes.c_uint32), ("param", ctypes.c_int32), ("adjoint", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("angle", ctypes.c_double * 3), ("matrix", ctypes.c_int64)]
+
+
+class qc_circuit(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int32), ("nops", ctypes.c_int32), ("ops", ctypes.POINTER(qc_op)),
+                ("pool", ctypes.POINTER(ctypes.c_double)), ("pool_len", ctypes.c_int64)]
+
+
+class qc_batch(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("layers", ctypes.c_int32), ("n", ctypes.POINTER(ctypes.c_int32)),
+                ("param_offset", ctypes.POINTER(ctypes.c_int64)), ("dev_params", ctypes.c_void_p),
+                ("nparams", ctypes.c_int64)]
+
+
+_P = ctypes.c_void_p
+_D = ctypes.POINTER(ctypes.c_double)
+_I = ctypes.POINTER(ctypes.c_int)
+_SIGS = {
+    "qc_last_error": (ctypes.c_char_p, []),
+    "qc_abi_version": (ctypes.c_int, []),
+    "qc_launch_count": (ctypes.c_uint64, []),
+    "qc_state_alloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(_P)]),
+    "qc_state_wrap": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, ctypes.POINTER(_P)]),
+    "qc_state_free": (ctypes.c_int, [_P]),
+    "qc_state_info": (ctypes.c_int, [_P, _I, _I, ctypes.POINTER(_P)]),
+    "qc_state_set_stream": (ctypes.c_int, [_P, _P]),
+    "qc_state_init_basis": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "qc_state_init_vector": (ctypes.c_int, [_P, _P, ctypes.c_int, ctypes.c_int]),
+    "qc_state_init_gaussian": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "qc_state_copy": (ctypes.c_int, [_P, _P]),
+    "qc_state_download": (ctypes.c_int, [_P, _P]),
+    "qc_apply_1q": (ctypes.c_int, [_P, ctypes.c_int, _D]),
+    "qc_apply_2q": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _D]),
+    "qc_apply_ctrl": (ctypes.c_int, [_P, _I, _I, ctypes.c_int, ctypes.c_int, _D]),
+    "qc_apply_fused_k": (ctypes.c_int, [_P, _I, ctypes.c_int, _D, ctypes.c_int]),
+    "qc_measure": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, _I, _D]),
+    "qc_collapse": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _D]),
+    "qc_outcome_prob": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _D]),
+    "qc_probs": (ctypes.c_int, [_P, _P]),
+    "qc_sample": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
+    "qc_sample_probs": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int64, _P]),
+    "qc_expect_pauli": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_char_p), _D, ctypes.c_int, _D]),
+    "qc_run_circuit": (ctypes.c_int, [_P, ctypes.POINTER(qc_circuit), _D, ctypes.c_int, ctypes.c_int]),
+    "qc_adjoint_grad": (ctypes.c_int, [ctypes.POINTER(qc_circuit), _D, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_char_p), _D, ctypes.c_int, ctypes.c_int, _P, _D,
+                                       _D]),
+    "qc_run_batch": (ctypes.c_int, [ctypes.POINTER(qc_batch), _P, _P]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library; raises if it was not built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("CUDA library %s is missing: run __graft_entry__.build() (no CPU fallback)" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name, None)
+            if f is None:
+                continue
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(name: str, st: int):
+    if st != 0:
+        msg = lib().qc_last_error().decode(errors="replace")
+        raise QCError(name, st, msg)
+
+
+def _call(name: str, *args):
+    _check(name, getattr(lib(), name)(*args))
+
+
+def _ptr(x) -> Optional[int]:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return int(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        return int(x.ctypes.data)
+    raise TypeError("expected a tensor, ndarray or address, got %r" % type(x))
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return int(torch.cuda.current_stream().cuda_stream) or None
+    if isinstance(stream, int):
+        return stream or None
+    return int(stream.cuda_stream) or None
+
+
+def _mat(U, dim: int):
+    a = np.ascontiguousarray(np.asarray(U, dtype=np.complex128).reshape(dim, dim)).view(np.float64).ravel()
+    return a, a.ctypes.data_as(_D)
+
+
+def qc_launch_count() -> int:
+    return int(lib().qc_launch_count())
+
+
+# ---------------------------------------------------------------------------
+# state handles
+# ---------------------------------------------------------------------------
+
+def qc_state_alloc(n: int, dtype: int = QC_C64, stream=None) -> int:
+    h = _P()
+    _call("qc_state_alloc", n, dtype, _stream(stream), ctypes.byref(h))
+    return h.value
+
+
+def qc_state_wrap(n: int, dtype: int, amps, stream=None) -> int:
+    h = _P()
+    _call("qc_state_wrap", n, dtype, _ptr(amps), _stream(stream), ctypes.byref(h))
+    return h.value
+
+
+def qc_state_free(h: int) -> None:
+    _call("qc_state_free", h)
+
+
+def qc_state_info(h: int):
+    n, dt, p = ctypes.c_int(), ctypes.c_int(), _P()
+    _call("qc_state_info", h, ctypes.byref(n), ctypes.byref(dt), ctypes.byref(p))
+    return n.value, dt.value, p.value
+
+
+def qc_state_set_stream(h: int, stream) -> None:
+    _call("qc_state_set_stream", h, _stream(stream))
+
+
+def qc_state_init_basis(h: int, index: int) -> None:
+    _call("qc_state_init_basis", h, ctypes.c_uint64(int(index)))
+
+
+def qc_state_init_vector(h: int, amps, src_dtype: int, on_host: bool) -> None:
+    _call("qc_state_init_vector", h, _ptr(amps), src_dtype, 1 if on_host else 0)
+
+
+def qc_state_init_gaussian(h: int, seed: int) -> None:
+    _call("qc_state_init_gaussian", h, ctypes.c_uint64(int(seed)))
+
+
+def qc_state_copy(dst: int, src: int) -> None:
+    _call("qc_state_copy", dst, src)
+
+
+def qc_state_download(h: int) -> np.ndarray:
+    n, dt, _ = qc_state_info(h)
+    out = np.empty(1 << n, dtype=np.complex64 if dt == QC_C64 else np.complex128)
+    _call("qc_state_download", h, out.ctypes.data)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# gates
+# ---------------------------------------------------------------------------
+
+def qc_apply_1q(h: int, q: int, U) -> None:
+    a, p = _mat(U, 2)
+    _call("qc_apply_1q", h, q, p)
+
+
+def qc_apply_2q(h: int, qa: int, qb: int, U) -> None:
+    a, p = _mat(U, 4)
+    _call("qc_apply_2q", h, qa, qb, p)
+
+
+def qc_apply_ctrl(h: int, ctrls: Sequence[int], ctrl_states: Optional[Sequence[int]], target: int, U) -> None:
+    a, p = _mat(U, 2)
+    c = (ctypes.c_int * max(1, len(ctrls)))(*ctrls)
+    s = None if ctrl_states is None else (ctypes.c_int * max(1, len(ctrls)))(*ctrl_states)
+    _call("qc_apply_ctrl", h, c, s, len(ctrls), target, p)
+
+
+def qc_apply_fused_k(h: int, qubits: Sequence[int], U, prec: int = QC_PREC_NATIVE) -> None:
+    k = len(qubits)
+    a, p = _mat(U, 1 << k)
+    q = (ctypes.c_int * k)(*qubits)
+    _call("qc_apply_fused_k", h, q, k, p, prec)
+
+
+# ---------------------------------------------------------------------------
+# measurement, probabilities, sampling, expectations
+# ---------------------------------------------------------------------------
+
+def qc_measure(h: int, q: int, u: float):
+    o, p = ctypes.c_int(), ctypes.c_double()
+    _call("qc_measure", h, q, float(u), ctypes.byref(o), ctypes.byref(p))
+    return o.value, p.value
+
+
+def qc_collapse(h: int, q: int, outcome: int) -> float:
+    p = ctypes.c_double()
+    _call("qc_collapse", h, q, outcome, ctypes.byref(p))
+    return p.value
+
+
+def qc_outcome_prob(h: int, q: int, outcome: int) -> float:
+    p = ctypes.c_double()
+    _call("qc_outcome_prob", h, q, outcome, ctypes.byref(p))
+    return p.value
+
+
+def qc_probs(h: int, out) -> None:
+    _call("qc_probs", h, _ptr(out))
+
+
+def qc_sample(h: int, u, shots: int, out) -> None:
+    _call("qc_sample", h, _ptr(u), int(shots), _ptr(out))
+
+
+def qc_sample_probs(h: int, p, n: int, u, shots: int, out) -> None:
+    _call("qc_sample_probs", h, _ptr(p), n, _ptr(u), int(shots), _ptr(out))
+
+
+def _strings(strings: Sequence[str]):
+    enc = [s.encode() for s in strings]
+    arr = (ctypes.c_char_p * max(1, len(enc)))(*enc)
+    return enc, arr
+
+
+def qc_expect_pauli(h: int, strings: Sequence[str], coeffs=None) -> np.ndarray:
+    enc, arr = _strings(strings)
+    out = np.zeros(len(strings))
+    c = None
+    if coeffs is not None:
+        c = np.ascontiguousarray(coeffs, dtype=np.float64)
+    _call("qc_expect_pauli", h, arr, None if c is None else c.ctypes.data_as(_D), len(strings),
+          out.ctypes.data_as(_D))
+    return out
+
+
+# ---------------------------------------------------------------------------
+# circuits
+# ---------------------------------------------------------------------------
+
+class Circuit:
+    """A qc_circuit built from workload descriptions (kind names as in
+    ``workloads.Op``); matrices of 'u1q' / 'u2q' / 'ctrl' ops go to the FP64 pool.
+    Holds the ctypes arrays alive."""
+
+    def __init__(self, n: int, ops):
+        self.n = n
+        pool = []
+        arr = (qc_op * max(1, len(ops)))()
+        for i, o in enumerate(ops):
+            kind = o.kind
+            adj = kind.endswith("_dag")
+            if adj:
+                kind = kind[:-4]
+            if kind not in GATE:
+                raise ValueError("gate kind %r has no C-ABI code" % kind)
+            r = arr[i]
+            r.kind = GATE[kind]
+            r.nq = len(o.qubits)
+            if r.nq > MAX_OP_QUBITS:
+                raise ValueError("too many qubits in op %d" % i)
+            for j, q in enumerate(o.qubits):
+                r.qubits[j] = int(q)
+            st = 0
+            if o.ctrl_states is not None:
+                for j, b in enumerate(o.ctrl_states):
+                    st |= (int(b) & 1) << j
+            elif kind in ("mcx", "ctrl"):
+                st = (1 << (r.nq - 1)) - 1
+            r.ctrl_states = st
+            r.adjoint = 1 if adj else 0
+            r.param = -1 if o.param_index is None else int(o.param_index)
+            for j, a in enumerate(o.params[:3]):
+                r.angle[j] = float(a)
+            r.matrix = -1
+            if o.matrix is not None:
+                r.matrix = len(pool)
+                pool.extend(np.ascontiguousarray(o.matrix, dtype=np.complex128).view(np.float64).ravel().tolist())
+        self._ops = arr
+        self._pool = np.ascontiguousarray(pool if pool else [0.0], dtype=np.float64)
+        self.c = qc_circuit(n, len(ops), arr, self._pool.ctypes.data_as(_D), len(pool))
+
+
+def qc_run_circuit(h: int, circuit: Circuit, params=None, mode: int = QC_RUN_PER_GATE,
+                   prec: int = QC_PREC_NATIVE) -> None:
+    p = None
+    if params is not None:
+        params = np.ascontiguousarray(params, dtype=np.float64)
+        p = params.ctypes.data_as(_D)
+    _call("qc_run_circuit", h, ctypes.byref(circuit.c), p, mode, prec)
+
+
+def qc_adjoint_grad(circuit: Circuit, params, strings: Sequence[str], coeffs, dtype: int, stream=None):
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    enc, arr = _strings(strings)
+    c = np.ascontiguousarray(coeffs if coeffs is not None else np.ones(len(strings)), dtype=np.float64)
+    e = ctypes.c_double()
+    g = np.zeros(params.size)
+    _call("qc_adjoint_grad", ctypes.byref(circuit.c), params.ctypes.data_as(_D), params.size, arr,
+          c.ctypes.data_as(_D), len(strings), dtype, _stream(stream), ctypes.byref(e), g.ctypes.data_as(_D))
+    return e.value, g
+
+
+def qc_run_batch(ns, layers: int, param_offsets, dev_params, nparams: int, out, stream=None) -> None:
+    ns = np.ascontiguousarray(ns, dtype=np.int32)
+    offs = np.ascontiguousarray(param_offsets, dtype=np.int64)
+    b = qc_batch(len(ns), layers, ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                 offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _ptr(dev_params), int(nparams))
+    _call("qc_run_batch", ctypes.byref(b), _stream(stream), _ptr(out))

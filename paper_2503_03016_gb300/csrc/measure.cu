@@ -1,0 +1,557 @@
+// Measurement, probabilities and sampling (QCLAB Sec. 3.3).
+//
+//  * P(o) = sum_{i : bit_q(i) = o} |psi_i|^2, reduced per block in FP64 and summed in a
+//    fixed order (deterministic).
+//  * Collapse keeps the outcome's half and divides it by sqrt(P(o)) in FP64.
+//  * Sampling draws min{k : u*T < cdf_k}.  The prefix sums are exact: every FP64
+//    p_i is converted to a 128-bit fixed-point integer (unit 2^-118), integer sums are
+//    associative, so any blocking gives the same cdf_k = round-to-nearest(exact
+//    prefix), which is what the sequential double-double oracle approximates to
+//    ~2^-100 relative.  The table kept between kernels is one 128-bit sum per leaf
+//    of 64 amplitudes; each shot re-derives its leaf's 64 prefix values with one warp.
+#include <cmath>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace qcgb {
+
+// ---------------------------------------------------------------------------
+// P(0), P(1) partials
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256) k_outcome_partials(const R* __restrict__ a, uint64_t N, uint64_t m,
+                                                          double* partials) {
+  double s0 = 0.0, s1 = 0.0;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  if (N >= 2) {
+    // two neighbouring amplitudes per step
+    for (uint64_t it = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; it < N / 2; it += stride) {
+      const uint64_t i = 2 * it;
+      Cplx<R> x0, x1;
+      ld_amp2<R>(a, i, x0, x1);
+      const double p0 = double(x0.re) * double(x0.re) + double(x0.im) * double(x0.im);
+      const double p1 = double(x1.re) * double(x1.re) + double(x1.im) * double(x1.im);
+      if (m == 1) {
+        s0 += p0;
+        s1 += p1;
+      } else if (i & m) {
+        s1 += p0 + p1;
+      } else {
+        s0 += p0 + p1;
+      }
+    }
+  }
+  s0 = block_sum(s0);
+  s1 = block_sum(s1);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = s0;
+    partials[2 * blockIdx.x + 1] = s1;
+  }
+}
+
+__global__ void k_sum2(const double* partials, int count, double* out) {
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    a += partials[2 * i];
+    b += partials[2 * i + 1];
+  }
+  a = block_sum(a);
+  b = block_sum(b);
+  if (threadIdx.x == 0) {
+    out[0] = a;
+    out[1] = b;
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_collapse(R* __restrict__ a, uint64_t N, uint64_t m, int outcome,
+                                                  double s) {
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < N; i += stride) {
+    const int b = (i & m) ? 1 : 0;
+    Cplx<R> v = ld_amp<R>(a, i);
+    if (b != outcome) {
+      v.re = R(0);
+      v.im = R(0);
+    } else {
+      v.re = R(__ddiv_rn(double(v.re), s));
+      v.im = R(__ddiv_rn(double(v.im), s));
+    }
+    st_amp<R>(a, i, v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// probabilities
+// ---------------------------------------------------------------------------
+template <typename R>
+__global__ void __launch_bounds__(256) k_probs(const R* __restrict__ a, uint64_t N, double* __restrict__ p) {
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  if (N == 1) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      Cplx<R> v = ld_amp<R>(a, 0);
+      p[0] = prob_fp64(double(v.re), double(v.im));
+    }
+    return;
+  }
+  for (uint64_t it = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; it < N / 2; it += stride) {
+    Cplx<R> x0, x1;
+    ld_amp2<R>(a, 2 * it, x0, x1);
+    reinterpret_cast<double2*>(p)[it] =
+        make_double2(prob_fp64(double(x0.re), double(x0.im)), prob_fp64(double(x1.re), double(x1.im)));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// exact prefix sums in 128-bit fixed point (unit 2^-118, sums below 2^10)
+// ---------------------------------------------------------------------------
+struct U128 {
+  uint64_t lo, hi;
+};
+__device__ __forceinline__ U128 add128(U128 a, U128 b) {
+  U128 r;
+  r.lo = a.lo + b.lo;
+  r.hi = a.hi + b.hi + (r.lo < a.lo ? 1ull : 0ull);
+  return r;
+}
+__device__ __forceinline__ U128 shfl_up128(U128 v, int d) {
+  U128 r;
+  r.lo = __shfl_up_sync(0xffffffffu, v.lo, d);
+  r.hi = __shfl_up_sync(0xffffffffu, v.hi, d);
+  return r;
+}
+__device__ __forceinline__ U128 shfl128(U128 v, int src) {
+  U128 r;
+  r.lo = __shfl_sync(0xffffffffu, v.lo, src);
+  r.hi = __shfl_sync(0xffffffffu, v.hi, src);
+  return r;
+}
+
+// p (finite, >= 0) in units of 2^-118, bits below the unit truncated.
+__device__ __forceinline__ U128 to_fixed(double p) {
+  const uint64_t b = uint64_t(__double_as_longlong(p));
+  const int e = int((b >> 52) & 0x7FF);
+  U128 r{0, 0};
+  if (e == 0) return r;  // zero or subnormal (< 2^-1022): below the unit
+  const uint64_t m = (b & ((1ull << 52) - 1)) | (1ull << 52);
+  const int sh = e - 957;  // p = m * 2^(e-1075) = m * 2^(e-957) units
+  if (sh >= 0) {
+    if (sh >= 64) {
+      r.hi = m << (sh - 64);
+    } else {
+      r.lo = m << sh;
+      r.hi = sh == 0 ? 0 : (m >> (64 - sh));
+    }
+  } else if (sh > -64) {
+    r.lo = m >> (-sh);
+  }
+  return r;
+}
+
+// round-to-nearest-even conversion back to FP64
+__device__ __forceinline__ double from_fixed(U128 x) {
+  if (x.hi == 0 && x.lo < (1ull << 53)) return ldexp(double(x.lo), -118);  // exact
+  int h = x.hi ? 127 - __clzll(x.hi) : 63 - __clzll(x.lo);                // top bit
+  const int sh = h - 52;                                                    // >= 1
+  uint64_t mant, rem_hi_bit, rem_rest;
+  // mant = x >> sh (53 bits)
+  if (sh >= 64) {
+    mant = x.hi >> (sh - 64);
+  } else {
+    mant = (x.lo >> sh) | (x.hi << (64 - sh));
+  }
+  // the bit just below the kept bits, and whether anything below it is set
+  const int hb = sh - 1;
+  if (hb >= 64) {
+    rem_hi_bit = (x.hi >> (hb - 64)) & 1;
+    rem_rest = (x.lo != 0) || ((hb - 64) > 0 && (x.hi & ((1ull << (hb - 64)) - 1)) != 0);
+  } else {
+    rem_hi_bit = (x.lo >> hb) & 1;
+    rem_rest = hb > 0 && (x.lo & ((1ull << hb) - 1)) != 0;
+  }
+  if (rem_hi_bit && (rem_rest || (mant & 1))) mant += 1;
+  return ldexp(double(mant), sh - 118);
+}
+
+// Sources of p_i: amplitudes (p = re*re + im*im in FP64) or a probability vector.
+template <typename R>
+struct AmpSource {
+  const R* a;
+  __device__ __forceinline__ void load2(uint64_t i, double& p0, double& p1) const {
+    Cplx<R> x0, x1;
+    ld_amp2<R>(a, i, x0, x1);
+    p0 = prob_fp64(double(x0.re), double(x0.im));
+    p1 = prob_fp64(double(x1.re), double(x1.im));
+  }
+  __device__ __forceinline__ double load1(uint64_t i) const {
+    Cplx<R> x = ld_amp<R>(a, i);
+    return prob_fp64(double(x.re), double(x.im));
+  }
+};
+struct ProbSource {
+  const double* p;
+  __device__ __forceinline__ void load2(uint64_t i, double& p0, double& p1) const {
+    double2 v = reinterpret_cast<const double2*>(p)[i >> 1];
+    p0 = v.x;
+    p1 = v.y;
+  }
+  __device__ __forceinline__ double load1(uint64_t i) const { return p[i]; }
+};
+
+constexpr int kLeaf = 64;  // amplitudes per leaf: two per lane of one warp
+
+// lane's two fixed-point values of leaf `leaf` (leaf size `ls` = min(64, N))
+template <typename Src>
+__device__ __forceinline__ void leaf_values(const Src& src, uint64_t leaf, int ls, int lane, U128& v0, U128& v1) {
+  const uint64_t i = leaf * uint64_t(ls) + 2 * lane;
+  v0 = U128{0, 0};
+  v1 = U128{0, 0};
+  if (2 * lane + 1 < ls) {
+    double p0, p1;
+    src.load2(i, p0, p1);
+    v0 = to_fixed(p0);
+    v1 = to_fixed(p1);
+  } else if (2 * lane < ls) {
+    v0 = to_fixed(src.load1(i));
+  }
+}
+
+__device__ __forceinline__ U128 warp_sum128(U128 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    U128 t;
+    t.lo = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    t.hi = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    v = add128(v, t);
+  }
+  return v;
+}
+
+// K1: one warp per leaf -> leaf sum
+template <typename Src>
+__global__ void __launch_bounds__(256) k_leaf_sums(Src src, uint64_t nleaf, int ls, U128* __restrict__ sums) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  for (uint64_t leaf = warp; leaf < nleaf; leaf += nwarps) {
+    U128 v0, v1;
+    leaf_values(src, leaf, ls, lane, v0, v1);
+    U128 t = warp_sum128(add128(v0, v1));
+    if (lane == 0) sums[leaf] = t;
+  }
+}
+
+// K2a: per chunk of leaves, the chunk total
+constexpr int kScanBlock = 256;
+constexpr int kChunk = 4096;  // leaves per chunk
+
+__device__ __forceinline__ U128 block_exclusive_scan128(U128 v, U128* total) {
+  __shared__ U128 wsum[kScanBlock / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  U128 inc = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    U128 t = shfl_up128(inc, d);
+    if (lane >= d) inc = add128(inc, t);
+  }
+  __syncthreads();
+  if (lane == 31) wsum[w] = inc;
+  __syncthreads();
+  U128 off{0, 0}, tot{0, 0};
+  for (int j = 0; j < kScanBlock / 32; ++j) {
+    if (j < w) off = add128(off, wsum[j]);
+    tot = add128(tot, wsum[j]);
+  }
+  *total = tot;
+  U128 exc = shfl_up128(inc, 1);
+  if (lane == 0) exc = U128{0, 0};
+  return add128(off, exc);
+}
+
+__global__ void __launch_bounds__(kScanBlock) k_chunk_sums(const U128* __restrict__ sums, uint64_t nleaf,
+                                                           U128* __restrict__ chunk) {
+  const uint64_t base = uint64_t(blockIdx.x) * kChunk;
+  U128 acc{0, 0};
+  for (int j = threadIdx.x; j < kChunk; j += kScanBlock) {
+    const uint64_t b = base + j;
+    if (b < nleaf) acc = add128(acc, sums[b]);
+  }
+  U128 tot;
+  block_exclusive_scan128(acc, &tot);
+  if (threadIdx.x == 0) chunk[blockIdx.x] = tot;
+}
+
+// K2b: exclusive scan of the chunk totals (one block); chunk[nchunk] = grand total
+__global__ void __launch_bounds__(kScanBlock) k_scan_chunks(U128* chunk, int nchunk) {
+  const int per = (nchunk + kScanBlock - 1) / kScanBlock;
+  const int beg = threadIdx.x * per;
+  U128 acc{0, 0};
+  for (int j = 0; j < per; ++j)
+    if (beg + j < nchunk) acc = add128(acc, chunk[beg + j]);
+  U128 tot;
+  U128 off = block_exclusive_scan128(acc, &tot);
+  __syncthreads();
+  for (int j = 0; j < per; ++j)
+    if (beg + j < nchunk) {
+      U128 v = chunk[beg + j];
+      chunk[beg + j] = off;
+      off = add128(off, v);
+    }
+  if (threadIdx.x == 0) chunk[nchunk] = tot;
+}
+
+// K2c: leaf exclusive offsets (in place) and the rounded cdf at each leaf's end
+__global__ void __launch_bounds__(kScanBlock) k_leaf_offsets(U128* __restrict__ sums, uint64_t nleaf,
+                                                             const U128* __restrict__ chunk,
+                                                             double* __restrict__ leaf_end) {
+  const uint64_t base = uint64_t(blockIdx.x) * kChunk;
+  constexpr int per = kChunk / kScanBlock;
+  const uint64_t beg = base + uint64_t(threadIdx.x) * per;
+  U128 acc{0, 0};
+  for (int j = 0; j < per; ++j)
+    if (beg + j < nleaf) acc = add128(acc, sums[beg + j]);
+  U128 tot;
+  U128 off = add128(block_exclusive_scan128(acc, &tot), chunk[blockIdx.x]);
+  for (int j = 0; j < per; ++j)
+    if (beg + j < nleaf) {
+      const U128 v = sums[beg + j];
+      sums[beg + j] = off;
+      off = add128(off, v);
+      leaf_end[beg + j] = from_fixed(off);
+    }
+}
+
+// K3: one warp per shot.
+template <typename Src>
+__global__ void __launch_bounds__(256) k_draw(Src src, uint64_t nleaf, int ls, const U128* __restrict__ leaf_off,
+                                              const double* __restrict__ leaf_end, const double* __restrict__ u,
+                                              int64_t shots, uint64_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
+  const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  const double T = leaf_end[nleaf - 1];
+  for (uint64_t s = warp; s < uint64_t(shots); s += nwarps) {
+    const double t = u[s] * T;
+    const bool below = t < T;
+    // first leaf whose end value passes the test (lane 0 searches, then broadcast)
+    uint64_t leaf = 0;
+    if (lane == 0) {
+      uint64_t lo = 0, hi = nleaf - 1;
+      while (lo < hi) {
+        const uint64_t mid = lo + (hi - lo) / 2;
+        const double c = leaf_end[mid];
+        if (below ? (t < c) : (c >= T))
+          hi = mid;
+        else
+          lo = mid + 1;
+      }
+      leaf = lo;
+    }
+    leaf = __shfl_sync(0xffffffffu, leaf, 0);
+    U128 v0, v1;
+    leaf_values(src, leaf, ls, lane, v0, v1);
+    // inclusive scan of the lane pairs
+    U128 inc = add128(v0, v1);
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      U128 x = shfl_up128(inc, d);
+      if (lane >= d) inc = add128(inc, x);
+    }
+    U128 exc = shfl_up128(inc, 1);
+    if (lane == 0) exc = U128{0, 0};
+    const U128 c0 = add128(add128(leaf_off[leaf], exc), v0);  // cdf of element 2*lane
+    const U128 c1 = add128(c0, v1);                           // cdf of element 2*lane+1
+    const bool valid0 = 2 * lane < ls, valid1 = 2 * lane + 1 < ls;
+    const double d0 = from_fixed(c0), d1 = from_fixed(c1);
+    const bool hit0 = valid0 && (below ? (t < d0) : (d0 >= T));
+    const bool hit1 = valid1 && (below ? (t < d1) : (d1 >= T));
+    const unsigned bal = __ballot_sync(0xffffffffu, hit0 || hit1);
+    const int first = __ffs(bal) - 1;  // leaf_end[leaf] passes, so some lane hits
+    if (lane == first) out[s] = leaf * uint64_t(ls) + 2 * lane + (hit0 ? 0 : 1);
+  }
+}
+
+template <typename Src>
+static qc_status sample_impl(qc_state* s, uint64_t N, const Src& src, const double* u, int64_t shots,
+                             uint64_t* out) {
+  const int ls = int(N < uint64_t(kLeaf) ? N : uint64_t(kLeaf));
+  const uint64_t nleaf = N / ls;
+  const uint64_t nchunk = (nleaf + kChunk - 1) / kChunk;
+  const size_t sums_b = ((nleaf * sizeof(U128)) + 255) & ~size_t(255);
+  const size_t chunk_b = (((nchunk + 1) * sizeof(U128)) + 255) & ~size_t(255);
+  const size_t end_b = ((nleaf * sizeof(double)) + 255) & ~size_t(255);
+  void* scr = nullptr;
+  if (qc_status st = state_scratch(s, sums_b + chunk_b + end_b, &scr)) return st;
+  U128* sums = reinterpret_cast<U128*>(scr);
+  U128* chunk = reinterpret_cast<U128*>(reinterpret_cast<char*>(scr) + sums_b);
+  double* leaf_end = reinterpret_cast<double*>(reinterpret_cast<char*>(scr) + sums_b + chunk_b);
+  const unsigned g1 = stream_grid(nleaf * 32, 256, 8);
+  QC_COUNT(), k_leaf_sums<Src><<<g1, 256, 0, s->stream>>>(src, nleaf, ls, sums);
+  QC_COUNT(), k_chunk_sums<<<unsigned(nchunk), kScanBlock, 0, s->stream>>>(sums, nleaf, chunk);
+  QC_COUNT(), k_scan_chunks<<<1, kScanBlock, 0, s->stream>>>(chunk, int(nchunk));
+  QC_COUNT(), k_leaf_offsets<<<unsigned(nchunk), kScanBlock, 0, s->stream>>>(sums, nleaf, chunk, leaf_end);
+  if (shots > 0) {
+    const unsigned g3 = stream_grid(uint64_t(shots) * 32, 256, 8);
+    QC_COUNT(), k_draw<Src><<<g3, 256, 0, s->stream>>>(src, nleaf, ls, sums, leaf_end, u, shots, out);
+  }
+  return check_launch("sampling");
+}
+
+}  // namespace qcgb
+
+using namespace qcgb;
+
+extern "C" {
+
+static qc_status outcome_sums(qc_state* s, int q, double* P0, double* P1) {
+  const uint64_t N = state_len(s);
+  const uint64_t m = uint64_t(1) << (s->n - 1 - q);
+  const unsigned g = stream_grid(N / 2 ? N / 2 : 1, 256, 8);
+  void* scr = nullptr;
+  if (qc_status st = state_scratch(s, sizeof(double) * (2 * g + 2), &scr)) return st;
+  double* part = reinterpret_cast<double*>(scr);
+  if (!s->host_buf) {
+    if (qc_status st = check_cuda(cudaMallocHost(&s->host_buf, 4 * sizeof(double)), "pinned buffer")) return st;
+  }
+  if (s->dtype == QC_C64)
+    QC_COUNT(), k_outcome_partials<float><<<g, 256, 0, s->stream>>>(reinterpret_cast<const float*>(s->amps), N, m, part);
+  else
+    QC_COUNT(), k_outcome_partials<double><<<g, 256, 0, s->stream>>>(reinterpret_cast<const double*>(s->amps), N, m, part);
+  QC_COUNT(), k_sum2<<<1, 1024, 0, s->stream>>>(part, int(g), part + 2 * g);
+  if (qc_status st = check_launch("outcome probabilities")) return st;
+  if (qc_status st = check_cuda(cudaMemcpyAsync(s->host_buf, part + 2 * g, 2 * sizeof(double),
+                                                cudaMemcpyDeviceToHost, s->stream),
+                                "D2H"))
+    return st;
+  if (qc_status st = check_cuda(cudaStreamSynchronize(s->stream), "outcome probabilities")) return st;
+  *P0 = s->host_buf[0];
+  *P1 = s->host_buf[1];
+  return QC_OK;
+}
+
+static qc_status check_q(const qc_state* s, int q) {
+  if (!s || !s->amps) {
+    set_error("invalid state handle");
+    return QC_ERR_INVALID_ARG;
+  }
+  if (q < 0 || q >= s->n) {
+    set_error("qubit %d out of range", q);
+    return QC_ERR_INVALID_ARG;
+  }
+  return QC_OK;
+}
+
+static qc_status do_collapse(qc_state* s, int q, int outcome, double P) {
+  const uint64_t N = state_len(s);
+  const uint64_t m = uint64_t(1) << (s->n - 1 - q);
+  const double sc = sqrt(P);
+  const unsigned g = stream_grid(N, 256);
+  if (s->dtype == QC_C64)
+    QC_COUNT(), k_collapse<float><<<g, 256, 0, s->stream>>>(reinterpret_cast<float*>(s->amps), N, m, outcome, sc);
+  else
+    QC_COUNT(), k_collapse<double><<<g, 256, 0, s->stream>>>(reinterpret_cast<double*>(s->amps), N, m, outcome, sc);
+  return check_launch("collapse");
+}
+
+qc_status qc_outcome_prob(const qc_state* cs, int q, int outcome, double* prob) {
+  clear_error();
+  qc_state* s = const_cast<qc_state*>(cs);
+  if (qc_status st = check_q(s, q)) return st;
+  if (!prob || (outcome != 0 && outcome != 1)) {
+    set_error("qc_outcome_prob: invalid arguments");
+    return QC_ERR_INVALID_ARG;
+  }
+  double P0, P1;
+  if (qc_status st = outcome_sums(s, q, &P0, &P1)) return st;
+  *prob = outcome ? P1 : P0;
+  return QC_OK;
+}
+
+qc_status qc_measure(qc_state* s, int q, double u, int* outcome, double* prob) {
+  clear_error();
+  if (qc_status st = check_q(s, q)) return st;
+  if (!outcome || !(u >= 0.0 && u < 1.0)) {
+    set_error("qc_measure: u must be in [0, 1) and outcome non-null");
+    return QC_ERR_INVALID_ARG;
+  }
+  double P0, P1;
+  if (qc_status st = outcome_sums(s, q, &P0, &P1)) return st;
+  const double T = P0 + P1;
+  if (!(T > 0.0)) {
+    set_error("qc_measure: state has zero norm");
+    return QC_ERR_ZERO_PROB;
+  }
+  const int o = (u * T >= P0) ? 1 : 0;
+  const double P = o ? P1 : P0;
+  if (qc_status st = do_collapse(s, q, o, P)) return st;
+  *outcome = o;
+  if (prob) *prob = P / T;
+  return QC_OK;
+}
+
+qc_status qc_collapse(qc_state* s, int q, int outcome, double* prob) {
+  clear_error();
+  if (qc_status st = check_q(s, q)) return st;
+  if (outcome != 0 && outcome != 1) {
+    set_error("qc_collapse: outcome must be 0 or 1");
+    return QC_ERR_INVALID_ARG;
+  }
+  double P0, P1;
+  if (qc_status st = outcome_sums(s, q, &P0, &P1)) return st;
+  const double T = P0 + P1;
+  const double P = outcome ? P1 : P0;
+  const double thr = s->dtype == QC_C64 ? 1e-6 : 1e-12;
+  if (!(T > 0.0) || P / T <= thr) {
+    set_error("qc_collapse: outcome %d has probability %.3g", outcome, T > 0 ? P / T : 0.0);
+    return QC_ERR_ZERO_PROB;
+  }
+  if (qc_status st = do_collapse(s, q, outcome, P)) return st;
+  if (prob) *prob = P / T;
+  return check_cuda(cudaStreamSynchronize(s->stream), "qc_collapse");
+}
+
+qc_status qc_probs(const qc_state* cs, double* dev_out) {
+  clear_error();
+  qc_state* s = const_cast<qc_state*>(cs);
+  if (!s || !s->amps || !dev_out || (reinterpret_cast<uintptr_t>(dev_out) & 15)) {
+    set_error("qc_probs: invalid arguments (output must be 16-byte aligned device memory)");
+    return QC_ERR_INVALID_ARG;
+  }
+  const uint64_t N = state_len(s);
+  const unsigned g = stream_grid(N / 2 ? N / 2 : 1, 256);
+  if (s->dtype == QC_C64)
+    QC_COUNT(), k_probs<float><<<g, 256, 0, s->stream>>>(reinterpret_cast<const float*>(s->amps), N, dev_out);
+  else
+    QC_COUNT(), k_probs<double><<<g, 256, 0, s->stream>>>(reinterpret_cast<const double*>(s->amps), N, dev_out);
+  return check_launch("qc_probs");
+}
+
+qc_status qc_sample(const qc_state* cs, const double* dev_u, int64_t shots, uint64_t* dev_out) {
+  clear_error();
+  qc_state* s = const_cast<qc_state*>(cs);
+  if (!s || !s->amps || shots < 0 || (shots > 0 && (!dev_u || !dev_out))) {
+    set_error("qc_sample: invalid arguments");
+    return QC_ERR_INVALID_ARG;
+  }
+  const uint64_t N = state_len(s);
+  if (s->dtype == QC_C64)
+    return sample_impl(s, N, AmpSource<float>{reinterpret_cast<const float*>(s->amps)}, dev_u, shots, dev_out);
+  return sample_impl(s, N, AmpSource<double>{reinterpret_cast<const double*>(s->amps)}, dev_u, shots, dev_out);
+}
+
+// Sampling from a caller-supplied probability vector (device, N = 2^n doubles, 16-byte
+// aligned, nonnegative, sum below 2^10), with the same rule as qc_sample.  `s`
+// provides the stream and the scratch; its amplitudes are not read.
+qc_status qc_sample_probs(qc_state* s, const double* dev_p, int n, const double* dev_u, int64_t shots,
+                          uint64_t* dev_out) {
+  clear_error();
+  if (!s || !dev_p || n < 1 || n > 34 || shots < 0 || (shots > 0 && (!dev_u || !dev_out)) ||
+      (reinterpret_cast<uintptr_t>(dev_p) & 15)) {
+    set_error("qc_sample_probs: invalid arguments");
+    return QC_ERR_INVALID_ARG;
+  }
+  return sample_impl(s, uint64_t(1) << n, ProbSource{dev_p}, dev_u, shots, dev_out);
+}
+
+}  // extern "C"

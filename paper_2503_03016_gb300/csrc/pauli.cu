@@ -1,0 +1,202 @@
+// Pauli-string expectations <psi| P |psi> (the expectations behind the density-matrix
+// estimate of QCLAB Sec. 5.2, and the Hamiltonians of the gradient workloads).
+//
+// With Y = i X Z per qubit, a string with X-or-Y bits x, Z-or-Y bits z and nY Y's is
+// P = i^nY X^x Z^z, so P|j> = i^nY (-1)^popc(j&z) |j^x> and
+//   <psi|P|psi> = sum_j conj(psi_{j^x}) psi_j i^nY (-1)^popc(j&z).
+// Terms that share x are evaluated in one pass.  For x = 0 the summand is
+// |psi_j|^2 (-1)^popc(j&z).  For x != 0 the pass visits each pair (j, j^x) once (j
+// with the lowest bit of x clear); with w = conj(psi_{j^x}) psi_j the pair contributes
+// 2 (-1)^popc(j&z) * {Re w, -Im w, -Re w, Im w}[nY mod 4].
+// Accumulation: complex64 states accumulate up to 16 terms per thread in FP32 before
+// each FP64 add; complex128 accumulates in FP64 throughout; the cross-thread and
+// cross-block reductions are FP64 in a fixed order.
+#include <string.h>
+
+#include <map>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace qcgb {
+
+constexpr int kMaxTermsPerPass = 16;
+
+struct PauliGroup {
+  uint64_t xmask;
+  int hbit;  // lowest set bit of xmask (-1 when xmask == 0)
+  int nt;
+  uint64_t z[kMaxTermsPerPass];
+  int mode[kMaxTermsPerPass];  // nY mod 4
+  int slot[kMaxTermsPerPass];  // output position of each term
+};
+
+template <typename R>
+__global__ void __launch_bounds__(256) k_pauli(const R* __restrict__ a, uint64_t N, PauliGroup g,
+                                               double* __restrict__ partials) {
+  using Acc = R;  // per-thread short-run accumulator
+  double acc[kMaxTermsPerPass];
+  Acc run[kMaxTermsPerPass];
+#pragma unroll
+  for (int t = 0; t < kMaxTermsPerPass; ++t) {
+    acc[t] = 0.0;
+    run[t] = Acc(0);
+  }
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  int cnt = 0;
+  if (g.hbit < 0) {
+    for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < N; i += stride) {
+      const Cplx<R> v = ld_amp<R>(a, i);
+      const R p = v.re * v.re + v.im * v.im;
+#pragma unroll
+      for (int t = 0; t < kMaxTermsPerPass; ++t)
+        if (t < g.nt) run[t] += (__popcll(i & g.z[t]) & 1) ? -p : p;
+      if (++cnt == 16) {
+#pragma unroll
+        for (int t = 0; t < kMaxTermsPerPass; ++t) {
+          acc[t] += double(run[t]);
+          run[t] = Acc(0);
+        }
+        cnt = 0;
+      }
+    }
+  } else {
+    const uint64_t lo = (uint64_t(1) << g.hbit) - 1;
+    for (uint64_t it = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; it < N / 2; it += stride) {
+      const uint64_t j = ((it & ~lo) << 1) | (it & lo);
+      const Cplx<R> x = ld_amp<R>(a, j), y = ld_amp<R>(a, j ^ g.xmask);
+      // w = conj(y) * x
+      const R wr = y.re * x.re + y.im * x.im;
+      const R wi = y.re * x.im - y.im * x.re;
+#pragma unroll
+      for (int t = 0; t < kMaxTermsPerPass; ++t) {
+        if (t < g.nt) {
+          const int m = g.mode[t];
+          R v = (m & 1) ? wi : wr;
+          if (m == 1 || m == 2) v = -v;
+          run[t] += (__popcll(j & g.z[t]) & 1) ? -v : v;
+        }
+      }
+      if (++cnt == 16) {
+#pragma unroll
+        for (int t = 0; t < kMaxTermsPerPass; ++t) {
+          acc[t] += 2.0 * double(run[t]);
+          run[t] = Acc(0);
+        }
+        cnt = 0;
+      }
+    }
+  }
+  const double scale = g.hbit < 0 ? 1.0 : 2.0;
+#pragma unroll
+  for (int t = 0; t < kMaxTermsPerPass; ++t) {
+    double v = acc[t] + scale * double(run[t]);
+    if (t < g.nt) {
+      v = block_sum(v);
+      if (threadIdx.x == 0) partials[size_t(blockIdx.x) * kMaxTermsPerPass + t] = v;
+    }
+  }
+}
+
+__global__ void k_sum_terms(const double* partials, int nblocks, PauliGroup g, double* out) {
+  for (int t = 0; t < g.nt; ++t) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += partials[size_t(i) * kMaxTermsPerPass + t];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) out[g.slot[t]] = acc;
+    __syncthreads();
+  }
+}
+
+struct ParsedTerm {
+  uint64_t x, z;
+  int ny;
+};
+
+qc_status parse_pauli(int n, const char* str, ParsedTerm* out) {
+  if (!str || int(strlen(str)) != n) {
+    set_error("Pauli string must have exactly n=%d characters", n);
+    return QC_ERR_INVALID_ARG;
+  }
+  ParsedTerm t{0, 0, 0};
+  for (int q = 0; q < n; ++q) {
+    const uint64_t b = uint64_t(1) << (n - 1 - q);
+    switch (str[q]) {
+      case 'I': case 'i': break;
+      case 'X': case 'x': t.x |= b; break;
+      case 'Z': case 'z': t.z |= b; break;
+      case 'Y': case 'y': t.x |= b; t.z |= b; t.ny++; break;
+      default:
+        set_error("invalid Pauli character '%c'", str[q]);
+        return QC_ERR_INVALID_ARG;
+    }
+  }
+  *out = t;
+  return QC_OK;
+}
+
+// values[t] = <psi|P_t|psi> (no coefficients), device buffer `dev_vals` of nterms
+qc_status expect_terms_device(qc_state* s, const ParsedTerm* terms, int nterms, double* dev_vals) {
+  const uint64_t N = state_len(s);
+  std::map<uint64_t, std::vector<int>> groups;
+  for (int t = 0; t < nterms; ++t) groups[terms[t].x].push_back(t);
+  const int B = 256;
+  const unsigned g = stream_grid(N, B, 8);
+  void* scr = nullptr;
+  if (qc_status st = state_scratch(s, sizeof(double) * size_t(g) * kMaxTermsPerPass + 256, &scr)) return st;
+  double* part = reinterpret_cast<double*>(scr);
+  for (auto& kv : groups) {
+    const std::vector<int>& idx = kv.second;
+    for (size_t beg = 0; beg < idx.size(); beg += kMaxTermsPerPass) {
+      PauliGroup pg{};
+      pg.xmask = kv.first;
+      pg.hbit = kv.first ? __builtin_ctzll(kv.first) : -1;
+      pg.nt = int(std::min<size_t>(kMaxTermsPerPass, idx.size() - beg));
+      for (int j = 0; j < pg.nt; ++j) {
+        pg.z[j] = terms[idx[beg + j]].z;
+        pg.mode[j] = terms[idx[beg + j]].ny & 3;
+        pg.slot[j] = idx[beg + j];
+      }
+      if (s->dtype == QC_C64)
+        QC_COUNT(), k_pauli<float><<<g, B, 0, s->stream>>>(reinterpret_cast<const float*>(s->amps), N, pg, part);
+      else
+        QC_COUNT(), k_pauli<double><<<g, B, 0, s->stream>>>(reinterpret_cast<const double*>(s->amps), N, pg, part);
+      QC_COUNT(), k_sum_terms<<<1, 1024, 0, s->stream>>>(part, int(g), pg, dev_vals);
+    }
+  }
+  return check_launch("Pauli expectation");
+}
+
+}  // namespace qcgb
+
+using namespace qcgb;
+
+extern "C" qc_status qc_expect_pauli(const qc_state* cs, const char* const* strings, const double* coeffs,
+                                     int nterms, double* host_out) {
+  clear_error();
+  qc_state* s = const_cast<qc_state*>(cs);
+  if (!s || !s->amps || nterms < 0 || (nterms > 0 && (!strings || !host_out))) {
+    set_error("qc_expect_pauli: invalid arguments");
+    return QC_ERR_INVALID_ARG;
+  }
+  if (nterms == 0) return QC_OK;
+  std::vector<ParsedTerm> terms(nterms);
+  for (int t = 0; t < nterms; ++t)
+    if (qc_status st = parse_pauli(s->n, strings[t], &terms[t])) return st;
+  double* dev = nullptr;
+  if (qc_status st = check_cuda(cudaMallocAsync(reinterpret_cast<void**>(&dev),
+                                                sizeof(double) * nterms, s->stream),
+                                "expectation buffer"))
+    return st;
+  qc_status st = expect_terms_device(s, terms.data(), nterms, dev);
+  std::vector<double> vals(nterms);
+  if (st == QC_OK)
+    st = check_cuda(cudaMemcpyAsync(vals.data(), dev, sizeof(double) * nterms, cudaMemcpyDeviceToHost, s->stream),
+                    "D2H");
+  cudaFreeAsync(dev, s->stream);
+  if (st == QC_OK) st = check_cuda(cudaStreamSynchronize(s->stream), "qc_expect_pauli");
+  if (st != QC_OK) return st;
+  for (int t = 0; t < nterms; ++t) host_out[t] = vals[t] * (coeffs ? coeffs[t] : 1.0);
+  return QC_OK;
+}
