@@ -324,7 +324,10 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--cpu-gates", type=int, default=24)
     ap.add_argument("--ref-gates", type=int, default=8)
+    ap.add_argument("--qubits", type=int, default=28, help="smaller cases for profiling only")
     args = ap.parse_args()
+    global N_QUBITS
+    N_QUBITS = args.qubits
     if args.impl == "reference":
         run_reference(args)
     else:
