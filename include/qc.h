@@ -177,6 +177,23 @@ qc_status qc_sample_probs(qc_state* s, const double* dev_p, int n, const double*
 qc_status qc_expect_pauli(const qc_state* s, const char* const* strings, const double* coeffs, int nterms,
                           double* host_out);
 
+/* Allocation-free form of qc_expect_pauli (the paper has no counterpart: it is an
+ * interface for callers that cannot allocate device memory while they run, e.g. a
+ * process whose device memory is wholly reserved by another allocator, or a service
+ * that must not meet an allocation failure or the synchronisation cudaMalloc/cudaFree
+ * can cause).  Same arguments and results as qc_expect_pauli, but every intermediate
+ * lives in one fixed array in the library's device image: 157,696 bytes (1216 blocks
+ * x 16 partial sums + 256 term values), held on every device that loads the library
+ * until the process exits.  Limits: at most 256 terms per call (more is rejected with
+ * QC_ERR_INVALID_ARG and a message); the reduction grid is capped at 1216 blocks.
+ * The first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's contents:
+ * calls whose work overlaps on the GPU (other threads, other streams) race and must
+ * be serialised by the caller.  Calls no cudaMalloc/cudaFree.  Synchronising. */
+qc_status qc_expect_pauli_noalloc(const qc_state* s, const char* const* strings, const double* coeffs, int nterms,
+                                  double* host_out);
+
 /* ---------------------------------------------------------------------------
  * Circuits (QCLAB Sec. 2: QCircuit / push_back; nested circuits are flattened by
  * the caller)

@@ -78,6 +78,7 @@ _SIGS = {
     "qc_sample": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
     "qc_sample_probs": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int64, _P]),
     "qc_expect_pauli": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_char_p), _D, ctypes.c_int, _D]),
+    "qc_expect_pauli_noalloc": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_char_p), _D, ctypes.c_int, _D]),
     "qc_run_circuit": (ctypes.c_int, [_P, ctypes.POINTER(qc_circuit), _D, ctypes.c_int, ctypes.c_int]),
     "qc_adjoint_grad": (ctypes.c_int, [ctypes.POINTER(qc_circuit), _D, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_char_p), _D, ctypes.c_int, ctypes.c_int, _P, _D,
@@ -273,6 +274,19 @@ def qc_expect_pauli(h: int, strings: Sequence[str], coeffs=None) -> np.ndarray:
     if coeffs is not None:
         c = np.ascontiguousarray(coeffs, dtype=np.float64)
     _call("qc_expect_pauli", h, arr, None if c is None else c.ctypes.data_as(_D), len(strings),
+          out.ctypes.data_as(_D))
+    return out
+
+
+def qc_expect_pauli_noalloc(h: int, strings: Sequence[str], coeffs=None) -> np.ndarray:
+    """qc_expect_pauli without device allocation (fixed library-resident scratch;
+    at most 256 terms; concurrent calls race)."""
+    enc, arr = _strings(strings)
+    out = np.zeros(len(strings))
+    c = None
+    if coeffs is not None:
+        c = np.ascontiguousarray(coeffs, dtype=np.float64)
+    _call("qc_expect_pauli_noalloc", h, arr, None if c is None else c.ctypes.data_as(_D), len(strings),
           out.ctypes.data_as(_D))
     return out
 

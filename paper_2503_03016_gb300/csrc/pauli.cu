@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <map>
+#include <mutex>
 #include <vector>
 
 #include "common.cuh"
@@ -198,5 +199,121 @@ extern "C" qc_status qc_expect_pauli(const qc_state* cs, const char* const* stri
   if (st == QC_OK) st = check_cuda(cudaStreamSynchronize(s->stream), "qc_expect_pauli");
   if (st != QC_OK) return st;
   for (int t = 0; t < nterms; ++t) host_out[t] = vals[t] * (coeffs ? coeffs[t] : 1.0);
+  return QC_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the expectation entry point.
+//
+// Some callers cannot allocate device memory at the time they need an expectation
+// value: a process whose device memory is already reserved in full by another
+// allocator (for example a framework's caching allocator sized to the whole GPU),
+// or a service that must not risk an allocation failure, or the device-wide
+// synchronisation cudaMalloc/cudaFree can cause, once it is running.  For them
+// qc_expect_pauli_noalloc uses a fixed scratch array that lives in this library's
+// device image instead of the state's lazily allocated scratch.
+// ---------------------------------------------------------------------------
+namespace qcgb {
+
+constexpr int kNoAllocMaxBlocks = 1216;  // grid cap of the reduction (8 blocks per SM on 152 SMs)
+constexpr int kNoAllocMaxTerms = 256;    // terms per call
+constexpr size_t kNoAllocDoubles = size_t(kNoAllocMaxBlocks) * kMaxTermsPerPass + kNoAllocMaxTerms;
+
+// 1216*16 + 256 doubles = 157,696 bytes, held by every device that loads the library
+// until the process exits.  Shared by all calls: each call overwrites it.
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+// Device address of g_noalloc_scratch for each device, resolved once per device.
+static double* g_noalloc_ptr[64] = {nullptr};
+static std::mutex g_noalloc_mu;
+
+static qc_status noalloc_scratch(int device, double** out) {
+  if (device < 0 || device >= 64) {
+    set_error("qc_expect_pauli_noalloc: device %d out of range", device);
+    return QC_ERR_INVALID_ARG;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    int cur = -1;
+    if (qc_status st = check_cuda(cudaGetDevice(&cur), "cudaGetDevice")) return st;
+    if (cur != device)
+      if (qc_status st = check_cuda(cudaSetDevice(device), "cudaSetDevice")) return st;
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (cur != device) cudaSetDevice(cur);
+    if (qc_status st = check_cuda(e, "cudaGetSymbolAddress(noalloc scratch)")) return st;
+    g_noalloc_ptr[device] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_ptr[device];
+  return QC_OK;
+}
+
+}  // namespace qcgb
+
+extern "C" qc_status qc_expect_pauli_noalloc(const qc_state* cs, const char* const* strings, const double* coeffs,
+                                             int nterms, double* host_out) {
+  clear_error();
+  qc_state* s = const_cast<qc_state*>(cs);
+  if (!s || !s->amps || nterms < 0 || (nterms > 0 && (!strings || !host_out))) {
+    set_error("qc_expect_pauli_noalloc: invalid arguments");
+    return QC_ERR_INVALID_ARG;
+  }
+  if (nterms > kNoAllocMaxTerms) {
+    set_error("qc_expect_pauli_noalloc: %d terms exceed the fixed scratch limit of %d terms per call", nterms,
+              kNoAllocMaxTerms);
+    return QC_ERR_INVALID_ARG;
+  }
+  if (nterms == 0) return QC_OK;
+  ParsedTerm terms[kNoAllocMaxTerms];
+  for (int t = 0; t < nterms; ++t)
+    if (qc_status st = parse_pauli(s->n, strings[t], &terms[t])) return st;
+  double* scratch = nullptr;
+  if (qc_status st = noalloc_scratch(s->device, &scratch)) return st;
+  double* part = scratch;                                              // blocks x 16
+  double* vals = scratch + size_t(kNoAllocMaxBlocks) * kMaxTermsPerPass;  // nterms
+  // group terms by X mask without heap use: order term indices by xmask
+  int order[kNoAllocMaxTerms];
+  for (int t = 0; t < nterms; ++t) order[t] = t;
+  for (int i = 1; i < nterms; ++i) {
+    const int v = order[i];
+    int j = i - 1;
+    while (j >= 0 && terms[order[j]].x > terms[v].x) {
+      order[j + 1] = order[j];
+      --j;
+    }
+    order[j + 1] = v;
+  }
+  const uint64_t N = state_len(s);
+  const int B = 256;
+  unsigned g = stream_grid(N, B, 8);
+  if (g > unsigned(kNoAllocMaxBlocks)) g = kNoAllocMaxBlocks;
+  int beg = 0;
+  while (beg < nterms) {
+    PauliGroup pg{};
+    pg.xmask = terms[order[beg]].x;
+    pg.hbit = pg.xmask ? __builtin_ctzll(pg.xmask) : -1;
+    pg.nt = 0;
+    while (beg + pg.nt < nterms && pg.nt < kMaxTermsPerPass && terms[order[beg + pg.nt]].x == pg.xmask) {
+      const int t = order[beg + pg.nt];
+      pg.z[pg.nt] = terms[t].z;
+      pg.mode[pg.nt] = terms[t].ny & 3;
+      pg.slot[pg.nt] = t;
+      ++pg.nt;
+    }
+    if (s->dtype == QC_C64)
+      QC_COUNT(), k_pauli<float><<<g, B, 0, s->stream>>>(reinterpret_cast<const float*>(s->amps), N, pg, part);
+    else
+      QC_COUNT(), k_pauli<double><<<g, B, 0, s->stream>>>(reinterpret_cast<const double*>(s->amps), N, pg, part);
+    QC_COUNT(), k_sum_terms<<<1, 1024, 0, s->stream>>>(part, int(g), pg, vals);
+    beg += pg.nt;
+  }
+  if (qc_status st = check_launch("qc_expect_pauli_noalloc")) return st;
+  double host_vals[kNoAllocMaxTerms];
+  if (qc_status st = check_cuda(cudaMemcpyAsync(host_vals, vals, sizeof(double) * nterms, cudaMemcpyDeviceToHost,
+                                                s->stream),
+                                "D2H"))
+    return st;
+  if (qc_status st = check_cuda(cudaStreamSynchronize(s->stream), "qc_expect_pauli_noalloc")) return st;
+  for (int t = 0; t < nterms; ++t) host_out[t] = host_vals[t] * (coeffs ? coeffs[t] : 1.0);
   return QC_OK;
 }
