@@ -273,10 +273,7 @@ def run_ours(args):
         st128.free()
 
     sbytes = (1 << N_QUBITS) * 8
-    if args.mode == "fused":
-        passes = P.planner_pass_count() if hasattr(P, "planner_pass_count") else None
-    else:
-        passes = len(ops)
+    passes = P.qc_last_pass_count() if args.mode == "fused" else len(ops)
     algo_bytes = (passes or len(ops)) * 2 * sbytes
     achieved = algo_bytes / (circ_ms * 1e-3) / 1e9
     # cpu baseline (rank 0, N=1 only)

@@ -66,6 +66,9 @@ int qc_abi_version(void);
 /* Number of CUDA kernels this library has launched in this process (all threads);
  * a diagnostic for benchmarks. */
 uint64_t qc_launch_count(void);
+/* Number of tile passes the planner used for the most recent QC_RUN_FUSED circuit
+ * (process-wide; a diagnostic for benchmarks). */
+int qc_last_pass_count(void);
 
 /* ---------------------------------------------------------------------------
  * State handles (QCLAB Sec. 3.1 "Initialization")

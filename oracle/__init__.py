@@ -340,17 +340,25 @@ def energy(n: int, ops, params, strings, coeffs) -> float:
 
 
 def param_shift_grad(n: int, ops, params, strings, coeffs, which=None) -> np.ndarray:
-    """Exact gradient of <H> for rotations exp(-i t G/2) with G^2 = I:
-    d<H>/dt = (<H>(t + pi/2) - <H>(t - pi/2)) / 2."""
+    """Exact gradient of <H> for rotations exp(-i t G/2) with G^2 = I.  For one gate,
+    d<H>/dt = (<H>(t + pi/2) - <H>(t - pi/2)) / 2.  A parameter used by several gates
+    gets the sum of the per-gate rules (chain rule): each occurrence is shifted on
+    its own, through a private copy of the parameter."""
+    from dataclasses import replace
     params = np.asarray(params, dtype=np.float64)
     idx = range(params.size) if which is None else which
     g = []
     for p in idx:
-        a = params.copy()
-        a[p] += np.pi / 2
-        b = params.copy()
-        b[p] -= np.pi / 2
-        g.append(0.5 * (energy(n, ops, a, strings, coeffs) - energy(n, ops, b, strings, coeffs)))
+        total = 0.0
+        for k, op in enumerate(ops):
+            if op.param_index != p:
+                continue
+            own = list(ops)
+            own[k] = replace(op, param_index=params.size)
+            for sgn in (1.0, -1.0):
+                ext = np.append(params, params[p] + sgn * np.pi / 2)
+                total += 0.5 * sgn * energy(n, own, ext, strings, coeffs)
+        g.append(total)
     return np.array(g)
 
 

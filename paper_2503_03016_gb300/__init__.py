@@ -7,3 +7,4 @@ its Python binding (argument marshalling) plus a torch-facing convenience layer.
 from ._binding import *  # noqa: F401,F403
 from ._binding import lib, QCError, Circuit  # noqa: F401
 from .state import State  # noqa: F401
+from .autograd import AdjointExpectation  # noqa: F401,E402

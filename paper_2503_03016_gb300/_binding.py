@@ -57,6 +57,7 @@ _SIGS = {
     "qc_last_error": (ctypes.c_char_p, []),
     "qc_abi_version": (ctypes.c_int, []),
     "qc_launch_count": (ctypes.c_uint64, []),
+    "qc_last_pass_count": (ctypes.c_int, []),
     "qc_state_alloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(_P)]),
     "qc_state_wrap": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, ctypes.POINTER(_P)]),
     "qc_state_free": (ctypes.c_int, [_P]),
@@ -144,6 +145,10 @@ def _mat(U, dim: int):
 
 def qc_launch_count() -> int:
     return int(lib().qc_launch_count())
+
+
+def qc_last_pass_count() -> int:
+    return int(lib().qc_last_pass_count())
 
 
 # ---------------------------------------------------------------------------

@@ -1,0 +1,346 @@
+// Adjoint (reverse-sweep) gradient of E(theta) = <psi(theta)| H |psi(theta)>.
+//
+// The circuit is the paper's gate sequence (Sec. 3.2) with rotation gates
+// U_l = exp(-i theta_l G_l / 2), G in {X, Y, Z}.  With psi_l the state after gate l and
+// lambda_l = U_{l+1}^dag ... U_L^dag H psi_L, dE/dtheta_l = 2 Re <lambda_l| dpsi_l/dtheta_l>
+// = 2 Re <lambda_l| (-i G_l / 2) |psi_l> = Im <lambda_l| G_l |psi_l>.
+// Sweep: psi = U_L ... U_1 |0>, lambda = H psi, E = Re <psi|lambda>; then for l = L..1:
+// g_l = Im <lambda|G_l|psi>, psi <- U_l^dag psi, lambda <- U_l^dag lambda.  For a
+// rotation gate the inner product and both un-applications are one pass over the
+// pairs of the target bit (read 2 states, write 2 states); block partial sums are
+// FP64 and reduced in a fixed order.
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <vector>
+
+#include "circuit.cuh"
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace qcgb {
+
+struct ParsedTermA {
+  uint64_t x, z;
+  int ny;
+};
+
+qc_status parse_pauli_a(int n, const char* str, ParsedTermA* out) {
+  if (!str || int(strlen(str)) != n) {
+    set_error("Pauli string must have exactly n=%d characters", n);
+    return QC_ERR_INVALID_ARG;
+  }
+  ParsedTermA t{0, 0, 0};
+  for (int q = 0; q < n; ++q) {
+    const uint64_t b = uint64_t(1) << (n - 1 - q);
+    switch (str[q]) {
+      case 'I': case 'i': break;
+      case 'X': case 'x': t.x |= b; break;
+      case 'Z': case 'z': t.z |= b; break;
+      case 'Y': case 'y': t.x |= b; t.z |= b; t.ny++; break;
+      default:
+        set_error("invalid Pauli character '%c'", str[q]);
+        return QC_ERR_INVALID_ARG;
+    }
+  }
+  *out = t;
+  return QC_OK;
+}
+
+constexpr int kHTerms = 16;
+struct HGroup {
+  uint64_t x;
+  int nt;
+  int first;  // nonzero: overwrite lambda instead of accumulating
+  uint64_t z[kHTerms];
+  double cre[kHTerms], cim[kHTerms];  // coeff * i^nY
+};
+
+// lambda_k (+)= sum_t c_t i^nY (-1)^popc((k^x) & z_t) psi_{k^x}
+template <typename R>
+__global__ void __launch_bounds__(256) k_apply_hsum(const R* __restrict__ psi, R* __restrict__ lam, uint64_t N,
+                                                    HGroup g) {
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t k = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; k < N; k += stride) {
+    const uint64_t j = k ^ g.x;
+    const Cplx<R> p = ld_amp<R>(psi, j);
+    double fr = 0.0, fi = 0.0;
+    for (int t = 0; t < g.nt; ++t) {
+      const double s = (__popcll(j & g.z[t]) & 1) ? -1.0 : 1.0;
+      fr += s * g.cre[t];
+      fi += s * g.cim[t];
+    }
+    Cplx<R> out{R(fr * double(p.re) - fi * double(p.im)), R(fr * double(p.im) + fi * double(p.re))};
+    if (!g.first) {
+      const Cplx<R> o = ld_amp<R>(lam, k);
+      out.re += o.re;
+      out.im += o.im;
+    }
+    st_amp<R>(lam, k, out);
+  }
+}
+
+// Re and Im of <a|b>, block partials
+template <typename R>
+__global__ void __launch_bounds__(256) k_inner_partials(const R* __restrict__ a, const R* __restrict__ b, uint64_t N,
+                                                        double* partials) {
+  double sr = 0.0, si = 0.0;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < N; i += stride) {
+    const Cplx<R> x = ld_amp<R>(a, i), y = ld_amp<R>(b, i);
+    sr += double(x.re) * double(y.re) + double(x.im) * double(y.im);
+    si += double(x.re) * double(y.im) - double(x.im) * double(y.re);
+  }
+  sr = block_sum(sr);
+  si = block_sum(si);
+  if (threadIdx.x == 0) {
+    partials[2 * blockIdx.x] = sr;
+    partials[2 * blockIdx.x + 1] = si;
+  }
+}
+
+// One reverse step of a rotation on bit `p` with generator G (0 X, 1 Y, 2 Z):
+// partial[block] = Im <lambda|G|psi>; then psi <- Ud psi, lambda <- Ud lambda.
+template <typename R>
+__global__ void __launch_bounds__(256) k_adjoint_rot(R* __restrict__ psi, R* __restrict__ lam, uint64_t half, int p,
+                                                     int gen, Mat2<R> ud, double* __restrict__ partial) {
+  const Cplx<R> u00{ud.m[0], ud.m[1]}, u01{ud.m[2], ud.m[3]}, u10{ud.m[4], ud.m[5]}, u11{ud.m[6], ud.m[7]};
+  const uint64_t m = uint64_t(1) << p, lo = m - 1;
+  double acc = 0.0;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t it = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; it < half; it += stride) {
+    const uint64_t i0 = ((it & ~lo) << 1) | (it & lo), i1 = i0 | m;
+    const Cplx<R> a0 = ld_amp<R>(psi, i0), a1 = ld_amp<R>(psi, i1);
+    const Cplx<R> l0 = ld_amp<R>(lam, i0), l1 = ld_amp<R>(lam, i1);
+    // (G psi) on the pair; then Im sum conj(l) * (G psi)
+    double gr0, gi0, gr1, gi1;
+    if (gen == 0) {  // X
+      gr0 = a1.re; gi0 = a1.im; gr1 = a0.re; gi1 = a0.im;
+    } else if (gen == 1) {  // Y: (G psi)_0 = -i a1, (G psi)_1 = i a0
+      gr0 = a1.im; gi0 = -double(a1.re); gr1 = -double(a0.im); gi1 = a0.re;
+    } else {  // Z
+      gr0 = a0.re; gi0 = a0.im; gr1 = -double(a1.re); gi1 = -double(a1.im);
+    }
+    acc += double(l0.re) * gi0 - double(l0.im) * gr0 + double(l1.re) * gi1 - double(l1.im) * gr1;
+    st_amp<R>(psi, i0, cmul2(u00, a0, u01, a1));
+    st_amp<R>(psi, i1, cmul2(u10, a0, u11, a1));
+    st_amp<R>(lam, i0, cmul2(u00, l0, u01, l1));
+    st_amp<R>(lam, i1, cmul2(u10, l0, u11, l1));
+  }
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+// grad[param[g]] += sum_b partials[g][b] for every recorded rotation g (fixed order)
+// sum of each rotation's block partials into its first slot; k_collect_grads then adds
+// the rotations that share a parameter, serially in gate order
+__global__ void k_reduce_grads(double* partials, int nblocks, int nrot) {
+  for (int g = blockIdx.x; g < nrot; g += gridDim.x) {
+    double acc = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) acc += partials[size_t(g) * nblocks + b];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) partials[size_t(g) * nblocks] = acc;
+    __syncthreads();
+  }
+}
+
+__global__ void k_sum2_adj(const double* partials, int count, double* out) {
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    a += partials[2 * i];
+    b += partials[2 * i + 1];
+  }
+  a = block_sum(a);
+  b = block_sum(b);
+  if (threadIdx.x == 0) {
+    out[0] = a;
+    out[1] = b;
+  }
+}
+
+__global__ void k_collect_grads(const double* partials, int nblocks, const int* params, int nrot, double* grad,
+                                int nparams) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  for (int p = 0; p < nparams; ++p) grad[p] = 0.0;
+  for (int g = 0; g < nrot; ++g) grad[params[g]] += partials[size_t(g) * nblocks];
+}
+
+// Per-process device workspace of the adjoint sweep (three state buffers and partials).
+struct AdjWork {
+  int device = -1;
+  size_t bytes = 0;
+  void* p = nullptr;
+};
+static AdjWork g_adj;
+
+template <typename R>
+static qc_status adjoint_impl(const qc_circuit* c, const double* params, int nparams,
+                              const std::vector<ParsedTermA>& terms, const double* coeffs, qc_dtype dtype,
+                              cudaStream_t stream, double* host_energy, double* host_grad) {
+  const int n = c->n;
+  const uint64_t N = uint64_t(1) << n;
+  const size_t sbytes = N * 2 * sizeof(R);
+  // rotations, in order, with their parameter
+  std::vector<ResolvedOp> rops(c->nops);
+  std::vector<int> gen(c->nops, -1), pidx(c->nops, -1);
+  int nrot = 0;
+  for (int i = 0; i < c->nops; ++i) {
+    const qc_op& op = c->ops[i];
+    if (qc_status st = resolve_op(c, op, params, &rops[i])) return st;
+    if (op.param >= 0) {
+      if (op.kind != QC_GATE_RX && op.kind != QC_GATE_RY && op.kind != QC_GATE_RZ) {
+        set_error("qc_adjoint_grad: parameterised op %d must be RX, RY or RZ", i);
+        return QC_ERR_UNSUPPORTED;
+      }
+      if (op.param >= nparams) {
+        set_error("qc_adjoint_grad: op %d uses parameter %d >= nparams", i, op.param);
+        return QC_ERR_INVALID_ARG;
+      }
+      gen[i] = op.kind == QC_GATE_RX ? 0 : op.kind == QC_GATE_RY ? 1 : 2;
+      pidx[i] = op.param;
+      ++nrot;
+    }
+  }
+  const int B = 256;
+  const unsigned grid = stream_grid(N / 2, B, 8);
+  const size_t pbytes = sizeof(double) * (size_t(std::max(nrot, 1)) * grid + 2 * grid + 2 + nparams) + sizeof(int) * (nrot + 1);
+  const size_t need = 2 * sbytes + ((pbytes + 255) & ~size_t(255)) + 256;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (g_adj.device != dev || g_adj.bytes < need) {
+    if (g_adj.p) {
+      cudaDeviceSynchronize();
+      cudaFree(g_adj.p);
+      g_adj.p = nullptr;
+    }
+    if (qc_status st = check_cuda(cudaMalloc(&g_adj.p, need), "adjoint workspace")) return st;
+    g_adj.bytes = need;
+    g_adj.device = dev;
+  }
+  char* w = static_cast<char*>(g_adj.p);
+  R* lam = reinterpret_cast<R*>(w);
+  double* part = reinterpret_cast<double*>(w + sbytes);
+  double* inner = part + size_t(std::max(nrot, 1)) * grid;
+  double* grad = inner + 2 * grid + 2;
+  int* dparams = reinterpret_cast<int*>(grad + nparams);
+  // psi: a state handle over the workspace so that the gate kernels can run on it
+  qc_state s{};
+  s.n = n;
+  s.dtype = dtype;
+  s.amps = w + sbytes + ((pbytes + 255) & ~size_t(255));
+  s.stream = stream;
+  s.device = dev;
+  qc_state sl = s;
+  sl.amps = lam;
+  qc_status st = QC_OK;
+  // forward
+  if ((st = qc_state_init_basis(&s, 0))) goto done;
+  if ((st = n >= 10 ? run_fused(&s, c, params, QC_PREC_NATIVE) : run_per_gate(&s, c, params))) goto done;
+  {
+    // lambda = H psi, grouped by X mask
+    std::map<uint64_t, std::vector<int>> groups;
+    for (size_t t = 0; t < terms.size(); ++t) groups[terms[t].x].push_back(int(t));
+    bool first = true;
+    const unsigned g2 = stream_grid(N, B);
+    for (auto& kv : groups)
+      for (size_t b0 = 0; b0 < kv.second.size(); b0 += kHTerms) {
+        HGroup hg{};
+        hg.x = kv.first;
+        hg.first = first ? 1 : 0;
+        first = false;
+        hg.nt = int(std::min<size_t>(kHTerms, kv.second.size() - b0));
+        for (int j = 0; j < hg.nt; ++j) {
+          const ParsedTermA& t = terms[kv.second[b0 + j]];
+          const double cf = coeffs ? coeffs[kv.second[b0 + j]] : 1.0;
+          const int ny = t.ny & 3;  // i^ny
+          hg.z[j] = t.z;
+          hg.cre[j] = ny == 0 ? cf : ny == 2 ? -cf : 0.0;
+          hg.cim[j] = ny == 1 ? cf : ny == 3 ? -cf : 0.0;
+        }
+        QC_COUNT(), k_apply_hsum<R><<<g2, B, 0, stream>>>(reinterpret_cast<const R*>(s.amps), lam, N, hg);
+      }
+    if (first) {  // empty Hamiltonian
+      cudaMemsetAsync(lam, 0, sbytes, stream);
+    }
+    QC_COUNT(), k_inner_partials<R><<<grid, B, 0, stream>>>(reinterpret_cast<const R*>(s.amps), lam, N, inner);
+    QC_COUNT(), k_sum2_adj<<<1, 1024, 0, stream>>>(inner, int(grid), inner + 2 * grid);
+  }
+  {
+    // reverse sweep
+    std::vector<int> rot_params;
+    int r = nrot;
+    for (int i = c->nops - 1; i >= 0; --i) {
+      ResolvedOp ud = rops[i];
+      const int dim = ud.form == FORM_2Q ? 4 : 2;
+      // U^dagger
+      double t[32];
+      for (int a = 0; a < dim; ++a)
+        for (int b = 0; b < dim; ++b) {
+          t[2 * (a * dim + b)] = ud.m[2 * (b * dim + a)];
+          t[2 * (a * dim + b) + 1] = -ud.m[2 * (b * dim + a) + 1];
+        }
+      memcpy(ud.m, t, sizeof(double) * 2 * dim * dim);
+      if (gen[i] >= 0) {
+        --r;
+        Mat2<R> m;
+        for (int e = 0; e < 8; ++e) m.m[e] = R(ud.m[e]);
+        QC_COUNT(), k_adjoint_rot<R><<<grid, B, 0, stream>>>(reinterpret_cast<R*>(s.amps), lam, N / 2, ud.bits[0],
+                                                             gen[i], m, part + size_t(r) * grid);
+        rot_params.push_back(pidx[i]);
+      } else {
+        if ((st = apply_resolved(&s, ud))) goto done;
+        if ((st = apply_resolved(&sl, ud))) goto done;
+      }
+    }
+    std::reverse(rot_params.begin(), rot_params.end());
+    if (nrot > 0) {
+      if ((st = check_cuda(cudaMemcpyAsync(dparams, rot_params.data(), sizeof(int) * nrot, cudaMemcpyHostToDevice,
+                                           stream),
+                           "upload")))
+        goto done;
+      QC_COUNT(), k_reduce_grads<<<std::min(nrot, 1024), 1024, 0, stream>>>(part, int(grid), nrot);
+    }
+    QC_COUNT(), k_collect_grads<<<1, 32, 0, stream>>>(part, int(grid), dparams, nrot, grad, nparams);
+    if ((st = check_launch("adjoint sweep"))) goto done;
+    std::vector<double> e(2);
+    if ((st = check_cuda(cudaMemcpyAsync(e.data(), inner + 2 * grid, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                         stream),
+                         "D2H")))
+      goto done;
+    if ((st = check_cuda(cudaMemcpyAsync(host_grad, grad, sizeof(double) * nparams, cudaMemcpyDeviceToHost, stream),
+                         "D2H")))
+      goto done;
+    if ((st = check_cuda(cudaStreamSynchronize(stream), "qc_adjoint_grad"))) goto done;
+    *host_energy = e[0];
+  }
+done:
+  if (s.scratch) {
+    cudaStreamSynchronize(stream);
+    cudaFree(s.scratch);
+  }
+  return st;
+}
+
+}  // namespace qcgb
+
+using namespace qcgb;
+
+extern "C" qc_status qc_adjoint_grad(const qc_circuit* c, const double* params, int nparams,
+                                     const char* const* strings, const double* coeffs, int nterms, qc_dtype dtype,
+                                     void* stream, double* host_energy, double* host_grad) {
+  clear_error();
+  if (!c || c->n < 1 || c->n > 32 || (c->nops > 0 && !c->ops) || nparams < 0 || (nparams > 0 && (!params || !host_grad)) ||
+      nterms < 0 || (nterms > 0 && !strings) || !host_energy || (dtype != QC_C64 && dtype != QC_C128)) {
+    set_error("qc_adjoint_grad: invalid arguments");
+    return QC_ERR_INVALID_ARG;
+  }
+  std::vector<ParsedTermA> terms(nterms);
+  for (int t = 0; t < nterms; ++t)
+    if (qc_status st = parse_pauli_a(c->n, strings[t], &terms[t])) return st;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (dtype == QC_C64)
+    return adjoint_impl<float>(c, params, nparams, terms, coeffs, dtype, s, host_energy, host_grad);
+  return adjoint_impl<double>(c, params, nparams, terms, coeffs, dtype, s, host_energy, host_grad);
+}

@@ -1,0 +1,97 @@
+"""GPU adjoint gradients against the oracle's exact parameter-shift gradient and
+against central differences (reading: each parameter enters once with frequency 1,
+so a central difference with step h equals f'(t) sin(h)/h exactly)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+from gpu_util import need_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def gpu_energy(n, ops, params, terms, coeffs, dtype):
+    import paper_2503_03016_gb300 as P
+    st = P.State(n, dtype).init_basis(0)
+    st.run(ops, params, mode=P.QC_RUN_FUSED)
+    return float(np.sum(st.expect(terms, coeffs)))
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-11), ("c64", 2e-5)])
+@pytest.mark.parametrize("n,layers", [(4, 2), (10, 3)])
+def test_adjoint_vs_parameter_shift(dtype, tol, n, layers):
+    import paper_2503_03016_gb300 as P
+    ops, params, terms, coeffs = W.adjoint_workload(n, layers, 5)
+    circ = P.Circuit(n, ops)
+    e, g = P.qc_adjoint_grad(circ, params, terms, coeffs, P.QC_C128 if dtype == "c128" else P.QC_C64)
+    e_ref = oracle.energy(n, ops, params, terms, coeffs)
+    g_ref = oracle.param_shift_grad(n, ops, params, terms, coeffs)
+    scale = np.abs(g_ref).max() + 1
+    assert abs(e - e_ref) <= tol * scale
+    np.testing.assert_allclose(g, g_ref, atol=tol * scale, rtol=0)
+
+
+def test_adjoint_mixed_generators_and_shared_parameters():
+    """RX/RY/RZ rotations, a parameter used by two gates, non-rotation gates between
+    them and a Hamiltonian with X, Y and Z strings."""
+    import paper_2503_03016_gb300 as P
+    from workloads import Op
+    n = 5
+    ops = [Op("h", (0,)), Op("rx", (1,), param_index=0), Op("cnot", (1, 2)), Op("ry", (2,), param_index=1),
+           Op("rz", (3,), param_index=2), Op("cz", (0, 3)), Op("rx", (4,), param_index=0), Op("swap", (1, 4)),
+           Op("ry", (0,), param_index=3), Op("cp", (2, 3), (0.4,)), Op("rz", (2,), param_index=1)]
+    params = np.array([0.3, 1.2, -0.7, 2.2])
+    terms = ["XYZII", "ZZIII", "IIYIX", "YIIIZ", "IXXXI"]
+    coeffs = np.array([0.5, -1.0, 0.7, 0.2, 1.3])
+    circ = P.Circuit(n, ops)
+    e, g = P.qc_adjoint_grad(circ, params, terms, coeffs, P.QC_C128)
+    assert abs(e - oracle.energy(n, ops, params, terms, coeffs)) < 1e-12
+    np.testing.assert_allclose(g, oracle.param_shift_grad(n, ops, params, terms, coeffs), atol=1e-12)
+
+
+def test_autograd_function():
+    import torch
+
+    import paper_2503_03016_gb300 as P
+    n, layers = 6, 2
+    ops, params, terms, coeffs = W.adjoint_workload(n, layers, 7)
+    circ = P.Circuit(n, ops)
+    theta = torch.tensor(params, dtype=torch.float64, requires_grad=True)
+    e = P.AdjointExpectation.apply(theta, circ, terms, coeffs, P.QC_C128)
+    (3.0 * e).backward()
+    g_ref = oracle.param_shift_grad(n, ops, params, terms, coeffs)
+    np.testing.assert_allclose(theta.grad.numpy(), 3.0 * g_ref, atol=1e-11)
+
+
+@pytest.mark.slow
+def test_adjoint_24q_central_differences():
+    """Full size: 24 qubits, 10 layers, 480 parameters, H = ring ZZ + sum X.  The
+    complex128 adjoint gradient against central differences of the GPU complex128
+    energy (step 1e-3, corrected by h/sin h) on 12 seeded parameters; complex64
+    against complex128."""
+    import paper_2503_03016_gb300 as P
+    n, layers = 24, 10
+    ops, params, terms, coeffs = W.adjoint_workload(n, layers, 5)
+    circ = P.Circuit(n, ops)
+    e128, g128 = P.qc_adjoint_grad(circ, params, terms, coeffs, P.QC_C128)
+    e64, g64 = P.qc_adjoint_grad(circ, params, terms, coeffs, P.QC_C64)
+    assert g128.size == 480
+    assert abs(e128 - gpu_energy(n, ops, params, terms, coeffs, "c128")) < 1e-10
+    h = 1e-3
+    idx = np.random.default_rng(5).choice(480, 12, replace=False)
+    for p in idx:
+        a = params.copy()
+        a[p] += h
+        b = params.copy()
+        b[p] -= h
+        fd = (gpu_energy(n, ops, a, terms, coeffs, "c128") - gpu_energy(n, ops, b, terms, coeffs, "c128")) / (2 * h)
+        assert abs(fd * h / np.sin(h) - g128[p]) < 1e-8, (p, fd, g128[p])
+    assert abs(e64 - e128) < 1e-4 * (1 + abs(e128))
+    assert np.abs(g64 - g128).max() < 1e-4 * (1 + np.abs(g128).max())

@@ -357,3 +357,17 @@ def test_param_shift_vs_central_difference():
     h = 1e-3
     cd = oracle.central_diff_grad(n, ops, params, terms, coeffs, h, range(params.size))
     np.testing.assert_allclose(cd * h / np.sin(h), ps, atol=5e-11)
+
+
+def test_param_shift_shared_parameter_vs_central_difference():
+    """A parameter used by two gates: the per-occurrence shift rule (chain rule) agrees
+    with a central difference (frequency <= 2, so FD error ~ h^2 f'''/6)."""
+    n = 3
+    ops = [Op("h", (0,)), Op("rx", (1,), param_index=0), Op("cnot", (0, 1)), Op("rx", (2,), param_index=0),
+           Op("ry", (1,), param_index=1), Op("cz", (1, 2)), Op("rx", (1,), param_index=0)]
+    params = np.array([0.7, -1.1])
+    terms, coeffs = ["ZZI", "IXY", "YIZ"], [1.0, 0.5, -0.3]
+    ps = oracle.param_shift_grad(n, ops, params, terms, coeffs)
+    h = 1e-4
+    cd = oracle.central_diff_grad(n, ops, params, terms, coeffs, h, range(2))
+    np.testing.assert_allclose(ps, cd, atol=1e-7)
