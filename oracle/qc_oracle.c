@@ -28,6 +28,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define RE(p, i) ((p)[2 * (i)])
 #define IM(p, i) ((p)[2 * (i) + 1])
@@ -296,10 +299,13 @@ void orc_dft_gaussian(uint64_t seed, int n, double norm2, int round_c64, const u
   const int64_t N = (int64_t)1 << n;
   const uint64_t mask = (uint64_t)N - 1;
   const double inv = 1.0 / sqrt(norm2);
-  for (int t = 0; t < nk; ++t) {
-    double sr = 0.0, si = 0.0;
-    const uint64_t k = ks[t];
-#pragma omp parallel for schedule(static) reduction(+ : sr, si)
+  for (int t = 0; t < 2 * nk; ++t) out[t] = 0.0;
+  /* one pass over j (each amplitude generated once); per-thread partial sums over a
+   * contiguous range of j, added in thread order at the end */
+#pragma omp parallel
+  {
+    double* acc = (double*)calloc((size_t)(2 * nk), sizeof(double));
+#pragma omp for schedule(static)
     for (int64_t j = 0; j < N; ++j) {
       double re, im;
       gauss_amp(seed, (uint64_t)j, &re, &im);
@@ -309,23 +315,28 @@ void orc_dft_gaussian(uint64_t seed, int n, double norm2, int round_c64, const u
         re = (double)(float)re;
         im = (double)(float)im;
       }
-      uint64_t r = ((uint64_t)j * k) & mask;
-      double ang = 2.0 * M_PI * ((double)r / (double)N);
-      double c = cos(ang), s = sin(ang);
-      double tr, ti;
-      cmul(re, im, c, s, &tr, &ti);
-      sr += tr;
-      si += ti;
+      for (int t = 0; t < nk; ++t) {
+        uint64_t r = ((uint64_t)j * ks[t]) & mask;
+        double ang = 2.0 * M_PI * ((double)r / (double)N);
+        double tr, ti;
+        cmul(re, im, cos(ang), sin(ang), &tr, &ti);
+        acc[2 * t] += tr;
+        acc[2 * t + 1] += ti;
+      }
     }
-    double sc = 1.0 / sqrt((double)N);
-    out[2 * t] = sr * sc;
-    out[2 * t + 1] = si * sc;
+#pragma omp for ordered schedule(static, 1)
+    for (int th = 0; th < omp_get_num_threads(); ++th) {
+#pragma omp ordered
+      for (int t = 0; t < 2 * nk; ++t) out[t] += acc[t];
+    }
+    free(acc);
   }
+  const double sc = 1.0 / sqrt((double)N);
+  for (int t = 0; t < 2 * nk; ++t) out[t] *= sc;
 }
 
 int orc_num_threads(void) {
 #ifdef _OPENMP
-  extern int omp_get_max_threads(void);
   return omp_get_max_threads();
 #else
   return 1;

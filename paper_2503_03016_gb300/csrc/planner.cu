@@ -42,8 +42,9 @@ struct TileOp {
   uint32_t lmask, lval;  // condition on the amplitude's local (in-tile) index
   int32_t pad;
   uint64_t gmask, gval;  // condition on the index bits outside the tile
-  int64_t mat;           // DENSE: offset of the matrix (R values) in the pool
-  int64_t tab;           // PHASE: offset (complex entries) of its tables in the pool
+  int64_t mat;           // DENSE: matrix / PHASE: 16-entry slot table, offset (R values) in
+                         // the pass's matrix block
+  int64_t tab;           // PHASE: offset (complex entries) of its other tables in the pool
 };
 
 struct TileStage {
@@ -55,6 +56,8 @@ struct TileStage {
 struct TilePass {
   int32_t m, L;
   int32_t stage0, nstages;
+  int32_t op0, nops;    // the pass's ops (staged in shared memory)
+  int32_t mat0, nmat;   // the pass's dense matrices and phase slot tables (R values)
   int8_t bits[16];   // B ascending (global bit positions); bits[0..L) = 0..L-1
   int32_t c0, c1;    // local phase-table chunks: local bits [0,c0) and [c0,m)
   int32_t cg;        // tile-index phase-table chunk width (3 chunks)
@@ -113,9 +116,11 @@ __device__ __forceinline__ void dense2(Cplx<R> (&v)[kStageAmps], const R* __rest
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const R* ur = u + 8 * r;
-      Cplx<R> a = cmul2(Cplx<R>{ur[0], ur[1]}, x0, Cplx<R>{ur[2], ur[3]}, x1);
-      Cplx<R> b = cmul2(Cplx<R>{ur[4], ur[5]}, x2, Cplx<R>{ur[6], ur[7]}, x3);
-      const Cplx<R> o{a.re + b.re, a.im + b.im};
+      Cplx<R> o;
+      o.re = fma(ur[0], x0.re, fma(-ur[1], x0.im, fma(ur[2], x1.re, fma(-ur[3], x1.im,
+             fma(ur[4], x2.re, fma(-ur[5], x2.im, fma(ur[6], x3.re, -ur[7] * x3.im)))))));
+      o.im = fma(ur[0], x0.im, fma(ur[1], x0.re, fma(ur[2], x1.im, fma(ur[3], x1.re,
+             fma(ur[4], x2.im, fma(ur[5], x2.re, fma(ur[6], x3.im, ur[7] * x3.re)))))));
       if (r == 0) v[i0] = o;
       else if (r == 1) v[i1] = o;
       else if (r == 2) v[i2] = o;
@@ -181,19 +186,27 @@ __device__ __forceinline__ void prefetch_tile(Cplx<R>* buf, const R* amps, uint6
 template <typename R, int NT>
 __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const TilePass P,
                                                       const TileStage* __restrict__ stages,
-                                                      const TileOp* __restrict__ ops, const R* __restrict__ pool) {
+                                                      const TileOp* __restrict__ ops, const R* __restrict__ pool,
+                                                      const R* __restrict__ mats) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = P.m, L = P.L;
   const uint32_t T = 1u << m;
   Cplx<R>* bufs = reinterpret_cast<Cplx<R>*>(smem_raw);  // 2 x T
   uint64_t* hioff = reinterpret_cast<uint64_t*>(smem_raw + 2 * sizeof(Cplx<R>) * T);
   const int nhi = m - L;
+  // the pass's plan, copied once into shared memory: stages, ops, matrices
+  TileStage* sst = reinterpret_cast<TileStage*>(hioff + (1u << nhi));
+  TileOp* sop = reinterpret_cast<TileOp*>(sst + P.nstages);
+  R* smat = reinterpret_cast<R*>(sop + P.nops);
   for (uint32_t h = threadIdx.x; h < (1u << nhi); h += blockDim.x) {
     uint64_t o = 0;
     for (int k = 0; k < nhi; ++k)
       if ((h >> k) & 1) o |= uint64_t(1) << P.bits[L + k];
     hioff[h] = o;
   }
+  for (int i = threadIdx.x; i < P.nstages; i += blockDim.x) sst[i] = stages[P.stage0 + i];
+  for (int i = threadIdx.x; i < P.nops; i += blockDim.x) sop[i] = ops[P.op0 + i];
+  for (int i = threadIdx.x; i < P.nmat; i += blockDim.x) smat[i] = mats[P.mat0 + i];
   __syncthreads();
   const uint32_t lowmask = (1u << L) - 1;
   const Cplx<R>* cpool = reinterpret_cast<const Cplx<R>*>(pool);
@@ -209,7 +222,7 @@ __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const
     cp_async_wait1();
     __syncthreads();
     for (int s = 0; s < P.nstages; ++s) {
-      const TileStage st = stages[P.stage0 + s];
+      const TileStage st = sst[s];
       const uint32_t r0 = uint32_t(insert_zero_bits(threadIdx.x, st.sorted, kStageBits));
       uint32_t sm[kStageBits], sw[kStageBits];
 #pragma unroll
@@ -222,17 +235,17 @@ __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const
 #pragma unroll
       for (int j = 0; j < kStageAmps; ++j) v[j] = tile[p0 ^ slot_xor(j, sw)];
       for (int q = 0; q < st.nops; ++q) {
-        const TileOp op = ops[st.op0 + q];
+        const TileOp& op = sop[st.op0 + q];
         if ((base & op.gmask) != op.gval) continue;
         if (op.type == TOP_DENSE1) {
-          apply_dense1<R>(op.s0, v, pool + op.mat, r0, sm, op.lmask, op.lval);
+          apply_dense1<R>(op.s0, v, smat + op.mat, r0, sm, op.lmask, op.lval);
         } else if (op.type == TOP_DENSE2) {
-          apply_dense2<R>(op.s0, op.s1, v, pool + op.mat);
+          apply_dense2<R>(op.s0, op.s1, v, smat + op.mat);
         } else {
           // exp(i (c + sum beta_p b_p)) factorised over: tile-index chunks (3), the
           // thread's inactive local bits (2 chunks) and the 16 slot combinations
-          const Cplx<R>* jt = cpool + op.tab;
-          const Cplx<R>* l0 = jt + kStageAmps;
+          const Cplx<R>* jt = reinterpret_cast<const Cplx<R>*>(smat + op.mat);
+          const Cplx<R>* l0 = cpool + op.tab;
           const Cplx<R>* l1 = l0 + (1 << P.c0);
           const Cplx<R>* g0 = l1 + (1 << (m - P.c0));
           const uint32_t gn = 1u << P.cg, gm = gn - 1;
@@ -345,6 +358,8 @@ static void to_plan_ops(const std::vector<ResolvedOp>& in, std::vector<PlanOp>& 
   }
 }
 
+constexpr int kMaxPassOps = 128;  // bounds the plan staged in shared memory per pass
+
 struct BuiltPass {
   std::vector<int> B;       // ascending
   std::vector<int> ops;     // indices into plan ops, in order
@@ -363,7 +378,7 @@ static std::vector<BuiltPass> build_passes(const std::vector<PlanOp>& ops, int n
     std::vector<int> excluded;
     for (int idx : remaining) {
       const PlanOp& p = ops[idx];
-      bool ok = (p.touched & blocked_all) == 0;
+      bool ok = (p.touched & blocked_all) == 0 && int(bp.ops.size()) < kMaxPassOps;
       if (ok && !p.phase) ok = (p.touched & blocked_diag) == 0;
       if (ok && !p.phase) {
         uint64_t need = 0;
@@ -407,7 +422,8 @@ struct HostPlan {
   std::vector<TilePass> passes;
   std::vector<TileStage> stages;
   std::vector<TileOp> ops;
-  std::vector<R> pool;
+  std::vector<R> pool;  // phase tables read per thread (global memory)
+  std::vector<R> mats;  // per-pass matrices and slot tables (staged in shared memory)
 };
 
 template <typename R>
@@ -422,6 +438,8 @@ static void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int 
   P.cg = (n - m + 2) / 3;
   if (P.cg < 1) P.cg = 1;
   P.stage0 = int(hp.stages.size());
+  P.op0 = int(hp.ops.size());
+  P.mat0 = int(hp.mats.size());
   int local_of[64];
   for (int b = 0; b < 64; ++b) local_of[b] = -1;
   for (int i = 0; i < m; ++i) local_of[bp.B[i]] = i;
@@ -472,7 +490,7 @@ static void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int 
     std::vector<int> srt = act;
     std::sort(srt.begin(), srt.end());
     for (int k = 0; k < kStageBits; ++k) st.sorted[k] = int8_t(srt[k]);
-    st.op0 = int(hp.ops.size());
+    st.op0 = int(hp.ops.size()) - P.op0;
     const size_t j = take.size();
     for (size_t q = 0; q < j; ++q) {
       const PlanOp& p = pops[take[q]];
@@ -500,8 +518,8 @@ static void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int 
         };
         op.s0 = slot(p.tb[0]);
         op.s1 = p.nt == 2 ? slot(p.tb[1]) : 0;
-        op.mat = int64_t(hp.pool.size());
-        for (int e = 0; e < (p.nt == 1 ? 8 : 32); ++e) hp.pool.push_back(R(p.m[e]));
+        op.mat = int64_t(hp.mats.size()) - P.mat0;
+        for (int e = 0; e < (p.nt == 1 ? 8 : 32); ++e) hp.mats.push_back(R(p.m[e]));
       } else {
         // merge following phase ops with the same condition (they commute)
         op.type = TOP_PHASE;
@@ -522,11 +540,13 @@ static void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int 
           hp.pool.push_back(R(std::cos(ang)));
           hp.pool.push_back(R(std::sin(ang)));
         };
+        op.mat = int64_t(hp.mats.size()) - P.mat0;
         for (int jj = 0; jj < kStageAmps; ++jj) {
           double a = 0;
           for (int k = 0; k < kStageBits; ++k)
             if ((jj >> k) & 1) a += beta[bp.B[st.slot_bit[k]]];
-          push(a);
+          hp.mats.push_back(R(std::cos(a)));
+          hp.mats.push_back(R(std::sin(a)));
         }
         // inactive local bits only (slot bits are zero in r0)
         for (int x = 0; x < (1 << P.c0); ++x) {
@@ -555,11 +575,13 @@ static void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int 
       }
       hp.ops.push_back(op);
     }
-    st.nops = int(hp.ops.size()) - st.op0;
+    st.nops = int(hp.ops.size()) - P.op0 - st.op0;
     hp.stages.push_back(st);
     rest.swap(skip);
   }
   P.nstages = int(hp.stages.size()) - P.stage0;
+  P.nops = int(hp.ops.size()) - P.op0;
+  P.nmat = int(hp.mats.size()) - P.mat0;
   hp.passes.push_back(P);
 }
 
@@ -575,27 +597,34 @@ static qc_status run_tiles(qc_state* s, const std::vector<ResolvedOp>& rops, int
   HostPlan<R> hp;
   for (const BuiltPass& bp : bps) emit_pass<R>(bp, pops, n, m, L, hp);
   g_last_pass_count = int(hp.passes.size());
-  // upload stages, ops and pool into the state's scratch (stream ordered)
-  const size_t sb = (hp.stages.size() * sizeof(TileStage) + 255) & ~size_t(255);
-  const size_t ob = (hp.ops.size() * sizeof(TileOp) + 255) & ~size_t(255);
-  const size_t pb = (hp.pool.size() * sizeof(R) + 255) & ~size_t(255);
+  // upload stages, ops, tables and matrices into the state's scratch (stream ordered)
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t sb = al(hp.stages.size() * sizeof(TileStage));
+  const size_t ob = al(hp.ops.size() * sizeof(TileOp));
+  const size_t pb = al(hp.pool.size() * sizeof(R));
+  const size_t mb = al(hp.mats.size() * sizeof(R));
   void* scr = nullptr;
-  if (qc_status st = state_scratch(s, sb + ob + pb + 256, &scr)) return st;
+  if (qc_status st = state_scratch(s, sb + ob + pb + mb + 256, &scr)) return st;
   char* base = static_cast<char*>(scr);
-  std::vector<char> host(sb + ob + pb, 0);
+  std::vector<char> host(sb + ob + pb + mb, 0);
   if (!hp.stages.empty()) memcpy(host.data(), hp.stages.data(), hp.stages.size() * sizeof(TileStage));
   if (!hp.ops.empty()) memcpy(host.data() + sb, hp.ops.data(), hp.ops.size() * sizeof(TileOp));
   if (!hp.pool.empty()) memcpy(host.data() + sb + ob, hp.pool.data(), hp.pool.size() * sizeof(R));
+  if (!hp.mats.empty()) memcpy(host.data() + sb + ob + pb, hp.mats.data(), hp.mats.size() * sizeof(R));
   if (qc_status st = check_cuda(cudaMemcpyAsync(base, host.data(), host.size(), cudaMemcpyHostToDevice, s->stream),
                                 "plan upload"))
     return st;
   const TileStage* dst = reinterpret_cast<const TileStage*>(base);
   const TileOp* dop = reinterpret_cast<const TileOp*>(base + sb);
   const R* dpool = reinterpret_cast<const R*>(base + sb + ob);
+  const R* dmats = reinterpret_cast<const R*>(base + sb + ob + pb);
   const int threads = 1 << (m - kStageBits);
-  const size_t smem = 2 * sizeof(Cplx<R>) * (size_t(1) << m) + sizeof(uint64_t) * (size_t(1) << (m - L));
+  size_t plan_max = 0;
+  for (const TilePass& P : hp.passes)
+    plan_max = std::max(plan_max, P.nstages * sizeof(TileStage) + P.nops * sizeof(TileOp) + P.nmat * sizeof(R));
+  const size_t smem = 2 * sizeof(Cplx<R>) * (size_t(1) << m) + sizeof(uint64_t) * (size_t(1) << (m - L)) + plan_max;
   constexpr int NT = sizeof(R) == 4 ? 512 : 256;
-  cudaFuncSetAttribute(k_tile_pass<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_tile_pass<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
   const uint64_t ntiles = uint64_t(1) << (n - m);
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_pass<R, NT>, threads, smem);
@@ -604,7 +633,7 @@ static qc_status run_tiles(qc_state* s, const std::vector<ResolvedOp>& rops, int
   const unsigned grid = unsigned(ntiles < cap ? ntiles : cap);
   R* a = reinterpret_cast<R*>(s->amps);
   for (const TilePass& P : hp.passes) {
-    QC_COUNT(), k_tile_pass<R, NT><<<grid, threads, smem, s->stream>>>(a, P, dst, dop, dpool);
+    QC_COUNT(), k_tile_pass<R, NT><<<grid, threads, smem, s->stream>>>(a, P, dst, dop, dpool, dmats);
   }
   return check_launch("tile pass");
 }
