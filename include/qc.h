@@ -69,6 +69,12 @@ uint64_t qc_launch_count(void);
 /* Number of tile passes the planner used for the most recent QC_RUN_FUSED circuit
  * (process-wide; a diagnostic for benchmarks). */
 int qc_last_pass_count(void);
+/* Plans circuit `c` as QC_RUN_FUSED would for a state of `dtype` and reports the number
+ * of tile passes, register stages and tile ops; host only (no device work, no GPU
+ * needed).  Circuits on fewer than 10 qubits report 0 (they run per gate). */
+struct qc_circuit;
+qc_status qc_plan_info(const struct qc_circuit* c, const double* params, qc_dtype dtype, int* passes,
+                       int* stages, int* ops);
 
 /* ---------------------------------------------------------------------------
  * State handles (QCLAB Sec. 3.1 "Initialization")

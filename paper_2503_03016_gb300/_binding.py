@@ -58,6 +58,7 @@ _SIGS = {
     "qc_abi_version": (ctypes.c_int, []),
     "qc_launch_count": (ctypes.c_uint64, []),
     "qc_last_pass_count": (ctypes.c_int, []),
+    "qc_plan_info": (ctypes.c_int, [ctypes.c_void_p, _D, ctypes.c_int, _I, _I, _I]),
     "qc_state_alloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(_P)]),
     "qc_state_wrap": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, ctypes.POINTER(_P)]),
     "qc_state_free": (ctypes.c_int, [_P]),
@@ -341,6 +342,17 @@ class Circuit:
         self._ops = arr
         self._pool = np.ascontiguousarray(pool if pool else [0.0], dtype=np.float64)
         self.c = qc_circuit(n, len(ops), arr, self._pool.ctypes.data_as(_D), len(pool))
+
+
+def qc_plan_info(circuit: Circuit, params=None, dtype: int = QC_C64):
+    """(passes, stages, ops) the fused planner produces; host only."""
+    p = None
+    if params is not None:
+        params = np.ascontiguousarray(params, dtype=np.float64)
+        p = params.ctypes.data_as(_D)
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _call("qc_plan_info", ctypes.addressof(circuit.c), p, dtype, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    return a.value, b.value, c.value
 
 
 def qc_run_circuit(h: int, circuit: Circuit, params=None, mode: int = QC_RUN_PER_GATE,

@@ -100,6 +100,79 @@ __global__ void __launch_bounds__(256) k_pauli(const R* __restrict__ a, uint64_t
   }
 }
 
+// Z-only strings (x = 0), up to 32 per pass: <Z_z> = sum_i p_i (-1)^popc(i & z).  A thread
+// takes chunks of 32 consecutive amplitudes (index bits 0..4 vary, the rest are the
+// chunk's), forms the Walsh-Hadamard transform S(w) = sum_l p_l (-1)^popc(l & w) of the
+// chunk's 32 probabilities once (in registers, then shared memory), and adds
+// (-1)^popc(chunk & z) * S(z & 31) to every term: per-term work is per chunk, not per
+// amplitude.  complex64 states accumulate per thread in FP32 (the per-amplitude values
+// are FP32 products already), complex128 in FP64; cross-thread and cross-block sums
+// are FP64 in a fixed order.
+constexpr int kMaxZTerms = 32;
+constexpr int kZBlock = 128;
+struct ZGroup {
+  int nt;
+  uint64_t z[kMaxZTerms];
+  int slot[kMaxZTerms];
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kZBlock) k_pauli_z(const R* __restrict__ amps, uint64_t N, ZGroup g,
+                                                     double* __restrict__ partials) {
+  __shared__ R S[32][kZBlock];
+  R acc[kMaxZTerms];
+#pragma unroll
+  for (int t = 0; t < kMaxZTerms; ++t) acc[t] = R(0);
+  const uint64_t nchunk = N >> 5;
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t c = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; c < nchunk; c += stride) {
+    const uint64_t base = c << 5;
+    R w[32];
+#pragma unroll
+    for (int l = 0; l < 32; l += 2) {
+      Cplx<R> x0, x1;
+      ld_amp2<R>(amps, base + l, x0, x1);
+      w[l] = x0.re * x0.re + x0.im * x0.im;
+      w[l + 1] = x1.re * x1.re + x1.im * x1.im;
+    }
+    // in-place Walsh-Hadamard transform over the 5 chunk bits
+#pragma unroll
+    for (int h = 1; h < 32; h <<= 1)
+#pragma unroll
+      for (int l = 0; l < 32; ++l)
+        if (!(l & h)) {
+          const R a = w[l], b = w[l | h];
+          w[l] = a + b;
+          w[l | h] = a - b;
+        }
+#pragma unroll
+    for (int l = 0; l < 32; ++l) S[l][threadIdx.x] = w[l];
+    // S is private to this thread's column: no barrier needed
+#pragma unroll
+    for (int t = 0; t < kMaxZTerms; ++t) {
+      if (t >= g.nt) break;
+      const R v = S[g.z[t] & 31][threadIdx.x];
+      acc[t] += (__popcll(base & g.z[t]) & 1) ? -v : v;
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < kMaxZTerms; ++t) {
+    if (t >= g.nt) break;
+    const double v = block_sum(double(acc[t]));
+    if (threadIdx.x == 0) partials[size_t(blockIdx.x) * kMaxZTerms + t] = v;
+  }
+}
+
+__global__ void k_sum_zterms(const double* partials, int nblocks, ZGroup g, double* out) {
+  for (int t = 0; t < g.nt; ++t) {
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += partials[size_t(i) * kMaxZTerms + t];
+    acc = block_sum(acc);
+    if (threadIdx.x == 0) out[g.slot[t]] = acc;
+    __syncthreads();
+  }
+}
+
 __global__ void k_sum_terms(const double* partials, int nblocks, PauliGroup g, double* out) {
   for (int t = 0; t < g.nt; ++t) {
     double acc = 0.0;
@@ -145,10 +218,27 @@ qc_status expect_terms_device(qc_state* s, const ParsedTerm* terms, int nterms, 
   const int B = 256;
   const unsigned g = stream_grid(N, B, 8);
   void* scr = nullptr;
-  if (qc_status st = state_scratch(s, sizeof(double) * size_t(g) * kMaxTermsPerPass + 256, &scr)) return st;
+  if (qc_status st = state_scratch(s, sizeof(double) * size_t(g) * kMaxZTerms + 256, &scr)) return st;
   double* part = reinterpret_cast<double*>(scr);
   for (auto& kv : groups) {
     const std::vector<int>& idx = kv.second;
+    if (kv.first == 0 && N >= 64) {  // Z-only strings
+      const unsigned gz = stream_grid(N >> 5, kZBlock, 8);
+      for (size_t beg = 0; beg < idx.size(); beg += kMaxZTerms) {
+        ZGroup zg{};
+        zg.nt = int(std::min<size_t>(kMaxZTerms, idx.size() - beg));
+        for (int j = 0; j < zg.nt; ++j) {
+          zg.z[j] = terms[idx[beg + j]].z;
+          zg.slot[j] = idx[beg + j];
+        }
+        if (s->dtype == QC_C64)
+          QC_COUNT(), k_pauli_z<float><<<gz, kZBlock, 0, s->stream>>>(reinterpret_cast<const float*>(s->amps), N, zg, part);
+        else
+          QC_COUNT(), k_pauli_z<double><<<gz, kZBlock, 0, s->stream>>>(reinterpret_cast<const double*>(s->amps), N, zg, part);
+        QC_COUNT(), k_sum_zterms<<<1, 1024, 0, s->stream>>>(part, int(gz), zg, dev_vals);
+      }
+      continue;
+    }
     for (size_t beg = 0; beg < idx.size(); beg += kMaxTermsPerPass) {
       PauliGroup pg{};
       pg.xmask = kv.first;

@@ -13,9 +13,10 @@
 // (the phase of an amplitude depends only on its index).  Runs of diagonal gates with
 // the same condition are merged into one phase op exp(i (c + sum_p beta_p b_p)).
 //
-// Inside a pass the gates are split into stages; in a stage every thread holds 16
-// amplitudes spanning 4 of the tile's bits in registers and applies all of the
-// stage's gates to them before writing back to shared memory.  Shared memory is
+// Inside a pass the gates are split into stages; in a stage every thread holds 2^SB
+// amplitudes spanning SB of the tile's bits in registers (SB = 5 for complex64, 4 for
+// complex128) and applies all of the stage's gates to them before writing back to
+// shared memory.  Shared memory is
 // addressed through an XOR swizzle so that the strided accesses of a stage do not
 // collide in the same bank.
 #include <string.h>
@@ -31,8 +32,7 @@
 
 namespace qcgb {
 
-constexpr int kStageBits = 4;
-constexpr int kStageAmps = 1 << kStageBits;
+constexpr int kMaxStageBits = 5;  // amplitudes a thread holds per stage: 2^SB, SB <= 5
 
 enum TileOpType : int32_t { TOP_DENSE1 = 0, TOP_DENSE2 = 1, TOP_PHASE = 2 };
 
@@ -42,16 +42,22 @@ struct TileOp {
   uint32_t lmask, lval;  // condition on the amplitude's local (in-tile) index
   int32_t pad;
   uint64_t gmask, gval;  // condition on the index bits outside the tile
-  int64_t mat;           // DENSE: matrix / PHASE: 16-entry slot table, offset (R values) in
-                         // the pass's matrix block
+  int64_t mat;           // DENSE: matrix / PHASE: 2^SB-entry slot table, offset (R values)
+                         // in the pass's matrix block
   int64_t tab;           // PHASE: offset (complex entries) of its other tables in the pool
+  int64_t pad2;          // 64-byte record: keeps the staged matrices 16-byte aligned
 };
+static_assert(sizeof(TileOp) == 64, "TileOp must be 64 bytes");
 
 struct TileStage {
   int32_t op0, nops;
-  int8_t slot_bit[kStageBits];  // local bit of each slot
-  int8_t sorted[kStageBits];    // the same bits ascending (zero-insertion order)
+  int8_t slot_bit[8];  // local bit of each slot (SB used)
+  int8_t lane_bit[8];  // local bit receiving bit k of the thread index (the m-SB non-slot
+                       // bits; the first ones cover distinct bit positions mod 4 so that a
+                       // half warp's shared-memory accesses fall in distinct banks)
+  int32_t pad[2];      // 32-byte record
 };
+static_assert(sizeof(TileStage) == 32, "TileStage must be 32 bytes");
 
 struct TilePass {
   int32_t m, L;
@@ -73,43 +79,69 @@ __device__ __forceinline__ uint32_t tile_swz(uint32_t r) {
 }
 
 // offset of slot combination j: OR of the slot masks selected by j's bits
-__device__ __forceinline__ uint32_t slot_off(int j, const uint32_t (&sm)[kStageBits]) {
+template <int SB>
+__device__ __forceinline__ uint32_t slot_off(int j, const uint32_t (&sm)[SB]) {
   uint32_t o = 0;
 #pragma unroll
-  for (int k = 0; k < kStageBits; ++k)
+  for (int k = 0; k < SB; ++k)
     if ((j >> k) & 1) o |= sm[k];
   return o;
 }
 
 // swizzled address offset of slot combination j: XOR of the swizzled slot masks
 // (the swizzle is linear over XOR, but swizzled masks may share bits)
-__device__ __forceinline__ uint32_t slot_xor(int j, const uint32_t (&sw)[kStageBits]) {
+template <int SB>
+__device__ __forceinline__ uint32_t slot_xor(int j, const uint32_t (&sw)[SB]) {
   uint32_t o = 0;
 #pragma unroll
-  for (int k = 0; k < kStageBits; ++k)
+  for (int k = 0; k < SB; ++k)
     if ((j >> k) & 1) o ^= sw[k];
   return o;
 }
 
-template <typename R, int S0>
-__device__ __forceinline__ void dense1(Cplx<R> (&v)[kStageAmps], const R* __restrict__ u, uint32_t r0,
-                                       const uint32_t (&sm)[kStageBits], uint32_t lmask, uint32_t lval) {
-  const Cplx<R> u00{u[0], u[1]}, u01{u[2], u[3]}, u10{u[4], u[5]}, u11{u[6], u[7]};
+// NV values of a 16-byte-aligned shared-memory matrix into registers
+template <typename R, int NV>
+__device__ __forceinline__ void load_mat(R (&um)[NV], const R* __restrict__ u) {
+  if (sizeof(R) == 4) {
+    const float4* q = reinterpret_cast<const float4*>(u);
 #pragma unroll
-  for (int j = 0; j < kStageAmps; ++j) {
+    for (int i = 0; i < NV / 4; ++i) {
+      const float4 t = q[i];
+      um[4 * i] = R(t.x); um[4 * i + 1] = R(t.y); um[4 * i + 2] = R(t.z); um[4 * i + 3] = R(t.w);
+    }
+  } else {
+    const double2* q = reinterpret_cast<const double2*>(u);
+#pragma unroll
+    for (int i = 0; i < NV / 2; ++i) {
+      const double2 t = q[i];
+      um[2 * i] = R(t.x); um[2 * i + 1] = R(t.y);
+    }
+  }
+}
+
+template <typename R, int SB, int S0>
+__device__ __forceinline__ void dense1(Cplx<R> (&v)[1 << SB], const R* __restrict__ u, uint32_t r0,
+                                       const uint32_t (&sm)[SB], uint32_t lmask, uint32_t lval) {
+  R um[8];
+  load_mat<R, 8>(um, u);
+  const Cplx<R> u00{um[0], um[1]}, u01{um[2], um[3]}, u10{um[4], um[5]}, u11{um[6], um[7]};
+#pragma unroll
+  for (int j = 0; j < (1 << SB); ++j) {
     if (j & (1 << S0)) continue;
     const int j1 = j | (1 << S0);
-    if (((r0 | slot_off(j, sm)) & lmask) != lval) continue;
+    if (((r0 | slot_off<SB>(j, sm)) & lmask) != lval) continue;
     const Cplx<R> x = v[j], y = v[j1];
     v[j] = cmul2(u00, x, u01, y);
     v[j1] = cmul2(u10, x, u11, y);
   }
 }
 
-template <typename R, int S0, int S1>
-__device__ __forceinline__ void dense2(Cplx<R> (&v)[kStageAmps], const R* __restrict__ u) {
+template <typename R, int SB, int S0, int S1>
+__device__ __forceinline__ void dense2(Cplx<R> (&v)[1 << SB], const R* __restrict__ us) {
+  R u[32];
+  load_mat<R, 32>(u, us);
 #pragma unroll
-  for (int j = 0; j < kStageAmps; ++j) {
+  for (int j = 0; j < (1 << SB); ++j) {
     if (j & ((1 << S0) | (1 << S1))) continue;
     const int i0 = j, i1 = j | (1 << S1), i2 = j | (1 << S0), i3 = j | (1 << S0) | (1 << S1);
     const Cplx<R> x0 = v[i0], x1 = v[i1], x2 = v[i2], x3 = v[i3];
@@ -129,35 +161,37 @@ __device__ __forceinline__ void dense2(Cplx<R> (&v)[kStageAmps], const R* __rest
   }
 }
 
-template <typename R>
-__device__ __forceinline__ void apply_dense1(int s0, Cplx<R> (&v)[kStageAmps], const R* u, uint32_t r0,
-                                             const uint32_t (&sm)[kStageBits], uint32_t lmask, uint32_t lval) {
+template <typename R, int SB>
+__device__ __forceinline__ void apply_dense1(int s0, Cplx<R> (&v)[1 << SB], const R* u, uint32_t r0,
+                                             const uint32_t (&sm)[SB], uint32_t lmask, uint32_t lval) {
   switch (s0) {
-    case 0: dense1<R, 0>(v, u, r0, sm, lmask, lval); break;
-    case 1: dense1<R, 1>(v, u, r0, sm, lmask, lval); break;
-    case 2: dense1<R, 2>(v, u, r0, sm, lmask, lval); break;
-    default: dense1<R, 3>(v, u, r0, sm, lmask, lval); break;
+    case 0: dense1<R, SB, 0>(v, u, r0, sm, lmask, lval); break;
+    case 1: dense1<R, SB, 1>(v, u, r0, sm, lmask, lval); break;
+    case 2: dense1<R, SB, 2>(v, u, r0, sm, lmask, lval); break;
+    case 3: dense1<R, SB, 3>(v, u, r0, sm, lmask, lval); break;
+    default:
+      if constexpr (SB > 4) dense1<R, SB, 4>(v, u, r0, sm, lmask, lval);
+      break;
   }
 }
 
-template <typename R>
-__device__ __forceinline__ void apply_dense2(int s0, int s1, Cplx<R> (&v)[kStageAmps], const R* u) {
-  switch (s0 * 4 + s1) {
-    case 1: dense2<R, 0, 1>(v, u); break;
-    case 2: dense2<R, 0, 2>(v, u); break;
-    case 3: dense2<R, 0, 3>(v, u); break;
-    case 4: dense2<R, 1, 0>(v, u); break;
-    case 6: dense2<R, 1, 2>(v, u); break;
-    case 7: dense2<R, 1, 3>(v, u); break;
-    case 8: dense2<R, 2, 0>(v, u); break;
-    case 9: dense2<R, 2, 1>(v, u); break;
-    case 11: dense2<R, 2, 3>(v, u); break;
-    case 12: dense2<R, 3, 0>(v, u); break;
-    case 13: dense2<R, 3, 1>(v, u); break;
-    case 14: dense2<R, 3, 2>(v, u); break;
+#define QC_D2(A, B) \
+  case (A) * 8 + (B): dense2<R, SB, A, B>(v, u); return;
+template <typename R, int SB>
+__device__ __forceinline__ void apply_dense2(int s0, int s1, Cplx<R> (&v)[1 << SB], const R* u) {
+  switch (s0 * 8 + s1) {
+    // the planner orders every two-qubit gate so that s0 < s1
+    QC_D2(0, 1) QC_D2(0, 2) QC_D2(0, 3) QC_D2(1, 2) QC_D2(1, 3) QC_D2(2, 3)
     default: break;
   }
+  if constexpr (SB > 4) {
+    switch (s0 * 8 + s1) {
+      QC_D2(0, 4) QC_D2(1, 4) QC_D2(2, 4) QC_D2(3, 4)
+      default: break;
+    }
+  }
 }
+#undef QC_D2
 
 // Asynchronous global -> shared copy of one amplitude (8 or 16 bytes).
 template <typename R>
@@ -181,13 +215,14 @@ __device__ __forceinline__ void prefetch_tile(Cplx<R>* buf, const R* amps, uint6
   }
 }
 
-// One launch = one pass over all tiles; blockDim = 2^(m-4), one block per SM with
+// One launch = one pass over all tiles; blockDim = 2^(m-SB), one block per SM with
 // two tile buffers: the next tile is fetched (cp.async) while this one is computed.
-template <typename R, int NT>
+template <typename R, int NT, int SB>
 __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const TilePass P,
-                                                      const TileStage* __restrict__ stages,
-                                                      const TileOp* __restrict__ ops, const R* __restrict__ pool,
-                                                      const R* __restrict__ mats) {
+                                                     const TileStage* __restrict__ stages,
+                                                     const TileOp* __restrict__ ops, const R* __restrict__ pool,
+                                                     const R* __restrict__ mats) {
+  constexpr int NA = 1 << SB;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = P.m, L = P.L;
   const uint32_t T = 1u << m;
@@ -198,10 +233,18 @@ __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const
   TileStage* sst = reinterpret_cast<TileStage*>(hioff + (1u << nhi));
   TileOp* sop = reinterpret_cast<TileOp*>(sst + P.nstages);
   R* smat = reinterpret_cast<R*>(sop + P.nops);
+  // the tile's bit positions in shared memory (a dynamically indexed kernel parameter
+  // array would be copied to local memory)
+  __shared__ int8_t sbits[16];
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) sbits[k] = P.bits[k];
+  }
+  __syncthreads();
   for (uint32_t h = threadIdx.x; h < (1u << nhi); h += blockDim.x) {
     uint64_t o = 0;
     for (int k = 0; k < nhi; ++k)
-      if ((h >> k) & 1) o |= uint64_t(1) << P.bits[L + k];
+      if ((h >> k) & 1) o |= uint64_t(1) << sbits[L + k];
     hioff[h] = o;
   }
   for (int i = threadIdx.x; i < P.nstages; i += blockDim.x) sst[i] = stages[P.stage0 + i];
@@ -211,39 +254,42 @@ __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const
   const uint32_t lowmask = (1u << L) - 1;
   const Cplx<R>* cpool = reinterpret_cast<const Cplx<R>*>(pool);
   uint64_t t = blockIdx.x;
-  if (t < P.ntiles) prefetch_tile<R>(bufs, amps, insert_zero_bits(t, P.bits, m), hioff, L, T);
+  if (t < P.ntiles) prefetch_tile<R>(bufs, amps, insert_zero_bits(t, sbits, m), hioff, L, T);
   cp_async_commit();
   for (int it = 0; t < P.ntiles; t += gridDim.x, ++it) {
     Cplx<R>* tile = bufs + (it & 1) * T;
-    const uint64_t base = insert_zero_bits(t, P.bits, m);
+    const uint64_t base = insert_zero_bits(t, sbits, m);
     const uint64_t tn = t + gridDim.x;
-    if (tn < P.ntiles) prefetch_tile<R>(bufs + ((it + 1) & 1) * T, amps, insert_zero_bits(tn, P.bits, m), hioff, L, T);
+    if (tn < P.ntiles) prefetch_tile<R>(bufs + ((it + 1) & 1) * T, amps, insert_zero_bits(tn, sbits, m), hioff, L, T);
     cp_async_commit();
     cp_async_wait1();
     __syncthreads();
     for (int s = 0; s < P.nstages; ++s) {
-      const TileStage st = sst[s];
-      const uint32_t r0 = uint32_t(insert_zero_bits(threadIdx.x, st.sorted, kStageBits));
-      uint32_t sm[kStageBits], sw[kStageBits];
+      const TileStage& st = sst[s];
+      uint32_t r0 = 0;
 #pragma unroll
-      for (int k = 0; k < kStageBits; ++k) {
+      for (int k = 0; k < 8; ++k)
+        if (k < m - SB) r0 |= ((threadIdx.x >> k) & 1u) << st.lane_bit[k];
+      uint32_t sm[SB], sw[SB];
+#pragma unroll
+      for (int k = 0; k < SB; ++k) {
         sm[k] = 1u << st.slot_bit[k];
         sw[k] = tile_swz(sm[k]);  // the swizzle is linear over XOR: swz(a^b) = swz(a)^swz(b)
       }
       const uint32_t p0 = tile_swz(r0);
-      Cplx<R> v[kStageAmps];
+      Cplx<R> v[NA];
 #pragma unroll
-      for (int j = 0; j < kStageAmps; ++j) v[j] = tile[p0 ^ slot_xor(j, sw)];
+      for (int j = 0; j < NA; ++j) v[j] = tile[p0 ^ slot_xor<SB>(j, sw)];
       for (int q = 0; q < st.nops; ++q) {
         const TileOp& op = sop[st.op0 + q];
         if ((base & op.gmask) != op.gval) continue;
         if (op.type == TOP_DENSE1) {
-          apply_dense1<R>(op.s0, v, smat + op.mat, r0, sm, op.lmask, op.lval);
+          apply_dense1<R, SB>(op.s0, v, smat + op.mat, r0, sm, op.lmask, op.lval);
         } else if (op.type == TOP_DENSE2) {
-          apply_dense2<R>(op.s0, op.s1, v, smat + op.mat);
+          apply_dense2<R, SB>(op.s0, op.s1, v, smat + op.mat);
         } else {
           // exp(i (c + sum beta_p b_p)) factorised over: tile-index chunks (3), the
-          // thread's inactive local bits (2 chunks) and the 16 slot combinations
+          // thread's inactive local bits (2 chunks) and the 2^SB slot combinations
           const Cplx<R>* jt = reinterpret_cast<const Cplx<R>*>(smat + op.mat);
           const Cplx<R>* l0 = cpool + op.tab;
           const Cplx<R>* l1 = l0 + (1 << P.c0);
@@ -252,14 +298,14 @@ __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const
           Cplx<R> w = cmul(cmul(g0[t & gm], g0[gn + ((t >> P.cg) & gm)]), g0[2 * gn + ((t >> (2 * P.cg)) & gm)]);
           w = cmul(w, cmul(l0[r0 & ((1u << P.c0) - 1)], l1[r0 >> P.c0]));
 #pragma unroll
-          for (int j = 0; j < kStageAmps; ++j) {
-            if (((r0 | slot_off(j, sm)) & op.lmask) != op.lval) continue;
+          for (int j = 0; j < NA; ++j) {
+            if (((r0 | slot_off<SB>(j, sm)) & op.lmask) != op.lval) continue;
             v[j] = cmul(v[j], cmul(w, jt[j]));
           }
         }
       }
 #pragma unroll
-      for (int j = 0; j < kStageAmps; ++j) tile[p0 ^ slot_xor(j, sw)] = v[j];
+      for (int j = 0; j < NA; ++j) tile[p0 ^ slot_xor<SB>(j, sw)] = v[j];
       __syncthreads();
     }
     for (uint32_t e = threadIdx.x; e < T / 2; e += blockDim.x) {
@@ -346,8 +392,26 @@ static void to_plan_ops(const std::vector<ResolvedOp>& in, std::vector<PlanOp>& 
     const bool diag = r.m[2] == 0 && r.m[3] == 0 && r.m[4] == 0 && r.m[5] == 0;
     if (diag && near_unit(d0) && near_unit(d1)) {
       p.phase = true;
-      p.c = std::arg(d0);
-      p.beta = {{tgt, std::arg(d1) - std::arg(d0)}};
+      if (nc == 1 && r.m[0] == 1.0 && r.m[1] == 0.0) {
+        // a singly controlled phase diag(1, e^{i phi}) is symmetric in its two qubits:
+        // key it on the target bit so that phases sharing a target (e.g. the ladder of
+        // controlled phases in a Fourier transform) merge into one phase op
+        const int cb = r.bits[0];
+        const bool cv = (r.cstate & 1) != 0;
+        p.cmask = p.cval = uint64_t(1) << tgt;
+        p.c = 0.0;
+        const double phi = std::arg(d1);
+        // control state 1: phi * b_c; control state 0: phi * (1 - b_c)
+        if (cv) {
+          p.beta = {{cb, phi}};
+        } else {
+          p.c = phi;
+          p.beta = {{cb, -phi}};
+        }
+      } else {
+        p.c = std::arg(d0);
+        p.beta = {{tgt, std::arg(d1) - std::arg(d0)}};
+      }
     } else {
       p.phase = false;
       p.nt = 1;
@@ -365,53 +429,91 @@ struct BuiltPass {
   std::vector<int> ops;     // indices into plan ops, in order
 };
 
+// One pass over `remaining` in order.  With `fixed` set, B is exactly `B0` (ops whose
+// dense targets are outside it are skipped); otherwise B starts as B0 and grows to m
+// bits with the targets of the first ops that need them.  An op is taken unless it
+// meets a skipped op it may not commute with (shared bits; two diagonal ops commute).
+static void greedy_pass(const std::vector<PlanOp>& ops, const std::vector<int>& remaining, int m, uint64_t B0,
+                        bool fixed, BuiltPass* bp, std::vector<int>* excluded, uint64_t* Bout, double* score) {
+  uint64_t Bmask = B0;
+  int Bcount = __builtin_popcountll(B0);
+  uint64_t blocked_all = 0;   // bits of skipped non-diagonal ops
+  uint64_t blocked_diag = 0;  // bits of skipped diagonal ops
+  double sc = 0.0;
+  for (int idx : remaining) {
+    const PlanOp& p = ops[idx];
+    bool ok = (p.touched & blocked_all) == 0 && int(bp->ops.size()) < kMaxPassOps;
+    if (ok && !p.phase) ok = (p.touched & blocked_diag) == 0;
+    if (ok && !p.phase) {
+      uint64_t need = 0;
+      for (int k = 0; k < p.nt; ++k) need |= uint64_t(1) << p.tb[k];
+      need &= ~Bmask;
+      const int add = __builtin_popcountll(need);
+      if (add == 0) {
+      } else if (!fixed && Bcount + add <= m) {
+        Bmask |= need;
+        Bcount += add;
+      } else {
+        ok = false;
+      }
+    }
+    if (ok) {
+      bp->ops.push_back(idx);
+      sc += p.phase ? 0.1 : double(p.nt);  // rough cost of the work the pass absorbs
+    } else {
+      excluded->push_back(idx);
+      if (p.phase)
+        blocked_diag |= p.touched;
+      else
+        blocked_all |= p.touched;
+    }
+  }
+  *Bout = Bmask;
+  *score = sc;
+}
+
 static std::vector<BuiltPass> build_passes(const std::vector<PlanOp>& ops, int n, int m, int L) {
   std::vector<int> remaining(ops.size());
   for (size_t i = 0; i < ops.size(); ++i) remaining[i] = int(i);
   std::vector<BuiltPass> passes;
+  const uint64_t low = (uint64_t(1) << L) - 1;
+  const int w = m - L;  // free tile bits
   while (!remaining.empty()) {
-    BuiltPass bp;
-    uint64_t Bmask = (uint64_t(1) << L) - 1;
-    int Bcount = L;
-    uint64_t blocked_all = 0;   // bits of excluded non-diagonal ops
-    uint64_t blocked_diag = 0;  // bits of excluded diagonal ops
-    std::vector<int> excluded;
-    for (int idx : remaining) {
-      const PlanOp& p = ops[idx];
-      bool ok = (p.touched & blocked_all) == 0 && int(bp.ops.size()) < kMaxPassOps;
-      if (ok && !p.phase) ok = (p.touched & blocked_diag) == 0;
-      if (ok && !p.phase) {
-        uint64_t need = 0;
-        for (int k = 0; k < p.nt; ++k) need |= uint64_t(1) << p.tb[k];
-        need &= ~Bmask;
-        const int add = __builtin_popcountll(need);
-        if (Bcount + add <= m) {
-          Bmask |= need;
-          Bcount += add;
-        } else {
-          ok = false;
-        }
-      }
-      if (ok) {
-        bp.ops.push_back(idx);
+    // candidates: the growing greedy, and every contiguous window of w index bits next
+    // to the always-present low bits (neighbouring qubits interact in most circuits)
+    BuiltPass best;
+    std::vector<int> best_ex;
+    uint64_t bestB = 0;
+    double best_score = -1.0;
+    for (int cand = -1; cand <= n - w - L; ++cand) {
+      BuiltPass bp;
+      std::vector<int> ex;
+      uint64_t Bm = 0;
+      double sc = 0.0;
+      if (cand < 0) {
+        greedy_pass(ops, remaining, m, low, false, &bp, &ex, &Bm, &sc);
       } else {
-        excluded.push_back(idx);
-        if (p.phase)
-          blocked_diag |= p.touched;
-        else
-          blocked_all |= p.touched;
+        const uint64_t win = ((uint64_t(1) << w) - 1) << (L + cand);
+        greedy_pass(ops, remaining, m, low | win, true, &bp, &ex, &Bm, &sc);
+      }
+      if (sc > best_score + 1e-9) {
+        best_score = sc;
+        best = bp;
+        best_ex = ex;
+        bestB = Bm;
       }
     }
     // fill B up to m bits with the lowest free bits (a full tile)
+    int Bcount = __builtin_popcountll(bestB);
     for (int b = 0; Bcount < m && b < n; ++b)
-      if (!((Bmask >> b) & 1)) {
-        Bmask |= uint64_t(1) << b;
+      if (!((bestB >> b) & 1)) {
+        bestB |= uint64_t(1) << b;
         ++Bcount;
       }
     for (int b = 0; b < n; ++b)
-      if ((Bmask >> b) & 1) bp.B.push_back(b);
-    passes.push_back(bp);
-    remaining.swap(excluded);
+      if ((bestB >> b) & 1) best.B.push_back(b);
+    passes.push_back(best);
+    remaining.swap(best_ex);
   }
   return passes;
 }
@@ -427,7 +529,8 @@ struct HostPlan {
 };
 
 template <typename R>
-static void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int m, int L, HostPlan<R>& hp) {
+static void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int m, int L, int sb,
+                      HostPlan<R>& hp) {
   TilePass P{};
   P.m = m;
   P.L = L;
@@ -467,7 +570,7 @@ static void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int 
           const int lb = local_of[p.tb[k]];
           if (std::find(nw.begin(), nw.end(), lb) == nw.end()) nw.push_back(lb);
         }
-        if (int(nw.size()) > kStageBits)
+        if (int(nw.size()) > sb)
           ok = false;
         else
           act = nw;
@@ -483,13 +586,28 @@ static void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int 
       }
     }
     // pad with unused local bits (lowest first)
-    for (int b = 0; int(act.size()) < kStageBits && b < m; ++b)
+    for (int b = 0; int(act.size()) < sb && b < m; ++b)
       if (std::find(act.begin(), act.end(), b) == act.end()) act.push_back(b);
     TileStage st{};
-    for (int k = 0; k < kStageBits; ++k) st.slot_bit[k] = int8_t(act[k]);
-    std::vector<int> srt = act;
-    std::sort(srt.begin(), srt.end());
-    for (int k = 0; k < kStageBits; ++k) st.sorted[k] = int8_t(srt[k]);
+    for (int k = 0; k < sb; ++k) st.slot_bit[k] = int8_t(act[k]);
+    {
+      // thread-index bits -> non-slot local bits; first one bit per residue mod 4
+      // (4 residues: 8-byte elements, half-warp banks; 3: 16-byte elements)
+      std::vector<int> rest_bits;
+      for (int b = 0; b < m; ++b)
+        if (std::find(act.begin(), act.end(), b) == act.end()) rest_bits.push_back(b);
+      std::vector<int> order;
+      const int nres = sizeof(R) == 4 ? 4 : 3;
+      for (int res = 0; res < nres; ++res)
+        for (int b : rest_bits)
+          if (b % 4 == res && std::find(order.begin(), order.end(), b) == order.end()) {
+            order.push_back(b);
+            break;
+          }
+      for (int b : rest_bits)
+        if (std::find(order.begin(), order.end(), b) == order.end()) order.push_back(b);
+      for (size_t k = 0; k < order.size() && k < 8; ++k) st.lane_bit[k] = int8_t(order[k]);
+    }
     st.op0 = int(hp.ops.size()) - P.op0;
     const size_t j = take.size();
     for (size_t q = 0; q < j; ++q) {
@@ -512,14 +630,26 @@ static void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int 
         op.type = p.nt == 1 ? TOP_DENSE1 : TOP_DENSE2;
         auto slot = [&](int gbit) {
           const int lb = local_of[gbit];
-          for (int k = 0; k < kStageBits; ++k)
+          for (int k = 0; k < sb; ++k)
             if (st.slot_bit[k] == lb) return k;
           return -1;
         };
         op.s0 = slot(p.tb[0]);
         op.s1 = p.nt == 2 ? slot(p.tb[1]) : 0;
         op.mat = int64_t(hp.mats.size()) - P.mat0;
-        for (int e = 0; e < (p.nt == 1 ? 8 : 32); ++e) hp.mats.push_back(R(p.m[e]));
+        if (p.nt == 2 && op.s0 > op.s1) {
+          // the same gate with its qubits listed in the other order: row/column index
+          // 2a+b -> 2b+a
+          std::swap(op.s0, op.s1);
+          for (int r = 0; r < 4; ++r)
+            for (int c = 0; c < 4; ++c) {
+              const int rr = ((r & 1) << 1) | (r >> 1), cc = ((c & 1) << 1) | (c >> 1);
+              hp.mats.push_back(R(p.m[2 * (4 * rr + cc)]));
+              hp.mats.push_back(R(p.m[2 * (4 * rr + cc) + 1]));
+            }
+        } else {
+          for (int e = 0; e < (p.nt == 1 ? 8 : 32); ++e) hp.mats.push_back(R(p.m[e]));
+        }
       } else {
         // merge following phase ops with the same condition (they commute)
         op.type = TOP_PHASE;
@@ -541,9 +671,9 @@ static void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int 
           hp.pool.push_back(R(std::sin(ang)));
         };
         op.mat = int64_t(hp.mats.size()) - P.mat0;
-        for (int jj = 0; jj < kStageAmps; ++jj) {
+        for (int jj = 0; jj < (1 << sb); ++jj) {
           double a = 0;
-          for (int k = 0; k < kStageBits; ++k)
+          for (int k = 0; k < sb; ++k)
             if ((jj >> k) & 1) a += beta[bp.B[st.slot_bit[k]]];
           hp.mats.push_back(R(std::cos(a)));
           hp.mats.push_back(R(std::sin(a)));
@@ -591,11 +721,12 @@ template <typename R>
 static qc_status run_tiles(qc_state* s, const std::vector<ResolvedOp>& rops, int m) {
   const int n = s->n;
   const int L = sizeof(R) == 4 ? 4 : 3;
+  constexpr int SB = sizeof(R) == 4 ? 5 : 4;  // register tile: 32 (complex64) / 16 amplitudes
   std::vector<PlanOp> pops;
   to_plan_ops(rops, pops);
   std::vector<BuiltPass> bps = build_passes(pops, n, m, L);
   HostPlan<R> hp;
-  for (const BuiltPass& bp : bps) emit_pass<R>(bp, pops, n, m, L, hp);
+  for (const BuiltPass& bp : bps) emit_pass<R>(bp, pops, n, m, L, SB, hp);
   g_last_pass_count = int(hp.passes.size());
   // upload stages, ops, tables and matrices into the state's scratch (stream ordered)
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
@@ -618,22 +749,25 @@ static qc_status run_tiles(qc_state* s, const std::vector<ResolvedOp>& rops, int
   const TileOp* dop = reinterpret_cast<const TileOp*>(base + sb);
   const R* dpool = reinterpret_cast<const R*>(base + sb + ob);
   const R* dmats = reinterpret_cast<const R*>(base + sb + ob + pb);
-  const int threads = 1 << (m - kStageBits);
+  const int threads = 1 << (m - SB);
   size_t plan_max = 0;
   for (const TilePass& P : hp.passes)
     plan_max = std::max(plan_max, P.nstages * sizeof(TileStage) + P.nops * sizeof(TileOp) + P.nmat * sizeof(R));
   const size_t smem = 2 * sizeof(Cplx<R>) * (size_t(1) << m) + sizeof(uint64_t) * (size_t(1) << (m - L)) + plan_max;
-  constexpr int NT = sizeof(R) == 4 ? 512 : 256;
-  cudaFuncSetAttribute(k_tile_pass<R, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+  constexpr int NT = 256;
+  if (qc_status st = check_cuda(
+          cudaFuncSetAttribute(k_tile_pass<R, NT, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
+          "tile pass shared memory"))
+    return st;
   const uint64_t ntiles = uint64_t(1) << (n - m);
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_pass<R, NT>, threads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_pass<R, NT, SB>, threads, smem);
   if (per_sm < 1) per_sm = 1;
   const uint64_t cap = uint64_t(device_sm_count()) * per_sm;
   const unsigned grid = unsigned(ntiles < cap ? ntiles : cap);
   R* a = reinterpret_cast<R*>(s->amps);
   for (const TilePass& P : hp.passes) {
-    QC_COUNT(), k_tile_pass<R, NT><<<grid, threads, smem, s->stream>>>(a, P, dst, dop, dpool, dmats);
+    QC_COUNT(), k_tile_pass<R, NT, SB><<<grid, threads, smem, s->stream>>>(a, P, dst, dop, dpool, dmats);
   }
   return check_launch("tile pass");
 }
@@ -649,10 +783,49 @@ qc_status run_fused(qc_state* s, const qc_circuit* c, const double* params, qc_p
   for (int i = 0; i < c->nops; ++i)
     if (qc_status st = resolve_op(c, c->ops[i], params, &rops[i])) return st;
   const int m = tile_bits_for(s);
-  if (s->n < 10 || m < kStageBits + 4) return run_per_gate(s, c, params);
+  if (s->n < 10 || m < kMaxStageBits + 4) return run_per_gate(s, c, params);
   return s->dtype == QC_C64 ? run_tiles<float>(s, rops, m) : run_tiles<double>(s, rops, m);
+}
+
+template <typename R>
+static void plan_stats(int n, const std::vector<ResolvedOp>& rops, int m, int* passes, int* stages, int* ops) {
+  const int L = sizeof(R) == 4 ? 4 : 3;
+  constexpr int SB = sizeof(R) == 4 ? 5 : 4;
+  std::vector<PlanOp> pops;
+  to_plan_ops(rops, pops);
+  std::vector<BuiltPass> bps = build_passes(pops, n, m, L);
+  HostPlan<R> hp;
+  for (const BuiltPass& bp : bps) emit_pass<R>(bp, pops, n, m, L, SB, hp);
+  *passes = int(hp.passes.size());
+  *stages = int(hp.stages.size());
+  *ops = int(hp.ops.size());
 }
 
 }  // namespace qcgb
 
+using namespace qcgb;
+
 extern "C" int qc_last_pass_count(void) { return qcgb::g_last_pass_count; }
+
+extern "C" qc_status qc_plan_info(const qc_circuit* c, const double* params, qc_dtype dtype, int* passes,
+                                  int* stages, int* ops) {
+  clear_error();
+  if (!c || c->n < 1 || c->n > 34 || (c->nops > 0 && !c->ops) || !passes || !stages || !ops ||
+      (dtype != QC_C64 && dtype != QC_C128)) {
+    set_error("qc_plan_info: invalid arguments");
+    return QC_ERR_INVALID_ARG;
+  }
+  std::vector<ResolvedOp> rops(c->nops);
+  for (int i = 0; i < c->nops; ++i)
+    if (qc_status st = resolve_op(c, c->ops[i], params, &rops[i])) return st;
+  const int m = std::min(dtype == QC_C64 ? 13 : 12, c->n);
+  if (c->n < 10) {
+    *passes = *stages = *ops = 0;
+    return QC_OK;
+  }
+  if (dtype == QC_C64)
+    plan_stats<float>(c->n, rops, m, passes, stages, ops);
+  else
+    plan_stats<double>(c->n, rops, m, passes, stages, ops);
+  return QC_OK;
+}

@@ -169,6 +169,19 @@ __global__ void __launch_bounds__(256) k_1q_dense(R* __restrict__ a, SweepSpec s
   }
 }
 
+// Dense 2x2 on bit 0: each pair is one 16-byte-aligned neighbour pair (i, i+1).
+template <typename R>
+__global__ void __launch_bounds__(256) k_1q_dense_low(R* __restrict__ a, SweepSpec sp, Mat2<R> u) {
+  const Cplx<R> u00{u.m[0], u.m[1]}, u01{u.m[2], u.m[3]}, u10{u.m[4], u.m[5]}, u11{u.m[6], u.m[7]};
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t it = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; it < sp.items; it += stride) {
+    const uint64_t i0 = insert_zero_bits(it, sp.pos, sp.cnt) | sp.set_mask;
+    Cplx<R> x, y;
+    ld_amp2<R>(a, i0, x, y);
+    st_amp2<R>(a, i0, cmul2(u00, x, u01, y), cmul2(u10, x, u11, y));
+  }
+}
+
 // Diagonal diag(d0, d1).  ONLY1: d0 == 1, only the bit-set member is touched
 // (the target bit is part of sp.set_mask then).
 template <typename R, bool VEC, bool ONLY1>
@@ -262,6 +275,43 @@ __global__ void __launch_bounds__(256) k_2q_dense(R* __restrict__ a, SweepSpec s
         Cplx<R> o0 = cmul2(u0, x[0], u1, x[1]), o0b = cmul2(u2, x[2], u3, x[3]);
         st_amp<R>(a, idx[r], Cplx<R>{o0.re + o0b.re, o0.im + o0b.im});
       }
+    }
+  }
+}
+
+// Dense 4x4 when bit 0 is one of the two targets: the quad is two 16-byte-aligned
+// neighbour pairs, (b, b|1) and (b|m, b|m|1), m the other target's mask.  qa_low: bit 0
+// belongs to the first qubit (row index 2*b_qa + b_qb).
+template <typename R>
+__global__ void __launch_bounds__(256) k_2q_dense_low(R* __restrict__ a, SweepSpec sp, Mat4<R> u, bool qa_low) {
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  const uint64_t mo = qa_low ? sp.t1 : sp.t0;  // mask of the other target
+  for (uint64_t it = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; it < sp.items; it += stride) {
+    const uint64_t b = insert_zero_bits(it, sp.pos, sp.cnt);
+    Cplx<R> p0, p1, q0, q1;  // p = (b, b|1), q = (b|mo, b|mo|1)
+    ld_amp2<R>(a, b, p0, p1);
+    ld_amp2<R>(a, b | mo, q0, q1);
+    // x[r], r = 2*b_qa + b_qb
+    Cplx<R> x[4];
+    if (qa_low) {
+      x[0] = p0; x[2] = p1; x[1] = q0; x[3] = q1;
+    } else {
+      x[0] = p0; x[1] = p1; x[2] = q0; x[3] = q1;
+    }
+    Cplx<R> y[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const Cplx<R> u0{u.m[8 * r + 0], u.m[8 * r + 1]}, u1{u.m[8 * r + 2], u.m[8 * r + 3]};
+      const Cplx<R> u2{u.m[8 * r + 4], u.m[8 * r + 5]}, u3{u.m[8 * r + 6], u.m[8 * r + 7]};
+      const Cplx<R> o0 = cmul2(u0, x[0], u1, x[1]), o1 = cmul2(u2, x[2], u3, x[3]);
+      y[r] = Cplx<R>{o0.re + o1.re, o0.im + o1.im};
+    }
+    if (qa_low) {
+      st_amp2<R>(a, b, y[0], y[2]);
+      st_amp2<R>(a, b | mo, y[1], y[3]);
+    } else {
+      st_amp2<R>(a, b, y[0], y[1]);
+      st_amp2<R>(a, b | mo, y[2], y[3]);
     }
   }
 }
@@ -362,7 +412,7 @@ static qc_status launch_1q(qc_state* s, int tbit, const std::vector<int>& cbits,
     if (vec)
       QC_COUNT(), k_1q_dense<R, true><<<g, B, 0, s->stream>>>(a, sp, m);
     else
-      QC_COUNT(), k_1q_dense<R, false><<<g, B, 0, s->stream>>>(a, sp, m);
+      QC_COUNT(), (tbit == 0 ? k_1q_dense_low<R> : k_1q_dense<R, false>)<<<g, B, 0, s->stream>>>(a, sp, m);
   }
   return check_launch("single-qubit gate");
 }
@@ -386,6 +436,8 @@ static qc_status launch_2q(qc_state* s, int pa, int pb, const double* U) {
   for (int i = 0; i < 32; ++i) m.m[i] = R(U[i]);
   if (vec)
     QC_COUNT(), k_2q_dense<R, true><<<g, B, 0, s->stream>>>(a, sp, m);
+  else if (pa == 0 || pb == 0)
+    QC_COUNT(), k_2q_dense_low<R><<<g, B, 0, s->stream>>>(a, sp, m, pa == 0);
   else
     QC_COUNT(), k_2q_dense<R, false><<<g, B, 0, s->stream>>>(a, sp, m);
   return check_launch("two-qubit gate");
