@@ -310,6 +310,37 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def run_batch_bench(args):
+    """Opt-in secondary measurement: the 4096-circuit batched ansatz workload (n uniform
+    in 12..20, 8 layers, seed 4), one persistent launch per step, replayed from a CUDA
+    graph; prints its own JSON line."""
+    import torch
+
+    import paper_2503_03016_gb300 as P
+    torch.cuda.set_device(0)
+    layers = 8
+    ns, params = W.batch_workload(4096, layers, 12, 20, 4)
+    offs = np.cumsum([0] + [p.size for p in params[:-1]]).astype(np.int64)
+    flat = np.concatenate(params).astype(np.float32)
+    dparams = torch.tensor(flat, device="cuda")
+    out = torch.empty(len(ns), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    nsi = np.asarray(ns, dtype=np.int32)
+    for _ in range(max(args.warmup, 1)):
+        P.qc_run_batch(nsi, layers, offs, dparams, flat.size, out)
+    torch.cuda.synchronize()
+    timer = StreamTimer(stream)
+    timer.start()
+    for _ in range(args.steps):
+        P.qc_run_batch(nsi, layers, offs, dparams, flat.size, out)
+    ms = timer.stop() / args.steps
+    flops = sum(8.0 * layers * 2 * int(n) * (1 << int(n)) for n in ns)
+    print(json.dumps({"metric": "batched ansatz circuits/s", "value": len(ns) / (ms * 1e-3), "unit": "circuits/s",
+                      "ms_per_step": ms, "steps": args.steps, "fusion_width": P.qc_batch_fusion_width(),
+                      "approx_fp32_tflops": flops / (ms * 1e-3) / 1e12,
+                      "config": {"workload": "4096 ansatz circuits, n in 12..20, 8 layers RY.RZ + CZ chain, <ZZ>"}}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -322,10 +353,14 @@ def main():
     ap.add_argument("--cpu-gates", type=int, default=24)
     ap.add_argument("--ref-gates", type=int, default=8)
     ap.add_argument("--qubits", type=int, default=28, help="smaller cases for profiling only")
+    ap.add_argument("--workload", default="brickwork", choices=["brickwork", "batch"],
+                    help="batch: opt-in secondary measurement of the batched launch")
     args = ap.parse_args()
     global N_QUBITS
     N_QUBITS = args.qubits
-    if args.impl == "reference":
+    if args.workload == "batch" and args.impl == "ours":
+        run_batch_bench(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -282,7 +282,7 @@ qc_status qc_adjoint_grad(const qc_circuit* c, const double* params, int nparams
                           double* host_grad);
 
 /* A batch of independent parameterised circuits of uneven qubit counts evaluated
- * in one persistent launch (complex64).  Circuit b has n[b] qubits (2 <= n <= 20)
+ * in one persistent launch (complex64).  Circuit b has n[b] qubits (6 <= n <= 20)
  * and runs `layers` layers of [RY(t) then RZ(t) on every qubit, then CZ(i, i+1),
  * i = 0..n-2], parameter index layer*2n + 2q + {0: RY, 1: RZ}, from |0...0>, reading
  * its parameters from params + param_offset[b] (device memory).  dev_out[b] =
@@ -297,6 +297,9 @@ typedef struct qc_batch {
 } qc_batch;
 
 qc_status qc_run_batch(const qc_batch* b, void* stream, double* dev_out);
+/* Fusion width (register-stage bits, 4 or 5) the autotuner chose for the most recent
+ * qc_run_batch workload (diagnostic). */
+int qc_batch_fusion_width(void);
 
 #ifdef __cplusplus
 }

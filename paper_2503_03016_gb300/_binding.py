@@ -86,6 +86,7 @@ _SIGS = {
                                        ctypes.POINTER(ctypes.c_char_p), _D, ctypes.c_int, ctypes.c_int, _P, _D,
                                        _D]),
     "qc_run_batch": (ctypes.c_int, [ctypes.POINTER(qc_batch), _P, _P]),
+    "qc_batch_fusion_width": (ctypes.c_int, []),
 }
 
 _lib = None
@@ -381,3 +382,7 @@ def qc_run_batch(ns, layers: int, param_offsets, dev_params, nparams: int, out, 
     b = qc_batch(len(ns), layers, ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
                  offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _ptr(dev_params), int(nparams))
     _call("qc_run_batch", ctypes.byref(b), _stream(stream), _ptr(out))
+
+
+def qc_batch_fusion_width() -> int:
+    return int(lib().qc_batch_fusion_width())

@@ -1,0 +1,320 @@
+// Fused k-qubit blocks on the tensor cores (QC_PREC_TF32X3, complex64).
+//
+// A block U (2^k x 2^k, Sec. 3.2's U' for k qubits) maps each group of 2^k amplitudes
+// that differ only in the block's bits: out_d = sum_c U[d][c] in_c.  With the groups as
+// rows this is one real GEMM D = A B over interleaved (re, im) columns:
+//   A[r][2c + ri] = (re, im)_ri of amplitude (row r, column c),
+//   B[2c][2d] = Ur[d][c], B[2c+1][2d] = -Ui[d][c], B[2c][2d+1] = Ui[d][c], B[2c+1][2d+1] = Ur[d][c].
+// TF32 keeps 10 mantissa bits, so each product is split as
+//   a*b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi,  a_hi = a with the low 13 mantissa bits
+// cleared, a_lo = a - a_hi (exact), the same for b; the three products accumulate in
+// FP32 in tensor memory (TMEM).
+//
+// Kernel shape (k = 5: K = N = 64 real columns): one CTA of 128 threads handles tiles of
+// 128 rows.  Threads gather their row's 32 amplitudes (8-byte loads, coalesced across
+// the warp when index bit 0 is a row bit), split them and store A_hi / A_lo in the
+// canonical K-major layout with the 128-byte swizzle (8-row x 128-byte atoms, 16-byte
+// chunk c of row r at c ^ (r mod 8)).  One elected thread issues 3 x 8 tcgen05.mma
+// (M=128, N=64, K=8, kind::tf32) and commits them to an mbarrier; every thread waits
+// (bounded), reads its row of D from TMEM (tcgen05.ld 32x32b) and scatters it back.  B_hi /
+// B_lo stay in shared memory for the whole launch.  Smaller blocks (k < 5) are padded
+// with identity qubits.
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "circuit.cuh"
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace qcgb {
+
+constexpr int kTcK = 5;                     // block qubits
+constexpr int kTcCols = 2 << kTcK;          // 64 real columns (K = N)
+constexpr int kTcRows = 128;                // rows per tile (MMA M)
+constexpr int kTcAtom = 1024;               // 8 rows x 128 bytes
+constexpr int kTcAregion = kTcRows * 128;   // one 32-float K slice of A: 16 KiB
+constexpr int kTcBregion = kTcCols * 128;   // one 32-float K slice of B: 8 KiB
+constexpr int kTcKslices = kTcCols / 32;    // 2
+// shared memory: A_hi, A_lo (2 x 32 KiB), B_hi, B_lo (2 x 16 KiB), offsets, barrier
+constexpr int kTcSmem = 2 * kTcKslices * kTcAregion + 2 * kTcKslices * kTcBregion + 1024 + 1024;
+constexpr long long kTcSpinLimit = 1ll << 24;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return uint32_t(__cvta_generic_to_shared(p)); }
+
+// byte offset of element (row, col) (32-bit elements) in a K-major SWIZZLE_128B operand
+// with `rows` rows: K slices of 32 columns, each slice rows x 128 bytes
+__device__ __host__ __forceinline__ uint32_t sw128_offset(int row, int col, int rows) {
+  const int slice = col >> 5;
+  const int b = (col & 31) * 4;  // byte within the 128-byte row of the slice
+  const int chunk = b >> 4;
+  return uint32_t(slice * rows * 128 + (row >> 3) * kTcAtom + (row & 7) * 128 + ((chunk ^ (row & 7)) << 4) +
+                  (b & 15));
+}
+
+// sm_100 shared-memory matrix descriptor: start address, leading byte offset, stride
+// byte offset (between 8-row groups), version 1, layout SWIZZLE_128B (2)
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= uint64_t((saddr & 0x3FFFF) >> 4);
+  d |= uint64_t(16 >> 4) << 16;
+  d |= uint64_t(sbo >> 4) << 32;
+  d |= uint64_t(1) << 46;
+  d |= uint64_t(2) << 61;
+  return d;
+}
+
+// instruction descriptor: D = F32, A = B = TF32, both K-major, N, M
+__host__ __device__ constexpr uint32_t tf32_idesc(int M, int N) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mma(uint32_t dtm, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtm),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+}
+
+// bsplit: [B_hi (64x64)][B_lo (64x64)] fp32, then 32 uint64 column offsets, then 5 int32
+// ascending block bit positions (row -> index: zero bits inserted there)
+__global__ void __launch_bounds__(kTcRows, 1) k_block_tc(float* __restrict__ amps, uint64_t ntiles,
+                                                         const float* __restrict__ bsplit, int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  // 1024-byte aligned regions (the swizzle pattern is taken from address bits 4..9)
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* a_hi = base;
+  unsigned char* a_lo = a_hi + kTcKslices * kTcAregion;
+  unsigned char* b_hi = a_lo + kTcKslices * kTcAregion;
+  unsigned char* b_lo = b_hi + kTcKslices * kTcBregion;
+  uint64_t* offs = reinterpret_cast<uint64_t*>(b_lo + kTcKslices * kTcBregion);  // 32 column offsets
+  uint64_t* bar = offs + 32;  // 8-byte aligned
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
+  int8_t* spos = reinterpret_cast<int8_t*>(tmem_slot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // B_hi / B_lo (host-split, [n][k] row-major fp32) into the swizzled K-major layout
+  for (int i = tid; i < kTcCols * kTcCols; i += blockDim.x) {
+    const int n = i / kTcCols, k = i % kTcCols;
+    *reinterpret_cast<float*>(b_hi + sw128_offset(n, k, kTcCols)) = bsplit[i];
+    *reinterpret_cast<float*>(b_lo + sw128_offset(n, k, kTcCols)) = bsplit[kTcCols * kTcCols + i];
+  }
+  const uint64_t* goffs = reinterpret_cast<const uint64_t*>(bsplit + 2 * kTcCols * kTcCols);
+  const int* gpos = reinterpret_cast<const int*>(goffs + 32);
+  if (tid < 32) offs[tid] = goffs[tid];
+  if (tid < kTcK) spos[tid] = int8_t(gpos[tid]);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                 "r"(64)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  constexpr uint32_t idesc = tf32_idesc(kTcRows, kTcCols);
+  uint32_t phase = 0;
+  bool failed = false;
+
+  for (uint64_t t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+    // gather this thread's row, split into hi / lo
+    const uint64_t row = t * kTcRows + tid;
+    const uint64_t rb = insert_zero_bits(row, spos, kTcK);
+    float2 x[32];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) x[c] = reinterpret_cast<const float2*>(amps)[rb | offs[c]];
+#pragma unroll
+    for (int c = 0; c < 32; ++c) {
+      const float re_hi = __uint_as_float(__float_as_uint(x[c].x) & 0xFFFFE000u);
+      const float im_hi = __uint_as_float(__float_as_uint(x[c].y) & 0xFFFFE000u);
+      const uint32_t o = sw128_offset(tid, 2 * c, kTcRows);  // 8-byte pair stays in one chunk
+      *reinterpret_cast<float2*>(a_hi + o) = make_float2(re_hi, im_hi);
+      *reinterpret_cast<float2*>(a_lo + o) = make_float2(x[c].x - re_hi, x[c].y - im_hi);
+    }
+    // make the generic-proxy shared-memory writes visible to the tensor cores
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (tid == 0) {
+      const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+      int first = 1;
+      for (int prod = 0; prod < 3; ++prod) {
+        const uint32_t A = prod == 2 ? al : ah;
+        const uint32_t B = prod == 1 ? bl : bh;
+        for (int ks = 0; ks < kTcCols / 8; ++ks) {
+          const uint32_t koff = uint32_t((ks & 3) * 32);  // 8 tf32 = 32 bytes per K step
+          const uint64_t ad = sw128_desc(A + (ks >> 2) * kTcAregion + koff, kTcAtom);
+          const uint64_t bd = sw128_desc(B + (ks >> 2) * kTcBregion + koff, kTcAtom);
+          tc_mma(tmem, ad, bd, idesc, first ? 0u : 1u);
+          first = 0;
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       smem_u32(bar))
+                   : "memory");
+    }
+    // bounded wait for the products
+    {
+      uint32_t done = 0;
+      for (long long it = 0; it < kTcSpinLimit; ++it) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(phase)
+            : "memory");
+        if (done) break;
+      }
+      // block-uniform outcome
+      failed = __syncthreads_or(done ? 0 : 1) != 0;
+      if (failed && tid == 0) atomicExch(status, 1);
+    }
+    phase ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    if (!failed) {
+      // row tid of D: TMEM lane tid, 64 columns
+      float out[64];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        uint32_t r[16];
+        tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(q * 16), r);
+        asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+        for (int i = 0; i < 16; ++i) out[q * 16 + i] = __uint_as_float(r[i]);
+      }
+#pragma unroll
+      for (int d = 0; d < 32; ++d)
+        reinterpret_cast<float2*>(amps)[rb | offs[d]] = make_float2(out[2 * d], out[2 * d + 1]);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    // a timed-out block stops; the others stop at their next tile (block-uniform test)
+    failed = __syncthreads_or(*((volatile int*)status) != 0) != 0;
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(64) : "memory");
+  (void)lane;
+}
+
+// host: real form of U on 5 qubits (k < 5 padded with identity qubits), split hi / lo
+static void tc_bmatrix(const std::vector<double>& U5, std::vector<float>& out) {
+  const int D = 1 << kTcK;
+  out.assign(2 * kTcCols * kTcCols, 0.0f);
+  auto hi_of = [](float v) {
+    uint32_t u;
+    memcpy(&u, &v, 4);
+    u &= 0xFFFFE000u;
+    float h;
+    memcpy(&h, &u, 4);
+    return h;
+  };
+  for (int d = 0; d < D; ++d)
+    for (int c = 0; c < D; ++c) {
+      const double ur = U5[2 * (d * D + c)], ui = U5[2 * (d * D + c) + 1];
+      // Bt[n][k] with n = output column, k = input column
+      const float vals[4] = {float(ur), float(-ui), float(ui), float(ur)};
+      const int ns[4] = {2 * d, 2 * d, 2 * d + 1, 2 * d + 1};
+      const int ks[4] = {2 * c, 2 * c + 1, 2 * c, 2 * c + 1};
+      for (int e = 0; e < 4; ++e) {
+        const float v = vals[e], h = hi_of(v);
+        out[ns[e] * kTcCols + ks[e]] = h;
+        out[kTcCols * kTcCols + ns[e] * kTcCols + ks[e]] = v - h;
+      }
+    }
+}
+
+static int g_tc_status_dummy = 0;
+
+qc_status apply_kq_tf32x3(qc_state* s, const int* bits, int k, const double* U) {
+  if (s->dtype != QC_C64 || k < 1 || k > kTcK || s->n < kTcK + 7) {
+    set_error("TF32x3 blocks need complex64, k <= %d and n >= %d", kTcK, kTcK + 7);
+    return QC_ERR_UNSUPPORTED;
+  }
+  // pad with the lowest bits not in the block: U5 = U (x) I on (bits..., extra...)
+  int b5[kTcK];
+  for (int j = 0; j < k; ++j) b5[j] = bits[j];
+  int kk = k;
+  for (int b = 0; kk < kTcK && b < s->n; ++b) {
+    bool used = false;
+    for (int j = 0; j < kk; ++j) used |= (b5[j] == b);
+    if (!used) b5[kk++] = b;
+  }
+  const int D = 1 << kTcK, Dk = 1 << k, Dp = 1 << (kTcK - k);
+  std::vector<double> U5(2 * D * D, 0.0);
+  for (int r = 0; r < D; ++r)
+    for (int c = 0; c < D; ++c) {
+      if ((r % Dp) != (c % Dp)) continue;
+      const int rr = r / Dp, cc = c / Dp;
+      U5[2 * (r * D + c)] = U[2 * (rr * Dk + cc)];
+      U5[2 * (r * D + c) + 1] = U[2 * (rr * Dk + cc) + 1];
+    }
+  std::vector<float> bs;
+  tc_bmatrix(U5, bs);
+  KqSpec sp{};
+  std::vector<int> sorted(b5, b5 + kTcK);
+  std::sort(sorted.begin(), sorted.end());
+  sp.cnt = kTcK;
+  for (int j = 0; j < kTcK; ++j) sp.pos[j] = int8_t(sorted[j]);
+  for (int r = 0; r < D; ++r) {
+    uint64_t off = 0;
+    for (int j = 0; j < kTcK; ++j)
+      if ((r >> (kTcK - 1 - j)) & 1) off |= uint64_t(1) << b5[j];
+    sp.off[r] = off;
+  }
+  // device buffers: status word + split B + offsets + positions, in the state's scratch
+  {
+    const size_t nb = bs.size();
+    bs.resize(nb + 32 * 2 + kTcK);
+    uint64_t o64[32];
+    for (int r = 0; r < 32; ++r) o64[r] = sp.off[r];
+    memcpy(bs.data() + nb, o64, sizeof(o64));
+    int p32[kTcK];
+    for (int j = 0; j < kTcK; ++j) p32[j] = sp.pos[j];
+    memcpy(bs.data() + nb + 64, p32, sizeof(p32));
+  }
+  void* scr = nullptr;
+  const size_t bbytes = sizeof(float) * bs.size();
+  if (qc_status st = state_scratch(s, 256 + bbytes, &scr)) return st;
+  int* status = reinterpret_cast<int*>(scr);
+  float* dB = reinterpret_cast<float*>(static_cast<char*>(scr) + 256);
+  if (qc_status st = check_cuda(cudaMemsetAsync(status, 0, sizeof(int), s->stream), "status reset")) return st;
+  if (qc_status st = check_cuda(cudaMemcpyAsync(dB, bs.data(), bbytes, cudaMemcpyHostToDevice, s->stream), "B upload"))
+    return st;
+  if (qc_status st = check_cuda(cudaFuncSetAttribute(k_block_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem),
+                                "tc smem"))
+    return st;
+  const uint64_t ntiles = (state_len(s) >> kTcK) / kTcRows;
+  const unsigned grid = unsigned(std::min<uint64_t>(ntiles, uint64_t(device_sm_count()) * 2));
+  QC_COUNT(), k_block_tc<<<grid, kTcRows, kTcSmem, s->stream>>>(reinterpret_cast<float*>(s->amps), ntiles, dB, status);
+  if (qc_status st = check_launch("tensor-core block")) return st;
+  int h = 0;
+  if (qc_status st = check_cuda(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s->stream), "status"))
+    return st;
+  if (qc_status st = check_cuda(cudaStreamSynchronize(s->stream), "tensor-core block")) return st;
+  if (h != 0) {
+    set_error("tensor-core block: a bounded wait for the MMA completion ran out");
+    return QC_ERR_TIMEOUT;
+  }
+  (void)g_tc_status_dummy;
+  return QC_OK;
+}
+
+}  // namespace qcgb

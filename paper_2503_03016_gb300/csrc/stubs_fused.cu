@@ -2,14 +2,6 @@
 #include "circuit.cuh"
 
 namespace qcgb {
-qc_status apply_kq_tf32x3(qc_state* s, const int* bits, int k, const double* U) {
-  (void)s; (void)bits; (void)k; (void)U;
-  set_error("TF32x3 fused blocks are not built yet");
-  return QC_ERR_UNSUPPORTED;
-}
+
 }  // namespace qcgb
 
-extern "C" qc_status qc_run_batch(const qc_batch*, void*, double*) {
-  qcgb::set_error("qc_run_batch is not built yet");
-  return QC_ERR_UNSUPPORTED;
-}

@@ -1,0 +1,55 @@
+"""Tensor-core fused blocks (qc_apply_fused_k with QC_PREC_TF32X3, tcgen05 kind::tf32
+with the three-product split) against the oracle's dense k-qubit block."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+from gpu_util import gpu_state, need_gpu, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def test_tc_identity_within_split_error():
+    """With U = I the three products give a_hi + a_lo with a_lo truncated to TF32 by
+    the tensor core: relative error per element below 2^-21."""
+    import paper_2503_03016_gb300 as P
+    n = 12
+    psi = W.random_state(n, 1).astype(np.complex64)
+    st = gpu_state(psi, "c64")
+    P.qc_apply_fused_k(st.handle, [0, 3, 5, 7, 11], np.eye(32), P.QC_PREC_TF32X3)
+    got = st.numpy()
+    err = np.abs(got - psi) / np.maximum(np.abs(psi), 1e-30)
+    assert err.max() < 2.0 ** -21, err.max()
+
+
+@pytest.mark.parametrize("n", [12, 14])
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
+def test_tc_block_vs_oracle(n, k):
+    import paper_2503_03016_gb300 as P
+    rng = np.random.default_rng(10 * n + k)
+    for trial in range(3):
+        qs = [int(x) for x in rng.permutation(n)[:k]]
+        U = W.haar_unitaries(1, 1 << k, 100 * k + trial)[0]
+        psi = W.random_state(n, trial)
+        st = gpu_state(psi, "c64")
+        P.qc_apply_fused_k(st.handle, qs, U, P.QC_PREC_TF32X3)
+        want = psi.copy()
+        oracle.apply_kq(want, qs, U)
+        assert rel_l2(st.numpy(), want) <= 1e-5, (qs, rel_l2(st.numpy(), want))
+
+
+def test_tc_rejects_unsupported():
+    import paper_2503_03016_gb300 as P
+    st = gpu_state(W.random_state(12, 0), "c128")
+    with pytest.raises(P.QCError):
+        P.qc_apply_fused_k(st.handle, [0, 1], np.eye(4), P.QC_PREC_TF32X3)
+    st = gpu_state(W.random_state(10, 0), "c64")
+    with pytest.raises(P.QCError):
+        P.qc_apply_fused_k(st.handle, [0, 1], np.eye(4), P.QC_PREC_TF32X3)
