@@ -120,9 +120,17 @@ def max_over_ranks(x: float, world: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def whole_job_rate(ms_local: float, steps: int, world: int):
+    """(value, ms_max): every rank ran `steps` independent circuits; the whole job's
+    throughput is all ranks' circuits over the slowest rank's time."""
+    ms_max = max_over_ranks(ms_local, world)
+    return steps * world / (ms_max * 1e-3), ms_max
 
 
 # ---------------------------------------------------------------------------
@@ -236,7 +244,7 @@ def run_ours(args):
     launches = P.qc_launch_count() - launches0
     torch.cuda.synchronize()
     barrier(world)
-    ms_max = max_over_ranks(ms, world)
+    value, ms_max = whole_job_rate(ms, args.steps, world)
 
     # end to end through the public API: host uniforms in, host samples out
     torch.cuda.synchronize()
@@ -274,8 +282,27 @@ def run_ours(args):
 
     sbytes = (1 << N_QUBITS) * 8
     passes = P.qc_last_pass_count() if args.mode == "fused" else len(ops)
-    algo_bytes = (passes or len(ops)) * 2 * sbytes
-    achieved = algo_bytes / (circ_ms * 1e-3) / 1e9
+    if args.mode == "fused":
+        # dominant kernel: the tile pass, bound by FP32 FMA for Haar gates.  Algorithmic
+        # work: every two-qubit gate is 4 complex multiply-adds (32 flops) per amplitude.
+        # Peak from unit counts: SMs x 128 FP32 lanes x 2 flops x SM clock under load.
+        flops = len(ops) * 32.0 * (1 << N_QUBITS)
+        sm_mhz = (clk.get("sm_mhz") or 2070.0) if isinstance(clk, dict) else 2070.0
+        peak = torch.cuda.get_device_properties(0).multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+        achieved = flops / (circ_ms * 1e-3) / 1e12
+        # ncu: 1013.25 MB per pass at 26 qubits (profiles/k_tile_pass_brickwork_n26.md),
+        # scaled by the 4x larger state
+        traffic = 1013.250304e6 * (1 << (N_QUBITS - 26))
+        roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "traffic_note": "per pass, ncu at 26 qubits scaled x4",
+                "algorithmic_bytes_per_pass": 2 * sbytes, "hbm_gbs_over_passes": passes * 2 * sbytes / (circ_ms * 1e-3) / 1e9,
+                "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz" % sm_mhz,
+                "kernel": "k_tile_pass<float,256,5>", "passes": passes}
+    else:
+        algo_bytes = len(ops) * 2 * sbytes
+        achieved = algo_bytes / (circ_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s", "frac": achieved / hbm_gbs,
+                "traffic": None, "peak_source": peak_src, "kernel": "k_2q_dense<float,1>", "launches": len(ops)}
     # cpu baseline (rank 0, N=1 only)
     cpu = None
     if rank == 0 and world == 1 and args.cpu_gates > 0:
@@ -285,7 +312,7 @@ def run_ours(args):
     if rank == 0:
         steps_total = args.steps * world
         line = {
-            "metric": METRIC, "value": steps_total / (ms_max * 1e-3), "unit": "circuits/s", "n_gpus": world,
+            "metric": METRIC, "value": value, "unit": "circuits/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
             "data": "synthetic",
@@ -294,9 +321,7 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (2 GiB state)"},
             "circuit_ms": circ_ms,
             "plain_fp64": plain,
-            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_gbs, "unit": "GB/s",
-                         "frac": achieved / hbm_gbs, "traffic": None, "peak_source": peak_src,
-                         "kernel": "circuit (%s)" % args.mode, "passes": passes},
+            "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": {"value": steps_total / (e2e_ms * 1e-3), "unit": "circuits/s",
                     "h2d_bytes_per_step": SHOTS * 8, "d2h_bytes_per_step": SHOTS * 8 + 8 * len(zz)},
@@ -341,6 +366,89 @@ def run_batch_bench(args):
                       "config": {"workload": "4096 ansatz circuits, n in 12..20, 8 layers RY.RZ + CZ chain, <ZZ>"}}))
 
 
+def run_block_bench(args):
+    """Opt-in secondary measurement: one dense 5-qubit block (Haar 32x32) on a 28-qubit
+    complex64 state, CUDA-core FMA (k_kq_native) vs tensor cores (TF32x3, k_block_tc)."""
+    import torch
+
+    import paper_2503_03016_gb300 as P
+    torch.cuda.set_device(0)
+    n = args.qubits
+    st = P.State(n, "c64").init_gaussian(7)
+    U = W.haar_unitaries(1, 32, 11)[0]
+    qs = [3, 9, 14, 20, n - 2]
+    stream = torch.cuda.current_stream()
+    res = {}
+    for name, prec in (("native", P.QC_PREC_NATIVE), ("tf32x3", P.QC_PREC_TF32X3)):
+        for _ in range(max(args.warmup, 1)):
+            P.qc_apply_fused_k(st.handle, qs, U, prec)
+        torch.cuda.synchronize()
+        t = StreamTimer(stream)
+        t.start()
+        for _ in range(args.steps):
+            P.qc_apply_fused_k(st.handle, qs, U, prec)
+        ms = t.stop() / args.steps
+        flops = 8.0 * 32 * (1 << n) * (3 if prec == P.QC_PREC_TF32X3 else 1)
+        res[name] = {"ms": ms, "gbs": 2 * 8 * (1 << n) / (ms * 1e-3) / 1e9, "tflops": flops / (ms * 1e-3) / 1e12}
+    print(json.dumps({"metric": "fused 5-qubit block on %d qubits" % n, "results": res}))
+
+
+def run_qft_bench(args):
+    """Opt-in secondary measurement: the 32-qubit QFT (544 gates) on the seeded Gaussian
+    state, per-gate vs fused tile passes, complex64 (32 GiB) and complex128 (64 GiB)."""
+    import torch
+
+    import paper_2503_03016_gb300 as P
+    torch.cuda.set_device(0)
+    n = args.qubits
+    ops = W.qft(n)
+    circ = P.Circuit(n, ops)
+    stream = torch.cuda.current_stream()
+    res = {}
+    for dt in ("c64", "c128"):
+        st = P.State(n, dt).init_gaussian(3)
+        sbytes = (1 << n) * (8 if dt == "c64" else 16)
+        for mode_name, mode in (("fused", P.QC_RUN_FUSED), ("per_gate", P.QC_RUN_PER_GATE)):
+            if dt == "c128" and mode_name == "per_gate" and args.steps > 1:
+                reps = 1
+            else:
+                reps = args.steps
+            P.qc_run_circuit(st.handle, circ, None, mode, P.QC_PREC_NATIVE)  # warm-up
+            torch.cuda.synchronize()
+            t = StreamTimer(stream)
+            t.start()
+            for _ in range(reps):
+                P.qc_run_circuit(st.handle, circ, None, mode, P.QC_PREC_NATIVE)
+            ms = t.stop() / reps
+            passes = P.qc_last_pass_count() if mode == P.QC_RUN_FUSED else None
+            res["%s_%s" % (dt, mode_name)] = {"ms": ms, "passes": passes,
+                                              "pass_gbs": (2 * sbytes * passes / (ms * 1e-3) / 1e9) if passes else None}
+        st.free()
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "QFT on %d qubits (544 gates at 32)" % n, "results": res}))
+
+
+def run_adjoint_bench(args):
+    """Opt-in secondary measurement: energy + full gradient of the 24-qubit, 10-layer
+    ansatz (480 parameters, H = ring ZZ + sum X) by the adjoint sweep."""
+    import paper_2503_03016_gb300 as P
+    import torch
+    torch.cuda.set_device(0)
+    n, layers = 24, 10
+    ops, params, terms, coeffs = W.adjoint_workload(n, layers, 5)
+    circ = P.Circuit(n, ops)
+    res = {}
+    for dt, code in (("c64", P.QC_C64), ("c128", P.QC_C128)):
+        P.qc_adjoint_grad(circ, params, terms, coeffs, code)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e, g = P.qc_adjoint_grad(circ, params, terms, coeffs, code)
+        ms = (time.perf_counter() - t0) * 1e3 / args.steps
+        res[dt] = {"ms_energy_and_gradient": ms, "energy": e, "grad_norm": float(np.linalg.norm(g))}
+    print(json.dumps({"metric": "adjoint gradient, 24 qubits, 720 gates, 480 parameters", "results": res}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -353,13 +461,19 @@ def main():
     ap.add_argument("--cpu-gates", type=int, default=24)
     ap.add_argument("--ref-gates", type=int, default=8)
     ap.add_argument("--qubits", type=int, default=28, help="smaller cases for profiling only")
-    ap.add_argument("--workload", default="brickwork", choices=["brickwork", "batch"],
+    ap.add_argument("--workload", default="brickwork", choices=["brickwork", "batch", "block", "qft", "adjoint"],
                     help="batch: opt-in secondary measurement of the batched launch")
     args = ap.parse_args()
     global N_QUBITS
     N_QUBITS = args.qubits
     if args.workload == "batch" and args.impl == "ours":
         run_batch_bench(args)
+    elif args.workload == "block" and args.impl == "ours":
+        run_block_bench(args)
+    elif args.workload == "qft" and args.impl == "ours":
+        run_qft_bench(args)
+    elif args.workload == "adjoint" and args.impl == "ours":
+        run_adjoint_bench(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -179,6 +179,20 @@ qc_status qc_sample(const qc_state* s, const double* dev_u, int64_t shots, uint6
 qc_status qc_sample_probs(qc_state* s, const double* dev_p, int n, const double* dev_u, int64_t shots,
                           uint64_t* dev_out);
 
+/* QCLAB's reducedStatevector (Sec. 5.1): the 2^(n-m) amplitudes whose `known` qubits
+ * (m distinct qubits) carry `bits` (0/1 each), in the order of the remaining qubits
+ * (the last remaining qubit is the least significant).  dev_out: device memory of the
+ * state's dtype, 16-byte aligned.  A gather, not renormalised.  0 <= m < n. */
+qc_status qc_reduced_state(const qc_state* s, const int* known, const int* bits, int m, void* dev_out);
+
+/* Marginal outcome distribution of measuring `qubits` (1 <= m <= 12, distinct):
+ * dev_out[x] = sum of p_i over indices whose measured qubits read x, with qubits[0] the
+ * most significant bit of x (Sec. 3.3's P(o) generalised to m qubits; with
+ * qc_sample_probs it gives counts(shots) of Sec. 5.2 for partial measurements).
+ * FP64; block partial histograms use FP64 shared-memory atomics, so the last bits
+ * may vary between runs. */
+qc_status qc_marginal_probs(const qc_state* s, const int* qubits, int m, double* dev_out);
+
 /* host_out[t] = coeffs[t] * <psi| P_t |psi> for Pauli strings P_t of n characters
  * in {I,X,Y,Z}, character j acting on qubit j (coeffs NULL = all 1).  Reductions in
  * FP64.  Synchronising.  (Sec. 5.2 builds a density-matrix estimate from such

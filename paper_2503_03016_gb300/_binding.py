@@ -80,6 +80,8 @@ _SIGS = {
     "qc_sample": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
     "qc_sample_probs": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int64, _P]),
     "qc_expect_pauli": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_char_p), _D, ctypes.c_int, _D]),
+    "qc_reduced_state": (ctypes.c_int, [_P, _I, _I, ctypes.c_int, _P]),
+    "qc_marginal_probs": (ctypes.c_int, [_P, _I, ctypes.c_int, _P]),
     "qc_expect_pauli_noalloc": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_char_p), _D, ctypes.c_int, _D]),
     "qc_run_circuit": (ctypes.c_int, [_P, ctypes.POINTER(qc_circuit), _D, ctypes.c_int, ctypes.c_int]),
     "qc_adjoint_grad": (ctypes.c_int, [ctypes.POINTER(qc_circuit), _D, ctypes.c_int,
@@ -266,6 +268,18 @@ def qc_sample(h: int, u, shots: int, out) -> None:
 
 def qc_sample_probs(h: int, p, n: int, u, shots: int, out) -> None:
     _call("qc_sample_probs", h, _ptr(p), n, _ptr(u), int(shots), _ptr(out))
+
+
+def qc_reduced_state(h: int, known: Sequence[int], bits: Sequence[int], out) -> None:
+    m = len(known)
+    k = (ctypes.c_int * max(1, m))(*known)
+    v = (ctypes.c_int * max(1, m))(*[int(x) for x in bits])
+    _call("qc_reduced_state", h, k, v, m, _ptr(out))
+
+
+def qc_marginal_probs(h: int, qubits: Sequence[int], out) -> None:
+    q = (ctypes.c_int * len(qubits))(*qubits)
+    _call("qc_marginal_probs", h, q, len(qubits), _ptr(out))
 
 
 def _strings(strings: Sequence[str]):
