@@ -132,13 +132,17 @@ __global__ void __launch_bounds__(kTcRows, 1) k_block_tc(float* __restrict__ amp
   uint32_t phase = 0;
   bool failed = false;
 
-  for (uint64_t t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
-    // gather this thread's row, split into hi / lo
-    const uint64_t row = t * kTcRows + tid;
-    const uint64_t rb = insert_zero_bits(row, spos, kTcK);
-    float2 x[32];
+  // software pipeline: the rows of tile t+grid are gathered into registers while the
+  // tensor cores work on tile t
+  float2 x[32];
+  uint64_t rb = 0;
+  if (uint64_t(blockIdx.x) < ntiles) {
+    rb = insert_zero_bits(uint64_t(blockIdx.x) * kTcRows + tid, spos, kTcK);
 #pragma unroll
     for (int c = 0; c < 32; ++c) x[c] = reinterpret_cast<const float2*>(amps)[rb | offs[c]];
+  }
+  for (uint64_t t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
+    // split this thread's row (already in registers) into hi / lo
 #pragma unroll
     for (int c = 0; c < 32; ++c) {
       const float re_hi = __uint_as_float(__float_as_uint(x[c].x) & 0xFFFFE000u);
@@ -170,6 +174,16 @@ __global__ void __launch_bounds__(kTcRows, 1) k_block_tc(float* __restrict__ amp
                        smem_u32(bar))
                    : "memory");
     }
+    // gather the next tile's rows while the products run (disjoint rows, own tiles)
+    const uint64_t rb_cur = rb;
+    {
+      const uint64_t tn = t + gridDim.x;
+      if (tn < ntiles) {
+        rb = insert_zero_bits(tn * kTcRows + tid, spos, kTcK);
+#pragma unroll
+        for (int c = 0; c < 32; ++c) x[c] = reinterpret_cast<const float2*>(amps)[rb | offs[c]];
+      }
+    }
     // bounded wait for the products
     {
       uint32_t done = 0;
@@ -200,7 +214,7 @@ __global__ void __launch_bounds__(kTcRows, 1) k_block_tc(float* __restrict__ amp
       }
 #pragma unroll
       for (int d = 0; d < 32; ++d)
-        reinterpret_cast<float2*>(amps)[rb | offs[d]] = make_float2(out[2 * d], out[2 * d + 1]);
+        reinterpret_cast<float2*>(amps)[rb_cur | offs[d]] = make_float2(out[2 * d], out[2 * d + 1]);
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
