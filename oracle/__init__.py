@@ -249,16 +249,20 @@ ZERO_PROB = 1e-12  # a branch whose probability is at most this is dropped
 
 def simulate(n: int, ops, init, params=None, zero_prob: float = ZERO_PROB):
     """QCLAB's ``simulate``: runs ``ops`` (gates and 'measure' / 'measure_x' /
-    'measure_y' ops) from ``init`` (bitstring or vector).  Every measurement with two
-    possible outcomes splits the run into branches, outcome 0 first.  Returns
+    'measure_y' / 'reset' ops) from ``init`` (bitstring or vector).  Every measurement
+    with two possible outcomes splits the run into branches, outcome 0 first.  Returns
     (results, probabilities, states) with results the measured bits in measurement
-    order."""
+    order.
+
+    Reset (mentioned in Sec. 3.3, not defined there) is read as a Z measurement whose
+    outcome-1 branch is then flipped by X, so the qubit ends in |0> on every branch;
+    its outcome is part of the branch label like any measurement's."""
     psi = basis_state(n, init) if isinstance(init, (str, int)) else np.array(init, dtype=np.complex128)
     branches = [("", 1.0, psi)]
     for op in ops:
-        if op.kind.startswith("measure"):
+        if op.kind.startswith("measure") or op.kind == "reset":
             q = op.qubits[0]
-            basis = op.kind[len("measure"):].lstrip("_") or "z"
+            basis = "z" if op.kind == "reset" else op.kind[len("measure"):].lstrip("_") or "z"
             new = []
             for res, pr, st in branches:
                 pre, post = _basis_change(basis)
@@ -272,6 +276,8 @@ def simulate(n: int, ops, init, params=None, zero_prob: float = ZERO_PROB):
                     collapse(s2, q, o, P)
                     for U in post:
                         apply_1q(s2, q, U)
+                    if op.kind == "reset" and o == 1:
+                        apply_1q(s2, q, gates.X)
                     new.append((res + str(o), pr * P, s2))
             branches = new
         else:

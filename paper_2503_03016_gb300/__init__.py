@@ -9,3 +9,4 @@ from ._binding import lib, QCError, Circuit  # noqa: F401
 from .state import State  # noqa: F401
 from .autograd import AdjointExpectation  # noqa: F401,E402
 from .simulate import simulate, reduced_statevector, counts  # noqa: F401,E402
+from .qasm import to_qasm, from_qasm, GateOp  # noqa: F401,E402

@@ -4,8 +4,10 @@ measurements with outcome branching.
 Host control flow only: every amplitude operation is a C-ABI call (qc_run_circuit,
 qc_state_copy, qc_collapse).  A measurement in the X or Y basis applies the basis
 change before and its inverse after the Z measurement (Sec. 3.3): X = H .. H, Y =
-S^dagger H .. H S.  A branch whose outcome probability is at most the zero threshold of
-qc_collapse is dropped (1e-12 complex128, 1e-6 complex64)."""
+S^dagger H .. H S.  A reset (mentioned in Sec. 3.3, not defined there) is a Z
+measurement whose outcome-1 branch is then flipped by X; its outcome labels the branch
+like a measurement's.  A branch whose outcome probability is at most the zero threshold
+of qc_collapse is dropped (1e-12 complex128, 1e-6 complex64)."""
 from __future__ import annotations
 
 from typing import List, Sequence, Tuple
@@ -61,12 +63,13 @@ def simulate(n: int, ops: Sequence, init, dtype: str = "c128", params=None,
             pending.clear()
 
     for op in ops:
-        if not op.kind.startswith("measure"):
+        reset = op.kind == "reset"
+        if not (op.kind.startswith("measure") or reset):
             pending.append(op)
             continue
         flush()
         q = op.qubits[0]
-        basis = op.kind[len("measure"):].lstrip("_") or "z"
+        basis = "z" if reset else op.kind[len("measure"):].lstrip("_") or "z"
         pre = [_Op(k, q) for k in _BASIS_PRE[basis]]
         post = [_Op(k, q) for k in _BASIS_POST[basis]]
         new = []
@@ -82,8 +85,9 @@ def simulate(n: int, ops: Sequence, init, dtype: str = "c128", params=None,
                         s2.free()
                         continue
                     raise
-                if post:
-                    B.qc_run_circuit(s2.handle, B.Circuit(n, post), None, B.QC_RUN_PER_GATE, B.QC_PREC_NATIVE)
+                after = post + ([_Op("x", q)] if reset and o == 1 else [])
+                if after:
+                    B.qc_run_circuit(s2.handle, B.Circuit(n, after), None, B.QC_RUN_PER_GATE, B.QC_PREC_NATIVE)
                 new.append((res + str(o), pr * p, s2))
             st.free()
         branches = new

@@ -52,6 +52,43 @@ def test_simulate_x_and_y_basis():
 
 
 @pytest.mark.parametrize("dtype", ["c128", "c64"])
+def test_simulate_mid_circuit_reset(dtype):
+    """Reset (Z measurement, then X on the 1-branch) in the middle of a circuit, with
+    gates after it, against the oracle branch by branch."""
+    import paper_2503_03016_gb300 as P
+    from workloads import Op
+    n = 4
+    v = W.random_state(n, seed=21)
+    ops = [Op("h", (0,)), Op("cnot", (0, 2)), Op("reset", (2,)), Op("ry", (2,), (0.7,)),
+           Op("cz", (2, 3)), Op("reset", (0,)), Op("measure_x", (3,))]
+    res, pr, st = P.simulate(n, ops, v, dtype=dtype)
+    wres, wpr, wst = oracle.simulate(n, ops, v)
+    assert res == wres
+    np.testing.assert_allclose(pr, wpr, rtol=TOL[dtype])
+    for a, b in zip(st, wst):
+        assert rel_l2(a.numpy(), b) <= TOL[dtype]
+
+
+@pytest.mark.parametrize("name", ["teleport.txt", "qec.txt"])
+def test_qasm_front_end_paper_examples(name):
+    """The teleportation and error-correction circuits written out as OpenQASM
+    (Sec. 4), read back and simulated on the GPU, against the oracle on the original
+    ops (open controls become X around ccx in the text)."""
+    import paper_2503_03016_gb300 as P
+    g = G.load(name)
+    n = int(g["n"])
+    ops = G.ops(g["ops"])
+    n2, back = P.from_qasm(P.to_qasm(n, ops, header=True))
+    assert n2 == n
+    res, pr, st = P.simulate(n, back, G.init_state(g["init"], n), dtype="c128")
+    wres, wpr, wst = oracle.simulate(n, ops, G.init_state(g["init"], n))
+    assert res == wres == g["results"].split()
+    np.testing.assert_allclose(pr, wpr, atol=1e-14)
+    for a, b in zip(st, wst):
+        assert rel_l2(a.numpy(), b) <= TOL["c128"]
+
+
+@pytest.mark.parametrize("dtype", ["c128", "c64"])
 def test_reduced_state_gather(dtype):
     import torch
 

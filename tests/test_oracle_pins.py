@@ -82,6 +82,24 @@ def test_tomography_exact_values():
     np.testing.assert_allclose(rho.ravel(), G.cvec(g["rho"]), atol=1e-15)
 
 
+def test_reset_closed_forms():
+    """Reset (Sec. 3.3; read as a Z measurement whose 1-branch is flipped by X):
+    |1> -> |0> with certainty; on a Bell pair each branch keeps q1's value with q0 = 0;
+    the branch keeps the collapsed state's phase."""
+    res, pr, st = oracle.simulate(1, [Op("reset", (0,))], "1")
+    assert res == ["1"] and pr == [1.0]
+    np.testing.assert_array_equal(st[0], [1, 0])
+    res, pr, st = oracle.simulate(2, [Op("h", (0,)), Op("cnot", (0, 1)), Op("reset", (0,))], "00")
+    assert res == ["0", "1"]
+    np.testing.assert_allclose(pr, [0.5, 0.5], atol=1e-15)
+    np.testing.assert_allclose(st[0], [1, 0, 0, 0], atol=1e-15)
+    np.testing.assert_allclose(st[1], [0, 1, 0, 0], atol=1e-15)
+    v = np.kron(np.array([1, 1j]) / np.sqrt(2), np.array([0, 1]))  # (|0> + i|1>)/sqrt2 on q0, |1> on q1
+    res, pr, st = oracle.simulate(2, [Op("reset", (0,))], v)
+    np.testing.assert_allclose(st[0], [0, 1, 0, 0], atol=1e-15)
+    np.testing.assert_allclose(st[1], [0, 1j, 0, 0], atol=1e-15)
+
+
 # ---------------------------------------------------------------------------
 # gate matrices against library routines and identities
 # ---------------------------------------------------------------------------
