@@ -119,25 +119,85 @@ __device__ __forceinline__ void load_mat(R (&um)[NV], const R* __restrict__ u) {
   }
 }
 
+// Complex64 gates on packed pairs.  For complex64 the planner stores each matrix entry
+// u = (ur, ui) as the two pairs (ur, ur) and (-ui, ui), so that u x is
+// (ur, ur) * (xr, xi) + (-ui, ui) * (xi, xr): two paired FMAs (one instruction each on
+// sm_100 and later) in place of four scalar ones.
+__device__ __forceinline__ float2 f2(Cplx<float> z) { return make_float2(z.re, z.im); }
+__device__ __forceinline__ float2 f2swap(Cplx<float> z) { return make_float2(z.im, z.re); }
+__device__ __forceinline__ Cplx<float> c2(float2 z) { return Cplx<float>{z.x, z.y}; }
+
+template <int NE>
+__device__ __forceinline__ void load_packed(float2 (&a)[NE], float2 (&b)[NE], const float* __restrict__ u) {
+  const float4* q = reinterpret_cast<const float4*>(u);
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    const float4 t = q[e];
+    a[e] = make_float2(t.x, t.y);
+    b[e] = make_float2(t.z, t.w);
+  }
+}
+
 template <typename R, int SB, int S0>
 __device__ __forceinline__ void dense1(Cplx<R> (&v)[1 << SB], const R* __restrict__ u, uint32_t r0,
                                        const uint32_t (&sm)[SB], uint32_t lmask, uint32_t lval) {
-  R um[8];
-  load_mat<R, 8>(um, u);
-  const Cplx<R> u00{um[0], um[1]}, u01{um[2], um[3]}, u10{um[4], um[5]}, u11{um[6], um[7]};
+  if constexpr (sizeof(R) == 4) {
+    float2 a[4], b[4];
+    load_packed<4>(a, b, u);
 #pragma unroll
-  for (int j = 0; j < (1 << SB); ++j) {
-    if (j & (1 << S0)) continue;
-    const int j1 = j | (1 << S0);
-    if (((r0 | slot_off<SB>(j, sm)) & lmask) != lval) continue;
-    const Cplx<R> x = v[j], y = v[j1];
-    v[j] = cmul2(u00, x, u01, y);
-    v[j1] = cmul2(u10, x, u11, y);
+    for (int j = 0; j < (1 << SB); ++j) {
+      if (j & (1 << S0)) continue;
+      const int j1 = j | (1 << S0);
+      if (((r0 | slot_off<SB>(j, sm)) & lmask) != lval) continue;
+      const float2 x = f2(v[j]), xs = f2swap(v[j]), y = f2(v[j1]), ys = f2swap(v[j1]);
+      v[j] = c2(__ffma2_rn(b[1], ys, __ffma2_rn(a[1], y, __ffma2_rn(b[0], xs, __fmul2_rn(a[0], x)))));
+      v[j1] = c2(__ffma2_rn(b[3], ys, __ffma2_rn(a[3], y, __ffma2_rn(b[2], xs, __fmul2_rn(a[2], x)))));
+    }
+  } else {
+    R um[8];
+    load_mat<R, 8>(um, u);
+    const Cplx<R> u00{um[0], um[1]}, u01{um[2], um[3]}, u10{um[4], um[5]}, u11{um[6], um[7]};
+#pragma unroll
+    for (int j = 0; j < (1 << SB); ++j) {
+      if (j & (1 << S0)) continue;
+      const int j1 = j | (1 << S0);
+      if (((r0 | slot_off<SB>(j, sm)) & lmask) != lval) continue;
+      const Cplx<R> x = v[j], y = v[j1];
+      v[j] = cmul2(u00, x, u01, y);
+      v[j1] = cmul2(u10, x, u11, y);
+    }
   }
 }
 
 template <typename R, int SB, int S0, int S1>
 __device__ __forceinline__ void dense2(Cplx<R> (&v)[1 << SB], const R* __restrict__ us) {
+  if constexpr (sizeof(R) == 4) {
+    float2 a[16], b[16];
+    load_packed<16>(a, b, us);
+#pragma unroll
+    for (int j = 0; j < (1 << SB); ++j) {
+      if (j & ((1 << S0) | (1 << S1))) continue;
+      const int i[4] = {j, j | (1 << S1), j | (1 << S0), j | (1 << S0) | (1 << S1)};
+      float2 x[4], xs[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        x[c] = f2(v[i[c]]);
+        xs[c] = f2swap(v[i[c]]);
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        float2 o = __fmul2_rn(a[4 * r], x[0]);
+        o = __ffma2_rn(b[4 * r], xs[0], o);
+#pragma unroll
+        for (int c = 1; c < 4; ++c) {
+          o = __ffma2_rn(a[4 * r + c], x[c], o);
+          o = __ffma2_rn(b[4 * r + c], xs[c], o);
+        }
+        v[i[r]] = c2(o);
+      }
+    }
+    return;
+  }
   R u[32];
   load_mat<R, 32>(u, us);
 #pragma unroll
@@ -637,6 +697,15 @@ static void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int 
         op.s0 = slot(p.tb[0]);
         op.s1 = p.nt == 2 ? slot(p.tb[1]) : 0;
         op.mat = int64_t(hp.mats.size()) - P.mat0;
+        // entry (re, im); complex64 stores it as the pairs (re, re), (-im, im)
+        auto entry = [&](double re, double im) {
+          hp.mats.push_back(R(re));
+          if (sizeof(R) == 4) {
+            hp.mats.push_back(R(re));
+            hp.mats.push_back(R(-im));
+          }
+          hp.mats.push_back(R(im));
+        };
         if (p.nt == 2 && op.s0 > op.s1) {
           // the same gate with its qubits listed in the other order: row/column index
           // 2a+b -> 2b+a
@@ -644,11 +713,10 @@ static void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int 
           for (int r = 0; r < 4; ++r)
             for (int c = 0; c < 4; ++c) {
               const int rr = ((r & 1) << 1) | (r >> 1), cc = ((c & 1) << 1) | (c >> 1);
-              hp.mats.push_back(R(p.m[2 * (4 * rr + cc)]));
-              hp.mats.push_back(R(p.m[2 * (4 * rr + cc) + 1]));
+              entry(p.m[2 * (4 * rr + cc)], p.m[2 * (4 * rr + cc) + 1]);
             }
         } else {
-          for (int e = 0; e < (p.nt == 1 ? 8 : 32); ++e) hp.mats.push_back(R(p.m[e]));
+          for (int e = 0; e < (p.nt == 1 ? 4 : 16); ++e) entry(p.m[2 * e], p.m[2 * e + 1]);
         }
       } else {
         // merge following phase ops with the same condition (they commute)
