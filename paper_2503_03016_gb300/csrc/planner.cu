@@ -51,11 +51,10 @@ static_assert(sizeof(TileOp) == 64, "TileOp must be 64 bytes");
 
 struct TileStage {
   int32_t op0, nops;
-  int8_t slot_bit[8];  // local bit of each slot (SB used)
-  int8_t lane_bit[8];  // local bit receiving bit k of the thread index (the m-SB non-slot
-                       // bits; the first ones cover distinct bit positions mod 4 so that a
-                       // half warp's shared-memory accesses fall in distinct banks)
-  int32_t pad[2];      // 32-byte record
+  int8_t slot_bit[8];   // local bit of each slot (SB used)
+  int8_t lane_bit[16];  // local bit receiving bit k of the thread index (the m-SB non-slot
+                        // bits; the first ones cover distinct bit positions mod 4 so that
+                        // a half warp's shared-memory accesses fall in distinct banks)
 };
 static_assert(sizeof(TileStage) == 32, "TileStage must be 32 bytes");
 
@@ -328,7 +327,7 @@ __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const
       const TileStage& st = sst[s];
       uint32_t r0 = 0;
 #pragma unroll
-      for (int k = 0; k < 8; ++k)
+      for (int k = 0; k < 16; ++k)
         if (k < m - SB) r0 |= ((threadIdx.x >> k) & 1u) << st.lane_bit[k];
       uint32_t sm[SB], sw[SB];
 #pragma unroll
@@ -666,7 +665,7 @@ static void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int 
           }
       for (int b : rest_bits)
         if (std::find(order.begin(), order.end(), b) == order.end()) order.push_back(b);
-      for (size_t k = 0; k < order.size() && k < 8; ++k) st.lane_bit[k] = int8_t(order[k]);
+      for (size_t k = 0; k < order.size() && k < 16; ++k) st.lane_bit[k] = int8_t(order[k]);
     }
     st.op0 = int(hp.ops.size()) - P.op0;
     const size_t j = take.size();
@@ -785,11 +784,24 @@ static void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int 
 
 static int g_last_pass_count = 0;
 
+// Register stage width SB (a thread holds 2^SB amplitudes) and block size of the tile
+// pass per precision: blockDim = 2^(m - SB) <= NT with m = 13 (complex64) / 12.
+template <typename R>
+struct TileShape;
+template <>
+struct TileShape<float> {
+  static constexpr int SB = 5, NT = 256;
+};
+template <>
+struct TileShape<double> {
+  static constexpr int SB = 4, NT = 256;
+};
+
 template <typename R>
 static qc_status run_tiles(qc_state* s, const std::vector<ResolvedOp>& rops, int m) {
   const int n = s->n;
   const int L = sizeof(R) == 4 ? 4 : 3;
-  constexpr int SB = sizeof(R) == 4 ? 5 : 4;  // register tile: 32 (complex64) / 16 amplitudes
+  constexpr int SB = TileShape<R>::SB;
   std::vector<PlanOp> pops;
   to_plan_ops(rops, pops);
   std::vector<BuiltPass> bps = build_passes(pops, n, m, L);
@@ -822,7 +834,7 @@ static qc_status run_tiles(qc_state* s, const std::vector<ResolvedOp>& rops, int
   for (const TilePass& P : hp.passes)
     plan_max = std::max(plan_max, P.nstages * sizeof(TileStage) + P.nops * sizeof(TileOp) + P.nmat * sizeof(R));
   const size_t smem = 2 * sizeof(Cplx<R>) * (size_t(1) << m) + sizeof(uint64_t) * (size_t(1) << (m - L)) + plan_max;
-  constexpr int NT = 256;
+  constexpr int NT = TileShape<R>::NT;
   if (qc_status st = check_cuda(
           cudaFuncSetAttribute(k_tile_pass<R, NT, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
           "tile pass shared memory"))
@@ -858,7 +870,7 @@ qc_status run_fused(qc_state* s, const qc_circuit* c, const double* params, qc_p
 template <typename R>
 static void plan_stats(int n, const std::vector<ResolvedOp>& rops, int m, int* passes, int* stages, int* ops) {
   const int L = sizeof(R) == 4 ? 4 : 3;
-  constexpr int SB = sizeof(R) == 4 ? 5 : 4;
+  constexpr int SB = TileShape<R>::SB;
   std::vector<PlanOp> pops;
   to_plan_ops(rops, pops);
   std::vector<BuiltPass> bps = build_passes(pops, n, m, L);
