@@ -173,27 +173,31 @@ __device__ __forceinline__ void dense2(Cplx<R> (&v)[1 << SB], const R* __restric
   if constexpr (sizeof(R) == 4) {
     float2 a[16], b[16];
     load_packed<16>(a, b, us);
+    // the four output rows are independent chains: step them together so that each
+    // packed FMA's result is not needed by the next instruction
 #pragma unroll
     for (int j = 0; j < (1 << SB); ++j) {
       if (j & ((1 << S0) | (1 << S1))) continue;
       const int i[4] = {j, j | (1 << S1), j | (1 << S0), j | (1 << S0) | (1 << S1)};
-      float2 x[4], xs[4];
+      float2 x[4], xs[4], o[4];
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         x[c] = f2(v[i[c]]);
         xs[c] = f2swap(v[i[c]]);
       }
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        float2 o = __fmul2_rn(a[4 * r], x[0]);
-        o = __ffma2_rn(b[4 * r], xs[0], o);
+      for (int r = 0; r < 4; ++r) o[r] = __fmul2_rn(a[4 * r], x[0]);
 #pragma unroll
-        for (int c = 1; c < 4; ++c) {
-          o = __ffma2_rn(a[4 * r + c], x[c], o);
-          o = __ffma2_rn(b[4 * r + c], xs[c], o);
+      for (int c = 0; c < 4; ++c) {
+        if (c > 0) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) o[r] = __ffma2_rn(a[4 * r + c], x[c], o[r]);
         }
-        v[i[r]] = c2(o);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) o[r] = __ffma2_rn(b[4 * r + c], xs[c], o[r]);
       }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) v[i[r]] = c2(o[r]);
     }
     return;
   }
