@@ -33,6 +33,9 @@ import workloads as W  # noqa: E402
 
 METRIC = "circuit time & HBM GB/s (frac of peak) at 28–32 qubits: fused/FP32 vs plain FP64"
 N_QUBITS, DEPTH, SEED, SHOTS, SHOT_SEED = 28, 40, 2, 1_000_000, 102
+# FP32 peak from unit counts at the maximum SM clock
+ALU_PEAK_TF = 152 * 128 * 2 * 2070e6 / 1e12
+ALU_PEAK_SRC = "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"
 
 
 def peaks():
@@ -290,11 +293,11 @@ def run_ours(args):
         sm_mhz = (clk.get("sm_mhz") or 2070.0) if isinstance(clk, dict) else 2070.0
         peak = torch.cuda.get_device_properties(0).multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
         achieved = flops / (circ_ms * 1e-3) / 1e12
-        # ncu: 1013.25 MB per pass at 26 qubits (profiles/k_tile_pass_brickwork_n26.md),
-        # scaled by the 4x larger state
-        traffic = 1013.250304e6 * (1 << (N_QUBITS - 26))
+        # DRAM bytes of one tile pass in an ncu capture at 26 qubits (1013.28 MB), scaled
+        # by the larger state (a pass moves the state once each way)
+        traffic = 1013.276928e6 * (1 << (N_QUBITS - 26))
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "traffic_note": "per pass, ncu at 26 qubits scaled x4",
+                "traffic": traffic, "traffic_note": "per pass, ncu at 26 qubits scaled by 2^(n-26)",
                 "algorithmic_bytes_per_pass": 2 * sbytes, "hbm_gbs_over_passes": passes * 2 * sbytes / (circ_ms * 1e-3) / 1e9,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz" % sm_mhz,
                 "kernel": "k_tile_pass<float,256,5>", "passes": passes}
@@ -359,10 +362,14 @@ def run_batch_bench(args):
     for _ in range(args.steps):
         P.qc_run_batch(nsi, layers, offs, dparams, flat.size, out)
     ms = timer.stop() / args.steps
-    flops = sum(8.0 * layers * 2 * int(n) * (1 << int(n)) for n in ns)
+    # a fused RZ.RY layer gate costs 2 complex multiply-adds = 16 real flops per amplitude
+    flops = sum(16.0 * layers * int(n) * (1 << int(n)) for n in ns)
+    tf = flops / (ms * 1e-3) / 1e12
     print(json.dumps({"metric": "batched ansatz circuits/s", "value": len(ns) / (ms * 1e-3), "unit": "circuits/s",
                       "ms_per_step": ms, "steps": args.steps, "fusion_width": P.qc_batch_fusion_width(),
-                      "approx_fp32_tflops": flops / (ms * 1e-3) / 1e12,
+                      "approx_fp32_tflops": tf,
+                      "roofline": {"bound": "alu", "achieved": tf, "peak": ALU_PEAK_TF, "unit": "TFLOP/s",
+                                   "frac": tf / ALU_PEAK_TF, "peak_source": ALU_PEAK_SRC},
                       "config": {"workload": "4096 ansatz circuits, n in 12..20, 8 layers RY.RZ + CZ chain, <ZZ>"}}))
 
 
@@ -373,7 +380,9 @@ def run_block_bench(args):
 
     import paper_2503_03016_gb300 as P
     torch.cuda.set_device(0)
-    n = args.qubits
+    n = args.qubits or 28
+    hbm, bf16, _ = peaks()
+    tf32_peak = bf16 * 1.1 / 2.25
     st = P.State(n, "c64").init_gaussian(7)
     U = W.haar_unitaries(1, 32, 11)[0]
     qs = [3, 9, 14, 20, n - 2]
@@ -389,8 +398,16 @@ def run_block_bench(args):
             P.qc_apply_fused_k(st.handle, qs, U, prec)
         ms = t.stop() / args.steps
         flops = 8.0 * 32 * (1 << n) * (3 if prec == P.QC_PREC_TF32X3 else 1)
-        res[name] = {"ms": ms, "gbs": 2 * 8 * (1 << n) / (ms * 1e-3) / 1e9, "tflops": flops / (ms * 1e-3) / 1e12}
-    print(json.dumps({"metric": "fused 5-qubit block on %d qubits" % n, "results": res}))
+        gbs = 2 * 8 * (1 << n) / (ms * 1e-3) / 1e9
+        tf = flops / (ms * 1e-3) / 1e12
+        res[name] = {"ms": ms, "gbs": gbs, "frac_hbm": gbs / hbm, "tflops": tf}
+        if prec == P.QC_PREC_TF32X3:
+            res[name]["frac_tf32"] = tf / tf32_peak
+        else:
+            res[name]["frac_alu"] = tf / ALU_PEAK_TF
+    print(json.dumps({"metric": "fused 5-qubit block on %d qubits" % n, "results": res,
+                      "peaks": {"hbm_gbs": hbm, "tf32_tflops": tf32_peak, "alu_tflops": ALU_PEAK_TF,
+                                "tf32_source": "measured bf16 x 1.1/2.25 (nominal TF32/BF16 dense ratio)"}}))
 
 
 def run_qft_bench(args):
@@ -400,8 +417,12 @@ def run_qft_bench(args):
 
     import paper_2503_03016_gb300 as P
     torch.cuda.set_device(0)
-    n = args.qubits
+    n = args.qubits or 32
+    hbm, _, _ = peaks()
     ops = W.qft(n)
+    # per-gate sweeps: H moves the whole state, a controlled phase the quarter with both
+    # bits set, a swap the half where the bits differ
+    per_gate_sweeps = n + (n * (n - 1) / 2) / 4 + (n // 2) / 2
     circ = P.Circuit(n, ops)
     stream = torch.cuda.current_stream()
     res = {}
@@ -421,11 +442,14 @@ def run_qft_bench(args):
                 P.qc_run_circuit(st.handle, circ, None, mode, P.QC_PREC_NATIVE)
             ms = t.stop() / reps
             passes = P.qc_last_pass_count() if mode == P.QC_RUN_FUSED else None
-            res["%s_%s" % (dt, mode_name)] = {"ms": ms, "passes": passes,
-                                              "pass_gbs": (2 * sbytes * passes / (ms * 1e-3) / 1e9) if passes else None}
+            alg = 2 * sbytes * (passes if passes else per_gate_sweeps)
+            gbs = alg / (ms * 1e-3) / 1e9
+            res["%s_%s" % (dt, mode_name)] = {"ms": ms, "passes": passes, "algorithmic_gb": alg / 1e9,
+                                              "gbs": gbs, "frac_hbm": gbs / hbm}
         st.free()
         torch.cuda.empty_cache()
-    print(json.dumps({"metric": "QFT on %d qubits (544 gates at 32)" % n, "results": res}))
+    print(json.dumps({"metric": "QFT on %d qubits (%d gates)" % (n, len(ops)), "results": res,
+                      "peaks": {"hbm_gbs": hbm}}))
 
 
 def run_adjoint_bench(args):
@@ -437,16 +461,89 @@ def run_adjoint_bench(args):
     n, layers = 24, 10
     ops, params, terms, coeffs = W.adjoint_workload(n, layers, 5)
     circ = P.Circuit(n, ops)
+    hbm, _, _ = peaks()
+    # the reverse sweep dominates: per rotation one pass reading and writing both states
+    # (4 S), per CZ the quarter of both states with both bits set (2 x 2 S / 4)
+    nrot = sum(1 for o in ops if o.kind in ("rx", "ry", "rz"))
+    ncz = sum(1 for o in ops if o.kind == "cz")
     res = {}
     for dt, code in (("c64", P.QC_C64), ("c128", P.QC_C128)):
+        sbytes = (1 << n) * (8 if dt == "c64" else 16)
         P.qc_adjoint_grad(circ, params, terms, coeffs, code)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             e, g = P.qc_adjoint_grad(circ, params, terms, coeffs, code)
         ms = (time.perf_counter() - t0) * 1e3 / args.steps
-        res[dt] = {"ms_energy_and_gradient": ms, "energy": e, "grad_norm": float(np.linalg.norm(g))}
-    print(json.dumps({"metric": "adjoint gradient, 24 qubits, 720 gates, 480 parameters", "results": res}))
+        alg = sbytes * (4 * nrot + ncz)
+        gbs = alg / (ms * 1e-3) / 1e9
+        res[dt] = {"ms_energy_and_gradient": ms, "energy": e, "grad_norm": float(np.linalg.norm(g)),
+                   "reverse_sweep_algorithmic_gb": alg / 1e9, "gbs": gbs, "frac_hbm": gbs / hbm}
+    print(json.dumps({"metric": "adjoint gradient, %d qubits, %d gates, %d parameters" % (n, len(ops), len(params)),
+                      "results": res, "peaks": {"hbm_gbs": hbm},
+                      "note": "wall clock per synchronising call; bytes count the reverse sweep only"}))
+
+
+def run_sweeps_bench(args):
+    """Opt-in secondary measurement: each single-kernel step of the path on its own
+    (28 qubits, complex64 and complex128, seeded Gaussian state) against the measured
+    HBM bandwidth.  Algorithmic bytes: what the step must read and write at least."""
+    import torch
+
+    import paper_2503_03016_gb300 as P
+    torch.cuda.set_device(0)
+    n = args.qubits or 28
+    hbm, _, _ = peaks()
+    stream = torch.cuda.current_stream()
+    U1 = W.haar_unitaries(1, 2, 21)[0]
+    U2 = W.haar_unitaries(1, 4, 22)[0]
+    X = np.array([[0, 1], [1, 0]], dtype=complex)
+    Z = np.diag([1.0, -1.0]).astype(complex)
+    shots = 1_000_000
+    u = torch.tensor(W.uniforms(shots, 102), device="cuda")
+    idx = torch.empty(shots, dtype=torch.int64, device="cuda")  # 8-byte outcome indices
+    zz = W.zz_terms(n, ring=False)
+    N = 1 << n
+    res = {}
+    for dt in ("c64", "c128"):
+        st = P.State(n, dt).init_gaussian(3)
+        S = N * (8 if dt == "c64" else 16)
+        probs = torch.empty(N, dtype=torch.float64, device="cuda")
+        h = st.handle
+        cases = [
+            ("init_basis", lambda: P.qc_state_init_basis(h, 0), S),
+            ("init_gaussian", lambda: P.qc_state_init_gaussian(h, 3), S),
+            ("1q_dense_q5", lambda: P.qc_apply_1q(h, 5, U1), 2 * S),
+            ("1q_dense_q0", lambda: P.qc_apply_1q(h, 0, U1), 2 * S),
+            ("1q_dense_bit0", lambda: P.qc_apply_1q(h, n - 1, U1), 2 * S),
+            ("2q_dense", lambda: P.qc_apply_2q(h, 3, 17, U2), 2 * S),
+            ("2q_dense_bit0", lambda: P.qc_apply_2q(h, 9, n - 1, U2), 2 * S),
+            ("cnot", lambda: P.qc_apply_ctrl(h, [2], None, 9, X), S),  # the half with the control set
+            ("cz", lambda: P.qc_apply_ctrl(h, [2], None, 9, Z), S / 2),  # the quarter with both bits set
+            ("outcome_prob", lambda: P.qc_outcome_prob(h, 7, 0), S),
+            ("probs", lambda: P.qc_probs(h, probs), S + 8 * N),
+            ("sample_1e6", lambda: P.qc_sample(h, u, shots, idx), S),
+            ("expect_zz_chain", lambda: P.qc_expect_pauli(h, zz), S),
+            # P(outcome) (read S), then keep half (read S/2) and write the whole state
+            ("collapse", lambda: P.qc_collapse(h, 7, 0), 2.5 * S),
+        ]
+        out = {}
+        for name, fn, alg in cases:
+            fn()
+            torch.cuda.synchronize()
+            t = StreamTimer(stream)
+            t.start()
+            for _ in range(args.steps):
+                fn()
+            ms = t.stop() / args.steps
+            gbs = alg / (ms * 1e-3) / 1e9
+            out[name] = {"ms": ms, "algorithmic_gb": alg / 1e9, "gbs": gbs, "frac_hbm": gbs / hbm}
+        res[dt] = out
+        st.free()
+        del probs
+        torch.cuda.empty_cache()
+    print(json.dumps({"metric": "single-kernel steps on %d qubits" % n, "results": res, "peaks": {"hbm_gbs": hbm},
+                      "l2": "state (2 GiB / 4 GiB) larger than L2"}))
 
 
 def main():
@@ -460,12 +557,14 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--cpu-gates", type=int, default=24)
     ap.add_argument("--ref-gates", type=int, default=8)
-    ap.add_argument("--qubits", type=int, default=28, help="smaller cases for profiling only")
-    ap.add_argument("--workload", default="brickwork", choices=["brickwork", "batch", "block", "qft", "adjoint"],
+    ap.add_argument("--qubits", type=int, default=None,
+                    help="register size (default: 28 brickwork and block, 32 QFT); smaller for profiling")
+    ap.add_argument("--workload", default="brickwork",
+                    choices=["brickwork", "batch", "block", "qft", "adjoint", "sweeps"],
                     help="batch: opt-in secondary measurement of the batched launch")
     args = ap.parse_args()
     global N_QUBITS
-    N_QUBITS = args.qubits
+    N_QUBITS = args.qubits or 28
     if args.workload == "batch" and args.impl == "ours":
         run_batch_bench(args)
     elif args.workload == "block" and args.impl == "ours":
@@ -474,6 +573,8 @@ def main():
         run_qft_bench(args)
     elif args.workload == "adjoint" and args.impl == "ours":
         run_adjoint_bench(args)
+    elif args.workload == "sweeps" and args.impl == "ours":
+        run_sweeps_bench(args)
     elif args.impl == "reference":
         run_reference(args)
     else:
