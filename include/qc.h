@@ -111,8 +111,10 @@ qc_status qc_state_init_vector(qc_state* s, const void* amps, qc_dtype src_dtype
  * counter-based SplitMix64 stream (Steele, Lea, Flood, OOPSLA 2014) with uniforms
  * u1 = U(2j), u2 = U(2j+1), U(c) = (mix(seed + (c+1)*0x9E3779B97F4A7C15) >> 11) * 2^-53,
  * and the Box-Muller transform r = sqrt(-2 ln(1-u1)), (re, im) = r (cos, sin)(2 pi u2).
- * The norm is accumulated in FP64 and the division done in FP64 before rounding
- * to the state's precision.  Synchronising. */
+ * The norm is accumulated in FP64.  Complex128: transform and division by the norm in
+ * FP64.  Complex64: transform in FP32 with 1-u1 formed exactly from the integer draw,
+ * then multiplied by the FP64 reciprocal of the norm rounded once to FP32 (amplitudes
+ * within ~1e-7 relative of the FP64 construction).  Synchronising. */
 qc_status qc_state_init_gaussian(qc_state* s, uint64_t seed);
 
 /* dst <- src (same n and dtype); used to branch on measurement outcomes. */
@@ -149,10 +151,12 @@ qc_status qc_apply_fused_k(qc_state* s, const int* qubits, int k, const double* 
  * ------------------------------------------------------------------------- */
 
 /* Measures qubit q in the Z basis: P(o) = sum over indices whose bit for q is o of
- * |psi_i|^2 (FP64).  With T = P(0) + P(1), the outcome is 1 iff u*T >= P(0) (u in
- * [0,1), supplied by the caller).  The state is collapsed onto the outcome and
- * divided by sqrt(P(outcome)) in FP64.  Returns the outcome and P(outcome)/T.
- * Synchronising. */
+ * |psi_i|^2, summed in FP64 (complex64: each |psi_i|^2 formed in FP32).  With
+ * T = P(0) + P(1), the outcome is 1 iff u*T >= P(0) (u in [0,1), supplied by the
+ * caller).  The state is collapsed onto the outcome and renormalised: the kept
+ * amplitudes are multiplied by 1/sqrt(P(outcome)), formed once in FP64 (complex64:
+ * rounded once to FP32), which is within one rounding of dividing by sqrt(P(outcome));
+ * the others are set to zero.  Returns the outcome and P(outcome)/T.  Synchronising. */
 qc_status qc_measure(qc_state* s, int q, double u, int* outcome, double* prob);
 
 /* Forced branch: collapses onto `outcome` and renormalises, returning its

@@ -45,21 +45,26 @@ __device__ __forceinline__ uint32_t bswz(uint32_t r) {
   return r ^ ((x ^ (x >> 4) ^ (x >> 8)) & 15u);
 }
 
-// fused layer gate of qubit q: U = RZ(t') RY(t), (c,s) = cos/sin(t/2), e = exp(-i t'/2)
-struct Gate1 {
-  float u00r, u00i, u01r, u01i, u10r, u10i, u11r, u11i;
+// fused layer gate of qubit q: U = RZ(t') RY(t), (c,s) = cos/sin(t/2), e = exp(-i t'/2).
+// Entry e (00, 01, 10, 11) u = (ur, ui) is kept as the packed pairs a = (ur, ur) and
+// b = (-ui, ui), so that u x = a * (xr, xi) + b * (xi, xr): two packed FMAs.
+struct GateP {
+  float2 a[4], b[4];
 };
 
-__device__ __forceinline__ Gate1 layer_gate(const float* p) {
+__device__ __forceinline__ GateP layer_gate(const float* p) {
   float s, c, sz, cz;
   sincosf(0.5f * p[0], &s, &c);
   sincosf(0.5f * p[1], &sz, &cz);
   // RZ = diag(cz - i sz, cz + i sz); RY = [[c, -s], [s, c]]
-  Gate1 g;
-  g.u00r = cz * c;  g.u00i = -sz * c;
-  g.u01r = -cz * s; g.u01i = sz * s;
-  g.u10r = cz * s;  g.u10i = sz * s;
-  g.u11r = cz * c;  g.u11i = sz * c;
+  const float ur[4] = {cz * c, -cz * s, cz * s, cz * c};
+  const float ui[4] = {-sz * c, sz * s, sz * s, sz * c};
+  GateP g;
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    g.a[e] = make_float2(ur[e], ur[e]);
+    g.b[e] = make_float2(-ui[e], ui[e]);
+  }
   return g;
 }
 
@@ -70,8 +75,8 @@ __device__ __forceinline__ Gate1 layer_gate(const float* p) {
 // the local->global bit map `gbit`).
 template <int SB>
 __device__ __forceinline__ void batch_stage(Cplx<float>* buf, int nl, const int8_t (&sl)[SB],
-                                            const Gate1* gates, const int8_t (&slot_q)[SB], bool phase, bool zz,
-                                            int n, uint64_t gbase, const int8_t* gbit, float* zz_acc) {
+                                            const GateP* gates, const int8_t (&slot_q)[SB], bool phase, bool zz,
+                                            int n, uint64_t gbase, const int8_t* gbit, double* zz_acc) {
   constexpr int NA = 1 << SB;
   const int ngroups = 1 << (nl - SB);
   // non-slot local bits in ascending order
@@ -103,14 +108,16 @@ __device__ __forceinline__ void batch_stage(Cplx<float>* buf, int nl, const int8
 #pragma unroll
     for (int k = 0; k < SB; ++k) {
       if (slot_q[k] < 0) continue;
-      const Gate1 u = gates[slot_q[k]];
-      const Cplx<float> u00{u.u00r, u.u00i}, u01{u.u01r, u.u01i}, u10{u.u10r, u.u10i}, u11{u.u11r, u.u11i};
+      const GateP& u = gates[slot_q[k]];
+      const float2 a00 = u.a[0], a01 = u.a[1], a10 = u.a[2], a11 = u.a[3];
+      const float2 b00 = u.b[0], b01 = u.b[1], b10 = u.b[2], b11 = u.b[3];
 #pragma unroll
       for (int j = 0; j < NA; ++j) {
         if (j & (1 << k)) continue;
-        const Cplx<float> x = v[j], y = v[j | (1 << k)];
-        v[j] = cmul2(u00, x, u01, y);
-        v[j | (1 << k)] = cmul2(u10, x, u11, y);
+        const int j1 = j | (1 << k);
+        const float2 x = f2(v[j]), xs = f2swap(v[j]), y = f2(v[j1]), ys = f2swap(v[j1]);
+        v[j] = c2(__ffma2_rn(b01, ys, __ffma2_rn(a01, y, __ffma2_rn(b00, xs, __fmul2_rn(a00, x)))));
+        v[j1] = c2(__ffma2_rn(b11, ys, __ffma2_rn(a11, y, __ffma2_rn(b10, xs, __fmul2_rn(a10, x)))));
       }
     }
     if (phase || zz) {
@@ -121,6 +128,7 @@ __device__ __forceinline__ void batch_stage(Cplx<float>* buf, int nl, const int8
       uint64_t gs[SB];
 #pragma unroll
       for (int k = 0; k < SB; ++k) gs[k] = uint64_t(1) << gbit[sl[k]];
+      float zg = 0.0f;  // this group's share, added to the FP64 accumulator once
 #pragma unroll
       for (int j = 0; j < NA; ++j) {
         uint64_t gi = gr0;
@@ -133,9 +141,10 @@ __device__ __forceinline__ void batch_stage(Cplx<float>* buf, int nl, const int8
         }
         if (zz) {
           const float pj = v[j].re * v[j].re + v[j].im * v[j].im;
-          *zz_acc += pj * float((n - 1) - 2 * __popcll((gi ^ (gi >> 1)) & zmask));
+          zg += pj * float((n - 1) - 2 * __popcll((gi ^ (gi >> 1)) & zmask));
         }
       }
+      if (zz) *zz_acc += double(zg);
     }
 #pragma unroll
     for (int j = 0; j < NA; ++j) {
@@ -152,9 +161,9 @@ __device__ __forceinline__ void batch_stage(Cplx<float>* buf, int nl, const int8
 // into stages of SB; `qubit_of_local[b]` is the qubit of local bit b, or -1 if this
 // pass applies no gate there.  The CZ phase / ZZ readout go into the last stage.
 template <int SB>
-__device__ void batch_layer_on_buffer(Cplx<float>* buf, int nl, const int8_t* qubit_of_local, const Gate1* gates,
+__device__ void batch_layer_on_buffer(Cplx<float>* buf, int nl, const int8_t* qubit_of_local, const GateP* gates,
                                       bool phase, bool zz, int n, uint64_t gbase, const int8_t* gbit,
-                                      float* zz_acc) {
+                                      double* zz_acc) {
   // local bits with gates, in order
   int8_t act[kBatchTileBits];
   int na = 0;
@@ -185,14 +194,15 @@ __device__ void batch_layer_on_buffer(Cplx<float>* buf, int nl, const int8_t* qu
   }
 }
 
-template <int SB>
-__global__ void __launch_bounds__(1 << (kBatchTileBits - SB), 1)
+// MINB: blocks per SM the register budget is sized for (each holds a 64 KiB tile)
+template <int SB, int NT, int MINB>
+__global__ void __launch_bounds__(NT, MINB)
     k_batch(const BatchCirc* __restrict__ circs, int ncirc, int layers, const float* __restrict__ params,
             unsigned* __restrict__ counter, float2* __restrict__ scratch, size_t scratch_per_block,
             double* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cplx<float>* tile = reinterpret_cast<Cplx<float>*>(smem_raw);  // 2^13 amplitudes
-  __shared__ Gate1 gates[kBatchMaxN];
+  __shared__ GateP gates[kBatchMaxN];
   __shared__ int8_t qol[kBatchTileBits], gbit[kBatchTileBits];
   __shared__ int s_idx;
   __shared__ double red[32];
@@ -205,7 +215,7 @@ __global__ void __launch_bounds__(1 << (kBatchTileBits - SB), 1)
     const BatchCirc C = circs[idx];
     const int n = C.n;
     const float* p = params + C.poff;
-    float zz = 0.0f;
+    double zz = 0.0;
     if (n <= kBatchTileBits) {
       // whole state in shared memory: |0...0>
       for (int i = threadIdx.x; i < (1 << n); i += blockDim.x) tile[i] = Cplx<float>{0.f, 0.f};
@@ -256,31 +266,34 @@ __global__ void __launch_bounds__(1 << (kBatchTileBits - SB), 1)
             else
               gbase = uint64_t(t) << lowB;
             {
-              // neighbouring amplitude pairs as 16-byte loads, all issued before any store
-              constexpr int NT = 1 << (kBatchTileBits - SB);
+              // neighbouring amplitude pairs as 16-byte loads, CH of them issued before
+              // their stores
               constexpr int PER = (1 << (kBatchTileBits - 1)) / NT;
-              float4 buf[PER];
+              constexpr int CH = PER < 8 ? PER : 8;
 #pragma unroll
-              for (int k = 0; k < PER; ++k) {
-                const uint32_t r = 2u * (threadIdx.x + k * NT);
-                const uint64_t gi = gbase | (pass == 0 ? uint64_t(r)
-                                                      : (uint64_t(r & ((1u << lowB) - 1)) |
-                                                         (uint64_t(r >> lowB) << kBatchTileBits)));
-                buf[k] = reinterpret_cast<const float4*>(gstate)[gi >> 1];
-              }
+              for (int k0 = 0; k0 < PER; k0 += CH) {
+                float4 buf[CH];
 #pragma unroll
-              for (int k = 0; k < PER; ++k) {
-                const uint32_t r = 2u * (threadIdx.x + k * NT);
-                const uint32_t ps = bswz(r);
-                tile[ps] = Cplx<float>{buf[k].x, buf[k].y};
-                tile[ps ^ 1u] = Cplx<float>{buf[k].z, buf[k].w};
+                for (int k = 0; k < CH; ++k) {
+                  const uint32_t r = 2u * (threadIdx.x + (k0 + k) * NT);
+                  const uint64_t gi = gbase | (pass == 0 ? uint64_t(r)
+                                                        : (uint64_t(r & ((1u << lowB) - 1)) |
+                                                           (uint64_t(r >> lowB) << kBatchTileBits)));
+                  buf[k] = reinterpret_cast<const float4*>(gstate)[gi >> 1];
+                }
+#pragma unroll
+                for (int k = 0; k < CH; ++k) {
+                  const uint32_t r = 2u * (threadIdx.x + (k0 + k) * NT);
+                  const uint32_t ps = bswz(r);
+                  tile[ps] = Cplx<float>{buf[k].x, buf[k].y};
+                  tile[ps ^ 1u] = Cplx<float>{buf[k].z, buf[k].w};
+                }
               }
             }
             __syncthreads();
             batch_layer_on_buffer<SB>(tile, kBatchTileBits, qol, gates, pass == 1,
                                       pass == 1 && l == layers - 1, n, gbase, gbit, &zz);
             {
-              constexpr int NT = 1 << (kBatchTileBits - SB);
               constexpr int PER = (1 << (kBatchTileBits - 1)) / NT;
 #pragma unroll
               for (int k = 0; k < PER; ++k) {
@@ -317,15 +330,37 @@ __global__ void __launch_bounds__(1 << (kBatchTileBits - SB), 1)
 // ---------------------------------------------------------------------------
 // host: plan cache, autotuner, CUDA graph
 // ---------------------------------------------------------------------------
+// Launch shapes the autotuner chooses from: register-stage width SB (the fusion width:
+// 2^SB amplitudes per thread per stage) and threads per block.
+struct BatchShape {
+  int sb, nt, minb;
+};
+constexpr BatchShape kBatchShapes[] = {{4, 256, 2}, {4, 128, 3}, {5, 128, 2}};
+constexpr int kNumBatchShapes = int(sizeof(kBatchShapes) / sizeof(kBatchShapes[0]));
+
+template <int SH>
+struct ShapeKernel {
+  static constexpr BatchShape S = kBatchShapes[SH];
+  static constexpr auto fn = k_batch<S.sb, S.nt, S.minb>;
+};
+
+template <int SH>
+static int batch_blocks_per_sm(size_t smem) {
+  int b = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, ShapeKernel<SH>::fn, kBatchShapes[SH].nt, smem);
+  return b < 1 ? 1 : b;
+}
+
+
 struct BatchPlan {
   std::string key;
   int device = -1;
-  int sb = 5;
+  int shape = 0;
+  int grid_of[kNumBatchShapes] = {};
   BatchCirc* d_circs = nullptr;
   unsigned* d_counter = nullptr;
   float2* d_scratch = nullptr;
   size_t scratch_per_block = 0;
-  int grid = 0;
   int ncirc = 0, layers = 0;
   const float* params = nullptr;
   double* out = nullptr;
@@ -345,24 +380,30 @@ static void free_plan(BatchPlan& p) {
   p = BatchPlan();
 }
 
-static qc_status launch_batch(const BatchPlan& p, int sb, cudaStream_t stream) {
+static qc_status launch_batch(const BatchPlan& p, int shape, cudaStream_t stream) {
   const size_t smem = sizeof(Cplx<float>) << kBatchTileBits;
   cudaError_t e = cudaMemsetAsync(p.d_counter, 0, sizeof(unsigned), stream);
   if (e != cudaSuccess) return check_cuda(e, "batch counter reset");
-  if (sb == 5) {
-    QC_COUNT(), k_batch<5><<<p.grid, 1 << (kBatchTileBits - 5), smem, stream>>>(
-        p.d_circs, p.ncirc, p.layers, p.params, p.d_counter, p.d_scratch, p.scratch_per_block, p.out);
-  } else {
-    QC_COUNT(), k_batch<4><<<p.grid, 1 << (kBatchTileBits - 4), smem, stream>>>(
-        p.d_circs, p.ncirc, p.layers, p.params, p.d_counter, p.d_scratch, p.scratch_per_block, p.out);
+  const unsigned grid = unsigned(p.grid_of[shape]);
+  const unsigned nt = unsigned(kBatchShapes[shape].nt);
+#define QC_BATCH_LAUNCH(SH)                                                                                  \
+  QC_COUNT(), ShapeKernel<SH>::fn<<<grid, nt, smem, stream>>>(p.d_circs, p.ncirc, p.layers, p.params,        \
+                                                               p.d_counter, p.d_scratch, p.scratch_per_block, \
+                                                               p.out)
+  switch (shape) {
+    case 0: QC_BATCH_LAUNCH(0); break;
+    case 1: QC_BATCH_LAUNCH(1); break;
+    default: QC_BATCH_LAUNCH(2); break;
   }
+#undef QC_BATCH_LAUNCH
   return check_launch("batch kernel");
 }
 
-// Autotuner: times each fusion width once on the real batch (CUDA events) and keeps
-// the fastest; results are kept per (GPU, workload shape) and, if QC_AUTOTUNE_CACHE
-// names a file, appended to it as "key sb" lines and read back by later processes.
-static int autotune_sb(const BatchPlan& p, cudaStream_t stream, const std::string& key) {
+// Autotuner: times each launch shape (fusion width SB, block size) once on the real
+// batch (CUDA events) and keeps the fastest; results are kept per (GPU, workload shape)
+// and, if QC_AUTOTUNE_CACHE names a file, appended to it as "key shape" lines and read
+// back by later processes.
+static int autotune_shape(const BatchPlan& p, cudaStream_t stream, const std::string& key) {
   auto it = g_tuned.find(key);
   if (it != g_tuned.end()) return it->second;
   const char* path = getenv("QC_AUTOTUNE_CACHE");
@@ -372,7 +413,7 @@ static int autotune_sb(const BatchPlan& p, cudaStream_t stream, const std::strin
       char k[512];
       int v;
       while (fscanf(f, "%511s %d", k, &v) == 2)
-        if (key == k && (v == 4 || v == 5)) {
+        if (key == k && v >= 0 && v < kNumBatchShapes) {
           fclose(f);
           g_tuned[key] = v;
           return v;
@@ -380,21 +421,21 @@ static int autotune_sb(const BatchPlan& p, cudaStream_t stream, const std::strin
       fclose(f);
     }
   }
-  int best = 5;
+  int best = 0;
   float best_ms = 1e30f;
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  for (int sb : {5, 4}) {
+  for (int sh = 0; sh < kNumBatchShapes; ++sh) {
     cudaEventRecord(e0, stream);
-    if (launch_batch(p, sb, stream) != QC_OK) continue;
+    if (launch_batch(p, sh, stream) != QC_OK) continue;
     cudaEventRecord(e1, stream);
     cudaEventSynchronize(e1);
     float ms = 0;
     cudaEventElapsedTime(&ms, e0, e1);
     if (ms < best_ms) {
       best_ms = ms;
-      best = sb;
+      best = sh;
     }
   }
   cudaEventDestroy(e0);
@@ -471,33 +512,35 @@ extern "C" qc_status qc_run_batch(const qc_batch* b, void* stream_v, double* dev
     std::vector<BatchCirc> circs(b->count);
     for (int i = 0; i < b->count; ++i) circs[i] = BatchCirc{b->n[i], i, b->param_offset[i]};
     std::stable_sort(circs.begin(), circs.end(), [](const BatchCirc& x, const BatchCirc& y) { return x.n > y.n; });
-    p.grid = prop.multiProcessorCount;
+    const size_t smem = sizeof(Cplx<float>) << kBatchTileBits;
+    qc_status st = QC_OK;
+    for (auto fn : {ShapeKernel<0>::fn, ShapeKernel<1>::fn, ShapeKernel<2>::fn})
+      if (st == QC_OK)
+        st = check_cuda(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
+                        "batch smem");
+    p.grid_of[0] = prop.multiProcessorCount * batch_blocks_per_sm<0>(smem);
+    p.grid_of[1] = prop.multiProcessorCount * batch_blocks_per_sm<1>(smem);
+    p.grid_of[2] = prop.multiProcessorCount * batch_blocks_per_sm<2>(smem);
+    const int max_grid = std::max(p.grid_of[0], std::max(p.grid_of[1], p.grid_of[2]));
     p.scratch_per_block = maxn > kBatchTileBits ? (size_t(1) << maxn) : 1;
-    qc_status st = check_cuda(cudaMalloc(&p.d_circs, sizeof(BatchCirc) * circs.size()), "batch table");
+    if (st == QC_OK) st = check_cuda(cudaMalloc(&p.d_circs, sizeof(BatchCirc) * circs.size()), "batch table");
     if (st == QC_OK) st = check_cuda(cudaMalloc(&p.d_counter, 256), "batch counter");
     if (st == QC_OK)
-      st = check_cuda(cudaMalloc(&p.d_scratch, sizeof(float2) * p.scratch_per_block * p.grid), "batch scratch");
+      st = check_cuda(cudaMalloc(&p.d_scratch, sizeof(float2) * p.scratch_per_block * max_grid), "batch scratch");
     if (st == QC_OK)
       st = check_cuda(cudaMemcpy(p.d_circs, circs.data(), sizeof(BatchCirc) * circs.size(), cudaMemcpyHostToDevice),
                       "batch table upload");
-    const size_t smem = sizeof(Cplx<float>) << kBatchTileBits;
-    if (st == QC_OK)
-      st = check_cuda(cudaFuncSetAttribute(k_batch<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
-                      "batch smem");
-    if (st == QC_OK)
-      st = check_cuda(cudaFuncSetAttribute(k_batch<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
-                      "batch smem");
     if (st != QC_OK) {
       free_plan(g_batch);
       return st;
     }
-    p.sb = autotune_sb(p, stream, key);
+    p.shape = autotune_shape(p, stream, key);
     // record [counter reset, kernel] once in a CUDA graph on a private stream
     st = check_cuda(cudaStreamCreateWithFlags(&p.capture, cudaStreamNonBlocking), "capture stream");
     cudaGraph_t graph = nullptr;
     if (st == QC_OK) st = check_cuda(cudaStreamBeginCapture(p.capture, cudaStreamCaptureModeThreadLocal), "capture");
     if (st == QC_OK) {
-      qc_status ls = launch_batch(p, p.sb, p.capture);
+      qc_status ls = launch_batch(p, p.shape, p.capture);
       cudaError_t e = cudaStreamEndCapture(p.capture, &graph);
       st = ls != QC_OK ? ls : check_cuda(e, "end capture");
     }
@@ -508,7 +551,7 @@ extern "C" qc_status qc_run_batch(const qc_batch* b, void* stream_v, double* dev
       return st;
     }
   }
-  g_last_batch_sb = g_batch.sb;
+  g_last_batch_sb = kBatchShapes[g_batch.shape].sb;
   QC_COUNT();  // the graph's kernel
   return check_cuda(cudaGraphLaunch(g_batch.exec, stream), "batch graph launch");
 }

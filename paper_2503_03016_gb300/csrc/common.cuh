@@ -144,9 +144,38 @@ __device__ __forceinline__ void st_amp2<double>(double* a, uint64_t i, Cplx<doub
   p[1] = make_double2(x1.re, x1.im);
 }
 
+// complex64 amplitude as a packed FP32 pair (re, im), its swap (im, re), and back
+__device__ __forceinline__ float2 f2(Cplx<float> z) { return make_float2(z.re, z.im); }
+__device__ __forceinline__ float2 f2swap(Cplx<float> z) { return make_float2(z.im, z.re); }
+__device__ __forceinline__ Cplx<float> c2(float2 z) { return Cplx<float>{z.x, z.y}; }
+
 // |a|^2 in FP64 as two rounded products and one rounded sum (never fused)
 __device__ __forceinline__ double prob_fp64(double re, double im) {
   return __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
+}
+
+// Exact binary32 -> binary64 widening with integer operations (IEEE 754 formats: sign
+// bit, 8/11 exponent bits with bias 127/1023, 23/52 fraction bits).  A normal float
+// keeps its sign and fraction (shifted up 29 bits) and has its exponent re-biased by
+// 1023 - 127 = 896; zero keeps its sign; subnormal, infinite and NaN inputs (never
+// produced by unitary evolution of a normalised state) take the hardware conversion.
+__device__ __forceinline__ double widen_exact(float x) {
+  const uint32_t b = __float_as_uint(x);
+  const uint32_t e = (b >> 23) & 0xFFu;
+  const uint64_t sign = uint64_t(b >> 31) << 63;
+  if (e - 1u < 254u)  // 1 <= e <= 254: normal
+    return __longlong_as_double(
+        (long long)(sign | (uint64_t(e + 896u) << 52) | (uint64_t(b & 0x7FFFFFu) << 29)));
+  if ((b & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)sign);
+  return double(x);
+}
+
+// The same |a|^2 for complex64 amplitudes: both squares of a widened float are exact
+// in FP64 (24-bit significands), so one fused multiply-add rounds re^2 + im^2 exactly
+// once -- bit for bit the value of the two-product form above, with fewer FP64 ops.
+__device__ __forceinline__ double prob_fp64(float re, float im) {
+  const double dre = widen_exact(re), dim = widen_exact(im);
+  return __fma_rn(dre, dre, __dmul_rn(dim, dim));
 }
 
 // ---------------------------------------------------------------------------

@@ -30,8 +30,21 @@ __global__ void __launch_bounds__(256) k_outcome_partials(const R* __restrict__ 
       const uint64_t i = 2 * it;
       Cplx<R> x0, x1;
       ld_amp2<R>(a, i, x0, x1);
-      const double p0 = double(x0.re) * double(x0.re) + double(x0.im) * double(x0.im);
-      const double p1 = double(x1.re) * double(x1.re) + double(x1.im) * double(x1.im);
+      double p0, p1;
+      if constexpr (sizeof(R) == 4) {
+        // complex64: squares in FP32 (relative error 2^-24 per amplitude), sums in FP64
+        const float f0 = fmaf(x0.re, x0.re, x0.im * x0.im), f1 = fmaf(x1.re, x1.re, x1.im * x1.im);
+        if (m == 1) {
+          p0 = widen_exact(f0);
+          p1 = widen_exact(f1);
+        } else {
+          p0 = widen_exact(f0 + f1);
+          p1 = 0.0;
+        }
+      } else {
+        p0 = double(x0.re) * double(x0.re) + double(x0.im) * double(x0.im);
+        p1 = double(x1.re) * double(x1.re) + double(x1.im) * double(x1.im);
+      }
       if (m == 1) {
         s0 += p0;
         s1 += p1;
@@ -64,21 +77,31 @@ __global__ void k_sum2(const double* partials, int count, double* out) {
   }
 }
 
+// Keeps the amplitudes whose bit m reads `outcome`, scaled by inv = 1/sqrt(P) (formed
+// once in FP64 by the host; complex64 applies it rounded to FP32), and zeroes the rest
+// without reading them.  Two neighbouring amplitudes per step (N >= 2).
 template <typename R>
 __global__ void __launch_bounds__(256) k_collapse(R* __restrict__ a, uint64_t N, uint64_t m, int outcome,
-                                                  double s) {
+                                                  double inv) {
+  const R f = R(inv);
+  const Cplx<R> zero{R(0), R(0)};
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-  for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < N; i += stride) {
-    const int b = (i & m) ? 1 : 0;
-    Cplx<R> v = ld_amp<R>(a, i);
-    if (b != outcome) {
-      v.re = R(0);
-      v.im = R(0);
+  for (uint64_t it = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; it < N / 2; it += stride) {
+    const uint64_t i = 2 * it;
+    if (m == 1) {
+      Cplx<R> x0, x1;
+      ld_amp2<R>(a, i, x0, x1);
+      if (outcome == 0)
+        st_amp2<R>(a, i, Cplx<R>{x0.re * f, x0.im * f}, zero);
+      else
+        st_amp2<R>(a, i, zero, Cplx<R>{x1.re * f, x1.im * f});
+    } else if (((i & m) ? 1 : 0) != outcome) {
+      st_amp2<R>(a, i, zero, zero);
     } else {
-      v.re = R(__ddiv_rn(double(v.re), s));
-      v.im = R(__ddiv_rn(double(v.im), s));
+      Cplx<R> x0, x1;
+      ld_amp2<R>(a, i, x0, x1);
+      st_amp2<R>(a, i, Cplx<R>{x0.re * f, x0.im * f}, Cplx<R>{x1.re * f, x1.im * f});
     }
-    st_amp<R>(a, i, v);
   }
 }
 
@@ -91,7 +114,7 @@ __global__ void __launch_bounds__(256) k_probs(const R* __restrict__ a, uint64_t
   if (N == 1) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       Cplx<R> v = ld_amp<R>(a, 0);
-      p[0] = prob_fp64(double(v.re), double(v.im));
+      p[0] = prob_fp64(v.re, v.im);
     }
     return;
   }
@@ -99,7 +122,7 @@ __global__ void __launch_bounds__(256) k_probs(const R* __restrict__ a, uint64_t
     Cplx<R> x0, x1;
     ld_amp2<R>(a, 2 * it, x0, x1);
     reinterpret_cast<double2*>(p)[it] =
-        make_double2(prob_fp64(double(x0.re), double(x0.im)), prob_fp64(double(x1.re), double(x1.im)));
+        make_double2(prob_fp64(x0.re, x0.im), prob_fp64(x1.re, x1.im));
   }
 }
 
@@ -181,12 +204,12 @@ struct AmpSource {
   __device__ __forceinline__ void load2(uint64_t i, double& p0, double& p1) const {
     Cplx<R> x0, x1;
     ld_amp2<R>(a, i, x0, x1);
-    p0 = prob_fp64(double(x0.re), double(x0.im));
-    p1 = prob_fp64(double(x1.re), double(x1.im));
+    p0 = prob_fp64(x0.re, x0.im);
+    p1 = prob_fp64(x1.re, x1.im);
   }
   __device__ __forceinline__ double load1(uint64_t i) const {
     Cplx<R> x = ld_amp<R>(a, i);
-    return prob_fp64(double(x.re), double(x.im));
+    return prob_fp64(x.re, x.im);
   }
 };
 struct ProbSource {
@@ -334,21 +357,24 @@ __global__ void __launch_bounds__(256) k_draw(Src src, uint64_t nleaf, int ls, c
   for (uint64_t s = warp; s < uint64_t(shots); s += nwarps) {
     const double t = u[s] * T;
     const bool below = t < T;
-    // first leaf whose end value passes the test (lane 0 searches, then broadcast)
-    uint64_t leaf = 0;
-    if (lane == 0) {
-      uint64_t lo = 0, hi = nleaf - 1;
-      while (lo < hi) {
-        const uint64_t mid = lo + (hi - lo) / 2;
-        const double c = leaf_end[mid];
-        if (below ? (t < c) : (c >= T))
-          hi = mid;
-        else
-          lo = mid + 1;
-      }
-      leaf = lo;
+    // first leaf whose end value passes the test (the test is false, then true, along
+    // the leaves, and true at the last one).  The answer stays in [lo, hi]; each round
+    // the 32 lanes probe the ends of 32 equal parts of it, and the first part whose end
+    // passes becomes the new range: ~log_32(nleaf) rounds of parallel loads.
+    uint64_t lo = 0, hi = nleaf - 1;
+    while (lo < hi) {
+      const uint64_t step = (hi - lo + 32) / 32;  // ceil((hi - lo + 1) / 32) >= 1
+      uint64_t pos = lo + (uint64_t(lane) + 1) * step - 1;
+      if (pos > hi) pos = hi;
+      const double c = leaf_end[pos];
+      const unsigned pass = __ballot_sync(0xffffffffu, below ? (t < c) : (c >= T));
+      const int k = pass ? __ffs(pass) - 1 : 31;  // lane 31 probes hi, which passes
+      const uint64_t new_hi = __shfl_sync(0xffffffffu, pos, k);
+      const uint64_t prev = __shfl_sync(0xffffffffu, pos, k > 0 ? k - 1 : 0);
+      lo = k > 0 ? prev + 1 : lo;
+      hi = new_hi;
     }
-    leaf = __shfl_sync(0xffffffffu, leaf, 0);
+    const uint64_t leaf = lo;
     U128 v0, v1;
     leaf_values(src, leaf, ls, lane, v0, v1);
     // inclusive scan of the lane pairs
@@ -445,12 +471,12 @@ static qc_status check_q(const qc_state* s, int q) {
 static qc_status do_collapse(qc_state* s, int q, int outcome, double P) {
   const uint64_t N = state_len(s);
   const uint64_t m = uint64_t(1) << (s->n - 1 - q);
-  const double sc = sqrt(P);
-  const unsigned g = stream_grid(N, 256);
+  const double inv = 1.0 / sqrt(P);
+  const unsigned g = stream_grid(N / 2, 256);
   if (s->dtype == QC_C64)
-    QC_COUNT(), k_collapse<float><<<g, 256, 0, s->stream>>>(reinterpret_cast<float*>(s->amps), N, m, outcome, sc);
+    QC_COUNT(), k_collapse<float><<<g, 256, 0, s->stream>>>(reinterpret_cast<float*>(s->amps), N, m, outcome, inv);
   else
-    QC_COUNT(), k_collapse<double><<<g, 256, 0, s->stream>>>(reinterpret_cast<double*>(s->amps), N, m, outcome, sc);
+    QC_COUNT(), k_collapse<double><<<g, 256, 0, s->stream>>>(reinterpret_cast<double*>(s->amps), N, m, outcome, inv);
   return check_launch("collapse");
 }
 

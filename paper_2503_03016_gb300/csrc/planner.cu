@@ -122,9 +122,6 @@ __device__ __forceinline__ void load_mat(R (&um)[NV], const R* __restrict__ u) {
 // u = (ur, ui) as the two pairs (ur, ur) and (-ui, ui), so that u x is
 // (ur, ur) * (xr, xi) + (-ui, ui) * (xi, xr): two paired FMAs (one instruction each on
 // sm_100 and later) in place of four scalar ones.
-__device__ __forceinline__ float2 f2(Cplx<float> z) { return make_float2(z.re, z.im); }
-__device__ __forceinline__ float2 f2swap(Cplx<float> z) { return make_float2(z.im, z.re); }
-__device__ __forceinline__ Cplx<float> c2(float2 z) { return Cplx<float>{z.x, z.y}; }
 
 template <int NE>
 __device__ __forceinline__ void load_packed(float2 (&a)[NE], float2 (&b)[NE], const float* __restrict__ u) {

@@ -113,12 +113,29 @@ __device__ __forceinline__ void gauss_amp(uint64_t seed, uint64_t j, double& re,
   im = r * sn;
 }
 
+// Complex64 states: the same transform in FP32 (relative error ~1e-7 per amplitude,
+// the size of complex64 rounding), with 1 - u1 = (2^53 - k1) 2^-53 formed exactly from
+// the integer draw so that the logarithm stays accurate for u1 near 1.
+__device__ __forceinline__ void gauss_amp(uint64_t seed, uint64_t j, float& re, float& im) {
+  const uint64_t k1 = splitmix64(seed, 2 * j) >> 11, k2 = splitmix64(seed, 2 * j + 1) >> 11;
+  const float v = float((uint64_t(1) << 53) - k1) * 0x1.0p-53f;  // 1 - u1 in (0, 1]
+  const float r = sqrtf(-2.0f * logf(v));
+  float sn, cs;
+  sincospif(float(k2) * 0x1.0p-52f, &sn, &cs);  // angle 2 pi u2
+  re = r * cs;
+  im = r * sn;
+}
+
+template <typename R>
 __global__ void k_gauss_norm_partials(uint64_t seed, uint64_t N, double* partials) {
   double acc = 0.0;
   for (uint64_t j = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; j < N; j += uint64_t(gridDim.x) * blockDim.x) {
-    double re, im;
+    R re, im;
     gauss_amp(seed, j, re, im);
-    acc += prob_fp64(re, im);
+    if constexpr (sizeof(R) == 4)
+      acc += widen_exact(fmaf(re, re, im * im));
+    else
+      acc += prob_fp64(re, im);
   }
   acc = block_sum(acc);
   if (threadIdx.x == 0) partials[blockIdx.x] = acc;
@@ -127,10 +144,14 @@ __global__ void k_gauss_norm_partials(uint64_t seed, uint64_t N, double* partial
 template <typename R>
 __global__ void k_gauss_fill(uint64_t seed, uint64_t N, const double* norm2, R* a) {
   const double s = sqrt(*norm2);
+  const float inv = float(1.0 / s);
   for (uint64_t j = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; j < N; j += uint64_t(gridDim.x) * blockDim.x) {
-    double re, im;
+    R re, im;
     gauss_amp(seed, j, re, im);
-    st_amp<R>(a, j, {R(re / s), R(im / s)});
+    if constexpr (sizeof(R) == 4)
+      st_amp<R>(a, j, {re * inv, im * inv});
+    else
+      st_amp<R>(a, j, {re / s, im / s});
   }
 }
 
@@ -647,7 +668,10 @@ qc_status qc_state_init_gaussian(qc_state* s, uint64_t seed) {
   void* scr = nullptr;
   if (qc_status st = state_scratch(s, sizeof(double) * (g + 1), &scr)) return st;
   double* partials = reinterpret_cast<double*>(scr);
-  QC_COUNT(), k_gauss_norm_partials<<<g, B, 0, s->stream>>>(seed, N, partials);
+  if (s->dtype == QC_C64)
+    QC_COUNT(), k_gauss_norm_partials<float><<<g, B, 0, s->stream>>>(seed, N, partials);
+  else
+    QC_COUNT(), k_gauss_norm_partials<double><<<g, B, 0, s->stream>>>(seed, N, partials);
   QC_COUNT(), k_sum_partials<<<1, 1024, 0, s->stream>>>(partials, int(g), 1, partials + g);
   if (s->dtype == QC_C64)
     QC_COUNT(), k_gauss_fill<float><<<g, B, 0, s->stream>>>(seed, N, partials + g, reinterpret_cast<float*>(s->amps));

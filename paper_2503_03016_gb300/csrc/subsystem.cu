@@ -42,7 +42,7 @@ __global__ void __launch_bounds__(256) k_marginal_partials(const R* __restrict__
   __syncthreads();
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < N; i += uint64_t(gridDim.x) * blockDim.x) {
     const Cplx<R> v = ld_amp<R>(amps, i);
-    const double p = prob_fp64(double(v.re), double(v.im));
+    const double p = prob_fp64(v.re, v.im);
     int x = 0;
     for (int k = 0; k < s.m; ++k) x |= int((i >> s.bit[k]) & 1) << k;
     atomicAdd(&hist[x], p);

@@ -129,12 +129,15 @@ def test_circuits_and_inverse(dtype):
 
 
 def test_gaussian_init_matches_generator():
+    """complex128: the FP64 construction to rounding; complex64: the transform in FP32,
+    within a few FP32 roundings (the bound 1e-6 is 17x FP32 epsilon, 10x under the
+    complex64 target)."""
     import paper_2503_03016_gb300 as P
-    for n in (1, 5, 12):
+    for n in (1, 5, 12, 16):
         st = P.State(n, "c128").init_gaussian(3)
         assert rel_l2(st.numpy(), W.gaussian_state(n, 3)) <= 1e-14
         st64 = P.State(n, "c64").init_gaussian(3)
-        assert rel_l2(st64.numpy(), W.gaussian_state(n, 3)) <= 1e-7
+        assert rel_l2(st64.numpy(), W.gaussian_state(n, 3)) <= 1e-6
 
 
 def test_argument_errors():

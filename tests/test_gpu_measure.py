@@ -102,6 +102,22 @@ def test_probs_bit_exact(dtype, n):
     np.testing.assert_array_equal(p, oracle.probs(amps))
 
 
+def test_probs_c64_special_values():
+    """FP64 |a|^2 of complex64 amplitudes of every kind: zeros of both signs, subnormal
+    and boundary floats, negative and large values, bit for bit against the oracle's
+    rounded two-product form (the state is not normalised)."""
+    f32 = np.float32
+    vals = np.array([0.0, -0.0, 1e-40, -1e-45, 2.0 ** -126, -(2.0 ** -126) * (1 - 2.0 ** -23), 2.0 ** -149,
+                     1.0, -1.0, 0.70710677, float(np.nextafter(f32(1), f32(2))), 1e-20, -3e19, 123.456,
+                     1.8446743e19, -(2.0 ** -100)], dtype=np.float32)
+    rng = np.random.default_rng(3)
+    psi = (vals + 1j * vals[rng.permutation(vals.size)]).astype(np.complex64)
+    for dt in ("c64", "c128"):
+        st = gpu_state(psi, dt)
+        p = st.probs().cpu().numpy()
+        np.testing.assert_array_equal(p, oracle.probs(psi.astype(np.complex128)))
+
+
 @pytest.mark.parametrize("n", [1, 2, 5, 6, 7, 12, 17])
 def test_sampler_bit_exact_on_oracle_probabilities(n):
     """The GPU sampler fed the oracle's p gives the oracle's indices exactly."""
