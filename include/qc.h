@@ -66,8 +66,8 @@ int qc_abi_version(void);
 /* Number of CUDA kernels this library has launched in this process (all threads);
  * a diagnostic for benchmarks. */
 uint64_t qc_launch_count(void);
-/* Number of tile passes the planner used for the most recent QC_RUN_FUSED circuit
- * (process-wide; a diagnostic for benchmarks). */
+/* Number of tile passes the planner used for the most recent QC_RUN_FUSED circuit or
+ * fused adjoint reverse sweep (process-wide; a diagnostic for benchmarks). */
 int qc_last_pass_count(void);
 /* Plans circuit `c` as QC_RUN_FUSED would for a state of `dtype` and reports the number
  * of tile passes, register stages and tile ops; host only (no device work, no GPU
@@ -294,7 +294,11 @@ qc_status qc_run_circuit(qc_state* s, const qc_circuit* c, const double* params,
  * U = exp(-i t G/2)); dE/dt_l = Im <lambda_l| G_l |psi_l> summed over the ops that use
  * parameter l, with psi_l the state after op l and lambda_l = U_{l+1}^dag ... U_L^dag H psi.
  * `params` (host, nparams doubles).  Writes *host_energy and host_grad[nparams].
- * Uses three state buffers of c->n qubits in `dtype`.  Synchronising. */
+ * Uses two state buffers of c->n qubits in `dtype` (library workspace, kept between
+ * calls).  Complex64 with n >= 12: the reverse sweep runs as tile passes over psi and
+ * lambda together (a recorded rotation's share is added before it is undone);
+ * otherwise one kernel per rotation.  Sums in FP64, fixed order (bitwise repeatable).
+ * Synchronising. */
 qc_status qc_adjoint_grad(const qc_circuit* c, const double* params, int nparams, const char* const* strings,
                           const double* coeffs, int nterms, qc_dtype dtype, void* stream, double* host_energy,
                           double* host_grad);

@@ -16,6 +16,7 @@
 #include <map>
 #include <vector>
 
+#include "adjoint_tiles.cuh"
 #include "circuit.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
@@ -90,8 +91,15 @@ __global__ void __launch_bounds__(256) k_inner_partials(const R* __restrict__ a,
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
   for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < N; i += stride) {
     const Cplx<R> x = ld_amp<R>(a, i), y = ld_amp<R>(b, i);
-    sr += double(x.re) * double(y.re) + double(x.im) * double(y.im);
-    si += double(x.re) * double(y.im) - double(x.im) * double(y.re);
+    // each term at the state's precision, the sums in FP64
+    const R tr = x.re * y.re + x.im * y.im, ti = x.re * y.im - x.im * y.re;
+    if constexpr (sizeof(R) == 4) {
+      sr += widen_exact(tr);
+      si += widen_exact(ti);
+    } else {
+      sr += tr;
+      si += ti;
+    }
   }
   sr = block_sum(sr);
   si = block_sum(si);
@@ -114,16 +122,21 @@ __global__ void __launch_bounds__(256) k_adjoint_rot(R* __restrict__ psi, R* __r
     const uint64_t i0 = ((it & ~lo) << 1) | (it & lo), i1 = i0 | m;
     const Cplx<R> a0 = ld_amp<R>(psi, i0), a1 = ld_amp<R>(psi, i1);
     const Cplx<R> l0 = ld_amp<R>(lam, i0), l1 = ld_amp<R>(lam, i1);
-    // (G psi) on the pair; then Im sum conj(l) * (G psi)
-    double gr0, gi0, gr1, gi1;
+    // (G psi) on the pair; then Im sum conj(l) * (G psi), the pair's share formed at the
+    // state's precision and added to the FP64 accumulator
+    R gr0, gi0, gr1, gi1;
     if (gen == 0) {  // X
       gr0 = a1.re; gi0 = a1.im; gr1 = a0.re; gi1 = a0.im;
     } else if (gen == 1) {  // Y: (G psi)_0 = -i a1, (G psi)_1 = i a0
-      gr0 = a1.im; gi0 = -double(a1.re); gr1 = -double(a0.im); gi1 = a0.re;
+      gr0 = a1.im; gi0 = -a1.re; gr1 = -a0.im; gi1 = a0.re;
     } else {  // Z
-      gr0 = a0.re; gi0 = a0.im; gr1 = -double(a1.re); gi1 = -double(a1.im);
+      gr0 = a0.re; gi0 = a0.im; gr1 = -a1.re; gi1 = -a1.im;
     }
-    acc += double(l0.re) * gi0 - double(l0.im) * gr0 + double(l1.re) * gi1 - double(l1.im) * gr1;
+    const R share = l0.re * gi0 - l0.im * gr0 + l1.re * gi1 - l1.im * gr1;
+    if constexpr (sizeof(R) == 4)
+      acc += widen_exact(share);
+    else
+      acc += share;
     st_amp<R>(psi, i0, cmul2(u00, a0, u01, a1));
     st_amp<R>(psi, i1, cmul2(u10, a0, u11, a1));
     st_amp<R>(lam, i0, cmul2(u00, l0, u01, l1));
@@ -174,6 +187,7 @@ struct AdjWork {
   void* p = nullptr;
 };
 static AdjWork g_adj;
+static AdjPlanBuf g_adj_plan;
 
 template <typename R>
 static qc_status adjoint_impl(const qc_circuit* c, const double* params, int nparams,
@@ -205,7 +219,15 @@ static qc_status adjoint_impl(const qc_circuit* c, const double* params, int npa
   }
   const int B = 256;
   const unsigned grid = stream_grid(N / 2, B, 8);
-  const size_t pbytes = sizeof(double) * (size_t(std::max(nrot, 1)) * grid + 2 * grid + 2 + nparams) + sizeof(int) * (nrot + 1);
+  // complex64 registers of 12 qubits and more take the fused sweep (tile passes over
+  // both states), which writes one partial per rotation and SM; the per-rotation kernels
+  // write one per block of `grid`.  Complex128 keeps the per-rotation kernels: it is
+  // bound by GB300's FP64 rate, and there the fused pass's phase multiplies (a CZ costs a
+  // complex product on half of both states instead of a sign flip on a quarter) outweigh
+  // the saved traffic.
+  const bool fused = sizeof(R) == 4 && n >= adjoint_tiles_min_qubits();
+  const unsigned pg = std::max<unsigned>(grid, unsigned(device_sm_count()));
+  const size_t pbytes = sizeof(double) * (size_t(std::max(nrot, 1)) * pg + 2 * grid + 2 + nparams) + sizeof(int) * (nrot + 1);
   const size_t need = 2 * sbytes + ((pbytes + 255) & ~size_t(255)) + 256;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -222,7 +244,7 @@ static qc_status adjoint_impl(const qc_circuit* c, const double* params, int npa
   char* w = static_cast<char*>(g_adj.p);
   R* lam = reinterpret_cast<R*>(w);
   double* part = reinterpret_cast<double*>(w + sbytes);
-  double* inner = part + size_t(std::max(nrot, 1)) * grid;
+  double* inner = part + size_t(std::max(nrot, 1)) * pg;
   double* grad = inner + 2 * grid + 2;
   int* dparams = reinterpret_cast<int*>(grad + nparams);
   // psi: a state handle over the workspace so that the gate kernels can run on it
@@ -271,6 +293,9 @@ static qc_status adjoint_impl(const qc_circuit* c, const double* params, int npa
     // reverse sweep
     std::vector<int> rot_params;
     int r = nrot;
+    int pgrid = int(grid);  // blocks whose partials each rotation sums
+    std::vector<ResolvedOp> rev;
+    std::vector<int> rgrad, rgen;
     for (int i = c->nops - 1; i >= 0; --i) {
       ResolvedOp ud = rops[i];
       const int dim = ud.form == FORM_2Q ? 4 : 2;
@@ -282,6 +307,14 @@ static qc_status adjoint_impl(const qc_circuit* c, const double* params, int npa
           t[2 * (a * dim + b) + 1] = -ud.m[2 * (b * dim + a) + 1];
         }
       memcpy(ud.m, t, sizeof(double) * 2 * dim * dim);
+      if (fused) {
+        // collected and run as tile passes below
+        rev.push_back(ud);
+        rgrad.push_back(gen[i] >= 0 ? --r : -1);
+        rgen.push_back(gen[i]);
+        if (gen[i] >= 0) rot_params.push_back(pidx[i]);
+        continue;
+      }
       if (gen[i] >= 0) {
         --r;
         Mat2<R> m;
@@ -294,15 +327,18 @@ static qc_status adjoint_impl(const qc_circuit* c, const double* params, int npa
         if ((st = apply_resolved(&sl, ud))) goto done;
       }
     }
+    if (fused && (st = adjoint_reverse_tiles<R>(n, rev, rgrad, rgen, reinterpret_cast<R*>(s.amps), lam, stream,
+                                                 &g_adj_plan, part, &pgrid)))
+      goto done;
     std::reverse(rot_params.begin(), rot_params.end());
     if (nrot > 0) {
       if ((st = check_cuda(cudaMemcpyAsync(dparams, rot_params.data(), sizeof(int) * nrot, cudaMemcpyHostToDevice,
                                            stream),
                            "upload")))
         goto done;
-      QC_COUNT(), k_reduce_grads<<<std::min(nrot, 1024), 1024, 0, stream>>>(part, int(grid), nrot);
+      QC_COUNT(), k_reduce_grads<<<std::min(nrot, 1024), 1024, 0, stream>>>(part, pgrid, nrot);
     }
-    QC_COUNT(), k_collect_grads<<<1, 32, 0, stream>>>(part, int(grid), dparams, nrot, grad, nparams);
+    QC_COUNT(), k_collect_grads<<<1, 32, 0, stream>>>(part, pgrid, dparams, nrot, grad, nparams);
     if ((st = check_launch("adjoint sweep"))) goto done;
     std::vector<double> e(2);
     if ((st = check_cuda(cudaMemcpyAsync(e.data(), inner + 2 * grid, 2 * sizeof(double), cudaMemcpyDeviceToHost,

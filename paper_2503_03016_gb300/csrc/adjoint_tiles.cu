@@ -1,0 +1,323 @@
+// Fused reverse sweep of the adjoint gradient (qc_adjoint_grad).
+//
+// The reverse sweep applies U_L^dag, ..., U_1^dag to psi and lambda and records, just
+// before a rotation U_l = exp(-i t_l G_l / 2) is undone, g_l = Im <lambda|G_l|psi>.  The
+// daggered gates in reverse order form a circuit like any other, so the tile planner
+// splits them into passes; this kernel runs a pass on BOTH states at once: it loads the
+// same tile (the same index bits) of psi and of lambda, applies every gate of the pass
+// to both in shared memory, and before each recorded rotation adds the tile's share of
+// Im <lambda|G|psi> -- a sum over the tile's amplitudes -- to that rotation's sum.  A
+// gate moved by the planner past gates it commutes with leaves the record unchanged:
+// Im <A lambda|G|A psi> = Im <lambda|G|psi> when the unitary A commutes with G.  Both
+// states then move once each way per pass instead of once per gate.
+//
+// Sums: each thread forms its share at the state's precision, a warp adds the 32
+// shares at that precision too, and each warp keeps one FP64 sum per recorded rotation
+// in shared memory; at the end every block writes its per-rotation totals, which are reduced over
+// blocks in a fixed order (deterministic).
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "adjoint_tiles.cuh"
+#include "circuit.cuh"
+#include "common.cuh"
+#include "kernels.cuh"
+#include "tiles.cuh"
+
+namespace qcgb {
+
+// Im(conj(a) b)
+template <typename R>
+__device__ __forceinline__ R im_conj_mul(Cplx<R> a, Cplx<R> b) {
+  return a.re * b.im - a.im * b.re;
+}
+
+// Share of Im <w|G|v> over the pairs along slot S0: G = X: (Gv)_0 = v_1, (Gv)_1 = v_0;
+// G = Y: (Gv)_0 = -i v_1, (Gv)_1 = i v_0.
+template <typename R, int SB, int S0>
+__device__ __forceinline__ R grad_pairs(const Cplx<R> (&v)[1 << SB], const Cplx<R> (&w)[1 << SB], int gen) {
+  R acc = R(0);
+#pragma unroll
+  for (int j = 0; j < (1 << SB); ++j) {
+    if (j & (1 << S0)) continue;
+    const int j1 = j | (1 << S0);
+    if (gen == 0) {
+      acc += im_conj_mul(w[j], v[j1]) + im_conj_mul(w[j1], v[j]);
+    } else {
+      const Cplx<R> g0{v[j1].im, -v[j1].re}, g1{-v[j].im, v[j].re};
+      acc += im_conj_mul(w[j], g0) + im_conj_mul(w[j1], g1);
+    }
+  }
+  return acc;
+}
+
+template <typename R, int SB>
+__device__ __forceinline__ R grad_pairs_at(int s0, const Cplx<R> (&v)[1 << SB], const Cplx<R> (&w)[1 << SB],
+                                           int gen) {
+  switch (s0) {
+    case 0: return grad_pairs<R, SB, 0>(v, w, gen);
+    case 1: return grad_pairs<R, SB, 1>(v, w, gen);
+    case 2: return grad_pairs<R, SB, 2>(v, w, gen);
+    case 3:
+      if constexpr (SB > 3) return grad_pairs<R, SB, 3>(v, w, gen);
+      return R(0);
+    default:
+      if constexpr (SB > 4) return grad_pairs<R, SB, 4>(v, w, gen);
+      return R(0);
+  }
+}
+
+template <typename R, int NT, int SB>
+__global__ void __launch_bounds__(NT, 1) k_adj_pass(R* __restrict__ psi, R* __restrict__ lam, const TilePass P,
+                                                    const TileStage* __restrict__ stages,
+                                                    const TileOp* __restrict__ ops, const R* __restrict__ pool,
+                                                    const R* __restrict__ mats, double* __restrict__ gpart) {
+  constexpr int NA = 1 << SB;
+  constexpr int NW = NT / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = P.m, L = P.L;
+  const uint32_t T = 1u << m;
+  Cplx<R>* bufs = reinterpret_cast<Cplx<R>*>(smem_raw);  // psi: 2 x T, lambda: 2 x T
+  uint64_t* hioff = reinterpret_cast<uint64_t*>(smem_raw + 4 * sizeof(Cplx<R>) * T);
+  const int nhi = m - L;
+  TileStage* sst = reinterpret_cast<TileStage*>(hioff + (1u << nhi));
+  TileOp* sop = reinterpret_cast<TileOp*>(sst + P.nstages);
+  R* smat = reinterpret_cast<R*>(sop + P.nops);
+  double* sacc = reinterpret_cast<double*>(smat + ((P.nmat + 1) & ~1));  // NW x ngrad
+  __shared__ int8_t sbits[16];
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) sbits[k] = P.bits[k];
+  }
+  __syncthreads();
+  for (uint32_t h = threadIdx.x; h < (1u << nhi); h += blockDim.x) {
+    uint64_t o = 0;
+    for (int k = 0; k < nhi; ++k)
+      if ((h >> k) & 1) o |= uint64_t(1) << sbits[L + k];
+    hioff[h] = o;
+  }
+  for (int i = threadIdx.x; i < P.nstages; i += blockDim.x) sst[i] = stages[P.stage0 + i];
+  for (int i = threadIdx.x; i < P.nops; i += blockDim.x) sop[i] = ops[P.op0 + i];
+  for (int i = threadIdx.x; i < P.nmat; i += blockDim.x) smat[i] = mats[P.mat0 + i];
+  for (int i = threadIdx.x; i < NW * P.ngrad; i += blockDim.x) sacc[i] = 0.0;
+  __syncthreads();
+  const uint32_t lowmask = (1u << L) - 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const Cplx<R>* cpool = reinterpret_cast<const Cplx<R>*>(pool);
+  uint64_t t = blockIdx.x;
+  if (t < P.ntiles) {
+    const uint64_t b0 = insert_zero_bits(t, sbits, m);
+    prefetch_tile<R>(bufs, psi, b0, hioff, L, T);
+    prefetch_tile<R>(bufs + 2 * T, lam, b0, hioff, L, T);
+  }
+  cp_async_commit();
+  for (int it = 0; t < P.ntiles; t += gridDim.x, ++it) {
+    Cplx<R>* tp = bufs + (it & 1) * T;
+    Cplx<R>* tl = bufs + 2 * T + (it & 1) * T;
+    const uint64_t base = insert_zero_bits(t, sbits, m);
+    const uint64_t tn = t + gridDim.x;
+    if (tn < P.ntiles) {
+      const uint64_t bn = insert_zero_bits(tn, sbits, m);
+      prefetch_tile<R>(bufs + ((it + 1) & 1) * T, psi, bn, hioff, L, T);
+      prefetch_tile<R>(bufs + 2 * T + ((it + 1) & 1) * T, lam, bn, hioff, L, T);
+    }
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    for (int s = 0; s < P.nstages; ++s) {
+      const TileStage& st = sst[s];
+      uint32_t r0 = 0;
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        if (k < m - SB) r0 |= ((threadIdx.x >> k) & 1u) << st.lane_bit[k];
+      uint32_t sw[SB];
+#pragma unroll
+      for (int k = 0; k < SB; ++k) sw[k] = tile_swz(1u << st.slot_bit[k]);
+      const uint32_t p0 = tile_swz(r0);
+      Cplx<R> v[NA], w[NA];
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        const uint32_t a = p0 ^ slot_xor<SB>(j, sw);
+        v[j] = tp[a];
+        w[j] = tl[a];
+      }
+      for (int q = 0; q < st.nops; ++q) {
+        const TileOp& op = sop[st.op0 + q];
+        if (op.grad >= 0) {
+          // recorded rotations carry no condition: every thread takes part
+          R share;
+          if (op.gen == 2) {
+            // Z on bit zloc (in the tile) or zglob (fixed by the tile number)
+            int ks = -1;
+#pragma unroll
+            for (int k = 0; k < SB; ++k)
+              if (st.slot_bit[k] == op.zloc) ks = k;
+            const uint32_t fixed = op.zloc >= 0 ? ((r0 >> op.zloc) & 1u) : uint32_t((base >> op.zglob) & 1u);
+            share = R(0);
+#pragma unroll
+            for (int j = 0; j < NA; ++j) {
+              const uint32_t b = ks >= 0 ? uint32_t((j >> ks) & 1) : fixed;
+              const R x = im_conj_mul(w[j], v[j]);
+              share += b ? -x : x;
+            }
+          } else {
+            share = grad_pairs_at<R, SB>(op.s0, v, w, op.gen);
+          }
+          // warp sum at the state's precision (32 shares), then one FP64 add per warp
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) share += __shfl_xor_sync(0xffffffffu, share, o);
+          if (lane == 0) sacc[warp * P.ngrad + op.gslot] += double(share);
+        }
+        if ((base & op.gmask) != op.gval) continue;  // condition on bits outside the tile
+        if ((r0 & op.lmask) != op.lval) continue;    // ... on the thread's lane bits
+        if (op.type == TOP_DENSE1) {
+          apply_dense1<R, SB>(op.s0, v, smat + op.mat, op.jmask);
+          apply_dense1<R, SB>(op.s0, w, smat + op.mat, op.jmask);
+        } else if (op.type == TOP_DENSE2) {
+          apply_dense2<R, SB>(op.s0, op.s1, v, smat + op.mat);
+          apply_dense2<R, SB>(op.s0, op.s1, w, smat + op.mat);
+        } else if (op.type == TOP_CZSET) {
+          const uint32_t flip = czset_flips<R, SB>(smat + op.mat, op.s0, r0, base);
+#pragma unroll
+          for (int j = 0; j < NA; ++j)
+            if ((flip >> j) & 1u) {
+              v[j] = Cplx<R>{-v[j].re, -v[j].im};
+              w[j] = Cplx<R>{-w[j].re, -w[j].im};
+            }
+        } else {
+          // exp(i (c + sum beta_p b_p)), the same factor on both states
+          const Cplx<R>* jt = reinterpret_cast<const Cplx<R>*>(smat + op.mat);
+          const Cplx<R>* l0 = cpool + op.tab;
+          const Cplx<R>* l1 = l0 + (1 << P.c0);
+          const Cplx<R>* g0 = l1 + (1 << (m - P.c0));
+          const uint32_t gn = 1u << P.cg, gm = gn - 1;
+          Cplx<R> f = cmul(cmul(g0[t & gm], g0[gn + ((t >> P.cg) & gm)]), g0[2 * gn + ((t >> (2 * P.cg)) & gm)]);
+          f = cmul(f, cmul(l0[r0 & ((1u << P.c0) - 1)], l1[r0 >> P.c0]));
+#pragma unroll
+          for (int j = 0; j < NA; ++j) {
+            if (!((op.jmask >> j) & 1u)) continue;  // ... on the slot bits
+            const Cplx<R> z = cmul(f, jt[j]);
+            v[j] = cmul(v[j], z);
+            w[j] = cmul(w[j], z);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        const uint32_t a = p0 ^ slot_xor<SB>(j, sw);
+        tp[a] = v[j];
+        tl[a] = w[j];
+      }
+      __syncthreads();
+    }
+    for (uint32_t e = threadIdx.x; e < T / 2; e += blockDim.x) {
+      const uint32_t r = 2 * e;
+      const uint64_t gi = base | hioff[r >> L] | (r & lowmask);
+      const uint32_t p = tile_swz(r);
+      st_amp2<R>(psi, gi, tp[p], tp[p ^ 1u]);
+      st_amp2<R>(lam, gi, tl[p], tl[p ^ 1u]);
+    }
+    __syncthreads();  // this buffer is refilled two iterations later
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+  // this block's total for each recorded rotation, warps added in a fixed order
+  for (int i = threadIdx.x; i < P.nops; i += blockDim.x) {
+    const TileOp& op = sop[i];
+    if (op.grad < 0) continue;
+    double a = 0.0;
+    for (int k = 0; k < NW; ++k) a += sacc[k * P.ngrad + op.gslot];
+    gpart[size_t(op.grad) * gridDim.x + blockIdx.x] = a;
+  }
+}
+
+// Tile shape of the fused sweep per precision: two states x two buffers of 2^m
+// amplitudes in shared memory (4 x 32 KiB), register stages of SB bits per state.
+template <typename R>
+struct AdjShape;
+template <>
+struct AdjShape<float> {
+  static constexpr int M = 12, L = 4, SB = 4, NT = 256;
+};
+template <>
+struct AdjShape<double> {
+  static constexpr int M = 11, L = 3, SB = 3, NT = 256;
+};
+
+int adjoint_tiles_min_qubits() { return 12; }
+
+template <typename R>
+qc_status adjoint_reverse_tiles(int n, const std::vector<ResolvedOp>& rev, const std::vector<int>& grad,
+                                const std::vector<int>& gen, R* psi, R* lam, cudaStream_t stream, AdjPlanBuf* buf,
+                                double* gpart, int* grid_out) {
+  using S = AdjShape<R>;
+  const int m = S::M, L = S::L;
+  if (n < m) {
+    set_error("fused adjoint sweep needs n >= %d", m);
+    return QC_ERR_UNSUPPORTED;
+  }
+  std::vector<PlanOp> pops;
+  to_plan_ops(rev, pops, &grad, &gen);
+  const std::vector<BuiltPass> bps = build_passes(pops, n, m, L);
+  HostPlan<R> hp;
+  for (const BuiltPass& bp : bps) emit_pass<R>(bp, pops, n, m, L, S::SB, hp, /*swap_ops=*/false);
+  g_last_pass_count = int(hp.passes.size());
+  auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
+  const size_t sb = al(hp.stages.size() * sizeof(TileStage));
+  const size_t ob = al(hp.ops.size() * sizeof(TileOp));
+  const size_t pb = al(hp.pool.size() * sizeof(R));
+  const size_t mb = al(hp.mats.size() * sizeof(R));
+  const size_t total = sb + ob + pb + mb + 256;
+  if (buf->bytes < total) {
+    if (buf->p) {
+      cudaStreamSynchronize(stream);
+      cudaFree(buf->p);
+      buf->p = nullptr;
+      buf->bytes = 0;
+    }
+    if (qc_status st = check_cuda(cudaMalloc(&buf->p, total), "adjoint plan")) return st;
+    buf->bytes = total;
+  }
+  buf->host.assign(sb + ob + pb + mb, 0);
+  char* h = buf->host.data();
+  if (!hp.stages.empty()) memcpy(h, hp.stages.data(), hp.stages.size() * sizeof(TileStage));
+  if (!hp.ops.empty()) memcpy(h + sb, hp.ops.data(), hp.ops.size() * sizeof(TileOp));
+  if (!hp.pool.empty()) memcpy(h + sb + ob, hp.pool.data(), hp.pool.size() * sizeof(R));
+  if (!hp.mats.empty()) memcpy(h + sb + ob + pb, hp.mats.data(), hp.mats.size() * sizeof(R));
+  char* base = static_cast<char*>(buf->p);
+  if (qc_status st = check_cuda(cudaMemcpyAsync(base, h, buf->host.size(), cudaMemcpyHostToDevice, stream),
+                                "adjoint plan upload"))
+    return st;
+  size_t plan_max = 0;
+  for (const TilePass& P : hp.passes)
+    plan_max = std::max(plan_max, P.nstages * sizeof(TileStage) + P.nops * sizeof(TileOp) +
+                                      ((P.nmat + 1) & ~1) * sizeof(R) + size_t(S::NT / 32) * P.ngrad * sizeof(double));
+  const size_t smem = 4 * sizeof(Cplx<R>) * (size_t(1) << m) + sizeof(uint64_t) * (size_t(1) << (m - L)) + plan_max;
+  if (qc_status st = check_cuda(cudaFuncSetAttribute(k_adj_pass<R, S::NT, S::SB>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
+                                "adjoint pass shared memory"))
+    return st;
+  const uint64_t ntiles = uint64_t(1) << (n - m);
+  const unsigned grid = unsigned(std::min<uint64_t>(ntiles, uint64_t(device_sm_count())));
+  const TileStage* dst = reinterpret_cast<const TileStage*>(base);
+  const TileOp* dop = reinterpret_cast<const TileOp*>(base + sb);
+  const R* dpool = reinterpret_cast<const R*>(base + sb + ob);
+  const R* dmats = reinterpret_cast<const R*>(base + sb + ob + pb);
+  const unsigned threads = 1u << (m - S::SB);
+  for (const TilePass& P : hp.passes)
+    QC_COUNT(), k_adj_pass<R, S::NT, S::SB><<<grid, threads, smem, stream>>>(psi, lam, P, dst, dop, dpool, dmats,
+                                                                             gpart);
+  *grid_out = int(grid);
+  return check_launch("adjoint pass");
+}
+
+template qc_status adjoint_reverse_tiles<float>(int, const std::vector<ResolvedOp>&, const std::vector<int>&,
+                                                const std::vector<int>&, float*, float*, cudaStream_t, AdjPlanBuf*,
+                                                double*, int*);
+template qc_status adjoint_reverse_tiles<double>(int, const std::vector<ResolvedOp>&, const std::vector<int>&,
+                                                 const std::vector<int>&, double*, double*, cudaStream_t,
+                                                 AdjPlanBuf*, double*, int*);
+
+}  // namespace qcgb

@@ -172,11 +172,18 @@ __device__ __forceinline__ U128 to_fixed(double p) {
   return r;
 }
 
-// round-to-nearest-even conversion back to FP64
-__device__ __forceinline__ double from_fixed(U128 x) {
-  if (x.hi == 0 && x.lo < (1ull << 53)) return ldexp(double(x.lo), -118);  // exact
-  int h = x.hi ? 127 - __clzll(x.hi) : 63 - __clzll(x.lo);                // top bit
-  const int sh = h - 52;                                                    // >= 1
+// Round-to-nearest-even conversion back to FP64, built as the double's bit pattern with
+// integer operations (IEEE 754 binary64: 11-bit exponent biased by 1023, 52 fraction
+// bits).  Values lie in [0, 2^10): every nonzero one is a normal double.
+__device__ __forceinline__ uint64_t fixed_to_bits(U128 x) {
+  constexpr uint64_t kFrac = (1ull << 52) - 1;
+  if (x.hi == 0 && x.lo < (1ull << 53)) {  // exact: at most 53 significant bits
+    if (x.lo == 0) return 0;
+    const int h = 63 - __clzll(x.lo);  // value = 1.f x 2^(h - 118)
+    return (uint64_t(h - 118 + 1023) << 52) | ((x.lo << (52 - h)) & kFrac);
+  }
+  const int h = x.hi ? 127 - __clzll(x.hi) : 63 - __clzll(x.lo);  // top bit
+  int sh = h - 52;                                                 // >= 1
   uint64_t mant, rem_hi_bit, rem_rest;
   // mant = x >> sh (53 bits)
   if (sh >= 64) {
@@ -194,8 +201,17 @@ __device__ __forceinline__ double from_fixed(U128 x) {
     rem_rest = hb > 0 && (x.lo & ((1ull << hb) - 1)) != 0;
   }
   if (rem_hi_bit && (rem_rest || (mant & 1))) mant += 1;
-  return ldexp(double(mant), sh - 118);
+  if (mant >> 53) {  // rounded up into the next binade
+    mant >>= 1;
+    sh += 1;
+  }
+  // value = mant x 2^(sh - 118) = 1.f x 2^(52 + sh - 118)
+  return (uint64_t(52 + sh - 118 + 1023) << 52) | (mant & kFrac);
 }
+__device__ __forceinline__ double from_fixed(U128 x) { return __longlong_as_double((long long)fixed_to_bits(x)); }
+
+// Non-negative doubles compare like their bit patterns as unsigned integers.
+__device__ __forceinline__ uint64_t dbits(double x) { return uint64_t(__double_as_longlong(x)); }
 
 // Sources of p_i: amplitudes (p = re*re + im*im in FP64) or a probability vector.
 template <typename R>
@@ -345,35 +361,54 @@ __global__ void __launch_bounds__(kScanBlock) k_leaf_offsets(U128* __restrict__ 
     }
 }
 
-// K3: one warp per shot.
+// K3: one warp per shot.  Comparisons of non-negative doubles are done on their bit
+// patterns (integer pipe).  The search starts in a table of kPivots leaf ends staged in
+// shared memory per block, then continues in global memory.
+constexpr int kPivots = 4096;
+
 template <typename Src>
 __global__ void __launch_bounds__(256) k_draw(Src src, uint64_t nleaf, int ls, const U128* __restrict__ leaf_off,
                                               const double* __restrict__ leaf_end, const double* __restrict__ u,
                                               int64_t shots, uint64_t* __restrict__ out) {
+  __shared__ uint64_t piv[kPivots];
   const int lane = threadIdx.x & 31;
   const uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
   const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
+  const uint64_t Tb = dbits(leaf_end[nleaf - 1]);
   const double T = leaf_end[nleaf - 1];
+  // pivot k = end of leaf min((k+1) seg - 1, nleaf - 1): the last pivot is the last leaf
+  const uint64_t seg = (nleaf + kPivots - 1) / kPivots;
+  for (int k = threadIdx.x; k < kPivots; k += blockDim.x) {
+    uint64_t e = (uint64_t(k) + 1) * seg - 1;
+    if (e > nleaf - 1) e = nleaf - 1;
+    piv[k] = dbits(leaf_end[e]);
+  }
+  __syncthreads();
   for (uint64_t s = warp; s < uint64_t(shots); s += nwarps) {
-    const double t = u[s] * T;
-    const bool below = t < T;
-    // first leaf whose end value passes the test (the test is false, then true, along
-    // the leaves, and true at the last one).  The answer stays in [lo, hi]; each round
-    // the 32 lanes probe the ends of 32 equal parts of it, and the first part whose end
-    // passes becomes the new range: ~log_32(nleaf) rounds of parallel loads.
-    uint64_t lo = 0, hi = nleaf - 1;
-    while (lo < hi) {
-      const uint64_t step = (hi - lo + 32) / 32;  // ceil((hi - lo + 1) / 32) >= 1
-      uint64_t pos = lo + (uint64_t(lane) + 1) * step - 1;
-      if (pos > hi) pos = hi;
-      const double c = leaf_end[pos];
-      const unsigned pass = __ballot_sync(0xffffffffu, below ? (t < c) : (c >= T));
-      const int k = pass ? __ffs(pass) - 1 : 31;  // lane 31 probes hi, which passes
-      const uint64_t new_hi = __shfl_sync(0xffffffffu, pos, k);
-      const uint64_t prev = __shfl_sync(0xffffffffu, pos, k > 0 ? k - 1 : 0);
-      lo = k > 0 ? prev + 1 : lo;
-      hi = new_hi;
-    }
+    const uint64_t tb = dbits(u[s] * T) & 0x7FFFFFFFFFFFFFFFull;  // -0 reads as +0
+    const bool below = tb < Tb;
+    // the test on a leaf end (false, then true, along the leaves; true at the last)
+    auto pass_test = [&](uint64_t cb) { return below ? (tb < cb) : (cb >= Tb); };
+    // 32-ary search: the answer stays in [lo, hi]; each round the 32 lanes probe the
+    // ends of 32 equal parts of it and the first part whose end passes is kept
+    auto narrow = [&](uint64_t& lo, uint64_t& hi, auto load) {
+      while (lo < hi) {
+        const uint64_t step = (hi - lo + 32) / 32;  // ceil((hi - lo + 1) / 32) >= 1
+        uint64_t pos = lo + (uint64_t(lane) + 1) * step - 1;
+        if (pos > hi) pos = hi;
+        const unsigned pass = __ballot_sync(0xffffffffu, pass_test(load(pos)));
+        const int k = pass ? __ffs(pass) - 1 : 31;  // lane 31 probes hi, which passes
+        const uint64_t new_hi = __shfl_sync(0xffffffffu, pos, k);
+        const uint64_t prev = __shfl_sync(0xffffffffu, pos, k > 0 ? k - 1 : 0);
+        lo = k > 0 ? prev + 1 : lo;
+        hi = new_hi;
+      }
+    };
+    uint64_t plo = 0, phi = kPivots - 1;
+    narrow(plo, phi, [&](uint64_t i) { return piv[i]; });
+    uint64_t lo = plo * seg, hi = (plo + 1) * seg - 1;
+    if (hi > nleaf - 1) hi = nleaf - 1;
+    narrow(lo, hi, [&](uint64_t i) { return dbits(leaf_end[i]); });
     const uint64_t leaf = lo;
     U128 v0, v1;
     leaf_values(src, leaf, ls, lane, v0, v1);
@@ -389,9 +424,8 @@ __global__ void __launch_bounds__(256) k_draw(Src src, uint64_t nleaf, int ls, c
     const U128 c0 = add128(add128(leaf_off[leaf], exc), v0);  // cdf of element 2*lane
     const U128 c1 = add128(c0, v1);                           // cdf of element 2*lane+1
     const bool valid0 = 2 * lane < ls, valid1 = 2 * lane + 1 < ls;
-    const double d0 = from_fixed(c0), d1 = from_fixed(c1);
-    const bool hit0 = valid0 && (below ? (t < d0) : (d0 >= T));
-    const bool hit1 = valid1 && (below ? (t < d1) : (d1 >= T));
+    const bool hit0 = valid0 && pass_test(fixed_to_bits(c0));
+    const bool hit1 = valid1 && pass_test(fixed_to_bits(c1));
     const unsigned bal = __ballot_sync(0xffffffffu, hit0 || hit1);
     const int first = __ffs(bal) - 1;  // leaf_end[leaf] passes, so some lane hits
     if (lane == first) out[s] = leaf * uint64_t(ls) + 2 * lane + (hit0 ? 0 : 1);

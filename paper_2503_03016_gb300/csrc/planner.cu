@@ -24,260 +24,21 @@
 #include <algorithm>
 #include <cmath>
 #include <complex>
+#include <mutex>
 #include <vector>
 
 #include "circuit.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
+#include "tiles.cuh"
 
 namespace qcgb {
 
-constexpr int kMaxStageBits = 5;  // amplitudes a thread holds per stage: 2^SB, SB <= 5
-
-enum TileOpType : int32_t { TOP_DENSE1 = 0, TOP_DENSE2 = 1, TOP_PHASE = 2 };
-
-struct TileOp {
-  int32_t type;
-  int32_t s0, s1;        // stage slots of the targets (DENSE2: s0 = first qubit = row MSB)
-  uint32_t lmask, lval;  // condition on the amplitude's local (in-tile) index
-  int32_t pad;
-  uint64_t gmask, gval;  // condition on the index bits outside the tile
-  int64_t mat;           // DENSE: matrix / PHASE: 2^SB-entry slot table, offset (R values)
-                         // in the pass's matrix block
-  int64_t tab;           // PHASE: offset (complex entries) of its other tables in the pool
-  int64_t pad2;          // 64-byte record: keeps the staged matrices 16-byte aligned
-};
-static_assert(sizeof(TileOp) == 64, "TileOp must be 64 bytes");
-
-struct TileStage {
-  int32_t op0, nops;
-  int8_t slot_bit[8];   // local bit of each slot (SB used)
-  int8_t lane_bit[16];  // local bit receiving bit k of the thread index (the m-SB non-slot
-                        // bits; the first ones cover distinct bit positions mod 4 so that
-                        // a half warp's shared-memory accesses fall in distinct banks)
-};
-static_assert(sizeof(TileStage) == 32, "TileStage must be 32 bytes");
-
-struct TilePass {
-  int32_t m, L;
-  int32_t stage0, nstages;
-  int32_t op0, nops;    // the pass's ops (staged in shared memory)
-  int32_t mat0, nmat;   // the pass's dense matrices and phase slot tables (R values)
-  int8_t bits[16];   // B ascending (global bit positions); bits[0..L) = 0..L-1
-  int32_t c0, c1;    // local phase-table chunks: local bits [0,c0) and [c0,m)
-  int32_t cg;        // tile-index phase-table chunk width (3 chunks)
-  uint64_t ntiles;
-};
-
-// ---------------------------------------------------------------------------
-// device side
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t tile_swz(uint32_t r) {
-  uint32_t x = r >> 4;
-  return r ^ ((x ^ (x >> 4) ^ (x >> 8)) & 15u);
-}
-
-// offset of slot combination j: OR of the slot masks selected by j's bits
-template <int SB>
-__device__ __forceinline__ uint32_t slot_off(int j, const uint32_t (&sm)[SB]) {
-  uint32_t o = 0;
-#pragma unroll
-  for (int k = 0; k < SB; ++k)
-    if ((j >> k) & 1) o |= sm[k];
-  return o;
-}
-
-// swizzled address offset of slot combination j: XOR of the swizzled slot masks
-// (the swizzle is linear over XOR, but swizzled masks may share bits)
-template <int SB>
-__device__ __forceinline__ uint32_t slot_xor(int j, const uint32_t (&sw)[SB]) {
-  uint32_t o = 0;
-#pragma unroll
-  for (int k = 0; k < SB; ++k)
-    if ((j >> k) & 1) o ^= sw[k];
-  return o;
-}
-
-// NV values of a 16-byte-aligned shared-memory matrix into registers
-template <typename R, int NV>
-__device__ __forceinline__ void load_mat(R (&um)[NV], const R* __restrict__ u) {
-  if (sizeof(R) == 4) {
-    const float4* q = reinterpret_cast<const float4*>(u);
-#pragma unroll
-    for (int i = 0; i < NV / 4; ++i) {
-      const float4 t = q[i];
-      um[4 * i] = R(t.x); um[4 * i + 1] = R(t.y); um[4 * i + 2] = R(t.z); um[4 * i + 3] = R(t.w);
-    }
-  } else {
-    const double2* q = reinterpret_cast<const double2*>(u);
-#pragma unroll
-    for (int i = 0; i < NV / 2; ++i) {
-      const double2 t = q[i];
-      um[2 * i] = R(t.x); um[2 * i + 1] = R(t.y);
-    }
-  }
-}
-
-// Complex64 gates on packed pairs.  For complex64 the planner stores each matrix entry
-// u = (ur, ui) as the two pairs (ur, ur) and (-ui, ui), so that u x is
-// (ur, ur) * (xr, xi) + (-ui, ui) * (xi, xr): two paired FMAs (one instruction each on
-// sm_100 and later) in place of four scalar ones.
-
-template <int NE>
-__device__ __forceinline__ void load_packed(float2 (&a)[NE], float2 (&b)[NE], const float* __restrict__ u) {
-  const float4* q = reinterpret_cast<const float4*>(u);
-#pragma unroll
-  for (int e = 0; e < NE; ++e) {
-    const float4 t = q[e];
-    a[e] = make_float2(t.x, t.y);
-    b[e] = make_float2(t.z, t.w);
-  }
-}
-
-template <typename R, int SB, int S0>
-__device__ __forceinline__ void dense1(Cplx<R> (&v)[1 << SB], const R* __restrict__ u, uint32_t r0,
-                                       const uint32_t (&sm)[SB], uint32_t lmask, uint32_t lval) {
-  if constexpr (sizeof(R) == 4) {
-    float2 a[4], b[4];
-    load_packed<4>(a, b, u);
-#pragma unroll
-    for (int j = 0; j < (1 << SB); ++j) {
-      if (j & (1 << S0)) continue;
-      const int j1 = j | (1 << S0);
-      if (((r0 | slot_off<SB>(j, sm)) & lmask) != lval) continue;
-      const float2 x = f2(v[j]), xs = f2swap(v[j]), y = f2(v[j1]), ys = f2swap(v[j1]);
-      v[j] = c2(__ffma2_rn(b[1], ys, __ffma2_rn(a[1], y, __ffma2_rn(b[0], xs, __fmul2_rn(a[0], x)))));
-      v[j1] = c2(__ffma2_rn(b[3], ys, __ffma2_rn(a[3], y, __ffma2_rn(b[2], xs, __fmul2_rn(a[2], x)))));
-    }
-  } else {
-    R um[8];
-    load_mat<R, 8>(um, u);
-    const Cplx<R> u00{um[0], um[1]}, u01{um[2], um[3]}, u10{um[4], um[5]}, u11{um[6], um[7]};
-#pragma unroll
-    for (int j = 0; j < (1 << SB); ++j) {
-      if (j & (1 << S0)) continue;
-      const int j1 = j | (1 << S0);
-      if (((r0 | slot_off<SB>(j, sm)) & lmask) != lval) continue;
-      const Cplx<R> x = v[j], y = v[j1];
-      v[j] = cmul2(u00, x, u01, y);
-      v[j1] = cmul2(u10, x, u11, y);
-    }
-  }
-}
-
-template <typename R, int SB, int S0, int S1>
-__device__ __forceinline__ void dense2(Cplx<R> (&v)[1 << SB], const R* __restrict__ us) {
-  if constexpr (sizeof(R) == 4) {
-    float2 a[16], b[16];
-    load_packed<16>(a, b, us);
-    // the four output rows are independent chains: step them together so that each
-    // packed FMA's result is not needed by the next instruction
-#pragma unroll
-    for (int j = 0; j < (1 << SB); ++j) {
-      if (j & ((1 << S0) | (1 << S1))) continue;
-      const int i[4] = {j, j | (1 << S1), j | (1 << S0), j | (1 << S0) | (1 << S1)};
-      float2 x[4], xs[4], o[4];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        x[c] = f2(v[i[c]]);
-        xs[c] = f2swap(v[i[c]]);
-      }
-#pragma unroll
-      for (int r = 0; r < 4; ++r) o[r] = __fmul2_rn(a[4 * r], x[0]);
-#pragma unroll
-      for (int c = 0; c < 4; ++c) {
-        if (c > 0) {
-#pragma unroll
-          for (int r = 0; r < 4; ++r) o[r] = __ffma2_rn(a[4 * r + c], x[c], o[r]);
-        }
-#pragma unroll
-        for (int r = 0; r < 4; ++r) o[r] = __ffma2_rn(b[4 * r + c], xs[c], o[r]);
-      }
-#pragma unroll
-      for (int r = 0; r < 4; ++r) v[i[r]] = c2(o[r]);
-    }
-    return;
-  }
-  R u[32];
-  load_mat<R, 32>(u, us);
-#pragma unroll
-  for (int j = 0; j < (1 << SB); ++j) {
-    if (j & ((1 << S0) | (1 << S1))) continue;
-    const int i0 = j, i1 = j | (1 << S1), i2 = j | (1 << S0), i3 = j | (1 << S0) | (1 << S1);
-    const Cplx<R> x0 = v[i0], x1 = v[i1], x2 = v[i2], x3 = v[i3];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      const R* ur = u + 8 * r;
-      Cplx<R> o;
-      o.re = fma(ur[0], x0.re, fma(-ur[1], x0.im, fma(ur[2], x1.re, fma(-ur[3], x1.im,
-             fma(ur[4], x2.re, fma(-ur[5], x2.im, fma(ur[6], x3.re, -ur[7] * x3.im)))))));
-      o.im = fma(ur[0], x0.im, fma(ur[1], x0.re, fma(ur[2], x1.im, fma(ur[3], x1.re,
-             fma(ur[4], x2.im, fma(ur[5], x2.re, fma(ur[6], x3.im, ur[7] * x3.re)))))));
-      if (r == 0) v[i0] = o;
-      else if (r == 1) v[i1] = o;
-      else if (r == 2) v[i2] = o;
-      else v[i3] = o;
-    }
-  }
-}
-
-template <typename R, int SB>
-__device__ __forceinline__ void apply_dense1(int s0, Cplx<R> (&v)[1 << SB], const R* u, uint32_t r0,
-                                             const uint32_t (&sm)[SB], uint32_t lmask, uint32_t lval) {
-  switch (s0) {
-    case 0: dense1<R, SB, 0>(v, u, r0, sm, lmask, lval); break;
-    case 1: dense1<R, SB, 1>(v, u, r0, sm, lmask, lval); break;
-    case 2: dense1<R, SB, 2>(v, u, r0, sm, lmask, lval); break;
-    case 3: dense1<R, SB, 3>(v, u, r0, sm, lmask, lval); break;
-    default:
-      if constexpr (SB > 4) dense1<R, SB, 4>(v, u, r0, sm, lmask, lval);
-      break;
-  }
-}
-
-#define QC_D2(A, B) \
-  case (A) * 8 + (B): dense2<R, SB, A, B>(v, u); return;
-template <typename R, int SB>
-__device__ __forceinline__ void apply_dense2(int s0, int s1, Cplx<R> (&v)[1 << SB], const R* u) {
-  switch (s0 * 8 + s1) {
-    // the planner orders every two-qubit gate so that s0 < s1
-    QC_D2(0, 1) QC_D2(0, 2) QC_D2(0, 3) QC_D2(1, 2) QC_D2(1, 3) QC_D2(2, 3)
-    default: break;
-  }
-  if constexpr (SB > 4) {
-    switch (s0 * 8 + s1) {
-      QC_D2(0, 4) QC_D2(1, 4) QC_D2(2, 4) QC_D2(3, 4)
-      default: break;
-    }
-  }
-}
-#undef QC_D2
-
-// Asynchronous global -> shared copy of one amplitude (8 or 16 bytes).
-template <typename R>
-__device__ __forceinline__ void cp_async_amp(Cplx<R>* dst, const R* src) {
-  const uint32_t d = uint32_t(__cvta_generic_to_shared(dst));
-  if (sizeof(R) == 4)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
-  else
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
-
-template <typename R>
-__device__ __forceinline__ void prefetch_tile(Cplx<R>* buf, const R* amps, uint64_t base, const uint64_t* hioff,
-                                              int L, uint32_t T) {
-  const uint32_t lowmask = (1u << L) - 1;
-  for (uint32_t r = threadIdx.x; r < T; r += blockDim.x) {
-    const uint64_t gi = base | hioff[r >> L] | (r & lowmask);
-    cp_async_amp<R>(buf + tile_swz(r), amps + 2 * gi);
-  }
-}
-
 // One launch = one pass over all tiles; blockDim = 2^(m-SB), one block per SM with
 // two tile buffers: the next tile is fetched (cp.async) while this one is computed.
-template <typename R, int NT, int SB>
+// SIGNOPS: the plan contains CZ sign ops (a second instantiation without them keeps the
+// gate bodies' code generation unchanged for plans that have none)
+template <typename R, int NT, int SB, bool SIGNOPS>
 __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const TilePass P,
                                                      const TileStage* __restrict__ stages,
                                                      const TileOp* __restrict__ ops, const R* __restrict__ pool,
@@ -330,23 +91,31 @@ __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const
 #pragma unroll
       for (int k = 0; k < 16; ++k)
         if (k < m - SB) r0 |= ((threadIdx.x >> k) & 1u) << st.lane_bit[k];
-      uint32_t sm[SB], sw[SB];
+      uint32_t sw[SB];
 #pragma unroll
-      for (int k = 0; k < SB; ++k) {
-        sm[k] = 1u << st.slot_bit[k];
-        sw[k] = tile_swz(sm[k]);  // the swizzle is linear over XOR: swz(a^b) = swz(a)^swz(b)
-      }
+      for (int k = 0; k < SB; ++k)
+        sw[k] = tile_swz(1u << st.slot_bit[k]);  // the swizzle is linear over XOR: swz(a^b) = swz(a)^swz(b)
       const uint32_t p0 = tile_swz(r0);
       Cplx<R> v[NA];
 #pragma unroll
       for (int j = 0; j < NA; ++j) v[j] = tile[p0 ^ slot_xor<SB>(j, sw)];
       for (int q = 0; q < st.nops; ++q) {
         const TileOp& op = sop[st.op0 + q];
-        if ((base & op.gmask) != op.gval) continue;
+        if ((base & op.gmask) != op.gval) continue;  // condition on bits outside the tile
+        if ((r0 & op.lmask) != op.lval) continue;    // ... on the thread's lane bits
         if (op.type == TOP_DENSE1) {
-          apply_dense1<R, SB>(op.s0, v, smat + op.mat, r0, sm, op.lmask, op.lval);
+          apply_dense1<R, SB>(op.s0, v, smat + op.mat, op.jmask);
         } else if (op.type == TOP_DENSE2) {
           apply_dense2<R, SB>(op.s0, op.s1, v, smat + op.mat);
+        } else if (sizeof(R) == 8 && op.type == TOP_SWAP) {
+          if constexpr (sizeof(R) == 8) apply_swap<R, SB>(op.s0, op.s1, v);
+        } else if (SIGNOPS && op.type == TOP_CZSET) {
+          if constexpr (SIGNOPS) {
+            const uint32_t flip = czset_flips<R, SB>(smat + op.mat, op.s0, r0, base);
+#pragma unroll
+            for (int j = 0; j < NA; ++j)
+              if ((flip >> j) & 1u) v[j] = Cplx<R>{-v[j].re, -v[j].im};
+          }
         } else {
           // exp(i (c + sum beta_p b_p)) factorised over: tile-index chunks (3), the
           // thread's inactive local bits (2 chunks) and the 2^SB slot combinations
@@ -359,7 +128,7 @@ __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const
           w = cmul(w, cmul(l0[r0 & ((1u << P.c0) - 1)], l1[r0 >> P.c0]));
 #pragma unroll
           for (int j = 0; j < NA; ++j) {
-            if (((r0 | slot_off<SB>(j, sm)) & op.lmask) != op.lval) continue;
+            if (!((op.jmask >> j) & 1u)) continue;  // ... on the slot bits
             v[j] = cmul(v[j], cmul(w, jt[j]));
           }
         }
@@ -384,26 +153,35 @@ __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const
 // ---------------------------------------------------------------------------
 using cd = std::complex<double>;
 
-struct PlanOp {
-  // dense: 1 or 2 target bits, matrix, control mask/values (global bits)
-  // phase: condition mask/values (global), constant angle and per-bit coefficients
-  bool phase;
-  int nt;
-  int tb[2];
-  double m[32];
-  uint64_t cmask, cval;
-  double c;
-  std::vector<std::pair<int, double>> beta;  // (bit, coefficient)
-  uint64_t touched;                          // every bit the op reads or writes
-};
-
 static bool near_unit(cd z) { return std::abs(std::abs(z) - 1.0) < 1e-12; }
 
 // Converts resolved gates to plan ops; diagonal gates become phase ops.
-static void to_plan_ops(const std::vector<ResolvedOp>& in, std::vector<PlanOp>& out) {
-  for (const ResolvedOp& r : in) {
+void to_plan_ops(const std::vector<ResolvedOp>& in, std::vector<PlanOp>& out, const std::vector<int>* grad,
+                 const std::vector<int>* gen) {
+  for (size_t i = 0; i < in.size(); ++i) {
+    const ResolvedOp& r = in[i];
     PlanOp p{};
     p.cmask = p.cval = 0;
+    if (grad && (*grad)[i] >= 0) {
+      // a recorded rotation: X/Y generators stay dense 2x2 (even where the matrix
+      // happens to be diagonal), Z rotations are phase ops on their own bit
+      const int tgt = r.bits[0];
+      p.grad = (*grad)[i];
+      p.gen = (*gen)[i];
+      p.touched = uint64_t(1) << tgt;
+      if (p.gen == 2) {
+        p.phase = true;
+        p.c = std::arg(cd(r.m[0], r.m[1]));
+        p.beta = {{tgt, std::arg(cd(r.m[6], r.m[7])) - std::arg(cd(r.m[0], r.m[1]))}};
+      } else {
+        p.phase = false;
+        p.nt = 1;
+        p.tb[0] = tgt;
+        memcpy(p.m, r.m, sizeof(double) * 8);
+      }
+      out.push_back(p);
+      continue;
+    }
     if (r.form == FORM_2Q) {
       const cd d0(r.m[0], r.m[1]), d1(r.m[10], r.m[11]), d2(r.m[20], r.m[21]), d3(r.m[30], r.m[31]);
       bool diag = true;
@@ -419,7 +197,7 @@ static void to_plan_ops(const std::vector<ResolvedOp>& in, std::vector<PlanOp>& 
         q.c = t00;
         q.beta = {{a, t10 - t00}, {b, t01 - t00}};
         q.touched = (uint64_t(1) << a) | (uint64_t(1) << b);
-        out.push_back(q);
+        if (t00 != 0.0 || t10 != t00 || t01 != t00) out.push_back(q);  // skip the identity
         const double quad = t11 - t10 - t01 + t00;
         if (quad != 0.0) {
           PlanOp w{};
@@ -482,12 +260,7 @@ static void to_plan_ops(const std::vector<ResolvedOp>& in, std::vector<PlanOp>& 
   }
 }
 
-constexpr int kMaxPassOps = 128;  // bounds the plan staged in shared memory per pass
 
-struct BuiltPass {
-  std::vector<int> B;       // ascending
-  std::vector<int> ops;     // indices into plan ops, in order
-};
 
 // One pass over `remaining` in order.  With `fixed` set, B is exactly `B0` (ops whose
 // dense targets are outside it are skipped); otherwise B starts as B0 and grows to m
@@ -532,7 +305,7 @@ static void greedy_pass(const std::vector<PlanOp>& ops, const std::vector<int>& 
   *score = sc;
 }
 
-static std::vector<BuiltPass> build_passes(const std::vector<PlanOp>& ops, int n, int m, int L) {
+static std::vector<BuiltPass> build_passes_uncached(const std::vector<PlanOp>& ops, int n, int m, int L) {
   std::vector<int> remaining(ops.size());
   for (size_t i = 0; i < ops.size(); ++i) remaining[i] = int(i);
   std::vector<BuiltPass> passes;
@@ -578,19 +351,50 @@ static std::vector<BuiltPass> build_passes(const std::vector<PlanOp>& ops, int n
   return passes;
 }
 
-// Device plan assembled on the host.
-template <typename R>
-struct HostPlan {
-  std::vector<TilePass> passes;
-  std::vector<TileStage> stages;
-  std::vector<TileOp> ops;
-  std::vector<R> pool;  // phase tables read per thread (global memory)
-  std::vector<R> mats;  // per-pass matrices and slot tables (staged in shared memory)
+// The pass structure depends only on each op's kind, targets and touched bits -- not on
+// its matrix or angles -- so it is reused when a circuit is run again with other
+// parameters (training loops, repeated gradients).  A few recent structures are kept.
+struct PassCacheEntry {
+  std::vector<int64_t> key;
+  std::vector<BuiltPass> passes;
 };
+static std::mutex g_pass_cache_mu;
+static std::vector<PassCacheEntry> g_pass_cache;  // most recent last
+constexpr size_t kPassCacheEntries = 8;
+
+std::vector<BuiltPass> build_passes(const std::vector<PlanOp>& ops, int n, int m, int L) {
+  std::vector<int64_t> key;
+  key.reserve(3 + 5 * ops.size());
+  key.push_back(n);
+  key.push_back(m);
+  key.push_back(L);
+  for (const PlanOp& p : ops) {
+    key.push_back(p.phase ? -1 : p.nt);
+    key.push_back(p.phase ? 0 : p.tb[0]);
+    key.push_back(!p.phase && p.nt == 2 ? p.tb[1] : 0);
+    key.push_back(int64_t(p.touched));
+  }
+  {
+    std::lock_guard<std::mutex> lock(g_pass_cache_mu);
+    for (size_t e = 0; e < g_pass_cache.size(); ++e)
+      if (g_pass_cache[e].key == key) {
+        PassCacheEntry hit = std::move(g_pass_cache[e]);
+        g_pass_cache.erase(g_pass_cache.begin() + long(e));
+        g_pass_cache.push_back(std::move(hit));
+        return g_pass_cache.back().passes;
+      }
+  }
+  std::vector<BuiltPass> passes = build_passes_uncached(ops, n, m, L);
+  std::lock_guard<std::mutex> lock(g_pass_cache_mu);
+  if (g_pass_cache.size() >= kPassCacheEntries) g_pass_cache.erase(g_pass_cache.begin());
+  g_pass_cache.push_back(PassCacheEntry{std::move(key), passes});
+  return passes;
+}
+
 
 template <typename R>
-static void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int m, int L, int sb,
-                      HostPlan<R>& hp) {
+void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int m, int L, int sb,
+               HostPlan<R>& hp, bool swap_ops) {
   TilePass P{};
   P.m = m;
   P.L = L;
@@ -606,11 +410,12 @@ static void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int 
   int local_of[64];
   for (int b = 0; b < 64; ++b) local_of[b] = -1;
   for (int i = 0; i < m; ++i) local_of[bp.B[i]] = i;
-  // tile-index bit of each global bit outside B
-  int tbit_of[64];
+  // global bit of each tile-index bit (the bits outside B, ascending)
+  int gbit_of_tb[64];
   {
     int k = 0;
-    for (int b = 0; b < n; ++b) tbit_of[b] = local_of[b] >= 0 ? -1 : k++;
+    for (int b = 0; b < n; ++b)
+      if (local_of[b] < 0) gbit_of_tb[k++] = b;
   }
   // stages: each takes, in order, every remaining op of the pass whose dense targets
   // fit in <= 4 active local bits and that no skipped op it fails to commute with
@@ -670,11 +475,56 @@ static void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int 
     }
     st.op0 = int(hp.ops.size()) - P.op0;
     const size_t j = take.size();
+    // a CZ: the phase pi on b_t b_c keyed on its target t (no constant, no tag)
+    auto is_cz = [&](const PlanOp& o) {
+      return o.phase && o.grad < 0 && o.c == 0.0 && o.beta.size() == 1 && o.beta[0].second == M_PI &&
+             o.cmask == o.cval && __builtin_popcountll(o.cmask) == 1;
+    };
+    // code of one end of a CZ pair in this stage: 0x80 | slot, a lane bit (< 16), or
+    // 0x40 | global bit for a bit fixed by the tile number
+    auto cz_end = [&](int gbit) -> uint32_t {
+      const int lb = local_of[gbit];
+      if (lb < 0) return 0x40u | uint32_t(gbit);
+      for (int k = 0; k < sb; ++k)
+        if (st.slot_bit[k] == lb) return 0x80u | uint32_t(k);
+      return uint32_t(lb);
+    };
     for (size_t q = 0; q < j; ++q) {
       const PlanOp& p = pops[take[q]];
       TileOp op{};
       op.lmask = op.lval = 0;
       op.gmask = op.gval = 0;
+      op.grad = p.grad;
+      op.gslot = -1;
+      if (is_cz(p)) {
+        // a run of CZs (they commute) becomes one sign op: the amplitude's sign is the
+        // parity of sum over pairs b_t b_c; the pair codes go into the matrix block
+        op.type = TOP_CZSET;
+        op.jmask = 0xFFFFFFFFu;
+        op.mat = int64_t(hp.mats.size()) - P.mat0;
+        int np = 0;
+        for (;;) {
+          const PlanOp& c = pops[take[q]];
+          const uint32_t code = cz_end(__builtin_ctzll(c.cmask)) | (cz_end(c.beta[0].first) << 8);
+          R word{};
+          memcpy(&word, &code, sizeof(code));  // a small bit pattern: never a NaN
+          hp.mats.push_back(word);
+          ++np;
+          if (q + 1 >= j || !is_cz(pops[take[q + 1]])) break;
+          ++q;
+        }
+        // keep the block's later matrices 16-byte aligned (they are read as 16-byte words)
+        while ((hp.mats.size() - size_t(P.mat0)) * sizeof(R) % 16) hp.mats.push_back(R(0));
+        op.s0 = np;
+        hp.ops.push_back(op);
+        continue;
+      }
+      if (p.grad >= 0) {
+        op.gen = int8_t(p.gen);
+        op.gslot = P.ngrad++;
+        op.zglob = int8_t(p.touched ? __builtin_ctzll(p.touched) : 0);
+        op.zloc = int8_t(local_of[op.zglob]);
+      }
       for (int b = 0; b < n; ++b) {
         if (!((p.cmask >> b) & 1)) continue;
         const bool v = (p.cval >> b) & 1;
@@ -686,14 +536,43 @@ static void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int 
           if (v) op.gval |= uint64_t(1) << b;
         }
       }
-      if (!p.phase) {
-        op.type = p.nt == 1 ? TOP_DENSE1 : TOP_DENSE2;
-        auto slot = [&](int gbit) {
-          const int lb = local_of[gbit];
+      {
+        // split the in-tile condition: slot bits -> a table over the 2^sb slot
+        // combinations (jmask), the rest stays a per-thread test on the lane bits
+        uint32_t slotmask = 0;
+        for (int k = 0; k < sb; ++k) slotmask |= 1u << st.slot_bit[k];
+        const uint32_t ls = op.lmask & slotmask, lvs = op.lval & slotmask;
+        op.jmask = 0;
+        for (int jj = 0; jj < (1 << sb); ++jj) {
+          uint32_t loc = 0;
           for (int k = 0; k < sb; ++k)
-            if (st.slot_bit[k] == lb) return k;
-          return -1;
-        };
+            if ((jj >> k) & 1) loc |= 1u << st.slot_bit[k];
+          if ((loc & ls) == lvs) op.jmask |= 1u << jj;
+        }
+        op.lmask &= ~slotmask;
+        op.lval &= ~slotmask;
+      }
+      // exactly the SWAP permutation (rows 0, 2, 1, 3 of the identity): a register
+      // permutation in the stage, symmetric in its two slots
+      bool is_swap = swap_ops && !p.phase && p.nt == 2;
+      for (int e = 0; is_swap && e < 16; ++e) {
+        const int r = e >> 2, c = e & 3;
+        const int want_c = r == 1 ? 2 : r == 2 ? 1 : r;
+        if (p.m[2 * e] != (c == want_c ? 1.0 : 0.0) || p.m[2 * e + 1] != 0.0) is_swap = false;
+      }
+      auto slot = [&](int gbit) {
+        const int lb = local_of[gbit];
+        for (int k = 0; k < sb; ++k)
+          if (st.slot_bit[k] == lb) return k;
+        return -1;
+      };
+      if (is_swap) {
+        op.type = TOP_SWAP;
+        op.s0 = std::min(slot(p.tb[0]), slot(p.tb[1]));
+        op.s1 = std::max(slot(p.tb[0]), slot(p.tb[1]));
+        op.mat = 0;
+      } else if (!p.phase) {
+        op.type = p.nt == 1 ? TOP_DENSE1 : TOP_DENSE2;
         op.s0 = slot(p.tb[0]);
         op.s1 = p.nt == 2 ? slot(p.tb[1]) : 0;
         op.mat = int64_t(hp.mats.size()) - P.mat0;
@@ -726,50 +605,54 @@ static void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int 
         for (auto& be : p.beta) beta[be.first] += be.second;
         while (q + 1 < j) {
           const PlanOp& nx = pops[take[q + 1]];
-          if (!nx.phase || nx.cmask != p.cmask || nx.cval != p.cval) break;
+          // a recorded rotation starts its own op: its record must see the state
+          // before it (a tagged op may absorb the untagged ones after it)
+          if (!nx.phase || nx.cmask != p.cmask || nx.cval != p.cval || nx.grad >= 0) break;
           c += nx.c;
           for (auto& be : nx.beta) beta[be.first] += be.second;
           ++q;
         }
-        // tables: [16 slot combos][2^c0 low local][2^c1 high local][3 x 2^cg tile index]
+        // tables: [2^sb slot combos][2^c0 low local][2^c1 high local][3 x 2^cg tile index].
+        // Entry x of a table over bits g_0..g_{k-1} is exp(i sum_{x_j = 1} beta_{g_j}),
+        // built by doubling: entry x = entry(x without its top bit) * exp(i beta_top)
+        // (one complex product per entry; k <= 8 products deep, ~1e-15 relative).
+        auto table = [&](const std::vector<int>& gbits, double c0) {
+          std::vector<cd> t(size_t(1) << gbits.size());
+          t[0] = std::polar(1.0, c0);
+          for (size_t k = 0; k < gbits.size(); ++k) {
+            const cd f = std::polar(1.0, gbits[k] >= 0 ? beta[gbits[k]] : 0.0);
+            const size_t h = size_t(1) << k;
+            for (size_t x = 0; x < h; ++x) t[h + x] = t[x] * f;
+          }
+          return t;
+        };
         while (hp.pool.size() % 2) hp.pool.push_back(R(0));
         op.tab = int64_t(hp.pool.size() / 2);
-        auto push = [&](double ang) {
-          hp.pool.push_back(R(std::cos(ang)));
-          hp.pool.push_back(R(std::sin(ang)));
+        auto push_all = [&](std::vector<R>& dst, const std::vector<cd>& t) {
+          for (const cd& z : t) {
+            dst.push_back(R(z.real()));
+            dst.push_back(R(z.imag()));
+          }
         };
         op.mat = int64_t(hp.mats.size()) - P.mat0;
-        for (int jj = 0; jj < (1 << sb); ++jj) {
-          double a = 0;
-          for (int k = 0; k < sb; ++k)
-            if ((jj >> k) & 1) a += beta[bp.B[st.slot_bit[k]]];
-          hp.mats.push_back(R(std::cos(a)));
-          hp.mats.push_back(R(std::sin(a)));
-        }
+        std::vector<int> gb;
+        for (int k = 0; k < sb; ++k) gb.push_back(bp.B[st.slot_bit[k]]);
+        push_all(hp.mats, table(gb, 0.0));
         // inactive local bits only (slot bits are zero in r0)
-        for (int x = 0; x < (1 << P.c0); ++x) {
-          double a = 0;
-          for (int k = 0; k < P.c0; ++k)
-            if ((x >> k) & 1) a += beta[bp.B[k]];
-          push(a);
-        }
-        for (int x = 0; x < (1 << P.c1); ++x) {
-          double a = 0;
-          for (int k = 0; k < P.c1; ++k)
-            if ((x >> k) & 1) a += beta[bp.B[P.c0 + k]];
-          push(a);
-        }
-        for (int ch = 0; ch < 3; ++ch)
-          for (int x = 0; x < (1 << P.cg); ++x) {
-            double a = ch == 0 ? c : 0.0;
-            for (int k = 0; k < P.cg; ++k) {
-              const int tb = ch * P.cg + k;
-              if (!((x >> k) & 1)) continue;
-              for (int b = 0; b < n; ++b)
-                if (tbit_of[b] == tb) a += beta[b];
-            }
-            push(a);
+        gb.clear();
+        for (int k = 0; k < P.c0; ++k) gb.push_back(bp.B[k]);
+        push_all(hp.pool, table(gb, 0.0));
+        gb.clear();
+        for (int k = 0; k < P.c1; ++k) gb.push_back(bp.B[P.c0 + k]);
+        push_all(hp.pool, table(gb, 0.0));
+        for (int ch = 0; ch < 3; ++ch) {
+          gb.clear();
+          for (int k = 0; k < P.cg; ++k) {
+            const int tb = ch * P.cg + k;
+            gb.push_back(tb < n - m ? gbit_of_tb[tb] : -1);  // past the last tile bit: no bit
           }
+          push_all(hp.pool, table(gb, ch == 0 ? c : 0.0));
+        }
       }
       hp.ops.push_back(op);
     }
@@ -783,7 +666,12 @@ static void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int 
   hp.passes.push_back(P);
 }
 
-static int g_last_pass_count = 0;
+template void emit_pass<float>(const BuiltPass&, const std::vector<PlanOp>&, int, int, int, int, HostPlan<float>&,
+                               bool);
+template void emit_pass<double>(const BuiltPass&, const std::vector<PlanOp>&, int, int, int, int, HostPlan<double>&,
+                                bool);
+
+int g_last_pass_count = 0;  // also set by the fused adjoint sweep
 
 // Register stage width SB (a thread holds 2^SB amplitudes) and block size of the tile
 // pass per precision: blockDim = 2^(m - SB) <= NT with m = 13 (complex64) / 12.
@@ -807,7 +695,10 @@ static qc_status run_tiles(qc_state* s, const std::vector<ResolvedOp>& rops, int
   to_plan_ops(rops, pops);
   std::vector<BuiltPass> bps = build_passes(pops, n, m, L);
   HostPlan<R> hp;
-  for (const BuiltPass& bp : bps) emit_pass<R>(bp, pops, n, m, L, SB, hp);
+  // complex128 applies an exact SWAP as a register permutation; in the complex64
+  // kernel that dispatch costs more (register allocation of every gate body) than the
+  // dense 4x4 it replaces
+  for (const BuiltPass& bp : bps) emit_pass<R>(bp, pops, n, m, L, SB, hp, /*swap_ops=*/sizeof(R) == 8);
   g_last_pass_count = int(hp.passes.size());
   // upload stages, ops, tables and matrices into the state's scratch (stream ordered)
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
@@ -836,19 +727,21 @@ static qc_status run_tiles(qc_state* s, const std::vector<ResolvedOp>& rops, int
     plan_max = std::max(plan_max, P.nstages * sizeof(TileStage) + P.nops * sizeof(TileOp) + P.nmat * sizeof(R));
   const size_t smem = 2 * sizeof(Cplx<R>) * (size_t(1) << m) + sizeof(uint64_t) * (size_t(1) << (m - L)) + plan_max;
   constexpr int NT = TileShape<R>::NT;
-  if (qc_status st = check_cuda(
-          cudaFuncSetAttribute(k_tile_pass<R, NT, SB>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
-          "tile pass shared memory"))
+  bool signops = false;
+  for (const TileOp& op : hp.ops) signops |= op.type == TOP_CZSET;
+  auto kern = signops ? k_tile_pass<R, NT, SB, true> : k_tile_pass<R, NT, SB, false>;
+  if (qc_status st = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
+                                "tile pass shared memory"))
     return st;
   const uint64_t ntiles = uint64_t(1) << (n - m);
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_pass<R, NT, SB>, threads, smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem);
   if (per_sm < 1) per_sm = 1;
   const uint64_t cap = uint64_t(device_sm_count()) * per_sm;
   const unsigned grid = unsigned(ntiles < cap ? ntiles : cap);
   R* a = reinterpret_cast<R*>(s->amps);
   for (const TilePass& P : hp.passes) {
-    QC_COUNT(), k_tile_pass<R, NT, SB><<<grid, threads, smem, s->stream>>>(a, P, dst, dop, dpool, dmats);
+    QC_COUNT(), kern<<<grid, threads, smem, s->stream>>>(a, P, dst, dop, dpool, dmats);
   }
   return check_launch("tile pass");
 }
@@ -876,7 +769,7 @@ static void plan_stats(int n, const std::vector<ResolvedOp>& rops, int m, int* p
   to_plan_ops(rops, pops);
   std::vector<BuiltPass> bps = build_passes(pops, n, m, L);
   HostPlan<R> hp;
-  for (const BuiltPass& bp : bps) emit_pass<R>(bp, pops, n, m, L, SB, hp);
+  for (const BuiltPass& bp : bps) emit_pass<R>(bp, pops, n, m, L, SB, hp, /*swap_ops=*/sizeof(R) == 8);
   *passes = int(hp.passes.size());
   *stages = int(hp.stages.size());
   *ops = int(hp.ops.size());

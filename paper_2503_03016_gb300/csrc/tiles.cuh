@@ -1,0 +1,391 @@
+// Shared-memory tile passes: the device plan records, the device helpers that apply a
+// pass's gates to a register stage, and the host planner's interface.  Used by the
+// circuit passes (planner.cu) and the fused adjoint sweep (adjoint_tiles.cu).
+#pragma once
+
+#include <complex>
+#include <utility>
+#include <vector>
+
+#include "circuit.cuh"
+#include "common.cuh"
+
+namespace qcgb {
+
+constexpr int kMaxStageBits = 5;  // amplitudes a thread holds per stage: 2^SB, SB <= 5
+
+enum TileOpType : int32_t { TOP_DENSE1 = 0, TOP_DENSE2 = 1, TOP_PHASE = 2, TOP_SWAP = 3, TOP_CZSET = 4 };
+
+struct TileOp {
+  int8_t type;
+  int8_t gen;            // adjoint sweep: generator of the recorded rotation (0 X, 1 Y, 2 Z)
+  int8_t zloc, zglob;    // Z rotation: local bit of its qubit (-1: outside the tile), global bit
+  int32_t s0, s1;        // stage slots of the targets (DENSE2: s0 = first qubit = row MSB)
+  uint32_t lmask, lval;  // condition on the thread's non-slot local (in-tile) index bits
+  uint32_t jmask;        // bit j: slot combination j meets the condition on the slot bits
+  uint64_t gmask, gval;  // condition on the index bits outside the tile
+  int64_t mat;           // DENSE: matrix / PHASE: 2^SB-entry slot table, offset (R values)
+                         // in the pass's matrix block
+  int64_t tab;           // PHASE: offset (complex entries) of its other tables in the pool
+  int32_t grad;          // adjoint sweep: rotation whose gradient is recorded before the op, or -1
+  int32_t gslot;         // ... its slot among the pass's recorded rotations
+};
+static_assert(sizeof(TileOp) == 64, "TileOp must be 64 bytes");
+
+struct TileStage {
+  int32_t op0, nops;
+  int8_t slot_bit[8];   // local bit of each slot (SB used)
+  int8_t lane_bit[16];  // local bit receiving bit k of the thread index (the m-SB non-slot
+                        // bits; the first ones cover distinct bit positions mod 4 so that
+                        // a half warp's shared-memory accesses fall in distinct banks)
+};
+static_assert(sizeof(TileStage) == 32, "TileStage must be 32 bytes");
+
+struct TilePass {
+  int32_t m, L;
+  int32_t stage0, nstages;
+  int32_t op0, nops;    // the pass's ops (staged in shared memory)
+  int32_t mat0, nmat;   // the pass's dense matrices and phase slot tables (R values)
+  int8_t bits[16];   // B ascending (global bit positions); bits[0..L) = 0..L-1
+  int32_t c0, c1;    // local phase-table chunks: local bits [0,c0) and [c0,m)
+  int32_t cg;        // tile-index phase-table chunk width (3 chunks)
+  uint64_t ntiles;
+  int32_t ngrad;     // adjoint sweep: rotations recorded in this pass
+};
+
+// ---------------------------------------------------------------------------
+// device side
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t tile_swz(uint32_t r) {
+  uint32_t x = r >> 4;
+  return r ^ ((x ^ (x >> 4) ^ (x >> 8)) & 15u);
+}
+
+// swizzled address offset of slot combination j: XOR of the swizzled slot masks
+// (the swizzle is linear over XOR, but swizzled masks may share bits)
+template <int SB>
+__device__ __forceinline__ uint32_t slot_xor(int j, const uint32_t (&sw)[SB]) {
+  uint32_t o = 0;
+#pragma unroll
+  for (int k = 0; k < SB; ++k)
+    if ((j >> k) & 1) o ^= sw[k];
+  return o;
+}
+
+// NV values of a 16-byte-aligned shared-memory matrix into registers
+template <typename R, int NV>
+__device__ __forceinline__ void load_mat(R (&um)[NV], const R* __restrict__ u) {
+  if (sizeof(R) == 4) {
+    const float4* q = reinterpret_cast<const float4*>(u);
+#pragma unroll
+    for (int i = 0; i < NV / 4; ++i) {
+      const float4 t = q[i];
+      um[4 * i] = R(t.x); um[4 * i + 1] = R(t.y); um[4 * i + 2] = R(t.z); um[4 * i + 3] = R(t.w);
+    }
+  } else {
+    const double2* q = reinterpret_cast<const double2*>(u);
+#pragma unroll
+    for (int i = 0; i < NV / 2; ++i) {
+      const double2 t = q[i];
+      um[2 * i] = R(t.x); um[2 * i + 1] = R(t.y);
+    }
+  }
+}
+
+// Complex64 gates on packed pairs.  For complex64 the planner stores each matrix entry
+// u = (ur, ui) as the two pairs (ur, ur) and (-ui, ui), so that u x is
+// (ur, ur) * (xr, xi) + (-ui, ui) * (xi, xr): two paired FMAs (one instruction each on
+// sm_100 and later) in place of four scalar ones.
+
+template <int NE>
+__device__ __forceinline__ void load_packed(float2 (&a)[NE], float2 (&b)[NE], const float* __restrict__ u) {
+  const float4* q = reinterpret_cast<const float4*>(u);
+#pragma unroll
+  for (int e = 0; e < NE; ++e) {
+    const float4 t = q[e];
+    a[e] = make_float2(t.x, t.y);
+    b[e] = make_float2(t.z, t.w);
+  }
+}
+
+// jmask bit j: the pair (j, j | 2^S0) meets the gate's condition (controls in the slots)
+template <typename R, int SB, int S0>
+__device__ __forceinline__ void dense1(Cplx<R> (&v)[1 << SB], const R* __restrict__ u, uint32_t jmask) {
+  if constexpr (sizeof(R) == 4) {
+    float2 a[4], b[4];
+    load_packed<4>(a, b, u);
+#pragma unroll
+    for (int j = 0; j < (1 << SB); ++j) {
+      if (j & (1 << S0)) continue;
+      const int j1 = j | (1 << S0);
+      if (!((jmask >> j) & 1u)) continue;
+      const float2 x = f2(v[j]), xs = f2swap(v[j]), y = f2(v[j1]), ys = f2swap(v[j1]);
+      v[j] = c2(__ffma2_rn(b[1], ys, __ffma2_rn(a[1], y, __ffma2_rn(b[0], xs, __fmul2_rn(a[0], x)))));
+      v[j1] = c2(__ffma2_rn(b[3], ys, __ffma2_rn(a[3], y, __ffma2_rn(b[2], xs, __fmul2_rn(a[2], x)))));
+    }
+  } else {
+    R um[8];
+    load_mat<R, 8>(um, u);
+    const Cplx<R> u00{um[0], um[1]}, u01{um[2], um[3]}, u10{um[4], um[5]}, u11{um[6], um[7]};
+#pragma unroll
+    for (int j = 0; j < (1 << SB); ++j) {
+      if (j & (1 << S0)) continue;
+      const int j1 = j | (1 << S0);
+      if (!((jmask >> j) & 1u)) continue;
+      const Cplx<R> x = v[j], y = v[j1];
+      v[j] = cmul2(u00, x, u01, y);
+      v[j1] = cmul2(u10, x, u11, y);
+    }
+  }
+}
+
+template <typename R, int SB, int S0, int S1>
+__device__ __forceinline__ void dense2(Cplx<R> (&v)[1 << SB], const R* __restrict__ us) {
+  if constexpr (sizeof(R) == 4) {
+    float2 a[16], b[16];
+    load_packed<16>(a, b, us);
+    // the four output rows are independent chains: step them together so that each
+    // packed FMA's result is not needed by the next instruction
+#pragma unroll
+    for (int j = 0; j < (1 << SB); ++j) {
+      if (j & ((1 << S0) | (1 << S1))) continue;
+      const int i[4] = {j, j | (1 << S1), j | (1 << S0), j | (1 << S0) | (1 << S1)};
+      float2 x[4], xs[4], o[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        x[c] = f2(v[i[c]]);
+        xs[c] = f2swap(v[i[c]]);
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) o[r] = __fmul2_rn(a[4 * r], x[0]);
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        if (c > 0) {
+#pragma unroll
+          for (int r = 0; r < 4; ++r) o[r] = __ffma2_rn(a[4 * r + c], x[c], o[r]);
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) o[r] = __ffma2_rn(b[4 * r + c], xs[c], o[r]);
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) v[i[r]] = c2(o[r]);
+    }
+    return;
+  }
+  R u[32];
+  load_mat<R, 32>(u, us);
+#pragma unroll
+  for (int j = 0; j < (1 << SB); ++j) {
+    if (j & ((1 << S0) | (1 << S1))) continue;
+    const int i0 = j, i1 = j | (1 << S1), i2 = j | (1 << S0), i3 = j | (1 << S0) | (1 << S1);
+    const Cplx<R> x0 = v[i0], x1 = v[i1], x2 = v[i2], x3 = v[i3];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const R* ur = u + 8 * r;
+      Cplx<R> o;
+      o.re = fma(ur[0], x0.re, fma(-ur[1], x0.im, fma(ur[2], x1.re, fma(-ur[3], x1.im,
+             fma(ur[4], x2.re, fma(-ur[5], x2.im, fma(ur[6], x3.re, -ur[7] * x3.im)))))));
+      o.im = fma(ur[0], x0.im, fma(ur[1], x0.re, fma(ur[2], x1.im, fma(ur[3], x1.re,
+             fma(ur[4], x2.im, fma(ur[5], x2.re, fma(ur[6], x3.im, ur[7] * x3.re)))))));
+      if (r == 0) v[i0] = o;
+      else if (r == 1) v[i1] = o;
+      else if (r == 2) v[i2] = o;
+      else v[i3] = o;
+    }
+  }
+}
+
+template <typename R, int SB>
+__device__ __forceinline__ void apply_dense1(int s0, Cplx<R> (&v)[1 << SB], const R* u, uint32_t jmask) {
+  // slots s0 >= SB do not exist for this stage width (the planner never emits them)
+  switch (s0) {
+    case 0: dense1<R, SB, 0>(v, u, jmask); break;
+    case 1: dense1<R, SB, 1>(v, u, jmask); break;
+    case 2: dense1<R, SB, 2>(v, u, jmask); break;
+    case 3:
+      if constexpr (SB > 3) dense1<R, SB, 3>(v, u, jmask);
+      break;
+    default:
+      if constexpr (SB > 4) dense1<R, SB, 4>(v, u, jmask);
+      break;
+  }
+}
+
+#define QC_D2(A, B) \
+  case (A) * 8 + (B): dense2<R, SB, A, B>(v, u); return;
+template <typename R, int SB>
+__device__ __forceinline__ void apply_dense2(int s0, int s1, Cplx<R> (&v)[1 << SB], const R* u) {
+  switch (s0 * 8 + s1) {
+    // the planner orders every two-qubit gate so that s0 < s1
+    QC_D2(0, 1) QC_D2(0, 2) QC_D2(1, 2)
+    default: break;
+  }
+  if constexpr (SB > 3) {
+    switch (s0 * 8 + s1) {
+      QC_D2(0, 3) QC_D2(1, 3) QC_D2(2, 3)
+      default: break;
+    }
+  }
+  if constexpr (SB > 4) {
+    switch (s0 * 8 + s1) {
+      QC_D2(0, 4) QC_D2(1, 4) QC_D2(2, 4) QC_D2(3, 4)
+      default: break;
+    }
+  }
+}
+#undef QC_D2
+
+// SWAP of slots S0 < S1: a permutation of the thread's registers, no arithmetic
+template <typename R, int SB, int S0, int S1>
+__device__ __forceinline__ void swap2(Cplx<R> (&v)[1 << SB]) {
+#pragma unroll
+  for (int j = 0; j < (1 << SB); ++j) {
+    if (j & ((1 << S0) | (1 << S1))) continue;
+    const Cplx<R> t = v[j | (1 << S0)];
+    v[j | (1 << S0)] = v[j | (1 << S1)];
+    v[j | (1 << S1)] = t;
+  }
+}
+
+#define QC_SW(A, B) \
+  case (A) * 8 + (B): swap2<R, SB, A, B>(v); return;
+template <typename R, int SB>
+__device__ __forceinline__ void apply_swap(int s0, int s1, Cplx<R> (&v)[1 << SB]) {
+  switch (s0 * 8 + s1) {
+    QC_SW(0, 1) QC_SW(0, 2) QC_SW(1, 2)
+    default: break;
+  }
+  if constexpr (SB > 3) {
+    switch (s0 * 8 + s1) {
+      QC_SW(0, 3) QC_SW(1, 3) QC_SW(2, 3)
+      default: break;
+    }
+  }
+  if constexpr (SB > 4) {
+    switch (s0 * 8 + s1) {
+      QC_SW(0, 4) QC_SW(1, 4) QC_SW(2, 4) QC_SW(3, 4)
+      default: break;
+    }
+  }
+}
+#undef QC_SW
+
+// Slot combinations j (of 2^SB) whose bit k is set, as a 32-bit mask.
+__device__ __forceinline__ uint32_t slot_set_mask(uint32_t k) {
+  switch (k) {
+    case 0: return 0xAAAAAAAAu;
+    case 1: return 0xCCCCCCCCu;
+    case 2: return 0xF0F0F0F0u;
+    case 3: return 0xFF00FF00u;
+    default: return 0xFFFF0000u;
+  }
+}
+
+// A set of CZ gates as one sign op: bit j of the result is the parity of
+// sum over pairs (a, b) of b_a b_b for slot combination j of this thread.  Each pair is a
+// 32-bit code word (stored in the matrix block, one R slot per pair): byte 0 end a,
+// byte 1 end b, each 0x80 | slot, a lane bit (< 16) or 0x40 | global bit.
+// (kept out of line: inlined, it changes the register allocation of the gate bodies)
+template <typename R, int SB>
+__device__ __noinline__ uint32_t czset_flips(const R* words, int npairs, uint32_t r0, uint64_t base) {
+  uint32_t flip = 0, fixed = 0;
+  for (int e = 0; e < npairs; ++e) {
+    uint32_t code;
+    memcpy(&code, words + e, sizeof(code));
+    uint32_t m[2], f[2];
+    bool slot[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const uint32_t c = (code >> (8 * h)) & 0xFFu;
+      slot[h] = (c & 0x80u) != 0;
+      m[h] = slot[h] ? slot_set_mask(c & 7u) : 0u;
+      f[h] = slot[h] ? 0u : (c & 0x40u) ? uint32_t(base >> (c & 63u)) & 1u : (r0 >> c) & 1u;
+    }
+    if (slot[0] && slot[1])
+      flip ^= m[0] & m[1];
+    else if (slot[0])
+      flip ^= f[1] ? m[0] : 0u;
+    else if (slot[1])
+      flip ^= f[0] ? m[1] : 0u;
+    else
+      fixed ^= f[0] & f[1];
+  }
+  return fixed ? ~flip : flip;
+}
+
+// Asynchronous global -> shared copy of one amplitude (8 or 16 bytes).
+template <typename R>
+__device__ __forceinline__ void cp_async_amp(Cplx<R>* dst, const R* src) {
+  const uint32_t d = uint32_t(__cvta_generic_to_shared(dst));
+  if (sizeof(R) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+template <typename R>
+__device__ __forceinline__ void prefetch_tile(Cplx<R>* buf, const R* amps, uint64_t base, const uint64_t* hioff,
+                                              int L, uint32_t T) {
+  const uint32_t lowmask = (1u << L) - 1;
+  for (uint32_t r = threadIdx.x; r < T; r += blockDim.x) {
+    const uint64_t gi = base | hioff[r >> L] | (r & lowmask);
+    cp_async_amp<R>(buf + tile_swz(r), amps + 2 * gi);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host planner interface (planner.cu)
+// ---------------------------------------------------------------------------
+struct PlanOp {
+  // dense: 1 or 2 target bits, matrix, control mask/values (global bits)
+  // phase: condition mask/values (global), constant angle and per-bit coefficients
+  // grad/gen: adjoint sweep only -- the rotation (and its generator) whose gradient
+  // Im <lambda|G|psi> is recorded just before this op is applied
+  bool phase;
+  int nt;
+  int tb[2];
+  double m[32];
+  uint64_t cmask, cval;
+  double c;
+  std::vector<std::pair<int, double>> beta;  // (bit, coefficient)
+  uint64_t touched;                          // every bit the op reads or writes
+  int grad = -1, gen = -1;
+};
+
+constexpr int kMaxPassOps = 128;  // bounds the plan staged in shared memory per pass
+
+struct BuiltPass {
+  std::vector<int> B;       // ascending
+  std::vector<int> ops;     // indices into plan ops, in order
+};
+
+// Device plan assembled on the host.
+template <typename R>
+struct HostPlan {
+  std::vector<TilePass> passes;
+  std::vector<TileStage> stages;
+  std::vector<TileOp> ops;
+  std::vector<R> pool;  // phase tables read per thread (global memory)
+  std::vector<R> mats;  // per-pass matrices and slot tables (staged in shared memory)
+};
+
+// tile passes of the most recent fused circuit run or fused adjoint reverse sweep
+extern int g_last_pass_count;
+
+// resolved gates -> plan ops (diagonal gates become phase ops); with `grad`/`gen`, op i
+// carries the tag grad[i] (>= 0: a rotation exp(-i t G/2) with generator gen[i]; X and Y
+// rotations stay dense, Z rotations become phase ops)
+void to_plan_ops(const std::vector<ResolvedOp>& in, std::vector<PlanOp>& out, const std::vector<int>* grad = nullptr,
+                 const std::vector<int>* gen = nullptr);
+// plan ops -> passes of tile bit sets B (m bits, the L lowest always included)
+std::vector<BuiltPass> build_passes(const std::vector<PlanOp>& ops, int n, int m, int L);
+// one pass -> its register stages, tile ops and matrices (sb: stage width); with
+// swap_ops, an exact SWAP becomes a register permutation (TOP_SWAP) instead of a dense
+// 4x4 (kernels that hold two states per thread keep the dense form: fewer registers)
+template <typename R>
+void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int m, int L, int sb,
+               HostPlan<R>& hp, bool swap_ops = true);
+
+}  // namespace qcgb

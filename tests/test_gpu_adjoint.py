@@ -56,6 +56,53 @@ def test_adjoint_mixed_generators_and_shared_parameters():
     np.testing.assert_allclose(g, oracle.param_shift_grad(n, ops, params, terms, coeffs), atol=1e-12)
 
 
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-11), ("c64", 2e-5)])
+def test_fused_sweep_vs_parameter_shift(dtype, tol):
+    """Registers of 12 qubits and more take the fused reverse sweep (tile passes over
+    psi and lambda together): 13 qubits, 2 layers, ring ZZ + sum X."""
+    import paper_2503_03016_gb300 as P
+    n, layers = 13, 2
+    ops, params, terms, coeffs = W.adjoint_workload(n, layers, 6)
+    circ = P.Circuit(n, ops)
+    e, g = P.qc_adjoint_grad(circ, params, terms, coeffs, P.QC_C128 if dtype == "c128" else P.QC_C64)
+    e_ref = oracle.energy(n, ops, params, terms, coeffs)
+    g_ref = oracle.param_shift_grad(n, ops, params, terms, coeffs)
+    scale = np.abs(g_ref).max() + 1
+    assert abs(e - e_ref) <= tol * scale
+    np.testing.assert_allclose(g, g_ref, atol=tol * scale, rtol=0)
+    # fixed-order sums: a second call gives the same bits
+    e2, g2 = P.qc_adjoint_grad(circ, params, terms, coeffs, P.QC_C128 if dtype == "c128" else P.QC_C64)
+    assert e2 == e
+    np.testing.assert_array_equal(g2, g)
+
+
+def test_fused_sweep_mixed_gates():
+    """The fused sweep with RX/RY/RZ on every kind of bit position (low bits, tile bits,
+    bits left to the tile number), shared parameters, dense two-qubit gates, controlled
+    and diagonal gates between the rotations, and X/Y/Z Hamiltonian strings."""
+    import paper_2503_03016_gb300 as P
+    from workloads import Op
+    n = 14
+    rng = np.random.default_rng(8)
+    U = W.haar_unitaries(2, 4, 9)
+    ops = []
+    k = 0
+    for layer in range(2):
+        for q in range(n):
+            kind = ("rx", "ry", "rz")[(q + layer) % 3]
+            ops.append(Op(kind, (q,), param_index=k % 20))  # parameters shared between gates
+            k += 1
+        ops += [Op("cnot", (0, 13)), Op("u2q", (3, 11), matrix=U[layer]), Op("cp", (5, 12), (0.7,)),
+                Op("swap", (2, 9)), Op("h", (7,)), Op("mcx", (1, 6, 10), ctrl_states=(1, 0)), Op("cz", (4, 8))]
+    params = rng.uniform(0, 2 * np.pi, 20)
+    terms = ["X" + "I" * 12 + "Z", "I" * 5 + "YY" + "I" * 7, "Z" * n, "I" * 12 + "XY", "IZIXIIIIIIYIII"]
+    coeffs = np.array([0.8, -0.4, 0.3, 1.1, -0.6])
+    circ = P.Circuit(n, ops)
+    e, g = P.qc_adjoint_grad(circ, params, terms, coeffs, P.QC_C128)
+    assert abs(e - oracle.energy(n, ops, params, terms, coeffs)) < 1e-11
+    np.testing.assert_allclose(g, oracle.param_shift_grad(n, ops, params, terms, coeffs), atol=1e-11)
+
+
 def test_autograd_function():
     import torch
 

@@ -98,6 +98,34 @@ def test_fused_ansatz_and_ladder(dtype):
     assert rel_l2(got, want) <= TOL[dtype]
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n", [12, 17])
+def test_fused_cz_runs(dtype, n):
+    """Runs of CZ gates (merged into sign ops) between dense layers: pairs between any
+    two bit positions (register slots, lane bits, bits fixed by the tile number), the
+    same pair twice, and interleaved gates that must not join a run (a CZ with an open
+    control, a controlled phase other than pi, a diagonal two-qubit gate with the CZ's
+    phases but a global phase)."""
+    rng = np.random.default_rng(n)
+    U = W.haar_unitaries(8, 4, 31)
+    ops = []
+    for layer in range(4):
+        for q in range(0, n - 1, 2):
+            ops.append(Op("u2q", (q, q + 1), matrix=U[(layer + q) % 8]))
+        for _ in range(3 * n):
+            a, b = (int(x) for x in rng.permutation(n)[:2])
+            ops.append(Op("cz", (a, b)))
+        ops.append(Op("cz", (ops[-1].qubits[0], ops[-1].qubits[1])))  # the same pair again
+        a, b = (int(x) for x in rng.permutation(n)[:2])
+        ops.append(Op("ctrl", (a, b), matrix=np.diag([1.0, -1.0]), ctrl_states=(0,)))
+        ops.append(Op("cz", (b, a)))
+        ops.append(Op("cp", (a, b), (3.0,)))
+        ops.append(Op("u2q", (b, a), matrix=np.diag([1j, 1j, 1j, -1j])))
+        ops.append(Op("cz", (a, (a + 1) % n)))
+    got, want, _ = run_both(n, ops, dtype)
+    assert rel_l2(got, want) <= TOL[dtype] * 10
+
+
 def test_fused_small_n_uses_per_gate():
     ops = W.brickwork(6, 4, 1)
     got, want, _ = run_both(6, ops, "c128")
