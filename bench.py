@@ -224,7 +224,9 @@ def run_ours(args):
         P.qc_state_init_basis(st.handle, 0)
         P.qc_run_circuit(st.handle, circ, None, mode, prec)
         P.qc_probs(st.handle, probs)
-        P.qc_sample(st.handle, u_dev, SHOTS, out_dev)
+        # shots drawn from the FP64 probabilities just computed (the same values the
+        # sampler would form from the amplitudes, so the same outcomes)
+        P.qc_sample_probs(st.handle, probs, N_QUBITS, u_dev, SHOTS, out_dev)
         ev = P.qc_expect_pauli(st.handle, zz)  # synchronising: returns host values
         if e2e:
             out_host.copy_(out_dev, non_blocking=True)
@@ -348,6 +350,13 @@ def run_batch_bench(args):
     torch.cuda.set_device(0)
     layers = 8
     ns, params = W.batch_workload(4096, layers, 12, 20, 4)
+    subset = ""
+    if args.batch_range:
+        # profiling only: the circuits of the workload whose qubit counts lie in LO..HI
+        lo, hi = (int(x) for x in args.batch_range.split("-"))
+        keep = [i for i, n in enumerate(ns) if lo <= n <= hi][:args.batch_count or None]
+        ns, params = [ns[i] for i in keep], [params[i] for i in keep]
+        subset = " (subset: %d circuits with %d..%d qubits)" % (len(ns), lo, hi)
     offs = np.cumsum([0] + [p.size for p in params[:-1]]).astype(np.int64)
     flat = np.concatenate(params).astype(np.float32)
     dparams = torch.tensor(flat, device="cuda")
@@ -370,7 +379,8 @@ def run_batch_bench(args):
                       "approx_fp32_tflops": tf,
                       "roofline": {"bound": "alu", "achieved": tf, "peak": ALU_PEAK_TF, "unit": "TFLOP/s",
                                    "frac": tf / ALU_PEAK_TF, "peak_source": ALU_PEAK_SRC},
-                      "config": {"workload": "4096 ansatz circuits, n in 12..20, 8 layers RY.RZ + CZ chain, <ZZ>"}}))
+                      "config": {"workload": "4096 ansatz circuits, n in 12..20, 8 layers RY.RZ + CZ chain, <ZZ>" +
+                                 subset}}))
 
 
 def run_block_bench(args):
@@ -564,6 +574,8 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--cpu-gates", type=int, default=24)
     ap.add_argument("--ref-gates", type=int, default=8)
+    ap.add_argument("--batch-range", default=None, help="batch workload: profile only circuits with LO-HI qubits")
+    ap.add_argument("--batch-count", type=int, default=0, help="batch workload: at most this many of them")
     ap.add_argument("--qubits", type=int, default=None,
                     help="register size (default: 28 brickwork and block, 32 QFT); smaller for profiling")
     ap.add_argument("--workload", default="brickwork",

@@ -144,7 +144,7 @@ __global__ void __launch_bounds__(NT, 1) k_adj_pass(R* __restrict__ psi, R* __re
         w[j] = tl[a];
       }
       for (int q = 0; q < st.nops; ++q) {
-        const TileOp& op = sop[st.op0 + q];
+        const TileOp op = sop[st.op0 + q];  // one copy into registers (the loop writes shared memory)
         if (op.grad >= 0) {
           // recorded rotations carry no condition: every thread takes part
           R share;

@@ -424,8 +424,37 @@ __global__ void __launch_bounds__(256) k_draw(Src src, uint64_t nleaf, int ls, c
     const U128 c0 = add128(add128(leaf_off[leaf], exc), v0);  // cdf of element 2*lane
     const U128 c1 = add128(c0, v1);                           // cdf of element 2*lane+1
     const bool valid0 = 2 * lane < ls, valid1 = 2 * lane + 1 < ls;
-    const bool hit0 = valid0 && pass_test(fixed_to_bits(c0));
-    const bool hit1 = valid1 && pass_test(fixed_to_bits(c1));
+    bool hit0, hit1;
+    if (below) {
+      // RN64(c) > t  <=>  c lies above the midpoint between t and the next double up,
+      // or on it when t's last significand bit is 1 (the tie goes to the even
+      // neighbour): one 128-bit comparison with a threshold formed once per shot
+      const int E = int((tb >> 52) & 0x7FF);
+      const uint64_t mt = (tb & ((1ull << 52) - 1)) | (E ? (1ull << 52) : 0ull);
+      const int e = E ? E : 1;                  // t = mt 2^(e-1075); midpoint (2 mt + 1) 2^(e-1076)
+      const uint64_t odd2 = 2 * mt + 1;         // < 2^54
+      const int sh = e - 958;                   // the midpoint in units of 2^-118: odd2 2^sh
+      U128 M;
+      bool exact;
+      if (sh >= 0) {
+        M.lo = sh >= 64 ? 0 : odd2 << sh;
+        M.hi = sh == 0 ? 0 : sh >= 64 ? odd2 << (sh - 64) : odd2 >> (64 - sh);
+        exact = true;
+      } else {
+        M.lo = -sh >= 64 ? 0 : odd2 >> (-sh);  // the floor; odd2 is odd, so never exact
+        M.hi = 0;
+        exact = false;
+      }
+      const bool tie_up = exact && (mt & 1);
+      auto above = [&](U128 c) {
+        return c.hi > M.hi || (c.hi == M.hi && (c.lo > M.lo || (tie_up && c.lo == M.lo)));
+      };
+      hit0 = valid0 && above(c0);
+      hit1 = valid1 && above(c1);
+    } else {
+      hit0 = valid0 && pass_test(fixed_to_bits(c0));
+      hit1 = valid1 && pass_test(fixed_to_bits(c1));
+    }
     const unsigned bal = __ballot_sync(0xffffffffu, hit0 || hit1);
     const int first = __ffs(bal) - 1;  // leaf_end[leaf] passes, so some lane hits
     if (lane == first) out[s] = leaf * uint64_t(ls) + 2 * lane + (hit0 ? 0 : 1);

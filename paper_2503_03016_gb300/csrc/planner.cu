@@ -100,7 +100,7 @@ __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const
 #pragma unroll
       for (int j = 0; j < NA; ++j) v[j] = tile[p0 ^ slot_xor<SB>(j, sw)];
       for (int q = 0; q < st.nops; ++q) {
-        const TileOp& op = sop[st.op0 + q];
+        const TileOp op = sop[st.op0 + q];  // one copy into registers
         if ((base & op.gmask) != op.gval) continue;  // condition on bits outside the tile
         if ((r0 & op.lmask) != op.lval) continue;    // ... on the thread's lane bits
         if (op.type == TOP_DENSE1) {
