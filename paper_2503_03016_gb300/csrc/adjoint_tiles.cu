@@ -178,6 +178,11 @@ __global__ void __launch_bounds__(NT, 1) k_adj_pass(R* __restrict__ psi, R* __re
         } else if (op.type == TOP_DENSE2) {
           apply_dense2<R, SB>(op.s0, op.s1, v, smat + op.mat);
           apply_dense2<R, SB>(op.s0, op.s1, w, smat + op.mat);
+        } else if (op.type == TOP_PHASE1) {
+          const uint32_t fixed =
+              op.s0 >= 0 ? 0u : op.zloc >= 0 ? (r0 >> op.zloc) & 1u : uint32_t((base >> op.zglob) & 1u);
+          apply_phase1<R, SB>(v, smat + op.mat, op.s0, fixed, op.jmask);
+          apply_phase1<R, SB>(w, smat + op.mat, op.s0, fixed, op.jmask);
         } else if (op.type == TOP_CZSET) {
           const uint32_t flip = czset_flips<R, SB>(smat + op.mat, op.s0, r0, base);
 #pragma unroll

@@ -36,9 +36,10 @@ namespace qcgb {
 
 // One launch = one pass over all tiles; blockDim = 2^(m-SB), one block per SM with
 // two tile buffers: the next tile is fetched (cp.async) while this one is computed.
-// SIGNOPS: the plan contains CZ sign ops (a second instantiation without them keeps the
-// gate bodies' code generation unchanged for plans that have none)
-template <typename R, int NT, int SB, bool SIGNOPS>
+// EXTOPS: the plan contains CZ sign ops or single-bit phase ops (a second instantiation
+// without them keeps the gate bodies' code generation unchanged for plans that have
+// none, e.g. circuits of dense two-qubit gates)
+template <typename R, int NT, int SB, bool EXTOPS>
 __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const TilePass P,
                                                      const TileStage* __restrict__ stages,
                                                      const TileOp* __restrict__ ops, const R* __restrict__ pool,
@@ -109,12 +110,18 @@ __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const
           apply_dense2<R, SB>(op.s0, op.s1, v, smat + op.mat);
         } else if (sizeof(R) == 8 && op.type == TOP_SWAP) {
           if constexpr (sizeof(R) == 8) apply_swap<R, SB>(op.s0, op.s1, v);
-        } else if (SIGNOPS && op.type == TOP_CZSET) {
-          if constexpr (SIGNOPS) {
+        } else if (EXTOPS && op.type == TOP_CZSET) {
+          if constexpr (EXTOPS) {
             const uint32_t flip = czset_flips<R, SB>(smat + op.mat, op.s0, r0, base);
 #pragma unroll
             for (int j = 0; j < NA; ++j)
               if ((flip >> j) & 1u) v[j] = Cplx<R>{-v[j].re, -v[j].im};
+          }
+        } else if (EXTOPS && op.type == TOP_PHASE1) {
+          if constexpr (EXTOPS) {
+            const uint32_t fixed =
+                op.s0 >= 0 ? 0u : op.zloc >= 0 ? (r0 >> op.zloc) & 1u : uint32_t((base >> op.zglob) & 1u);
+            apply_phase1<R, SB>(v, smat + op.mat, op.s0, fixed, op.jmask);
           }
         } else {
           // exp(i (c + sum beta_p b_p)) factorised over: tile-index chunks (3), the
@@ -394,7 +401,7 @@ std::vector<BuiltPass> build_passes(const std::vector<PlanOp>& ops, int n, int m
 
 template <typename R>
 void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int m, int L, int sb,
-               HostPlan<R>& hp, bool swap_ops) {
+               HostPlan<R>& hp, bool swap_ops, bool phase1_ops) {
   TilePass P{};
   P.m = m;
   P.L = L;
@@ -612,6 +619,35 @@ void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int 
           for (auto& be : nx.beta) beta[be.first] += be.second;
           ++q;
         }
+        int nbeta = 0, bbit = -1;
+        for (int b = 0; b < 64; ++b)
+          if (beta[b] != 0.0) {
+            ++nbeta;
+            bbit = b;
+          }
+        if (phase1_ops && nbeta <= 1) {
+          // exp(i (c + beta b)) on at most one bit: the two factors e^{ic}, e^{i(c+beta)}
+          // go into the matrix block; the bit is a register slot (s0), a lane bit (zloc)
+          // or a bit fixed by the tile number (zglob)
+          op.type = TOP_PHASE1;
+          if (bbit < 0) bbit = 0;  // a constant phase: both factors equal
+          op.mat = int64_t(hp.mats.size()) - P.mat0;
+          const cd z0 = std::polar(1.0, c), z1 = std::polar(1.0, c + beta[bbit]);
+          hp.mats.push_back(R(z0.real()));
+          hp.mats.push_back(R(z0.imag()));
+          hp.mats.push_back(R(z1.real()));
+          hp.mats.push_back(R(z1.imag()));
+          const int lb = local_of[bbit];
+          op.s0 = -1;
+          for (int k = 0; k < sb; ++k)
+            if (lb >= 0 && st.slot_bit[k] == lb) op.s0 = k;
+          if (p.grad < 0) {  // a recorded Z rotation already carries its own bit here
+            op.zloc = int8_t(lb);
+            op.zglob = int8_t(bbit);
+          }
+          hp.ops.push_back(op);
+          continue;
+        }
         // tables: [2^sb slot combos][2^c0 low local][2^c1 high local][3 x 2^cg tile index].
         // Entry x of a table over bits g_0..g_{k-1} is exp(i sum_{x_j = 1} beta_{g_j}),
         // built by doubling: entry x = entry(x without its top bit) * exp(i beta_top)
@@ -667,9 +703,9 @@ void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int 
 }
 
 template void emit_pass<float>(const BuiltPass&, const std::vector<PlanOp>&, int, int, int, int, HostPlan<float>&,
-                               bool);
+                               bool, bool);
 template void emit_pass<double>(const BuiltPass&, const std::vector<PlanOp>&, int, int, int, int, HostPlan<double>&,
-                                bool);
+                                bool, bool);
 
 int g_last_pass_count = 0;  // also set by the fused adjoint sweep
 
@@ -727,9 +763,9 @@ static qc_status run_tiles(qc_state* s, const std::vector<ResolvedOp>& rops, int
     plan_max = std::max(plan_max, P.nstages * sizeof(TileStage) + P.nops * sizeof(TileOp) + P.nmat * sizeof(R));
   const size_t smem = 2 * sizeof(Cplx<R>) * (size_t(1) << m) + sizeof(uint64_t) * (size_t(1) << (m - L)) + plan_max;
   constexpr int NT = TileShape<R>::NT;
-  bool signops = false;
-  for (const TileOp& op : hp.ops) signops |= op.type == TOP_CZSET;
-  auto kern = signops ? k_tile_pass<R, NT, SB, true> : k_tile_pass<R, NT, SB, false>;
+  bool extops = false;
+  for (const TileOp& op : hp.ops) extops |= op.type == TOP_CZSET || op.type == TOP_PHASE1;
+  auto kern = extops ? k_tile_pass<R, NT, SB, true> : k_tile_pass<R, NT, SB, false>;
   if (qc_status st = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
                                 "tile pass shared memory"))
     return st;

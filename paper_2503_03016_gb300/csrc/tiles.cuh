@@ -14,7 +14,7 @@ namespace qcgb {
 
 constexpr int kMaxStageBits = 5;  // amplitudes a thread holds per stage: 2^SB, SB <= 5
 
-enum TileOpType : int32_t { TOP_DENSE1 = 0, TOP_DENSE2 = 1, TOP_PHASE = 2, TOP_SWAP = 3, TOP_CZSET = 4 };
+enum TileOpType : int32_t { TOP_DENSE1 = 0, TOP_DENSE2 = 1, TOP_PHASE = 2, TOP_SWAP = 3, TOP_CZSET = 4, TOP_PHASE1 = 5 };
 
 struct TileOp {
   int8_t type;
@@ -270,6 +270,21 @@ __device__ __forceinline__ void apply_swap(int s0, int s1, Cplx<R> (&v)[1 << SB]
 }
 #undef QC_SW
 
+// TOP_PHASE1: multiply by z0 or z1 as the op's bit reads 0 or 1 -- the bit is register
+// slot ks (>= 0), or fixed for the thread (`fixed`)
+template <typename R, int SB>
+__device__ __forceinline__ void apply_phase1(Cplx<R> (&v)[1 << SB], const R* zs, int ks, uint32_t fixed,
+                                             uint32_t jmask) {
+  const Cplx<R> z0{zs[0], zs[1]}, z1{zs[2], zs[3]};
+  const Cplx<R> zf = fixed ? z1 : z0;
+#pragma unroll
+  for (int j = 0; j < (1 << SB); ++j) {
+    if (!((jmask >> j) & 1u)) continue;
+    const Cplx<R> z = ks >= 0 ? (((j >> ks) & 1) ? z1 : z0) : zf;
+    v[j] = cmul(v[j], z);
+  }
+}
+
 // Slot combinations j (of 2^SB) whose bit k is set, as a 32-bit mask.
 __device__ __forceinline__ uint32_t slot_set_mask(uint32_t k) {
   switch (k) {
@@ -383,9 +398,11 @@ void to_plan_ops(const std::vector<ResolvedOp>& in, std::vector<PlanOp>& out, co
 std::vector<BuiltPass> build_passes(const std::vector<PlanOp>& ops, int n, int m, int L);
 // one pass -> its register stages, tile ops and matrices (sb: stage width); with
 // swap_ops, an exact SWAP becomes a register permutation (TOP_SWAP) instead of a dense
-// 4x4 (kernels that hold two states per thread keep the dense form: fewer registers)
+// 4x4 (kernels that hold two states per thread keep the dense form: fewer registers);
+// with phase1_ops, a phase op on at most one bit becomes TOP_PHASE1 (two factors, no
+// per-thread table lookups)
 template <typename R>
 void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int m, int L, int sb,
-               HostPlan<R>& hp, bool swap_ops = true);
+               HostPlan<R>& hp, bool swap_ops = true, bool phase1_ops = true);
 
 }  // namespace qcgb
