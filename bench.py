@@ -33,6 +33,7 @@ import workloads as W  # noqa: E402
 
 METRIC = "circuit time & HBM GB/s (frac of peak) at 28–32 qubits: fused/FP32 vs plain FP64"
 N_QUBITS, DEPTH, SEED, SHOTS, SHOT_SEED = 28, 40, 2, 1_000_000, 102
+WORKLOAD = "brickwork n=28 depth=40 Haar 2q (540 gates, seed 2) + probs + 1e6 shots + <ZZ>"
 # FP32 peak from unit counts at the maximum SM clock
 ALU_PEAK_TF = 152 * 128 * 2 * 2070e6 / 1e12
 ALU_PEAK_SRC = "152 SMs x 128 FP32 lanes x 2 flops x 2070 MHz"
@@ -165,12 +166,14 @@ def run_reference(args):
         return
     ops = W.brickwork(N_QUBITS, DEPTH, SEED)
     rate, sec_per_step, cores = oracle_rate(args.ref_gates, args.steps, args.warmup, ops)
-    sample = "%d of the %d brickwork gates per step on 28 qubits (complex128), extrapolated" % (
-        args.ref_gates, len(ops))
+    sample = ("%d of the %d brickwork gates per step on 28 qubits (complex128), extrapolated to the circuit; "
+              "gates only (the probabilities, shots and <ZZ> would add to the oracle's time)" % (
+                  args.ref_gates, len(ops)))
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": "circuits/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_per_step * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "brickwork n=28 depth=40 Haar 2q (540 gates), 1e6 shots", "n_qubits": N_QUBITS},
+            "config": {"workload": WORKLOAD, "mode": "oracle (plain per-gate loops, complex128)",
+                       "parallelism": "host cores", "n_qubits": N_QUBITS},
             "cpu_baseline": {"value": rate, "unit": "circuits/s", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": rate, "unit": "circuits/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -321,8 +324,8 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
             "data": "synthetic",
-            "config": {"workload": "brickwork n=28 depth=40 Haar 2q (540 gates, seed 2) + probs + 1e6 shots + <ZZ>",
-                       "mode": args.mode, "prec": args.prec, "parallelism": "replicas" if world > 1 else "single",
+            "config": {"workload": WORKLOAD, "mode": args.mode, "prec": args.prec,
+                       "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (2 GiB state)"},
             "circuit_ms": circ_ms,
             "plain_fp64": plain,
