@@ -108,10 +108,21 @@ __global__ void __launch_bounds__(256) k_pauli(const R* __restrict__ a, uint64_t
 // amplitude.  complex64 states accumulate per thread in FP32 (the per-amplitude values
 // are FP32 products already), complex128 in FP64; cross-thread and cross-block sums
 // are FP64 in a fixed order.
+//
+// Signs: there are 2^K virtual threads (K = kbits_base; one resident wave of blocks
+// loops over them) and virtual thread g takes the chunks g + k 2^K, k = 0 ..
+// 2^kbits - 1, so (-1)^popc(chunk*32 & z) splits into a per-thread sign (from g) and a
+// sign from k shared by all threads.  k runs in Gray-code order: the step from the j-th
+// to the (j+1)-th k flips bit ctz(j+1) of k, which toggles the signs of the terms whose
+// z has the matching index bit (flip[b], from the host).
 constexpr int kMaxZTerms = 32;
 constexpr int kZBlock = 128;
+constexpr int kZMaxThreadBits = 20;  // at most 2^20 virtual threads (8192 virtual blocks)
 struct ZGroup {
   int nt;
+  int kbits_base;     // K: log2 of the number of virtual threads
+  int kbits;          // chunks per virtual thread = 2^kbits
+  uint32_t flip[16];  // bit t: term t's z has index bit 5 + K + b
   uint64_t z[kMaxZTerms];
   int slot[kMaxZTerms];
 };
@@ -124,35 +135,48 @@ __global__ void __launch_bounds__(kZBlock) k_pauli_z(const R* __restrict__ amps,
 #pragma unroll
   for (int t = 0; t < kMaxZTerms; ++t) acc[t] = R(0);
   const uint64_t nchunk = N >> 5;
-  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-  for (uint64_t c = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; c < nchunk; c += stride) {
-    const uint64_t base = c << 5;
-    R w[32];
+  // 2^K virtual threads in virtual blocks of kZBlock, spread over the resident grid
+  const uint64_t nvb = uint64_t(1) << (g.kbits_base - 7);
+  for (uint64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+    const uint64_t gt = vb * kZBlock + threadIdx.x;
+    if (gt >= nchunk) continue;
+    // this thread's signs (bit t: term t's sign for chunk gt, i.e. k = 0)
+    uint32_t sign = 0;
 #pragma unroll
-    for (int l = 0; l < 32; l += 2) {
-      Cplx<R> x0, x1;
-      ld_amp2<R>(amps, base + l, x0, x1);
-      w[l] = x0.re * x0.re + x0.im * x0.im;
-      w[l + 1] = x1.re * x1.re + x1.im * x1.im;
-    }
-    // in-place Walsh-Hadamard transform over the 5 chunk bits
+    for (int t = 0; t < kMaxZTerms; ++t)
+      if (t < g.nt) sign |= uint32_t(__popcll((gt << 5) & g.z[t]) & 1) << t;
+    const uint64_t nk = uint64_t(1) << g.kbits;
+    for (uint64_t j = 0; j < nk; ++j) {
+      const uint64_t k = j ^ (j >> 1);  // Gray code
+      const uint64_t base = (gt + (k << g.kbits_base)) << 5;
+      R w[32];
 #pragma unroll
-    for (int h = 1; h < 32; h <<= 1)
+      for (int l = 0; l < 32; l += 2) {
+        Cplx<R> x0, x1;
+        ld_amp2<R>(amps, base + l, x0, x1);
+        w[l] = x0.re * x0.re + x0.im * x0.im;
+        w[l + 1] = x1.re * x1.re + x1.im * x1.im;
+      }
+      // in-place Walsh-Hadamard transform over the 5 chunk bits
 #pragma unroll
-      for (int l = 0; l < 32; ++l)
-        if (!(l & h)) {
-          const R a = w[l], b = w[l | h];
-          w[l] = a + b;
-          w[l | h] = a - b;
-        }
+      for (int h = 1; h < 32; h <<= 1)
 #pragma unroll
-    for (int l = 0; l < 32; ++l) S[l][threadIdx.x] = w[l];
-    // S is private to this thread's column: no barrier needed
+        for (int l = 0; l < 32; ++l)
+          if (!(l & h)) {
+            const R a = w[l], b = w[l | h];
+            w[l] = a + b;
+            w[l | h] = a - b;
+          }
 #pragma unroll
-    for (int t = 0; t < kMaxZTerms; ++t) {
-      if (t >= g.nt) break;
-      const R v = S[g.z[t] & 31][threadIdx.x];
-      acc[t] += (__popcll(base & g.z[t]) & 1) ? -v : v;
+      for (int l = 0; l < 32; ++l) S[l][threadIdx.x] = w[l];
+      // S is private to this thread's column: no barrier needed
+#pragma unroll
+      for (int t = 0; t < kMaxZTerms; ++t) {
+        if (t >= g.nt) break;
+        const R v = S[g.z[t] & 31][threadIdx.x];
+        acc[t] += ((sign >> t) & 1u) ? -v : v;
+      }
+      if (j + 1 < nk) sign ^= g.flip[__ffsll((long long)(j + 1)) - 1];
     }
   }
 #pragma unroll
@@ -217,19 +241,36 @@ qc_status expect_terms_device(qc_state* s, const ParsedTerm* terms, int nterms, 
   for (int t = 0; t < nterms; ++t) groups[terms[t].x].push_back(t);
   const int B = 256;
   const unsigned g = stream_grid(N, B, 8);
+  // block partials: the X/Y-string kernels use g blocks, the Z-string kernel at most
+  // one resident wave (below 32 blocks per SM)
+  const size_t nblk = std::max<size_t>(g, size_t(32) * device_sm_count());
   void* scr = nullptr;
-  if (qc_status st = state_scratch(s, sizeof(double) * size_t(g) * kMaxZTerms + 256, &scr)) return st;
+  if (qc_status st = state_scratch(s, sizeof(double) * nblk * kMaxZTerms + 256, &scr)) return st;
   double* part = reinterpret_cast<double*>(scr);
   for (auto& kv : groups) {
     const std::vector<int>& idx = kv.second;
     if (kv.first == 0 && N >= 64) {  // Z-only strings
-      const unsigned gz = stream_grid(N >> 5, kZBlock, 8);
+      // 2^K virtual threads (at least one block), each taking 2^kbits chunks of 32
+      // amplitudes; the launch is one resident wave of blocks looping over them
+      const int cbits = s->n - 5;  // log2 of the chunk count
+      const int K = std::max(7, std::min(cbits, kZMaxThreadBits));
+      int per_sm = 0;
+      if (s->dtype == QC_C64)
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pauli_z<float>, kZBlock, 0);
+      else
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pauli_z<double>, kZBlock, 0);
+      per_sm = std::min(std::max(per_sm, 1), 32);
+      const unsigned gz = unsigned(std::min<uint64_t>(uint64_t(1) << (K - 7), uint64_t(per_sm) * device_sm_count()));
       for (size_t beg = 0; beg < idx.size(); beg += kMaxZTerms) {
         ZGroup zg{};
         zg.nt = int(std::min<size_t>(kMaxZTerms, idx.size() - beg));
+        zg.kbits_base = K;
+        zg.kbits = std::max(0, cbits - K);
         for (int j = 0; j < zg.nt; ++j) {
           zg.z[j] = terms[idx[beg + j]].z;
           zg.slot[j] = idx[beg + j];
+          for (int b = 0; b < zg.kbits; ++b)
+            if ((zg.z[j] >> (5 + K + b)) & 1) zg.flip[b] |= 1u << j;
         }
         if (s->dtype == QC_C64)
           QC_COUNT(), k_pauli_z<float><<<gz, kZBlock, 0, s->stream>>>(reinterpret_cast<const float*>(s->amps), N, zg, part);

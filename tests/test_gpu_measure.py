@@ -181,6 +181,26 @@ def test_pauli_expectations(dtype, n):
     np.testing.assert_allclose(got, want, atol=tol * (1 + np.abs(coeffs).max()))
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_z_strings_24_qubits(dtype):
+    """24 qubits (the Z-string kernel then gives each thread several chunks of 32
+    amplitudes): strings on the highest index bits (qubits 0 and 1), on the chunk's own
+    bits (< 5) and in between, plus the full ZZ ring, against the oracle."""
+    n = 24
+    psi = W.gaussian_state(n, 17)
+    strings = W.zz_terms(n, ring=True)
+    for qs in ((0,), (1,), (0, 1), (0, 23), (1, 20, 23), (2, 19), (0, 1, 2, 3, 21, 22, 23)):
+        s = ["I"] * n
+        for q in qs:
+            s[q] = "Z"
+        strings.append("".join(s))
+    st = gpu_state(psi, dtype)
+    got = st.expect(strings)
+    want = oracle.expect_pauli(st.numpy().astype(np.complex128), strings)  # the stored amplitudes
+    tol = 1e-12 if dtype == "c128" else 2e-6
+    np.testing.assert_allclose(got, want, atol=tol)
+
+
 def test_tomography_values_on_gpu():
     """Sec. 5.2: <X> = 0, <Y> = 1, <Z> = 0 for v = (1, i)/sqrt(2)."""
     st = gpu_state(np.array([1, 1j]) / np.sqrt(2), "c128")
