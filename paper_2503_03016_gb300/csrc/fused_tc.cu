@@ -132,24 +132,28 @@ __global__ void __launch_bounds__(kTcRows, 1) k_block_tc(float* __restrict__ amp
   uint32_t phase = 0;
   bool failed = false;
 
-  // software pipeline: the rows of tile t+grid are gathered into registers while the
-  // tensor cores work on tile t
-  float2 x[32];
-  uint64_t rb = 0;
-  if (uint64_t(blockIdx.x) < ntiles) {
-    rb = insert_zero_bits(uint64_t(blockIdx.x) * kTcRows + tid, spos, kTcK);
+  // software pipeline, two tiles deep: a thread's rows of tile t live in one of two
+  // register buffers; right after they are split into shared memory that buffer is
+  // refilled with tile t + 2 grid, so the gathers of the next two tiles are in flight
+  // while the tensor cores and the epilogue work on tile t
+  const uint64_t G = gridDim.x;
+  auto gather = [&](float2 (&x)[32], uint64_t& rb, uint64_t t) {
+    rb = insert_zero_bits(t * kTcRows + tid, spos, kTcK);
 #pragma unroll
     for (int c = 0; c < 32; ++c) x[c] = reinterpret_cast<const float2*>(amps)[rb | offs[c]];
-  }
-  for (uint64_t t = blockIdx.x; t < ntiles && !failed; t += gridDim.x) {
-    // split this thread's row (already in registers) into hi / lo
+  };
+  auto step = [&](float2 (&x)[32], uint64_t& rb, uint64_t t) {
+    // split this thread's row (in registers) into hi / lo; amplitudes 2c and 2c+1 fill
+    // one 16-byte chunk of the swizzled layout, written with one 16-byte store (a warp's
+    // stores then take the minimum number of shared-memory wavefronts)
+    auto hi = [](float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); };
 #pragma unroll
-    for (int c = 0; c < 32; ++c) {
-      const float re_hi = __uint_as_float(__float_as_uint(x[c].x) & 0xFFFFE000u);
-      const float im_hi = __uint_as_float(__float_as_uint(x[c].y) & 0xFFFFE000u);
-      const uint32_t o = sw128_offset(tid, 2 * c, kTcRows);  // 8-byte pair stays in one chunk
-      *reinterpret_cast<float2*>(a_hi + o) = make_float2(re_hi, im_hi);
-      *reinterpret_cast<float2*>(a_lo + o) = make_float2(x[c].x - re_hi, x[c].y - im_hi);
+    for (int c = 0; c < 16; ++c) {
+      const float2 u = x[2 * c], v = x[2 * c + 1];
+      const float4 h = make_float4(hi(u.x), hi(u.y), hi(v.x), hi(v.y));
+      const uint32_t o = sw128_offset(tid, 4 * c, kTcRows);  // start of the chunk
+      *reinterpret_cast<float4*>(a_hi + o) = h;
+      *reinterpret_cast<float4*>(a_lo + o) = make_float4(u.x - h.x, u.y - h.y, v.x - h.z, v.y - h.w);
     }
     // make the generic-proxy shared-memory writes visible to the tensor cores
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -174,16 +178,9 @@ __global__ void __launch_bounds__(kTcRows, 1) k_block_tc(float* __restrict__ amp
                        smem_u32(bar))
                    : "memory");
     }
-    // gather the next tile's rows while the products run (disjoint rows, own tiles)
+    // the buffer is free: gather tile t + 2 grid into it (disjoint rows, own tiles)
     const uint64_t rb_cur = rb;
-    {
-      const uint64_t tn = t + gridDim.x;
-      if (tn < ntiles) {
-        rb = insert_zero_bits(tn * kTcRows + tid, spos, kTcK);
-#pragma unroll
-        for (int c = 0; c < 32; ++c) x[c] = reinterpret_cast<const float2*>(amps)[rb | offs[c]];
-      }
-    }
+    if (t + 2 * G < ntiles) gather(x, rb, t + 2 * G);
     // bounded wait for the products
     {
       uint32_t done = 0;
@@ -202,24 +199,32 @@ __global__ void __launch_bounds__(kTcRows, 1) k_block_tc(float* __restrict__ amp
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (!failed) {
-      // row tid of D: TMEM lane tid, 64 columns
-      float out[64];
+      // row tid of D: TMEM lane tid, 64 columns, stored 16 columns (8 amplitudes) at a time
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         uint32_t r[16];
         tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + uint32_t(q * 16), r);
         asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
 #pragma unroll
-        for (int i = 0; i < 16; ++i) out[q * 16 + i] = __uint_as_float(r[i]);
+        for (int i = 0; i < 8; ++i)
+          reinterpret_cast<float2*>(amps)[rb_cur | offs[q * 8 + i]] =
+              make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
       }
-#pragma unroll
-      for (int d = 0; d < 32; ++d)
-        reinterpret_cast<float2*>(amps)[rb_cur | offs[d]] = make_float2(out[2 * d], out[2 * d + 1]);
     }
+    // one barrier: the epilogue's TMEM reads are done before the next tile's products
+    // overwrite the accumulator, and a timed-out block stops; the others stop at their
+    // next tile (block-uniform test)
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    // a timed-out block stops; the others stop at their next tile (block-uniform test)
     failed = __syncthreads_or(*((volatile int*)status) != 0) != 0;
+  };
+  float2 xa[32], xb[32];
+  uint64_t rba = 0, rbb = 0;
+  const uint64_t t0 = blockIdx.x;
+  if (t0 < ntiles) gather(xa, rba, t0);
+  if (t0 + G < ntiles) gather(xb, rbb, t0 + G);
+  for (uint64_t t = t0; t < ntiles && !failed; t += 2 * G) {
+    step(xa, rba, t);
+    if (t + G < ntiles && !failed) step(xb, rbb, t + G);
   }
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -254,8 +259,6 @@ static void tc_bmatrix(const std::vector<double>& U5, std::vector<float>& out) {
       }
     }
 }
-
-static int g_tc_status_dummy = 0;
 
 qc_status apply_kq_tf32x3(qc_state* s, const int* bits, int k, const double* U) {
   if (s->dtype != QC_C64 || k < 1 || k > kTcK || s->n < kTcK + 7) {
@@ -327,7 +330,6 @@ qc_status apply_kq_tf32x3(qc_state* s, const int* bits, int k, const double* U) 
     set_error("tensor-core block: a bounded wait for the MMA completion ran out");
     return QC_ERR_TIMEOUT;
   }
-  (void)g_tc_status_dummy;
   return QC_OK;
 }
 
