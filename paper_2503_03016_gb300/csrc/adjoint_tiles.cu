@@ -215,7 +215,10 @@ __global__ void __launch_bounds__(NT, 1) k_adj_pass(R* __restrict__ psi, R* __re
         tp[a] = v[j];
         tl[a] = w[j];
       }
-      __syncthreads();
+      if (st.warp_local)
+        __syncwarp();  // the next stage gives this warp the same amplitudes
+      else
+        __syncthreads();
     }
     for (uint32_t e = threadIdx.x; e < T / 2; e += blockDim.x) {
       const uint32_t r = 2 * e;

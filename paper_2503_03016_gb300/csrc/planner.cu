@@ -142,7 +142,10 @@ __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const
       }
 #pragma unroll
       for (int j = 0; j < NA; ++j) tile[p0 ^ slot_xor<SB>(j, sw)] = v[j];
-      __syncthreads();
+      if (st.warp_local)
+        __syncwarp();  // the next stage gives this warp the same amplitudes
+      else
+        __syncthreads();
     }
     for (uint32_t e = threadIdx.x; e < T / 2; e += blockDim.x) {
       const uint32_t r = 2 * e;
@@ -399,6 +402,93 @@ std::vector<BuiltPass> build_passes(const std::vector<PlanOp>& ops, int n, int m
 }
 
 
+// Slot and thread-index bits of each stage of a pass.  acts[s] holds the local bits
+// stage s's gates act on (at most sb); it is padded to sb slot bits, and the other
+// m - sb local bits receive the thread-index bits: the first ones (lanes) one local bit
+// per residue mod nres, so that a half warp's shared-memory accesses fall in distinct
+// banks; the bits from 5 up pick the warp, so they fix the set of amplitudes a warp
+// holds.  Those warp bits are kept the same over runs of consecutive stages (disjoint
+// from every slot of the run), chosen greedily to make each run as long as possible
+// (which gives the fewest runs): inside a run a warp only exchanges amplitudes with
+// itself, and a warp barrier replaces the block barrier between its stages.
+static std::vector<TileStage> stage_layouts(const std::vector<std::vector<int>>& acts, int m, int sb, int nres) {
+  const int nthr = m - sb;
+  const int nl = std::min(nthr, 5), nw = nthr - nl;
+  const int need = std::min(nres, nl);
+  const uint32_t all = (1u << m) - 1;
+  auto resmask = [&](int r) {
+    uint32_t mk = 0;
+    for (int b = r; b < m; b += 4) mk |= 1u << b;
+    return mk;
+  };
+  std::vector<uint32_t> amask(acts.size(), 0);
+  for (size_t s = 0; s < acts.size(); ++s)
+    for (int b : acts[s]) amask[s] |= 1u << b;
+  // stage s can take warp bits W: W misses its active bits and the remaining bits hold
+  // every residue the lanes need (padding then takes only surplus bits)
+  auto fits = [&](size_t s, uint32_t W) {
+    if (W & amask[s]) return false;
+    const uint32_t rest = all & ~(amask[s] | W);
+    for (int r = 0; r < need; ++r)
+      if (!(rest & resmask(r))) return false;
+    return true;
+  };
+  std::vector<uint32_t> wsets;
+  for (uint32_t W = all;; W = (W - 1) & all) {  // descending: high bits first on ties
+    if (__builtin_popcount(W) == nw) wsets.push_back(W);
+    if (W == 0) break;
+  }
+  std::vector<TileStage> recs(acts.size());
+  size_t s = 0;
+  while (s < acts.size()) {
+    uint32_t best = 0;
+    size_t best_len = 0;
+    for (uint32_t W : wsets) {
+      size_t len = 0;
+      while (s + len < acts.size() && fits(s + len, W)) ++len;
+      if (len > best_len) {
+        best_len = len;
+        best = W;
+      }
+    }
+    const bool run = best_len > 0;
+    if (!run) best_len = 1;  // no choice covers the lanes' residues: the plain layout
+    for (size_t k = 0; k < best_len; ++k) {
+      TileStage& st = recs[s + k];
+      std::vector<int> act = acts[s + k];
+      const uint32_t W = run ? best : 0;
+      uint32_t used = amask[s + k] | W;
+      // pad the slots: bits whose residue keeps another free bit first, lowest first
+      while (int(act.size()) < sb) {
+        int pick = -1;
+        for (int b = 0; b < m && pick < 0; ++b)
+          if (!((used >> b) & 1) && __builtin_popcount(all & ~used & resmask(b % 4)) > 1) pick = b;
+        for (int b = 0; b < m && pick < 0; ++b)
+          if (!((used >> b) & 1)) pick = b;
+        act.push_back(pick);
+        used |= 1u << pick;
+      }
+      for (int q = 0; q < sb; ++q) st.slot_bit[q] = int8_t(act[q]);
+      std::vector<int> order;
+      for (int r = 0; r < nres; ++r)
+        for (int b = r; b < m; b += 4)
+          if (!((used >> b) & 1)) {
+            order.push_back(b);
+            used |= 1u << b;
+            break;
+          }
+      for (int b = 0; b < m; ++b)
+        if (!((used >> b) & 1)) order.push_back(b);
+      for (int b = 0; b < m; ++b)
+        if ((W >> b) & 1) order.push_back(b);
+      for (size_t q = 0; q < order.size() && q < 16; ++q) st.lane_bit[q] = int8_t(order[q]);
+      st.warp_local = int8_t(run && k + 1 < best_len ? 1 : 0);
+    }
+    s += best_len;
+  }
+  return recs;
+}
+
 template <typename R>
 void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int m, int L, int sb,
                HostPlan<R>& hp, bool swap_ops, bool phase1_ops) {
@@ -428,6 +518,7 @@ void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int 
   // fit in <= 4 active local bits and that no skipped op it fails to commute with
   // precedes (same rule as for passes); skipped ops go to later stages in order.
   std::vector<int> rest = bp.ops;
+  std::vector<std::vector<int>> takes, acts;
   while (!rest.empty()) {
     std::vector<int> act;
     std::vector<int> take, skip;
@@ -457,29 +548,15 @@ void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int 
           blocked_all |= p.touched;
       }
     }
-    // pad with unused local bits (lowest first)
-    for (int b = 0; int(act.size()) < sb && b < m; ++b)
-      if (std::find(act.begin(), act.end(), b) == act.end()) act.push_back(b);
-    TileStage st{};
-    for (int k = 0; k < sb; ++k) st.slot_bit[k] = int8_t(act[k]);
-    {
-      // thread-index bits -> non-slot local bits; first one bit per residue mod 4
-      // (4 residues: 8-byte elements, half-warp banks; 3: 16-byte elements)
-      std::vector<int> rest_bits;
-      for (int b = 0; b < m; ++b)
-        if (std::find(act.begin(), act.end(), b) == act.end()) rest_bits.push_back(b);
-      std::vector<int> order;
-      const int nres = sizeof(R) == 4 ? 4 : 3;
-      for (int res = 0; res < nres; ++res)
-        for (int b : rest_bits)
-          if (b % 4 == res && std::find(order.begin(), order.end(), b) == order.end()) {
-            order.push_back(b);
-            break;
-          }
-      for (int b : rest_bits)
-        if (std::find(order.begin(), order.end(), b) == order.end()) order.push_back(b);
-      for (size_t k = 0; k < order.size() && k < 16; ++k) st.lane_bit[k] = int8_t(order[k]);
-    }
+    takes.push_back(take);
+    acts.push_back(act);
+    rest.swap(skip);
+  }
+  // 4 residues: 8-byte elements, half-warp banks; 3: 16-byte elements
+  const std::vector<TileStage> recs = stage_layouts(acts, m, sb, sizeof(R) == 4 ? 4 : 3);
+  for (size_t si = 0; si < takes.size(); ++si) {
+    const std::vector<int>& take = takes[si];
+    TileStage st = recs[si];
     st.op0 = int(hp.ops.size()) - P.op0;
     const size_t j = take.size();
     // a CZ: the phase pi on b_t b_c keyed on its target t (no constant, no tag)
@@ -694,7 +771,6 @@ void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int 
     }
     st.nops = int(hp.ops.size()) - P.op0 - st.op0;
     hp.stages.push_back(st);
-    rest.swap(skip);
   }
   P.nstages = int(hp.stages.size()) - P.stage0;
   P.nops = int(hp.ops.size()) - P.op0;

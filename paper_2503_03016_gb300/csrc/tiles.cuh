@@ -34,7 +34,10 @@ static_assert(sizeof(TileOp) == 64, "TileOp must be 64 bytes");
 
 struct TileStage {
   int32_t op0, nops;
-  int8_t slot_bit[8];   // local bit of each slot (SB used)
+  int8_t slot_bit[7];   // local bit of each slot (SB used)
+  int8_t warp_local;    // 1: the next stage gives every warp the same amplitudes (the same
+                        // local bits receive thread-index bits 5 and up), so a warp
+                        // barrier ends this stage; 0: a block barrier
   int8_t lane_bit[16];  // local bit receiving bit k of the thread index (the m-SB non-slot
                         // bits; the first ones cover distinct bit positions mod 4 so that
                         // a half warp's shared-memory accesses fall in distinct banks)
