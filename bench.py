@@ -290,7 +290,22 @@ def run_ours(args):
 
     sbytes = (1 << N_QUBITS) * 8
     passes = P.qc_last_pass_count() if args.mode == "fused" else len(ops)
-    if args.mode == "fused":
+    tc_path = args.mode == "fused" and P.qc_last_fused_path() == 2
+    if tc_path:
+        # dominant kernel: the tile pass with tensor-core stages.  Each stage is a
+        # 128 x 64 x 64 real GEMM per 4096-amplitude tile, three TF32 products:
+        # 2 * 64 * 64 * 128 * 3 / 4096 = 768 flops per amplitude per stage.
+        stages = P.qc_last_stage_count()
+        flops = stages * 768.0 * (1 << N_QUBITS)
+        tf32_peak = bf16_tflops * 1.1 / 2.25
+        achieved = flops / (circ_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
+                "frac": achieved / tf32_peak, "traffic": None,
+                "traffic_note": "not captured for this kernel at this size",
+                "peak_source": "%s bf16 x 1.1/2.25 (nominal dense TF32/BF16 ratio)" % peak_src,
+                "kernel": "k_tile_pass_tc", "passes": passes, "stages": stages,
+                "gate_tflops_fp32_equivalent": len(ops) * 32.0 * (1 << N_QUBITS) / (circ_ms * 1e-3) / 1e12}
+    elif args.mode == "fused":
         # dominant kernel: the tile pass, bound by FP32 FMA for Haar gates.  Algorithmic
         # work: every two-qubit gate is 4 complex multiply-adds (32 flops) per amplitude.
         # Peak from unit counts: SMs x 128 FP32 lanes x 2 flops x SM clock under load.
@@ -322,7 +337,8 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": "circuits/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "tf32x3" if tc_path else "c64",
             "data": "synthetic",
             "config": {"workload": WORKLOAD, "mode": args.mode, "prec": args.prec,
                        "parallelism": "replicas" if world > 1 else "single",

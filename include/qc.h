@@ -69,6 +69,13 @@ uint64_t qc_launch_count(void);
 /* Number of tile passes the planner used for the most recent QC_RUN_FUSED circuit or
  * fused adjoint reverse sweep (process-wide; a diagnostic for benchmarks). */
 int qc_last_pass_count(void);
+/* How the most recent QC_RUN_FUSED circuit ran (process-wide; a diagnostic): 0 one
+ * sweep per gate (fewer than 10 qubits), 1 tile passes on the CUDA cores, 2 tile passes
+ * whose stages ran as 32 x 32 blocks on the tensor cores (QC_PREC_TF32X3). */
+int qc_last_fused_path(void);
+/* Register stages (CUDA-core passes) or 32 x 32 stage blocks (tensor-core passes) of
+ * the most recent QC_RUN_FUSED circuit (process-wide; a diagnostic). */
+int qc_last_stage_count(void);
 /* Plans circuit `c` as QC_RUN_FUSED would for a state of `dtype` and reports the number
  * of tile passes, register stages and tile ops; host only (no device work, no GPU
  * needed).  Circuits on fewer than 10 qubits report 0 (they run per gate). */
@@ -280,7 +287,13 @@ typedef enum {
 
 /* Applies every op of `c` (c->n must equal the state's n) in order.  `params`
  * (host, may be NULL if no op uses it) supplies angles for ops with param >= 0.
- * `prec` selects the arithmetic of fused blocks in QC_RUN_FUSED. */
+ * `prec` selects the arithmetic of fused blocks in QC_RUN_FUSED: with QC_PREC_TF32X3 and a
+ * complex64 state of n >= 12 qubits, the tile passes (2^12 amplitudes) run each stage --
+ * the ops on 5 of the tile's bits, controls and phase bits included -- as one 32 x 32
+ * block on the tensor cores (host FP64 product of the stage's gates; TF32 split with
+ * round-to-nearest, eight FP32 partial accumulators per output added on the CUDA cores;
+ * synchronising: a bounded-wait timeout returns QC_ERR_TIMEOUT).  A circuit with an op
+ * whose control or phase bit lies outside its stage runs on the CUDA-core passes. */
 qc_status qc_run_circuit(qc_state* s, const qc_circuit* c, const double* params, qc_run_mode mode,
                          qc_prec prec);
 

@@ -58,6 +58,8 @@ _SIGS = {
     "qc_abi_version": (ctypes.c_int, []),
     "qc_launch_count": (ctypes.c_uint64, []),
     "qc_last_pass_count": (ctypes.c_int, []),
+    "qc_last_fused_path": (ctypes.c_int, []),
+    "qc_last_stage_count": (ctypes.c_int, []),
     "qc_plan_info": (ctypes.c_int, [ctypes.c_void_p, _D, ctypes.c_int, _I, _I, _I]),
     "qc_state_alloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(_P)]),
     "qc_state_wrap": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, ctypes.POINTER(_P)]),
@@ -153,6 +155,16 @@ def qc_launch_count() -> int:
 
 def qc_last_pass_count() -> int:
     return int(lib().qc_last_pass_count())
+
+
+def qc_last_fused_path() -> int:
+    """0 per gate, 1 CUDA-core tile passes, 2 tile passes with tensor-core stages."""
+    return int(lib().qc_last_fused_path())
+
+
+def qc_last_stage_count() -> int:
+    """Register stages (or tensor-core stage blocks) of the most recent fused circuit."""
+    return int(lib().qc_last_stage_count())
 
 
 # ---------------------------------------------------------------------------

@@ -1,6 +1,8 @@
 // Circuit-level declarations shared by circuit.cu, planner.cu and the fused kernels.
 #pragma once
 
+#include <vector>
+
 #include "common.cuh"
 
 namespace qcgb {
@@ -31,6 +33,9 @@ qc_status resolve_op(const qc_circuit* c, const qc_op& op, const double* params,
 qc_status apply_resolved(qc_state* s, const ResolvedOp& r);
 qc_status run_per_gate(qc_state* s, const qc_circuit* c, const double* params);
 qc_status run_fused(qc_state* s, const qc_circuit* c, const double* params, qc_prec prec);
+// complex64 tile passes whose stages run as 32 x 32 blocks on the tensor cores (TF32x3);
+// *handled is false (nothing applied) when a stage's op depends on bits outside its slots
+qc_status run_tiles_tc(qc_state* s, const std::vector<ResolvedOp>& rops, bool* handled);
 qc_status apply_kq_native(qc_state* s, const int* bits, int k, const double* U);
 qc_status apply_kq_tf32x3(qc_state* s, const int* bits, int k, const double* U);
 

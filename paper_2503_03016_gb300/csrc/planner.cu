@@ -411,7 +411,58 @@ std::vector<BuiltPass> build_passes(const std::vector<PlanOp>& ops, int n, int m
 // from every slot of the run), chosen greedily to make each run as long as possible
 // (which gives the fewest runs): inside a run a warp only exchanges amplitudes with
 // itself, and a warp barrier replaces the block barrier between its stages.
-static std::vector<TileStage> stage_layouts(const std::vector<std::vector<int>>& acts, int m, int sb, int nres) {
+// Register stages of a pass: each takes, in order, every remaining op of the pass whose
+// dense targets fit in <= sb active local bits and that no skipped op it fails to
+// commute with precedes (same rule as for passes); skipped ops go to later stages in
+// order.  takes[s]: the ops of stage s; acts[s]: the local bits their targets occupy.
+// With whole_ops, an op's in-tile control and phase bits count as active bits too (a
+// stage applied as one block must see every bit its ops depend on).
+void split_stages(const BuiltPass& bp, const std::vector<PlanOp>& pops, const int* local_of, int sb,
+                  std::vector<std::vector<int>>& takes, std::vector<std::vector<int>>& acts, bool whole_ops) {
+  std::vector<int> rest = bp.ops;
+  while (!rest.empty()) {
+    std::vector<int> act;
+    std::vector<int> take, skip;
+    uint64_t blocked_all = 0, blocked_diag = 0;
+    for (int idx : rest) {
+      const PlanOp& p = pops[idx];
+      bool ok = (p.touched & blocked_all) == 0;
+      if (ok && !p.phase) ok = (p.touched & blocked_diag) == 0;
+      if (ok && (whole_ops || !p.phase)) {
+        std::vector<int> nw = act;
+        auto add = [&](int gbit) {
+          const int lb = local_of[gbit];
+          if (lb >= 0 && std::find(nw.begin(), nw.end(), lb) == nw.end()) nw.push_back(lb);
+        };
+        if (!p.phase)
+          for (int k = 0; k < p.nt; ++k) add(p.tb[k]);
+        if (whole_ops) {
+          for (int b = 0; b < 64; ++b)
+            if ((p.cmask >> b) & 1) add(b);
+          for (const auto& be : p.beta) add(be.first);
+        }
+        if (int(nw.size()) > sb)
+          ok = false;
+        else
+          act = nw;
+      }
+      if (ok) {
+        take.push_back(idx);
+      } else {
+        skip.push_back(idx);
+        if (p.phase)
+          blocked_diag |= p.touched;
+        else
+          blocked_all |= p.touched;
+      }
+    }
+    takes.push_back(take);
+    acts.push_back(act);
+    rest.swap(skip);
+  }
+}
+
+std::vector<TileStage> stage_layouts(const std::vector<std::vector<int>>& acts, int m, int sb, int nres) {
   const int nthr = m - sb;
   const int nl = std::min(nthr, 5), nw = nthr - nl;
   const int need = std::min(nres, nl);
@@ -514,44 +565,8 @@ void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int 
     for (int b = 0; b < n; ++b)
       if (local_of[b] < 0) gbit_of_tb[k++] = b;
   }
-  // stages: each takes, in order, every remaining op of the pass whose dense targets
-  // fit in <= 4 active local bits and that no skipped op it fails to commute with
-  // precedes (same rule as for passes); skipped ops go to later stages in order.
-  std::vector<int> rest = bp.ops;
   std::vector<std::vector<int>> takes, acts;
-  while (!rest.empty()) {
-    std::vector<int> act;
-    std::vector<int> take, skip;
-    uint64_t blocked_all = 0, blocked_diag = 0;
-    for (int idx : rest) {
-      const PlanOp& p = pops[idx];
-      bool ok = (p.touched & blocked_all) == 0;
-      if (ok && !p.phase) ok = (p.touched & blocked_diag) == 0;
-      if (ok && !p.phase) {
-        std::vector<int> nw = act;
-        for (int k = 0; k < p.nt; ++k) {
-          const int lb = local_of[p.tb[k]];
-          if (std::find(nw.begin(), nw.end(), lb) == nw.end()) nw.push_back(lb);
-        }
-        if (int(nw.size()) > sb)
-          ok = false;
-        else
-          act = nw;
-      }
-      if (ok) {
-        take.push_back(idx);
-      } else {
-        skip.push_back(idx);
-        if (p.phase)
-          blocked_diag |= p.touched;
-        else
-          blocked_all |= p.touched;
-      }
-    }
-    takes.push_back(take);
-    acts.push_back(act);
-    rest.swap(skip);
-  }
+  split_stages(bp, pops, local_of, sb, takes, acts);
   // 4 residues: 8-byte elements, half-warp banks; 3: 16-byte elements
   const std::vector<TileStage> recs = stage_layouts(acts, m, sb, sizeof(R) == 4 ? 4 : 3);
   for (size_t si = 0; si < takes.size(); ++si) {
@@ -784,6 +799,8 @@ template void emit_pass<double>(const BuiltPass&, const std::vector<PlanOp>&, in
                                 bool, bool);
 
 int g_last_pass_count = 0;  // also set by the fused adjoint sweep
+int g_last_fused_path = 0;
+int g_last_stage_count = 0;
 
 // Register stage width SB (a thread holds 2^SB amplitudes) and block size of the tile
 // pass per precision: blockDim = 2^(m - SB) <= NT with m = 13 (complex64) / 12.
@@ -812,6 +829,8 @@ static qc_status run_tiles(qc_state* s, const std::vector<ResolvedOp>& rops, int
   // dense 4x4 it replaces
   for (const BuiltPass& bp : bps) emit_pass<R>(bp, pops, n, m, L, SB, hp, /*swap_ops=*/sizeof(R) == 8);
   g_last_pass_count = int(hp.passes.size());
+  g_last_fused_path = 1;
+  g_last_stage_count = int(hp.stages.size());
   // upload stages, ops, tables and matrices into the state's scratch (stream ordered)
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t sb = al(hp.stages.size() * sizeof(TileStage));
@@ -864,12 +883,20 @@ int tile_bits_for(const qc_state* s) {
 }
 
 qc_status run_fused(qc_state* s, const qc_circuit* c, const double* params, qc_prec prec) {
-  (void)prec;
   std::vector<ResolvedOp> rops(c->nops);
   for (int i = 0; i < c->nops; ++i)
     if (qc_status st = resolve_op(c, c->ops[i], params, &rops[i])) return st;
+  if (prec == QC_PREC_TF32X3 && s->dtype == QC_C64) {
+    bool handled = false;
+    if (qc_status st = run_tiles_tc(s, rops, &handled)) return st;
+    if (handled) return QC_OK;
+  }
   const int m = tile_bits_for(s);
-  if (s->n < 10 || m < kMaxStageBits + 4) return run_per_gate(s, c, params);
+  if (s->n < 10 || m < kMaxStageBits + 4) {
+    g_last_fused_path = 0;
+    g_last_stage_count = 0;
+    return run_per_gate(s, c, params);
+  }
   return s->dtype == QC_C64 ? run_tiles<float>(s, rops, m) : run_tiles<double>(s, rops, m);
 }
 
@@ -892,6 +919,8 @@ static void plan_stats(int n, const std::vector<ResolvedOp>& rops, int m, int* p
 using namespace qcgb;
 
 extern "C" int qc_last_pass_count(void) { return qcgb::g_last_pass_count; }
+extern "C" int qc_last_fused_path(void) { return qcgb::g_last_fused_path; }
+extern "C" int qc_last_stage_count(void) { return qcgb::g_last_stage_count; }
 
 extern "C" qc_status qc_plan_info(const qc_circuit* c, const double* params, qc_dtype dtype, int* passes,
                                   int* stages, int* ops) {

@@ -391,6 +391,11 @@ struct HostPlan {
 
 // tile passes of the most recent fused circuit run or fused adjoint reverse sweep
 extern int g_last_pass_count;
+// how the most recent QC_RUN_FUSED circuit ran: 0 per gate, 1 CUDA-core tile passes,
+// 2 tile passes with tensor-core stages
+extern int g_last_fused_path;
+// register stages (or tensor-core stage blocks) of the most recent fused circuit run
+extern int g_last_stage_count;
 
 // resolved gates -> plan ops (diagonal gates become phase ops); with `grad`/`gen`, op i
 // carries the tag grad[i] (>= 0: a rotation exp(-i t G/2) with generator gen[i]; X and Y
@@ -407,5 +412,13 @@ std::vector<BuiltPass> build_passes(const std::vector<PlanOp>& ops, int n, int m
 template <typename R>
 void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int m, int L, int sb,
                HostPlan<R>& hp, bool swap_ops = true, bool phase1_ops = true);
+// a pass's ops -> register stages (local_of: local bit of each global bit, -1 outside
+// the tile); takes[s] = the ops of stage s, acts[s] = the local bits their targets use
+// (whole_ops: control and phase bits in the tile count as active bits too)
+void split_stages(const BuiltPass& bp, const std::vector<PlanOp>& pops, const int* local_of, int sb,
+                  std::vector<std::vector<int>>& takes, std::vector<std::vector<int>>& acts, bool whole_ops = false);
+// slot bits (acts[s] padded to sb) and thread-index bits of each stage (m - sb of them,
+// the first ones one per residue mod nres); warp bits kept over runs of stages
+std::vector<TileStage> stage_layouts(const std::vector<std::vector<int>>& acts, int m, int sb, int nres);
 
 }  // namespace qcgb
