@@ -51,16 +51,23 @@ __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const
   Cplx<R>* bufs = reinterpret_cast<Cplx<R>*>(smem_raw);  // 2 x T
   uint64_t* hioff = reinterpret_cast<uint64_t*>(smem_raw + 2 * sizeof(Cplx<R>) * T);
   const int nhi = m - L;
+  // write-out gather after relabeled swaps: tile position of output local index u is
+  // rlo[u mod 2^L] | rhi[u >> L]
+  uint32_t* rhi = reinterpret_cast<uint32_t*>(hioff + (1u << nhi));
   // the pass's plan, copied once into shared memory: stages, ops, matrices
-  TileStage* sst = reinterpret_cast<TileStage*>(hioff + (1u << nhi));
+  TileStage* sst = reinterpret_cast<TileStage*>(rhi + (1u << nhi));
   TileOp* sop = reinterpret_cast<TileOp*>(sst + P.nstages);
   R* smat = reinterpret_cast<R*>(sop + P.nops);
   // the tile's bit positions in shared memory (a dynamically indexed kernel parameter
   // array would be copied to local memory)
-  __shared__ int8_t sbits[16];
+  __shared__ int8_t sbits[16], srbit[16];
+  __shared__ uint32_t rlo[16];
   if (threadIdx.x == 0) {
 #pragma unroll
-    for (int k = 0; k < 16; ++k) sbits[k] = P.bits[k];
+    for (int k = 0; k < 16; ++k) {
+      sbits[k] = P.bits[k];
+      srbit[k] = P.rbit[k];
+    }
   }
   __syncthreads();
   for (uint32_t h = threadIdx.x; h < (1u << nhi); h += blockDim.x) {
@@ -68,6 +75,20 @@ __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const
     for (int k = 0; k < nhi; ++k)
       if ((h >> k) & 1) o |= uint64_t(1) << sbits[L + k];
     hioff[h] = o;
+  }
+  if constexpr (EXTOPS) {
+    for (uint32_t h = threadIdx.x; h < (1u << nhi); h += blockDim.x) {
+      uint32_t q = 0;
+      for (int k = 0; k < nhi; ++k)
+        if ((h >> k) & 1) q |= 1u << srbit[L + k];
+      rhi[h] = q;
+    }
+    if (threadIdx.x < (1u << L)) {
+      uint32_t q = 0;
+      for (int k = 0; k < L; ++k)
+        if ((threadIdx.x >> k) & 1) q |= 1u << srbit[k];
+      rlo[threadIdx.x] = q;
+    }
   }
   for (int i = threadIdx.x; i < P.nstages; i += blockDim.x) sst[i] = stages[P.stage0 + i];
   for (int i = threadIdx.x; i < P.nops; i += blockDim.x) sop[i] = ops[P.op0 + i];
@@ -147,11 +168,22 @@ __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const
       else
         __syncthreads();
     }
-    for (uint32_t e = threadIdx.x; e < T / 2; e += blockDim.x) {
-      const uint32_t r = 2 * e;
-      const uint64_t gi = base | hioff[r >> L] | (r & lowmask);
-      const uint32_t p = tile_swz(r);
-      st_amp2<R>(amps, gi, tile[p], tile[p ^ 1u]);
+    if constexpr (EXTOPS) {
+      // (identity tables unless the pass relabeled swaps; plans with relabeled swaps
+      // run this variant)
+      for (uint32_t e = threadIdx.x; e < T / 2; e += blockDim.x) {
+        const uint32_t u = 2 * e;
+        const uint64_t gi = base | hioff[u >> L] | (u & lowmask);
+        const uint32_t hi = rhi[u >> L];
+        st_amp2<R>(amps, gi, tile[tile_swz(hi | rlo[u & lowmask])], tile[tile_swz(hi | rlo[(u | 1u) & lowmask])]);
+      }
+    } else {
+      for (uint32_t e = threadIdx.x; e < T / 2; e += blockDim.x) {
+        const uint32_t r = 2 * e;
+        const uint64_t gi = base | hioff[r >> L] | (r & lowmask);
+        const uint32_t p = tile_swz(r);
+        st_amp2<R>(amps, gi, tile[p], tile[p ^ 1u]);
+      }
     }
     __syncthreads();  // this buffer is refilled two iterations later
   }
@@ -540,13 +572,70 @@ std::vector<TileStage> stage_layouts(const std::vector<std::vector<int>>& acts, 
   return recs;
 }
 
+// exactly the SWAP permutation (rows 0, 2, 1, 3 of the identity), no condition
+static bool is_exact_swap(const PlanOp& p) {
+  if (p.phase || p.nt != 2 || p.cmask != 0 || p.grad >= 0) return false;
+  for (int e = 0; e < 16; ++e) {
+    const int r = e >> 2, c = e & 3;
+    const int want_c = r == 1 ? 2 : r == 2 ? 1 : r;
+    if (p.m[2 * e] != (c == want_c ? 1.0 : 0.0) || p.m[2 * e + 1] != 0.0) return false;
+  }
+  return true;
+}
+
+// an op with its global bits renamed: bit b -> ren[b]
+static PlanOp renamed(const PlanOp& p, const int* ren) {
+  PlanOp q = p;
+  for (int k = 0; k < p.nt && !p.phase; ++k) q.tb[k] = ren[p.tb[k]];
+  auto map_mask = [&](uint64_t mk) {
+    uint64_t o = 0;
+    for (int b = 0; b < 64; ++b)
+      if ((mk >> b) & 1) o |= uint64_t(1) << ren[b];
+    return o;
+  };
+  q.cmask = map_mask(p.cmask);
+  q.cval = map_mask(p.cval);
+  q.touched = map_mask(p.touched);
+  for (auto& be : q.beta) be.first = ren[be.first];
+  return q;
+}
+
 template <typename R>
-void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int m, int L, int sb,
-               HostPlan<R>& hp, bool swap_ops, bool phase1_ops) {
+void emit_pass(const BuiltPass& bp0, const std::vector<PlanOp>& pops0, int n, int m, int L, int sb,
+               HostPlan<R>& hp, bool swap_ops, bool phase1_ops, bool relabel_swaps) {
   TilePass P{};
   P.m = m;
   P.L = L;
-  for (int i = 0; i < m; ++i) P.bits[i] = int8_t(bp.B[i]);
+  for (int i = 0; i < m; ++i) P.bits[i] = int8_t(bp0.B[i]);
+  for (int i = 0; i < 16; ++i) P.rbit[i] = int8_t(i);
+  // The pass's ops, in order.  An exact SWAP of two tile bits moves no data: from there
+  // on the data of either qubit sits where the other's was, so the pass's later ops are
+  // renamed (ren[b]: where the data of global bit b sits in the tile as loaded), and the
+  // write-out takes the amplitude for local index u (bit k of u = global bit B[k]) from
+  // the tile position whose bit rbit[k] is bit k of u.
+  std::vector<PlanOp> pops;
+  BuiltPass bp;
+  bp.B = bp0.B;
+  {
+    int ren[64], loc[64];
+    for (int b = 0; b < 64; ++b) {
+      ren[b] = b;
+      loc[b] = -1;
+    }
+    for (int i = 0; i < m; ++i) loc[bp0.B[i]] = i;
+    for (int idx : bp0.ops) {
+      const PlanOp& p = pops0[idx];
+      if (relabel_swaps && is_exact_swap(p) && loc[ren[p.tb[0]]] >= 0 && loc[ren[p.tb[1]]] >= 0) {
+        std::swap(ren[p.tb[0]], ren[p.tb[1]]);
+        P.permuted = 1;
+        continue;
+      }
+      bp.ops.push_back(int(pops.size()));
+      pops.push_back(renamed(p, ren));
+    }
+    if (P.permuted)
+      for (int k = 0; k < m; ++k) P.rbit[k] = int8_t(loc[ren[bp0.B[k]]]);
+  }
   P.ntiles = uint64_t(1) << (n - m);
   P.c0 = m / 2;
   P.c1 = m - P.c0;
@@ -794,9 +883,9 @@ void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int 
 }
 
 template void emit_pass<float>(const BuiltPass&, const std::vector<PlanOp>&, int, int, int, int, HostPlan<float>&,
-                               bool, bool);
+                               bool, bool, bool);
 template void emit_pass<double>(const BuiltPass&, const std::vector<PlanOp>&, int, int, int, int, HostPlan<double>&,
-                                bool, bool);
+                                bool, bool, bool);
 
 int g_last_pass_count = 0;  // also set by the fused adjoint sweep
 int g_last_fused_path = 0;
@@ -827,7 +916,8 @@ static qc_status run_tiles(qc_state* s, const std::vector<ResolvedOp>& rops, int
   // complex128 applies an exact SWAP as a register permutation; in the complex64
   // kernel that dispatch costs more (register allocation of every gate body) than the
   // dense 4x4 it replaces
-  for (const BuiltPass& bp : bps) emit_pass<R>(bp, pops, n, m, L, SB, hp, /*swap_ops=*/sizeof(R) == 8);
+  for (const BuiltPass& bp : bps)
+    emit_pass<R>(bp, pops, n, m, L, SB, hp, /*swap_ops=*/sizeof(R) == 8, /*phase1_ops=*/true, /*relabel_swaps=*/true);
   g_last_pass_count = int(hp.passes.size());
   g_last_fused_path = 1;
   g_last_stage_count = int(hp.stages.size());
@@ -856,10 +946,11 @@ static qc_status run_tiles(qc_state* s, const std::vector<ResolvedOp>& rops, int
   size_t plan_max = 0;
   for (const TilePass& P : hp.passes)
     plan_max = std::max(plan_max, P.nstages * sizeof(TileStage) + P.nops * sizeof(TileOp) + P.nmat * sizeof(R));
-  const size_t smem = 2 * sizeof(Cplx<R>) * (size_t(1) << m) + sizeof(uint64_t) * (size_t(1) << (m - L)) + plan_max;
+  const size_t smem = 2 * sizeof(Cplx<R>) * (size_t(1) << m) + (sizeof(uint64_t) + sizeof(uint32_t)) * (size_t(1) << (m - L)) + plan_max;
   constexpr int NT = TileShape<R>::NT;
   bool extops = false;
   for (const TileOp& op : hp.ops) extops |= op.type == TOP_CZSET || op.type == TOP_PHASE1;
+  for (const TilePass& P : hp.passes) extops |= P.permuted != 0;
   auto kern = extops ? k_tile_pass<R, NT, SB, true> : k_tile_pass<R, NT, SB, false>;
   if (qc_status st = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
                                 "tile pass shared memory"))
@@ -908,7 +999,8 @@ static void plan_stats(int n, const std::vector<ResolvedOp>& rops, int m, int* p
   to_plan_ops(rops, pops);
   std::vector<BuiltPass> bps = build_passes(pops, n, m, L);
   HostPlan<R> hp;
-  for (const BuiltPass& bp : bps) emit_pass<R>(bp, pops, n, m, L, SB, hp, /*swap_ops=*/sizeof(R) == 8);
+  for (const BuiltPass& bp : bps)
+    emit_pass<R>(bp, pops, n, m, L, SB, hp, /*swap_ops=*/sizeof(R) == 8, /*phase1_ops=*/true, /*relabel_swaps=*/true);
   *passes = int(hp.passes.size());
   *stages = int(hp.stages.size());
   *ops = int(hp.ops.size());

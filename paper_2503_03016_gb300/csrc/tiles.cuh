@@ -54,6 +54,8 @@ struct TilePass {
   int32_t cg;        // tile-index phase-table chunk width (3 chunks)
   uint64_t ntiles;
   int32_t ngrad;     // adjoint sweep: rotations recorded in this pass
+  int32_t permuted;  // exact SWAPs taken as relabelings: the data of global bit bits[k]
+  int8_t rbit[16];   // sits at local bit rbit[k] when the pass writes the tile back
 };
 
 // ---------------------------------------------------------------------------
@@ -409,9 +411,11 @@ std::vector<BuiltPass> build_passes(const std::vector<PlanOp>& ops, int n, int m
 // 4x4 (kernels that hold two states per thread keep the dense form: fewer registers);
 // with phase1_ops, a phase op on at most one bit becomes TOP_PHASE1 (two factors, no
 // per-thread table lookups)
+// with relabel_swaps, an exact SWAP of two tile bits applies no arithmetic: the pass's
+// later ops name the exchanged bits and the write-out reads the tile accordingly
 template <typename R>
 void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int m, int L, int sb,
-               HostPlan<R>& hp, bool swap_ops = true, bool phase1_ops = true);
+               HostPlan<R>& hp, bool swap_ops = true, bool phase1_ops = true, bool relabel_swaps = false);
 // a pass's ops -> register stages (local_of: local bit of each global bit, -1 outside
 // the tile); takes[s] = the ops of stage s, acts[s] = the local bits their targets use
 // (whole_ops: control and phase bits in the tile count as active bits too)

@@ -126,6 +126,32 @@ def test_fused_cz_runs(dtype, n):
     assert rel_l2(got, want) <= TOL[dtype] * 10
 
 
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("n", [12, 15])
+def test_fused_swaps_relabeled(dtype, n):
+    """Exact SWAPs inside a tile move no data: the pass's later ops are renamed and the
+    write-out reads the tile through the permutation.  Chains of swaps over low and
+    high bits, the same pair twice, swaps followed by dense gates, controls and phases
+    on the swapped qubits, and a circuit of swaps alone."""
+    rng = np.random.default_rng(100 + n)
+    U = W.haar_unitaries(16, 4, 5)
+    ops = []
+    for layer in range(6):
+        for _ in range(6):
+            a, b = (int(x) for x in rng.permutation(n)[:2])
+            ops.append(Op("swap", (a, b)))
+        ops += [Op("swap", (n - 1, n - 2)), Op("swap", (n - 1, 0)), Op("swap", (n - 1, 0))]
+        a, b, c = (int(x) for x in rng.permutation(n)[:3])
+        ops += [Op("u2q", (a, b), matrix=U[layer]), Op("cnot", (c, a)), Op("cp", (b, c), (0.7,)),
+                Op("u3", (a,), (0.3, 1.2, 2.1)), Op("mcx", (a, b, c), ctrl_states=(1, 0)),
+                Op("swap", (a, c)), Op("rz", (a,), (0.9,)), Op("cz", (c, b)), Op("h", (c,))]
+    got, want, _ = run_both(n, ops, dtype)
+    assert rel_l2(got, want) <= TOL[dtype]
+    only = [Op("swap", (int(a), int(b))) for a, b in (rng.permutation(n)[:2] for _ in range(40))]
+    got, want, _ = run_both(n, only, dtype)
+    assert rel_l2(got, want) <= TOL[dtype]
+
+
 def test_fused_small_n_uses_per_gate():
     ops = W.brickwork(6, 4, 1)
     got, want, _ = run_both(6, ops, "c128")
