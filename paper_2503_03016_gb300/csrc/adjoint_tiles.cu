@@ -82,7 +82,8 @@ __global__ void __launch_bounds__(NT, 1) k_adj_pass(R* __restrict__ psi, R* __re
   Cplx<R>* bufs = reinterpret_cast<Cplx<R>*>(smem_raw);  // psi: 2 x T, lambda: 2 x T
   uint64_t* hioff = reinterpret_cast<uint64_t*>(smem_raw + 4 * sizeof(Cplx<R>) * T);
   const int nhi = m - L;
-  TileStage* sst = reinterpret_cast<TileStage*>(hioff + (1u << nhi));
+  uint64_t* tnt = hioff + (1u << nhi);  // tile number -> base
+  TileStage* sst = reinterpret_cast<TileStage*>(tnt + kTileNumberTab);
   TileOp* sop = reinterpret_cast<TileOp*>(sst + P.nstages);
   R* smat = reinterpret_cast<R*>(sop + P.nops);
   double* sacc = reinterpret_cast<double*>(smat + ((P.nmat + 1) & ~1));  // NW x ngrad
@@ -98,6 +99,7 @@ __global__ void __launch_bounds__(NT, 1) k_adj_pass(R* __restrict__ psi, R* __re
       if ((h >> k) & 1) o |= uint64_t(1) << sbits[L + k];
     hioff[h] = o;
   }
+  build_tile_number_tables(tnt, sbits, m, __ffsll(static_cast<long long>(P.ntiles)) - 1);
   for (int i = threadIdx.x; i < P.nstages; i += blockDim.x) sst[i] = stages[P.stage0 + i];
   for (int i = threadIdx.x; i < P.nops; i += blockDim.x) sop[i] = ops[P.op0 + i];
   for (int i = threadIdx.x; i < P.nmat; i += blockDim.x) smat[i] = mats[P.mat0 + i];
@@ -108,7 +110,7 @@ __global__ void __launch_bounds__(NT, 1) k_adj_pass(R* __restrict__ psi, R* __re
   const Cplx<R>* cpool = reinterpret_cast<const Cplx<R>*>(pool);
   uint64_t t = blockIdx.x;
   if (t < P.ntiles) {
-    const uint64_t b0 = insert_zero_bits(t, sbits, m);
+    const uint64_t b0 = tile_base(t, tnt);
     prefetch_tile<R>(bufs, psi, b0, hioff, L, T);
     prefetch_tile<R>(bufs + 2 * T, lam, b0, hioff, L, T);
   }
@@ -116,10 +118,10 @@ __global__ void __launch_bounds__(NT, 1) k_adj_pass(R* __restrict__ psi, R* __re
   for (int it = 0; t < P.ntiles; t += gridDim.x, ++it) {
     Cplx<R>* tp = bufs + (it & 1) * T;
     Cplx<R>* tl = bufs + 2 * T + (it & 1) * T;
-    const uint64_t base = insert_zero_bits(t, sbits, m);
+    const uint64_t base = tile_base(t, tnt);
     const uint64_t tn = t + gridDim.x;
     if (tn < P.ntiles) {
-      const uint64_t bn = insert_zero_bits(tn, sbits, m);
+      const uint64_t bn = tile_base(tn, tnt);
       prefetch_tile<R>(bufs + ((it + 1) & 1) * T, psi, bn, hioff, L, T);
       prefetch_tile<R>(bufs + 2 * T + ((it + 1) & 1) * T, lam, bn, hioff, L, T);
     }
@@ -302,7 +304,8 @@ qc_status adjoint_reverse_tiles(int n, const std::vector<ResolvedOp>& rev, const
   for (const TilePass& P : hp.passes)
     plan_max = std::max(plan_max, P.nstages * sizeof(TileStage) + P.nops * sizeof(TileOp) +
                                       ((P.nmat + 1) & ~1) * sizeof(R) + size_t(S::NT / 32) * P.ngrad * sizeof(double));
-  const size_t smem = 4 * sizeof(Cplx<R>) * (size_t(1) << m) + sizeof(uint64_t) * (size_t(1) << (m - L)) + plan_max;
+  const size_t smem = 4 * sizeof(Cplx<R>) * (size_t(1) << m) + sizeof(uint64_t) * (size_t(1) << (m - L)) +
+                      sizeof(uint64_t) * kTileNumberTab + plan_max;
   if (qc_status st = check_cuda(cudaFuncSetAttribute(k_adj_pass<R, S::NT, S::SB>,
                                                      cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
                                 "adjoint pass shared memory"))

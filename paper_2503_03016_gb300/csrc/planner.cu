@@ -54,8 +54,9 @@ __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const
   // write-out gather after relabeled swaps: tile position of output local index u is
   // rlo[u mod 2^L] | rhi[u >> L]
   uint32_t* rhi = reinterpret_cast<uint32_t*>(hioff + (1u << nhi));
+  uint64_t* tnt = reinterpret_cast<uint64_t*>(rhi + (1u << nhi));  // tile number -> base
   // the pass's plan, copied once into shared memory: stages, ops, matrices
-  TileStage* sst = reinterpret_cast<TileStage*>(rhi + (1u << nhi));
+  TileStage* sst = reinterpret_cast<TileStage*>(tnt + kTileNumberTab);
   TileOp* sop = reinterpret_cast<TileOp*>(sst + P.nstages);
   R* smat = reinterpret_cast<R*>(sop + P.nops);
   // the tile's bit positions in shared memory (a dynamically indexed kernel parameter
@@ -90,6 +91,7 @@ __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const
       rlo[threadIdx.x] = q;
     }
   }
+  build_tile_number_tables(tnt, sbits, m, __ffsll(static_cast<long long>(P.ntiles)) - 1);
   for (int i = threadIdx.x; i < P.nstages; i += blockDim.x) sst[i] = stages[P.stage0 + i];
   for (int i = threadIdx.x; i < P.nops; i += blockDim.x) sop[i] = ops[P.op0 + i];
   for (int i = threadIdx.x; i < P.nmat; i += blockDim.x) smat[i] = mats[P.mat0 + i];
@@ -97,13 +99,13 @@ __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const
   const uint32_t lowmask = (1u << L) - 1;
   const Cplx<R>* cpool = reinterpret_cast<const Cplx<R>*>(pool);
   uint64_t t = blockIdx.x;
-  if (t < P.ntiles) prefetch_tile<R>(bufs, amps, insert_zero_bits(t, sbits, m), hioff, L, T);
+  if (t < P.ntiles) prefetch_tile<R>(bufs, amps, tile_base(t, tnt), hioff, L, T);
   cp_async_commit();
   for (int it = 0; t < P.ntiles; t += gridDim.x, ++it) {
     Cplx<R>* tile = bufs + (it & 1) * T;
-    const uint64_t base = insert_zero_bits(t, sbits, m);
+    const uint64_t base = tile_base(t, tnt);
     const uint64_t tn = t + gridDim.x;
-    if (tn < P.ntiles) prefetch_tile<R>(bufs + ((it + 1) & 1) * T, amps, insert_zero_bits(tn, sbits, m), hioff, L, T);
+    if (tn < P.ntiles) prefetch_tile<R>(bufs + ((it + 1) & 1) * T, amps, tile_base(tn, tnt), hioff, L, T);
     cp_async_commit();
     cp_async_wait1();
     __syncthreads();
@@ -946,7 +948,8 @@ static qc_status run_tiles(qc_state* s, const std::vector<ResolvedOp>& rops, int
   size_t plan_max = 0;
   for (const TilePass& P : hp.passes)
     plan_max = std::max(plan_max, P.nstages * sizeof(TileStage) + P.nops * sizeof(TileOp) + P.nmat * sizeof(R));
-  const size_t smem = 2 * sizeof(Cplx<R>) * (size_t(1) << m) + (sizeof(uint64_t) + sizeof(uint32_t)) * (size_t(1) << (m - L)) + plan_max;
+  const size_t smem = 2 * sizeof(Cplx<R>) * (size_t(1) << m) + (sizeof(uint64_t) + sizeof(uint32_t)) * (size_t(1) << (m - L)) +
+                      sizeof(uint64_t) * kTileNumberTab + plan_max;
   constexpr int NT = TileShape<R>::NT;
   bool extops = false;
   for (const TileOp& op : hp.ops) extops |= op.type == TOP_CZSET || op.type == TOP_PHASE1;

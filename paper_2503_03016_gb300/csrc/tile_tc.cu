@@ -61,7 +61,8 @@ struct TcStage {
 static_assert(sizeof(TcStage) == 16, "TcStage must be 16 bytes");
 
 constexpr size_t kTtSmem = 1024 /* alignment slack */ + 2 * kTtAbytes + 2 * kTtBimg + 2 * kTtTileBytes +
-                           kTtHi * sizeof(uint64_t) + kTtMaxStages * sizeof(TcStage) + 64;
+                           kTtHi * sizeof(uint64_t) + kTileNumberTab * sizeof(uint64_t) +
+                           kTtMaxStages * sizeof(TcStage) + 64;
 
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
   for (long long it = 0; it < kTcSpinLimit; ++it) {
@@ -96,7 +97,8 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
   unsigned char* bbuf = a_lo + kTtAbytes;  // two stage images
   Cplx<float>* tiles = reinterpret_cast<Cplx<float>*>(bbuf + 2 * kTtBimg);
   uint64_t* hioff = reinterpret_cast<uint64_t*>(bbuf + 2 * kTtBimg + 2 * kTtTileBytes);
-  TcStage* sst = reinterpret_cast<TcStage*>(hioff + kTtHi);
+  uint64_t* tnt = hioff + kTtHi;  // tile number -> base
+  TcStage* sst = reinterpret_cast<TcStage*>(tnt + kTileNumberTab);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sst + kTtMaxStages);  // products, B buffer 0, B buffer 1
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3);
   __shared__ int8_t sbits[16];
@@ -134,6 +136,7 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
       if ((h >> k) & 1) o |= uint64_t(1) << sbits[L + k];
     hioff[h] = o;
   }
+  build_tile_number_tables(tnt, sbits, m, __ffsll(static_cast<long long>(P.ntiles)) - 1);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -163,14 +166,14 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
   const uint64_t G = gridDim.x;
   const int row = tid & (kTtRows - 1), half = tid >> 7;
   uint64_t t = blockIdx.x;
-  if (t < P.ntiles) prefetch_tile<float>(tiles, amps, insert_zero_bits(t, sbits, m), hioff, L, T);
+  if (t < P.ntiles) prefetch_tile<float>(tiles, amps, tile_base(t, tnt), hioff, L, T);
   cp_async_commit();
   for (int it = 0; t < P.ntiles && !failed; t += G, ++it) {
     Cplx<float>* tile = tiles + (it & 1) * T;
-    const uint64_t tbase = insert_zero_bits(t, sbits, m);
+    const uint64_t tbase = tile_base(t, tnt);
     const uint64_t tn = t + G;
     if (tn < P.ntiles)
-      prefetch_tile<float>(tiles + ((it + 1) & 1) * T, amps, insert_zero_bits(tn, sbits, m), hioff, L, T);
+      prefetch_tile<float>(tiles + ((it + 1) & 1) * T, amps, tile_base(tn, tnt), hioff, L, T);
     cp_async_commit();
     cp_async_wait1();
     __syncthreads();

@@ -349,10 +349,33 @@ template <typename R>
 __device__ __forceinline__ void prefetch_tile(Cplx<R>* buf, const R* amps, uint64_t base, const uint64_t* hioff,
                                               int L, uint32_t T) {
   const uint32_t lowmask = (1u << L) - 1;
-  for (uint32_t r = threadIdx.x; r < T; r += blockDim.x) {
-    const uint64_t gi = base | hioff[r >> L] | (r & lowmask);
-    cp_async_amp<R>(buf + tile_swz(r), amps + 2 * gi);
+  const R* src = amps + 2 * base;  // the tile's bits and base's bits are disjoint
+  for (uint32_t r = threadIdx.x; r < T; r += blockDim.x)
+    cp_async_amp<R>(buf + tile_swz(r), src + 2 * (hioff[r >> L] | (r & lowmask)));
+}
+
+// Tile number t -> its index bits outside the tile (t's bits deposited, in order, on
+// the global bits not in the tile), by three lookups in tables of 256 entries that
+// cover the tile number 8 bits at a time (at most 24 tile-number bits).
+constexpr int kTileNumberTab = 3 * 256;
+__device__ __forceinline__ void build_tile_number_tables(uint64_t* tab, const int8_t* sbits, int m, int nt_bits) {
+  for (int e = threadIdx.x; e < kTileNumberTab; e += blockDim.x) {
+    const int c = e >> 8, v = e & 255;
+    uint64_t o = 0;
+    int idx = 0, j = 0;  // tile-number bit counter; next tile bit (sbits ascending)
+    for (int b = 0; b < 64 && idx < nt_bits && idx < 8 * c + 8; ++b) {
+      if (j < m && sbits[j] == b) {
+        ++j;
+        continue;
+      }
+      if (idx >= 8 * c && ((v >> (idx - 8 * c)) & 1)) o |= uint64_t(1) << b;
+      ++idx;
+    }
+    tab[e] = o;
   }
+}
+__device__ __forceinline__ uint64_t tile_base(uint64_t t, const uint64_t* tab) {
+  return tab[t & 255] | tab[256 + ((t >> 8) & 255)] | tab[512 + ((t >> 16) & 255)];
 }
 
 // ---------------------------------------------------------------------------
