@@ -481,6 +481,48 @@ def run_qft_bench(args):
                       "peaks": {"hbm_gbs": hbm}}))
 
 
+def run_window_bench(args):
+    """Opt-in secondary measurement: where the tensor-core stages pay.  540 Haar gates in
+    brickwork order on a window of the lowest 5 or 10 qubits of a 28-qubit complex64
+    state (deep stages: many gates per 5-bit block), on the CUDA-core tile passes and on
+    the passes with tensor-core stages."""
+    import torch
+
+    import paper_2503_03016_gb300 as P
+    torch.cuda.set_device(0)
+    n = args.qubits or 28
+    _, bf16, src = peaks()
+    sm_peak = torch.cuda.get_device_properties(0).multi_processor_count * 128 * 2 * 2070e6 / 1e12
+    tf32_peak = bf16 * 1.1 / 2.25
+    stream = torch.cuda.current_stream()
+    st = P.State(n, "c64").init_gaussian(3)
+    res = {}
+    for width in (5, 10):
+        ops = W.window_chain(n, n - width, width, 540, 7)
+        circ = P.Circuit(n, ops)
+        for name, prec in (("fp32", P.QC_PREC_NATIVE), ("tf32x3", P.QC_PREC_TF32X3)):
+            P.qc_run_circuit(st.handle, circ, None, P.QC_RUN_FUSED, prec)  # warm-up
+            torch.cuda.synchronize()
+            t = StreamTimer(stream)
+            t.start()
+            for _ in range(args.steps):
+                P.qc_run_circuit(st.handle, circ, None, P.QC_RUN_FUSED, prec)
+            ms = t.stop() / args.steps
+            gate_tf = len(ops) * 32.0 * (1 << n) / (ms * 1e-3) / 1e12
+            r = {"ms": ms, "path": P.qc_last_fused_path(), "passes": P.qc_last_pass_count(),
+                 "stages": P.qc_last_stage_count(), "gate_tflops_fp32_equivalent": gate_tf}
+            if r["path"] == 2:
+                tf = r["stages"] * 768.0 * (1 << n) / (ms * 1e-3) / 1e12
+                r.update({"tf32_tflops": tf, "frac_tf32_peak": tf / tf32_peak})
+            else:
+                r.update({"frac_fp32_peak": gate_tf / sm_peak})
+            res["w%d_%s" % (width, name)] = r
+    st.free()
+    print(json.dumps({"metric": "540 Haar gates on the lowest 5 / 10 of %d qubits (complex64)" % n,
+                      "results": res, "peaks": {"fp32_tflops": sm_peak, "tf32_tflops": tf32_peak,
+                                                "tf32_source": "%s bf16 x 1.1/2.25" % src}}))
+
+
 def run_adjoint_bench(args):
     """Opt-in secondary measurement: energy + full gradient of the 24-qubit, 10-layer
     ansatz (480 parameters, H = ring ZZ + sum X) by the adjoint sweep."""
@@ -598,7 +640,7 @@ def main():
     ap.add_argument("--qubits", type=int, default=None,
                     help="register size (default: 28 brickwork and block, 32 QFT); smaller for profiling")
     ap.add_argument("--workload", default="brickwork",
-                    choices=["brickwork", "batch", "block", "qft", "adjoint", "sweeps"],
+                    choices=["brickwork", "batch", "block", "qft", "adjoint", "sweeps", "window"],
                     help="batch: opt-in secondary measurement of the batched launch")
     args = ap.parse_args()
     global N_QUBITS
@@ -613,6 +655,8 @@ def main():
         run_adjoint_bench(args)
     elif args.workload == "sweeps" and args.impl == "ours":
         run_sweeps_bench(args)
+    elif args.workload == "window" and args.impl == "ours":
+        run_window_bench(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

@@ -169,6 +169,21 @@ def brickwork(n: int = 28, depth: int = 40, seed: int = 2) -> list:
     return [Op("u2q", p, matrix=mats[i]) for i, p in enumerate(pairs)]
 
 
+def window_chain(n: int, first: int, width: int, count: int, seed: int) -> list:
+    """`count` Haar-random two-qubit unitaries in brickwork order on the neighbouring
+    pairs of qubits first .. first+width-1 only (a deep circuit on a window of the
+    register); drawn by :func:`haar_unitaries`."""
+    pairs = []
+    layer = 0
+    while len(pairs) < count:
+        start = 0 if layer % 2 == 0 else 1
+        pairs.extend((first + a, first + a + 1) for a in range(start, width - 1, 2))
+        layer += 1
+    pairs = pairs[:count]
+    mats = haar_unitaries(len(pairs), 4, seed)
+    return [Op("u2q", p, matrix=mats[i]) for i, p in enumerate(pairs)]
+
+
 def qft(n: int) -> list:
     """Textbook quantum Fourier transform with qubit 0 as the most significant
     bit: for j = 0..n-1, H(q_j) then CP(2 pi / 2**k) on (q_{j+k-1}, q_j) for
