@@ -14,7 +14,10 @@ namespace qcgb {
 
 constexpr int kMaxStageBits = 5;  // amplitudes a thread holds per stage: 2^SB, SB <= 5
 
-enum TileOpType : int32_t { TOP_DENSE1 = 0, TOP_DENSE2 = 1, TOP_PHASE = 2, TOP_SWAP = 3, TOP_CZSET = 4, TOP_PHASE1 = 5 };
+enum TileOpType : int32_t {
+  TOP_DENSE1 = 0, TOP_DENSE2 = 1, TOP_PHASE = 2, TOP_SWAP = 3, TOP_CZSET = 4, TOP_PHASE1 = 5,
+  TOP_BFLY = 6  // s [[1, 1], [1, -1]] (a Hadamard): a butterfly, no general 2x2 product
+};
 
 struct TileOp {
   int8_t type;
@@ -290,6 +293,45 @@ __device__ __forceinline__ void apply_phase1(Cplx<R> (&v)[1 << SB], const R* zs,
   }
 }
 
+// TOP_BFLY on slot S0: (x0, x1) -> (s x0 + s x1, s x0 - s x1), t = s x0 formed once;
+// three FMA-pipe operations per pair (complex64: on packed pairs) instead of the eight
+// products and sums of a general 2x2.  ss = (s, s, -s, -s) in the matrix block.
+template <typename R, int SB, int S0>
+__device__ __forceinline__ void bfly(Cplx<R> (&v)[1 << SB], const R* __restrict__ ss, uint32_t jmask) {
+#pragma unroll
+  for (int j = 0; j < (1 << SB); ++j) {
+    if (j & (1 << S0)) continue;
+    if (!((jmask >> j) & 1u)) continue;
+    const int j1 = j | (1 << S0);
+    if constexpr (sizeof(R) == 4) {
+      const float2 sp = make_float2(ss[0], ss[1]), sn = make_float2(ss[2], ss[3]);
+      const float2 t = __fmul2_rn(f2(v[j]), sp), x1 = f2(v[j1]);
+      v[j] = c2(__ffma2_rn(x1, sp, t));
+      v[j1] = c2(__ffma2_rn(x1, sn, t));
+    } else {
+      const R sp = ss[0];
+      const R tr = v[j].re * sp, ti = v[j].im * sp;
+      const Cplx<R> x1 = v[j1];
+      v[j] = Cplx<R>{fma(x1.re, sp, tr), fma(x1.im, sp, ti)};
+      v[j1] = Cplx<R>{fma(x1.re, -sp, tr), fma(x1.im, -sp, ti)};
+    }
+  }
+}
+
+template <typename R, int SB>
+__device__ __forceinline__ void apply_bfly(int s0, Cplx<R> (&v)[1 << SB], const R* ss, uint32_t jmask) {
+  switch (s0) {
+    case 0: bfly<R, SB, 0>(v, ss, jmask); return;
+    case 1: bfly<R, SB, 1>(v, ss, jmask); return;
+    case 2: bfly<R, SB, 2>(v, ss, jmask); return;
+    default: break;
+  }
+  if constexpr (SB > 3)
+    if (s0 == 3) bfly<R, SB, 3>(v, ss, jmask);
+  if constexpr (SB > 4)
+    if (s0 == 4) bfly<R, SB, 4>(v, ss, jmask);
+}
+
 // Slot combinations j (of 2^SB) whose bit k is set, as a 32-bit mask.
 __device__ __forceinline__ uint32_t slot_set_mask(uint32_t k) {
   switch (k) {
@@ -435,10 +477,13 @@ std::vector<BuiltPass> build_passes(const std::vector<PlanOp>& ops, int n, int m
 // with phase1_ops, a phase op on at most one bit becomes TOP_PHASE1 (two factors, no
 // per-thread table lookups)
 // with relabel_swaps, an exact SWAP of two tile bits applies no arithmetic: the pass's
-// later ops name the exchanged bits and the write-out reads the tile accordingly
+// later ops name the exchanged bits and the write-out reads the tile accordingly; with
+// bfly_ops, a 1-qubit matrix s [[1, 1], [1, -1]] becomes TOP_BFLY (kernels that know it;
+// the circuit passes use it for complex128, where FP64 arithmetic bounds the pass)
 template <typename R>
 void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int m, int L, int sb,
-               HostPlan<R>& hp, bool swap_ops = true, bool phase1_ops = true, bool relabel_swaps = false);
+               HostPlan<R>& hp, bool swap_ops = true, bool phase1_ops = true, bool relabel_swaps = false,
+               bool bfly_ops = false);
 // a pass's ops -> register stages (local_of: local bit of each global bit, -1 outside
 // the tile); takes[s] = the ops of stage s, acts[s] = the local bits their targets use
 // (whole_ops: control and phase bits in the tile count as active bits too)
