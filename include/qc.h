@@ -308,7 +308,7 @@ qc_status qc_run_circuit(qc_state* s, const qc_circuit* c, const double* params,
  * parameter l, with psi_l the state after op l and lambda_l = U_{l+1}^dag ... U_L^dag H psi.
  * `params` (host, nparams doubles).  Writes *host_energy and host_grad[nparams].
  * Uses two state buffers of c->n qubits in `dtype` (library workspace, kept between
- * calls).  Complex64 with n >= 12: the reverse sweep runs as tile passes over psi and
+ * calls).  With n >= 12 (both dtypes): the reverse sweep runs as tile passes over psi and
  * lambda together (a recorded rotation's share is added before it is undone);
  * otherwise one kernel per rotation.  Sums in FP64, fixed order (bitwise repeatable).
  * Synchronising. */

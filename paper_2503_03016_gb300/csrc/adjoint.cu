@@ -219,13 +219,11 @@ static qc_status adjoint_impl(const qc_circuit* c, const double* params, int npa
   }
   const int B = 256;
   const unsigned grid = stream_grid(N / 2, B, 8);
-  // complex64 registers of 12 qubits and more take the fused sweep (tile passes over
-  // both states), which writes one partial per rotation and SM; the per-rotation kernels
-  // write one per block of `grid`.  Complex128 keeps the per-rotation kernels: it is
-  // bound by GB300's FP64 rate, and there the fused pass's phase multiplies (a CZ costs a
-  // complex product on half of both states instead of a sign flip on a quarter) outweigh
-  // the saved traffic.
-  const bool fused = sizeof(R) == 4 && n >= adjoint_tiles_min_qubits();
+  // registers of 12 qubits and more take the fused sweep (tile passes over both
+  // states), which writes one partial per rotation and SM; the per-rotation kernels
+  // write one per block of `grid`.  (Complex128 is bound by GB300's FP64 rate either
+  // way; with runs of CZ as sign ops the fused passes still come out ahead.)
+  const bool fused = n >= adjoint_tiles_min_qubits();
   const unsigned pg = std::max<unsigned>(grid, unsigned(device_sm_count()));
   const size_t pbytes = sizeof(double) * (size_t(std::max(nrot, 1)) * pg + 2 * grid + 2 + nparams) + sizeof(int) * (nrot + 1);
   const size_t need = 2 * sbytes + ((pbytes + 255) & ~size_t(255)) + 256;
