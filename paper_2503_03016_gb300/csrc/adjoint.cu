@@ -257,7 +257,10 @@ static qc_status adjoint_impl(const qc_circuit* c, const double* params, int npa
   qc_status st = QC_OK;
   // forward
   if ((st = qc_state_init_basis(&s, 0))) goto done;
-  if ((st = n >= 10 ? run_fused(&s, c, params, QC_PREC_NATIVE) : run_per_gate(&s, c, params))) goto done;
+  // (the energy and the gradient do not see the forward state's global phase)
+  if ((st = n >= 10 ? run_fused(&s, c, params, QC_PREC_NATIVE, /*drop_global_phase=*/true)
+                    : run_per_gate(&s, c, params)))
+    goto done;
   {
     // lambda = H psi, grouped by X mask
     std::map<uint64_t, std::vector<int>> groups;

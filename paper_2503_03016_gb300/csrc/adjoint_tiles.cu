@@ -270,6 +270,10 @@ qc_status adjoint_reverse_tiles(int n, const std::vector<ResolvedOp>& rev, const
   }
   std::vector<PlanOp> pops;
   to_plan_ops(rev, pops, &grad, &gen);
+  // psi and lambda take every op together, so a global phase of an op multiplies both
+  // and cancels in Im<lambda|G|psi>: leave it out (a Z rotation then changes only the
+  // amplitudes whose bit reads 1)
+  drop_global_phases(pops);
   const std::vector<BuiltPass> bps = build_passes(pops, n, m, L);
   HostPlan<R> hp;
   for (const BuiltPass& bp : bps) emit_pass<R>(bp, pops, n, m, L, S::SB, hp, /*swap_ops=*/false);

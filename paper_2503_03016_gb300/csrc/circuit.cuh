@@ -32,7 +32,10 @@ struct KqSpec {
 qc_status resolve_op(const qc_circuit* c, const qc_op& op, const double* params, ResolvedOp* out);
 qc_status apply_resolved(qc_state* s, const ResolvedOp& r);
 qc_status run_per_gate(qc_state* s, const qc_circuit* c, const double* params);
-qc_status run_fused(qc_state* s, const qc_circuit* c, const double* params, qc_prec prec);
+// drop_global_phase: the constant of every unconditioned phase op is left out (the
+// result differs by a global phase; for callers that only form expectation values)
+qc_status run_fused(qc_state* s, const qc_circuit* c, const double* params, qc_prec prec,
+                    bool drop_global_phase = false);
 // complex64 tile passes whose stages run as 32 x 32 blocks on the tensor cores (TF32x3);
 // *handled is false (nothing applied) when a stage's op depends on bits outside its slots
 qc_status run_tiles_tc(qc_state* s, const std::vector<ResolvedOp>& rops, bool* handled);

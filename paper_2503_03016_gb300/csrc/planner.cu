@@ -842,6 +842,22 @@ void emit_pass(const BuiltPass& bp0, const std::vector<PlanOp>& pops0, int n, in
             op.zloc = int8_t(lb);
             op.zglob = int8_t(bbit);
           }
+          if (c == 0.0 && nbeta == 1 && !((p.cmask >> bbit) & 1)) {
+            // e^{ic} = 1: only the amplitudes whose bit reads 1 change (a further
+            // condition on that bit: its slot combinations, its lane, or the tile number)
+            if (op.s0 >= 0) {
+              uint32_t keep = 0;
+              for (int jj = 0; jj < (1 << sb); ++jj)
+                if ((jj >> op.s0) & 1) keep |= 1u << jj;
+              op.jmask &= keep;
+            } else if (lb >= 0) {
+              op.lmask |= 1u << lb;
+              op.lval |= 1u << lb;
+            } else {
+              op.gmask |= uint64_t(1) << bbit;
+              op.gval |= uint64_t(1) << bbit;
+            }
+          }
           hp.ops.push_back(op);
           continue;
         }
@@ -921,12 +937,13 @@ struct TileShape<double> {
 };
 
 template <typename R>
-static qc_status run_tiles(qc_state* s, const std::vector<ResolvedOp>& rops, int m) {
+static qc_status run_tiles(qc_state* s, const std::vector<ResolvedOp>& rops, int m, bool drop_global_phase) {
   const int n = s->n;
   const int L = sizeof(R) == 4 ? 4 : 3;
   constexpr int SB = TileShape<R>::SB;
   std::vector<PlanOp> pops;
   to_plan_ops(rops, pops);
+  if (drop_global_phase) drop_global_phases(pops);
   std::vector<BuiltPass> bps = build_passes(pops, n, m, L);
   HostPlan<R> hp;
   // complex128 applies an exact SWAP as a register permutation; in the complex64
@@ -991,7 +1008,12 @@ int tile_bits_for(const qc_state* s) {
   return std::min(want, s->n);
 }
 
-qc_status run_fused(qc_state* s, const qc_circuit* c, const double* params, qc_prec prec) {
+void drop_global_phases(std::vector<PlanOp>& pops) {
+  for (PlanOp& p : pops)
+    if (p.phase && p.cmask == 0) p.c = 0.0;
+}
+
+qc_status run_fused(qc_state* s, const qc_circuit* c, const double* params, qc_prec prec, bool drop_global_phase) {
   std::vector<ResolvedOp> rops(c->nops);
   for (int i = 0; i < c->nops; ++i)
     if (qc_status st = resolve_op(c, c->ops[i], params, &rops[i])) return st;
@@ -1006,7 +1028,8 @@ qc_status run_fused(qc_state* s, const qc_circuit* c, const double* params, qc_p
     g_last_stage_count = 0;
     return run_per_gate(s, c, params);
   }
-  return s->dtype == QC_C64 ? run_tiles<float>(s, rops, m) : run_tiles<double>(s, rops, m);
+  return s->dtype == QC_C64 ? run_tiles<float>(s, rops, m, drop_global_phase)
+                            : run_tiles<double>(s, rops, m, drop_global_phase);
 }
 
 template <typename R>

@@ -469,6 +469,8 @@ extern int g_last_stage_count;
 // rotations stay dense, Z rotations become phase ops)
 void to_plan_ops(const std::vector<ResolvedOp>& in, std::vector<PlanOp>& out, const std::vector<int>* grad = nullptr,
                  const std::vector<int>* gen = nullptr);
+// sets the constant of every unconditioned phase op to 0 (a global phase)
+void drop_global_phases(std::vector<PlanOp>& pops);
 // plan ops -> passes of tile bit sets B (m bits, the L lowest always included)
 std::vector<BuiltPass> build_passes(const std::vector<PlanOp>& ops, int n, int m, int L);
 // one pass -> its register stages, tile ops and matrices (sb: stage width); with
