@@ -177,6 +177,9 @@ __global__ void __launch_bounds__(NT, 1) k_adj_pass(R* __restrict__ psi, R* __re
         if (op.type == TOP_DENSE1) {
           apply_dense1<R, SB>(op.s0, v, smat + op.mat, op.jmask);
           apply_dense1<R, SB>(op.s0, w, smat + op.mat, op.jmask);
+        } else if (op.type == TOP_REAL1) {
+          apply_real1<R, SB>(op.s0, v, smat + op.mat, op.jmask);
+          apply_real1<R, SB>(op.s0, w, smat + op.mat, op.jmask);
         } else if (op.type == TOP_DENSE2) {
           apply_dense2<R, SB>(op.s0, op.s1, v, smat + op.mat);
           apply_dense2<R, SB>(op.s0, op.s1, w, smat + op.mat);
@@ -276,7 +279,9 @@ qc_status adjoint_reverse_tiles(int n, const std::vector<ResolvedOp>& rev, const
   drop_global_phases(pops);
   const std::vector<BuiltPass> bps = build_passes(pops, n, m, L);
   HostPlan<R> hp;
-  for (const BuiltPass& bp : bps) emit_pass<R>(bp, pops, n, m, L, S::SB, hp, /*swap_ops=*/false);
+  for (const BuiltPass& bp : bps)
+    emit_pass<R>(bp, pops, n, m, L, S::SB, hp, /*swap_ops=*/false, /*phase1_ops=*/true, /*relabel_swaps=*/false,
+                 /*bfly_ops=*/false, /*real1_ops=*/true);
   g_last_pass_count = int(hp.passes.size());
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t sb = al(hp.stages.size() * sizeof(TileStage));

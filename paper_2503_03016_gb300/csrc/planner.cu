@@ -142,6 +142,8 @@ __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const
           }
         } else if (sizeof(R) == 8 && EXTOPS && op.type == TOP_BFLY) {
           if constexpr (sizeof(R) == 8 && EXTOPS) apply_bfly<R, SB>(op.s0, v, smat + op.mat, op.jmask);
+        } else if (sizeof(R) == 8 && EXTOPS && op.type == TOP_REAL1) {
+          if constexpr (sizeof(R) == 8 && EXTOPS) apply_real1<R, SB>(op.s0, v, smat + op.mat, op.jmask);
         } else if (EXTOPS && op.type == TOP_PHASE1) {
           if constexpr (EXTOPS) {
             const uint32_t fixed =
@@ -606,7 +608,8 @@ static PlanOp renamed(const PlanOp& p, const int* ren) {
 
 template <typename R>
 void emit_pass(const BuiltPass& bp0, const std::vector<PlanOp>& pops0, int n, int m, int L, int sb,
-               HostPlan<R>& hp, bool swap_ops, bool phase1_ops, bool relabel_swaps, bool bfly_ops) {
+               HostPlan<R>& hp, bool swap_ops, bool phase1_ops, bool relabel_swaps, bool bfly_ops,
+               bool real1_ops) {
   TilePass P{};
   P.m = m;
   P.L = L;
@@ -775,6 +778,17 @@ void emit_pass(const BuiltPass& bp0, const std::vector<PlanOp>& pops0, int n, in
         hp.mats.push_back(sv);
         hp.mats.push_back(-sv);
         hp.mats.push_back(-sv);
+      } else if (real1_ops && !p.phase && p.nt == 1 && p.m[1] == 0.0 && p.m[3] == 0.0 && p.m[5] == 0.0 &&
+                 p.m[7] == 0.0) {
+        // a real 2x2 matrix
+        op.type = TOP_REAL1;
+        op.s0 = slot(p.tb[0]);
+        op.s1 = 0;
+        op.mat = int64_t(hp.mats.size()) - P.mat0;
+        for (int e = 0; e < 4; ++e) {
+          hp.mats.push_back(R(p.m[2 * e]));
+          if (sizeof(R) == 4) hp.mats.push_back(R(p.m[2 * e]));
+        }
       } else if (!p.phase) {
         op.type = p.nt == 1 ? TOP_DENSE1 : TOP_DENSE2;
         op.s0 = slot(p.tb[0]);
@@ -915,9 +929,9 @@ void emit_pass(const BuiltPass& bp0, const std::vector<PlanOp>& pops0, int n, in
 }
 
 template void emit_pass<float>(const BuiltPass&, const std::vector<PlanOp>&, int, int, int, int, HostPlan<float>&,
-                               bool, bool, bool, bool);
+                               bool, bool, bool, bool, bool);
 template void emit_pass<double>(const BuiltPass&, const std::vector<PlanOp>&, int, int, int, int, HostPlan<double>&,
-                                bool, bool, bool, bool);
+                                bool, bool, bool, bool, bool);
 
 int g_last_pass_count = 0;  // also set by the fused adjoint sweep
 int g_last_fused_path = 0;
@@ -951,7 +965,7 @@ static qc_status run_tiles(qc_state* s, const std::vector<ResolvedOp>& rops, int
   // dense 4x4 it replaces
   for (const BuiltPass& bp : bps)
     emit_pass<R>(bp, pops, n, m, L, SB, hp, /*swap_ops=*/sizeof(R) == 8, /*phase1_ops=*/true, /*relabel_swaps=*/true,
-                 /*bfly_ops=*/sizeof(R) == 8);
+                 /*bfly_ops=*/sizeof(R) == 8, /*real1_ops=*/sizeof(R) == 8);
   g_last_pass_count = int(hp.passes.size());
   g_last_fused_path = 1;
   g_last_stage_count = int(hp.stages.size());
@@ -984,7 +998,8 @@ static qc_status run_tiles(qc_state* s, const std::vector<ResolvedOp>& rops, int
                       sizeof(uint64_t) * kTileNumberTab + plan_max;
   constexpr int NT = TileShape<R>::NT;
   bool extops = false;
-  for (const TileOp& op : hp.ops) extops |= op.type == TOP_CZSET || op.type == TOP_PHASE1 || op.type == TOP_BFLY;
+  for (const TileOp& op : hp.ops)
+    extops |= op.type == TOP_CZSET || op.type == TOP_PHASE1 || op.type == TOP_BFLY || op.type == TOP_REAL1;
   for (const TilePass& P : hp.passes) extops |= P.permuted != 0;
   auto kern = extops ? k_tile_pass<R, NT, SB, true> : k_tile_pass<R, NT, SB, false>;
   if (qc_status st = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
@@ -1042,7 +1057,7 @@ static void plan_stats(int n, const std::vector<ResolvedOp>& rops, int m, int* p
   HostPlan<R> hp;
   for (const BuiltPass& bp : bps)
     emit_pass<R>(bp, pops, n, m, L, SB, hp, /*swap_ops=*/sizeof(R) == 8, /*phase1_ops=*/true, /*relabel_swaps=*/true,
-                 /*bfly_ops=*/sizeof(R) == 8);
+                 /*bfly_ops=*/sizeof(R) == 8, /*real1_ops=*/sizeof(R) == 8);
   *passes = int(hp.passes.size());
   *stages = int(hp.stages.size());
   *ops = int(hp.ops.size());

@@ -16,7 +16,8 @@ constexpr int kMaxStageBits = 5;  // amplitudes a thread holds per stage: 2^SB, 
 
 enum TileOpType : int32_t {
   TOP_DENSE1 = 0, TOP_DENSE2 = 1, TOP_PHASE = 2, TOP_SWAP = 3, TOP_CZSET = 4, TOP_PHASE1 = 5,
-  TOP_BFLY = 6  // s [[1, 1], [1, -1]] (a Hadamard): a butterfly, no general 2x2 product
+  TOP_BFLY = 6,  // s [[1, 1], [1, -1]] (a Hadamard): a butterfly, no general 2x2 product
+  TOP_REAL1 = 7  // a real 2x2 matrix (a Y rotation, X): real coefficients on complex amplitudes
 };
 
 struct TileOp {
@@ -332,6 +333,53 @@ __device__ __forceinline__ void apply_bfly(int s0, Cplx<R> (&v)[1 << SB], const 
     if (s0 == 4) bfly<R, SB, 4>(v, ss, jmask);
 }
 
+// TOP_REAL1 on slot S0: a real 2x2 matrix [[a, b], [c, d]]: each output is two real
+// multiply-adds per component (complex64: two packed operations, no swapped copies)
+// instead of two complex products.  rm = (a, a, b, b, c, c, d, d) for complex64,
+// (a, b, c, d) for complex128, in the matrix block.
+template <typename R, int SB, int S0>
+__device__ __forceinline__ void real1(Cplx<R> (&v)[1 << SB], const R* __restrict__ rm, uint32_t jmask) {
+  if constexpr (sizeof(R) == 4) {
+    const float4 ab = *reinterpret_cast<const float4*>(rm), cd = *reinterpret_cast<const float4*>(rm + 4);
+    const float2 a = make_float2(ab.x, ab.y), b = make_float2(ab.z, ab.w);
+    const float2 c = make_float2(cd.x, cd.y), d = make_float2(cd.z, cd.w);
+#pragma unroll
+    for (int j = 0; j < (1 << SB); ++j) {
+      if (j & (1 << S0)) continue;
+      if (!((jmask >> j) & 1u)) continue;
+      const int j1 = j | (1 << S0);
+      const float2 x0 = f2(v[j]), x1 = f2(v[j1]);
+      v[j] = c2(__ffma2_rn(x1, b, __fmul2_rn(x0, a)));
+      v[j1] = c2(__ffma2_rn(x1, d, __fmul2_rn(x0, c)));
+    }
+  } else {
+    const R a = rm[0], b = rm[1], c = rm[2], d = rm[3];
+#pragma unroll
+    for (int j = 0; j < (1 << SB); ++j) {
+      if (j & (1 << S0)) continue;
+      if (!((jmask >> j) & 1u)) continue;
+      const int j1 = j | (1 << S0);
+      const Cplx<R> x0 = v[j], x1 = v[j1];
+      v[j] = Cplx<R>{fma(x1.re, b, x0.re * a), fma(x1.im, b, x0.im * a)};
+      v[j1] = Cplx<R>{fma(x1.re, d, x0.re * c), fma(x1.im, d, x0.im * c)};
+    }
+  }
+}
+
+template <typename R, int SB>
+__device__ __forceinline__ void apply_real1(int s0, Cplx<R> (&v)[1 << SB], const R* rm, uint32_t jmask) {
+  switch (s0) {
+    case 0: real1<R, SB, 0>(v, rm, jmask); return;
+    case 1: real1<R, SB, 1>(v, rm, jmask); return;
+    case 2: real1<R, SB, 2>(v, rm, jmask); return;
+    default: break;
+  }
+  if constexpr (SB > 3)
+    if (s0 == 3) real1<R, SB, 3>(v, rm, jmask);
+  if constexpr (SB > 4)
+    if (s0 == 4) real1<R, SB, 4>(v, rm, jmask);
+}
+
 // Slot combinations j (of 2^SB) whose bit k is set, as a 32-bit mask.
 __device__ __forceinline__ uint32_t slot_set_mask(uint32_t k) {
   switch (k) {
@@ -482,10 +530,11 @@ std::vector<BuiltPass> build_passes(const std::vector<PlanOp>& ops, int n, int m
 // later ops name the exchanged bits and the write-out reads the tile accordingly; with
 // bfly_ops, a 1-qubit matrix s [[1, 1], [1, -1]] becomes TOP_BFLY (kernels that know it;
 // the circuit passes use it for complex128, where FP64 arithmetic bounds the pass)
+// with real1_ops, a real 1-qubit matrix becomes TOP_REAL1 (kernels that know it)
 template <typename R>
 void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int m, int L, int sb,
                HostPlan<R>& hp, bool swap_ops = true, bool phase1_ops = true, bool relabel_swaps = false,
-               bool bfly_ops = false);
+               bool bfly_ops = false, bool real1_ops = false);
 // a pass's ops -> register stages (local_of: local bit of each global bit, -1 outside
 // the tile); takes[s] = the ops of stage s, acts[s] = the local bits their targets use
 // (whole_ops: control and phase bits in the tile count as active bits too)
