@@ -9,7 +9,7 @@
 // lives in a per-block global buffer and each layer is two tile passes of 2^13
 // amplitudes (the 13 low index bits, then the remaining high bits plus enough low bits
 // for 512-byte runs).  Within a tile, register stages of SB bits apply the layer's
-// fused 2x2 gates U = RZ(t') RY(t); the CZ chain is the diagonal (-1)^popc(i & i>>1)
+// fused 2x2 gates U = RZ(t') RY(t) (up to a global phase); the CZ chain is the diagonal (-1)^popc(i & i>>1)
 // and Z_iZ_{i+1} the sign (n-1) - 2 popc((i ^ i>>1) & (2^(n-1)-1)) of index i, both
 // folded into the last stage.  The stage width SB (the fusion width) is chosen by the
 // autotuner; the launch is recorded once in a CUDA graph and replayed.
@@ -45,26 +45,27 @@ __device__ __forceinline__ uint32_t bswz(uint32_t r) {
   return r ^ ((x ^ (x >> 4) ^ (x >> 8)) & 15u);
 }
 
-// fused layer gate of qubit q: U = RZ(t') RY(t), (c,s) = cos/sin(t/2), e = exp(-i t'/2).
-// Entry e (00, 01, 10, 11) u = (ur, ui) is kept as the packed pairs a = (ur, ur) and
-// b = (-ui, ui), so that u x = a * (xr, xi) + b * (xi, xr): two packed FMAs.
+// Fused layer gate of qubit q: U = RZ(t') RY(t) up to its global phase e^{-it'/2}, which
+// no output of the batch sees (each circuit yields <sum Z_i Z_i+1>): U' = diag(1, e) RY(t)
+// with e = e^{it'}, RY(t) = [[c, -s], [s, c]], (c, s) = cos/sin(t/2).  Row 0 is real;
+// row 1 is e times a real combination.  Kept as packed pairs: cc = (c, c), ms = (-s, -s),
+// ss = (s, s), er = (Re e, Re e), ei = (-Im e, Im e), so that per pair
+//   out0 = cc x0 + ms x1,   t = ss x0 + cc x1,   out1 = er t + ei (t_im, t_re):
+// six packed operations, against eight for a general complex 2x2.
 struct GateP {
-  float2 a[4], b[4];
+  float2 cc, ms, ss, er, ei;
 };
 
 __device__ __forceinline__ GateP layer_gate(const float* p) {
   float s, c, sz, cz;
   sincosf(0.5f * p[0], &s, &c);
-  sincosf(0.5f * p[1], &sz, &cz);
-  // RZ = diag(cz - i sz, cz + i sz); RY = [[c, -s], [s, c]]
-  const float ur[4] = {cz * c, -cz * s, cz * s, cz * c};
-  const float ui[4] = {-sz * c, sz * s, sz * s, sz * c};
+  sincosf(p[1], &sz, &cz);
   GateP g;
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    g.a[e] = make_float2(ur[e], ur[e]);
-    g.b[e] = make_float2(-ui[e], ui[e]);
-  }
+  g.cc = make_float2(c, c);
+  g.ms = make_float2(-s, -s);
+  g.ss = make_float2(s, s);
+  g.er = make_float2(cz, cz);
+  g.ei = make_float2(-sz, sz);
   return g;
 }
 
@@ -109,15 +110,15 @@ __device__ __forceinline__ void batch_stage(Cplx<float>* buf, int nl, const int8
     for (int k = 0; k < SB; ++k) {
       if (slot_q[k] < 0) continue;
       const GateP& u = gates[slot_q[k]];
-      const float2 a00 = u.a[0], a01 = u.a[1], a10 = u.a[2], a11 = u.a[3];
-      const float2 b00 = u.b[0], b01 = u.b[1], b10 = u.b[2], b11 = u.b[3];
+      const float2 cc = u.cc, ms = u.ms, ss = u.ss, er = u.er, ei = u.ei;
 #pragma unroll
       for (int j = 0; j < NA; ++j) {
         if (j & (1 << k)) continue;
         const int j1 = j | (1 << k);
-        const float2 x = f2(v[j]), xs = f2swap(v[j]), y = f2(v[j1]), ys = f2swap(v[j1]);
-        v[j] = c2(__ffma2_rn(b01, ys, __ffma2_rn(a01, y, __ffma2_rn(b00, xs, __fmul2_rn(a00, x)))));
-        v[j1] = c2(__ffma2_rn(b11, ys, __ffma2_rn(a11, y, __ffma2_rn(b10, xs, __fmul2_rn(a10, x)))));
+        const float2 x = f2(v[j]), y = f2(v[j1]);
+        const float2 t = __ffma2_rn(cc, y, __fmul2_rn(ss, x));
+        v[j] = c2(__ffma2_rn(ms, y, __fmul2_rn(cc, x)));
+        v[j1] = c2(__ffma2_rn(ei, make_float2(t.y, t.x), __fmul2_rn(er, t)));
       }
     }
     if (phase || zz) {
