@@ -455,48 +455,74 @@ std::vector<BuiltPass> build_passes(const std::vector<PlanOp>& ops, int n, int m
 // order.  takes[s]: the ops of stage s; acts[s]: the local bits their targets occupy.
 // With whole_ops, an op's in-tile control and phase bits count as active bits too (a
 // stage applied as one block must see every bit its ops depend on).
+// One stage over `rest` (in order): an op is taken if the local bits it needs join the
+// stage's set without exceeding sb bits (with `fixed` >= 0: stay inside that set of
+// local bits) and no skipped op it fails to commute with precedes it.
+static void stage_sweep(const std::vector<int>& rest, const std::vector<PlanOp>& pops, const int* local_of, int sb,
+                        bool whole_ops, int64_t fixed, std::vector<int>& take, std::vector<int>& skip,
+                        std::vector<int>& act) {
+  take.clear();
+  skip.clear();
+  act.clear();
+  uint64_t blocked_all = 0, blocked_diag = 0;
+  for (int idx : rest) {
+    const PlanOp& p = pops[idx];
+    bool ok = (p.touched & blocked_all) == 0;
+    if (ok && !p.phase) ok = (p.touched & blocked_diag) == 0;
+    if (ok && (whole_ops || !p.phase)) {
+      std::vector<int> nw = act;
+      bool outside = false;
+      auto add = [&](int gbit) {
+        const int lb = local_of[gbit];
+        if (lb < 0) return;
+        if (fixed >= 0 && !((fixed >> lb) & 1)) outside = true;
+        if (std::find(nw.begin(), nw.end(), lb) == nw.end()) nw.push_back(lb);
+      };
+      if (!p.phase)
+        for (int k = 0; k < p.nt; ++k) add(p.tb[k]);
+      if (whole_ops) {
+        for (int b = 0; b < 64; ++b)
+          if ((p.cmask >> b) & 1) add(b);
+        for (const auto& be : p.beta) add(be.first);
+      }
+      if (outside || int(nw.size()) > sb)
+        ok = false;
+      else
+        act = nw;
+    }
+    if (ok) {
+      take.push_back(idx);
+    } else {
+      skip.push_back(idx);
+      if (p.phase)
+        blocked_diag |= p.touched;
+      else
+        blocked_all |= p.touched;
+    }
+  }
+}
+
 void split_stages(const BuiltPass& bp, const std::vector<PlanOp>& pops, const int* local_of, int sb,
                   std::vector<std::vector<int>>& takes, std::vector<std::vector<int>>& acts, bool whole_ops) {
+  int m = 0;
+  for (int b = 0; b < 64; ++b) m = std::max(m, local_of[b] + 1);
   std::vector<int> rest = bp.ops;
+  std::vector<int> take, skip, act, btake, bskip, bact;
   while (!rest.empty()) {
-    std::vector<int> act;
-    std::vector<int> take, skip;
-    uint64_t blocked_all = 0, blocked_diag = 0;
-    for (int idx : rest) {
-      const PlanOp& p = pops[idx];
-      bool ok = (p.touched & blocked_all) == 0;
-      if (ok && !p.phase) ok = (p.touched & blocked_diag) == 0;
-      if (ok && (whole_ops || !p.phase)) {
-        std::vector<int> nw = act;
-        auto add = [&](int gbit) {
-          const int lb = local_of[gbit];
-          if (lb >= 0 && std::find(nw.begin(), nw.end(), lb) == nw.end()) nw.push_back(lb);
-        };
-        if (!p.phase)
-          for (int k = 0; k < p.nt; ++k) add(p.tb[k]);
-        if (whole_ops) {
-          for (int b = 0; b < 64; ++b)
-            if ((p.cmask >> b) & 1) add(b);
-          for (const auto& be : p.beta) add(be.first);
-        }
-        if (int(nw.size()) > sb)
-          ok = false;
-        else
-          act = nw;
-      }
-      if (ok) {
-        take.push_back(idx);
-      } else {
-        skip.push_back(idx);
-        if (p.phase)
-          blocked_diag |= p.touched;
-        else
-          blocked_all |= p.touched;
+    // candidates: the growing first-fit set, and every window of sb neighbouring local
+    // bits; the one that takes the most ops wins (the first-fit set on ties)
+    stage_sweep(rest, pops, local_of, sb, whole_ops, -1, btake, bskip, bact);
+    for (int w = 0; w + sb <= m; ++w) {
+      stage_sweep(rest, pops, local_of, sb, whole_ops, ((int64_t(1) << sb) - 1) << w, take, skip, act);
+      if (take.size() > btake.size()) {
+        btake.swap(take);
+        bskip.swap(skip);
+        bact.swap(act);
       }
     }
-    takes.push_back(take);
-    acts.push_back(act);
-    rest.swap(skip);
+    takes.push_back(btake);
+    acts.push_back(bact);
+    rest.swap(bskip);
   }
 }
 
