@@ -299,9 +299,11 @@ def run_ours(args):
         flops = stages * 768.0 * (1 << N_QUBITS)
         tf32_peak = bf16_tflops * 1.1 / 2.25
         achieved = flops / (circ_ms * 1e-3) / 1e12
+        # DRAM bytes of one tensor-core tile pass in an ncu capture at 26 qubits
+        # (1013.25 MB), scaled by the larger state
         roof = {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
-                "frac": achieved / tf32_peak, "traffic": None,
-                "traffic_note": "not captured for this kernel at this size",
+                "frac": achieved / tf32_peak, "traffic": 1013.248768e6 * (1 << (N_QUBITS - 26)),
+                "traffic_note": "per pass, ncu at 26 qubits scaled by 2^(n-26)",
                 "peak_source": "%s bf16 x 1.1/2.25 (nominal dense TF32/BF16 ratio)" % peak_src,
                 "kernel": "k_tile_pass_tc", "passes": passes, "stages": stages,
                 "gate_tflops_fp32_equivalent": len(ops) * 32.0 * (1 << N_QUBITS) / (circ_ms * 1e-3) / 1e12}
