@@ -405,8 +405,9 @@ def run_batch_bench(args):
 
 
 def run_block_bench(args):
-    """Opt-in secondary measurement: one dense 5-qubit block (Haar 32x32) on a 28-qubit
-    complex64 state, CUDA-core FMA (k_kq_native) vs tensor cores (TF32x3, k_block_tc)."""
+    """Opt-in secondary measurement: one dense 5-qubit block (Haar 32x32) and one dense
+    6-qubit block (Haar 64x64) on a 28-qubit complex64 state, CUDA-core FMA (k_kq_native)
+    vs tensor cores (TF32x3: k_block_tc, k_block_tc6)."""
     import torch
 
     import paper_2503_03016_gb300 as P
@@ -415,28 +416,30 @@ def run_block_bench(args):
     hbm, bf16, _ = peaks()
     tf32_peak = bf16 * 1.1 / 2.25
     st = P.State(n, "c64").init_gaussian(7)
-    U = W.haar_unitaries(1, 32, 11)[0]
-    qs = [3, 9, 14, 20, n - 2]
     stream = torch.cuda.current_stream()
     res = {}
-    for name, prec in (("native", P.QC_PREC_NATIVE), ("tf32x3", P.QC_PREC_TF32X3)):
-        for _ in range(max(args.warmup, 1)):
-            P.qc_apply_fused_k(st.handle, qs, U, prec)
-        torch.cuda.synchronize()
-        t = StreamTimer(stream)
-        t.start()
-        for _ in range(args.steps):
-            P.qc_apply_fused_k(st.handle, qs, U, prec)
-        ms = t.stop() / args.steps
-        flops = 8.0 * 32 * (1 << n) * (3 if prec == P.QC_PREC_TF32X3 else 1)
-        gbs = 2 * 8 * (1 << n) / (ms * 1e-3) / 1e9
-        tf = flops / (ms * 1e-3) / 1e12
-        res[name] = {"ms": ms, "gbs": gbs, "frac_hbm": gbs / hbm, "tflops": tf}
-        if prec == P.QC_PREC_TF32X3:
-            res[name]["frac_tf32"] = tf / tf32_peak
-        else:
-            res[name]["frac_alu"] = tf / ALU_PEAK_TF
-    print(json.dumps({"metric": "fused 5-qubit block on %d qubits" % n, "results": res,
+    for k, qs in ((5, [3, 9, 14, 20, n - 2]), (6, [3, 9, 14, 20, 23, n - 2])):
+        U = W.haar_unitaries(1, 1 << k, 11)[0]
+        for name, prec in (("native", P.QC_PREC_NATIVE), ("tf32x3", P.QC_PREC_TF32X3)):
+            for _ in range(max(args.warmup, 1)):
+                P.qc_apply_fused_k(st.handle, qs, U, prec)
+            torch.cuda.synchronize()
+            t = StreamTimer(stream)
+            t.start()
+            for _ in range(args.steps):
+                P.qc_apply_fused_k(st.handle, qs, U, prec)
+            ms = t.stop() / args.steps
+            # 2^k complex multiply-adds per amplitude, 8 flops each (x3 for the split)
+            flops = 8.0 * (1 << k) * (1 << n) * (3 if prec == P.QC_PREC_TF32X3 else 1)
+            gbs = 2 * 8 * (1 << n) / (ms * 1e-3) / 1e9
+            tf = flops / (ms * 1e-3) / 1e12
+            r = {"ms": ms, "gbs": gbs, "frac_hbm": gbs / hbm, "tflops": tf}
+            if prec == P.QC_PREC_TF32X3:
+                r["frac_tf32"] = tf / tf32_peak
+            else:
+                r["frac_alu"] = tf / ALU_PEAK_TF
+            res["k%d_%s" % (k, name)] = r
+    print(json.dumps({"metric": "fused 5- and 6-qubit blocks on %d qubits" % n, "results": res,
                       "peaks": {"hbm_gbs": hbm, "tf32_tflops": tf32_peak, "alu_tflops": ALU_PEAK_TF,
                                 "tf32_source": "measured bf16 x 1.1/2.25 (nominal TF32/BF16 dense ratio)"}}))
 

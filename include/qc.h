@@ -149,7 +149,8 @@ qc_status qc_apply_ctrl(qc_state* s, const int* ctrls, const int* ctrl_states, i
                         const double U[8]);
 
 /* A dense 2^k x 2^k block on qubits[0..k-1] (qubits[0] = MSB of the block index),
- * 1 <= k <= 7 (QC_PREC_TF32X3: 2 <= k <= 6).  The product of consecutive gates that
+ * 1 <= k <= 7 (QC_PREC_TF32X3: 2 <= k <= 6, complex64, n >= k_eff + 7 where k_eff = 5
+ * for k <= 5 (padded with identity qubits) and 6 for k = 6).  The product of consecutive gates that
  * act on at most k qubits (gate fusion). */
 qc_status qc_apply_fused_k(qc_state* s, const int* qubits, int k, const double* U, qc_prec prec);
 

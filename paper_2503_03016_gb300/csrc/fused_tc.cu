@@ -187,10 +187,158 @@ __global__ void __launch_bounds__(kTcRows, 1) k_block_tc(float* __restrict__ amp
   (void)lane;
 }
 
-// host: real form of U on 5 qubits (k < 5 padded with identity qubits), split hi / lo
-static void tc_bmatrix(const std::vector<double>& U5, std::vector<float>& out) {
-  const int D = 1 << kTcK;
-  out.assign(2 * kTcCols * kTcCols, 0.0f);
+// Six-qubit blocks (k = 6): rows of 64 amplitudes, K = N = 128 real columns.  B (128 x
+// 128, hi and lo: 128 KiB) stays in shared memory for the launch; A would need another
+// 128 KiB, so it passes through one 64 KiB buffer in two K halves: the threads holding
+// block-index bit 5 = 0 store their half of every row (K slices 0, 1), one thread issues
+// that half's 3 x 8 products (M = N = 128, K = 8) into the accumulator, and after they
+// complete the other threads store K slices 2, 3 for the second half.  256 threads, two
+// per row (thread t: row t mod 128, block-index bit 5 = t / 128).
+constexpr int k6K = 6;
+constexpr int k6Cols = 2 << k6K;                    // 128
+constexpr int k6Aregion = kTcRows * 128;            // one K slice of A: 16 KiB
+constexpr int k6Bregion = k6Cols * 128;             // one K slice of B: 16 KiB
+constexpr int k6Smem = 2 * 2 * k6Aregion /* A_hi, A_lo: two slices each */ +
+                       2 * 4 * k6Bregion /* B_hi, B_lo: four slices each */ + 1024 + 1024;
+
+__global__ void __launch_bounds__(2 * kTcRows, 1) k_block_tc6(float* __restrict__ amps, uint64_t ntiles,
+                                                              const float* __restrict__ bsplit,
+                                                              int* __restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  unsigned char* a_hi = base;
+  unsigned char* a_lo = a_hi + 2 * k6Aregion;
+  unsigned char* b_hi = a_lo + 2 * k6Aregion;
+  unsigned char* b_lo = b_hi + 4 * k6Bregion;
+  uint64_t* offs = reinterpret_cast<uint64_t*>(b_lo + 4 * k6Bregion);  // 64 column offsets
+  uint64_t* bar = offs + 64;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bar + 1);
+  int8_t* spos = reinterpret_cast<int8_t*>(tmem_slot + 1);
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int row = tid & (kTcRows - 1), half = tid >> 7;
+
+  for (int i = tid; i < k6Cols * k6Cols; i += blockDim.x) {
+    const int n = i / k6Cols, k = i % k6Cols;
+    *reinterpret_cast<float*>(b_hi + sw128_offset(n, k, k6Cols)) = bsplit[i];
+    *reinterpret_cast<float*>(b_lo + sw128_offset(n, k, k6Cols)) = bsplit[k6Cols * k6Cols + i];
+  }
+  const uint64_t* goffs = reinterpret_cast<const uint64_t*>(bsplit + 2 * k6Cols * k6Cols);
+  const int* gpos = reinterpret_cast<const int*>(goffs + 64);
+  if (tid < 64) offs[tid] = goffs[tid];
+  if (tid < k6K) spos[tid] = int8_t(gpos[tid]);
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(tmem_slot)),
+                 "r"(k6Cols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  constexpr uint32_t idesc = tf32_idesc(kTcRows, k6Cols);
+  uint32_t phase = 0;
+  bool failed = false;
+  auto hi = [](float v) { return __uint_as_float(__float_as_uint(v) & 0xFFFFE000u); };
+
+  // software pipeline, two tiles deep (as for five-qubit blocks): once a thread's half
+  // row of tile t is in the A buffer, its register buffer is refilled with tile t + 2 grid
+  const uint64_t G = gridDim.x;
+  auto gather = [&](float2 (&x)[32], uint64_t& rb, uint64_t t) {
+    rb = insert_zero_bits(t * kTcRows + row, spos, k6K);
+#pragma unroll
+    for (int j = 0; j < 32; ++j) x[j] = reinterpret_cast<const float2*>(amps)[rb | offs[32 * half + j]];
+  };
+  auto step = [&](float2 (&x)[32], uint64_t& rb, uint64_t t) {
+    const uint64_t rb_cur = rb;
+    for (int h = 0; h < 2 && !failed; ++h) {
+      if (half == h) {
+        // K columns 64 h .. 64 h + 63 of this row: slices 0 and 1 of the A buffer
+#pragma unroll
+        for (int c = 0; c < 16; ++c) {
+          const float2 u = x[2 * c], v = x[2 * c + 1];
+          const float4 hv = make_float4(hi(u.x), hi(u.y), hi(v.x), hi(v.y));
+          const uint32_t o = sw128_offset(row, 4 * c, kTcRows);
+          *reinterpret_cast<float4*>(a_hi + o) = hv;
+          *reinterpret_cast<float4*>(a_lo + o) = make_float4(u.x - hv.x, u.y - hv.y, v.x - hv.z, v.y - hv.w);
+        }
+        if (t + 2 * G < ntiles) gather(x, rb, t + 2 * G);  // the buffer is free
+      }
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+      if (tid == 0) {
+        const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo), bh = smem_u32(b_hi), bl = smem_u32(b_lo);
+        for (int prod = 0; prod < 3; ++prod) {
+          const uint32_t A = prod == 2 ? al : ah;
+          const uint32_t B = prod == 1 ? bl : bh;
+          for (int ks = 0; ks < 8; ++ks) {
+            const uint32_t koff = uint32_t((ks & 3) * 32);
+            const uint64_t ad = sw128_desc(A + (ks >> 2) * k6Aregion + koff, kTcAtom);
+            const uint64_t bd = sw128_desc(B + (2 * h + (ks >> 2)) * k6Bregion + koff, kTcAtom);
+            tc_mma(tmem, ad, bd, idesc, (h == 0 && prod == 0 && ks == 0) ? 0u : 1u);
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                         smem_u32(bar))
+                     : "memory");
+      }
+      // bounded wait for this half's products (they read the A buffer the next half
+      // overwrites, and the accumulator the epilogue reads)
+      uint32_t done = 0;
+      for (long long it = 0; it < kTcSpinLimit; ++it) {
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(phase)
+            : "memory");
+        if (done) break;
+      }
+      phase ^= 1u;
+      failed = __syncthreads_or(done ? 0 : 1) != 0;
+      if (failed && tid == 0) atomicExch(status, 1);
+      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    }
+    if (failed) return;
+    // row `row` of D, the 64 columns of this thread's outputs (block index 32 half + j)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      uint32_t r[16];
+      tmem_ld16(tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(64 * half + 16 * q), r);
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+        reinterpret_cast<float2*>(amps)[rb_cur | offs[32 * half + 8 * q + i]] =
+            make_float2(__uint_as_float(r[2 * i]), __uint_as_float(r[2 * i + 1]));
+    }
+    // the epilogue's TMEM reads end before the next tile's products overwrite D
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    failed = __syncthreads_or(*((volatile int*)status) != 0) != 0;
+  };
+  float2 xa[32], xb[32];
+  uint64_t rba = 0, rbb = 0;
+  const uint64_t t0 = blockIdx.x;
+  if (t0 < ntiles) gather(xa, rba, t0);
+  if (t0 + G < ntiles) gather(xb, rbb, t0 + G);
+  for (uint64_t t = t0; t < ntiles && !failed; t += 2 * G) {
+    step(xa, rba, t);
+    if (t + G < ntiles && !failed) step(xb, rbb, t + G);
+  }
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(k6Cols) : "memory");
+}
+
+// host: real form of U on kq qubits (row-major Bt[n][k], 2^(kq+1) columns), split hi / lo
+static void tc_bmatrix(const std::vector<double>& U5, std::vector<float>& out, int kq = kTcK) {
+  const int D = 1 << kq, C = 2 << kq;
+  out.assign(2 * C * C, 0.0f);
   auto hi_of = [](float v) {
     uint32_t u;
     memcpy(&u, &v, 4);
@@ -208,13 +356,70 @@ static void tc_bmatrix(const std::vector<double>& U5, std::vector<float>& out) {
       const int ks[4] = {2 * c, 2 * c + 1, 2 * c, 2 * c + 1};
       for (int e = 0; e < 4; ++e) {
         const float v = vals[e], h = hi_of(v);
-        out[ns[e] * kTcCols + ks[e]] = h;
-        out[kTcCols * kTcCols + ns[e] * kTcCols + ks[e]] = v - h;
+        out[ns[e] * C + ks[e]] = h;
+        out[C * C + ns[e] * C + ks[e]] = v - h;
       }
     }
 }
 
+// k = 6: the whole 64 x 64 block (no padding) through k_block_tc6
+static qc_status apply_k6_tf32x3(qc_state* s, const int* bits, const double* U) {
+  if (s->dtype != QC_C64 || s->n < k6K + 7) {
+    set_error("TF32x3 six-qubit blocks need complex64 and n >= %d", k6K + 7);
+    return QC_ERR_UNSUPPORTED;
+  }
+  constexpr int D = 1 << k6K;
+  std::vector<double> U6(U, U + 2 * D * D);
+  std::vector<float> bs;
+  tc_bmatrix(U6, bs, k6K);
+  // column c of a row (block index c, bits[0] its MSB) sits at offset off[c]; rows
+  // enumerate the other bits (zeros inserted at the block's bits, ascending)
+  std::vector<int> sorted(bits, bits + k6K);
+  std::sort(sorted.begin(), sorted.end());
+  {
+    const size_t nb = bs.size();
+    bs.resize(nb + 64 * 2 + k6K);
+    uint64_t o64[64];
+    for (int r = 0; r < D; ++r) {
+      uint64_t off = 0;
+      for (int j = 0; j < k6K; ++j)
+        if ((r >> (k6K - 1 - j)) & 1) off |= uint64_t(1) << bits[j];
+      o64[r] = off;
+    }
+    memcpy(bs.data() + nb, o64, sizeof(o64));
+    int p32[k6K];
+    for (int j = 0; j < k6K; ++j) p32[j] = sorted[j];
+    memcpy(bs.data() + nb + 128, p32, sizeof(p32));
+  }
+  void* scr = nullptr;
+  const size_t bbytes = sizeof(float) * bs.size();
+  if (qc_status st = state_scratch(s, 256 + bbytes, &scr)) return st;
+  int* status = reinterpret_cast<int*>(scr);
+  float* dB = reinterpret_cast<float*>(static_cast<char*>(scr) + 256);
+  if (qc_status st = check_cuda(cudaMemsetAsync(status, 0, sizeof(int), s->stream), "status reset")) return st;
+  if (qc_status st = check_cuda(cudaMemcpyAsync(dB, bs.data(), bbytes, cudaMemcpyHostToDevice, s->stream), "B upload"))
+    return st;
+  if (qc_status st = check_cuda(cudaFuncSetAttribute(k_block_tc6, cudaFuncAttributeMaxDynamicSharedMemorySize, k6Smem),
+                                "tc6 smem"))
+    return st;
+  const uint64_t ntiles = (state_len(s) >> k6K) / kTcRows;
+  const unsigned grid = unsigned(std::min<uint64_t>(ntiles, uint64_t(device_sm_count())));
+  QC_COUNT(), k_block_tc6<<<grid, 2 * kTcRows, k6Smem, s->stream>>>(reinterpret_cast<float*>(s->amps), ntiles, dB,
+                                                                    status);
+  if (qc_status st = check_launch("tensor-core six-qubit block")) return st;
+  int h = 0;
+  if (qc_status st = check_cuda(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s->stream), "status"))
+    return st;
+  if (qc_status st = check_cuda(cudaStreamSynchronize(s->stream), "tensor-core six-qubit block")) return st;
+  if (h != 0) {
+    set_error("tensor-core block: a bounded wait for the MMA completion ran out");
+    return QC_ERR_TIMEOUT;
+  }
+  return QC_OK;
+}
+
 qc_status apply_kq_tf32x3(qc_state* s, const int* bits, int k, const double* U) {
+  if (k == k6K) return apply_k6_tf32x3(s, bits, U);
   if (s->dtype != QC_C64 || k < 1 || k > kTcK || s->n < kTcK + 7) {
     set_error("TF32x3 blocks need complex64, k <= %d and n >= %d", kTcK, kTcK + 7);
     return QC_ERR_UNSUPPORTED;

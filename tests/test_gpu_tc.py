@@ -29,9 +29,10 @@ def test_tc_identity_within_split_error():
     assert err.max() < 2.0 ** -21, err.max()
 
 
-@pytest.mark.parametrize("n", [12, 14])
-@pytest.mark.parametrize("k", [2, 3, 4, 5])
+@pytest.mark.parametrize("n,k", [(n, k) for n in (12, 14) for k in (2, 3, 4, 5)] + [(13, 6), (15, 6)])
 def test_tc_block_vs_oracle(n, k):
+    """k <= 5 run as 5-qubit blocks (padded with identity qubits); k = 6 through the
+    six-qubit kernel (two K halves of A through one buffer)."""
     import paper_2503_03016_gb300 as P
     rng = np.random.default_rng(10 * n + k)
     for trial in range(3):
@@ -45,6 +46,27 @@ def test_tc_block_vs_oracle(n, k):
         assert rel_l2(st.numpy(), want) <= 1e-5, (qs, rel_l2(st.numpy(), want))
 
 
+def test_tc_six_qubit_identity_and_low_bits():
+    """A six-qubit identity block returns the state within the split error, and a block
+    on the six lowest index bits (whole rows contiguous) matches the oracle."""
+    import paper_2503_03016_gb300 as P
+    n = 14
+    psi = W.random_state(n, 3).astype(np.complex64)
+    st = gpu_state(psi, "c64")
+    P.qc_apply_fused_k(st.handle, [1, 4, 6, 9, 12, 13], np.eye(64), P.QC_PREC_TF32X3)
+    got = st.numpy()
+    err = np.abs(got - psi) / np.maximum(np.abs(psi), 1e-30)
+    assert err.max() < 2.0 ** -20, err.max()
+    U = W.haar_unitaries(1, 64, 77)[0]
+    qs = list(range(n - 6, n))
+    psi = W.random_state(n, 4)
+    st = gpu_state(psi, "c64")
+    P.qc_apply_fused_k(st.handle, qs, U, P.QC_PREC_TF32X3)
+    want = psi.copy()
+    oracle.apply_kq(want, qs, U)
+    assert rel_l2(st.numpy(), want) <= 1e-5
+
+
 def test_tc_rejects_unsupported():
     import paper_2503_03016_gb300 as P
     st = gpu_state(W.random_state(12, 0), "c128")
@@ -53,3 +75,6 @@ def test_tc_rejects_unsupported():
     st = gpu_state(W.random_state(10, 0), "c64")
     with pytest.raises(P.QCError):
         P.qc_apply_fused_k(st.handle, [0, 1], np.eye(4), P.QC_PREC_TF32X3)
+    st = gpu_state(W.random_state(12, 0), "c64")  # six-qubit blocks need n >= 13
+    with pytest.raises(P.QCError):
+        P.qc_apply_fused_k(st.handle, [0, 1, 2, 3, 4, 5], np.eye(64), P.QC_PREC_TF32X3)
