@@ -67,14 +67,14 @@ int qc_abi_version(void);
  * a diagnostic for benchmarks. */
 uint64_t qc_launch_count(void);
 /* Number of tile passes the planner used for the most recent QC_RUN_FUSED circuit or
- * fused adjoint reverse sweep (process-wide; a diagnostic for benchmarks). */
+ * fused adjoint reverse sweep (of the calling thread; a diagnostic for benchmarks). */
 int qc_last_pass_count(void);
-/* How the most recent QC_RUN_FUSED circuit ran (process-wide; a diagnostic): 0 one
+/* How the calling thread's most recent QC_RUN_FUSED circuit ran (a diagnostic): 0 one
  * sweep per gate (fewer than 10 qubits), 1 tile passes on the CUDA cores, 2 tile passes
  * whose stages ran as 32 x 32 blocks on the tensor cores (QC_PREC_TF32X3). */
 int qc_last_fused_path(void);
 /* Register stages (CUDA-core passes) or 32 x 32 stage blocks (tensor-core passes) of
- * the most recent QC_RUN_FUSED circuit (process-wide; a diagnostic). */
+ * the calling thread's most recent QC_RUN_FUSED circuit (a diagnostic). */
 int qc_last_stage_count(void);
 /* Plans circuit `c` as QC_RUN_FUSED would for a state of `dtype` and reports the number
  * of tile passes, register stages and tile ops; host only (no device work, no GPU

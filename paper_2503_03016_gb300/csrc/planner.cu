@@ -959,9 +959,9 @@ template void emit_pass<float>(const BuiltPass&, const std::vector<PlanOp>&, int
 template void emit_pass<double>(const BuiltPass&, const std::vector<PlanOp>&, int, int, int, int, HostPlan<double>&,
                                 bool, bool, bool, bool, bool);
 
-int g_last_pass_count = 0;  // also set by the fused adjoint sweep
-int g_last_fused_path = 0;
-int g_last_stage_count = 0;
+thread_local int g_last_pass_count = 0;  // also set by the fused adjoint sweep
+thread_local int g_last_fused_path = 0;
+thread_local int g_last_stage_count = 0;
 
 // Register stage width SB (a thread holds 2^SB amplitudes) and block size of the tile
 // pass per precision: blockDim = 2^(m - SB) <= NT with m = 13 (complex64) / 12.

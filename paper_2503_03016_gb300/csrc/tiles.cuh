@@ -505,12 +505,12 @@ struct HostPlan {
 };
 
 // tile passes of the most recent fused circuit run or fused adjoint reverse sweep
-extern int g_last_pass_count;
+extern thread_local int g_last_pass_count;
 // how the most recent QC_RUN_FUSED circuit ran: 0 per gate, 1 CUDA-core tile passes,
 // 2 tile passes with tensor-core stages
-extern int g_last_fused_path;
+extern thread_local int g_last_fused_path;
 // register stages (or tensor-core stage blocks) of the most recent fused circuit run
-extern int g_last_stage_count;
+extern thread_local int g_last_stage_count;
 
 // resolved gates -> plan ops (diagonal gates become phase ops); with `grad`/`gen`, op i
 // carries the tag grad[i] (>= 0: a rotation exp(-i t G/2) with generator gen[i]; X and Y
