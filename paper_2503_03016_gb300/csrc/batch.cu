@@ -6,10 +6,11 @@
 //
 // Work split: one block per SM takes circuits from an atomic counter, largest first.
 // A circuit of n <= 13 qubits stays in shared memory for its whole run; a larger one
-// lives in a per-block global buffer and each layer is two tile passes of 2^13
-// amplitudes (the 13 low index bits, then the remaining high bits plus enough low bits
-// for 512-byte runs).  Within a tile, register stages of SB bits apply the layer's
-// fused 2x2 gates U = RZ(t') RY(t) (up to a global phase); the CZ chain is the diagonal (-1)^popc(i & i>>1)
+// lives in a per-block global buffer and goes through tile passes of 2^13 amplitudes
+// that alternate between the 13 low index bits and the remaining high bits plus enough
+// low bits for 512-byte runs, zig-zagging over the layers (layers + 1 passes).  Within
+// a tile, register stages of SB bits apply the layer's fused 2x2 gates U = RZ(t') RY(t)
+// (up to a global phase); the CZ chain is the diagonal (-1)^popc(i & i>>1)
 // and Z_iZ_{i+1} the sign (n-1) - 2 popc((i ^ i>>1) & (2^(n-1)-1)) of index i, both
 // folded into the last stage.  The stage width SB (the fusion width) is chosen by the
 // autotuner; the launch is recorded once in a CUDA graph and replayed.
@@ -203,7 +204,7 @@ __global__ void __launch_bounds__(NT, MINB)
             double* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   Cplx<float>* tile = reinterpret_cast<Cplx<float>*>(smem_raw);  // 2^13 amplitudes
-  __shared__ GateP gates[kBatchMaxN];
+  __shared__ GateP gates[kBatchMaxN], gates2[kBatchMaxN];
   __shared__ int8_t qol[kBatchTileBits], gbit[kBatchTileBits];
   __shared__ int s_idx;
   __shared__ double red[32];
@@ -241,12 +242,21 @@ __global__ void __launch_bounds__(NT, MINB)
       __threadfence_block();
       const int h = n - kBatchTileBits;  // high bits for pass B
       const int lowB = kBatchTileBits - h;  // low bits kept in pass B
-      for (int l = 0; l < layers; ++l) {
+      // Zig-zag over the layers: pass pp (0 .. layers) takes the low tile (pass A, the 13
+      // low index bits) for even pp and the high tile (pass B) for odd pp, and applies
+      // the second part of layer pp - 1 (its gates on this tile's qubits, then its CZ
+      // chain, which follows the other part done by the previous pass) and the first part
+      // of layer pp.  layers + 1 passes over the state instead of two per layer.
+      for (int pp = 0; pp <= layers; ++pp) {
+        const int pass = pp & 1;
+        const int l0 = pp - 1, l1 = pp;
         __syncthreads();
-        for (int q = threadIdx.x; q < n; q += blockDim.x) gates[q] = layer_gate(p + l * 2 * n + 2 * q);
-        for (int pass = 0; pass < 2; ++pass) {
+        for (int q = threadIdx.x; q < n; q += blockDim.x) {
+          if (l0 >= 0) gates[q] = layer_gate(p + l0 * 2 * n + 2 * q);
+          if (l1 < layers) gates2[q] = layer_gate(p + l1 * 2 * n + 2 * q);
+        }
+        {
           // local bit -> global bit map and the qubit each local bit carries a gate for
-          __syncthreads();
           if (threadIdx.x < kBatchTileBits) {
             const int b = threadIdx.x;
             if (pass == 0) {
@@ -292,8 +302,11 @@ __global__ void __launch_bounds__(NT, MINB)
               }
             }
             __syncthreads();
-            batch_layer_on_buffer<SB>(tile, kBatchTileBits, qol, gates, pass == 1,
-                                      pass == 1 && l == layers - 1, n, gbase, gbit, &zz);
+            if (l0 >= 0)
+              batch_layer_on_buffer<SB>(tile, kBatchTileBits, qol, gates, true, l0 == layers - 1, n, gbase, gbit,
+                                        &zz);
+            if (l1 < layers)
+              batch_layer_on_buffer<SB>(tile, kBatchTileBits, qol, gates2, false, false, n, gbase, gbit, &zz);
             {
               constexpr int PER = (1 << (kBatchTileBits - 1)) / NT;
 #pragma unroll
