@@ -220,7 +220,8 @@ qc_status qc_expect_pauli(const qc_state* s, const char* const* strings, const d
  * lives in one fixed array in the library's device image: 157,696 bytes (1216 blocks
  * x 16 partial sums + 256 term values), held on every device that loads the library
  * until the process exits.  Limits: at most 256 terms per call (more is rejected with
- * QC_ERR_INVALID_ARG and a message); the reduction grid is capped at 1216 blocks.
+ * QC_ERR_INVALID_ARG and a message); the reduction grid is capped at 1216 blocks
+ * (608 blocks x 32 partial sums for the Z-only strings, in the same array).
  * The first call on a device resolves the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call before any
  * stream capture.  All calls share the array and it keeps the last call's contents:

@@ -154,28 +154,62 @@ __device__ __forceinline__ double prob_fp64(double re, double im) {
   return __dadd_rn(__dmul_rn(re, re), __dmul_rn(im, im));
 }
 
-// Exact binary32 -> binary64 widening with integer operations (IEEE 754 formats: sign
-// bit, 8/11 exponent bits with bias 127/1023, 23/52 fraction bits).  A normal float
-// keeps its sign and fraction (shifted up 29 bits) and has its exponent re-biased by
-// 1023 - 127 = 896; zero keeps its sign; subnormal, infinite and NaN inputs (never
-// produced by unitary evolution of a normalised state) take the hardware conversion.
+// Exact binary32 -> binary64 widening with integer operations only (IEEE 754 formats:
+// sign bit, 8/11 exponent bits with bias 127/1023, 23/52 fraction bits), so that no
+// conversion occupies the FP64 pipe.  A normal float keeps its sign and fraction
+// (shifted up 29 bits) and has its exponent re-biased by 1023 - 127 = 896; zero keeps
+// its sign; a subnormal m * 2^-149 with leading fraction bit p becomes a normal double
+// with exponent p - 149 (biased: p + 874) and the bits below p as its fraction;
+// infinities and NaNs keep their fraction under the all-ones exponent.
 __device__ __forceinline__ double widen_exact(float x) {
   const uint32_t b = __float_as_uint(x);
   const uint32_t e = (b >> 23) & 0xFFu;
+  const uint32_t m = b & 0x7FFFFFu;
   const uint64_t sign = uint64_t(b >> 31) << 63;
-  if (e - 1u < 254u)  // 1 <= e <= 254: normal
-    return __longlong_as_double(
-        (long long)(sign | (uint64_t(e + 896u) << 52) | (uint64_t(b & 0x7FFFFFu) << 29)));
-  if ((b & 0x7FFFFFFFu) == 0u) return __longlong_as_double((long long)sign);
-  return double(x);
+  uint64_t ed, md;
+  if (e == 255u) {
+    ed = 2047u;
+    md = uint64_t(m) << 29;
+  } else if (e != 0u) {
+    ed = e + 896u;
+    md = uint64_t(m) << 29;
+  } else if (m == 0u) {
+    ed = 0u;
+    md = 0u;
+  } else {
+    const int p = 31 - __clz(int(m));
+    ed = uint64_t(p + 874);
+    md = (uint64_t(m) << (52 - p)) & ((uint64_t(1) << 52) - 1);
+  }
+  return __longlong_as_double((long long)(sign | (ed << 52) | md));
 }
 
-// The same |a|^2 for complex64 amplitudes: both squares of a widened float are exact
-// in FP64 (24-bit significands), so one fused multiply-add rounds re^2 + im^2 exactly
-// once -- bit for bit the value of the two-product form above, with fewer FP64 ops.
+// x^2 as an exact double with integer operations only.  For a float with biased
+// exponent e, |x| = M * 2^(max(e,1) - 150) with M = fraction | 2^23 for a normal float
+// (M = fraction for a subnormal one), so x^2 = M^2 * 2^(2 max(e,1) - 300).  M^2 is
+// an exact 48-bit integer product; with t its leading bit, x^2 is the normal double
+// with exponent t + 2 max(e,1) - 300 and the bits of M^2 below t as its fraction.
+// Infinities and NaNs keep their fraction under the all-ones exponent.
+__device__ __forceinline__ double square_exact(float x) {
+  const uint32_t b = __float_as_uint(x) & 0x7FFFFFFFu;
+  const uint32_t e = b >> 23, m = b & 0x7FFFFFu;
+  if (e == 255u) return __longlong_as_double((long long)((uint64_t(2047) << 52) | (uint64_t(m) << 29)));
+  if (b == 0u) return 0.0;
+  const uint32_t M = e ? (m | 0x800000u) : m;
+  const int off = 2 * int(e ? e : 1u) - 300;
+  const uint64_t P = uint64_t(M) * M;
+  const int t = 63 - __clzll((long long)P);
+  return __longlong_as_double(
+      (long long)((uint64_t(t + off + 1023) << 52) | ((P << (52 - t)) & ((uint64_t(1) << 52) - 1))));
+}
+
+// The same |a|^2 for complex64 amplitudes: the squares of widened floats are exact in
+// FP64 (24-bit significands), so one fused multiply-add of im * im onto the exact re^2
+// rounds re^2 + im^2 once -- bit for bit the value of the two-product form above, with
+// a single FP64 operation (re^2 is built with integer operations).
 __device__ __forceinline__ double prob_fp64(float re, float im) {
-  const double dre = widen_exact(re), dim = widen_exact(im);
-  return __fma_rn(dre, dre, __dmul_rn(dim, dim));
+  const double dim = widen_exact(im);
+  return __fma_rn(dim, dim, square_exact(re));
 }
 
 // ---------------------------------------------------------------------------

@@ -19,41 +19,71 @@ namespace qcgb {
 // ---------------------------------------------------------------------------
 // P(0), P(1) partials
 // ---------------------------------------------------------------------------
+// Two neighbouring amplitudes i, i+1 into the outcome sums: complex128 adds the four
+// squares into the FP64 sums with fused multiply-adds; complex64 forms the squared
+// magnitudes in FP32 (relative error 2^-24 each) and adds them to the FP32 group sums
+// g0, g1, which the caller widens into the FP64 sums every four steps (eight
+// amplitudes: relative error below 7 * 2^-24 per group), so that the FP64 pipe sees
+// one add per group and outcome instead of one per step.
+template <typename R>
+__device__ __forceinline__ void outcome_add(uint64_t i, uint64_t m, const Cplx<R>& x0, const Cplx<R>& x1, R& g0,
+                                            R& g1) {
+  if constexpr (sizeof(R) == 4) {
+    const float f0 = fmaf(x0.re, x0.re, x0.im * x0.im), f1 = fmaf(x1.re, x1.re, x1.im * x1.im);
+    if (m == 1) {
+      g0 += f0;
+      g1 += f1;
+    } else if (i & m) {
+      g1 += f0 + f1;
+    } else {
+      g0 += f0 + f1;
+    }
+  } else {
+    if (m == 1) {
+      g0 = fma(x0.im, x0.im, fma(x0.re, x0.re, g0));
+      g1 = fma(x1.im, x1.im, fma(x1.re, x1.re, g1));
+    } else {
+      R& g = (i & m) ? g1 : g0;
+      g = fma(x1.im, x1.im, fma(x1.re, x1.re, fma(x0.im, x0.im, fma(x0.re, x0.re, g))));
+    }
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void outcome_flush(float& g0, float& g1, double& s0, double& s1) {
+  s0 += widen_exact(g0);
+  s1 += widen_exact(g1);
+  g0 = g1 = 0.f;
+}
+
+// Two neighbouring amplitudes per step; each thread issues the loads of four steps
+// before it uses them, so enough bytes are in flight to cover the memory latency.
 template <typename R>
 __global__ void __launch_bounds__(256) k_outcome_partials(const R* __restrict__ a, uint64_t N, uint64_t m,
                                                           double* partials) {
+  // complex64: FP32 group sums g, FP64 sums s; complex128: the FP64 sums directly
+  R g0 = R(0), g1 = R(0);
   double s0 = 0.0, s1 = 0.0;
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-  if (N >= 2) {
-    // two neighbouring amplitudes per step
-    for (uint64_t it = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; it < N / 2; it += stride) {
-      const uint64_t i = 2 * it;
-      Cplx<R> x0, x1;
-      ld_amp2<R>(a, i, x0, x1);
-      double p0, p1;
-      if constexpr (sizeof(R) == 4) {
-        // complex64: squares in FP32 (relative error 2^-24 per amplitude), sums in FP64
-        const float f0 = fmaf(x0.re, x0.re, x0.im * x0.im), f1 = fmaf(x1.re, x1.re, x1.im * x1.im);
-        if (m == 1) {
-          p0 = widen_exact(f0);
-          p1 = widen_exact(f1);
-        } else {
-          p0 = widen_exact(f0 + f1);
-          p1 = 0.0;
-        }
-      } else {
-        p0 = double(x0.re) * double(x0.re) + double(x0.im) * double(x0.im);
-        p1 = double(x1.re) * double(x1.re) + double(x1.im) * double(x1.im);
-      }
-      if (m == 1) {
-        s0 += p0;
-        s1 += p1;
-      } else if (i & m) {
-        s1 += p0 + p1;
-      } else {
-        s0 += p0 + p1;
-      }
-    }
+  const uint64_t half = N / 2;
+  uint64_t it = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x;
+  for (; it + 3 * stride < half; it += 4 * stride) {
+    Cplx<R> x[8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) ld_amp2<R>(a, 2 * (it + u * stride), x[2 * u], x[2 * u + 1]);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) outcome_add<R>(2 * (it + u * stride), m, x[2 * u], x[2 * u + 1], g0, g1);
+    if constexpr (sizeof(R) == 4) outcome_flush<R>(g0, g1, s0, s1);
+  }
+  for (; it < half; it += stride) {
+    Cplx<R> x0, x1;
+    ld_amp2<R>(a, 2 * it, x0, x1);
+    outcome_add<R>(2 * it, m, x0, x1, g0, g1);
+    if constexpr (sizeof(R) == 4) outcome_flush<R>(g0, g1, s0, s1);
+  }
+  if constexpr (sizeof(R) == 8) {
+    s0 = g0;
+    s1 = g1;
   }
   s0 = block_sum(s0);
   s1 = block_sum(s1);
@@ -79,29 +109,54 @@ __global__ void k_sum2(const double* partials, int count, double* out) {
 
 // Keeps the amplitudes whose bit m reads `outcome`, scaled by inv = 1/sqrt(P) (formed
 // once in FP64 by the host; complex64 applies it rounded to FP32), and zeroes the rest
-// without reading them.  Two neighbouring amplitudes per step (N >= 2).
+// without reading them.  Two neighbouring amplitudes per step (N >= 2); each thread
+// issues the loads of four steps before their stores.
+template <typename R>
+__device__ __forceinline__ bool collapse_reads(uint64_t i, uint64_t m, int outcome) {
+  return m == 1 || ((i & m) ? 1 : 0) == outcome;
+}
+
+template <typename R>
+__device__ __forceinline__ void collapse_store(R* a, uint64_t i, uint64_t m, int outcome, R f, const Cplx<R>& x0,
+                                               const Cplx<R>& x1) {
+  const Cplx<R> zero{R(0), R(0)};
+  if (m == 1) {
+    if (outcome == 0)
+      st_amp2<R>(a, i, Cplx<R>{x0.re * f, x0.im * f}, zero);
+    else
+      st_amp2<R>(a, i, zero, Cplx<R>{x1.re * f, x1.im * f});
+  } else if (((i & m) ? 1 : 0) != outcome) {
+    st_amp2<R>(a, i, zero, zero);
+  } else {
+    st_amp2<R>(a, i, Cplx<R>{x0.re * f, x0.im * f}, Cplx<R>{x1.re * f, x1.im * f});
+  }
+}
+
 template <typename R>
 __global__ void __launch_bounds__(256) k_collapse(R* __restrict__ a, uint64_t N, uint64_t m, int outcome,
                                                   double inv) {
   const R f = R(inv);
-  const Cplx<R> zero{R(0), R(0)};
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
-  for (uint64_t it = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; it < N / 2; it += stride) {
-    const uint64_t i = 2 * it;
-    if (m == 1) {
-      Cplx<R> x0, x1;
-      ld_amp2<R>(a, i, x0, x1);
-      if (outcome == 0)
-        st_amp2<R>(a, i, Cplx<R>{x0.re * f, x0.im * f}, zero);
+  const uint64_t half = N / 2;
+  uint64_t it = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x;
+  for (; it + 3 * stride < half; it += 4 * stride) {
+    Cplx<R> x[8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const uint64_t i = 2 * (it + u * stride);
+      if (collapse_reads<R>(i, m, outcome))
+        ld_amp2<R>(a, i, x[2 * u], x[2 * u + 1]);
       else
-        st_amp2<R>(a, i, zero, Cplx<R>{x1.re * f, x1.im * f});
-    } else if (((i & m) ? 1 : 0) != outcome) {
-      st_amp2<R>(a, i, zero, zero);
-    } else {
-      Cplx<R> x0, x1;
-      ld_amp2<R>(a, i, x0, x1);
-      st_amp2<R>(a, i, Cplx<R>{x0.re * f, x0.im * f}, Cplx<R>{x1.re * f, x1.im * f});
+        x[2 * u] = x[2 * u + 1] = Cplx<R>{R(0), R(0)};
     }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) collapse_store<R>(a, 2 * (it + u * stride), m, outcome, f, x[2 * u], x[2 * u + 1]);
+  }
+  for (; it < half; it += stride) {
+    const uint64_t i = 2 * it;
+    Cplx<R> x0{R(0), R(0)}, x1{R(0), R(0)};
+    if (collapse_reads<R>(i, m, outcome)) ld_amp2<R>(a, i, x0, x1);
+    collapse_store<R>(a, i, m, outcome, f, x0, x1);
   }
 }
 

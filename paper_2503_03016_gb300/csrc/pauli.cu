@@ -100,29 +100,32 @@ __global__ void __launch_bounds__(256) k_pauli(const R* __restrict__ a, uint64_t
   }
 }
 
-// Z-only strings (x = 0), up to 32 per pass: <Z_z> = sum_i p_i (-1)^popc(i & z).  A thread
-// takes chunks of 32 consecutive amplitudes (index bits 0..4 vary, the rest are the
-// chunk's), forms the Walsh-Hadamard transform S(w) = sum_l p_l (-1)^popc(l & w) of the
-// chunk's 32 probabilities once (in registers, then shared memory), and adds
-// (-1)^popc(chunk & z) * S(z & 31) to every term: per-term work is per chunk, not per
-// amplitude.  complex64 states accumulate per thread in FP32 (the per-amplitude values
-// are FP32 products already), complex128 in FP64; cross-thread and cross-block sums
-// are FP64 in a fixed order.
+// Z-only strings (x = 0), up to 32 per pass: <Z_z> = sum_i p_i (-1)^popc(i & z).  With
+// h = n - 5, index i = (l << h) | c splits into the 5 top bits l (qubits 0..4) and a
+// chunk number c.  A thread takes chunk c, the 32 amplitudes (l << h) | c, forms the
+// Walsh-Hadamard transform S(w) = sum_l p_l (-1)^popc(l & w) of their probabilities once
+// (in registers, then shared memory), and adds (-1)^popc(c & z) * S(z >> h) to every
+// term: per-term work is per chunk, not per amplitude.  Neighbouring threads take
+// neighbouring chunks, so each of a warp's 32 loads is one contiguous run of amplitudes.
+// complex64 states accumulate per thread in FP32 (the per-amplitude values are FP32
+// products already), complex128 in FP64; cross-thread and cross-block sums are FP64 in
+// a fixed order.
 //
 // Signs: there are 2^K virtual threads (K = kbits_base; one resident wave of blocks
 // loops over them) and virtual thread g takes the chunks g + k 2^K, k = 0 ..
-// 2^kbits - 1, so (-1)^popc(chunk*32 & z) splits into a per-thread sign (from g) and a
-// sign from k shared by all threads.  k runs in Gray-code order: the step from the j-th
-// to the (j+1)-th k flips bit ctz(j+1) of k, which toggles the signs of the terms whose
-// z has the matching index bit (flip[b], from the host).
+// 2^kbits - 1, so (-1)^popc(c & z) splits into a per-thread sign (from g) and a sign
+// from k shared by all threads.  k runs in Gray-code order: the step from the j-th to
+// the (j+1)-th k flips bit ctz(j+1) of k, which toggles the signs of the terms whose z
+// has the matching index bit (flip[b], from the host).
 constexpr int kMaxZTerms = 32;
 constexpr int kZBlock = 128;
 constexpr int kZMaxThreadBits = 20;  // at most 2^20 virtual threads (8192 virtual blocks)
 struct ZGroup {
   int nt;
+  int hshift;         // h = n - 5: log2 of the chunk count, shift of the top 5 bits
   int kbits_base;     // K: log2 of the number of virtual threads
   int kbits;          // chunks per virtual thread = 2^kbits
-  uint32_t flip[16];  // bit t: term t's z has index bit 5 + K + b
+  uint32_t flip[16];  // bit t: term t's z has index bit K + b
   uint64_t z[kMaxZTerms];
   int slot[kMaxZTerms];
 };
@@ -134,6 +137,7 @@ __global__ void __launch_bounds__(kZBlock) k_pauli_z(const R* __restrict__ amps,
   R acc[kMaxZTerms];
 #pragma unroll
   for (int t = 0; t < kMaxZTerms; ++t) acc[t] = R(0);
+  const int h = g.hshift;
   const uint64_t nchunk = N >> 5;
   // 2^K virtual threads in virtual blocks of kZBlock, spread over the resident grid
   const uint64_t nvb = uint64_t(1) << (g.kbits_base - 7);
@@ -144,28 +148,26 @@ __global__ void __launch_bounds__(kZBlock) k_pauli_z(const R* __restrict__ amps,
     uint32_t sign = 0;
 #pragma unroll
     for (int t = 0; t < kMaxZTerms; ++t)
-      if (t < g.nt) sign |= uint32_t(__popcll((gt << 5) & g.z[t]) & 1) << t;
+      if (t < g.nt) sign |= uint32_t(__popcll(gt & g.z[t]) & 1) << t;
     const uint64_t nk = uint64_t(1) << g.kbits;
     for (uint64_t j = 0; j < nk; ++j) {
       const uint64_t k = j ^ (j >> 1);  // Gray code
-      const uint64_t base = (gt + (k << g.kbits_base)) << 5;
+      const uint64_t c = gt + (k << g.kbits_base);
       R w[32];
 #pragma unroll
-      for (int l = 0; l < 32; l += 2) {
-        Cplx<R> x0, x1;
-        ld_amp2<R>(amps, base + l, x0, x1);
-        w[l] = x0.re * x0.re + x0.im * x0.im;
-        w[l + 1] = x1.re * x1.re + x1.im * x1.im;
+      for (int l = 0; l < 32; ++l) {
+        const Cplx<R> x = ld_amp<R>(amps, (uint64_t(l) << h) | c);
+        w[l] = x.re * x.re + x.im * x.im;
       }
-      // in-place Walsh-Hadamard transform over the 5 chunk bits
+      // in-place Walsh-Hadamard transform over the 5 top bits
 #pragma unroll
-      for (int h = 1; h < 32; h <<= 1)
+      for (int hb = 1; hb < 32; hb <<= 1)
 #pragma unroll
         for (int l = 0; l < 32; ++l)
-          if (!(l & h)) {
-            const R a = w[l], b = w[l | h];
+          if (!(l & hb)) {
+            const R a = w[l], b = w[l | hb];
             w[l] = a + b;
-            w[l | h] = a - b;
+            w[l | hb] = a - b;
           }
 #pragma unroll
       for (int l = 0; l < 32; ++l) S[l][threadIdx.x] = w[l];
@@ -173,7 +175,7 @@ __global__ void __launch_bounds__(kZBlock) k_pauli_z(const R* __restrict__ amps,
 #pragma unroll
       for (int t = 0; t < kMaxZTerms; ++t) {
         if (t >= g.nt) break;
-        const R v = S[g.z[t] & 31][threadIdx.x];
+        const R v = S[g.z[t] >> h][threadIdx.x];
         acc[t] += ((sign >> t) & 1u) ? -v : v;
       }
       if (j + 1 < nk) sign ^= g.flip[__ffsll((long long)(j + 1)) - 1];
@@ -187,24 +189,22 @@ __global__ void __launch_bounds__(kZBlock) k_pauli_z(const R* __restrict__ amps,
   }
 }
 
-__global__ void k_sum_zterms(const double* partials, int nblocks, ZGroup g, double* out) {
-  for (int t = 0; t < g.nt; ++t) {
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += partials[size_t(i) * kMaxZTerms + t];
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) out[g.slot[t]] = acc;
-    __syncthreads();
-  }
+// Cross-block sums, one block per term (grid = number of terms): each block adds its
+// term's block partials in a fixed order.
+__global__ void __launch_bounds__(256) k_sum_zterms(const double* partials, int nblocks, ZGroup g, double* out) {
+  const int t = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += partials[size_t(i) * kMaxZTerms + t];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) out[g.slot[t]] = acc;
 }
 
-__global__ void k_sum_terms(const double* partials, int nblocks, PauliGroup g, double* out) {
-  for (int t = 0; t < g.nt; ++t) {
-    double acc = 0.0;
-    for (int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += partials[size_t(i) * kMaxTermsPerPass + t];
-    acc = block_sum(acc);
-    if (threadIdx.x == 0) out[g.slot[t]] = acc;
-    __syncthreads();
-  }
+__global__ void __launch_bounds__(256) k_sum_terms(const double* partials, int nblocks, PauliGroup g, double* out) {
+  const int t = blockIdx.x;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < nblocks; i += blockDim.x) acc += partials[size_t(i) * kMaxTermsPerPass + t];
+  acc = block_sum(acc);
+  if (threadIdx.x == 0) out[g.slot[t]] = acc;
 }
 
 struct ParsedTerm {
@@ -234,8 +234,62 @@ qc_status parse_pauli(int n, const char* str, ParsedTerm* out) {
   return QC_OK;
 }
 
-// values[t] = <psi|P_t|psi> (no coefficients), device buffer `dev_vals` of nterms
-qc_status expect_terms_device(qc_state* s, const ParsedTerm* terms, int nterms, double* dev_vals) {
+// Resident k_pauli_z blocks per SM (1..32), queried once per (dtype, device).
+static int z_blocks_per_sm(bool c64, int device) {
+  static std::mutex mu;
+  static std::map<std::pair<bool, int>, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find({c64, device});
+  if (it != cache.end()) return it->second;
+  int per_sm = 0;
+  if (c64)
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pauli_z<float>, kZBlock, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pauli_z<double>, kZBlock, 0);
+  per_sm = std::min(std::max(per_sm, 1), 32);
+  cache[{c64, device}] = per_sm;
+  return per_sm;
+}
+
+// Z-only strings z[0..nt) (N >= 64), values to vals[slot[j]]: passes of up to 32 terms,
+// each a k_pauli_z launch (one resident wave of blocks looping over 2^K virtual threads
+// that take 2^kbits chunks of 32 amplitudes each; at most max_blocks blocks, whose
+// partials go to `part`) and a k_sum_zterms launch.
+static void launch_z_strings(qc_state* s, const uint64_t* z, const int* slot, int nt, double* part,
+                             size_t max_blocks, double* vals) {
+  const uint64_t N = state_len(s);
+  const int cbits = s->n - 5;  // log2 of the chunk count
+  const int K = std::max(7, std::min(cbits, kZMaxThreadBits));
+  const int per_sm = z_blocks_per_sm(s->dtype == QC_C64, s->device);
+  uint64_t gz = std::min<uint64_t>(uint64_t(1) << (K - 7), uint64_t(per_sm) * device_sm_count());
+  gz = std::max<uint64_t>(1, std::min<uint64_t>(gz, max_blocks));
+  for (int beg = 0; beg < nt; beg += kMaxZTerms) {
+    ZGroup zg{};
+    zg.nt = std::min(kMaxZTerms, nt - beg);
+    zg.hshift = cbits;
+    zg.kbits_base = K;
+    zg.kbits = std::max(0, cbits - K);
+    for (int j = 0; j < zg.nt; ++j) {
+      zg.z[j] = z[beg + j];
+      zg.slot[j] = slot[beg + j];
+      for (int b = 0; b < zg.kbits; ++b)
+        if ((zg.z[j] >> (K + b)) & 1) zg.flip[b] |= 1u << j;
+    }
+    if (s->dtype == QC_C64)
+      QC_COUNT(), k_pauli_z<float><<<unsigned(gz), kZBlock, 0, s->stream>>>(reinterpret_cast<const float*>(s->amps),
+                                                                          N, zg, part);
+    else
+      QC_COUNT(), k_pauli_z<double><<<unsigned(gz), kZBlock, 0, s->stream>>>(reinterpret_cast<const double*>(s->amps),
+                                                                           N, zg, part);
+    QC_COUNT(), k_sum_zterms<<<zg.nt, 256, 0, s->stream>>>(part, int(gz), zg, vals);
+  }
+}
+
+// values[t] = <psi|P_t|psi> (no coefficients) into a device buffer of nterms doubles:
+// `dev_vals`, or with dev_vals == nullptr the end of the state's scratch (returned in
+// *vals_out; valid until the next call that uses the scratch).
+qc_status expect_terms_device(qc_state* s, const ParsedTerm* terms, int nterms, double* dev_vals,
+                              double** vals_out = nullptr) {
   const uint64_t N = state_len(s);
   std::map<uint64_t, std::vector<int>> groups;
   for (int t = 0; t < nterms; ++t) groups[terms[t].x].push_back(t);
@@ -245,39 +299,17 @@ qc_status expect_terms_device(qc_state* s, const ParsedTerm* terms, int nterms, 
   // one resident wave (below 32 blocks per SM)
   const size_t nblk = std::max<size_t>(g, size_t(32) * device_sm_count());
   void* scr = nullptr;
-  if (qc_status st = state_scratch(s, sizeof(double) * nblk * kMaxZTerms + 256, &scr)) return st;
+  if (qc_status st = state_scratch(s, sizeof(double) * (nblk * kMaxZTerms + size_t(nterms)) + 256, &scr))
+    return st;
   double* part = reinterpret_cast<double*>(scr);
+  if (!dev_vals) dev_vals = part + nblk * kMaxZTerms;
+  if (vals_out) *vals_out = dev_vals;
   for (auto& kv : groups) {
     const std::vector<int>& idx = kv.second;
     if (kv.first == 0 && N >= 64) {  // Z-only strings
-      // 2^K virtual threads (at least one block), each taking 2^kbits chunks of 32
-      // amplitudes; the launch is one resident wave of blocks looping over them
-      const int cbits = s->n - 5;  // log2 of the chunk count
-      const int K = std::max(7, std::min(cbits, kZMaxThreadBits));
-      int per_sm = 0;
-      if (s->dtype == QC_C64)
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pauli_z<float>, kZBlock, 0);
-      else
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pauli_z<double>, kZBlock, 0);
-      per_sm = std::min(std::max(per_sm, 1), 32);
-      const unsigned gz = unsigned(std::min<uint64_t>(uint64_t(1) << (K - 7), uint64_t(per_sm) * device_sm_count()));
-      for (size_t beg = 0; beg < idx.size(); beg += kMaxZTerms) {
-        ZGroup zg{};
-        zg.nt = int(std::min<size_t>(kMaxZTerms, idx.size() - beg));
-        zg.kbits_base = K;
-        zg.kbits = std::max(0, cbits - K);
-        for (int j = 0; j < zg.nt; ++j) {
-          zg.z[j] = terms[idx[beg + j]].z;
-          zg.slot[j] = idx[beg + j];
-          for (int b = 0; b < zg.kbits; ++b)
-            if ((zg.z[j] >> (5 + K + b)) & 1) zg.flip[b] |= 1u << j;
-        }
-        if (s->dtype == QC_C64)
-          QC_COUNT(), k_pauli_z<float><<<gz, kZBlock, 0, s->stream>>>(reinterpret_cast<const float*>(s->amps), N, zg, part);
-        else
-          QC_COUNT(), k_pauli_z<double><<<gz, kZBlock, 0, s->stream>>>(reinterpret_cast<const double*>(s->amps), N, zg, part);
-        QC_COUNT(), k_sum_zterms<<<1, 1024, 0, s->stream>>>(part, int(gz), zg, dev_vals);
-      }
+      std::vector<uint64_t> z(idx.size());
+      for (size_t j = 0; j < idx.size(); ++j) z[j] = terms[idx[j]].z;
+      launch_z_strings(s, z.data(), idx.data(), int(idx.size()), part, nblk, dev_vals);
       continue;
     }
     for (size_t beg = 0; beg < idx.size(); beg += kMaxTermsPerPass) {
@@ -294,7 +326,7 @@ qc_status expect_terms_device(qc_state* s, const ParsedTerm* terms, int nterms, 
         QC_COUNT(), k_pauli<float><<<g, B, 0, s->stream>>>(reinterpret_cast<const float*>(s->amps), N, pg, part);
       else
         QC_COUNT(), k_pauli<double><<<g, B, 0, s->stream>>>(reinterpret_cast<const double*>(s->amps), N, pg, part);
-      QC_COUNT(), k_sum_terms<<<1, 1024, 0, s->stream>>>(part, int(g), pg, dev_vals);
+      QC_COUNT(), k_sum_terms<<<pg.nt, 256, 0, s->stream>>>(part, int(g), pg, dev_vals);
     }
   }
   return check_launch("Pauli expectation");
@@ -316,17 +348,12 @@ extern "C" qc_status qc_expect_pauli(const qc_state* cs, const char* const* stri
   std::vector<ParsedTerm> terms(nterms);
   for (int t = 0; t < nterms; ++t)
     if (qc_status st = parse_pauli(s->n, strings[t], &terms[t])) return st;
-  double* dev = nullptr;
-  if (qc_status st = check_cuda(cudaMallocAsync(reinterpret_cast<void**>(&dev),
-                                                sizeof(double) * nterms, s->stream),
-                                "expectation buffer"))
-    return st;
-  qc_status st = expect_terms_device(s, terms.data(), nterms, dev);
+  double* dev = nullptr;  // values at the end of the state's scratch
+  qc_status st = expect_terms_device(s, terms.data(), nterms, nullptr, &dev);
   std::vector<double> vals(nterms);
   if (st == QC_OK)
     st = check_cuda(cudaMemcpyAsync(vals.data(), dev, sizeof(double) * nterms, cudaMemcpyDeviceToHost, s->stream),
                     "D2H");
-  cudaFreeAsync(dev, s->stream);
   if (st == QC_OK) st = check_cuda(cudaStreamSynchronize(s->stream), "qc_expect_pauli");
   if (st != QC_OK) return st;
   for (int t = 0; t < nterms; ++t) host_out[t] = vals[t] * (coeffs ? coeffs[t] : 1.0);
@@ -431,11 +458,23 @@ extern "C" qc_status qc_expect_pauli_noalloc(const qc_state* cs, const char* con
       pg.slot[pg.nt] = t;
       ++pg.nt;
     }
+    if (pg.xmask == 0 && N >= 64) {
+      // Z-only strings: all of them (they are contiguous in `order`) in the Z kernel,
+      // its block partials within the same fixed scratch
+      int nz = pg.nt;
+      while (beg + nz < nterms && terms[order[beg + nz]].x == 0) ++nz;
+      uint64_t z[kNoAllocMaxTerms];
+      for (int j = 0; j < nz; ++j) z[j] = terms[order[beg + j]].z;
+      launch_z_strings(s, z, order + beg, nz, part, size_t(kNoAllocMaxBlocks) * kMaxTermsPerPass / kMaxZTerms,
+                       vals);
+      beg += nz;
+      continue;
+    }
     if (s->dtype == QC_C64)
       QC_COUNT(), k_pauli<float><<<g, B, 0, s->stream>>>(reinterpret_cast<const float*>(s->amps), N, pg, part);
     else
       QC_COUNT(), k_pauli<double><<<g, B, 0, s->stream>>>(reinterpret_cast<const double*>(s->amps), N, pg, part);
-    QC_COUNT(), k_sum_terms<<<1, 1024, 0, s->stream>>>(part, int(g), pg, vals);
+    QC_COUNT(), k_sum_terms<<<pg.nt, 256, 0, s->stream>>>(part, int(g), pg, vals);
     beg += pg.nt;
   }
   if (qc_status st = check_launch("qc_expect_pauli_noalloc")) return st;

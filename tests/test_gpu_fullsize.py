@@ -96,3 +96,56 @@ def test_brickwork28_probs_and_shots_bit_exact():
     np.testing.assert_array_equal(p, p_ref)
     np.testing.assert_array_equal(idx, oracle.sample(oracle.cdf(p_ref), u))
     st.free()
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_z_strings_28_qubit_product_state(dtype):
+    """<Z_S> on RY(t_0) x ... x RY(t_27)|0...0> is prod_{q in S} cos t_q (each factor
+    is cos^2(t/2) - sin^2(t/2)).  28 qubits put strings on every part of the Z-string
+    kernel's index split: the five transformed top bits (qubits 0..4), the Gray-code
+    bits of the chunk number (qubits 5..7) and the per-thread low bits; the identity
+    string checks that every chunk is counted once."""
+    import paper_2503_03016_gb300 as P
+    n = 28
+    if _free_gb() < (2 if dtype == "c64" else 4) * 1.5:
+        pytest.skip("not enough device memory")
+    rng = np.random.default_rng(28)
+    t = rng.uniform(0.2, 1.2, n)
+    st = P.State(n, dtype).init_basis(0)
+    for q in range(n):
+        c, s = np.cos(t[q] / 2), np.sin(t[q] / 2)
+        st.apply_1q(q, np.array([[c, -s], [s, c]]))
+    sets = [(q, q + 1) for q in range(n - 1)]
+    sets += [(), (0,), (4,), (5,), (6,), (7,), (0, 4), (3, 5), (5, 6, 7), (4, 8), (7, 27),
+             (0, 1, 2, 3, 4), (2, 6, 13, 21, 27), (1, 5, 7, 20, 26)]
+    strings = []
+    for S in sets:
+        s = ["I"] * n
+        for q in S:
+            s[q] = "Z"
+        strings.append("".join(s))
+    got = st.expect(strings)
+    want = np.array([np.prod(np.cos(t[list(S)])) for S in sets])
+    tol = 1e-12 if dtype == "c128" else 1e-5
+    np.testing.assert_allclose(got, want, atol=tol)
+    st.free()
+
+
+def test_z_strings_26_qubit_gaussian_state():
+    """A general 26-qubit state (the chunk number then has one Gray-code bit, index bit
+    20 = qubit 5): Z strings across the kernel's index split against the oracle on the
+    stored (widened) amplitudes."""
+    import paper_2503_03016_gb300 as P
+    n = 26
+    st = P.State(n, "c64").init_gaussian(26)
+    sets = [(5,), (0, 5, 25), (4, 5, 6), (1, 2, 3, 4, 5, 20), (0, 1)]
+    strings = []
+    for S in sets:
+        s = ["I"] * n
+        for q in S:
+            s[q] = "Z"
+        strings.append("".join(s))
+    got = st.expect(strings)
+    want = oracle.expect_pauli(st.numpy().astype(np.complex128), strings)
+    np.testing.assert_allclose(got, want, atol=2e-6)
+    st.free()

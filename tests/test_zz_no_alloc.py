@@ -45,6 +45,23 @@ def test_noalloc_matches_regular_entry_point(dtype, tol, n):
                                atol=tol * 2, rtol=0)
 
 
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-12), ("c64", 2e-6)])
+def test_noalloc_z_strings_against_oracle(dtype, tol):
+    """More Z-only strings than one pass of the Z-string kernel takes (32), mixed with
+    X/Y strings in the term list, against the oracle."""
+    import oracle
+    import paper_2503_03016_gb300 as P
+    n = 12
+    rng = np.random.default_rng(5)
+    psi = W.random_state(n, 23)
+    strings = ["".join(rng.choice(list("IZ"), n)) for _ in range(45)] + ["I" * n]
+    strings += ["".join(rng.choice(list("IXYZ"), n)) for _ in range(10)]
+    strings = [strings[i] for i in rng.permutation(len(strings))]
+    st = gpu_state(psi, dtype)
+    got = P.qc_expect_pauli_noalloc(st.handle, strings)
+    np.testing.assert_allclose(got, oracle.expect_pauli(psi, strings), atol=tol, rtol=0)
+
+
 def test_noalloc_rejects_too_many_terms():
     import paper_2503_03016_gb300 as P
     st = gpu_state(W.random_state(3, 1), "c64")
