@@ -322,23 +322,51 @@ __device__ __forceinline__ U128 warp_sum128(U128 v) {
   return v;
 }
 
-// K1: one warp per leaf -> leaf sum
+// K1: leaf sums.  Full leaves (ls = 64): eight lanes per leaf, each converting and adding
+// eight consecutive values, then three shuffle levels combine the eight lanes; a warp
+// takes four neighbouring leaves at a time.  The integer sums are exact, so the leaf
+// sum does not depend on this grouping.  A single short leaf (N < 64): the whole warp,
+// two values per lane.
 template <typename Src>
 __global__ void __launch_bounds__(256) k_leaf_sums(Src src, uint64_t nleaf, int ls, U128* __restrict__ sums) {
   const int lane = threadIdx.x & 31;
   const uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
   const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
-  for (uint64_t leaf = warp; leaf < nleaf; leaf += nwarps) {
-    U128 v0, v1;
-    leaf_values(src, leaf, ls, lane, v0, v1);
-    U128 t = warp_sum128(add128(v0, v1));
-    if (lane == 0) sums[leaf] = t;
+  if (ls < kLeaf) {
+    for (uint64_t leaf = warp; leaf < nleaf; leaf += nwarps) {
+      U128 v0, v1;
+      leaf_values(src, leaf, ls, lane, v0, v1);
+      U128 t = warp_sum128(add128(v0, v1));
+      if (lane == 0) sums[leaf] = t;
+    }
+    return;
+  }
+  const int sub = lane >> 3, part = lane & 7;  // leaf within the warp's four, eighth of it
+  for (uint64_t l0 = 4 * warp; l0 < nleaf; l0 += 4 * nwarps) {
+    const uint64_t leaf = l0 + sub;
+    U128 acc{0, 0};
+    if (leaf < nleaf) {
+      const uint64_t i = leaf * kLeaf + 8 * part;
+      double p[8];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) src.load2(i + 2 * q, p[2 * q], p[2 * q + 1]);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc = add128(acc, to_fixed(p[q]));
+    }
+#pragma unroll
+    for (int o = 4; o > 0; o >>= 1) {
+      U128 t;
+      t.lo = __shfl_xor_sync(0xffffffffu, acc.lo, o);
+      t.hi = __shfl_xor_sync(0xffffffffu, acc.hi, o);
+      acc = add128(acc, t);
+    }
+    if (part == 0 && leaf < nleaf) sums[leaf] = acc;
   }
 }
 
 // K2a: per chunk of leaves, the chunk total
 constexpr int kScanBlock = 256;
-constexpr int kChunk = 4096;  // leaves per chunk
+constexpr int kChunk = 2048;  // leaves per chunk
 
 __device__ __forceinline__ U128 block_exclusive_scan128(U128 v, U128* total) {
   __shared__ U128 wsum[kScanBlock / 32];
@@ -395,25 +423,60 @@ __global__ void __launch_bounds__(kScanBlock) k_scan_chunks(U128* chunk, int nch
   if (threadIdx.x == 0) chunk[nchunk] = tot;
 }
 
-// K2c: leaf exclusive offsets (in place) and the rounded cdf at each leaf's end
+// K2c: leaf exclusive offsets (in place) and the rounded cdf at each leaf's end.  A block
+// takes its chunk of kChunk leaves through shared memory: coalesced loads, each thread
+// scans kChunk / kScanBlock consecutive leaves, coalesced stores.  One padding slot per
+// thread run keeps both access patterns free of bank conflicts.
 __global__ void __launch_bounds__(kScanBlock) k_leaf_offsets(U128* __restrict__ sums, uint64_t nleaf,
                                                              const U128* __restrict__ chunk,
                                                              double* __restrict__ leaf_end) {
-  const uint64_t base = uint64_t(blockIdx.x) * kChunk;
   constexpr int per = kChunk / kScanBlock;
-  const uint64_t beg = base + uint64_t(threadIdx.x) * per;
+  __shared__ U128 st[kChunk + kChunk / per];
+  auto slot = [](int i) { return i + i / per; };
+  const uint64_t base = uint64_t(blockIdx.x) * kChunk;
+  const int t = threadIdx.x;
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    const int i = t + k * kScanBlock;
+    st[slot(i)] = base + i < nleaf ? sums[base + i] : U128{0, 0};
+  }
+  __syncthreads();
+  U128 v[per];
   U128 acc{0, 0};
-  for (int j = 0; j < per; ++j)
-    if (beg + j < nleaf) acc = add128(acc, sums[beg + j]);
+#pragma unroll
+  for (int j = 0; j < per; ++j) {
+    v[j] = st[slot(t * per + j)];
+    acc = add128(acc, v[j]);
+  }
   U128 tot;
   U128 off = add128(block_exclusive_scan128(acc, &tot), chunk[blockIdx.x]);
-  for (int j = 0; j < per; ++j)
-    if (beg + j < nleaf) {
-      const U128 v = sums[beg + j];
-      sums[beg + j] = off;
-      off = add128(off, v);
-      leaf_end[beg + j] = from_fixed(off);
-    }
+  double e[per];
+#pragma unroll
+  for (int j = 0; j < per; ++j) {
+    const U128 o = off;
+    off = add128(off, v[j]);
+    e[j] = from_fixed(off);
+    v[j] = o;
+  }
+  __syncthreads();  // every thread has read its run
+#pragma unroll
+  for (int j = 0; j < per; ++j) st[slot(t * per + j)] = v[j];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    const int i = t + k * kScanBlock;
+    if (base + i < nleaf) sums[base + i] = st[slot(i)];
+  }
+  __syncthreads();
+  double* sd = reinterpret_cast<double*>(st);
+#pragma unroll
+  for (int j = 0; j < per; ++j) sd[slot(t * per + j)] = e[j];
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    const int i = t + k * kScanBlock;
+    if (base + i < nleaf) leaf_end[base + i] = sd[slot(i)];
+  }
 }
 
 // K3: one warp per shot.  Comparisons of non-negative doubles are done on their bit
@@ -530,7 +593,7 @@ static qc_status sample_impl(qc_state* s, uint64_t N, const Src& src, const doub
   U128* sums = reinterpret_cast<U128*>(scr);
   U128* chunk = reinterpret_cast<U128*>(reinterpret_cast<char*>(scr) + sums_b);
   double* leaf_end = reinterpret_cast<double*>(reinterpret_cast<char*>(scr) + sums_b + chunk_b);
-  const unsigned g1 = stream_grid(nleaf * 32, 256, 8);
+  const unsigned g1 = stream_grid(ls < kLeaf ? nleaf * 32 : nleaf * 8, 256, 8);
   QC_COUNT(), k_leaf_sums<Src><<<g1, 256, 0, s->stream>>>(src, nleaf, ls, sums);
   QC_COUNT(), k_chunk_sums<<<unsigned(nchunk), kScanBlock, 0, s->stream>>>(sums, nleaf, chunk);
   QC_COUNT(), k_scan_chunks<<<1, kScanBlock, 0, s->stream>>>(chunk, int(nchunk));
