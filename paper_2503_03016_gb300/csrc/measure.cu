@@ -8,7 +8,7 @@
 //    associative, so any blocking gives the same cdf_k = round-to-nearest(exact
 //    prefix), which is what the sequential double-double oracle approximates to
 //    ~2^-100 relative.  The table kept between kernels is one 128-bit sum per leaf
-//    of 64 amplitudes; each shot re-derives its leaf's 64 prefix values with one warp.
+//    of 64 amplitudes; each shot re-derives its leaf's 64 prefix values with half a warp.
 #include <cmath>
 
 #include "common.cuh"
@@ -479,17 +479,20 @@ __global__ void __launch_bounds__(kScanBlock) k_leaf_offsets(U128* __restrict__ 
   }
 }
 
-// K3: one warp per shot.  Comparisons of non-negative doubles are done on their bit
-// patterns (integer pipe).  The search starts in a table of kPivots leaf ends staged in
-// shared memory per block, then continues in global memory.
+// K3: two shots per warp, one per half-warp of 16 lanes, so that every warp instruction
+// serves two shots.  Comparisons of non-negative doubles are done on their bit patterns
+// (integer pipe).  The search starts in a table of kPivots leaf ends staged in shared
+// memory per block, then continues in global memory; then each lane converts four of
+// the leaf's values and the half-warp scans their 128-bit sums.
 constexpr int kPivots = 4096;
 
 template <typename Src>
 __global__ void __launch_bounds__(256) k_draw(Src src, uint64_t nleaf, int ls, const U128* __restrict__ leaf_off,
                                               const double* __restrict__ leaf_end, const double* __restrict__ u,
                                               int64_t shots, uint64_t* __restrict__ out) {
+  constexpr unsigned kFull = 0xffffffffu;
   __shared__ uint64_t piv[kPivots];
-  const int lane = threadIdx.x & 31;
+  const int lane = threadIdx.x & 31, hl = lane & 15, half = lane >> 4;
   const uint64_t warp = (blockIdx.x * uint64_t(blockDim.x) + threadIdx.x) >> 5;
   const uint64_t nwarps = (uint64_t(gridDim.x) * blockDim.x) >> 5;
   const uint64_t Tb = dbits(leaf_end[nleaf - 1]);
@@ -502,24 +505,31 @@ __global__ void __launch_bounds__(256) k_draw(Src src, uint64_t nleaf, int ls, c
     piv[k] = dbits(leaf_end[e]);
   }
   __syncthreads();
-  for (uint64_t s = warp; s < uint64_t(shots); s += nwarps) {
-    const uint64_t tb = dbits(u[s] * T) & 0x7FFFFFFFFFFFFFFFull;  // -0 reads as +0
+  for (uint64_t s0 = 2 * warp; s0 < uint64_t(shots); s0 += 2 * nwarps) {
+    const uint64_t s = s0 + half;
+    const bool active = s < uint64_t(shots);  // an idle half searches for t = 0, writes nothing
+    const uint64_t tb = active ? dbits(u[s] * T) & 0x7FFFFFFFFFFFFFFFull : 0;  // -0 reads as +0
     const bool below = tb < Tb;
     // the test on a leaf end (false, then true, along the leaves; true at the last)
     auto pass_test = [&](uint64_t cb) { return below ? (tb < cb) : (cb >= Tb); };
-    // 32-ary search: the answer stays in [lo, hi]; each round the 32 lanes probe the
-    // ends of 32 equal parts of it and the first part whose end passes is kept
+    // 16-ary search: the answer stays in [lo, hi]; each round the 16 lanes of a half
+    // probe the ends of 16 equal parts of it and the first part whose end passes is
+    // kept.  Both halves step together (every lane takes part in the shuffles); a half
+    // whose interval is a single leaf keeps it.
     auto narrow = [&](uint64_t& lo, uint64_t& hi, auto load) {
-      while (lo < hi) {
-        const uint64_t step = (hi - lo + 32) / 32;  // ceil((hi - lo + 1) / 32) >= 1
-        uint64_t pos = lo + (uint64_t(lane) + 1) * step - 1;
+      while (__any_sync(kFull, lo < hi)) {
+        const bool open = lo < hi;
+        const uint64_t step = open ? (hi - lo + 16) / 16 : 1;  // ceil((hi - lo + 1) / 16)
+        uint64_t pos = lo + (uint64_t(hl) + 1) * step - 1;
         if (pos > hi) pos = hi;
-        const unsigned pass = __ballot_sync(0xffffffffu, pass_test(load(pos)));
-        const int k = pass ? __ffs(pass) - 1 : 31;  // lane 31 probes hi, which passes
-        const uint64_t new_hi = __shfl_sync(0xffffffffu, pos, k);
-        const uint64_t prev = __shfl_sync(0xffffffffu, pos, k > 0 ? k - 1 : 0);
-        lo = k > 0 ? prev + 1 : lo;
-        hi = new_hi;
+        const unsigned pass = (__ballot_sync(kFull, pass_test(load(pos))) >> (16 * half)) & 0xFFFFu;
+        const int k = pass ? __ffs(pass) - 1 : 15;  // lane 15 of a half probes hi, which passes
+        const uint64_t new_hi = __shfl_sync(kFull, pos, 16 * half + k);
+        const uint64_t prev = __shfl_sync(kFull, pos, 16 * half + (k > 0 ? k - 1 : 0));
+        if (open) {
+          lo = k > 0 ? prev + 1 : lo;
+          hi = new_hi;
+        }
       }
     };
     uint64_t plo = 0, phi = kPivots - 1;
@@ -528,21 +538,40 @@ __global__ void __launch_bounds__(256) k_draw(Src src, uint64_t nleaf, int ls, c
     if (hi > nleaf - 1) hi = nleaf - 1;
     narrow(lo, hi, [&](uint64_t i) { return dbits(leaf_end[i]); });
     const uint64_t leaf = lo;
-    U128 v0, v1;
-    leaf_values(src, leaf, ls, lane, v0, v1);
-    // inclusive scan of the lane pairs
-    U128 inc = add128(v0, v1);
+    // this lane's four values (elements e0 .. e0 + 3 of the leaf) and their prefix sums
+    const int e0 = 4 * hl;
+    U128 c[4];
+    const uint64_t i0 = leaf * uint64_t(ls) + e0;
+    if (e0 + 3 < ls) {
+      double p0, p1, p2, p3;
+      src.load2(i0, p0, p1);
+      src.load2(i0 + 2, p2, p3);
+      c[0] = to_fixed(p0);
+      c[1] = to_fixed(p1);
+      c[2] = to_fixed(p2);
+      c[3] = to_fixed(p3);
+    } else {
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      U128 x = shfl_up128(inc, d);
-      if (lane >= d) inc = add128(inc, x);
+      for (int q = 0; q < 4; ++q) c[q] = e0 + q < ls ? to_fixed(src.load1(i0 + q)) : U128{0, 0};
     }
-    U128 exc = shfl_up128(inc, 1);
-    if (lane == 0) exc = U128{0, 0};
-    const U128 c0 = add128(add128(leaf_off[leaf], exc), v0);  // cdf of element 2*lane
-    const U128 c1 = add128(c0, v1);                           // cdf of element 2*lane+1
-    const bool valid0 = 2 * lane < ls, valid1 = 2 * lane + 1 < ls;
-    bool hit0, hit1;
+    c[1] = add128(c[1], c[0]);
+    c[2] = add128(c[2], c[1]);
+    c[3] = add128(c[3], c[2]);
+    // inclusive scan of the lane totals over the half-warp, then the exclusive offset
+    U128 inc = c[3];
+#pragma unroll
+    for (int d = 1; d < 16; d <<= 1) {
+      U128 x;
+      x.lo = __shfl_up_sync(kFull, inc.lo, d, 16);
+      x.hi = __shfl_up_sync(kFull, inc.hi, d, 16);
+      if (hl >= d) inc = add128(inc, x);
+    }
+    U128 exc;
+    exc.lo = __shfl_up_sync(kFull, inc.lo, 1, 16);
+    exc.hi = __shfl_up_sync(kFull, inc.hi, 1, 16);
+    if (hl == 0) exc = U128{0, 0};
+    const U128 off = add128(leaf_off[leaf], exc);
+    bool hit[4];
     if (below) {
       // RN64(c) > t  <=>  c lies above the midpoint between t and the next double up,
       // or on it when t's last significand bit is 1 (the tie goes to the even
@@ -564,18 +593,20 @@ __global__ void __launch_bounds__(256) k_draw(Src src, uint64_t nleaf, int ls, c
         exact = false;
       }
       const bool tie_up = exact && (mt & 1);
-      auto above = [&](U128 c) {
-        return c.hi > M.hi || (c.hi == M.hi && (c.lo > M.lo || (tie_up && c.lo == M.lo)));
-      };
-      hit0 = valid0 && above(c0);
-      hit1 = valid1 && above(c1);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const U128 cq = add128(off, c[q]);  // cdf of element e0 + q
+        hit[q] = e0 + q < ls && (cq.hi > M.hi || (cq.hi == M.hi && (cq.lo > M.lo || (tie_up && cq.lo == M.lo))));
+      }
     } else {
-      hit0 = valid0 && pass_test(fixed_to_bits(c0));
-      hit1 = valid1 && pass_test(fixed_to_bits(c1));
+#pragma unroll
+      for (int q = 0; q < 4; ++q) hit[q] = e0 + q < ls && pass_test(fixed_to_bits(add128(off, c[q])));
     }
-    const unsigned bal = __ballot_sync(0xffffffffu, hit0 || hit1);
-    const int first = __ffs(bal) - 1;  // leaf_end[leaf] passes, so some lane hits
-    if (lane == first) out[s] = leaf * uint64_t(ls) + 2 * lane + (hit0 ? 0 : 1);
+    const bool any = hit[0] || hit[1] || hit[2] || hit[3];
+    const unsigned bal = (__ballot_sync(kFull, any) >> (16 * half)) & 0xFFFFu;
+    const int first = __ffs(bal) - 1;  // leaf_end[leaf] passes, so some lane of an active half hits
+    if (active && hl == first)
+      out[s] = leaf * uint64_t(ls) + e0 + (hit[0] ? 0 : hit[1] ? 1 : hit[2] ? 2 : 3);
   }
 }
 
@@ -599,7 +630,7 @@ static qc_status sample_impl(qc_state* s, uint64_t N, const Src& src, const doub
   QC_COUNT(), k_scan_chunks<<<1, kScanBlock, 0, s->stream>>>(chunk, int(nchunk));
   QC_COUNT(), k_leaf_offsets<<<unsigned(nchunk), kScanBlock, 0, s->stream>>>(sums, nleaf, chunk, leaf_end);
   if (shots > 0) {
-    const unsigned g3 = stream_grid(uint64_t(shots) * 32, 256, 8);
+    const unsigned g3 = stream_grid(uint64_t(shots) * 16, 256, 8);
     QC_COUNT(), k_draw<Src><<<g3, 256, 0, s->stream>>>(src, nleaf, ls, sums, leaf_end, u, shots, out);
   }
   return check_launch("sampling");

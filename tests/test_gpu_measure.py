@@ -138,6 +138,27 @@ def test_sampler_bit_exact_on_oracle_probabilities(n):
     np.testing.assert_array_equal(out.cpu().numpy().astype(np.uint64), want)
 
 
+@pytest.mark.parametrize("shots", [1, 3, 7, 1001])
+def test_sampler_odd_shot_counts(shots):
+    """A warp draws two shots; an odd count leaves the last warp's second half idle
+    (it must write nothing).  The entries past `shots` keep their sentinel."""
+    import torch
+
+    import paper_2503_03016_gb300 as P
+    n = 12
+    rng = np.random.default_rng(shots)
+    p = rng.random(1 << n) ** 2
+    p /= p.sum()
+    u = W.uniforms(shots, 40 + shots)
+    want = oracle.sample(oracle.cdf(p), u)
+    st = P.State(n, "c64").init_basis(0)
+    out = torch.full((shots + 1,), -7, dtype=torch.int64, device="cuda")
+    P.qc_sample_probs(st.handle, torch.tensor(p, device="cuda"), n, torch.tensor(u, device="cuda"), shots, out)
+    got = out.cpu().numpy()
+    np.testing.assert_array_equal(got[:shots].astype(np.uint64), want)
+    assert got[shots] == -7
+
+
 @pytest.mark.parametrize("n", [4, 10, 16])
 def test_sample_state_c128_bit_exact(n):
     import torch
