@@ -538,11 +538,8 @@ def run_adjoint_bench(args):
     ops, params, terms, coeffs = W.adjoint_workload(n, layers, 5)
     circ = P.Circuit(n, ops)
     hbm, _, _ = peaks()
-    # reverse sweep bytes: complex64 runs it as tile passes over psi and lambda together
-    # (4 S per pass); complex128 one kernel per rotation (4 S) and per CZ (both states'
-    # quarter with both bits set, 2 x 2 S / 4)
-    nrot = sum(1 for o in ops if o.kind in ("rx", "ry", "rz"))
-    ncz = sum(1 for o in ops if o.kind == "cz")
+    # reverse sweep bytes: both dtypes run it as tile passes over psi and lambda together
+    # (each pass reads and writes both states: 4 S per pass)
     res = {}
     for dt, code in (("c64", P.QC_C64), ("c128", P.QC_C128)):
         sbytes = (1 << n) * (8 if dt == "c64" else 16)
@@ -552,11 +549,8 @@ def run_adjoint_bench(args):
         for _ in range(args.steps):
             e, g = P.qc_adjoint_grad(circ, params, terms, coeffs, code)
         ms = (time.perf_counter() - t0) * 1e3 / args.steps
-        if dt == "c64":
-            passes = P.qc_last_pass_count()
-            alg, form = 4 * sbytes * passes, "fused: %d tile passes over both states" % passes
-        else:
-            alg, form = sbytes * (4 * nrot + ncz), "per rotation and per CZ"
+        passes = P.qc_last_pass_count()
+        alg, form = 4 * sbytes * passes, "fused: %d tile passes over both states" % passes
         gbs = alg / (ms * 1e-3) / 1e9
         res[dt] = {"ms_energy_and_gradient": ms, "energy": e, "grad_norm": float(np.linalg.norm(g)),
                    "reverse_sweep": form, "reverse_sweep_algorithmic_gb": alg / 1e9, "gbs": gbs,
