@@ -52,19 +52,21 @@ qc_status parse_pauli_a(int n, const char* str, ParsedTermA* out) {
 
 constexpr int kHTerms = 32;
 struct HGroup {
-  uint64_t x;
   int nt;
-  int first;  // nonzero: overwrite lambda instead of accumulating
+  int first;                          // nonzero: overwrite lambda instead of accumulating
+  uint64_t x[kHTerms];                // X-or-Y mask of each term; equal masks are adjacent
   uint64_t z[kHTerms];
   double cre[kHTerms], cim[kHTerms];  // coeff * i^nY
   float fre[kHTerms], fim[kHTerms];   // the same, rounded to FP32 (complex64 states)
 };
 
-// lambda_k (+)= sum_t c_t i^nY (-1)^popc((k^x) & z_t) psi_{k^x}.  Two neighbouring k per
-// step (k even): their sources k^x and (k+1)^x are the two halves of one aligned pair,
-// read with one access and swapped when x has bit 0.  The coefficient sum and the
-// product are formed at the state's precision (complex64: FP32, whose result is stored
-// in FP32 anyway; complex128: FP64); a term's sign is a select, not a product.
+// lambda_k (+)= sum_t c_t i^nY (-1)^popc((k^x_t) & z_t) psi_{k^x_t} over up to kHTerms
+// terms of one or more X masks, so that lambda is read and written once per launch and
+// psi is read once per distinct mask.  Two neighbouring k per step (k even): their
+// sources k^x and (k+1)^x are the two halves of one aligned pair, read with one access
+// and swapped when x has bit 0.  The coefficient sums and products are formed at the
+// state's precision (complex64: FP32, whose result is stored in FP32 anyway;
+// complex128: FP64); a term's sign is a select, not a product.
 template <typename R>
 __device__ __forceinline__ R hsum_re(const HGroup& g, int t) {
   if constexpr (sizeof(R) == 4) return g.fre[t]; else return g.cre[t];
@@ -79,7 +81,7 @@ __global__ void __launch_bounds__(256) k_apply_hsum(const R* __restrict__ psi, R
                                                     HGroup g) {
   const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
   const uint64_t tid = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x;
-  if (N < 2) {  // a single amplitude (x = 0)
+  if (N < 2) {  // a single amplitude (every x is 0)
     if (tid == 0) {
       const Cplx<R> p = ld_amp<R>(psi, 0);
       R fr = R(0), fi = R(0);
@@ -97,32 +99,32 @@ __global__ void __launch_bounds__(256) k_apply_hsum(const R* __restrict__ psi, R
     }
     return;
   }
-  const bool swap = g.x & 1;
   for (uint64_t it = tid; it < N / 2; it += stride) {
     const uint64_t k = 2 * it;
-    const uint64_t j0 = k ^ g.x;  // source of k; (k + 1)'s source is j0 ^ 1
-    Cplx<R> a, b;
-    ld_amp2<R>(psi, j0 & ~uint64_t(1), a, b);
-    const Cplx<R> p0 = swap ? b : a, p1 = swap ? a : b;
-    R f0r = R(0), f0i = R(0), f1r = R(0), f1i = R(0);
-    for (int t = 0; t < g.nt; ++t) {
-      const R cr = hsum_re<R>(g, t), ci = hsum_im<R>(g, t);
-      const bool s0 = __popcll(j0 & g.z[t]) & 1;
-      const bool s1 = s0 ^ bool(g.z[t] & 1);
-      f0r += s0 ? -cr : cr;
-      f0i += s0 ? -ci : ci;
-      f1r += s1 ? -cr : cr;
-      f1i += s1 ? -ci : ci;
-    }
-    Cplx<R> o0{f0r * p0.re - f0i * p0.im, f0r * p0.im + f0i * p0.re};
-    Cplx<R> o1{f1r * p1.re - f1i * p1.im, f1r * p1.im + f1i * p1.re};
-    if (!g.first) {
-      Cplx<R> l0, l1;
-      ld_amp2<R>(lam, k, l0, l1);
-      o0.re += l0.re;
-      o0.im += l0.im;
-      o1.re += l1.re;
-      o1.im += l1.im;
+    Cplx<R> o0{R(0), R(0)}, o1{R(0), R(0)};
+    if (!g.first) ld_amp2<R>(lam, k, o0, o1);
+    int t = 0;
+    while (t < g.nt) {
+      // the terms of one X mask (the same for every thread: no divergence)
+      const uint64_t x = g.x[t];
+      const uint64_t j0 = k ^ x;  // source of k; (k + 1)'s source is j0 ^ 1
+      Cplx<R> a, b;
+      ld_amp2<R>(psi, j0 & ~uint64_t(1), a, b);
+      const Cplx<R> p0 = (x & 1) ? b : a, p1 = (x & 1) ? a : b;
+      R f0r = R(0), f0i = R(0), f1r = R(0), f1i = R(0);
+      do {
+        const R cr = hsum_re<R>(g, t), ci = hsum_im<R>(g, t);
+        const bool s0 = __popcll(j0 & g.z[t]) & 1;
+        const bool s1 = s0 ^ bool(g.z[t] & 1);
+        f0r += s0 ? -cr : cr;
+        f0i += s0 ? -ci : ci;
+        f1r += s1 ? -cr : cr;
+        f1i += s1 ? -ci : ci;
+      } while (++t < g.nt && g.x[t] == x);
+      o0.re += f0r * p0.re - f0i * p0.im;
+      o0.im += f0r * p0.im + f0i * p0.re;
+      o1.re += f1r * p1.re - f1i * p1.im;
+      o1.im += f1r * p1.im + f1i * p1.re;
     }
     st_amp2<R>(lam, k, o0, o1);
   }
@@ -307,30 +309,30 @@ static qc_status adjoint_impl(const qc_circuit* c, const double* params, int npa
                     : run_per_gate(&s, c, params)))
     goto done;
   {
-    // lambda = H psi, grouped by X mask
-    std::map<uint64_t, std::vector<int>> groups;
-    for (size_t t = 0; t < terms.size(); ++t) groups[terms[t].x].push_back(int(t));
+    // lambda = H psi: the terms ordered by X mask, up to kHTerms per launch
+    std::vector<int> order(terms.size());
+    for (size_t t = 0; t < terms.size(); ++t) order[t] = int(t);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return terms[a].x < terms[b].x; });
     bool first = true;
     const unsigned g2 = stream_grid(N / 2 ? N / 2 : 1, B);
-    for (auto& kv : groups)
-      for (size_t b0 = 0; b0 < kv.second.size(); b0 += kHTerms) {
-        HGroup hg{};
-        hg.x = kv.first;
-        hg.first = first ? 1 : 0;
-        first = false;
-        hg.nt = int(std::min<size_t>(kHTerms, kv.second.size() - b0));
-        for (int j = 0; j < hg.nt; ++j) {
-          const ParsedTermA& t = terms[kv.second[b0 + j]];
-          const double cf = coeffs ? coeffs[kv.second[b0 + j]] : 1.0;
-          const int ny = t.ny & 3;  // i^ny
-          hg.z[j] = t.z;
-          hg.cre[j] = ny == 0 ? cf : ny == 2 ? -cf : 0.0;
-          hg.cim[j] = ny == 1 ? cf : ny == 3 ? -cf : 0.0;
-          hg.fre[j] = float(hg.cre[j]);
-          hg.fim[j] = float(hg.cim[j]);
-        }
-        QC_COUNT(), k_apply_hsum<R><<<g2, B, 0, stream>>>(reinterpret_cast<const R*>(s.amps), lam, N, hg);
+    for (size_t b0 = 0; b0 < order.size(); b0 += kHTerms) {
+      HGroup hg{};
+      hg.first = first ? 1 : 0;
+      first = false;
+      hg.nt = int(std::min<size_t>(kHTerms, order.size() - b0));
+      for (int j = 0; j < hg.nt; ++j) {
+        const ParsedTermA& t = terms[order[b0 + j]];
+        const double cf = coeffs ? coeffs[order[b0 + j]] : 1.0;
+        const int ny = t.ny & 3;  // i^ny
+        hg.x[j] = t.x;
+        hg.z[j] = t.z;
+        hg.cre[j] = ny == 0 ? cf : ny == 2 ? -cf : 0.0;
+        hg.cim[j] = ny == 1 ? cf : ny == 3 ? -cf : 0.0;
+        hg.fre[j] = float(hg.cre[j]);
+        hg.fim[j] = float(hg.cim[j]);
       }
+      QC_COUNT(), k_apply_hsum<R><<<g2, B, 0, stream>>>(reinterpret_cast<const R*>(s.amps), lam, N, hg);
+    }
     if (first) {  // empty Hamiltonian
       cudaMemsetAsync(lam, 0, sbytes, stream);
     }
