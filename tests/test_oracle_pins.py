@@ -260,6 +260,29 @@ def test_ghz_closed_forms(n):
     np.testing.assert_allclose(oracle.expect_pauli(psi, ["X" * n]), [1.0], atol=1e-14)
 
 
+def test_pauli_expectation_product_state_closed_form():
+    """RY(t_q) on qubit q of |0...0> (Sec. 2 gate definitions, qubit 0 the most
+    significant): <Z_q> = cos t_q, <X_q> = sin t_q, <Y_q> = 0, and a string on several
+    qubits is the product of its factors.  Distinct angles pin the character-to-qubit
+    order and the signs independently of the dense Kronecker reference."""
+    n = 6
+    rng = np.random.default_rng(12)
+    t = rng.uniform(0.2, 2.9, n)
+    psi = oracle.run(oracle.basis_state(n, 0), [Op("ry", (q,), (float(t[q]),)) for q in range(n)])
+    single = {"Z": np.cos, "X": np.sin, "Y": lambda a: 0.0 * a}
+    strings, want = [], []
+    for spec in [(("Z", 0),), (("Z", 5),), (("X", 2),), (("Y", 3),), (("Z", 0), ("Z", 1)),
+                 (("X", 1), ("Z", 4)), (("Z", 0), ("X", 3), ("Z", 5)), (("X", 0), ("X", 5))]:
+        s_ = ["I"] * n
+        v = 1.0
+        for c, q in spec:
+            s_[q] = c
+            v *= single[c](t[q])
+        strings.append("".join(s_))
+        want.append(v)
+    np.testing.assert_allclose(oracle.expect_pauli(psi, strings), want, atol=1e-14)
+
+
 def test_pauli_expectation_vs_dense():
     n = 5
     rng = np.random.default_rng(11)
