@@ -220,11 +220,17 @@ __global__ void k_sum2_adj(const double* partials, int count, double* out) {
   }
 }
 
+// grad[p] = the sum of the recorded rotations g with params[g] == p, added in gate order
+// (the order a serial loop over g would use, so the result does not depend on the
+// launch); one thread per parameter.
 __global__ void k_collect_grads(const double* partials, int nblocks, const int* params, int nrot, double* grad,
                                 int nparams) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
-  for (int p = 0; p < nparams; ++p) grad[p] = 0.0;
-  for (int g = 0; g < nrot; ++g) grad[params[g]] += partials[size_t(g) * nblocks];
+  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < nparams; p += gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int g = 0; g < nrot; ++g)
+      if (params[g] == p) acc += partials[size_t(g) * nblocks];
+    grad[p] = acc;
+  }
 }
 
 // Per-process device workspace of the adjoint sweep (three state buffers and partials).
@@ -388,7 +394,8 @@ static qc_status adjoint_impl(const qc_circuit* c, const double* params, int npa
         goto done;
       QC_COUNT(), k_reduce_grads<<<std::min(nrot, 1024), 1024, 0, stream>>>(part, pgrid, nrot);
     }
-    QC_COUNT(), k_collect_grads<<<1, 32, 0, stream>>>(part, pgrid, dparams, nrot, grad, nparams);
+    QC_COUNT(), k_collect_grads<<<unsigned(std::max(1, (nparams + 255) / 256)), 256, 0, stream>>>(part, pgrid, dparams,
+                                                                                                nrot, grad, nparams);
     if ((st = check_launch("adjoint sweep"))) goto done;
     std::vector<double> e(2);
     if ((st = check_cuda(cudaMemcpyAsync(e.data(), inner + 2 * grid, 2 * sizeof(double), cudaMemcpyDeviceToHost,
