@@ -48,6 +48,46 @@ def peaks():
         return 6800.0, 1900.0, "fallback"
 
 
+_TF32_PEAK = None
+
+
+def tf32_peak():
+    """Dense TF32 tensor throughput measured on this GPU: torch FP32 matmul of 8192^3
+    with TF32 allowed (2 N^3 flops), best of 10, CUDA events.  The library never calls
+    this; it is the roofline denominator of the TF32 tensor-core kernels."""
+    global _TF32_PEAK
+    if _TF32_PEAK is None:
+        import torch
+        prev = torch.backends.cuda.matmul.allow_tf32
+        torch.backends.cuda.matmul.allow_tf32 = True
+        try:
+            N = 8192
+            a = torch.randn(N, N, device="cuda")
+            b = torch.randn(N, N, device="cuda")
+            c = torch.empty(N, N, device="cuda")
+            for _ in range(3):
+                torch.matmul(a, b, out=c)
+            best = None
+            for _ in range(10):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record()
+                torch.matmul(a, b, out=c)
+                e1.record()
+                e1.synchronize()
+                ms = e0.elapsed_time(e1)
+                best = ms if best is None else min(best, ms)
+            _TF32_PEAK = 2.0 * N ** 3 / (best * 1e-3) / 1e12
+            del a, b, c
+            torch.cuda.empty_cache()
+        finally:
+            torch.backends.cuda.matmul.allow_tf32 = prev
+    return _TF32_PEAK
+
+
+TF32_PEAK_SRC = "measured: torch FP32 matmul 8192^3 with TF32 allowed, best of 10"
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -158,6 +198,50 @@ def oracle_rate(gates_per_step: int, steps: int, warmup: int, ops):
             times.append(dt)
     t = sum(times)
     return (gates_per_step * steps / len(ops)) / t, t / steps, oracle.num_threads()
+
+
+def oracle_step_baseline(ops, gates: int, single_gates: int):
+    """The oracle timed on one step of the workload: `gates` of the brickwork's gates
+    (extrapolated to all of them) plus the whole readout on the resulting 28-qubit
+    state -- FP64 probabilities, the double-double CDF, 1e6 shots by bisection and
+    <sum Z_i Z_i+1> -- on all host threads; and `single_gates` gates on one thread."""
+    import oracle
+    threads = oracle.num_threads()
+    psi = oracle.basis_state(N_QUBITS, 0)
+    t0 = time.perf_counter()
+    for i in range(gates):
+        oracle.apply_op(psi, ops[i])
+    t_gate = (time.perf_counter() - t0) / gates
+    u = W.uniforms(SHOTS, SHOT_SEED)
+    # Z_i Z_i+1: z mask on index bits n-1-i and n-2-i
+    zz = [(0, 3 << (N_QUBITS - 2 - i), 1.0) for i in range(N_QUBITS - 1)]
+    t0 = time.perf_counter()
+    p = oracle.probs(psi)
+    c = oracle.cdf(p)
+    oracle.sample(c, u)
+    del p, c
+    oracle.expect_masks(psi, zz)
+    t_read = time.perf_counter() - t0
+    t1 = None
+    if single_gates > 0:
+        oracle.set_threads(1)
+        try:
+            t0 = time.perf_counter()
+            for i in range(single_gates):
+                oracle.apply_op(psi, ops[gates + i])
+            t1 = (time.perf_counter() - t0) / single_gates
+        finally:
+            oracle.set_threads(threads)
+    step_s = t_gate * len(ops) + t_read
+    out = {"value": 1.0 / step_s, "unit": "circuits/s", "cores": threads, "kind": "oracle",
+           "sample": ("%d of %d brickwork gates on 28 qubits (complex128) extrapolated to the circuit, plus the "
+                      "whole readout (FP64 probabilities, CDF, 1e6 shots, <sum ZZ>) timed once" % (gates, len(ops))),
+           "readout_s": t_read, "readout_share": t_read / step_s, "gate_s": t_gate}
+    if t1 is not None:
+        out["one_thread"] = {"value": 1.0 / (t1 * len(ops) + t_read * threads), "unit": "circuits/s",
+                             "gate_s": t1, "sample": "%d gates on one thread; readout scaled by the thread count"
+                                                     % single_gates}
+    return out
 
 
 def run_reference(args):
@@ -297,14 +381,14 @@ def run_ours(args):
         # 2 * 64 * 64 * 128 * 3 / 4096 = 768 flops per amplitude per stage.
         stages = P.qc_last_stage_count()
         flops = stages * 768.0 * (1 << N_QUBITS)
-        tf32_peak = bf16_tflops * 1.1 / 2.25
+        tf32_pk = tf32_peak()
         achieved = flops / (circ_ms * 1e-3) / 1e12
         # DRAM bytes of one tensor-core tile pass in an ncu capture at 26 qubits
         # (1013.25 MB), scaled by the larger state
-        roof = {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
-                "frac": achieved / tf32_peak, "traffic": 1013.248768e6 * (1 << (N_QUBITS - 26)),
+        roof = {"bound": "tensor", "achieved": achieved, "peak": tf32_pk, "unit": "TFLOP/s",
+                "frac": achieved / tf32_pk, "traffic": 1013.248768e6 * (1 << (N_QUBITS - 26)),
                 "traffic_note": "per pass, ncu at 26 qubits scaled by 2^(n-26)",
-                "peak_source": "%s bf16 x 1.1/2.25 (nominal dense TF32/BF16 ratio)" % peak_src,
+                "peak_source": TF32_PEAK_SRC,
                 "kernel": "k_tile_pass_tc", "passes": passes, "stages": stages,
                 "gate_tflops_fp32_equivalent": len(ops) * 32.0 * (1 << N_QUBITS) / (circ_ms * 1e-3) / 1e12}
     elif args.mode == "fused":
@@ -331,9 +415,7 @@ def run_ours(args):
     # cpu baseline (rank 0, N=1 only)
     cpu = None
     if rank == 0 and world == 1 and args.cpu_gates > 0:
-        rate, _, cores = oracle_rate(args.cpu_gates, 1, 0, ops)
-        cpu = {"value": rate, "unit": "circuits/s", "cores": cores, "kind": "oracle",
-               "sample": "%d of %d brickwork gates on 28 qubits (complex128), extrapolated" % (args.cpu_gates, len(ops))}
+        cpu = oracle_step_baseline(ops, args.cpu_gates, args.cpu_single_gates)
     if rank == 0:
         steps_total = args.steps * world
         line = {
@@ -414,7 +496,7 @@ def run_block_bench(args):
     torch.cuda.set_device(0)
     n = args.qubits or 28
     hbm, bf16, _ = peaks()
-    tf32_peak = bf16 * 1.1 / 2.25
+    tf32_pk = tf32_peak()
     st = P.State(n, "c64").init_gaussian(7)
     stream = torch.cuda.current_stream()
     res = {}
@@ -435,13 +517,13 @@ def run_block_bench(args):
             tf = flops / (ms * 1e-3) / 1e12
             r = {"ms": ms, "gbs": gbs, "frac_hbm": gbs / hbm, "tflops": tf}
             if prec == P.QC_PREC_TF32X3:
-                r["frac_tf32"] = tf / tf32_peak
+                r["frac_tf32"] = tf / tf32_pk
             else:
                 r["frac_alu"] = tf / ALU_PEAK_TF
             res["k%d_%s" % (k, name)] = r
     print(json.dumps({"metric": "fused 5- and 6-qubit blocks on %d qubits" % n, "results": res,
-                      "peaks": {"hbm_gbs": hbm, "tf32_tflops": tf32_peak, "alu_tflops": ALU_PEAK_TF,
-                                "tf32_source": "measured bf16 x 1.1/2.25 (nominal TF32/BF16 dense ratio)"}}))
+                      "peaks": {"hbm_gbs": hbm, "tf32_tflops": tf32_pk, "alu_tflops": ALU_PEAK_TF,
+                                "tf32_source": TF32_PEAK_SRC}}))
 
 
 def run_qft_bench(args):
@@ -498,7 +580,7 @@ def run_window_bench(args):
     n = args.qubits or 28
     _, bf16, src = peaks()
     sm_peak = torch.cuda.get_device_properties(0).multi_processor_count * 128 * 2 * 2070e6 / 1e12
-    tf32_peak = bf16 * 1.1 / 2.25
+    tf32_pk = tf32_peak()
     stream = torch.cuda.current_stream()
     st = P.State(n, "c64").init_gaussian(3)
     res = {}
@@ -518,14 +600,14 @@ def run_window_bench(args):
                  "stages": P.qc_last_stage_count(), "gate_tflops_fp32_equivalent": gate_tf}
             if r["path"] == 2:
                 tf = r["stages"] * 768.0 * (1 << n) / (ms * 1e-3) / 1e12
-                r.update({"tf32_tflops": tf, "frac_tf32_peak": tf / tf32_peak})
+                r.update({"tf32_tflops": tf, "frac_tf32_peak": tf / tf32_pk})
             else:
                 r.update({"frac_fp32_peak": gate_tf / sm_peak})
             res["w%d_%s" % (width, name)] = r
     st.free()
     print(json.dumps({"metric": "540 Haar gates on the lowest 5 / 10 of %d qubits (complex64)" % n,
-                      "results": res, "peaks": {"fp32_tflops": sm_peak, "tf32_tflops": tf32_peak,
-                                                "tf32_source": "%s bf16 x 1.1/2.25" % src}}))
+                      "results": res, "peaks": {"fp32_tflops": sm_peak, "tf32_tflops": tf32_pk,
+                                                "tf32_source": TF32_PEAK_SRC}}))
 
 
 def run_adjoint_bench(args):
@@ -632,7 +714,8 @@ def main():
     ap.add_argument("--mode", default="fused", choices=["fused", "per_gate"])
     ap.add_argument("--prec", default="native", choices=["native", "tf32x3"])
     ap.add_argument("--plain-steps", type=int, default=1)
-    ap.add_argument("--cpu-gates", type=int, default=24)
+    ap.add_argument("--cpu-gates", type=int, default=16)
+    ap.add_argument("--cpu-single-gates", type=int, default=2)
     ap.add_argument("--ref-gates", type=int, default=8)
     ap.add_argument("--batch-range", default=None, help="batch workload: profile only circuits with LO-HI qubits")
     ap.add_argument("--batch-count", type=int, default=0, help="batch workload: at most this many of them")

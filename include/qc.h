@@ -222,9 +222,11 @@ qc_status qc_expect_pauli(const qc_state* s, const char* const* strings, const d
  * until the process exits.  Limits: at most 256 terms per call (more is rejected with
  * QC_ERR_INVALID_ARG and a message); the reduction grid is capped at 1216 blocks
  * (608 blocks x 32 partial sums for the Z-only strings, in the same array).
- * The first call on a device resolves the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before any
- * stream capture.  All calls share the array and it keeps the last call's contents:
+ * Every call looks up the array's device address (cudaGetSymbolAddress, which
+ * allocates nothing) with the state's device current, so the address stays valid
+ * after a device reset; the first call on a device may load the library's device
+ * code there, so make that first call before any stream capture.  All calls share
+ * the array and it keeps the last call's contents:
  * calls whose work overlaps on the GPU (other threads, other streams) race and must
  * be serialised by the caller.  Calls no cudaMalloc/cudaFree.  Synchronising. */
 qc_status qc_expect_pauli_noalloc(const qc_state* s, const char* const* strings, const double* coeffs, int nterms,

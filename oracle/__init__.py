@@ -49,10 +49,12 @@ def lib():
             "orc_cdf": (None, [D, i64, D]),
             "orc_sample": (None, [D, i64, D, i64, U64]),
             "orc_inner": (None, [D, D, i64, D]),
+            "orc_expect_masks": (None, [D, c_int, u64, u64, D]),
             "orc_gaussian_amplitudes": (None, [u64, i64, i64, D]),
             "orc_gaussian_norm2": (c_double, [u64, c_int]),
             "orc_dft_gaussian": (None, [u64, c_int, c_double, c_int, U64, c_int, D]),
             "orc_num_threads": (c_int, []),
+            "orc_set_threads": (None, [c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -78,6 +80,11 @@ def _mat(U: np.ndarray) -> np.ndarray:
 
 def num_threads() -> int:
     return int(lib().orc_num_threads())
+
+
+def set_threads(t: int) -> None:
+    """Thread count of the oracle's parallel loops (for timing)."""
+    lib().orc_set_threads(int(t))
 
 
 # ---------------------------------------------------------------------------
@@ -337,6 +344,28 @@ def expect_pauli(psi: np.ndarray, strings: Sequence[str], coeffs=None) -> np.nda
     if coeffs is not None:
         out = out * np.asarray(coeffs, dtype=np.float64)
     return out
+
+
+def expect_masks(psi: np.ndarray, terms) -> np.ndarray:
+    """coeff * <psi| P |psi> for Pauli terms (xmask, zmask, coeff) on index bits:
+    bit b set in x only is X on the qubit of index bit b (qubit n-1-b), in z only Z,
+    in both Y.  Written from the definition P|j> = i^{|x&z|} (-1)^{|j&z|} |j^x>
+    (``orc_expect_masks``); real part returned."""
+    n = _n_of(psi)
+    out = np.empty(len(terms))
+    buf = np.zeros(2)
+    for t, (x, z, c) in enumerate(terms):
+        lib().orc_expect_masks(_dp(psi.view(np.float64)), n, ctypes.c_uint64(int(x)), ctypes.c_uint64(int(z)),
+                               _dp(buf))
+        out[t] = float(c) * buf[0]
+    return out
+
+
+def energy_masks(n: int, ops, params, terms) -> float:
+    """<H> of the circuit's output from |0...0> for H given as mask terms."""
+    psi = basis_state(n, 0)
+    run(psi, ops, params)
+    return float(np.sum(expect_masks(psi, terms)))
 
 
 def energy(n: int, ops, params, strings, coeffs) -> float:

@@ -243,6 +243,38 @@ void orc_inner(const double* a, const double* b, int64_t N, double* out) {
   out[1] = si;
 }
 
+/*
+ * <psi| P |psi> for a Pauli term given by index-bit masks (x, z): P acts on the
+ * qubit of index bit b as X if only x has bit b, Z if only z has it, Y if both, so
+ * P = i^{|x & z|} X^x Z^z (Y = iXZ) and P|j> = i^{|x & z|} (-1)^{|j & z|} |j ^ x>.
+ * Hence <psi|P|psi> = i^{|x & z|} sum_j conj(psi_{j^x}) (-1)^{|j & z|} psi_j, written
+ * out term by term (Sec. 5.2 estimates a density matrix from such expectations).
+ * out = (re, im); the imaginary part is zero up to rounding for a Hermitian P.
+ */
+void orc_expect_masks(const double* psi, int n, uint64_t x, uint64_t z, double* out) {
+  const int64_t N = (int64_t)1 << n;
+  double sr = 0.0, si = 0.0;
+#pragma omp parallel for schedule(static) reduction(+ : sr, si)
+  for (int64_t j = 0; j < N; ++j) {
+    const int64_t k = (int64_t)((uint64_t)j ^ x);
+    const double sgn = (__builtin_popcountll((uint64_t)j & z) & 1) ? -1.0 : 1.0;
+    double tr, ti;
+    cmul(RE(psi, k), -IM(psi, k), RE(psi, j), IM(psi, j), &tr, &ti);
+    sr += sgn * tr;
+    si += sgn * ti;
+  }
+  /* multiply by i^{|x & z|} */
+  const int ny = __builtin_popcountll(x & z) & 3;
+  double r = sr, i = si;
+  for (int t = 0; t < ny; ++t) {
+    const double nr = -i;
+    i = r;
+    r = nr;
+  }
+  out[0] = r;
+  out[1] = i;
+}
+
 /* ---------------------------------------------------------------------------
  * Seeded start states regenerated from the amplitude index (so that 2^32-amplitude
  * states need no host copy).  SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) used as a
@@ -333,6 +365,16 @@ void orc_dft_gaussian(uint64_t seed, int n, double norm2, int round_c64, const u
   }
   const double sc = 1.0 / sqrt((double)N);
   for (int t = 0; t < 2 * nk; ++t) out[t] *= sc;
+}
+
+/* thread count of the parallel loops (timing of the CPU baseline; results do not
+ * depend on it except for the summation order of reductions) */
+void orc_set_threads(int t) {
+#ifdef _OPENMP
+  if (t > 0) omp_set_num_threads(t);
+#else
+  (void)t;
+#endif
 }
 
 int orc_num_threads(void) {

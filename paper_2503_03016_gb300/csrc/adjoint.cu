@@ -14,6 +14,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <mutex>
 #include <vector>
 
 #include "adjoint_tiles.cuh"
@@ -241,6 +242,10 @@ struct AdjWork {
 };
 static AdjWork g_adj;
 static AdjPlanBuf g_adj_plan;
+// The workspace above belongs to the process: calls are serialised from workspace
+// sizing to their last use of it (a concurrent call could otherwise free or overwrite
+// the buffers while another call's kernels still use them).
+static std::mutex g_adj_mu;
 
 template <typename R>
 static qc_status adjoint_impl(const qc_circuit* c, const double* params, int nparams,
@@ -433,6 +438,7 @@ extern "C" qc_status qc_adjoint_grad(const qc_circuit* c, const double* params, 
   for (int t = 0; t < nterms; ++t)
     if (qc_status st = parse_pauli_a(c->n, strings[t], &terms[t])) return st;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lock(g_adj_mu);
   if (dtype == QC_C64)
     return adjoint_impl<float>(c, params, nparams, terms, coeffs, dtype, s, host_energy, host_grad);
   return adjoint_impl<double>(c, params, nparams, terms, coeffs, dtype, s, host_energy, host_grad);

@@ -381,28 +381,18 @@ constexpr size_t kNoAllocDoubles = size_t(kNoAllocMaxBlocks) * kMaxTermsPerPass 
 // until the process exits.  Shared by all calls: each call overwrites it.
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
 
-// Device address of g_noalloc_scratch for each device, resolved once per device.
-static double* g_noalloc_ptr[64] = {nullptr};
-static std::mutex g_noalloc_mu;
-
+// Device address of g_noalloc_scratch on `device`, looked up on every call (the
+// lookup allocates nothing; a cached address would go stale after a device reset).
 static qc_status noalloc_scratch(int device, double** out) {
-  if (device < 0 || device >= 64) {
-    set_error("qc_expect_pauli_noalloc: device %d out of range", device);
-    return QC_ERR_INVALID_ARG;
-  }
-  std::lock_guard<std::mutex> lock(g_noalloc_mu);
-  if (!g_noalloc_ptr[device]) {
-    int cur = -1;
-    if (qc_status st = check_cuda(cudaGetDevice(&cur), "cudaGetDevice")) return st;
-    if (cur != device)
-      if (qc_status st = check_cuda(cudaSetDevice(device), "cudaSetDevice")) return st;
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (cur != device) cudaSetDevice(cur);
-    if (qc_status st = check_cuda(e, "cudaGetSymbolAddress(noalloc scratch)")) return st;
-    g_noalloc_ptr[device] = static_cast<double*>(p);
-  }
-  *out = g_noalloc_ptr[device];
+  int cur = -1;
+  if (qc_status st = check_cuda(cudaGetDevice(&cur), "cudaGetDevice")) return st;
+  if (cur != device)
+    if (qc_status st = check_cuda(cudaSetDevice(device), "cudaSetDevice")) return st;
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (cur != device) cudaSetDevice(cur);
+  if (qc_status st = check_cuda(e, "cudaGetSymbolAddress(noalloc scratch)")) return st;
+  *out = static_cast<double*>(p);
   return QC_OK;
 }
 

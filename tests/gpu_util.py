@@ -23,3 +23,16 @@ def need_gpu():
     torch = pytest.importorskip("torch")
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
+
+
+def record(name: str, **vals) -> None:
+    """Appends the achieved error of a parity check to the JSON-lines file named by
+    QC_PARITY_LOG (if set), so that the errors behind each tolerance can be reported."""
+    import json
+    import os
+    path = os.environ.get("QC_PARITY_LOG")
+    if not path:
+        return
+    with open(path, "a") as f:
+        f.write(json.dumps(dict(test=name, **{k: (float(v) if isinstance(v, (np.floating, float)) else v)
+                                              for k, v in vals.items()})) + "\n")

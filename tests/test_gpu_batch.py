@@ -9,7 +9,7 @@ import pytest
 import oracle
 import workloads as W
 
-from gpu_util import need_gpu
+from gpu_util import need_gpu, record
 
 pytestmark = pytest.mark.gpu
 
@@ -38,16 +38,23 @@ def oracle_value(n, layers, p32):
     return oracle.energy(n, ops, p32.astype(np.float64), terms, np.ones(len(terms)))
 
 
+def check_values(got, want, ns, name):
+    """<sum ZZ> has n - 1 terms of size <= 1; the complex64 target (1e-5 relative) is
+    read as an error of at most 1e-5 times the scale sum_i |<Z_i Z_i+1>| <= n - 1 of
+    the value, per circuit.  The achieved errors are recorded."""
+    err = np.abs(np.asarray(got) - np.asarray(want)) / (np.asarray(ns, dtype=np.float64) - 1)
+    record(name, max_err_over_scale=float(err.max()), circuits=len(err))
+    assert err.max() <= 1e-5, err.max()
+
+
 def test_small_mixed_batch():
     rng = np.random.default_rng(11)
     layers = 3
     ns = [int(x) for x in rng.integers(6, 16, 40)]
     params = [rng.uniform(0, 2 * np.pi, layers * 2 * n) for n in ns]
     got, flat, offs, _ = run_batch(ns, params, layers)
-    for i, n in enumerate(ns):
-        p32 = flat[offs[i]:offs[i] + layers * 2 * n]
-        want = oracle_value(n, layers, p32)
-        assert abs(got[i] - want) <= 2e-5 * n, (i, n, got[i], want)
+    want = np.array([oracle_value(n, layers, flat[offs[i]:offs[i] + layers * 2 * n]) for i, n in enumerate(ns)])
+    check_values(got, want, ns, "batch_small_mixed")
 
 
 @pytest.mark.slow
@@ -67,8 +74,6 @@ def test_batch_4096_sampled_against_oracle():
     np.testing.assert_array_equal(got, out.cpu().numpy())
     rng = np.random.default_rng(4)
     pick = list(rng.choice(4096, 16, replace=False)) + [int(np.argmax(ns)), int(np.argmin(ns))]
-    for i in pick:
-        n = int(ns[i])
-        p32 = flat[offs[i]:offs[i] + layers * 2 * n]
-        want = oracle_value(n, layers, p32)
-        assert abs(got[i] - want) <= 2e-5 * n, (i, n, got[i], want)
+    want = np.array([oracle_value(int(ns[i]), layers, flat[offs[i]:offs[i] + layers * 2 * int(ns[i])])
+                     for i in pick])
+    check_values(got[pick], want, ns[pick], "batch_4096_sampled")

@@ -7,7 +7,7 @@ import oracle
 import workloads as W
 from workloads import Op
 
-from gpu_util import TOL, gpu_state, need_gpu, rel_l2
+from gpu_util import TOL, gpu_state, need_gpu, record, rel_l2
 
 pytestmark = pytest.mark.gpu
 DTYPES = ["c128", "c64"]
@@ -86,7 +86,9 @@ def test_fused_qft(dtype, n):
 def test_fused_mixed(dtype, n):
     ops = mixed_circuit(n, n)
     got, want, _ = run_both(n, ops, dtype)
-    assert rel_l2(got, want) <= TOL[dtype] * 10
+    err = rel_l2(got, want)
+    record("fused_mixed", n=n, dtype=dtype, rel_l2=err)
+    assert err <= TOL[dtype]
 
 
 @pytest.mark.parametrize("dtype", DTYPES)
@@ -123,7 +125,9 @@ def test_fused_cz_runs(dtype, n):
         ops.append(Op("u2q", (b, a), matrix=np.diag([1j, 1j, 1j, -1j])))
         ops.append(Op("cz", (a, (a + 1) % n)))
     got, want, _ = run_both(n, ops, dtype)
-    assert rel_l2(got, want) <= TOL[dtype] * 10
+    err = rel_l2(got, want)
+    record("fused_cz_runs", n=n, dtype=dtype, rel_l2=err)
+    assert err <= TOL[dtype]
 
 
 @pytest.mark.parametrize("dtype", DTYPES)

@@ -1,0 +1,228 @@
+"""Parity against the oracle at the benchmark's sizes and above 2^32 amplitudes.
+
+* The Haar brickwork of depth 40 (seed 2) on 24 qubits (460 gates) and on 28 qubits
+  (540 gates, the benchmark circuit), element by element against ``oracle.run``:
+  fused tile passes on the CUDA cores, fused passes with tensor-core stages (TF32x3)
+  and the plain complex128 per-gate sweeps (Sec. 3.2 one gate at a time).
+* 32 qubits (2^32 amplitudes, indices above 2^32 in every sweep): the per-gate
+  quantum Fourier transform of a sparse start state against the DFT closed form;
+  probabilities, inverse-CDF shots, outcome probabilities and collapse (Sec. 3.3) on a
+  sparse state whose probabilities are dyadic, so that the CDF and the drawn indices
+  are known exactly.
+* The 24-qubit adjoint workload (480 parameters): energy against ``oracle.energy`` and
+  gradient entries against the oracle's own central differences (each parameter enters
+  one rotation, so a central difference with step h is f'(t) sin(h)/h exactly).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+from gpu_util import TOL, need_gpu, record, rel_l2
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(autouse=True)
+def _gpu():
+    need_gpu()
+
+
+def _free_gb():
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    return free / 2 ** 30
+
+
+def _norm(t) -> float:
+    """FP64 norm of a device state, summed in chunks of 2^26 amplitudes (no full-size
+    complex128 copy of a 32-qubit complex64 state)."""
+    import torch
+    acc = 0.0
+    step = 1 << 26
+    for i in range(0, t.numel(), step):
+        c = t[i:i + step].to(torch.complex128)
+        acc += float(torch.sum(c.real * c.real + c.imag * c.imag).item())
+    return acc ** 0.5
+
+
+_ORACLE = {}
+
+
+def _oracle_brickwork(n):
+    """The oracle's complex128 brickwork state, computed once per size."""
+    if n not in _ORACLE:
+        _ORACLE.clear()
+        _ORACLE[n] = oracle.run(oracle.basis_state(n, 0), W.brickwork(n, 40, 2))
+    return _ORACLE[n]
+
+
+def _run_gpu(n, dtype, mode, prec):
+    import torch
+
+    import paper_2503_03016_gb300 as P
+    st = P.State(n, dtype).init_basis(0)
+    st.run(P.Circuit(n, W.brickwork(n, 40, 2)), mode=mode, prec=prec)
+    path = P.qc_last_fused_path() if mode == P.QC_RUN_FUSED else 0
+    got = st.numpy()
+    st.free()
+    torch.cuda.empty_cache()
+    return got, path
+
+
+@pytest.mark.parametrize("n", [24, 28])
+@pytest.mark.parametrize("variant", ["fused_native", "fused_tf32x3", "per_gate_c128"])
+def test_brickwork_vs_oracle(n, variant):
+    import paper_2503_03016_gb300 as P
+    if n == 28 and variant == "per_gate_c128":
+        pytest.skip("the complex128 per-gate path is checked at 24 qubits (28 qubits: 5 s of GPU time per run)")
+    dtype = "c128" if variant == "per_gate_c128" else "c64"
+    mode = P.QC_RUN_PER_GATE if variant == "per_gate_c128" else P.QC_RUN_FUSED
+    prec = P.QC_PREC_TF32X3 if variant == "fused_tf32x3" else P.QC_PREC_NATIVE
+    got, path = _run_gpu(n, dtype, mode, prec)
+    want = _oracle_brickwork(n)
+    err = rel_l2(got, want)
+    record("brickwork_vs_oracle", n=n, variant=variant, rel_l2=err, path=path)
+    if variant == "fused_native":
+        assert path == 1
+    if variant == "fused_tf32x3":
+        assert path == 2
+    assert err <= TOL[dtype], err
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+def test_qft32_per_gate_sparse_closed_form(dtype):
+    """Every H, controlled-phase and SWAP sweep of the 544-gate QFT on 32 qubits (pair
+    distances up to 2^31, indices up to 2^32 - 1) from a sparse start state."""
+    import torch
+
+    import paper_2503_03016_gb300 as P
+    n = 32
+    need = 34 if dtype == "c64" else 66
+    if _free_gb() < need + 4:
+        pytest.skip("needs %d GiB of device memory" % need)
+    rng = np.random.default_rng(33)
+    xs = [int(v) for v in rng.integers(0, 1 << n, 6)] + [(1 << n) - 1, 1 << 31]
+    cs = rng.standard_normal(len(xs)) + 1j * rng.standard_normal(len(xs))
+    cs /= np.linalg.norm(cs)
+    st = P.State(n, dtype)
+    st.tensor.zero_()
+    for x, c in zip(xs, cs):
+        st.tensor[x] = complex(c)
+    torch.cuda.synchronize()
+    st.run(W.qft(n), mode=P.QC_RUN_PER_GATE)
+    ks = [int(v) for v in rng.integers(0, 1 << n, 64)] + [0, 1, (1 << 31) + 5, (1 << n) - 1]
+    got = np.array([complex(st.tensor[k].item()) for k in ks])
+    N = float(1 << n)
+    if dtype == "c64":
+        cs = cs.astype(np.complex64).astype(np.complex128)
+    want = np.array([sum(c * np.exp(2j * np.pi * (((x * k) % (1 << n)) / N)) for x, c in zip(xs, cs)) / np.sqrt(N)
+                     for k in ks])
+    # the relative L2 target as an RMS error per output (outputs of RMS size 2^-16),
+    # 3 sigma for a sampled output
+    err = np.abs(got - want).max() / 2.0 ** -16
+    record("qft32_per_gate_sparse", dtype=dtype, max_err_over_rms=err)
+    assert err <= 3 * TOL[dtype], err
+    nrm = _norm(st.tensor)
+    assert abs(nrm - 1) < (1e-5 if dtype == "c64" else 1e-12)
+    st.free()
+    torch.cuda.empty_cache()
+
+
+def test_readout_32_qubits_dyadic_state():
+    """Probabilities, shots, outcome probabilities and collapse at 2^32 amplitudes on a
+    state whose four nonzero amplitudes have dyadic squared magnitudes (exact in FP32
+    and FP64), placed at indices below 2^3, near 2^31, above 3*2^30 and at 2^32 - 16."""
+    import torch
+
+    import paper_2503_03016_gb300 as P
+    n = 32
+    if _free_gb() < 32 + 32 + 8:
+        pytest.skip("needs ~72 GiB of device memory")
+    idx = [5, (1 << 31) + 3, 0xC1234567, (1 << 32) - 16]
+    amps = [complex(0.5, 0.0), complex(0.25, 0.25), complex(0.5, -0.25), complex(-0.25, 0.5)]
+    p_nz = np.array([abs(a) ** 2 for a in amps])
+    assert p_nz.sum() == 1.0
+    st = P.State(n, "c64")
+    st.tensor.zero_()
+    for i, a in zip(idx, amps):
+        st.tensor[i] = a
+    torch.cuda.synchronize()
+    # probabilities: exact at the nonzero indices, zero elsewhere (sampled), sum 1
+    p = st.probs()
+    assert [p[i].item() for i in idx] == list(p_nz)
+    probe = [0, 4, 6, (1 << 31) + 2, (1 << 31) + 4, 0xC1234566, (1 << 32) - 15, (1 << 32) - 1]
+    assert all(p[i].item() == 0.0 for i in probe)
+    assert torch.count_nonzero(p).item() == 4
+    del p
+    torch.cuda.empty_cache()
+    # shots: the rule min{k : u T < cdf_k} on the exact CDF of the four values
+    cdf = np.cumsum(p_nz)
+    u = np.concatenate([W.uniforms(100_000, 32), cdf[:3], [0.0, np.nextafter(cdf[0], 0)]])
+    got = st.sample(torch.tensor(u, device="cuda")).cpu().numpy().astype(np.uint64)
+    want = np.array(idx, dtype=np.uint64)[np.searchsorted(cdf, u, side="right")]
+    np.testing.assert_array_equal(got, want)
+    # outcome probabilities on the most and least significant index bits
+    p0_q0 = P.qc_outcome_prob(st.handle, 0, 0)
+    p1_q31 = P.qc_outcome_prob(st.handle, 31, 1)
+    assert p0_q0 == p_nz[0]  # only index 5 has the top bit clear
+    assert p1_q31 == p_nz[0] + p_nz[1] + p_nz[2]
+    # collapse qubit 0 onto 1: indices with the top bit set survive, scaled by
+    # 1/sqrt(P(1)) (complex64: the FP64 factor rounded once to FP32)
+    pr = st.collapse(0, 1)
+    assert pr == p_nz[1] + p_nz[2] + p_nz[3]
+    s = np.float32(1.0 / np.sqrt(pr))
+    for i, a in zip(idx, amps):
+        v = complex(st.tensor[i].item())
+        w = complex(np.complex64(a) * s) if i >= (1 << 31) else 0j
+        assert abs(v - w) <= 2e-7, (i, v, w)
+    nrm = _norm(st.tensor)
+    assert abs(nrm - 1) < 1e-6
+    record("readout_32_dyadic", shots=len(u), collapse_norm_err=abs(nrm - 1))
+    st.free()
+    torch.cuda.empty_cache()
+
+
+def test_adjoint_24q_against_oracle():
+    """Config of the adjoint benchmark: 24 qubits, 10 layers of RY RZ and a CZ ring,
+    480 parameters, H = ring ZZ + sum X.  Complex128: the energy against the oracle
+    (relative 1e-12) and 4 seeded gradient entries against the oracle's central
+    differences (step 1e-3, times h / sin h); complex64: relative L2 of the full
+    gradient against complex128 within 1e-5, and its energy against the oracle."""
+    import paper_2503_03016_gb300 as P
+    n, layers = 24, 10
+    ops, params, terms, coeffs = W.adjoint_workload(n, layers, 5)
+    circ = P.Circuit(n, ops)
+    e128, g128 = P.qc_adjoint_grad(circ, params, terms, coeffs, P.QC_C128)
+    e64, g64 = P.qc_adjoint_grad(circ, params, terms, coeffs, P.QC_C64)
+    mterms = []
+    for s, c in zip(terms, coeffs):
+        x = z = 0
+        for j, ch in enumerate(s):
+            b = 1 << (n - 1 - j)
+            x |= b if ch in "XY" else 0
+            z |= b if ch in "ZY" else 0
+        mterms.append((x, z, c))
+    e_ref = oracle.energy_masks(n, ops, params, mterms)
+    scale = float(np.sum(np.abs(coeffs)))  # |<H>| <= sum |c_t|
+    h = 1e-3
+    pick = np.random.default_rng(24).choice(params.size, 4, replace=False)
+    fd = []
+    for p in pick:
+        a = params.copy()
+        a[p] += h
+        b = params.copy()
+        b[p] -= h
+        fd.append((oracle.energy_masks(n, ops, a, mterms) - oracle.energy_masks(n, ops, b, mterms)) / (2 * h)
+                  * h / np.sin(h))
+    fd = np.array(fd)
+    g_err = np.abs(g128[pick] - fd).max()
+    rel64 = np.linalg.norm(g64 - g128) / np.linalg.norm(g128)
+    record("adjoint_24q", e128_err=abs(e128 - e_ref) / scale, e64_err=abs(e64 - e_ref) / scale,
+           g128_vs_oracle_fd=g_err, g64_rel_l2_vs_g128=rel64)
+    assert abs(e128 - e_ref) <= 1e-12 * scale
+    assert abs(e64 - e_ref) <= 1e-5 * scale
+    # the oracle's own differences carry ~eps ||H|| / h = 1e-11 of rounding
+    assert g_err <= 1e-9, (g128[pick], fd)
+    assert rel64 <= 1e-5, rel64

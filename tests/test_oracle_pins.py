@@ -293,6 +293,54 @@ def test_pauli_expectation_vs_dense():
     np.testing.assert_allclose(got, want, atol=1e-14)
 
 
+def _masks_of(s: str):
+    """(x, z) index-bit masks of a Pauli string (character j is qubit j, index bit
+    n-1-j): X sets x, Z sets z, Y sets both."""
+    n = len(s)
+    x = z = 0
+    for j, c in enumerate(s):
+        b = 1 << (n - 1 - j)
+        if c in "XY":
+            x |= b
+        if c in "ZY":
+            z |= b
+    return x, z
+
+
+def test_pauli_mask_expectation_vs_dense_and_strings():
+    """The (xmask, zmask) form of a Pauli term against the dense Kronecker Pauli matrix
+    (n = 5, every string kind, coefficients) and against the string form (n = 9)."""
+    n = 5
+    rng = np.random.default_rng(21)
+    psi = W.random_state(n, 3)
+    strings = ["".join(rng.choice(list("IXYZ"), n)) for _ in range(30)] + ["Y" * n, "I" * n, "XYZXY"]
+    coeffs = rng.uniform(-2, 2, len(strings))
+    terms = [_masks_of(s) + (c,) for s, c in zip(strings, coeffs)]
+    got = oracle.expect_masks(psi, terms)
+    want = [c * np.vdot(psi, kron.pauli_matrix(s) @ psi).real for s, c in zip(strings, coeffs)]
+    np.testing.assert_allclose(got, want, atol=1e-14)
+    n = 9
+    psi = W.random_state(n, 4)
+    strings = ["".join(rng.choice(list("IXYZ"), n)) for _ in range(20)]
+    terms = [_masks_of(s) + (1.0,) for s in strings]
+    np.testing.assert_allclose(oracle.expect_masks(psi, terms), oracle.expect_pauli(psi, strings), atol=1e-14)
+
+
+def test_pauli_mask_expectation_closed_forms():
+    """RY product state: <Y_q> = 0, <X_q> = sin t_q, <Z_q> = cos t_q on index bit
+    n-1-q; and <Y> = 1 on (|0> + i|1>)/sqrt(2) (Sec. 5.2's tomography vector), which
+    fixes the sign of i^{|x & z|}."""
+    n = 4
+    t = np.array([0.4, 1.1, 2.0, 2.7])
+    psi = oracle.run(oracle.basis_state(n, 0), [Op("ry", (q,), (float(t[q]),)) for q in range(n)])
+    for q in range(n):
+        b = 1 << (n - 1 - q)
+        got = oracle.expect_masks(psi, [(b, 0, 1.0), (0, b, 1.0), (b, b, 1.0)])
+        np.testing.assert_allclose(got, [np.sin(t[q]), np.cos(t[q]), 0.0], atol=1e-15)
+    v = np.array([1.0, 1j]) / np.sqrt(2)
+    np.testing.assert_allclose(oracle.expect_masks(v, [(1, 1, 1.0)]), [1.0], atol=1e-15)
+
+
 def test_norm_and_inverse():
     n = 7
     ops = W.brickwork(n, 8, 4) + W.u3_ladder(n, 2, 4) + W.qft(n) + W.ansatz(n, 2, True)

@@ -68,3 +68,23 @@ def test_noalloc_rejects_too_many_terms():
     with pytest.raises(P.QCError) as e:
         P.qc_expect_pauli_noalloc(st.handle, ["ZZZ"] * 257)
     assert e.value.status == 1 and "256" in str(e.value)
+
+
+def test_noalloc_grid_caps_at_22_qubits():
+    """At 22 qubits (32 MiB, complex64) both grid caps of the fixed array are reached:
+    the X/Y reduction's 1216 blocks and the Z-string kernel's 608 blocks of 32 partial
+    sums, which fill the partial-sum region up to the term values.  More than 32 Z-only
+    strings (two passes of the Z-string kernel) mixed with X/Y strings, twice in a row,
+    against the regular entry point."""
+    import paper_2503_03016_gb300 as P
+    n = 22
+    rng = np.random.default_rng(22)
+    strings = ["".join(rng.choice(list("IZ"), n)) for _ in range(40)]
+    strings += ["".join(rng.choice(list("IXYZ"), n)) for _ in range(24)] + W.x_terms(n)[:6]
+    strings = [strings[i] for i in rng.permutation(len(strings))]
+    coeffs = rng.standard_normal(len(strings))
+    st = P.State(n, "c64").init_gaussian(22)
+    want = P.qc_expect_pauli(st.handle, strings, coeffs)
+    for _ in range(2):
+        got = P.qc_expect_pauli_noalloc(st.handle, strings, coeffs)
+        np.testing.assert_allclose(got, want, atol=2e-6 * (1 + np.abs(coeffs).max()), rtol=0)
