@@ -467,12 +467,12 @@ def run_batch_bench(args):
     stream = torch.cuda.current_stream()
     nsi = np.asarray(ns, dtype=np.int32)
     for _ in range(max(args.warmup, 1)):
-        P.qc_run_batch(nsi, layers, offs, dparams, flat.size, out)
+        P.qc_run_ansatz_batch(nsi, layers, offs, dparams, flat.size, out)
     torch.cuda.synchronize()
     timer = StreamTimer(stream)
     timer.start()
     for _ in range(args.steps):
-        P.qc_run_batch(nsi, layers, offs, dparams, flat.size, out)
+        P.qc_run_ansatz_batch(nsi, layers, offs, dparams, flat.size, out)
     ms = timer.stop() / args.steps
     # a fused RZ.RY layer gate costs 2 complex multiply-adds = 16 real flops per amplitude
     flops = sum(16.0 * layers * int(n) * (1 << int(n)) for n in ns)

@@ -305,6 +305,23 @@ qc_status qc_run_circuit(qc_state* s, const qc_circuit* c, const double* params,
  * Batched circuits and adjoint gradients (parameterised ansatz circuits)
  * ------------------------------------------------------------------------- */
 
+/* One term coeff * P of a Pauli sum on the index bits: bit b of xmask / zmask acts on
+ * qubit n-1-b as X (xmask only), Z (zmask only) or Y (both), i.e.
+ * P = i^{|xmask & zmask|} X^xmask Z^zmask and P|j> = i^{|x & z|} (-1)^{|j & z|} |j ^ x>
+ * (the Pauli decomposition behind Sec. 5.2's density-matrix estimate). */
+typedef struct qc_pauli_term {
+  uint64_t xmask;
+  uint64_t zmask;
+  double coeff;
+} qc_pauli_term;
+
+/* H = sum_t terms[t] (host memory). */
+typedef struct qc_hamiltonian {
+  int32_t nterms;
+  int32_t reserved;
+  const qc_pauli_term* terms;
+} qc_hamiltonian;
+
 /* Adjoint (reverse-sweep) gradient of E(theta) = <psi(theta)| H |psi(theta)>,
  * psi(theta) = U_L ... U_1 |0...0>, H = sum_t coeffs[t] P_t (Pauli strings as in
  * qc_expect_pauli).  Parameterised ops must be RX/RY/RZ with param >= 0 (each
@@ -315,29 +332,84 @@ qc_status qc_run_circuit(qc_state* s, const qc_circuit* c, const double* params,
  * calls).  With n >= 12 (both dtypes): the reverse sweep runs as tile passes over psi and
  * lambda together (a recorded rotation's share is added before it is undone);
  * otherwise one kernel per rotation.  Sums in FP64, fixed order (bitwise repeatable).
+ * The two state buffers, the reduction partials and the plan buffers are one
+ * process-wide workspace owned by the library (grown when a larger register needs it,
+ * kept until the process exits); calls are serialised by the library, and a call on
+ * another stream waits (on the device) for the previous call's kernels.
  * Synchronising. */
 qc_status qc_adjoint_grad(const qc_circuit* c, const double* params, int nparams, const char* const* strings,
                           const double* coeffs, int nterms, qc_dtype dtype, void* stream, double* host_energy,
                           double* host_grad);
 
-/* A batch of independent parameterised circuits of uneven qubit counts evaluated
- * in one persistent launch (complex64).  Circuit b has n[b] qubits (6 <= n <= 20)
- * and runs `layers` layers of [RY(t) then RZ(t) on every qubit, then CZ(i, i+1),
- * i = 0..n-2], parameter index layer*2n + 2q + {0: RY, 1: RZ}, from |0...0>, reading
- * its parameters from params + param_offset[b] (device memory).  dev_out[b] =
- * <psi_b| sum_{i<n-1} Z_i Z_{i+1} |psi_b>, accumulated in FP64. */
+/* Device-pointer form of qc_adjoint_grad for training loops on one stream: the angles
+ * in device memory (`dev_params`, nparams FP64), H as mask terms (qc_hamiltonian, host),
+ * the energy (one FP64) and the gradient (nparams FP64) written to device memory on
+ * `stream`.  The gate plan is built on the host from the angle values, so the call
+ * copies dev_params to the host on `stream` and waits for that copy; every step after
+ * it, the outputs included, is queued on `stream` without a host round trip (the
+ * outputs are valid once `stream` reaches them).  Same workspace, serialisation and
+ * arithmetic as qc_adjoint_grad. */
+qc_status qc_adjoint_grad_dev(const qc_circuit* c, const double* dev_params, int nparams, const qc_hamiltonian* H,
+                              qc_dtype dtype, void* stream, double* dev_energy, double* dev_grad);
+
+/* A batch of independent circuits of uneven qubit counts (QCLAB Sec. 2 circuits,
+ * Sec. 3.2 applied to each one's own register from |0...0>), evaluated in one
+ * persistent launch, complex64 state, FP32 gate arithmetic.
+ *   circuits[b]     : any gate kinds, 1 <= n <= 20 qubits, host memory.
+ *   dev_params      : device FP64 angles; an op of circuit b with param p >= 0 (RX, RY,
+ *                     RZ, CP: one angle; U3: three) reads dev_params[param_offset[b] + p
+ *                     ...]; its matrix is formed on the device in FP64 and rounded to
+ *                     FP32.  NULL if no op is parameterised.  param_offset NULL = 0.
+ *   observables     : host; one qc_hamiltonian per circuit, or one for all when
+ *                     shared_observable is nonzero; dev_out[b] = <psi_b| H_b |psi_b>
+ *                     (per-amplitude products in FP32, sums in FP64 over groups of 16
+ *                     amplitudes).  NULL: no values (dev_out may be NULL).
+ *   dev_states      : host array of `count` device pointers, each to 2^n[b] complex64
+ *                     amplitudes (16-byte aligned) that receive circuit b's final state;
+ *                     NULL entries or a NULL array: not stored.
+ * Circuits of at most 13 qubits live in shared memory for their whole run; larger ones
+ * in a device workspace (or in their dev_states buffer), one sweep per gate by one
+ * block.  When every circuit is the layered RY.RZ + CZ-chain ansatz (parameter index
+ * layer*2n + 2q + {0: RY, 1: RZ}, n >= 6) and every observable is sum_i Z_i Z_{i+1} of
+ * the chain with unit coefficients, the batch runs on the ansatz kernel below instead
+ * (angles rounded to FP32 first).  Asynchronous on `stream`; the tables are uploaded
+ * from host memory during the call.  Calls are serialised by the library (one
+ * process-wide workspace). */
 typedef struct qc_batch {
+  int32_t count;
+  int32_t shared_observable;
+  const qc_circuit* circuits;
+  const int64_t* param_offset;
+  const double* dev_params;
+  int64_t nparams;
+  const qc_hamiltonian* observables;
+  void* const* dev_states;
+} qc_batch;
+
+qc_status qc_run_batch(const qc_batch* b, void* stream, double* dev_out);
+/* Which kernel the calling thread's most recent qc_run_batch used (a diagnostic):
+ * 0 the general batch kernel, 1 the ansatz kernel. */
+int qc_last_batch_path(void);
+
+/* The layered ansatz as its own batch entry point (the fast path qc_run_batch picks):
+ * circuit b has n[b] qubits (6 <= n <= 20) and runs `layers` layers of [RY(t) then
+ * RZ(t) on every qubit, then CZ(i, i+1), i = 0..n-2], parameter index
+ * layer*2n + 2q + {0: RY, 1: RZ}, from |0...0>, reading FP32 angles from
+ * dev_params + param_offset[b] (device memory).  dev_out[b] =
+ * <psi_b| sum_{i<n-1} Z_i Z_{i+1} |psi_b>, accumulated in FP64.  One persistent launch,
+ * recorded once in a CUDA graph and replayed; its launch shape is chosen by timing. */
+typedef struct qc_ansatz_batch {
   int32_t count;                /* number of circuits                                */
   int32_t layers;
   const int32_t* n;             /* host: qubit count per circuit                     */
   const int64_t* param_offset;  /* host: offset of circuit b's parameters            */
   const float* dev_params;      /* device: all parameters (FP32 angles)              */
   int64_t nparams;              /* total number of parameters                        */
-} qc_batch;
+} qc_ansatz_batch;
 
-qc_status qc_run_batch(const qc_batch* b, void* stream, double* dev_out);
+qc_status qc_run_ansatz_batch(const qc_ansatz_batch* b, void* stream, double* dev_out);
 /* Fusion width (register-stage bits, 4 or 5) the autotuner chose for the most recent
- * qc_run_batch workload (diagnostic). */
+ * ansatz batch (diagnostic). */
 int qc_batch_fusion_width(void);
 
 #ifdef __cplusplus

@@ -44,10 +44,25 @@ class qc_circuit(ctypes.Structure):
                 ("pool", ctypes.POINTER(ctypes.c_double)), ("pool_len", ctypes.c_int64)]
 
 
-class qc_batch(ctypes.Structure):
+class qc_ansatz_batch(ctypes.Structure):
     _fields_ = [("count", ctypes.c_int32), ("layers", ctypes.c_int32), ("n", ctypes.POINTER(ctypes.c_int32)),
                 ("param_offset", ctypes.POINTER(ctypes.c_int64)), ("dev_params", ctypes.c_void_p),
                 ("nparams", ctypes.c_int64)]
+
+
+class qc_pauli_term(ctypes.Structure):
+    _fields_ = [("xmask", ctypes.c_uint64), ("zmask", ctypes.c_uint64), ("coeff", ctypes.c_double)]
+
+
+class qc_hamiltonian(ctypes.Structure):
+    _fields_ = [("nterms", ctypes.c_int32), ("reserved", ctypes.c_int32), ("terms", ctypes.POINTER(qc_pauli_term))]
+
+
+class qc_batch(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_int32), ("shared_observable", ctypes.c_int32),
+                ("circuits", ctypes.POINTER(qc_circuit)), ("param_offset", ctypes.POINTER(ctypes.c_int64)),
+                ("dev_params", ctypes.c_void_p), ("nparams", ctypes.c_int64),
+                ("observables", ctypes.POINTER(qc_hamiltonian)), ("dev_states", ctypes.POINTER(ctypes.c_void_p))]
 
 
 _P = ctypes.c_void_p
@@ -89,7 +104,11 @@ _SIGS = {
     "qc_adjoint_grad": (ctypes.c_int, [ctypes.POINTER(qc_circuit), _D, ctypes.c_int,
                                        ctypes.POINTER(ctypes.c_char_p), _D, ctypes.c_int, ctypes.c_int, _P, _D,
                                        _D]),
+    "qc_adjoint_grad_dev": (ctypes.c_int, [ctypes.POINTER(qc_circuit), _P, ctypes.c_int, ctypes.POINTER(qc_hamiltonian),
+                                           ctypes.c_int, _P, _P, _P]),
+    "qc_run_ansatz_batch": (ctypes.c_int, [ctypes.POINTER(qc_ansatz_batch), _P, _P]),
     "qc_run_batch": (ctypes.c_int, [ctypes.POINTER(qc_batch), _P, _P]),
+    "qc_last_batch_path": (ctypes.c_int, []),
     "qc_batch_fusion_width": (ctypes.c_int, []),
 }
 
@@ -402,12 +421,83 @@ def qc_adjoint_grad(circuit: Circuit, params, strings: Sequence[str], coeffs, dt
     return e.value, g
 
 
-def qc_run_batch(ns, layers: int, param_offsets, dev_params, nparams: int, out, stream=None) -> None:
+def qc_adjoint_grad_dev(circuit: "Circuit", dev_params, hamiltonian: "Hamiltonian", dtype: int, dev_energy,
+                        dev_grad, stream=None) -> None:
+    """Device-pointer adjoint gradient: dev_params (device FP64, contiguous), outputs
+    dev_energy (one FP64) and dev_grad (device FP64, len = params) on the stream."""
+    n = int(dev_params.numel()) if hasattr(dev_params, "numel") else 0
+    _call("qc_adjoint_grad_dev", ctypes.byref(circuit.c), _ptr(dev_params), n, ctypes.byref(hamiltonian.h), dtype,
+          _stream(stream), _ptr(dev_energy), _ptr(dev_grad))
+
+
+def qc_run_ansatz_batch(ns, layers: int, param_offsets, dev_params, nparams: int, out, stream=None) -> None:
     ns = np.ascontiguousarray(ns, dtype=np.int32)
     offs = np.ascontiguousarray(param_offsets, dtype=np.int64)
-    b = qc_batch(len(ns), layers, ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
-                 offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _ptr(dev_params), int(nparams))
+    b = qc_ansatz_batch(len(ns), layers, ns.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                        offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _ptr(dev_params), int(nparams))
+    _call("qc_run_ansatz_batch", ctypes.byref(b), _stream(stream), _ptr(out))
+
+
+class Hamiltonian:
+    """A Pauli sum as qc_pauli_term records (xmask, zmask, coeff) on index bits; holds
+    the ctypes array alive.  ``from_strings`` converts strings of I/X/Y/Z (character j
+    acts on qubit j, i.e. index bit n-1-j) to masks."""
+
+    def __init__(self, terms):
+        terms = list(terms)
+        self.arr = (qc_pauli_term * max(1, len(terms)))()
+        for i, (x, z, c) in enumerate(terms):
+            self.arr[i] = qc_pauli_term(int(x), int(z), float(c))
+        self.h = qc_hamiltonian(len(terms), 0, self.arr)
+        self.terms = terms
+
+    @classmethod
+    def from_strings(cls, strings, coeffs=None):
+        out = []
+        for t, s in enumerate(strings):
+            n = len(s)
+            x = z = 0
+            for j, ch in enumerate(s.upper()):
+                b = 1 << (n - 1 - j)
+                if ch in "XY":
+                    x |= b
+                if ch in "ZY":
+                    z |= b
+                if ch not in "IXYZ":
+                    raise ValueError("invalid Pauli character %r" % ch)
+            out.append((x, z, 1.0 if coeffs is None else float(coeffs[t])))
+        return cls(out)
+
+
+def qc_run_batch(circuits, observables=None, dev_params=None, param_offsets=None, dev_states=None, out=None,
+                 stream=None, shared_observable: bool = False, nparams: Optional[int] = None) -> None:
+    """One launch over independent circuits (list of :class:`Circuit`).  observables:
+    one :class:`Hamiltonian` per circuit (or one with shared_observable); out: device
+    FP64 tensor of len(circuits); dev_params: device FP64 tensor; dev_states: list of
+    device complex64 tensors (or None entries) receiving the final states."""
+    cnt = len(circuits)
+    carr = (qc_circuit * max(1, cnt))(*[c.c for c in circuits])
+    offs = None
+    if param_offsets is not None:
+        offs = np.ascontiguousarray(param_offsets, dtype=np.int64)
+    harr = None
+    if observables is not None:
+        hs = observables if isinstance(observables, (list, tuple)) else [observables]
+        harr = (qc_hamiltonian * max(1, len(hs)))(*[h.h for h in hs])
+    sarr = None
+    if dev_states is not None:
+        sarr = (ctypes.c_void_p * max(1, cnt))(*[(_ptr(t) if t is not None else None) for t in dev_states])
+    if nparams is None:
+        nparams = int(dev_params.numel()) if dev_params is not None and hasattr(dev_params, "numel") else 0
+    b = qc_batch(cnt, 1 if shared_observable else 0, carr,
+                 None if offs is None else offs.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                 _ptr(dev_params), int(nparams), harr, sarr)
     _call("qc_run_batch", ctypes.byref(b), _stream(stream), _ptr(out))
+
+
+def qc_last_batch_path() -> int:
+    """0 general batch kernel, 1 ansatz kernel (most recent qc_run_batch of this thread)."""
+    return int(lib().qc_last_batch_path())
 
 
 def qc_batch_fusion_width() -> int:

@@ -239,6 +239,10 @@ struct AdjWork {
   int device = -1;
   size_t bytes = 0;
   void* p = nullptr;
+  void* scratch = nullptr;  // the psi handle's plan and reduction scratch, kept between calls
+  size_t scratch_bytes = 0;
+  cudaEvent_t done = nullptr;  // recorded after a call's last use of the workspace
+  bool pending = false;
 };
 static AdjWork g_adj;
 static AdjPlanBuf g_adj_plan;
@@ -250,7 +254,8 @@ static std::mutex g_adj_mu;
 template <typename R>
 static qc_status adjoint_impl(const qc_circuit* c, const double* params, int nparams,
                               const std::vector<ParsedTermA>& terms, const double* coeffs, qc_dtype dtype,
-                              cudaStream_t stream, double* host_energy, double* host_grad) {
+                              cudaStream_t stream, double* host_energy, double* host_grad, double* dev_energy,
+                              double* dev_grad) {
   const int n = c->n;
   const uint64_t N = uint64_t(1) << n;
   const size_t sbytes = N * 2 * sizeof(R);
@@ -287,7 +292,19 @@ static qc_status adjoint_impl(const qc_circuit* c, const double* params, int npa
   const size_t need = 2 * sbytes + ((pbytes + 255) & ~size_t(255)) + 256;
   int dev = 0;
   cudaGetDevice(&dev);
-  if (g_adj.device != dev || g_adj.bytes < need) {
+  if (g_adj.device != dev) {
+    if (g_adj.p || g_adj.scratch) cudaDeviceSynchronize();
+    if (g_adj.p) cudaFree(g_adj.p);
+    if (g_adj.scratch) cudaFree(g_adj.scratch);
+    g_adj = AdjWork();
+    if (qc_status st = check_cuda(cudaEventCreateWithFlags(&g_adj.done, cudaEventDisableTiming), "adjoint event"))
+      return st;
+    g_adj.device = dev;
+  }
+  // a previous call (possibly on another stream) is done with the workspace first
+  if (g_adj.pending)
+    if (qc_status st = check_cuda(cudaStreamWaitEvent(stream, g_adj.done, 0), "adjoint ordering")) return st;
+  if (g_adj.bytes < need) {
     if (g_adj.p) {
       cudaDeviceSynchronize();
       cudaFree(g_adj.p);
@@ -310,6 +327,8 @@ static qc_status adjoint_impl(const qc_circuit* c, const double* params, int npa
   s.amps = w + sbytes + ((pbytes + 255) & ~size_t(255));
   s.stream = stream;
   s.device = dev;
+  s.scratch = g_adj.scratch;
+  s.scratch_bytes = g_adj.scratch_bytes;
   qc_state sl = s;
   sl.amps = lam;
   qc_status st = QC_OK;
@@ -402,22 +421,35 @@ static qc_status adjoint_impl(const qc_circuit* c, const double* params, int npa
     QC_COUNT(), k_collect_grads<<<unsigned(std::max(1, (nparams + 255) / 256)), 256, 0, stream>>>(part, pgrid, dparams,
                                                                                                 nrot, grad, nparams);
     if ((st = check_launch("adjoint sweep"))) goto done;
-    std::vector<double> e(2);
-    if ((st = check_cuda(cudaMemcpyAsync(e.data(), inner + 2 * grid, 2 * sizeof(double), cudaMemcpyDeviceToHost,
-                                         stream),
-                         "D2H")))
-      goto done;
-    if ((st = check_cuda(cudaMemcpyAsync(host_grad, grad, sizeof(double) * nparams, cudaMemcpyDeviceToHost, stream),
-                         "D2H")))
-      goto done;
-    if ((st = check_cuda(cudaStreamSynchronize(stream), "qc_adjoint_grad"))) goto done;
-    *host_energy = e[0];
+    if (dev_energy) {
+      // device outputs, asynchronous on the stream
+      if ((st = check_cuda(cudaMemcpyAsync(dev_energy, inner + 2 * grid, sizeof(double), cudaMemcpyDeviceToDevice,
+                                           stream),
+                           "energy output")))
+        goto done;
+      if (nparams > 0 &&
+          (st = check_cuda(cudaMemcpyAsync(dev_grad, grad, sizeof(double) * nparams, cudaMemcpyDeviceToDevice, stream),
+                           "gradient output")))
+        goto done;
+    } else {
+      std::vector<double> e(2);
+      if ((st = check_cuda(cudaMemcpyAsync(e.data(), inner + 2 * grid, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                           stream),
+                           "D2H")))
+        goto done;
+      if ((st = check_cuda(cudaMemcpyAsync(host_grad, grad, sizeof(double) * nparams, cudaMemcpyDeviceToHost,
+                                           stream),
+                           "D2H")))
+        goto done;
+      if ((st = check_cuda(cudaStreamSynchronize(stream), "qc_adjoint_grad"))) goto done;
+      *host_energy = e[0];
+    }
   }
 done:
-  if (s.scratch) {
-    cudaStreamSynchronize(stream);
-    cudaFree(s.scratch);
-  }
+  // the psi handle's scratch stays with the workspace for the next call
+  g_adj.scratch = s.scratch;
+  g_adj.scratch_bytes = s.scratch_bytes;
+  if (cudaEventRecord(g_adj.done, stream) == cudaSuccess) g_adj.pending = true;
   return st;
 }
 
@@ -440,6 +472,46 @@ extern "C" qc_status qc_adjoint_grad(const qc_circuit* c, const double* params, 
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   std::lock_guard<std::mutex> lock(g_adj_mu);
   if (dtype == QC_C64)
-    return adjoint_impl<float>(c, params, nparams, terms, coeffs, dtype, s, host_energy, host_grad);
-  return adjoint_impl<double>(c, params, nparams, terms, coeffs, dtype, s, host_energy, host_grad);
+    return adjoint_impl<float>(c, params, nparams, terms, coeffs, dtype, s, host_energy, host_grad, nullptr, nullptr);
+  return adjoint_impl<double>(c, params, nparams, terms, coeffs, dtype, s, host_energy, host_grad, nullptr, nullptr);
+}
+
+extern "C" qc_status qc_adjoint_grad_dev(const qc_circuit* c, const double* dev_params, int nparams,
+                                         const qc_hamiltonian* H, qc_dtype dtype, void* stream, double* dev_energy,
+                                         double* dev_grad) {
+  clear_error();
+  if (!c || c->n < 1 || c->n > 32 || (c->nops > 0 && !c->ops) || nparams < 0 ||
+      (nparams > 0 && (!dev_params || !dev_grad)) || !H || H->nterms < 0 || (H->nterms > 0 && !H->terms) ||
+      !dev_energy || (dtype != QC_C64 && dtype != QC_C128)) {
+    set_error("qc_adjoint_grad_dev: invalid arguments");
+    return QC_ERR_INVALID_ARG;
+  }
+  const uint64_t lim = c->n >= 64 ? ~uint64_t(0) : (uint64_t(1) << c->n);
+  std::vector<ParsedTermA> terms(H->nterms);
+  std::vector<double> coeffs(H->nterms);
+  for (int t = 0; t < H->nterms; ++t) {
+    const qc_pauli_term& T = H->terms[t];
+    if (T.xmask >= lim || T.zmask >= lim) {
+      set_error("qc_adjoint_grad_dev: term %d acts outside the %d qubits", t, c->n);
+      return QC_ERR_INVALID_ARG;
+    }
+    terms[t] = ParsedTermA{T.xmask, T.zmask, __builtin_popcountll(T.xmask & T.zmask)};
+    coeffs[t] = T.coeff;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // the plan is built on the host from the parameter values: one copy, waited for
+  std::vector<double> params(size_t(std::max(nparams, 1)));
+  if (nparams > 0) {
+    if (qc_status st = check_cuda(cudaMemcpyAsync(params.data(), dev_params, sizeof(double) * nparams,
+                                                  cudaMemcpyDeviceToHost, s),
+                                  "parameter read"))
+      return st;
+    if (qc_status st = check_cuda(cudaStreamSynchronize(s), "parameter read")) return st;
+  }
+  std::lock_guard<std::mutex> lock(g_adj_mu);
+  if (dtype == QC_C64)
+    return adjoint_impl<float>(c, params.data(), nparams, terms, coeffs.data(), dtype, s, nullptr, nullptr,
+                               dev_energy, dev_grad);
+  return adjoint_impl<double>(c, params.data(), nparams, terms, coeffs.data(), dtype, s, nullptr, nullptr, dev_energy,
+                              dev_grad);
 }

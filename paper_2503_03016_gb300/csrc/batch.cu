@@ -1,4 +1,5 @@
-// Batched ansatz circuits in one persistent launch (qc_run_batch).
+// Batched ansatz circuits in one persistent launch (qc_run_ansatz_batch, and the fast
+// path of qc_run_batch).
 //
 // Each circuit is the paper's gate sequence (Sec. 3.2) on its own register: per layer
 // RY(t) then RZ(t') on every qubit, then CZ(i, i+1) for i = 0..n-2; the result is
@@ -473,10 +474,10 @@ using namespace qcgb;
 
 extern "C" int qc_batch_fusion_width(void) { return g_last_batch_sb; }
 
-extern "C" qc_status qc_run_batch(const qc_batch* b, void* stream_v, double* dev_out) {
+extern "C" qc_status qc_run_ansatz_batch(const qc_ansatz_batch* b, void* stream_v, double* dev_out) {
   clear_error();
   if (!b || b->count < 0 || b->layers < 0 || (b->count > 0 && (!b->n || !b->param_offset || !b->dev_params || !dev_out))) {
-    set_error("qc_run_batch: invalid arguments");
+    set_error("qc_run_ansatz_batch: invalid arguments");
     return QC_ERR_INVALID_ARG;
   }
   if (b->count == 0) return QC_OK;
@@ -485,11 +486,11 @@ extern "C" qc_status qc_run_batch(const qc_batch* b, void* stream_v, double* dev
   for (int i = 0; i < b->count; ++i) {
     const int n = b->n[i];
     if (n < kBatchMinN || n > kBatchMaxN) {
-      set_error("qc_run_batch: circuit %d has n=%d (supported %d..%d)", i, n, kBatchMinN, kBatchMaxN);
+      set_error("qc_run_ansatz_batch: circuit %d has n=%d (supported %d..%d)", i, n, kBatchMinN, kBatchMaxN);
       return QC_ERR_UNSUPPORTED;
     }
     if (b->param_offset[i] < 0 || b->param_offset[i] + int64_t(b->layers) * 2 * n > b->nparams) {
-      set_error("qc_run_batch: parameters of circuit %d exceed nparams", i);
+      set_error("qc_run_ansatz_batch: parameters of circuit %d exceed nparams", i);
       return QC_ERR_INVALID_ARG;
     }
     maxn = std::max(maxn, n);

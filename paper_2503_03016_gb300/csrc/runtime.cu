@@ -514,7 +514,7 @@ using namespace qcgb;
 extern "C" {
 
 const char* qc_last_error(void) { return g_err; }
-int qc_abi_version(void) { return 1; }
+int qc_abi_version(void) { return 2; }
 uint64_t qc_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 static qc_status valid_state(const qc_state* s) {

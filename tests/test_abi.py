@@ -32,7 +32,7 @@ def test_library_exports_every_declared_symbol():
 def test_library_loads_on_cpu():
     import paper_2503_03016_gb300 as P
     L = P.lib()
-    assert L.qc_abi_version() == 1
+    assert L.qc_abi_version() == 2
     assert L.qc_last_error() == b""
 
 

@@ -143,3 +143,56 @@ def test_adjoint_24q_central_differences():
         assert abs(fd * h / np.sin(h) - g128[p]) < 1e-8, (p, fd, g128[p])
     assert abs(e64 - e128) < 1e-4 * (1 + abs(e128))
     assert np.abs(g64 - g128).max() < 1e-4 * (1 + np.abs(g128).max())
+
+
+@pytest.mark.parametrize("dtype,tol", [("c128", 1e-11), ("c64", 2e-5)])
+def test_adjoint_device_form_matches_host_form(dtype, tol):
+    """qc_adjoint_grad_dev (device angles, mask-form H, device outputs on the stream)
+    gives the host form's values bit for bit, and both match the oracle's parameter
+    shift; two calls in a row on another stream leave the same outputs."""
+    import torch
+
+    import paper_2503_03016_gb300 as P
+    n, layers = 13, 2
+    ops, params, terms, coeffs = W.adjoint_workload(n, layers, 11)
+    circ = P.Circuit(n, ops)
+    code = P.QC_C128 if dtype == "c128" else P.QC_C64
+    e_host, g_host = P.qc_adjoint_grad(circ, params, terms, coeffs, code)
+    ham = P.Hamiltonian.from_strings(terms, coeffs)
+    dp = torch.tensor(params, dtype=torch.float64, device="cuda")
+    e = torch.empty(1, dtype=torch.float64, device="cuda")
+    g = torch.empty(params.size, dtype=torch.float64, device="cuda")
+    P.qc_adjoint_grad_dev(circ, dp, ham, code, e, g)
+    torch.cuda.synchronize()
+    assert e.item() == e_host
+    np.testing.assert_array_equal(g.cpu().numpy(), g_host)
+    side = torch.cuda.Stream()
+    e2 = torch.empty_like(e)
+    g2 = torch.empty_like(g)
+    with torch.cuda.stream(side):
+        P.qc_adjoint_grad_dev(circ, dp, ham, code, e2, g2)
+        P.qc_adjoint_grad_dev(circ, dp, ham, code, e2, g2)
+    side.synchronize()
+    assert e2.item() == e_host
+    np.testing.assert_array_equal(g2.cpu().numpy(), g_host)
+    g_ref = oracle.param_shift_grad(n, ops, params, terms, coeffs)
+    scale = np.abs(g_ref).max() + 1
+    np.testing.assert_allclose(g_host, g_ref, atol=tol * scale, rtol=0)
+
+
+def test_autograd_function_on_device():
+    """The autograd function with CUDA parameters: the gradient stays on the device."""
+    import torch
+
+    import paper_2503_03016_gb300 as P
+    n, layers = 6, 2
+    ops, params, terms, coeffs = W.adjoint_workload(n, layers, 8)
+    circ = P.Circuit(n, ops)
+    theta = torch.tensor(params, dtype=torch.float64, device="cuda", requires_grad=True)
+    e = P.AdjointExpectation.apply(theta, circ, terms, coeffs, P.QC_C128)
+    assert e.device.type == "cuda"
+    (2.0 * e).backward()
+    assert theta.grad.device.type == "cuda"
+    g_ref = oracle.param_shift_grad(n, ops, params, terms, coeffs)
+    np.testing.assert_allclose(theta.grad.cpu().numpy(), 2.0 * g_ref, atol=1e-11)
+    assert abs(e.item() - oracle.energy(n, ops, params, terms, coeffs)) < 1e-12

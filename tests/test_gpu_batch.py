@@ -1,4 +1,4 @@
-"""Batched persistent launch (qc_run_batch) against the oracle, circuit by circuit.
+"""Batched ansatz launch (qc_run_ansatz_batch) against the oracle, circuit by circuit.
 
 Each circuit: `layers` x [RY(t), RZ(t') on every qubit, CZ(i, i+1) chain] from |0...0>,
 value <sum_i Z_i Z_{i+1}>; parameters are the FP32 angles the GPU reads, widened
@@ -27,7 +27,7 @@ def run_batch(ns, params, layers):
     flat = np.concatenate(params).astype(np.float32)
     dparams = torch.tensor(flat, device="cuda")
     out = torch.empty(len(ns), dtype=torch.float64, device="cuda")
-    P.qc_run_batch(np.asarray(ns, dtype=np.int32), layers, offs, dparams, flat.size, out)
+    P.qc_run_ansatz_batch(np.asarray(ns, dtype=np.int32), layers, offs, dparams, flat.size, out)
     torch.cuda.synchronize()
     return out.cpu().numpy(), flat, offs, (dparams, out)
 
@@ -69,7 +69,7 @@ def test_batch_4096_sampled_against_oracle():
     got, flat, offs, (dparams, out) = run_batch(list(ns), params, layers)
     assert P.qc_batch_fusion_width() in (4, 5)
     # same buffers: the recorded graph is replayed
-    P.qc_run_batch(np.asarray(ns, dtype=np.int32), layers, offs, dparams, flat.size, out)
+    P.qc_run_ansatz_batch(np.asarray(ns, dtype=np.int32), layers, offs, dparams, flat.size, out)
     torch.cuda.synchronize()
     np.testing.assert_array_equal(got, out.cpu().numpy())
     rng = np.random.default_rng(4)
