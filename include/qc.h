@@ -172,6 +172,20 @@ qc_status qc_measure(qc_state* s, int q, double u, int* outcome, double* prob);
  * is <= 1e-12 (complex128) or <= 1e-6 (complex64).  Synchronising. */
 qc_status qc_collapse(qc_state* s, int q, int outcome, double* prob);
 
+/* Collapse with a caller-supplied normaliser, for a register split into shards over
+ * several processes (each process holds one shard as a state; the outcome probability
+ * of Sec. 3.3 is then the sum of the shards' sums): keeps the amplitudes whose qubit q
+ * reads `outcome` (q = -1: every amplitude) and multiplies them by 1/sqrt(p), formed
+ * once in FP64 as in qc_collapse; the others are set to zero; p = 0 sets the whole
+ * state to zero.  n >= 1.  Asynchronous. */
+qc_status qc_collapse_norm(qc_state* s, int q, int outcome, double p);
+
+/* <a|b> = sum_i conj(a_i) b_i (same n and dtype; both on a's stream): host_out[0] =
+ * real part, host_out[1] = imaginary part; each product at the states' precision, the
+ * sums in FP64 (fixed order).  The inner product Sec. 5.2's expectations reduce to.
+ * Synchronising. */
+qc_status qc_inner(const qc_state* a, const qc_state* b, double* host_out);
+
 /* P(outcome) for qubit q without collapsing (host scalar, synchronising). */
 qc_status qc_outcome_prob(const qc_state* s, int q, int outcome, double* prob);
 

@@ -93,6 +93,8 @@ _SIGS = {
     "qc_measure": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, _I, _D]),
     "qc_collapse": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _D]),
     "qc_outcome_prob": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, _D]),
+    "qc_collapse_norm": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_int, ctypes.c_double]),
+    "qc_inner": (ctypes.c_int, [_P, _P, _D]),
     "qc_probs": (ctypes.c_int, [_P, _P]),
     "qc_sample": (ctypes.c_int, [_P, _P, ctypes.c_int64, _P]),
     "qc_sample_probs": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, ctypes.c_int64, _P]),
@@ -281,6 +283,16 @@ def qc_collapse(h: int, q: int, outcome: int) -> float:
     p = ctypes.c_double()
     _call("qc_collapse", h, q, outcome, ctypes.byref(p))
     return p.value
+
+
+def qc_inner(a: int, b: int) -> complex:
+    out = np.zeros(2)
+    _call("qc_inner", a, b, out.ctypes.data_as(_D))
+    return complex(out[0], out[1])
+
+
+def qc_collapse_norm(h: int, q: int, outcome: int, p: float) -> None:
+    _call("qc_collapse_norm", h, q, outcome, float(p))
 
 
 def qc_outcome_prob(h: int, q: int, outcome: int) -> float:

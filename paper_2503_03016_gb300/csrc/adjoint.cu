@@ -476,6 +476,37 @@ extern "C" qc_status qc_adjoint_grad(const qc_circuit* c, const double* params, 
   return adjoint_impl<double>(c, params, nparams, terms, coeffs, dtype, s, host_energy, host_grad, nullptr, nullptr);
 }
 
+extern "C" qc_status qc_inner(const qc_state* ca, const qc_state* cb, double* host_out) {
+  clear_error();
+  qc_state* a = const_cast<qc_state*>(ca);
+  if (!a || !cb || !a->amps || !cb->amps || !host_out || a->n != cb->n || a->dtype != cb->dtype) {
+    set_error("qc_inner: invalid arguments (same n and dtype required)");
+    return QC_ERR_INVALID_ARG;
+  }
+  const uint64_t N = state_len(a);
+  const int B = 256;
+  const unsigned grid = stream_grid(N, B, 8);
+  void* scr = nullptr;
+  if (qc_status st = state_scratch(a, sizeof(double) * (2 * size_t(grid) + 2), &scr)) return st;
+  double* part = static_cast<double*>(scr);
+  if (a->dtype == QC_C64)
+    QC_COUNT(), k_inner_partials<float><<<grid, B, 0, a->stream>>>(reinterpret_cast<const float*>(a->amps),
+                                                                   reinterpret_cast<const float*>(cb->amps), N, part);
+  else
+    QC_COUNT(), k_inner_partials<double><<<grid, B, 0, a->stream>>>(reinterpret_cast<const double*>(a->amps),
+                                                                    reinterpret_cast<const double*>(cb->amps), N, part);
+  QC_COUNT(), k_sum2_adj<<<1, 1024, 0, a->stream>>>(part, int(grid), part + 2 * grid);
+  if (qc_status st = check_launch("qc_inner")) return st;
+  double h[2];
+  if (qc_status st = check_cuda(cudaMemcpyAsync(h, part + 2 * grid, sizeof(h), cudaMemcpyDeviceToHost, a->stream),
+                                "D2H"))
+    return st;
+  if (qc_status st = check_cuda(cudaStreamSynchronize(a->stream), "qc_inner")) return st;
+  host_out[0] = h[0];
+  host_out[1] = h[1];
+  return QC_OK;
+}
+
 extern "C" qc_status qc_adjoint_grad_dev(const qc_circuit* c, const double* dev_params, int nparams,
                                          const qc_hamiltonian* H, qc_dtype dtype, void* stream, double* dev_energy,
                                          double* dev_grad) {

@@ -749,6 +749,26 @@ qc_status qc_collapse(qc_state* s, int q, int outcome, double* prob) {
   return check_cuda(cudaStreamSynchronize(s->stream), "qc_collapse");
 }
 
+qc_status qc_collapse_norm(qc_state* s, int q, int outcome, double p) {
+  clear_error();
+  if (!s || !s->amps || q < -1 || q >= s->n || (outcome != 0 && outcome != 1) || !(p >= 0.0)) {
+    set_error("qc_collapse_norm: invalid arguments");
+    return QC_ERR_INVALID_ARG;
+  }
+  const uint64_t N = state_len(s);
+  // q = -1: no qubit is measured (mask 0 keeps every amplitude); p = 0 zeroes them
+  const uint64_t m = q < 0 ? 0 : uint64_t(1) << (s->n - 1 - q);
+  const double inv = p > 0.0 ? 1.0 / sqrt(p) : 0.0;
+  const unsigned g = stream_grid(N / 2, 256);
+  if (s->dtype == QC_C64)
+    QC_COUNT(), k_collapse<float><<<g, 256, 0, s->stream>>>(reinterpret_cast<float*>(s->amps), N, m, q < 0 ? 0 : outcome,
+                                                           inv);
+  else
+    QC_COUNT(), k_collapse<double><<<g, 256, 0, s->stream>>>(reinterpret_cast<double*>(s->amps), N, m,
+                                                            q < 0 ? 0 : outcome, inv);
+  return check_launch("qc_collapse_norm");
+}
+
 qc_status qc_probs(const qc_state* cs, double* dev_out) {
   clear_error();
   qc_state* s = const_cast<qc_state*>(cs);
