@@ -1,33 +1,57 @@
 // Tile passes with tensor-core stages (QC_PREC_TF32X3, complex64).
 //
 // A tile of 2^12 amplitudes (the pass's bit set B, as for the CUDA-core passes) goes
-// through the pass's stages in shared memory.  A stage owns 5 of the tile's bits (its
-// slots); every op of the stage acts on, and is conditioned on, slot bits only, so the
-// stage is one 32 x 32 block U_s = G_k ... G_1 (Sec. 3.2's U' of each gate, embedded
-// on the slots and multiplied on the host in FP64).  With the 2^7 combinations of the
-// tile's other bits as rows, a stage is the real GEMM D = A B of the fused-block
-// kernel (A[r][2c + ri] = (re, im) of block index c in row r; B the real form of U_s^T),
-// M = 128, N = K = 64, with the TF32 split a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi.
-// Both splits round to nearest (hi = RN_tf32(a), lo = RN_tf32(a - hi)): the products
-// then err in both directions, so a circuit's hundreds of stages do not drift in norm.
+// through the pass's stages.  A stage owns 5 of the tile's bits (its slots); every op of
+// the stage acts on, and is conditioned on, slot bits only, so the stage is one 32 x 32
+// block U_s = G_k ... G_1 (Sec. 3.2's U' of each gate, embedded on the slots and
+// multiplied on the host in FP64).  With the 2^7 combinations of the tile's other bits
+// as rows, a stage is the real GEMM D = A B (A[r][2c + ri] = (re, im) of block index c
+// in row r; B the real form of U_s^T), M = 128, N = K = 64, with the TF32 split
+// a b ~ a_hi b_hi + a_hi b_lo + a_lo b_hi (a_hi = RN_tf32(a), a_lo = a - a_hi, which the
+// tensor cores read to TF32 precision; B split with round-to-nearest on the host),
+// accumulated in FP32.
 //
-// Kernel: one 256-thread CTA per SM; thread t holds half of row t mod 128 (block index
-// bit 4 = t / 128 selects the half, which is exactly one 32-column K slice of A).  Per
-// stage: gather 16 amplitudes from the swizzled tile, split, store A_hi / A_lo in the
-// K-major 128-byte-swizzled layout; one thread issues 3 x 8 tcgen05.mma (kind::tf32),
-// each K step's three products into its own TMEM accumulator, and commits them to an
-// mbarrier; every thread reads its half-row of the eight partial sums (tcgen05.ld),
-// adds them and writes the result back into the tile.  The stages' B images (host-built,
-// already in the swizzled layout, 32 KiB each) stream through two shared-memory
-// buffers by bulk copies (cp.async.bulk, mbarrier transaction counts): the next
-// stage's B lands while this stage computes.  Passes with one or two stages keep them
-// resident.  Tiles are double-buffered with cp.async as in the CUDA-core passes.
-// Every wait is bounded: on a timeout the kernel sets a status word, waits (bounded)
-// for its copies and products in flight, frees its TMEM and returns.
+// Kernel: one CTA per SM, 288 threads: two epilogue groups of 128 threads (warps 0-3
+// and 4-7), each working on its own tile, and one MMA warp (warp 8) whose first lane
+// issues every tcgen05.mma.  Thread r of a group owns row r of its tile's current
+// stage, which is TMEM lane r: it reads its row's 32 amplitudes from the group's tile
+// in shared memory (byte offsets formed in Gray-code order, one XOR each, and kept for
+// the write-back), splits them and writes A_hi and A_lo into TMEM (tcgen05.st), so A
+// never passes through shared memory as an operand (the tensor cores read only B
+// there), and arrives on the group's mbarrier; the last arrival lets the MMA warp go.  The MMA warp
+// issues the stage's 24 products (A from TMEM, B from shared memory) into two FP32
+// accumulators and commits them to the group's mbarrier.  The group reads its rows of
+// D back (tcgen05.ld), adds the two partial sums, writes the outputs into the tile at
+// this stage's positions (the transposition between stages' row and slot bits) and,
+// after a group barrier, gathers the next stage's rows.  While one group's products
+// run on the tensor cores the other group moves its tile, so the tensor pipe is fed
+// from both.  A group's memory traffic also runs in the windows where it waits for its
+// products: the write-back of its previous tile (16-byte stores from shared memory)
+// during stage 0, the load of its next tile (cp.async into the buffer just written
+// back) during the following stages.
+//
+// Accumulation: the tensor cores truncate the FP32 accumulator toward zero after each
+// product step, which a circuit's stages compound into a norm loss when large partial
+// sums are accumulated many times.  Each accumulator takes half of the K steps, its
+// small products (a_hi b_lo, a_lo b_hi) first and the four a_hi b_hi products last, and
+// the two halves are added on the CUDA cores with round-to-nearest.
+//
+// B images (host-built, already in the K-major 128-byte-swizzled layout, 32 KiB per
+// stage) stream through two shared-memory buffers by bulk copies with mbarrier
+// transaction counts; buffer (x & 1) serves the x-th stage execution of the CTA, and
+// the next image is loaded into the other buffer as soon as both groups have issued
+// stage x (both then have finished x - 1, whose products read that buffer).  Passes
+// with one or two stages keep them resident.
+//
+// Every wait is bounded and also watches a CTA-wide abort word: a wait that runs out
+// sets it, so every other waiter leaves too (the group votes on the outcome in a
+// barrier, so the group's threads leave together); before TMEM is released the MMA thread commits and waits
+// (bounded) for its outstanding products, and every bulk copy in flight is waited for.
 #include <string.h>
 
 #include <algorithm>
 #include <complex>
+#include <mutex>
 #include <vector>
 
 #include "circuit.cuh"
@@ -41,30 +65,36 @@ namespace qcgb {
 constexpr int kTtM = 12;                        // tile bits
 constexpr int kTtL = 4;                         // lowest index bits always in the tile
 constexpr int kTtSB = 5;                        // stage (block) bits
-constexpr int kTtRows = 1 << (kTtM - kTtSB);    // 128 rows = MMA M
-constexpr int kTtThreads = 2 * kTtRows;         // two threads per row (one per K slice)
+constexpr int kTtRows = 1 << (kTtM - kTtSB);    // 128 rows = MMA M = TMEM lanes
+constexpr int kTtGroups = 2;                    // tiles in flight per CTA
+constexpr int kTtGroupThreads = kTtRows;        // one thread per row
+constexpr int kTtThreads = kTtGroups * kTtGroupThreads + 32;  // + the MMA warp
+constexpr int kTtMmaWarp = kTtGroups * kTtGroupThreads / 32;
 constexpr int kTtCols = 2 << kTtSB;             // 64 real columns (K = N)
-constexpr int kTtAregion = kTtRows * 128;       // one 32-column K slice of A: 16 KiB
 constexpr int kTtBregion = kTtCols * 128;       // one 32-column K slice of B: 8 KiB
-constexpr int kTtAbytes = 2 * kTtAregion;       // A_hi (or A_lo): 32 KiB
 constexpr int kTtBimg = 2 * 2 * kTtBregion;     // B_hi + B_lo of one stage: 32 KiB
 constexpr int kTtImgFloats = kTtBimg / 4;
 constexpr int kTtTileBytes = (1 << kTtM) * 8;   // complex64 tile: 32 KiB
 constexpr int kTtMaxStages = kMaxPassOps;
 constexpr int kTtHi = 1 << (kTtM - kTtL);       // 128-byte runs per tile
+// TMEM columns of a group: A_hi [0, 64), A_lo [64, 128), accumulators [128, 256)
+constexpr int kTmemPerGroup = 256;
+constexpr int kTmemCols = kTtGroups * kTmemPerGroup;  // 512
 
 struct TcStage {
-  int32_t img;         // index of the stage's B image
-  int8_t slot_bit[5];  // local bit of block-index bit k
-  int8_t lane_bit[7];  // local bit receiving bit k of the row index
+  int32_t img;          // index of the stage's B image
+  uint32_t swz[5];      // byte offset in the swizzled tile of block-index bit k
+  int8_t lane_bit[7];   // local bit receiving bit k of the row index
+  int8_t pad;
 };
-static_assert(sizeof(TcStage) == 16, "TcStage must be 16 bytes");
+static_assert(sizeof(TcStage) == 32, "TcStage must be 32 bytes");
 
-constexpr size_t kTtSmem = 1024 /* alignment slack */ + 2 * kTtAbytes + 2 * kTtBimg + 2 * kTtTileBytes +
+constexpr size_t kTtSmem = 1024 /* alignment slack */ + 2 * kTtBimg + 2 * kTtGroups * kTtTileBytes +
                            kTtHi * sizeof(uint64_t) + kTileNumberTab * sizeof(uint64_t) +
-                           kTtMaxStages * sizeof(TcStage) + 64;
+                           kTtMaxStages * sizeof(TcStage) + 128;
 
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity) {
+// bounded mbarrier wait that also gives up when another thread has set *abort
+__device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, const volatile int* abort) {
   for (long long it = 0; it < kTcSpinLimit; ++it) {
     uint32_t done;
     asm volatile(
@@ -73,6 +103,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity)
         : "r"(bar), "r"(parity)
         : "memory");
     if (done) return true;
+    if ((it & 63) == 63 && *abort) return false;
   }
   return false;
 }
@@ -85,6 +116,67 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
                : "memory");
 }
 
+// barrier of one epilogue group (named barrier 1 + g, all its threads), with an OR vote
+__device__ __forceinline__ bool group_sync_or(int g, bool v) {
+  uint32_t r;
+  asm volatile(
+      "{\n .reg .pred p, q;\n setp.ne.u32 p, %1, 0;\n bar.red.or.pred q, %2, %3, p;\n selp.u32 %0, 1, 0, q;\n}\n"
+      : "=r"(r)
+      : "r"(v ? 1u : 0u), "r"(1 + g), "n"(kTtGroupThreads)
+      : "memory");
+  return r != 0;
+}
+__device__ __forceinline__ void group_sync(int g) {
+  asm volatile("bar.sync %0, %1;\n" ::"r"(1 + g), "n"(kTtGroupThreads) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,"
+      "%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};\n" ::"r"(taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]), "r"(r[17]), "r"(r[18]),
+      "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]),
+      "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(
+          taddr),
+      "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+      "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+      : "memory");
+}
+
+// D (+)= A B with A in TMEM (M = 128 lanes, K = 8 TF32 columns from a_tmem), B from
+// shared memory (descriptor)
+__device__ __forceinline__ void tc_mma_ts(uint32_t dtm, uint32_t atm, uint64_t bd, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(dtm),
+      "r"(atm), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// tiles of group g of this CTA: 2 blockIdx + g + k (2 gridDim), k = 0, 1, ...
+__device__ __forceinline__ uint32_t group_tiles(uint64_t ntiles, int g) {
+  const uint64_t t0 = 2 * uint64_t(blockIdx.x) + g, step = 2 * uint64_t(gridDim.x);
+  return t0 < ntiles ? uint32_t((ntiles - 1 - t0) / step + 1) : 0u;
+}
+
 __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restrict__ amps, const TilePass P,
                                                                  const TcStage* __restrict__ stages,
                                                                  const float* __restrict__ imgs,
@@ -92,34 +184,32 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  unsigned char* a_hi = base;
-  unsigned char* a_lo = a_hi + kTtAbytes;
-  unsigned char* bbuf = a_lo + kTtAbytes;  // two stage images
-  Cplx<float>* tiles = reinterpret_cast<Cplx<float>*>(bbuf + 2 * kTtBimg);
-  uint64_t* hioff = reinterpret_cast<uint64_t*>(bbuf + 2 * kTtBimg + 2 * kTtTileBytes);
+  unsigned char* bbuf = base;  // two stage images
+  Cplx<float>* tiles = reinterpret_cast<Cplx<float>*>(bbuf + 2 * kTtBimg);  // [group][buffer]
+  uint64_t* hioff = reinterpret_cast<uint64_t*>(bbuf + 2 * kTtBimg + 2 * kTtGroups * kTtTileBytes);
   uint64_t* tnt = hioff + kTtHi;  // tile number -> base
   TcStage* sst = reinterpret_cast<TcStage*>(tnt + kTileNumberTab);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sst + kTtMaxStages);  // products, B buffer 0, B buffer 1
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 3);
+  // mbarriers: full[2] (the group's rows are in TMEM: one arrival per row), done[2]
+  // (products complete),
+  // bfull[2] (B image landed), fin (the MMA thread's last products), bfree[2] (the
+  // products of the last execution that read B buffer b are complete)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sst + kTtMaxStages);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 9);
+  volatile int* abort_word = reinterpret_cast<volatile int*>(tmem_slot + 1);
   __shared__ int8_t sbits[16];
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int m = kTtM, L = kTtL;
   constexpr uint32_t T = 1u << m;
   const int S = P.nstages;
-  // The tensor cores truncate their FP32 accumulator toward zero after each product
-  // step; in one accumulator for all 24 products the last steps, taken at the size of
-  // the result, shrink every output a little and a circuit's stages compound it into a
-  // norm loss (28-qubit brickwork ~4e-5).  So K step ks accumulates its three products
-  // in its own 64 TMEM columns, small products first, and the eight partial sums are
-  // added on the CUDA cores with round-to-nearest.
-  constexpr int kTmemCols = 512;
 
   if (tid == 0) {
 #pragma unroll
     for (int k = 0; k < 16; ++k) sbits[k] = P.bits[k];
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bars)) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bars + 1)) : "memory");
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bars + 2)) : "memory");
+    for (int b = 0; b < 9; ++b) {
+      const uint32_t cnt = b < 2 ? uint32_t(kTtGroupThreads) : 1u;
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bars + b)), "r"(cnt) : "memory");
+    }
+    *abort_word = 0;
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -141,149 +231,230 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const uint32_t mbar = smem_u32(bars);
-  const uint32_t bfull = smem_u32(bars + 1);  // buffer b: bfull + 8 b
-  constexpr uint32_t idesc = tf32_idesc(kTtRows, kTtCols);
+  const uint32_t full0 = smem_u32(bars), done0 = smem_u32(bars + 2), bfull0 = smem_u32(bars + 4),
+                 fin = smem_u32(bars + 6), bfree0 = smem_u32(bars + 7);
+  const uint32_t K0 = group_tiles(P.ntiles, 0), K1 = group_tiles(P.ntiles, 1);
 
-  // B images (thread 0): with one or two stages they stay resident, else buffer g & 1
-  // serves stage execution g and the next execution's image is loaded into the other
-  const bool resident = S <= 2;
-  uint32_t bpar = 0;      // bit b: parity of buffer b's next completion
-  uint32_t inflight = 0;  // bit b: a load into buffer b not waited for yet
-  auto load_b = [&](int b, int s) {
-    bulk_load(smem_u32(bbuf + b * kTtBimg), imgs + size_t(sst[s].img) * kTtImgFloats, kTtBimg, bfull + 8u * b);
-    inflight |= 1u << b;
-  };
-  if (tid == 0 && S > 0) {
-    load_b(0, 0);
-    if (resident && S == 2) load_b(1, 1);
-  }
-
-  uint32_t mpar = 0;
-  bool mma_pending = false;  // thread 0: products issued and not yet seen complete
-  bool failed = false;
-  uint64_t g = 0;
-  const uint64_t G = gridDim.x;
-  const int row = tid & (kTtRows - 1), half = tid >> 7;
-  uint64_t t = blockIdx.x;
-  if (t < P.ntiles) prefetch_tile<float>(tiles, amps, tile_base(t, tnt), hioff, L, T);
-  cp_async_commit();
-  for (int it = 0; t < P.ntiles && !failed; t += G, ++it) {
-    Cplx<float>* tile = tiles + (it & 1) * T;
-    const uint64_t tbase = tile_base(t, tnt);
-    const uint64_t tn = t + G;
-    if (tn < P.ntiles)
-      prefetch_tile<float>(tiles + ((it + 1) & 1) * T, amps, tile_base(tn, tnt), hioff, L, T);
-    cp_async_commit();
-    cp_async_wait1();
-    __syncthreads();
-    for (int s = 0; s < S; ++s, ++g) {
-      const TcStage& st = sst[s];
-      uint32_t r0 = uint32_t(half) << st.slot_bit[4];
-#pragma unroll
-      for (int k = 0; k < 7; ++k) r0 |= uint32_t((row >> k) & 1) << st.lane_bit[k];
-      uint32_t sw[4];
-#pragma unroll
-      for (int k = 0; k < 4; ++k) sw[k] = tile_swz(1u << st.slot_bit[k]);
-      const uint32_t p0 = tile_swz(r0);
-      // this thread's 16 amplitudes (block index c = j + 16 half) -> TF32 hi / lo,
-      // two amplitudes per 16-byte chunk of K slice `half`
-#pragma unroll
-      for (int c4 = 0; c4 < 8; ++c4) {
-        const Cplx<float> u = tile[p0 ^ slot_xor<4>(2 * c4, sw)];
-        const Cplx<float> v = tile[p0 ^ slot_xor<4>(2 * c4 + 1, sw)];
-        const float4 h = make_float4(tf32_rna(u.re), tf32_rna(u.im), tf32_rna(v.re), tf32_rna(v.im));
-        const float4 l =
-            make_float4(tf32_rna(u.re - h.x), tf32_rna(u.im - h.y), tf32_rna(v.re - h.z), tf32_rna(v.im - h.w));
-        const uint32_t o = sw128_offset(row, 32 * half + 4 * c4, kTtRows);
-        *reinterpret_cast<float4*>(a_hi + o) = h;
-        *reinterpret_cast<float4*>(a_lo + o) = l;
+  if (warp == kTtMmaWarp) {
+    // ------------------------------------------------------------------ MMA warp
+    if (lane == 0) {
+      constexpr uint32_t idesc = tf32_idesc(kTtRows, kTtCols);
+      const bool resident = S <= 2;
+      uint32_t bpar = 0, inflight = 0;
+      uint32_t fpar_b = 0, freeing = 0;  // bfree[b]: parity of its next phase; a commit not yet waited for
+      auto load_b = [&](int b, int s) {
+        bulk_load(smem_u32(bbuf + b * kTtBimg), imgs + size_t(sst[s].img) * kTtImgFloats, kTtBimg, bfull0 + 8u * b);
+        inflight |= 1u << b;
+      };
+      if (S > 0) {
+        load_b(0, 0);
+        if (S == 2) load_b(1, 1);
       }
-      const int b = resident ? s : int(g & 1);
-      bool bad = false;
-      if (tid == 0 && ((inflight >> b) & 1u)) {
-        bad = !mbar_wait_bounded(bfull + 8u * b, (bpar >> b) & 1u);
-        if (!bad) {
-          bpar ^= 1u << b;
-          inflight &= ~(1u << b);
+      uint32_t fpar = 0;  // bit g: parity of group g's next full phase
+      bool issued = false, ok = true;
+      uint64_t x = 0;  // stage executions of this CTA
+      const uint32_t Kmax = K0 > K1 ? K0 : K1;
+      for (uint32_t k = 0; k < Kmax && ok; ++k) {
+        for (int s = 0; s < S && ok; ++s, ++x) {
+          const int b = resident ? s : int(x & 1);
+          if ((inflight >> b) & 1u) {
+            ok = mbar_wait_ab(bfull0 + 8u * b, (bpar >> b) & 1u, abort_word);
+            if (!ok) break;
+            bpar ^= 1u << b;
+            inflight &= ~(1u << b);
+          }
+          const uint32_t bh = smem_u32(bbuf + b * kTtBimg), bl = bh + 2 * kTtBregion;
+          for (int g = 0; g < kTtGroups; ++g) {
+            if (k >= (g ? K1 : K0)) continue;
+            ok = mbar_wait_ab(full0 + 8u * g, (fpar >> g) & 1u, abort_word);
+            if (!ok) break;
+            fpar ^= 1u << g;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            const uint32_t gb = tmem + uint32_t(g * kTmemPerGroup);
+            for (int h = 0; h < 2; ++h) {
+              const uint32_t d = gb + 128u + uint32_t(64 * h);
+              // the small products first, then the a_hi b_hi products
+              for (int ks = 4 * h; ks < 4 * h + 4; ++ks) {
+                const uint32_t boff = uint32_t((ks >> 2) * kTtBregion + (ks & 3) * 32);
+                tc_mma_ts(d, gb + uint32_t(8 * ks), sw128_desc(bl + boff, kTcAtom), idesc, ks == 4 * h ? 0u : 1u);
+                tc_mma_ts(d, gb + 64u + uint32_t(8 * ks), sw128_desc(bh + boff, kTcAtom), idesc, 1u);
+              }
+              for (int ks = 4 * h; ks < 4 * h + 4; ++ks) {
+                const uint32_t boff = uint32_t((ks >> 2) * kTtBregion + (ks & 3) * 32);
+                tc_mma_ts(d, gb + uint32_t(8 * ks), sw128_desc(bh + boff, kTcAtom), idesc, 1u);
+              }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             done0 + 8u * g)
+                         : "memory");
+            issued = true;
+          }
+          if (!ok) break;
+          if (!resident) {
+            // completion of this execution's products frees buffer b
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                             bfree0 + 8u * b)
+                         : "memory");
+            freeing |= 1u << b;
+            // the next execution's image goes into the other buffer once the products
+            // of the execution before this one (the last to read it) are complete
+            const bool more = (s + 1 < S) || (k + 1 < Kmax);
+            const int nb = b ^ 1;
+            if (more) {
+              if ((freeing >> nb) & 1u) {
+                ok = mbar_wait_ab(bfree0 + 8u * nb, (fpar_b >> nb) & 1u, abort_word);
+                if (!ok) break;
+                fpar_b ^= 1u << nb;
+                freeing &= ~(1u << nb);
+              }
+              load_b(nb, s + 1 < S ? s + 1 : 0);
+            }
+          }
         }
       }
-      // the generic-proxy stores of A become visible to the tensor cores
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-      failed = __syncthreads_or(bad ? 1 : 0) != 0;
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      if (failed) break;
-      if (tid == 0) {
-        const uint32_t ah = smem_u32(a_hi), al = smem_u32(a_lo);
-        const uint32_t bh = smem_u32(bbuf + b * kTtBimg), bl = bh + 2 * kTtBregion;
-        for (int ks = 0; ks < kTtCols / 8; ++ks) {
-          const uint32_t koff = uint32_t((ks & 3) * 32);
-          const uint32_t aoff = (ks >> 2) * kTtAregion + koff, boff = (ks >> 2) * kTtBregion + koff;
-          const uint32_t d = tmem + uint32_t(64 * ks);
-          // the two small products first: only the last accumulation (adding a_hi b_hi)
-          // is truncated at the size of the partial sum
-          tc_mma(d, sw128_desc(ah + aoff, kTcAtom), sw128_desc(bl + boff, kTcAtom), idesc, 0u);
-          tc_mma(d, sw128_desc(al + aoff, kTcAtom), sw128_desc(bh + boff, kTcAtom), idesc, 1u);
-          tc_mma(d, sw128_desc(ah + aoff, kTcAtom), sw128_desc(bh + boff, kTcAtom), idesc, 1u);
-        }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar)
+      if (!ok) *abort_word = 1;
+      // outstanding products and copies finish before the block leaves (bounded)
+      if (issued) {
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(fin)
                      : "memory");
-        mma_pending = true;
-        // the other buffer's last readers (the previous stage's products) are done
-        if (!resident) load_b(b ^ 1, s + 1 < S ? s + 1 : 0);
+        const volatile int never = 0;
+        if (!mbar_wait_ab(fin, 0, &never)) *abort_word = 1;
       }
-      const bool done = mbar_wait_bounded(mbar, mpar);
-      mpar ^= 1u;
-      asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-      // this thread's half-row of D: TMEM lane `row`, columns 32 half .. 32 half + 31
-      {
-        const uint32_t ta = tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(32 * half);
+      for (int b = 0; b < 2; ++b)
+        if ((inflight >> b) & 1u) {
+          const volatile int never = 0;
+          mbar_wait_ab(bfull0 + 8u * b, (bpar >> b) & 1u, &never);
+        }
+    }
+  } else {
+    // ------------------------------------------------------------ epilogue groups
+    const int g = warp >> 2;                        // group
+    const int row = tid & (kTtRows - 1);            // this thread's row = TMEM lane
+    const uint32_t Kg = g ? K1 : K0;
+    Cplx<float>* buf0 = tiles + size_t(g) * 2 * T;
+    const uint32_t ta = tmem + (uint32_t(32 * (warp & 3)) << 16) + uint32_t(g * kTmemPerGroup);
+    const uint64_t G2 = 2 * uint64_t(gridDim.x);
+    const uint64_t t0 = 2 * uint64_t(blockIdx.x) + g;
+    constexpr uint32_t lowmask = (1u << L) - 1;
+    uint32_t dpar = 0;
+    bool failed = false;
+    // this thread's share (elements i = part, part + parts, ... of its row's stride) of
+    // the asynchronous load of tile t into dst
+    auto prefetch = [&](Cplx<float>* dst, uint64_t t, int part, int parts) {
+      const float* src = amps + 2 * tile_base(t, tnt);
+      for (uint32_t r = row + uint32_t(part) * kTtGroupThreads; r < T; r += uint32_t(parts) * kTtGroupThreads)
+        cp_async_amp<float>(dst + tile_swz(r), src + 2 * (hioff[r >> L] | (r & lowmask)));
+    };
+    // write-back of tile t from src, two amplitudes (16 bytes) per store
+    auto store = [&](const Cplx<float>* src, uint64_t t) {
+      const uint64_t tbase = tile_base(t, tnt);
+      for (uint32_t e = row; e < T / 2; e += kTtGroupThreads) {
+        const uint32_t r = 2 * e;
+        const uint64_t gi = tbase | hioff[r >> L] | (r & lowmask);
+        const uint32_t p = tile_swz(r);
+        st_amp2<float>(amps, gi, src[p], src[p ^ 1u]);
+      }
+    };
+    if (Kg > 0) prefetch(buf0, t0, 0, 1);
+    cp_async_commit();
+    // Tile k works in buffer k & 1.  Its write-back is deferred to the wait for the
+    // products of stage 0 of tile k + 1, and the load of tile k + 1 (into the buffer
+    // just written back) is spread over the waits of the stages after stage 0 of tile k
+    // (after the group barrier that ends stage 0), so both overlap the tensor cores.
+    for (uint32_t k = 0; k < Kg && !failed; ++k) {
+      Cplx<float>* cur = buf0 + (k & 1) * T;
+      Cplx<float>* other = buf0 + ((k + 1) & 1) * T;
+      unsigned char* curb = reinterpret_cast<unsigned char*>(cur);
+      const uint64_t t = t0 + k * G2;
+      const bool next = k + 1 < Kg;
+      const int nparts = S >= 3 ? 2 : 1;  // load windows: stages 1 .. nparts
+      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+      group_sync(g);
+      for (int s = 0; s < S; ++s) {
+        const TcStage& st = sst[s];
+        uint32_t r0 = 0;
+#pragma unroll
+        for (int b = 0; b < 7; ++b) r0 |= uint32_t((row >> b) & 1) << st.lane_bit[b];
+        uint32_t sw[5];
+#pragma unroll
+        for (int b = 0; b < 5; ++b) sw[b] = st.swz[b];
+        // byte offsets of block indices c = i ^ (i >> 1) (Gray order: one XOR each);
+        // formed again for the write-back of this stage's outputs (not kept in
+        // registers over the wait, whose window runs the memory traffic)
+        const uint32_t off0 = tile_swz(r0) * 8u;
+        uint32_t off[32];
+        off[0] = off0;
+#pragma unroll
+        for (int i = 1; i < 32; ++i) off[i] = off[i - 1] ^ sw[(i & 1) ? 0 : (i & 2) ? 1 : (i & 4) ? 2 : (i & 8) ? 3 : 4];
+        // this row's 32 amplitudes -> TF32 hi / lo in TMEM (A_hi columns 0..63, A_lo
+        // columns 64..127, column 2c + ri); chunk q holds c in [16q, 16q + 16)
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-          float y[16];
+          uint32_t hi[32], lo[32];
 #pragma unroll
-          for (int i = 0; i < 16; ++i) y[i] = 0.0f;
-#pragma unroll
-          for (int ks = 0; ks < 8; ks += 2) {
-            uint32_t pa[16], pb[16];  // partial sums of K steps ks and ks + 1
-            tmem_ld16(ta + uint32_t(64 * ks + 16 * q), pa);
-            tmem_ld16(ta + uint32_t(64 * (ks + 1) + 16 * q), pb);
-            asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-            for (int i = 0; i < 16; ++i) y[i] += __uint_as_float(pa[i]) + __uint_as_float(pb[i]);
+          for (int i = 16 * q; i < 16 * q + 16; ++i) {
+            const int c = (i ^ (i >> 1)) - 16 * q;
+            const float2 v = *reinterpret_cast<const float2*>(curb + off[i]);
+            const float hr = tf32_rna(v.x), hm = tf32_rna(v.y);
+            hi[2 * c] = __float_as_uint(hr);
+            hi[2 * c + 1] = __float_as_uint(hm);
+            lo[2 * c] = __float_as_uint(v.x - hr);
+            lo[2 * c + 1] = __float_as_uint(v.y - hm);
           }
-#pragma unroll
-          for (int j = 0; j < 8; ++j) tile[p0 ^ slot_xor<4>(8 * q + j, sw)] = Cplx<float>{y[2 * j], y[2 * j + 1]};
+          tmem_st32(ta + uint32_t(32 * q), hi);
+          tmem_st32(ta + 64u + uint32_t(32 * q), lo);
         }
+        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(full0 + 8u * g) : "memory");
+        // work for the memory system while the products run
+        if (s == 0 && k > 0) store(other, t - G2);
+        if (next && s >= 1 && s <= nparts) prefetch(other, t + G2, s - 1, nparts);
+        const bool ok = mbar_wait_ab(done0 + 8u * g, dpar, abort_word);
+        dpar ^= 1u;
+        if (group_sync_or(g, !ok)) {
+          failed = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        // the row of D: the two partial sums added, written into the tile at this
+        // stage's positions (for the next stage's gather, or the write-back)
+        off[0] = off0;
+#pragma unroll
+        for (int i = 1; i < 32; ++i) off[i] = off[i - 1] ^ sw[(i & 1) ? 0 : (i & 2) ? 1 : (i & 4) ? 2 : (i & 8) ? 3 : 4];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          uint32_t d0[32], d1[32];
+          tmem_ld32(ta + 128u + uint32_t(32 * q), d0);
+          tmem_ld32(ta + 192u + uint32_t(32 * q), d1);
+          asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+          for (int i = 16 * q; i < 16 * q + 16; ++i) {
+            const int c = (i ^ (i >> 1)) - 16 * q;
+            *reinterpret_cast<float2*>(curb + off[i]) =
+                make_float2(__uint_as_float(d0[2 * c]) + __uint_as_float(d1[2 * c]),
+                            __uint_as_float(d0[2 * c + 1]) + __uint_as_float(d1[2 * c + 1]));
+          }
+        }
+        group_sync(g);  // the tile is complete before the next stage gathers
       }
-      // the tile is complete before the next stage gathers, and the TMEM reads are done
-      // before the next products overwrite D
-      asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-      failed = __syncthreads_or(done ? 0 : 1) != 0;
-      if (!failed && tid == 0) mma_pending = false;
       if (failed) break;
+      if (S == 0 && k > 0) {  // no stage windows: write back and load here
+        store(other, t - G2);
+        group_sync(g);
+      }
+      if (next && (S <= 1)) prefetch(other, t + G2, 0, 1);
+      cp_async_commit();
     }
-    if (failed) break;
-    for (uint32_t e = tid; e < T / 2; e += kTtThreads) {
-      const uint32_t r = 2 * e;
-      const uint64_t gi = tbase | hioff[r >> L] | (r & ((1u << L) - 1));
-      const uint32_t p = tile_swz(r);
-      st_amp2<float>(amps, gi, tile[p], tile[p ^ 1u]);
-    }
-    __syncthreads();  // this buffer is refilled two iterations later
-  }
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-  if (tid == 0) {
-    if (failed) atomicExch(status, 1);
-    // copies and products still in flight finish before the block leaves (bounded)
-    for (int b = 0; b < 2; ++b)
-      if ((inflight >> b) & 1u) mbar_wait_bounded(bfull + 8u * b, (bpar >> b) & 1u);
-    if (mma_pending) mbar_wait_bounded(mbar, mpar ^ 1u);
+    // the last tile's write-back
+    if (!failed && Kg > 0) store(buf0 + ((Kg - 1) & 1) * T, t0 + uint64_t(Kg - 1) * G2);
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+    if (failed) *abort_word = 1;
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+  if (tid == 0 && *abort_word) atomicExch(status, 1);
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
@@ -292,6 +463,13 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
 // host
 // ---------------------------------------------------------------------------
 using cd = std::complex<double>;
+
+// the device tile swizzle (tile_swz) on the host: index bits 0..3 XOR-ed with a hash of
+// the higher bits
+static uint32_t tile_swz_host(uint32_t r) {
+  const uint32_t x = r >> 4;
+  return r ^ ((x ^ (x >> 4) ^ (x >> 8)) & 15u);
+}
 
 // nearest TF32 value (ties to even) of a finite fp32 value of modest size
 static float tf32_rne_host(float v) {
@@ -397,23 +575,59 @@ static bool tc_pass_blocks(const BuiltPass& bp, const std::vector<PlanOp>& pops,
           lo[off] = tf32_rne_host(v - h);
         }
       }
-    for (int k = 0; k < kTtSB; ++k) ts.slot_bit[k] = recs[si].slot_bit[k];
+    for (int k = 0; k < kTtSB; ++k) ts.swz[k] = tile_swz_host(1u << recs[si].slot_bit[k]) * 8u;
     for (int k = 0; k < kTtM - kTtSB; ++k) ts.lane_bit[k] = recs[si].lane_bit[k];
     out.push_back(ts);
   }
   return true;
 }
 
-qc_status run_tiles_tc(qc_state* s, const std::vector<ResolvedOp>& rops, bool* handled) {
-  *handled = false;
+// The most recent tensor-core circuit plan of the process: the resolved ops it was built
+// from (compared exactly on the next call), its passes, and on the device its stage
+// records and B images.  A repeated circuit (the usual case: the same circuit on new
+// inputs) skips planning, the host products of the stage blocks and the upload.
+struct TcPlanCache {
+  int device = -1;
+  int n = 0;
+  std::vector<ResolvedOp> rops;
+  bool valid = false;
+  bool tc = false;  // false: an op depends on a bit outside its stage (CUDA-core passes)
+  std::vector<TilePass> passes;
+  int nstages = 0;
+  std::vector<char> host;  // staging of the upload (kept until the next rebuild)
+  void* dev = nullptr;
+  size_t dev_bytes = 0;
+  size_t stage_bytes = 0;
+  cudaEvent_t done = nullptr;  // recorded after the launches that read `dev`
+  bool pending = false;
+};
+static TcPlanCache g_tc;
+static std::mutex g_tc_mu;
+
+static bool same_ops(const std::vector<ResolvedOp>& a, const std::vector<ResolvedOp>& b) {
+  if (a.size() != b.size()) return false;
+  for (size_t i = 0; i < a.size(); ++i) {
+    const ResolvedOp &x = a[i], &y = b[i];
+    if (x.form != y.form || x.nq != y.nq || x.cstate != y.cstate) return false;
+    for (int k = 0; k < x.nq; ++k)
+      if (x.bits[k] != y.bits[k]) return false;
+    const int dim = x.form == FORM_2Q ? 4 : 2;
+    if (memcmp(x.m, y.m, sizeof(double) * 2 * dim * dim) != 0) return false;
+  }
+  return true;
+}
+
+// plans `rops` into the cache (host stage blocks, B images, upload)
+static qc_status tc_plan(qc_state* s, const std::vector<ResolvedOp>& rops, int dev) {
   const int n = s->n;
-  if (s->dtype != QC_C64 || n < kTtM) return QC_OK;
+  g_tc.valid = false;
   std::vector<PlanOp> pops;
   to_plan_ops(rops, pops);
   const std::vector<BuiltPass> bps = build_passes(pops, n, kTtM, kTtL);
   std::vector<TilePass> passes;
   std::vector<TcStage> stages;
   std::vector<float> imgs;
+  bool tc = true;
   for (const BuiltPass& bp : bps) {
     TilePass P{};
     P.m = kTtM;
@@ -421,51 +635,99 @@ qc_status run_tiles_tc(qc_state* s, const std::vector<ResolvedOp>& rops, bool* h
     for (int i = 0; i < kTtM; ++i) P.bits[i] = int8_t(bp.B[i]);
     P.ntiles = uint64_t(1) << (n - kTtM);
     P.stage0 = int(stages.size());
-    if (!tc_pass_blocks(bp, pops, n, stages, imgs)) return QC_OK;  // the CUDA-core passes take it
+    if (!tc_pass_blocks(bp, pops, n, stages, imgs)) {  // the CUDA-core passes take it
+      tc = false;
+      break;
+    }
     P.nstages = int(stages.size()) - P.stage0;
-    if (P.nstages > kTtMaxStages) return QC_OK;
+    if (P.nstages > kTtMaxStages) {
+      tc = false;
+      break;
+    }
     passes.push_back(P);
   }
+  g_tc.device = dev;
+  g_tc.n = n;
+  g_tc.rops = rops;
+  g_tc.tc = tc;
+  g_tc.valid = true;
+  if (!tc) return QC_OK;
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t sb = al(stages.size() * sizeof(TcStage) + 1);
   const size_t ib = imgs.size() * sizeof(float);
-  void* scr = nullptr;
-  if (qc_status st = state_scratch(s, 256 + sb + ib, &scr)) return st;
-  char* base = static_cast<char*>(scr);
-  int* status = reinterpret_cast<int*>(base);
-  const TcStage* dst = reinterpret_cast<const TcStage*>(base + 256);
-  const float* dimg = reinterpret_cast<const float*>(base + 256 + sb);
-  std::vector<char> host(sb + ib, 0);
-  if (!stages.empty()) memcpy(host.data(), stages.data(), stages.size() * sizeof(TcStage));
-  if (ib) memcpy(host.data() + sb, imgs.data(), ib);
-  if (qc_status st = check_cuda(cudaMemsetAsync(status, 0, sizeof(int), s->stream), "status reset")) return st;
-  if (qc_status st = check_cuda(cudaMemcpyAsync(base + 256, host.data(), host.size(), cudaMemcpyHostToDevice,
+  g_tc.host.assign(sb + ib, 0);
+  if (!stages.empty()) memcpy(g_tc.host.data(), stages.data(), stages.size() * sizeof(TcStage));
+  if (ib) memcpy(g_tc.host.data() + sb, imgs.data(), ib);
+  // the previous plan's launches are done with the buffer before it is overwritten
+  if (g_tc.pending) cudaEventSynchronize(g_tc.done);
+  g_tc.pending = false;
+  if (g_tc.dev_bytes < sb + ib) {
+    if (g_tc.dev) cudaFree(g_tc.dev);
+    g_tc.dev = nullptr;
+    g_tc.dev_bytes = 0;
+    if (qc_status st = check_cuda(cudaMalloc(&g_tc.dev, sb + ib), "tensor-core plan buffer")) {
+      g_tc.valid = false;
+      return st;
+    }
+    g_tc.dev_bytes = sb + ib;
+  }
+  if (qc_status st = check_cuda(cudaMemcpyAsync(g_tc.dev, g_tc.host.data(), sb + ib, cudaMemcpyHostToDevice,
                                                 s->stream),
-                                "tensor-core plan upload"))
+                                "tensor-core plan upload")) {
+    g_tc.valid = false;
     return st;
+  }
+  g_tc.passes = passes;
+  g_tc.nstages = int(stages.size());
+  g_tc.stage_bytes = sb;
+  return QC_OK;
+}
+
+qc_status run_tiles_tc(qc_state* s, const std::vector<ResolvedOp>& rops, bool* handled) {
+  *handled = false;
+  const int n = s->n;
+  if (s->dtype != QC_C64 || n < kTtM) return QC_OK;
+  int dev = 0;
+  if (qc_status st = check_cuda(cudaGetDevice(&dev), "cudaGetDevice")) return st;
+  std::lock_guard<std::mutex> lock(g_tc_mu);
+  if (!g_tc.done)
+    if (qc_status st = check_cuda(cudaEventCreateWithFlags(&g_tc.done, cudaEventDisableTiming), "plan event"))
+      return st;
+  if (!(g_tc.valid && g_tc.device == dev && g_tc.n == n && same_ops(g_tc.rops, rops)))
+    if (qc_status st = tc_plan(s, rops, dev)) return st;
+  if (!g_tc.tc) return QC_OK;
+  void* scr = nullptr;
+  if (qc_status st = state_scratch(s, 256, &scr)) return st;
+  int* status = static_cast<int*>(scr);
+  const TcStage* dst = static_cast<const TcStage*>(g_tc.dev);
+  const float* dimg = reinterpret_cast<const float*>(static_cast<char*>(g_tc.dev) + g_tc.stage_bytes);
+  if (qc_status st = check_cuda(cudaMemsetAsync(status, 0, sizeof(int), s->stream), "status reset")) return st;
   auto kern = k_tile_pass_tc;
   if (qc_status st = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTtSmem)),
                                 "tensor-core tile pass shared memory"))
     return st;
   const uint64_t ntiles = uint64_t(1) << (n - kTtM);
-  const unsigned grid = unsigned(std::min<uint64_t>(ntiles, uint64_t(device_sm_count())));
+  // one CTA per SM, two tiles in flight per CTA
+  const unsigned grid = unsigned(std::min<uint64_t>((ntiles + 1) / 2, uint64_t(device_sm_count())));
   float* a = reinterpret_cast<float*>(s->amps);
-  for (const TilePass& P : passes) {
+  for (const TilePass& P : g_tc.passes) {
     QC_COUNT(), kern<<<grid, kTtThreads, kTtSmem, s->stream>>>(a, P, dst, dimg, status);
   }
   if (qc_status st = check_launch("tensor-core tile pass")) return st;
+  if (qc_status st = check_cuda(cudaEventRecord(g_tc.done, s->stream), "plan event")) return st;
+  g_tc.pending = true;
   int h = 0;
   if (qc_status st = check_cuda(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s->stream),
                                 "status"))
     return st;
   if (qc_status st = check_cuda(cudaStreamSynchronize(s->stream), "tensor-core tile pass")) return st;
   if (h != 0) {
-    set_error("tensor-core tile pass: a bounded wait for a copy or the products ran out");
+    set_error("tensor-core tile pass: a bounded wait for a copy or the products ran out (the state is undefined)");
     return QC_ERR_TIMEOUT;
   }
-  g_last_pass_count = int(passes.size());
+  g_last_pass_count = int(g_tc.passes.size());
   g_last_fused_path = 2;
-  g_last_stage_count = int(stages.size());
+  g_last_stage_count = g_tc.nstages;
   *handled = true;
   return QC_OK;
 }
