@@ -18,7 +18,8 @@
 // in shared memory (byte offsets formed in Gray-code order, one XOR each, and kept for
 // the write-back), splits them and writes A_hi and A_lo into TMEM (tcgen05.st), so A
 // never passes through shared memory as an operand (the tensor cores read only B
-// there), and arrives on the group's mbarrier; the last arrival lets the MMA warp go.  The MMA warp
+// there), and arrives on the group's mbarrier of that half of the columns: the MMA warp
+// starts the K steps of the first half while the second half is being gathered.  The MMA warp
 // issues the stage's 24 products (A from TMEM, B from shared memory) into two FP32
 // accumulators and commits them to the group's mbarrier.  The group reads its rows of
 // D back (tcgen05.ld), adds the two partial sums, writes the outputs into the tile at
@@ -47,6 +48,8 @@
 // sets it, so every other waiter leaves too (the group votes on the outcome in a
 // barrier, so the group's threads leave together); before TMEM is released the MMA thread commits and waits
 // (bounded) for its outstanding products, and every bulk copy in flight is waited for.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <string.h>
 
 #include <algorithm>
@@ -91,7 +94,25 @@ static_assert(sizeof(TcStage) == 32, "TcStage must be 32 bytes");
 
 constexpr size_t kTtSmem = 1024 /* alignment slack */ + 2 * kTtBimg + 2 * kTtGroups * kTtTileBytes +
                            kTtHi * sizeof(uint64_t) + kTileNumberTab * sizeof(uint64_t) +
-                           kTtMaxStages * sizeof(TcStage) + 128;
+                           kTtMaxStages * sizeof(TcStage) + 256;
+
+// A pass whose tile is one box of the state for the tensor memory accelerator: the
+// state's index bits as at most 5 runs (dimension 0: bits 0..3, 16 amplitudes = 128
+// bytes; then alternating runs of bits in and out of the tile), box = the whole of the
+// tile's runs and one element of the others.  The box lands in shared memory with the
+// 128-byte swizzle (16-byte chunk c of 128-byte row r at chunk c ^ (r & 7)).
+struct TcTma {
+  int32_t tma;         // 1: tiles move by cp.async.bulk.tensor, 0: by cp.async
+  int8_t start[5];     // first index bit of dimension d
+  int8_t len[5];       // its bits (0: a padding dimension of size 1)
+  int8_t tile[5];      // 1: dimension d is in the tile (coordinate 0)
+  int8_t pad;
+};
+
+// byte offset of local index u in a tile with the 128-byte swizzle (XOR-linear in u)
+__host__ __device__ __forceinline__ uint32_t tma_swz_bytes(uint32_t u) {
+  return ((u >> 4) << 7) | ((((u >> 1) ^ (u >> 4)) & 7u) << 4) | ((u & 1u) << 3);
+}
 
 // bounded mbarrier wait that also gives up when another thread has set *abort
 __device__ __forceinline__ bool mbar_wait_ab(uint32_t bar, uint32_t parity, const volatile int* abort) {
@@ -177,10 +198,40 @@ __device__ __forceinline__ uint32_t group_tiles(uint64_t ntiles, int g) {
   return t0 < ntiles ? uint32_t((ntiles - 1 - t0) / step + 1) : 0u;
 }
 
+// coordinates of tile t's box: its base index's bits in the dimensions outside the tile
+__device__ __forceinline__ void tma_coords(uint64_t base, const TcTma& tm, int32_t (&c)[5]) {
+#pragma unroll
+  for (int d = 0; d < 5; ++d)
+    c[d] = tm.tile[d] || tm.len[d] == 0 ? 0 : int32_t((base >> tm.start[d]) & ((uint64_t(1) << tm.len[d]) - 1));
+}
+
+__device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap* map, const int32_t (&c)[5],
+                                              uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(uint32_t(kTtTileBytes))
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
+      "%6}], [%7];\n" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_store_tile(uint32_t src, const CUtensorMap* map, const int32_t (&c)[5]) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];\n" ::"l"(
+          reinterpret_cast<uint64_t>(map)),
+      "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(src)
+      : "memory");
+  asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+
+template <bool TMA>
 __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restrict__ amps, const TilePass P,
                                                                  const TcStage* __restrict__ stages,
                                                                  const float* __restrict__ imgs,
-                                                                 int* __restrict__ status) {
+                                                                 int* __restrict__ status,
+                                                                 const __grid_constant__ CUtensorMap tmap,
+                                                                 const TcTma tm) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -189,12 +240,13 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
   uint64_t* hioff = reinterpret_cast<uint64_t*>(bbuf + 2 * kTtBimg + 2 * kTtGroups * kTtTileBytes);
   uint64_t* tnt = hioff + kTtHi;  // tile number -> base
   TcStage* sst = reinterpret_cast<TcStage*>(tnt + kTileNumberTab);
-  // mbarriers: full[2] (the group's rows are in TMEM: one arrival per row), done[2]
-  // (products complete),
+  // mbarriers: full[2][2] (half h of the group's rows' columns is in TMEM: one arrival
+  // per row), done[2] (products complete),
   // bfull[2] (B image landed), fin (the MMA thread's last products), bfree[2] (the
-  // products of the last execution that read B buffer b are complete)
+  // products of the last execution that read B buffer b are complete), tload[2] (a
+  // group's tile landed)
   uint64_t* bars = reinterpret_cast<uint64_t*>(sst + kTtMaxStages);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 9);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 13);
   volatile int* abort_word = reinterpret_cast<volatile int*>(tmem_slot + 1);
   __shared__ int8_t sbits[16];
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -205,8 +257,8 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
   if (tid == 0) {
 #pragma unroll
     for (int k = 0; k < 16; ++k) sbits[k] = P.bits[k];
-    for (int b = 0; b < 9; ++b) {
-      const uint32_t cnt = b < 2 ? uint32_t(kTtGroupThreads) : 1u;
+    for (int b = 0; b < 13; ++b) {
+      const uint32_t cnt = b < 4 ? uint32_t(kTtGroupThreads) : 1u;
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bars + b)), "r"(cnt) : "memory");
     }
     *abort_word = 0;
@@ -231,8 +283,8 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const uint32_t full0 = smem_u32(bars), done0 = smem_u32(bars + 2), bfull0 = smem_u32(bars + 4),
-                 fin = smem_u32(bars + 6), bfree0 = smem_u32(bars + 7);
+  const uint32_t full0 = smem_u32(bars), done0 = smem_u32(bars + 4), bfull0 = smem_u32(bars + 6),
+                 fin = smem_u32(bars + 8), bfree0 = smem_u32(bars + 9), tload0 = smem_u32(bars + 11);
   const uint32_t K0 = group_tiles(P.ntiles, 0), K1 = group_tiles(P.ntiles, 1);
 
   if (warp == kTtMmaWarp) {
@@ -266,12 +318,13 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
           const uint32_t bh = smem_u32(bbuf + b * kTtBimg), bl = bh + 2 * kTtBregion;
           for (int g = 0; g < kTtGroups; ++g) {
             if (k >= (g ? K1 : K0)) continue;
-            ok = mbar_wait_ab(full0 + 8u * g, (fpar >> g) & 1u, abort_word);
-            if (!ok) break;
-            fpar ^= 1u << g;
-            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             const uint32_t gb = tmem + uint32_t(g * kTmemPerGroup);
-            for (int h = 0; h < 2; ++h) {
+            for (int h = 0; h < 2 && ok; ++h) {
+              // the K steps of half h read A columns [32h, 32h + 32) (+ 64): they start
+              // as soon as every row has written that half
+              ok = mbar_wait_ab(full0 + 8u * (2 * g + h), (fpar >> g) & 1u, abort_word);
+              if (!ok) break;
+              asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
               const uint32_t d = gb + 128u + uint32_t(64 * h);
               // the small products first, then the a_hi b_hi products
               for (int ks = 4 * h; ks < 4 * h + 4; ++ks) {
@@ -284,6 +337,8 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
                 tc_mma_ts(d, gb + uint32_t(8 * ks), sw128_desc(bh + boff, kTcAtom), idesc, 1u);
               }
             }
+            if (!ok) break;
+            fpar ^= 1u << g;
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
                              done0 + 8u * g)
                          : "memory");
@@ -355,7 +410,20 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
         st_amp2<float>(amps, gi, src[p], src[p ^ 1u]);
       }
     };
-    if (Kg > 0) prefetch(buf0, t0, 0, 1);
+    constexpr bool tma = TMA;
+    const bool elect = row == 0;
+    const uint32_t tload = tload0 + 8u * g;
+    uint32_t nload = 0, nwait = 0;  // (TMA) tile loads issued (elected thread) / waited for
+    if (Kg > 0) {
+      if (!tma) {
+        prefetch(buf0, t0, 0, 1);
+      } else if (elect) {
+        int32_t c[5];
+        tma_coords(tile_base(t0, tnt), tm, c);
+        tma_load_tile(smem_u32(buf0), &tmap, c, tload);
+        ++nload;
+      }
+    }
     cp_async_commit();
     // Tile k works in buffer k & 1.  Its write-back is deferred to the wait for the
     // products of stage 0 of tile k + 1, and the load of tile k + 1 (into the buffer
@@ -368,8 +436,31 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
       const uint64_t t = t0 + k * G2;
       const bool next = k + 1 < Kg;
       const int nparts = S >= 3 ? 2 : 1;  // load windows: stages 1 .. nparts
-      asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-      group_sync(g);
+      if (tma) {
+        if (!mbar_wait_ab(tload, k & 1u, abort_word))
+          failed = true;
+        else
+          ++nwait;
+        if (group_sync_or(g, failed)) {
+          failed = true;
+          break;
+        }
+      } else {
+        asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+        group_sync(g);
+      }
+      bool loaded = false;  // (TMA) the load of tile k + 1 is issued
+      auto tma_next = [&]() {
+        if (elect && next) {
+          // the write-back of tile k - 1 has read `other` before it is refilled
+          asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
+          int32_t c[5];
+          tma_coords(tile_base(t + G2, tnt), tm, c);
+          tma_load_tile(smem_u32(other), &tmap, c, tload);
+          ++nload;
+        }
+        loaded = true;
+      };
       for (int s = 0; s < S; ++s) {
         const TcStage& st = sst[s];
         uint32_t r0 = 0;
@@ -381,7 +472,7 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
         // byte offsets of block indices c = i ^ (i >> 1) (Gray order: one XOR each);
         // formed again for the write-back of this stage's outputs (not kept in
         // registers over the wait, whose window runs the memory traffic)
-        const uint32_t off0 = tile_swz(r0) * 8u;
+        const uint32_t off0 = tma ? tma_swz_bytes(r0) : tile_swz(r0) * 8u;
         uint32_t off[32];
         off[0] = off0;
 #pragma unroll
@@ -403,13 +494,18 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
           }
           tmem_st32(ta + uint32_t(32 * q), hi);
           tmem_st32(ta + 64u + uint32_t(32 * q), lo);
+          // this half of the row is in TMEM: its K steps may start
+          asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
+          asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(full0 + 8u * (2 * g + q)) : "memory");
         }
-        asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(full0 + 8u * g) : "memory");
         // work for the memory system while the products run
-        if (s == 0 && k > 0) store(other, t - G2);
-        if (next && s >= 1 && s <= nparts) prefetch(other, t + G2, s - 1, nparts);
+        if (tma) {
+          if (s == 0) tma_next();
+        } else {
+          if (s == 0 && k > 0) store(other, t - G2);
+          if (next && s >= 1 && s <= nparts) prefetch(other, t + G2, s - 1, nparts);
+        }
         const bool ok = mbar_wait_ab(done0 + 8u * g, dpar, abort_word);
         dpar ^= 1u;
         if (group_sync_or(g, !ok)) {
@@ -436,9 +532,21 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
                             __uint_as_float(d0[2 * c + 1]) + __uint_as_float(d1[2 * c + 1]));
           }
         }
+        // (TMA) the generic-proxy writes of the last stage become visible to the
+        // tensor memory accelerator that writes the tile back
+        if (tma && s == S - 1) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         group_sync(g);  // the tile is complete before the next stage gathers
       }
       if (failed) break;
+      if (tma) {
+        if (elect) {
+          int32_t c[5];
+          tma_coords(tile_base(t, tnt), tm, c);
+          tma_store_tile(smem_u32(cur), &tmap, c);
+        }
+        if (!loaded) tma_next();
+        continue;
+      }
       if (S == 0 && k > 0) {  // no stage windows: write back and load here
         store(other, t - G2);
         group_sync(g);
@@ -446,8 +554,20 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
       if (next && (S <= 1)) prefetch(other, t + G2, 0, 1);
       cp_async_commit();
     }
-    // the last tile's write-back
-    if (!failed && Kg > 0) store(buf0 + ((Kg - 1) & 1) * T, t0 + uint64_t(Kg - 1) * G2);
+    if (tma) {
+      // the write-backs are complete before the block leaves (and the loads, if a
+      // failure cut the loop short)
+      if (elect) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+      if (elect && nload > nwait) {
+        // a failure cut the loop short with a load in flight (at most one: a load is
+        // issued only after the previous one was waited for)
+        const volatile int never = 0;
+        mbar_wait_ab(tload, (nload - 1) & 1u, &never);
+      }
+    } else if (!failed && Kg > 0) {
+      // the last tile's write-back
+      store(buf0 + ((Kg - 1) & 1) * T, t0 + uint64_t(Kg - 1) * G2);
+    }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     if (failed) *abort_word = 1;
   }
@@ -484,8 +604,8 @@ static float tf32_rne_host(float v) {
 
 // The stages of one pass as 32 x 32 blocks and their B images; false if an op of a
 // stage depends on a bit outside the stage's slots (a control or a phase bit elsewhere).
-static bool tc_pass_blocks(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, std::vector<TcStage>& out,
-                           std::vector<float>& imgs) {
+static bool tc_pass_blocks(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, bool tma,
+                           std::vector<TcStage>& out, std::vector<float>& imgs) {
   int local_of[64];
   for (int b = 0; b < 64; ++b) local_of[b] = -1;
   for (int i = 0; i < kTtM; ++i) local_of[bp.B[i]] = i;
@@ -575,11 +695,98 @@ static bool tc_pass_blocks(const BuiltPass& bp, const std::vector<PlanOp>& pops,
           lo[off] = tf32_rne_host(v - h);
         }
       }
-    for (int k = 0; k < kTtSB; ++k) ts.swz[k] = tile_swz_host(1u << recs[si].slot_bit[k]) * 8u;
+    for (int k = 0; k < kTtSB; ++k)
+      ts.swz[k] = tma ? tma_swz_bytes(1u << recs[si].slot_bit[k]) : tile_swz_host(1u << recs[si].slot_bit[k]) * 8u;
     for (int k = 0; k < kTtM - kTtSB; ++k) ts.lane_bit[k] = recs[si].lane_bit[k];
+    if (tma) {
+      // With the 128-byte swizzle, local bit p moves an 8-byte access to bank slot bit
+      // (p = 0: 0; 1..3: p; 4..6: p - 3; 7 and up: none).  Rows are a warp's lanes, so
+      // the first four row bits take one bit of each of these classes where the
+      // stage's slots leave one (a half warp then reads 16 distinct slots).
+      int8_t order[kTtM - kTtSB];
+      bool used[kTtM - kTtSB] = {false};
+      int no = 0;
+      for (int cls = 0; cls < 4; ++cls)
+        for (int k = 0; k < kTtM - kTtSB; ++k) {
+          const int p = recs[si].lane_bit[k];
+          const int c = p == 0 ? 0 : p <= 3 ? p : p <= 6 ? p - 3 : -1;
+          if (!used[k] && c == cls) {
+            used[k] = true;
+            order[no++] = int8_t(p);
+            break;
+          }
+        }
+      for (int k = 0; k < kTtM - kTtSB; ++k)
+        if (!used[k]) order[no++] = recs[si].lane_bit[k];
+      for (int k = 0; k < kTtM - kTtSB; ++k) ts.lane_bit[k] = order[k];
+    }
     out.push_back(ts);
   }
   return true;
+}
+
+// The runs of a pass's tile for a box copy (at most 5 dimensions), or tma = 0.
+static TcTma tma_runs(const std::vector<int>& B, int n) {
+  TcTma tm{};
+  bool in[64] = {false};
+  for (int b : B) in[b] = true;
+  int nd = 0;
+  auto add = [&](int start, int len, bool tile) {
+    if (nd < 5) {
+      tm.start[nd] = int8_t(start);
+      tm.len[nd] = int8_t(len);
+      tm.tile[nd] = tile ? 1 : 0;
+    }
+    ++nd;
+  };
+  add(0, kTtL, true);
+  for (int b = kTtL; b < n;) {
+    const int start = b;
+    const bool t = in[b];
+    while (b < n && in[b] == t) ++b;
+    add(start, b - start, t);
+  }
+  if (nd > 5) return TcTma{};
+  for (int d = nd; d < 5; ++d) {  // padding dimensions of size 1 above the state
+    tm.start[d] = int8_t(n);
+    tm.len[d] = 0;
+    tm.tile[d] = 0;
+  }
+  tm.tma = 1;
+  return tm;
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    else
+      cudaGetLastError();
+  }
+  return fn;
+}
+
+// the tensor map of a pass's box over the state at `amps` (complex64, n qubits)
+static bool encode_tile_map(CUtensorMap* map, const TcTma& tm, void* amps, int n) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  cuuint64_t gdim[5], gstride[4];
+  cuuint32_t box[5], estr[5] = {1, 1, 1, 1, 1};
+  for (int d = 0; d < 5; ++d) {
+    gdim[d] = cuuint64_t(1) << tm.len[d];
+    box[d] = tm.tile[d] ? (cuuint32_t(1) << tm.len[d]) : 1u;
+    if (d > 0) gstride[d - 1] = (cuuint64_t(1) << tm.start[d]) * 8u;
+  }
+  (void)n;
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT64, 5, amps, gdim, gstride, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
 // The most recent tensor-core circuit plan of the process: the resolved ops it was built
@@ -593,6 +800,7 @@ struct TcPlanCache {
   bool valid = false;
   bool tc = false;  // false: an op depends on a bit outside its stage (CUDA-core passes)
   std::vector<TilePass> passes;
+  std::vector<TcTma> tmas;  // per pass: box copies or cp.async
   int nstages = 0;
   std::vector<char> host;  // staging of the upload (kept until the next rebuild)
   void* dev = nullptr;
@@ -625,17 +833,23 @@ static qc_status tc_plan(qc_state* s, const std::vector<ResolvedOp>& rops, int d
   to_plan_ops(rops, pops);
   const std::vector<BuiltPass> bps = build_passes(pops, n, kTtM, kTtL);
   std::vector<TilePass> passes;
+  std::vector<TcTma> tmas;
   std::vector<TcStage> stages;
   std::vector<float> imgs;
   bool tc = true;
   for (const BuiltPass& bp : bps) {
+    TcTma tm = tma_runs(bp.B, n);
+    if (tm.tma) {  // a trial encoding with this state's address
+      alignas(64) CUtensorMap probe;
+      if (!encode_tile_map(&probe, tm, s->amps, n)) tm = TcTma{};
+    }
     TilePass P{};
     P.m = kTtM;
     P.L = kTtL;
     for (int i = 0; i < kTtM; ++i) P.bits[i] = int8_t(bp.B[i]);
     P.ntiles = uint64_t(1) << (n - kTtM);
     P.stage0 = int(stages.size());
-    if (!tc_pass_blocks(bp, pops, n, stages, imgs)) {  // the CUDA-core passes take it
+    if (!tc_pass_blocks(bp, pops, n, tm.tma != 0, stages, imgs)) {  // the CUDA-core passes take it
       tc = false;
       break;
     }
@@ -645,6 +859,7 @@ static qc_status tc_plan(qc_state* s, const std::vector<ResolvedOp>& rops, int d
       break;
     }
     passes.push_back(P);
+    tmas.push_back(tm);
   }
   g_tc.device = dev;
   g_tc.n = n;
@@ -678,6 +893,7 @@ static qc_status tc_plan(qc_state* s, const std::vector<ResolvedOp>& rops, int d
     return st;
   }
   g_tc.passes = passes;
+  g_tc.tmas = tmas;
   g_tc.nstages = int(stages.size());
   g_tc.stage_bytes = sb;
   return QC_OK;
@@ -702,16 +918,29 @@ qc_status run_tiles_tc(qc_state* s, const std::vector<ResolvedOp>& rops, bool* h
   const TcStage* dst = static_cast<const TcStage*>(g_tc.dev);
   const float* dimg = reinterpret_cast<const float*>(static_cast<char*>(g_tc.dev) + g_tc.stage_bytes);
   if (qc_status st = check_cuda(cudaMemsetAsync(status, 0, sizeof(int), s->stream), "status reset")) return st;
-  auto kern = k_tile_pass_tc;
-  if (qc_status st = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kTtSmem)),
-                                "tensor-core tile pass shared memory"))
-    return st;
+  for (auto kern : {k_tile_pass_tc<false>, k_tile_pass_tc<true>})
+    if (qc_status st = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       int(kTtSmem)),
+                                  "tensor-core tile pass shared memory"))
+      return st;
   const uint64_t ntiles = uint64_t(1) << (n - kTtM);
   // one CTA per SM, two tiles in flight per CTA
   const unsigned grid = unsigned(std::min<uint64_t>((ntiles + 1) / 2, uint64_t(device_sm_count())));
   float* a = reinterpret_cast<float*>(s->amps);
-  for (const TilePass& P : g_tc.passes) {
-    QC_COUNT(), kern<<<grid, kTtThreads, kTtSmem, s->stream>>>(a, P, dst, dimg, status);
+  for (size_t i = 0; i < g_tc.passes.size(); ++i) {
+    alignas(64) CUtensorMap map;
+    memset(&map, 0, sizeof(map));
+    const TcTma& tm = g_tc.tmas[i];
+    if (tm.tma && !encode_tile_map(&map, tm, s->amps, n)) {
+      set_error("tensor-core tile pass: tensor map encoding failed");
+      return QC_ERR_CUDA;
+    }
+    if (tm.tma)
+      QC_COUNT(), k_tile_pass_tc<true><<<grid, kTtThreads, kTtSmem, s->stream>>>(a, g_tc.passes[i], dst, dimg, status,
+                                                                              map, tm);
+    else
+      QC_COUNT(), k_tile_pass_tc<false><<<grid, kTtThreads, kTtSmem, s->stream>>>(a, g_tc.passes[i], dst, dimg,
+                                                                               status, map, tm);
   }
   if (qc_status st = check_launch("tensor-core tile pass")) return st;
   if (qc_status st = check_cuda(cudaEventRecord(g_tc.done, s->stream), "plan event")) return st;
