@@ -494,10 +494,13 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
           }
           tmem_st32(ta + uint32_t(32 * q), hi);
           tmem_st32(ta + 64u + uint32_t(32 * q), lo);
-          // this half of the row is in TMEM: its K steps may start
+          // this half of the row is in TMEM: its K steps may start (one arrival per
+          // warp, counting its 32 rows)
           asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory");
           asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-          asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(full0 + 8u * (2 * g + q)) : "memory");
+          __syncwarp();
+          if (lane == 0)
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], 32;\n" ::"r"(full0 + 8u * (2 * g + q)) : "memory");
         }
         // work for the memory system while the products run
         if (tma) {
