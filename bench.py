@@ -301,7 +301,7 @@ def run_ours(args):
     out_host = torch.empty(SHOTS, dtype=torch.int64).pin_memory()
     zz = W.zz_terms(N_QUBITS, ring=False)
     mode = P.QC_RUN_FUSED if args.mode == "fused" else P.QC_RUN_PER_GATE
-    prec = P.QC_PREC_TF32X3 if args.prec == "tf32x3" else P.QC_PREC_NATIVE
+    prec = {"tf32x3": P.QC_PREC_TF32X3, "native": P.QC_PREC_NATIVE, "auto": P.QC_PREC_AUTO}[args.prec]
     st = P.State(N_QUBITS, "c64", stream)
     probs = torch.empty(1 << N_QUBITS, dtype=torch.float64, device="cuda")
 
@@ -712,7 +712,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--mode", default="fused", choices=["fused", "per_gate"])
-    ap.add_argument("--prec", default="native", choices=["native", "tf32x3"])
+    ap.add_argument("--prec", default="auto", choices=["auto", "native", "tf32x3"],
+                    help="fused passes: auto (the faster of the two for the circuit, timed once), CUDA-core "
+                         "(native) or tensor-core stages (tf32x3)")
     ap.add_argument("--plain-steps", type=int, default=1)
     ap.add_argument("--cpu-gates", type=int, default=16)
     ap.add_argument("--cpu-single-gates", type=int, default=2)

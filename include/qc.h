@@ -52,9 +52,16 @@ typedef enum { QC_C64 = 0, QC_C128 = 1 } qc_dtype;
 /* Arithmetic of fused k-qubit blocks (qc_apply_fused_k, qc_run_circuit). */
 typedef enum {
   QC_PREC_NATIVE = 0, /* FMA in the state's own precision on the CUDA cores        */
-  QC_PREC_TF32X3 = 1  /* complex64 only: tensor cores (tcgen05, kind::tf32), each
+  QC_PREC_TF32X3 = 1, /* complex64 only: tensor cores (tcgen05, kind::tf32), each
                          product split as a_hi*b_hi + a_hi*b_lo + a_lo*b_hi with
                          FP32 accumulation                                          */
+  QC_PREC_BF16X3 = 2, /* the same split in BF16 (8-bit significands): rejected with
+                         QC_ERR_UNSUPPORTED -- its products keep about 16 bits, too
+                         few for 1e-5 relative L2 over a circuit's stages            */
+  QC_PREC_AUTO = 3    /* qc_run_circuit, QC_RUN_FUSED: the faster of QC_PREC_NATIVE's
+                         CUDA-core tile passes and QC_PREC_TF32X3's tensor-core stage
+                         passes for the circuit's structure (complex64, n >= 12;
+                         otherwise QC_PREC_NATIVE), chosen by timing both once      */
 } qc_prec;
 
 typedef struct qc_state qc_state; /* opaque */
@@ -310,8 +317,14 @@ typedef enum {
  * the ops on 5 of the tile's bits, controls and phase bits included -- as one 32 x 32
  * block on the tensor cores (host FP64 product of the stage's gates; TF32 split with
  * round-to-nearest, eight FP32 partial accumulators per output added on the CUDA cores;
- * synchronising: a bounded-wait timeout returns QC_ERR_TIMEOUT).  A circuit with an op
- * whose control or phase bit lies outside its stage runs on the CUDA-core passes. */
+ * synchronising: a bounded-wait timeout returns QC_ERR_TIMEOUT, after which the state's
+ * amplitudes are undefined).  A circuit with an op whose control or phase bit lies
+ * outside its stage runs on the CUDA-core passes.  With QC_PREC_AUTO the first run of a
+ * circuit structure (gate kinds, qubits and controls; not the angles or matrices) on a
+ * device times both kinds of pass on a scratch state of the same size (allocated and
+ * freed by the call; if that allocation fails, the tensor-core passes are taken) and
+ * keeps the faster for later runs; with the environment variable QC_AUTOTUNE_CACHE
+ * naming a file, choices are appended to it and read back by later processes. */
 qc_status qc_run_circuit(qc_state* s, const qc_circuit* c, const double* params, qc_run_mode mode,
                          qc_prec prec);
 

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libqcgb.so")
 
 QC_C64, QC_C128 = 0, 1
-QC_PREC_NATIVE, QC_PREC_TF32X3 = 0, 1
+QC_PREC_NATIVE, QC_PREC_TF32X3, QC_PREC_BF16X3, QC_PREC_AUTO = 0, 1, 2, 3
 QC_RUN_PER_GATE, QC_RUN_FUSED = 0, 1
 STATUS = {0: "QC_OK", 1: "QC_ERR_INVALID_ARG", 2: "QC_ERR_OOM", 3: "QC_ERR_CUDA", 4: "QC_ERR_UNSUPPORTED",
           5: "QC_ERR_ZERO_PROB", 6: "QC_ERR_TIMEOUT"}

@@ -298,6 +298,11 @@ qc_status qc_apply_fused_k(qc_state* s, const int* qubits, int k, const double* 
       }
     bits[j] = s->n - 1 - qubits[j];
   }
+  if (prec == QC_PREC_BF16X3) {
+    set_error("qc_apply_fused_k: BF16x3 products keep about 16 significant bits, too few for 1e-5");
+    return QC_ERR_UNSUPPORTED;
+  }
+  if (prec == QC_PREC_AUTO) prec = QC_PREC_NATIVE;  // one block: nothing to choose between passes
   if (prec != QC_PREC_NATIVE && prec != QC_PREC_TF32X3) {
     set_error("qc_apply_fused_k: unknown precision mode %d", int(prec));
     return QC_ERR_INVALID_ARG;
@@ -313,6 +318,14 @@ qc_status qc_run_circuit(qc_state* s, const qc_circuit* c, const double* params,
   clear_error();
   if (!s || !s->amps || !c || (c->nops > 0 && !c->ops) || c->n != s->n) {
     set_error("qc_run_circuit: invalid arguments (circuit n must equal state n)");
+    return QC_ERR_INVALID_ARG;
+  }
+  if (prec == QC_PREC_BF16X3) {
+    set_error("qc_run_circuit: BF16x3 products keep about 16 significant bits, too few for 1e-5");
+    return QC_ERR_UNSUPPORTED;
+  }
+  if (prec != QC_PREC_NATIVE && prec != QC_PREC_TF32X3 && prec != QC_PREC_AUTO) {
+    set_error("qc_run_circuit: unknown precision mode %d", int(prec));
     return QC_ERR_INVALID_ARG;
   }
   if (mode == QC_RUN_PER_GATE) return run_per_gate(s, c, params);

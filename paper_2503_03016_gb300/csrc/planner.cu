@@ -25,6 +25,10 @@
 #include <cmath>
 #include <complex>
 #include <mutex>
+#include <map>
+#include <string>
+#include <cstdio>
+#include <cstdlib>
 #include <vector>
 
 #include "circuit.cuh"
@@ -1054,10 +1058,121 @@ void drop_global_phases(std::vector<PlanOp>& pops) {
     if (p.phase && p.cmask == 0) p.c = 0.0;
 }
 
+// QC_PREC_AUTO: the choice between the CUDA-core tile passes (0) and the tensor-core
+// stage passes (2) per (device name, n, circuit structure), made by timing both once on
+// a scratch state; optionally appended to / read from the file QC_AUTOTUNE_CACHE.
+static std::mutex g_auto_mu;
+static std::map<std::string, int> g_auto_choice;
+
+static std::string auto_key(const qc_state* s, const std::vector<ResolvedOp>& rops) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](uint64_t v) { h = (h ^ v) * 1099511628211ull; };
+  for (const ResolvedOp& r : rops) {
+    mix(uint64_t(r.form));
+    mix(uint64_t(r.nq));
+    for (int k = 0; k < r.nq; ++k) mix(uint64_t(r.bits[k]));
+    mix(uint64_t(r.cstate));
+  }
+  cudaDeviceProp prop;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaGetDeviceProperties(&prop, dev);
+  std::string key = std::string("fused|") + prop.name + "|" + std::to_string(s->n) + "|" + std::to_string(rops.size()) +
+                    "|" + std::to_string(h);
+  for (char& ch : key)
+    if (ch == ' ') ch = '_';
+  return key;
+}
+
+static qc_status time_path(qc_state* t, const std::vector<ResolvedOp>& rops, int path, float* ms) {
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  qc_status st = QC_OK;
+  for (int rep = 0; rep < 2 && st == QC_OK; ++rep) {  // the first run plans and uploads
+    cudaEventRecord(e0, t->stream);
+    if (path == 2) {
+      bool handled = false;
+      st = run_tiles_tc(t, rops, &handled);
+      if (st == QC_OK && !handled) *ms = 1e30f;
+    } else {
+      st = run_tiles<float>(t, rops, tile_bits_for(t), false);
+    }
+    cudaEventRecord(e1, t->stream);
+    cudaEventSynchronize(e1);
+    if (st == QC_OK && !(path == 2 && *ms >= 1e30f)) cudaEventElapsedTime(ms, e0, e1);
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
+}
+
+static qc_status auto_choice(qc_state* s, const std::vector<ResolvedOp>& rops, int* choice) {
+  const std::string key = auto_key(s, rops);
+  std::lock_guard<std::mutex> lock(g_auto_mu);
+  auto it = g_auto_choice.find(key);
+  if (it != g_auto_choice.end()) {
+    *choice = it->second;
+    return QC_OK;
+  }
+  const char* path = getenv("QC_AUTOTUNE_CACHE");
+  if (path) {
+    if (FILE* f = fopen(path, "r")) {
+      char k[512];
+      int v;
+      while (fscanf(f, "%511s %d", k, &v) == 2)
+        if (key == k && (v == 0 || v == 2)) {
+          fclose(f);
+          g_auto_choice[key] = v;
+          *choice = v;
+          return QC_OK;
+        }
+      fclose(f);
+    }
+  }
+  // a scratch state of the same size (timing does not depend on the amplitudes)
+  qc_state t = *s;
+  t.amps = nullptr;
+  t.owned = false;
+  t.scratch = nullptr;
+  t.scratch_bytes = 0;
+  t.host_buf = nullptr;
+  if (cudaMalloc(&t.amps, state_len(s) * amp_bytes(s->dtype)) != cudaSuccess) {
+    cudaGetLastError();
+    *choice = 2;  // no room to time: the tensor-core passes
+    return QC_OK;
+  }
+  qc_status st = qc_state_init_basis(&t, 0);
+  float ms_cuda = 1e30f, ms_tc = 1e30f;
+  if (st == QC_OK) st = time_path(&t, rops, 0, &ms_cuda);
+  if (st == QC_OK) st = time_path(&t, rops, 2, &ms_tc);
+  cudaStreamSynchronize(t.stream);
+  cudaFree(t.amps);
+  if (t.scratch) cudaFree(t.scratch);
+  if (st != QC_OK) return st;
+  *choice = ms_tc < ms_cuda ? 2 : 0;
+  g_auto_choice[key] = *choice;
+  if (path) {
+    if (FILE* f = fopen(path, "a")) {
+      fprintf(f, "%s %d\n", key.c_str(), *choice);
+      fclose(f);
+    }
+  }
+  return QC_OK;
+}
+
 qc_status run_fused(qc_state* s, const qc_circuit* c, const double* params, qc_prec prec, bool drop_global_phase) {
   std::vector<ResolvedOp> rops(c->nops);
   for (int i = 0; i < c->nops; ++i)
     if (qc_status st = resolve_op(c, c->ops[i], params, &rops[i])) return st;
+  if (prec == QC_PREC_AUTO) {
+    prec = QC_PREC_NATIVE;
+    if (s->dtype == QC_C64 && s->n >= 12 && !drop_global_phase) {
+      int choice = 0;
+      if (qc_status st = auto_choice(s, rops, &choice)) return st;
+      if (choice == 2) prec = QC_PREC_TF32X3;
+    }
+  }
   if (prec == QC_PREC_TF32X3 && s->dtype == QC_C64) {
     bool handled = false;
     if (qc_status st = run_tiles_tc(s, rops, &handled)) return st;

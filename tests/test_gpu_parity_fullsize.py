@@ -82,7 +82,13 @@ def test_brickwork_vs_oracle(n, variant):
     got, path = _run_gpu(n, dtype, mode, prec)
     want = _oracle_brickwork(n)
     err = rel_l2(got, want)
-    record("brickwork_vs_oracle", n=n, variant=variant, rel_l2=err, path=path)
+    # the error split into its radial part (the norm) and the rest
+    g = got.astype(np.complex128)
+    nrm = float(np.linalg.norm(g))
+    along = complex(np.vdot(want, g)) / float(np.vdot(want, want).real)
+    perp = float(np.linalg.norm(g - along * want) / np.linalg.norm(want))
+    record("brickwork_vs_oracle", n=n, variant=variant, rel_l2=err, path=path, norm_minus_1=nrm - 1.0,
+           err_orthogonal=perp, err_along=abs(along - 1.0))
     if variant == "fused_native":
         assert path == 1
     if variant == "fused_tf32x3":

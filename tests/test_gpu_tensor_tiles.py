@@ -129,3 +129,36 @@ def test_tc_brickwork_28_inverse_property():
     P.qc_run_circuit(a.handle, inv, None, P.QC_RUN_FUSED, P.QC_PREC_TF32X3)
     amp0 = a.tensor[0].item()
     assert abs(amp0 - 1) < 2e-5, amp0
+
+
+def test_auto_precision_picks_and_caches_a_path(tmp_path, monkeypatch):
+    """QC_PREC_AUTO times both kinds of fused pass once per circuit structure, keeps the
+    faster (recorded in QC_AUTOTUNE_CACHE), and either way matches the oracle; a second
+    run of the same structure with other matrices takes the same path without timing."""
+    import paper_2503_03016_gb300 as P
+    n = 16
+    cache = tmp_path / "autotune.txt"
+    monkeypatch.setenv("QC_AUTOTUNE_CACHE", str(cache))
+    ops = W.brickwork(n, 10, 77)
+    psi = W.random_state(n, 4)
+    st = gpu_state(psi, "c64")
+    st.run(ops, mode=P.QC_RUN_FUSED, prec=P.QC_PREC_AUTO)
+    path = P.qc_last_fused_path()
+    assert path in (1, 2)
+    assert rel_l2(st.numpy(), oracle.run(psi.copy(), ops)) <= TOL["c64"]
+    lines = cache.read_text().split("\n")
+    assert any(l.endswith(" 0") or l.endswith(" 2") for l in lines)
+    ops2 = W.brickwork(n, 10, 78)  # same structure, other unitaries
+    st2 = gpu_state(psi, "c64")
+    st2.run(ops2, mode=P.QC_RUN_FUSED, prec=P.QC_PREC_AUTO)
+    assert P.qc_last_fused_path() == path
+    assert len(cache.read_text().strip().split("\n")) == len([l for l in lines if l.strip()])
+    assert rel_l2(st2.numpy(), oracle.run(psi.copy(), ops2)) <= TOL["c64"]
+
+
+def test_bf16x3_is_rejected():
+    import paper_2503_03016_gb300 as P
+    st = gpu_state(W.random_state(12, 1), "c64")
+    with pytest.raises(P.QCError) as e:
+        st.run(W.brickwork(12, 2, 1), mode=P.QC_RUN_FUSED, prec=P.QC_PREC_BF16X3)
+    assert e.value.status == 4
