@@ -1089,19 +1089,19 @@ static qc_status time_path(qc_state* t, const std::vector<ResolvedOp>& rops, int
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   qc_status st = QC_OK;
-  for (int rep = 0; rep < 2 && st == QC_OK; ++rep) {  // the first run plans and uploads
+  bool ran = true;
+  for (int rep = 0; rep < 2 && st == QC_OK && ran; ++rep) {  // the first run plans and uploads
     cudaEventRecord(e0, t->stream);
     if (path == 2) {
-      bool handled = false;
-      st = run_tiles_tc(t, rops, &handled);
-      if (st == QC_OK && !handled) *ms = 1e30f;
+      st = run_tiles_tc(t, rops, &ran);  // ran = false: the circuit does not fit the stages
     } else {
       st = run_tiles<float>(t, rops, tile_bits_for(t), false);
     }
     cudaEventRecord(e1, t->stream);
     cudaEventSynchronize(e1);
-    if (st == QC_OK && !(path == 2 && *ms >= 1e30f)) cudaEventElapsedTime(ms, e0, e1);
+    if (st == QC_OK && ran) cudaEventElapsedTime(ms, e0, e1);
   }
+  if (!ran) *ms = 1e30f;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   return st;

@@ -109,6 +109,23 @@ struct TcTma {
   int8_t pad;
 };
 
+// Norm restoration across the passes of a circuit.  The tensor cores truncate their
+// FP32 accumulator toward zero, so every stage shrinks the amplitudes slightly (a
+// 28-qubit brickwork: about 9e-6 of norm in all, nearly all of its error), while a
+// unitary circuit keeps the norm exactly.  The first pass sums the norm of its input,
+// every pass the norm of its output (per block, in a fixed order, into norms[]), and a
+// later pass multiplies each amplitude it loads by sqrt(input norm / previous output
+// norm), formed in FP64 from those sums.
+struct TcNorm {
+  int32_t first;        // this pass sums the circuit's input norm
+  int32_t apply;        // this pass scales its input (a previous pass wrote out_prev)
+  int32_t nblocks;      // blocks of the previous pass (partials in in_part / out_prev)
+  int32_t pad;
+  double* in_part;      // [nblocks] input norm per block (written by the first pass)
+  double* out_prev;     // [nblocks] output norm per block of the previous pass
+  double* out_cur;      // [gridDim.x] output norm per block of this pass
+};
+
 // byte offset of local index u in a tile with the 128-byte swizzle (XOR-linear in u)
 __host__ __device__ __forceinline__ uint32_t tma_swz_bytes(uint32_t u) {
   return ((u >> 4) << 7) | ((((u >> 1) ^ (u >> 4)) & 7u) << 4) | ((u & 1u) << 3);
@@ -231,7 +248,7 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
                                                                  const float* __restrict__ imgs,
                                                                  int* __restrict__ status,
                                                                  const __grid_constant__ CUtensorMap tmap,
-                                                                 const TcTma tm) {
+                                                                 const TcTma tm, const TcNorm nrm) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -249,6 +266,8 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 13);
   volatile int* abort_word = reinterpret_cast<volatile int*>(tmem_slot + 1);
   __shared__ int8_t sbits[16];
+  __shared__ float s_fac;                                 // this pass's input scale
+  __shared__ double s_norm[2][kTtGroups * kTtGroupThreads];  // per-thread norm sums
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int m = kTtM, L = kTtL;
   constexpr uint32_t T = 1u << m;
@@ -262,6 +281,16 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bars + b)), "r"(cnt) : "memory");
     }
     *abort_word = 0;
+    double f = 1.0;
+    if (nrm.apply) {  // fixed-order FP64 sums of the previous partials
+      double a = 0.0, b = 0.0;
+      for (int i = 0; i < nrm.nblocks; ++i) {
+        a += nrm.in_part[i];
+        b += nrm.out_prev[i];
+      }
+      if (a > 0.0 && b > 0.0) f = sqrt(a / b);
+    }
+    s_fac = float(f);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -414,6 +443,8 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
     const bool elect = row == 0;
     const uint32_t tload = tload0 + 8u * g;
     uint32_t nload = 0, nwait = 0;  // (TMA) tile loads issued (elected thread) / waited for
+    const float fac = s_fac;
+    double nin = 0.0, nout = 0.0;   // this thread's norm sums (input of a first pass, output)
     if (Kg > 0) {
       if (!tma) {
         prefetch(buf0, t0, 0, 1);
@@ -479,13 +510,19 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
         for (int i = 1; i < 32; ++i) off[i] = off[i - 1] ^ sw[(i & 1) ? 0 : (i & 2) ? 1 : (i & 4) ? 2 : (i & 8) ? 3 : 4];
         // this row's 32 amplitudes -> TF32 hi / lo in TMEM (A_hi columns 0..63, A_lo
         // columns 64..127, column 2c + ri); chunk q holds c in [16q, 16q + 16)
+        float sin_ = 0.0f;
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           uint32_t hi[32], lo[32];
 #pragma unroll
           for (int i = 16 * q; i < 16 * q + 16; ++i) {
             const int c = (i ^ (i >> 1)) - 16 * q;
-            const float2 v = *reinterpret_cast<const float2*>(curb + off[i]);
+            float2 v = *reinterpret_cast<const float2*>(curb + off[i]);
+            if (s == 0) {  // the tile as loaded: its norm (first pass), the pass's scale
+              sin_ = fmaf(v.x, v.x, fmaf(v.y, v.y, sin_));
+              v.x *= fac;
+              v.y *= fac;
+            }
             const float hr = tf32_rna(v.x), hm = tf32_rna(v.y);
             hi[2 * c] = __float_as_uint(hr);
             hi[2 * c + 1] = __float_as_uint(hm);
@@ -502,6 +539,7 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
           if (lane == 0)
             asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], 32;\n" ::"r"(full0 + 8u * (2 * g + q)) : "memory");
         }
+        if (s == 0) nin += double(sin_);
         // work for the memory system while the products run
         if (tma) {
           if (s == 0) tma_next();
@@ -521,6 +559,7 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
         off[0] = off0;
 #pragma unroll
         for (int i = 1; i < 32; ++i) off[i] = off[i - 1] ^ sw[(i & 1) ? 0 : (i & 2) ? 1 : (i & 4) ? 2 : (i & 8) ? 3 : 4];
+        float sout = 0.0f;
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
           uint32_t d0[32], d1[32];
@@ -530,11 +569,13 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
 #pragma unroll
           for (int i = 16 * q; i < 16 * q + 16; ++i) {
             const int c = (i ^ (i >> 1)) - 16 * q;
-            *reinterpret_cast<float2*>(curb + off[i]) =
-                make_float2(__uint_as_float(d0[2 * c]) + __uint_as_float(d1[2 * c]),
-                            __uint_as_float(d0[2 * c + 1]) + __uint_as_float(d1[2 * c + 1]));
+            const float2 y = make_float2(__uint_as_float(d0[2 * c]) + __uint_as_float(d1[2 * c]),
+                                         __uint_as_float(d0[2 * c + 1]) + __uint_as_float(d1[2 * c + 1]));
+            sout = fmaf(y.x, y.x, fmaf(y.y, y.y, sout));
+            *reinterpret_cast<float2*>(curb + off[i]) = y;
           }
         }
+        if (s == S - 1) nout += double(sout);
         // (TMA) the generic-proxy writes of the last stage become visible to the
         // tensor memory accelerator that writes the tile back
         if (tma && s == S - 1) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -573,11 +614,23 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
     }
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
     if (failed) *abort_word = 1;
+    s_norm[0][tid] = nin;
+    s_norm[1][tid] = nout;
   }
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
   if (tid == 0 && *abort_word) atomicExch(status, 1);
+  // this block's norm sums, added in thread order (the same on every run)
+  if (tid == 0) {
+    double a = 0.0, b = 0.0;
+    for (int i = 0; i < kTtGroups * kTtGroupThreads; ++i) {
+      a += s_norm[0][i];
+      b += s_norm[1][i];
+    }
+    if (nrm.first) nrm.in_part[blockIdx.x] = a;
+    nrm.out_cur[blockIdx.x] = b;
+  }
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols) : "memory");
 }
@@ -915,9 +968,16 @@ qc_status run_tiles_tc(qc_state* s, const std::vector<ResolvedOp>& rops, bool* h
   if (!(g_tc.valid && g_tc.device == dev && g_tc.n == n && same_ops(g_tc.rops, rops)))
     if (qc_status st = tc_plan(s, rops, dev)) return st;
   if (!g_tc.tc) return QC_OK;
+  const uint64_t ntiles0 = uint64_t(1) << (n - kTtM);
+  const unsigned grid0 = unsigned(std::min<uint64_t>((ntiles0 + 1) / 2, uint64_t(device_sm_count())));
   void* scr = nullptr;
-  if (qc_status st = state_scratch(s, 256, &scr)) return st;
+  if (qc_status st = state_scratch(s, 256 + 3 * sizeof(double) * grid0, &scr)) return st;
   int* status = static_cast<int*>(scr);
+  double* norm_in = reinterpret_cast<double*>(static_cast<char*>(scr) + 256);
+  double* norm_out[2] = {norm_in + grid0, norm_in + 2 * grid0};
+  // norm restoration needs every pass to have a stage (stage 0 scales, the last sums)
+  bool restore = true;
+  for (const TilePass& P : g_tc.passes) restore &= P.nstages > 0;
   const TcStage* dst = static_cast<const TcStage*>(g_tc.dev);
   const float* dimg = reinterpret_cast<const float*>(static_cast<char*>(g_tc.dev) + g_tc.stage_bytes);
   if (qc_status st = check_cuda(cudaMemsetAsync(status, 0, sizeof(int), s->stream), "status reset")) return st;
@@ -938,12 +998,19 @@ qc_status run_tiles_tc(qc_state* s, const std::vector<ResolvedOp>& rops, bool* h
       set_error("tensor-core tile pass: tensor map encoding failed");
       return QC_ERR_CUDA;
     }
+    TcNorm nm{};
+    nm.first = i == 0 ? 1 : 0;
+    nm.apply = restore && i > 0 ? 1 : 0;
+    nm.nblocks = int(grid);
+    nm.in_part = norm_in;
+    nm.out_prev = norm_out[(i + 1) & 1];
+    nm.out_cur = norm_out[i & 1];
     if (tm.tma)
       QC_COUNT(), k_tile_pass_tc<true><<<grid, kTtThreads, kTtSmem, s->stream>>>(a, g_tc.passes[i], dst, dimg, status,
-                                                                              map, tm);
+                                                                              map, tm, nm);
     else
       QC_COUNT(), k_tile_pass_tc<false><<<grid, kTtThreads, kTtSmem, s->stream>>>(a, g_tc.passes[i], dst, dimg,
-                                                                               status, map, tm);
+                                                                               status, map, tm, nm);
   }
   if (qc_status st = check_launch("tensor-core tile pass")) return st;
   if (qc_status st = check_cuda(cudaEventRecord(g_tc.done, s->stream), "plan event")) return st;
