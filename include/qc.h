@@ -70,6 +70,13 @@ typedef struct qc_state qc_state; /* opaque */
 const char* qc_last_error(void);
 /* ABI version (incremented on incompatible changes). */
 int qc_abi_version(void);
+/* The status the tensor-core entry points (QC_PREC_TF32X3 blocks and passes) return for
+ * the status word their kernels write: 0 -> QC_OK; 1 (a bounded wait for a copy or for
+ * the products ran out: the kernel set the word, waited (bounded) for its copies and
+ * products in flight, released its tensor memory and returned early) -> QC_ERR_TIMEOUT,
+ * after which the state's amplitudes are undefined; anything else -> QC_ERR_CUDA.  Host
+ * only; the message is set as by those entry points. */
+qc_status qc_status_of_device_word(int word);
 /* Number of CUDA kernels this library has launched in this process (all threads);
  * a diagnostic for benchmarks. */
 uint64_t qc_launch_count(void);

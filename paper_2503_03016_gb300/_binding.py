@@ -72,6 +72,7 @@ _SIGS = {
     "qc_last_error": (ctypes.c_char_p, []),
     "qc_abi_version": (ctypes.c_int, []),
     "qc_launch_count": (ctypes.c_uint64, []),
+    "qc_status_of_device_word": (ctypes.c_int, [ctypes.c_int]),
     "qc_last_pass_count": (ctypes.c_int, []),
     "qc_last_fused_path": (ctypes.c_int, []),
     "qc_last_stage_count": (ctypes.c_int, []),

@@ -46,6 +46,9 @@ void count_launch();
 // Per-state scratch of at least `bytes`, aligned to 256 bytes.
 qc_status state_scratch(qc_state* s, size_t bytes, void** out);
 int device_sm_count();
+// The status of a tensor-core kernel's device status word (0: completed; 1: a bounded
+// wait ran out, the state's amplitudes are undefined), with the message set.
+qc_status device_status(int word, const char* what);
 
 inline uint64_t state_len(const qc_state* s) { return uint64_t(1) << s->n; }
 inline size_t amp_bytes(qc_dtype d) { return d == QC_C64 ? 8 : 16; }

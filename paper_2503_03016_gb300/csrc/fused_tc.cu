@@ -411,11 +411,7 @@ static qc_status apply_k6_tf32x3(qc_state* s, const int* bits, const double* U) 
   if (qc_status st = check_cuda(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s->stream), "status"))
     return st;
   if (qc_status st = check_cuda(cudaStreamSynchronize(s->stream), "tensor-core six-qubit block")) return st;
-  if (h != 0) {
-    set_error("tensor-core block: a bounded wait for the MMA completion ran out");
-    return QC_ERR_TIMEOUT;
-  }
-  return QC_OK;
+  return device_status(h, "tensor-core block");
 }
 
 qc_status apply_kq_tf32x3(qc_state* s, const int* bits, int k, const double* U) {
@@ -485,11 +481,7 @@ qc_status apply_kq_tf32x3(qc_state* s, const int* bits, int k, const double* U) 
   if (qc_status st = check_cuda(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s->stream), "status"))
     return st;
   if (qc_status st = check_cuda(cudaStreamSynchronize(s->stream), "tensor-core block")) return st;
-  if (h != 0) {
-    set_error("tensor-core block: a bounded wait for the MMA completion ran out");
-    return QC_ERR_TIMEOUT;
-  }
-  return QC_OK;
+  return device_status(h, "tensor-core block");
 }
 
 }  // namespace qcgb

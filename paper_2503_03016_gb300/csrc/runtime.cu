@@ -60,6 +60,16 @@ int device_sm_count() {
   return cached[dev];
 }
 
+qc_status device_status(int word, const char* what) {
+  if (word == 0) return QC_OK;
+  if (word == 1) {
+    set_error("%s: a bounded wait for a copy or the products ran out; the state's amplitudes are undefined", what);
+    return QC_ERR_TIMEOUT;
+  }
+  set_error("%s: unexpected device status word %d; the state's amplitudes are undefined", what, word);
+  return QC_ERR_CUDA;
+}
+
 qc_status state_scratch(qc_state* s, size_t bytes, void** out) {
   bytes = (bytes + 255) & ~size_t(255);
   if (s->scratch_bytes < bytes) {
@@ -515,6 +525,11 @@ extern "C" {
 
 const char* qc_last_error(void) { return g_err; }
 int qc_abi_version(void) { return 2; }
+
+qc_status qc_status_of_device_word(int word) {
+  clear_error();
+  return device_status(word, "tensor-core kernel");
+}
 uint64_t qc_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
 
 static qc_status valid_state(const qc_state* s) {

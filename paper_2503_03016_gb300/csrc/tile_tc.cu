@@ -1020,10 +1020,7 @@ qc_status run_tiles_tc(qc_state* s, const std::vector<ResolvedOp>& rops, bool* h
                                 "status"))
     return st;
   if (qc_status st = check_cuda(cudaStreamSynchronize(s->stream), "tensor-core tile pass")) return st;
-  if (h != 0) {
-    set_error("tensor-core tile pass: a bounded wait for a copy or the products ran out (the state is undefined)");
-    return QC_ERR_TIMEOUT;
-  }
+  if (qc_status st = device_status(h, "tensor-core tile pass")) return st;
   g_last_pass_count = int(g_tc.passes.size());
   g_last_fused_path = 2;
   g_last_stage_count = g_tc.nstages;

@@ -52,3 +52,18 @@ def test_product_does_not_import_oracle():
             src = open(path).read()
             assert not re.search(r"^\s*(import|from)\s+oracle\b", src, flags=re.M), path
             assert "qc_oracle" not in src and "libqcoracle" not in src, path
+
+
+def test_device_status_word_mapping():
+    """The status the tensor-core entry points return for their kernels' status word
+    (host only, no kernel: a timed-out wait is never provoked on a GPU)."""
+    import ctypes
+
+    import paper_2503_03016_gb300 as P
+    L = P.lib()
+    assert L.qc_status_of_device_word(0) == 0
+    assert L.qc_status_of_device_word(1) == 6  # QC_ERR_TIMEOUT
+    msg = L.qc_last_error().decode()
+    assert "undefined" in msg and "bounded wait" in msg
+    assert L.qc_status_of_device_word(7) == 3  # QC_ERR_CUDA
+    assert "7" in L.qc_last_error().decode()
