@@ -486,6 +486,50 @@ def run_batch_bench(args):
                                  subset}}))
 
 
+def run_batch_general_bench(args):
+    """Opt-in secondary measurement: the general batch entry point on a mixed family of
+    1024 circuits (QFTs, depth-8 Haar brickworks, 4-layer RY.RZ ansatz with a CZ ring;
+    n uniform in 10..16, seed 9), each with its own sum_i Z_i Z_i+1 + sum_i X_i
+    observable, in one launch per step (complex64)."""
+    import torch
+
+    import paper_2503_03016_gb300 as P
+    torch.cuda.set_device(0)
+    rng = np.random.default_rng(9)
+    circs, hams, offs, flat = [], [], [], []
+    nps = 0
+    for i in range(1024):
+        n = int(rng.integers(10, 17))
+        kind = i % 3
+        if kind == 0:
+            ops, p = W.qft(n), None
+        elif kind == 1:
+            ops, p = W.brickwork(n, 8, 1000 + i), None
+        else:
+            ops, p = W.ansatz(n, 4, ring=True), W.ansatz_params(n, 4, 2000 + i)
+        circs.append(P.Circuit(n, ops))
+        hams.append(P.Hamiltonian.from_strings(W.zz_terms(n, True) + W.x_terms(n)))
+        offs.append(nps)
+        if p is not None:
+            flat.append(p)
+            nps += p.size
+    dparams = torch.tensor(np.concatenate(flat), dtype=torch.float64, device="cuda")
+    out = torch.empty(len(circs), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+    for _ in range(max(args.warmup, 1)):
+        P.qc_run_batch(circs, hams, dparams, offs, None, out)
+    torch.cuda.synchronize()
+    t = StreamTimer(stream)
+    t.start()
+    for _ in range(args.steps):
+        P.qc_run_batch(circs, hams, dparams, offs, None, out)
+    ms = t.stop() / args.steps
+    print(json.dumps({"metric": "general batch circuits/s", "value": len(circs) / (ms * 1e-3), "unit": "circuits/s",
+                      "ms_per_step": ms, "steps": args.steps, "path": P.qc_last_batch_path(),
+                      "config": {"workload": "1024 circuits (QFT, brickwork depth 8, ansatz 4 layers), n in 10..16, "
+                                             "observable ring ZZ + sum X, one launch (tables uploaded per call)"}}))
+
+
 def run_block_bench(args):
     """Opt-in secondary measurement: one dense 5-qubit block (Haar 32x32) and one dense
     6-qubit block (Haar 64x64) on a 28-qubit complex64 state, CUDA-core FMA (k_kq_native)
@@ -724,13 +768,15 @@ def main():
     ap.add_argument("--qubits", type=int, default=None,
                     help="register size (default: 28 brickwork and block, 32 QFT); smaller for profiling")
     ap.add_argument("--workload", default="brickwork",
-                    choices=["brickwork", "batch", "block", "qft", "adjoint", "sweeps", "window"],
+                    choices=["brickwork", "batch", "batch_general", "block", "qft", "adjoint", "sweeps", "window"],
                     help="batch: opt-in secondary measurement of the batched launch")
     args = ap.parse_args()
     global N_QUBITS
     N_QUBITS = args.qubits or 28
     if args.workload == "batch" and args.impl == "ours":
         run_batch_bench(args)
+    elif args.workload == "batch_general" and args.impl == "ours":
+        run_batch_general_bench(args)
     elif args.workload == "block" and args.impl == "ours":
         run_block_bench(args)
     elif args.workload == "qft" and args.impl == "ours":
