@@ -190,6 +190,15 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32
       : "memory");
 }
 
+__device__ __forceinline__ float2 lds2(uint32_t addr) {
+  float2 v;
+  asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];\n" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+  return v;
+}
+__device__ __forceinline__ void sts2(uint32_t addr, float2 v) {
+  asm volatile("st.shared.v2.f32 [%0], {%1, %2};\n" ::"r"(addr), "f"(v.x), "f"(v.y) : "memory");
+}
+
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t (&r)[16]) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};\n" ::"r"(
@@ -463,7 +472,7 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
     for (uint32_t k = 0; k < Kg && !failed; ++k) {
       Cplx<float>* cur = buf0 + (k & 1) * T;
       Cplx<float>* other = buf0 + ((k + 1) & 1) * T;
-      unsigned char* curb = reinterpret_cast<unsigned char*>(cur);
+      const uint32_t curs = smem_u32(cur);  // shared-window address of the tile
       const uint64_t t = t0 + k * G2;
       const bool next = k + 1 < Kg;
       const int nparts = S >= 3 ? 2 : 1;  // load windows: stages 1 .. nparts
@@ -517,7 +526,7 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
 #pragma unroll
           for (int i = 16 * q; i < 16 * q + 16; ++i) {
             const int c = (i ^ (i >> 1)) - 16 * q;
-            float2 v = *reinterpret_cast<const float2*>(curb + off[i]);
+            float2 v = lds2(curs + off[i]);
             if (s == 0) {  // the tile as loaded: its norm (first pass), the pass's scale
               sin_ = fmaf(v.x, v.x, fmaf(v.y, v.y, sin_));
               v.x *= fac;
@@ -572,7 +581,7 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
             const float2 y = make_float2(__uint_as_float(d0[2 * c]) + __uint_as_float(d1[2 * c]),
                                          __uint_as_float(d0[2 * c + 1]) + __uint_as_float(d1[2 * c + 1]));
             sout = fmaf(y.x, y.x, fmaf(y.y, y.y, sout));
-            *reinterpret_cast<float2*>(curb + off[i]) = y;
+            sts2(curs + off[i], y);
           }
         }
         if (s == S - 1) nout += double(sout);
