@@ -50,4 +50,19 @@ qc_status apply_1q_bits(qc_state* s, int tbit, const int* cbits, const int* cval
 qc_status apply_2q_bits(qc_state* s, int pa, int pb, const double* U);
 qc_status apply_kq_bits(qc_state* s, const int* bits, int k, const double* U, qc_prec prec);
 
+// Complex128 states of at least 2^kDfMinQubits amplitudes run their arithmetic gate
+// sweeps in double-float arithmetic (sweeps_df.cu: FP32 pairs, 48-bit significands,
+// no FP64 instruction); smaller ones, where the sweep is launch-bound, keep FP64.
+constexpr int kDfMinQubits = 14;
+// Entries as (re, im) binary64; low: -1 when bit 0 is not a target, else 1 when the
+// first target (qa) is bit 0 and 0 when the second is.
+qc_status df_1q_dense(double* a, const SweepSpec& sp, bool vec, bool low, const double* U, unsigned g,
+                      cudaStream_t st);
+qc_status df_1q_diag(double* a, const SweepSpec& sp, bool vec, bool only1, const double* d0, const double* d1,
+                     unsigned g, cudaStream_t st);
+qc_status df_1q_anti(double* a, const SweepSpec& sp, bool vec, const double* b, const double* c, unsigned g,
+                     cudaStream_t st);
+qc_status df_2q_dense(double* a, const SweepSpec& sp, bool vec, int low, const double* U, unsigned g,
+                      cudaStream_t st);
+
 }  // namespace qcgb

@@ -409,6 +409,8 @@ static qc_status launch_1q(qc_state* s, int tbit, const std::vector<int>& cbits,
     SweepSpec sp = make_spec(s->n, special, cset | tm, tm, 0, vec);
     const Cplx<R> d1{R(U[6]), R(U[7])};
     const unsigned g = stream_grid(sp.items, B);
+    if (sizeof(R) == 8 && s->n >= kDfMinQubits)
+      return df_1q_diag(reinterpret_cast<double*>(a), sp, vec, true, U, U + 6, g, s->stream);
     if (vec)
       QC_COUNT(), k_1q_diag<R, true, true><<<g, B, 0, s->stream>>>(a, sp, d1, d1);
     else
@@ -417,6 +419,13 @@ static qc_status launch_1q(qc_state* s, int tbit, const std::vector<int>& cbits,
   }
   SweepSpec sp = make_spec(s->n, special, cset, tm, 0, vec);
   const unsigned g = stream_grid(sp.items, B);
+  const bool pure_anti = anti && is_one(U[2], U[3]) && is_one(U[4], U[5]);
+  if (sizeof(R) == 8 && s->n >= kDfMinQubits && !pure_anti) {
+    double* ad = reinterpret_cast<double*>(a);
+    if (diag) return df_1q_diag(ad, sp, vec, false, U, U + 6, g, s->stream);
+    if (anti) return df_1q_anti(ad, sp, vec, U + 2, U + 4, g, s->stream);
+    return df_1q_dense(ad, sp, vec, tbit == 0, U, g, s->stream);
+  }
   if (diag) {
     const Cplx<R> d0{R(U[0]), R(U[1])}, d1{R(U[6]), R(U[7])};
     if (vec)
@@ -425,8 +434,7 @@ static qc_status launch_1q(qc_state* s, int tbit, const std::vector<int>& cbits,
       QC_COUNT(), k_1q_diag<R, false, false><<<g, B, 0, s->stream>>>(a, sp, d0, d1);
   } else if (anti) {
     const Cplx<R> b{R(U[2]), R(U[3])}, c{R(U[4]), R(U[5])};
-    const bool pure = is_one(U[2], U[3]) && is_one(U[4], U[5]);
-    if (pure) {
+    if (pure_anti) {
       if (vec)
         QC_COUNT(), k_1q_anti<R, true, true><<<g, B, 0, s->stream>>>(a, sp, b, c);
       else
@@ -463,6 +471,9 @@ static qc_status launch_2q(qc_state* s, int pa, int pb, const double* U) {
   SweepSpec sp = make_spec(s->n, {pa, pb}, 0, uint64_t(1) << pa, uint64_t(1) << pb, vec);
   const int B = 256;
   const unsigned g = stream_grid(sp.items, B);
+  if (sizeof(R) == 8 && s->n >= kDfMinQubits)
+    return df_2q_dense(reinterpret_cast<double*>(a), sp, vec, vec ? -1 : pa == 0 ? 1 : pb == 0 ? 0 : -1, U, g,
+                       s->stream);
   Mat4<R> m;
   for (int i = 0; i < 32; ++i) m.m[i] = R(U[i]);
   if (vec)
