@@ -335,7 +335,7 @@ static qc_status adjoint_impl(const qc_circuit* c, const double* params, int npa
   // forward
   if ((st = qc_state_init_basis(&s, 0))) goto done;
   // (the energy and the gradient do not see the forward state's global phase)
-  if ((st = n >= 10 ? run_fused(&s, c, params, QC_PREC_NATIVE, /*drop_global_phase=*/true)
+  if ((st = n >= 10 ? run_fused(&s, c, params, QC_PREC_AUTO, /*drop_global_phase=*/true)
                     : run_per_gate(&s, c, params)))
     goto done;
   {

@@ -12,9 +12,12 @@
 // states then move once each way per pass instead of once per gate.
 //
 // Sums: each thread forms its share at the state's precision, a warp adds the 32
-// shares at that precision too, and each warp keeps one FP64 sum per recorded rotation
-// in shared memory; at the end every block writes its per-rotation totals, which are reduced over
-// blocks in a fixed order (deterministic).
+// shares at that precision too, and each warp keeps one running sum per recorded
+// rotation in shared memory -- complex64: a pair of FP32 numbers (hi, lo) updated by
+// Knuth's TwoSum (TAOCP Vol. 2, Sec. 4.2.2), so that the sum keeps about 48 bits
+// without an FP64 instruction (GB300 runs FP64 at 2 operations per clock per SM);
+// complex128: FP64.  At the end every block writes its per-rotation totals (FP64), which
+// are reduced over blocks in a fixed order (deterministic).
 #include <string.h>
 
 #include <algorithm>
@@ -27,6 +30,66 @@
 #include "tiles.cuh"
 
 namespace qcgb {
+
+// running per-warp sum of a recorded rotation's shares
+template <typename R>
+struct GradAcc;
+template <>
+struct GradAcc<float> {
+  using T = float2;  // the sum is hi + lo
+  __device__ static T zero() { return make_float2(0.0f, 0.0f); }
+  __device__ static void add(T& a, float x) {
+    const float s = __fadd_rn(a.x, x);
+    const float bb = __fsub_rn(s, a.x);
+    const float err = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(x, bb));
+    a.x = s;
+    a.y = __fadd_rn(a.y, err);
+  }
+  __device__ static double value(T a) { return double(a.x) + double(a.y); }
+};
+template <>
+struct GradAcc<double> {
+  using T = double;
+  __device__ static T zero() { return 0.0; }
+  __device__ static void add(T& a, double x) { a += x; }
+  __device__ static double value(T a) { return a; }
+};
+
+// Share of Im <w|Z_b|v> where bit b is register slot KS (>= 0) or reads `fixed` for
+// every amplitude of the thread (KS = -1): the signs are known at compile time.
+template <typename R, int SB, int KS>
+__device__ __forceinline__ R grad_z(const Cplx<R> (&v)[1 << SB], const Cplx<R> (&w)[1 << SB], uint32_t fixed) {
+  R pos = R(0), neg = R(0);
+#pragma unroll
+  for (int j = 0; j < (1 << SB); ++j) {
+    const R x = im_conj_mul(w[j], v[j]);
+    if (KS >= 0 && ((j >> KS) & 1))
+      neg += x;
+    else
+      pos += x;
+  }
+  if (KS < 0) return fixed ? -pos : pos;
+  return pos - neg;
+}
+
+template <typename R, int SB>
+__device__ __forceinline__ R grad_z_at(int ks, const Cplx<R> (&v)[1 << SB], const Cplx<R> (&w)[1 << SB],
+                                       uint32_t fixed) {
+  switch (ks) {
+    case 0: return grad_z<R, SB, 0>(v, w, fixed);
+    case 1: return grad_z<R, SB, 1>(v, w, fixed);
+    case 2:
+      if constexpr (SB > 2) return grad_z<R, SB, 2>(v, w, fixed);
+      return R(0);
+    case 3:
+      if constexpr (SB > 3) return grad_z<R, SB, 3>(v, w, fixed);
+      return R(0);
+    case 4:
+      if constexpr (SB > 4) return grad_z<R, SB, 4>(v, w, fixed);
+      return R(0);
+    default: return grad_z<R, SB, -1>(v, w, fixed);
+  }
+}
 
 // Im(conj(a) b)
 template <typename R>
@@ -86,7 +149,8 @@ __global__ void __launch_bounds__(NT, 1) k_adj_pass(R* __restrict__ psi, R* __re
   TileStage* sst = reinterpret_cast<TileStage*>(tnt + kTileNumberTab);
   TileOp* sop = reinterpret_cast<TileOp*>(sst + P.nstages);
   R* smat = reinterpret_cast<R*>(sop + P.nops);
-  double* sacc = reinterpret_cast<double*>(smat + ((P.nmat + 1) & ~1));  // NW x ngrad
+  using GA = GradAcc<R>;
+  typename GA::T* sacc = reinterpret_cast<typename GA::T*>(smat + ((P.nmat + 1) & ~1));  // NW x ngrad
   __shared__ int8_t sbits[16];
   if (threadIdx.x == 0) {
 #pragma unroll
@@ -103,7 +167,7 @@ __global__ void __launch_bounds__(NT, 1) k_adj_pass(R* __restrict__ psi, R* __re
   for (int i = threadIdx.x; i < P.nstages; i += blockDim.x) sst[i] = stages[P.stage0 + i];
   for (int i = threadIdx.x; i < P.nops; i += blockDim.x) sop[i] = ops[P.op0 + i];
   for (int i = threadIdx.x; i < P.nmat; i += blockDim.x) smat[i] = mats[P.mat0 + i];
-  for (int i = threadIdx.x; i < NW * P.ngrad; i += blockDim.x) sacc[i] = 0.0;
+  for (int i = threadIdx.x; i < NW * P.ngrad; i += blockDim.x) sacc[i] = GA::zero();
   __syncthreads();
   const uint32_t lowmask = (1u << L) - 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -157,20 +221,27 @@ __global__ void __launch_bounds__(NT, 1) k_adj_pass(R* __restrict__ psi, R* __re
             for (int k = 0; k < SB; ++k)
               if (st.slot_bit[k] == op.zloc) ks = k;
             const uint32_t fixed = op.zloc >= 0 ? ((r0 >> op.zloc) & 1u) : uint32_t((base >> op.zglob) & 1u);
-            share = R(0);
+            if constexpr (sizeof(R) == 4) {
+              // the signs of the slot combinations as compile-time constants
+              share = grad_z_at<R, SB>(ks, v, w, fixed);
+            } else {
+              // (complex128: the selecting form keeps the FP64 pass's register allocation)
+              share = R(0);
 #pragma unroll
-            for (int j = 0; j < NA; ++j) {
-              const uint32_t b = ks >= 0 ? uint32_t((j >> ks) & 1) : fixed;
-              const R x = im_conj_mul(w[j], v[j]);
-              share += b ? -x : x;
+              for (int j = 0; j < NA; ++j) {
+                const uint32_t b = ks >= 0 ? uint32_t((j >> ks) & 1) : fixed;
+                const R x = im_conj_mul(w[j], v[j]);
+                share += b ? -x : x;
+              }
             }
           } else {
             share = grad_pairs_at<R, SB>(op.s0, v, w, op.gen);
           }
-          // warp sum at the state's precision (32 shares), then one FP64 add per warp
+          // warp sum at the state's precision (32 shares), then one update of the
+          // warp's running sum
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) share += __shfl_xor_sync(0xffffffffu, share, o);
-          if (lane == 0) sacc[warp * P.ngrad + op.gslot] += double(share);
+          if (lane == 0) GA::add(sacc[warp * P.ngrad + op.gslot], share);
         }
         if ((base & op.gmask) != op.gval) continue;  // condition on bits outside the tile
         if ((r0 & op.lmask) != op.lval) continue;    // ... on the thread's lane bits
@@ -241,7 +312,7 @@ __global__ void __launch_bounds__(NT, 1) k_adj_pass(R* __restrict__ psi, R* __re
     const TileOp& op = sop[i];
     if (op.grad < 0) continue;
     double a = 0.0;
-    for (int k = 0; k < NW; ++k) a += sacc[k * P.ngrad + op.gslot];
+    for (int k = 0; k < NW; ++k) a += GA::value(sacc[k * P.ngrad + op.gslot]);
     gpart[size_t(op.grad) * gridDim.x + blockIdx.x] = a;
   }
 }
@@ -252,7 +323,7 @@ template <typename R>
 struct AdjShape;
 template <>
 struct AdjShape<float> {
-  static constexpr int M = 12, L = 4, SB = 4, NT = 256;
+  static constexpr int M = 12, L = 4, SB = 3, NT = 512;
 };
 template <>
 struct AdjShape<double> {

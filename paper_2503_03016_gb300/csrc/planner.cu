@@ -1084,7 +1084,8 @@ static std::string auto_key(const qc_state* s, const std::vector<ResolvedOp>& ro
   return key;
 }
 
-static qc_status time_path(qc_state* t, const std::vector<ResolvedOp>& rops, int path, float* ms) {
+static qc_status time_path(qc_state* t, const std::vector<ResolvedOp>& rops, int path, bool drop_global_phase,
+                           float* ms) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -1095,7 +1096,7 @@ static qc_status time_path(qc_state* t, const std::vector<ResolvedOp>& rops, int
     if (path == 2) {
       st = run_tiles_tc(t, rops, &ran);  // ran = false: the circuit does not fit the stages
     } else {
-      st = run_tiles<float>(t, rops, tile_bits_for(t), false);
+      st = run_tiles<float>(t, rops, tile_bits_for(t), drop_global_phase);
     }
     cudaEventRecord(e1, t->stream);
     cudaEventSynchronize(e1);
@@ -1107,8 +1108,8 @@ static qc_status time_path(qc_state* t, const std::vector<ResolvedOp>& rops, int
   return st;
 }
 
-static qc_status auto_choice(qc_state* s, const std::vector<ResolvedOp>& rops, int* choice) {
-  const std::string key = auto_key(s, rops);
+static qc_status auto_choice(qc_state* s, const std::vector<ResolvedOp>& rops, bool drop_global_phase, int* choice) {
+  const std::string key = auto_key(s, rops) + (drop_global_phase ? "|nophase" : "");
   std::lock_guard<std::mutex> lock(g_auto_mu);
   auto it = g_auto_choice.find(key);
   if (it != g_auto_choice.end()) {
@@ -1144,8 +1145,8 @@ static qc_status auto_choice(qc_state* s, const std::vector<ResolvedOp>& rops, i
   }
   qc_status st = qc_state_init_basis(&t, 0);
   float ms_cuda = 1e30f, ms_tc = 1e30f;
-  if (st == QC_OK) st = time_path(&t, rops, 0, &ms_cuda);
-  if (st == QC_OK) st = time_path(&t, rops, 2, &ms_tc);
+  if (st == QC_OK) st = time_path(&t, rops, 0, drop_global_phase, &ms_cuda);
+  if (st == QC_OK) st = time_path(&t, rops, 2, drop_global_phase, &ms_tc);
   cudaStreamSynchronize(t.stream);
   cudaFree(t.amps);
   if (t.scratch) cudaFree(t.scratch);
@@ -1167,9 +1168,11 @@ qc_status run_fused(qc_state* s, const qc_circuit* c, const double* params, qc_p
     if (qc_status st = resolve_op(c, c->ops[i], params, &rops[i])) return st;
   if (prec == QC_PREC_AUTO) {
     prec = QC_PREC_NATIVE;
-    if (s->dtype == QC_C64 && s->n >= 12 && !drop_global_phase) {
+    // (the tensor-core passes keep a global phase the CUDA-core passes may drop; the
+    // callers that drop it accept either)
+    if (s->dtype == QC_C64 && s->n >= 12) {
       int choice = 0;
-      if (qc_status st = auto_choice(s, rops, &choice)) return st;
+      if (qc_status st = auto_choice(s, rops, drop_global_phase, &choice)) return st;
       if (choice == 2) prec = QC_PREC_TF32X3;
     }
   }

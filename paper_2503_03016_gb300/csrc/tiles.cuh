@@ -281,16 +281,48 @@ __device__ __forceinline__ void apply_swap(int s0, int s1, Cplx<R> (&v)[1 << SB]
 
 // TOP_PHASE1: multiply by z0 or z1 as the op's bit reads 0 or 1 -- the bit is register
 // slot ks (>= 0), or fixed for the thread (`fixed`)
+// complex64: the slot is a template argument (KS; -1: the bit is fixed), so that each
+// slot combination's factor is known at compile time instead of being selected per
+// amplitude; complex128 keeps the selecting form (its FP64 passes are bound elsewhere,
+// and the switch costs them registers)
+template <typename R, int SB, int KS>
+__device__ __forceinline__ void phase1_k(Cplx<R> (&v)[1 << SB], Cplx<R> z0, Cplx<R> z1, uint32_t jmask) {
+#pragma unroll
+  for (int j = 0; j < (1 << SB); ++j) {
+    if (!((jmask >> j) & 1u)) continue;
+    v[j] = cmul(v[j], (KS >= 0 && ((j >> KS) & 1)) ? z1 : z0);
+  }
+}
+
 template <typename R, int SB>
 __device__ __forceinline__ void apply_phase1(Cplx<R> (&v)[1 << SB], const R* zs, int ks, uint32_t fixed,
                                              uint32_t jmask) {
   const Cplx<R> z0{zs[0], zs[1]}, z1{zs[2], zs[3]};
-  const Cplx<R> zf = fixed ? z1 : z0;
+  if constexpr (sizeof(R) == 4) {
+    switch (ks) {
+      case 0: phase1_k<R, SB, 0>(v, z0, z1, jmask); return;
+      case 1: phase1_k<R, SB, 1>(v, z0, z1, jmask); return;
+      case 2:
+        if constexpr (SB > 2) phase1_k<R, SB, 2>(v, z0, z1, jmask);
+        return;
+      case 3:
+        if constexpr (SB > 3) phase1_k<R, SB, 3>(v, z0, z1, jmask);
+        return;
+      case 4:
+        if constexpr (SB > 4) phase1_k<R, SB, 4>(v, z0, z1, jmask);
+        return;
+      default:
+        phase1_k<R, SB, -1>(v, fixed ? z1 : z0, z1, jmask);
+        return;
+    }
+  } else {
+    const Cplx<R> zf = fixed ? z1 : z0;
 #pragma unroll
-  for (int j = 0; j < (1 << SB); ++j) {
-    if (!((jmask >> j) & 1u)) continue;
-    const Cplx<R> z = ks >= 0 ? (((j >> ks) & 1) ? z1 : z0) : zf;
-    v[j] = cmul(v[j], z);
+    for (int j = 0; j < (1 << SB); ++j) {
+      if (!((jmask >> j) & 1u)) continue;
+      const Cplx<R> z = ks >= 0 ? (((j >> ks) & 1) ? z1 : z0) : zf;
+      v[j] = cmul(v[j], z);
+    }
   }
 }
 
