@@ -48,7 +48,7 @@ __device__ __forceinline__ float df_scale2(float f, int k) {
 }
 
 // binary64 -> (hi, lo) for any input.  x = s M 2^(e - 1075) with the 53-bit significand M.
-__device__ __noinline__ float2 df_split_general(double x) {
+static __device__ __noinline__ float2 df_split_general(double x) {
   const uint64_t b = uint64_t(__double_as_longlong(x));
   const bool neg = (b >> 63) != 0;
   const int e = int((b >> 52) & 0x7FFu);
@@ -64,7 +64,7 @@ __device__ __noinline__ float2 df_split_general(double x) {
 
 // hi + lo -> binary64 for any pair: the two significands assembled as one integer and
 // rounded to nearest (ties to even); lo below 2^-61 of hi is truncated before rounding.
-__device__ __noinline__ double df_join_general(float hi, float lo) {
+static __device__ __noinline__ double df_join_general(float hi, float lo) {
   const uint32_t uh = __float_as_uint(hi), ul = __float_as_uint(lo);
   const int eh = int((uh >> 23) & 0xFFu), el = int((ul >> 23) & 0xFFu);
   if (eh == 255) return double(hi);

@@ -963,6 +963,29 @@ template void emit_pass<float>(const BuiltPass&, const std::vector<PlanOp>&, int
 template void emit_pass<double>(const BuiltPass&, const std::vector<PlanOp>&, int, int, int, int, HostPlan<double>&,
                                 bool, bool, bool, bool, bool);
 
+void encode_df_slots(HostPlan<double>& hp) {
+  auto enc = [](double x) {
+    const float h = float(x), l = float(x - double(h));  // x - h is exact in binary64
+    uint32_t hb, lb;
+    memcpy(&hb, &h, 4);
+    memcpy(&lb, &l, 4);
+    const uint64_t u = uint64_t(hb) | (uint64_t(lb) << 32);
+    double d;
+    memcpy(&d, &u, 8);
+    return d;
+  };
+  std::vector<char> words(hp.mats.size(), 0);  // CZ code words: not numbers
+  for (const TilePass& P : hp.passes)
+    for (int i = 0; i < P.nops; ++i) {
+      const TileOp& op = hp.ops[size_t(P.op0) + i];
+      if (op.type == TOP_CZSET)
+        for (int e = 0; e < op.s0; ++e) words[size_t(P.mat0) + size_t(op.mat) + e] = 1;
+    }
+  for (size_t i = 0; i < hp.mats.size(); ++i)
+    if (!words[i]) hp.mats[i] = enc(hp.mats[i]);
+  for (double& x : hp.pool) x = enc(x);
+}
+
 thread_local int g_last_pass_count = 0;  // also set by the fused adjoint sweep
 thread_local int g_last_fused_path = 0;
 thread_local int g_last_stage_count = 0;
@@ -984,7 +1007,9 @@ template <typename R>
 static qc_status run_tiles(qc_state* s, const std::vector<ResolvedOp>& rops, int m, bool drop_global_phase) {
   const int n = s->n;
   const int L = sizeof(R) == 4 ? 4 : 3;
-  constexpr int SB = TileShape<R>::SB;
+  // complex128 states of 2^kDfMinQubits amplitudes or more: double-float passes
+  const bool df = sizeof(R) == 8 && n >= kDfMinQubits;
+  const int SB = df ? kDfTileSB : TileShape<R>::SB;
   std::vector<PlanOp> pops;
   to_plan_ops(rops, pops);
   if (drop_global_phase) drop_global_phases(pops);
@@ -999,6 +1024,9 @@ static qc_status run_tiles(qc_state* s, const std::vector<ResolvedOp>& rops, int
   g_last_pass_count = int(hp.passes.size());
   g_last_fused_path = 1;
   g_last_stage_count = int(hp.stages.size());
+  if constexpr (sizeof(R) == 8) {
+    if (df) encode_df_slots(hp);
+  }
   // upload stages, ops, tables and matrices into the state's scratch (stream ordered)
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t sb = al(hp.stages.size() * sizeof(TileStage));
@@ -1031,7 +1059,11 @@ static qc_status run_tiles(qc_state* s, const std::vector<ResolvedOp>& rops, int
   for (const TileOp& op : hp.ops)
     extops |= op.type == TOP_CZSET || op.type == TOP_PHASE1 || op.type == TOP_BFLY || op.type == TOP_REAL1;
   for (const TilePass& P : hp.passes) extops |= P.permuted != 0;
-  auto kern = extops ? k_tile_pass<R, NT, SB, true> : k_tile_pass<R, NT, SB, false>;
+  constexpr int SBK = TileShape<R>::SB;
+  auto kern = extops ? k_tile_pass<R, NT, SBK, true> : k_tile_pass<R, NT, SBK, false>;
+  if constexpr (sizeof(R) == 8) {
+    if (df) kern = tile_pass_df_kernel(extops);
+  }
   if (qc_status st = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
                                 "tile pass shared memory"))
     return st;
@@ -1194,7 +1226,7 @@ qc_status run_fused(qc_state* s, const qc_circuit* c, const double* params, qc_p
 template <typename R>
 static void plan_stats(int n, const std::vector<ResolvedOp>& rops, int m, int* passes, int* stages, int* ops) {
   const int L = sizeof(R) == 4 ? 4 : 3;
-  constexpr int SB = TileShape<R>::SB;
+  const int SB = sizeof(R) == 8 && n >= kDfMinQubits ? kDfTileSB : TileShape<R>::SB;
   std::vector<PlanOp> pops;
   to_plan_ops(rops, pops);
   std::vector<BuiltPass> bps = build_passes(pops, n, m, L);

@@ -536,6 +536,19 @@ struct HostPlan {
   std::vector<R> mats;  // per-pass matrices and slot tables (staged in shared memory)
 };
 
+// the complex128 circuit pass in double-float arithmetic (tiles_df.cu): the same
+// launch signature as k_tile_pass<double>; its matrices and tables are double-float
+// slots (encode_df_slots)
+using TilePassFn = void (*)(double*, const TilePass, const TileStage*, const TileOp*, const double*, const double*);
+TilePassFn tile_pass_df_kernel(bool extops);
+// its register stages: 2^3 amplitudes per thread, 512 threads (16 warps per SM: the
+// double-float gate bodies are latency-bound at 8)
+constexpr int kDfTileSB = 3, kDfTileNT = 512;
+// a plan's numeric matrix entries and phase tables -> double-float slots in place (8 bytes
+// per value: binary32 hi in the low half, lo = the rest rounded, in the high half); the
+// CZ code words are left as they are
+void encode_df_slots(HostPlan<double>& hp);
+
 // tile passes of the most recent fused circuit run or fused adjoint reverse sweep
 extern thread_local int g_last_pass_count;
 // how the most recent QC_RUN_FUSED circuit ran: 0 per gate, 1 CUDA-core tile passes,
