@@ -14,14 +14,15 @@
  *   - Gate matrices are passed from the host in FP64, row-major, as (re, im) pairs;
  *     complex64 states round them to FP32.
  *   - Complex128 arithmetic: the per-gate sweeps (qc_apply_1q, qc_apply_2q,
- *     qc_apply_ctrl and circuits run per gate) and the fused circuit passes
- *     (QC_RUN_FUSED) on states of 2^14 amplitudes or more compute in double-float
- *     arithmetic: each binary64 value taken as a pair of
+ *     qc_apply_ctrl and circuits run per gate), the fused circuit passes
+ *     (QC_RUN_FUSED) and the adjoint gradient's forward and reverse passes on states
+ *     of 2^14 amplitudes or more compute in double-float arithmetic: each binary64 value taken as a pair of
  *     binary32 numbers (48-bit significand) and every product and sum formed with
  *     error-free transformations on the FP32 pipe, about 2^-47 relative error per
  *     gate.  Magnitudes below 2^-74 keep 24 bits, below 2^-126 fewer (binary32
- *     subnormals) and below 2^-149 become zero.  Smaller states, the readouts, the
- *     adjoint gradient and every other kernel compute in FP64.
+ *     subnormals) and below 2^-149 become zero.  Smaller states, the readouts
+ *     (probabilities, sampling, expectations, collapse), the adjoint's H psi and
+ *     energy, and every other kernel compute in FP64.
  *
  * Errors: every call returns a qc_status.  Argument errors are reported before
  * anything is launched and leave the state untouched.  CUDA errors surface as

@@ -28,6 +28,7 @@
 #include "common.cuh"
 #include "kernels.cuh"
 #include "tiles.cuh"
+#include "tiles_df.cuh"
 
 namespace qcgb {
 
@@ -317,6 +318,306 @@ __global__ void __launch_bounds__(NT, 1) k_adj_pass(R* __restrict__ psi, R* __re
   }
 }
 
+// ---------------------------------------------------------------------------
+// complex128 in double-float arithmetic (states of 2^kDfMinQubits amplitudes or more)
+// ---------------------------------------------------------------------------
+// (hi, lo) scalar sums
+__device__ __forceinline__ float2 dfs_add(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float bb = __fsub_rn(s, a.x);
+  float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+  e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+  const float hi = __fadd_rn(s, e);
+  return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
+}
+// the sum of the two lanes of a packed double-float result
+__device__ __forceinline__ float2 df_lane_total(const DF2& r) {
+  return dfs_add(make_float2(r.hi.x, r.lo.x), make_float2(r.hi.y, r.lo.y));
+}
+// one packed product term c x (c's hi, lo; its -hi formed here) into the accumulator
+__device__ __forceinline__ void dfg_term(DF2Acc& a, bool first, float2 ch, float2 cl, const DF2& x) {
+  const float2 cn = make_float2(-ch.x, -ch.y);
+  if (first)
+    df2_first(a, ch, cn, cl, x);
+  else
+    df2_mac(a, ch, cn, cl, x);
+}
+
+// Im <w|Z_b|v> with bit b the register slot KS (>= 0) or reading `fixed` (KS = -1):
+// lanes (w.re, -w.im) * (v.im, v.re), the sign of each slot combination at compile time
+template <int SB, int KS>
+__device__ __forceinline__ float2 dfgrad_z(const DFC (&v)[1 << SB], const DFC (&w)[1 << SB], uint32_t fixed) {
+  DF2Acc a;
+#pragma unroll
+  for (int j = 0; j < (1 << SB); ++j) {
+    float2 ch = make_float2(w[j].hi.x, -w[j].hi.y), cl = make_float2(w[j].lo.x, -w[j].lo.y);
+    if (KS >= 0 && ((j >> KS) & 1)) {
+      ch = make_float2(-ch.x, -ch.y);
+      cl = make_float2(-cl.x, -cl.y);
+    }
+    dfg_term(a, j == 0, ch, cl, dfc_sw(v[j]));
+  }
+  const float2 t = df_lane_total(df2_result(a));
+  return (KS < 0 && fixed) ? make_float2(-t.x, -t.y) : t;
+}
+
+template <int SB>
+__device__ __forceinline__ float2 dfgrad_z_at(int ks, const DFC (&v)[1 << SB], const DFC (&w)[1 << SB],
+                                              uint32_t fixed) {
+  switch (ks) {
+    case 0: return dfgrad_z<SB, 0>(v, w, fixed);
+    case 1: return dfgrad_z<SB, 1>(v, w, fixed);
+    case 2:
+      if constexpr (SB > 2) return dfgrad_z<SB, 2>(v, w, fixed);
+      return make_float2(0.0f, 0.0f);
+    case 3:
+      if constexpr (SB > 3) return dfgrad_z<SB, 3>(v, w, fixed);
+      return make_float2(0.0f, 0.0f);
+    default: return dfgrad_z<SB, -1>(v, w, fixed);
+  }
+}
+
+// Im <w|G|v> over the pairs along slot S0: G = X (gen 0):
+//   (w0.re, -w0.im) * (v1.im, v1.re) + (w1.re, -w1.im) * (v0.im, v0.re);
+// G = Y (gen 1): Im(conj(w0) (-i v1)) + Im(conj(w1) (i v0)) =
+//   (w1.re, w1.im) * (v0.re, v0.im) - (w0.re, w0.im) * (v1.re, v1.im)
+template <int SB, int S0>
+__device__ __forceinline__ float2 dfgrad_pairs(const DFC (&v)[1 << SB], const DFC (&w)[1 << SB], int gen) {
+  DF2Acc a;
+  bool first = true;
+#pragma unroll
+  for (int j = 0; j < (1 << SB); ++j) {
+    if (j & (1 << S0)) continue;
+    const int j1 = j | (1 << S0);
+    if (gen == 0) {
+      dfg_term(a, first, make_float2(w[j].hi.x, -w[j].hi.y), make_float2(w[j].lo.x, -w[j].lo.y), dfc_sw(v[j1]));
+      dfg_term(a, false, make_float2(w[j1].hi.x, -w[j1].hi.y), make_float2(w[j1].lo.x, -w[j1].lo.y),
+               dfc_sw(v[j]));
+    } else {
+      dfg_term(a, first, w[j1].hi, w[j1].lo, dfc_x(v[j]));
+      dfg_term(a, false, make_float2(-w[j].hi.x, -w[j].hi.y), make_float2(-w[j].lo.x, -w[j].lo.y), dfc_x(v[j1]));
+    }
+    first = false;
+  }
+  return df_lane_total(df2_result(a));
+}
+
+template <int SB>
+__device__ __forceinline__ float2 dfgrad_pairs_at(int s0, const DFC (&v)[1 << SB], const DFC (&w)[1 << SB],
+                                                  int gen) {
+  switch (s0) {
+    case 0: return dfgrad_pairs<SB, 0>(v, w, gen);
+    case 1: return dfgrad_pairs<SB, 1>(v, w, gen);
+    case 2:
+      if constexpr (SB > 2) return dfgrad_pairs<SB, 2>(v, w, gen);
+      return make_float2(0.0f, 0.0f);
+    default:
+      if constexpr (SB > 3) return dfgrad_pairs<SB, 3>(v, w, gen);
+      return make_float2(0.0f, 0.0f);
+  }
+}
+
+// The reverse pass of k_adj_pass for complex128 in double-float arithmetic: both tiles
+// split in place after their load, every op's double-float body applied to psi and
+// lambda, each record's share a double-float sum, summed over the warp with TwoSum and
+// kept per warp and rotation as (hi, lo); the matrices and tables are double-float slots.
+template <int NT, int SB>
+__global__ void __launch_bounds__(NT, 1) k_adj_pass_df(double* __restrict__ psi, double* __restrict__ lam,
+                                                       const TilePass P, const TileStage* __restrict__ stages,
+                                                       const TileOp* __restrict__ ops, const double* __restrict__ pool,
+                                                       const double* __restrict__ mats, double* __restrict__ gpart) {
+  constexpr int NA = 1 << SB;
+  constexpr int NW = NT / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = P.m, L = P.L;
+  const uint32_t T = 1u << m;
+  Cplx<double>* bufs = reinterpret_cast<Cplx<double>*>(smem_raw);  // psi: 2 x T, lambda: 2 x T
+  uint64_t* hioff = reinterpret_cast<uint64_t*>(smem_raw + 4 * sizeof(Cplx<double>) * T);
+  const int nhi = m - L;
+  uint64_t* tnt = hioff + (1u << nhi);
+  TileStage* sst = reinterpret_cast<TileStage*>(tnt + kTileNumberTab);
+  TileOp* sop = reinterpret_cast<TileOp*>(sst + P.nstages);
+  double* smat = reinterpret_cast<double*>(sop + P.nops);
+  float2* sacc = reinterpret_cast<float2*>(smat + ((P.nmat + 1) & ~1));  // NW x ngrad
+  __shared__ int8_t sbits[16];
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 16; ++k) sbits[k] = P.bits[k];
+  }
+  __syncthreads();
+  for (uint32_t h = threadIdx.x; h < (1u << nhi); h += blockDim.x) {
+    uint64_t o = 0;
+    for (int k = 0; k < nhi; ++k)
+      if ((h >> k) & 1) o |= uint64_t(1) << sbits[L + k];
+    hioff[h] = o;
+  }
+  build_tile_number_tables(tnt, sbits, m, __ffsll(static_cast<long long>(P.ntiles)) - 1);
+  for (int i = threadIdx.x; i < P.nstages; i += blockDim.x) sst[i] = stages[P.stage0 + i];
+  for (int i = threadIdx.x; i < P.nops; i += blockDim.x) sop[i] = ops[P.op0 + i];
+  for (int i = threadIdx.x; i < P.nmat; i += blockDim.x) smat[i] = mats[P.mat0 + i];
+  for (int i = threadIdx.x; i < NW * P.ngrad; i += blockDim.x) sacc[i] = make_float2(0.0f, 0.0f);
+  __syncthreads();
+  const uint32_t lowmask = (1u << L) - 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint64_t t = blockIdx.x;
+  if (t < P.ntiles) {
+    const uint64_t b0 = tile_base(t, tnt);
+    prefetch_tile<double>(bufs, psi, b0, hioff, L, T);
+    prefetch_tile<double>(bufs + 2 * T, lam, b0, hioff, L, T);
+  }
+  cp_async_commit();
+  for (int it = 0; t < P.ntiles; t += gridDim.x, ++it) {
+    Cplx<double>* dp = bufs + (it & 1) * T;
+    Cplx<double>* dl = bufs + 2 * T + (it & 1) * T;
+    float4* tp = reinterpret_cast<float4*>(dp);
+    float4* tl = reinterpret_cast<float4*>(dl);
+    const uint64_t base = tile_base(t, tnt);
+    const uint64_t tn = t + gridDim.x;
+    if (tn < P.ntiles) {
+      const uint64_t bn = tile_base(tn, tnt);
+      prefetch_tile<double>(bufs + ((it + 1) & 1) * T, psi, bn, hioff, L, T);
+      prefetch_tile<double>(bufs + 2 * T + ((it + 1) & 1) * T, lam, bn, hioff, L, T);
+    }
+    cp_async_commit();
+    cp_async_wait1();
+    __syncthreads();
+    for (uint32_t p = threadIdx.x; p < T; p += blockDim.x) {
+      const Cplx<double> a = dp[p], b = dl[p];
+      float rh, rl, ih, il;
+      df_split(a.re, rh, rl);
+      df_split(a.im, ih, il);
+      tp[p] = make_float4(rh, ih, rl, il);
+      df_split(b.re, rh, rl);
+      df_split(b.im, ih, il);
+      tl[p] = make_float4(rh, ih, rl, il);
+    }
+    __syncthreads();
+    for (int s = 0; s < P.nstages; ++s) {
+      const TileStage& st = sst[s];
+      uint32_t r0 = 0;
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        if (k < m - SB) r0 |= ((threadIdx.x >> k) & 1u) << st.lane_bit[k];
+      uint32_t sw[SB];
+#pragma unroll
+      for (int k = 0; k < SB; ++k) sw[k] = tile_swz(1u << st.slot_bit[k]);
+      const uint32_t p0 = tile_swz(r0);
+      DFC v[NA], w[NA];
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        const uint32_t a = p0 ^ slot_xor<SB>(j, sw);
+        v[j] = dfc_ld(tp, a);
+        w[j] = dfc_ld(tl, a);
+      }
+      for (int q = 0; q < st.nops; ++q) {
+        const TileOp op = sop[st.op0 + q];
+        if (op.grad >= 0) {
+          float2 share;
+          if (op.gen == 2) {
+            int ks = -1;
+#pragma unroll
+            for (int k = 0; k < SB; ++k)
+              if (st.slot_bit[k] == op.zloc) ks = k;
+            const uint32_t fixed = op.zloc >= 0 ? ((r0 >> op.zloc) & 1u) : uint32_t((base >> op.zglob) & 1u);
+            share = dfgrad_z_at<SB>(ks, v, w, fixed);
+          } else {
+            share = dfgrad_pairs_at<SB>(op.s0, v, w, op.gen);
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1)
+            share = dfs_add(share, make_float2(__shfl_xor_sync(0xffffffffu, share.x, o),
+                                               __shfl_xor_sync(0xffffffffu, share.y, o)));
+          if (lane == 0) sacc[warp * P.ngrad + op.gslot] = dfs_add(sacc[warp * P.ngrad + op.gslot], share);
+        }
+        if ((base & op.gmask) != op.gval) continue;
+        if ((r0 & op.lmask) != op.lval) continue;
+        const double* mm = smat + op.mat;
+        if (op.type == TOP_DENSE1) {
+          df_apply_dense1<SB>(op.s0, v, mm, op.jmask);
+          df_apply_dense1<SB>(op.s0, w, mm, op.jmask);
+        } else if (op.type == TOP_REAL1) {
+          df_apply_real1<SB>(op.s0, v, mm, op.jmask);
+          df_apply_real1<SB>(op.s0, w, mm, op.jmask);
+        } else if (op.type == TOP_DENSE2) {
+          df_apply_dense2<SB>(op.s0, op.s1, v, mm);
+          df_apply_dense2<SB>(op.s0, op.s1, w, mm);
+        } else if (op.type == TOP_PHASE1) {
+          const uint32_t fixed =
+              op.s0 >= 0 ? 0u : op.zloc >= 0 ? (r0 >> op.zloc) & 1u : uint32_t((base >> op.zglob) & 1u);
+          df_apply_phase1<SB>(v, mm, op.s0, fixed, op.jmask);
+          df_apply_phase1<SB>(w, mm, op.s0, fixed, op.jmask);
+        } else if (op.type == TOP_CZSET) {
+          const uint32_t flip = czset_flips<double, SB>(mm, op.s0, r0, base);
+#pragma unroll
+          for (int j = 0; j < NA; ++j)
+            if ((flip >> j) & 1u) {
+              v[j].hi = make_float2(-v[j].hi.x, -v[j].hi.y);
+              v[j].lo = make_float2(-v[j].lo.x, -v[j].lo.y);
+              w[j].hi = make_float2(-w[j].hi.x, -w[j].hi.y);
+              w[j].lo = make_float2(-w[j].lo.x, -w[j].lo.y);
+            }
+        } else {
+          // exp(i (c + sum beta_p b_p)), the same factor on both states
+          const double* l0 = pool + 2 * op.tab;
+          const double* l1 = l0 + 2 * (1 << P.c0);
+          const double* g0 = l1 + 2 * (1 << (m - P.c0));
+          const uint32_t gn = 1u << P.cg, gm = gn - 1;
+          DFC f = dfc_mul(dfc_slots(g0 + 2 * (t & gm)), dfc_slots(g0 + 2 * (gn + ((t >> P.cg) & gm))));
+          f = dfc_mul(dfc_slots(g0 + 2 * (2 * gn + ((t >> (2 * P.cg)) & gm))), f);
+          f = dfc_mul(dfc_slots(l0 + 2 * (r0 & ((1u << P.c0) - 1))), f);
+          f = dfc_mul(dfc_slots(l1 + 2 * (r0 >> P.c0)), f);
+          const DFPair pf = df_pairs(f);
+#pragma unroll
+          for (int j = 0; j < NA; ++j) {
+            if (!((op.jmask >> j) & 1u)) continue;
+            DF2Acc a;
+            dfc_first(a, pf, dfc_slots(mm + 2 * j));
+            const DFPair pz = df_pairs(dfc_res(a));
+            DF2Acc b0, b1;
+            dfc_first(b0, pz, v[j]);
+            dfc_first(b1, pz, w[j]);
+            v[j] = dfc_res(b0);
+            w[j] = dfc_res(b1);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NA; ++j) {
+        const uint32_t a = p0 ^ slot_xor<SB>(j, sw);
+        dfc_st(tp, a, v[j]);
+        dfc_st(tl, a, w[j]);
+      }
+      if (st.warp_local)
+        __syncwarp();
+      else
+        __syncthreads();
+    }
+    for (uint32_t e = threadIdx.x; e < T / 2; e += blockDim.x) {
+      const uint32_t r = 2 * e;
+      const uint64_t gi = base | hioff[r >> L] | (r & lowmask);
+      const uint32_t p = tile_swz(r);
+      const float4 a0 = tp[p], a1 = tp[p ^ 1u], b0 = tl[p], b1 = tl[p ^ 1u];
+      st_amp2<double>(psi, gi, Cplx<double>{df_join(a0.x, a0.z), df_join(a0.y, a0.w)},
+                      Cplx<double>{df_join(a1.x, a1.z), df_join(a1.y, a1.w)});
+      st_amp2<double>(lam, gi, Cplx<double>{df_join(b0.x, b0.z), df_join(b0.y, b0.w)},
+                      Cplx<double>{df_join(b1.x, b1.z), df_join(b1.y, b1.w)});
+    }
+    __syncthreads();
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+  for (int i = threadIdx.x; i < P.nops; i += blockDim.x) {
+    const TileOp& op = sop[i];
+    if (op.grad < 0) continue;
+    double a = 0.0;
+    for (int k = 0; k < NW; ++k) {
+      const float2 x = sacc[k * P.ngrad + op.gslot];
+      a += double(x.x) + double(x.y);
+    }
+    gpart[size_t(op.grad) * gridDim.x + blockIdx.x] = a;
+  }
+}
+
 // Tile shape of the fused sweep per precision: two states x two buffers of 2^m
 // amplitudes in shared memory (4 x 32 KiB), register stages of SB bits per state.
 template <typename R>
@@ -330,6 +631,11 @@ struct AdjShape<double> {
   static constexpr int M = 11, L = 3, SB = 3, NT = 256;
 };
 
+// complex128 in double-float arithmetic: the same tiles, 2-bit register stages per
+// state with 512 threads (3-bit stages with 256 threads: 90 against 81 ms per 24-qubit
+// gradient call; the register cap of 512 threads costs a 152-byte spill)
+constexpr int kAdjDfSB = 2, kAdjDfNT = 512;
+
 int adjoint_tiles_min_qubits() { return 12; }
 
 template <typename R>
@@ -342,6 +648,8 @@ qc_status adjoint_reverse_tiles(int n, const std::vector<ResolvedOp>& rev, const
     set_error("fused adjoint sweep needs n >= %d", m);
     return QC_ERR_UNSUPPORTED;
   }
+  const bool df = sizeof(R) == 8 && n >= kDfMinQubits;
+  const int sbw = df ? kAdjDfSB : S::SB, ntw = df ? kAdjDfNT : S::NT;
   std::vector<PlanOp> pops;
   to_plan_ops(rev, pops, &grad, &gen);
   // psi and lambda take every op together, so a global phase of an op multiplies both
@@ -351,9 +659,12 @@ qc_status adjoint_reverse_tiles(int n, const std::vector<ResolvedOp>& rev, const
   const std::vector<BuiltPass> bps = build_passes(pops, n, m, L);
   HostPlan<R> hp;
   for (const BuiltPass& bp : bps)
-    emit_pass<R>(bp, pops, n, m, L, S::SB, hp, /*swap_ops=*/false, /*phase1_ops=*/true, /*relabel_swaps=*/false,
+    emit_pass<R>(bp, pops, n, m, L, sbw, hp, /*swap_ops=*/false, /*phase1_ops=*/true, /*relabel_swaps=*/false,
                  /*bfly_ops=*/false, /*real1_ops=*/true);
   g_last_pass_count = int(hp.passes.size());
+  if constexpr (sizeof(R) == 8) {
+    if (df) encode_df_slots(hp);
+  }
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t sb = al(hp.stages.size() * sizeof(TileStage));
   const size_t ob = al(hp.ops.size() * sizeof(TileOp));
@@ -383,11 +694,14 @@ qc_status adjoint_reverse_tiles(int n, const std::vector<ResolvedOp>& rev, const
   size_t plan_max = 0;
   for (const TilePass& P : hp.passes)
     plan_max = std::max(plan_max, P.nstages * sizeof(TileStage) + P.nops * sizeof(TileOp) +
-                                      ((P.nmat + 1) & ~1) * sizeof(R) + size_t(S::NT / 32) * P.ngrad * sizeof(double));
+                                      ((P.nmat + 1) & ~1) * sizeof(R) + size_t(ntw / 32) * P.ngrad * sizeof(double));
   const size_t smem = 4 * sizeof(Cplx<R>) * (size_t(1) << m) + sizeof(uint64_t) * (size_t(1) << (m - L)) +
                       sizeof(uint64_t) * kTileNumberTab + plan_max;
-  if (qc_status st = check_cuda(cudaFuncSetAttribute(k_adj_pass<R, S::NT, S::SB>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
+  auto kern = k_adj_pass<R, S::NT, S::SB>;
+  if constexpr (sizeof(R) == 8) {
+    if (df) kern = k_adj_pass_df<kAdjDfNT, kAdjDfSB>;
+  }
+  if (qc_status st = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
                                 "adjoint pass shared memory"))
     return st;
   const uint64_t ntiles = uint64_t(1) << (n - m);
@@ -396,10 +710,9 @@ qc_status adjoint_reverse_tiles(int n, const std::vector<ResolvedOp>& rev, const
   const TileOp* dop = reinterpret_cast<const TileOp*>(base + sb);
   const R* dpool = reinterpret_cast<const R*>(base + sb + ob);
   const R* dmats = reinterpret_cast<const R*>(base + sb + ob + pb);
-  const unsigned threads = 1u << (m - S::SB);
+  const unsigned threads = 1u << (m - sbw);
   for (const TilePass& P : hp.passes)
-    QC_COUNT(), k_adj_pass<R, S::NT, S::SB><<<grid, threads, smem, stream>>>(psi, lam, P, dst, dop, dpool, dmats,
-                                                                             gpart);
+    QC_COUNT(), kern<<<grid, threads, smem, stream>>>(psi, lam, P, dst, dop, dpool, dmats, gpart);
   *grid_out = int(grid);
   return check_launch("adjoint pass");
 }
