@@ -20,7 +20,8 @@
  *     binary32 numbers (48-bit significand) and every product and sum formed with
  *     error-free transformations on the FP32 pipe, about 2^-47 relative error per
  *     gate.  Magnitudes below 2^-74 keep 24 bits, below 2^-126 fewer (binary32
- *     subnormals) and below 2^-149 become zero.  Smaller states, the readouts
+ *     subnormals) and below 2^-149 become zero; magnitudes of 2^128 or more (never
+ *     those of a normalised state) overflow to infinity.  Smaller states, the readouts
  *     (probabilities, sampling, expectations, collapse), the adjoint's H psi and
  *     energy, and every other kernel compute in FP64.
  *
