@@ -21,9 +21,11 @@
  *     error-free transformations on the FP32 pipe, about 2^-47 relative error per
  *     gate.  Magnitudes below 2^-74 keep 24 bits, below 2^-126 fewer (binary32
  *     subnormals) and below 2^-149 become zero; magnitudes of 2^128 or more (never
- *     those of a normalised state) overflow to infinity.  Smaller states, the readouts
- *     (probabilities, sampling, expectations, collapse), the adjoint's H psi and
- *     energy, and every other kernel compute in FP64.
+ *     those of a normalised state) overflow to infinity.  The adjoint's H psi and the
+ *     per-thread sums of Z-string expectations use the same arithmetic (block and
+ *     cross-block sums in FP64).  Smaller states, the other readouts (probabilities,
+ *     sampling, X/Y-string expectations, collapse), the adjoint's energy and every
+ *     other kernel compute in FP64.
  *
  * Errors: every call returns a qc_status.  Argument errors are reported before
  * anything is launched and leave the state untouched.  CUDA errors surface as

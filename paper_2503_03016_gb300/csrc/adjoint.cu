@@ -21,6 +21,7 @@
 #include "circuit.cuh"
 #include "common.cuh"
 #include "kernels.cuh"
+#include "tiles_df.cuh"
 
 namespace qcgb {
 
@@ -58,7 +59,8 @@ struct HGroup {
   uint64_t x[kHTerms];                // X-or-Y mask of each term; equal masks are adjacent
   uint64_t z[kHTerms];
   double cre[kHTerms], cim[kHTerms];  // coeff * i^nY
-  float fre[kHTerms], fim[kHTerms];   // the same, rounded to FP32 (complex64 states)
+  float fre[kHTerms], fim[kHTerms];   // the same, rounded to FP32 (complex64 states; the hi parts)
+  float lre[kHTerms], lim[kHTerms];   // the rest rounded to FP32 (double-float lo parts)
 };
 
 // lambda_k (+)= sum_t c_t i^nY (-1)^popc((k^x_t) & z_t) psi_{k^x_t} over up to kHTerms
@@ -128,6 +130,59 @@ __global__ void __launch_bounds__(256) k_apply_hsum(const R* __restrict__ psi, R
       o1.im += f1r * p1.im + f1i * p1.re;
     }
     st_amp2<R>(lam, k, o0, o1);
+  }
+}
+
+// The same lambda (+)= H psi for complex128 states of 2^kDfMinQubits amplitudes or more
+// in double-float arithmetic: amplitudes split into FP32 pairs, each X mask's signed
+// coefficient sum added with TwoSum, its product with psi and the sum over masks as
+// packed double-float terms, lambda joined back to binary64.
+__global__ void __launch_bounds__(256) k_apply_hsum_df(const double* __restrict__ psi, double* __restrict__ lam,
+                                                       uint64_t N, HGroup g) {
+  const uint64_t stride = uint64_t(gridDim.x) * blockDim.x;
+  for (uint64_t it = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; it < N / 2; it += stride) {
+    const uint64_t k = 2 * it;
+    DF2Acc o0{make_float2(0.0f, 0.0f), make_float2(0.0f, 0.0f)}, o1 = o0;
+    if (!g.first) {
+      Cplx<double> a, b;
+      ld_amp2<double>(lam, k, a, b);
+      const DFC A = dfc_of(a), B = dfc_of(b);
+      o0 = DF2Acc{A.hi, A.lo};
+      o1 = DF2Acc{B.hi, B.lo};
+    }
+    int t = 0;
+    while (t < g.nt) {
+      const uint64_t x = g.x[t];
+      const uint64_t j0 = k ^ x;
+      Cplx<double> a, b;
+      ld_amp2<double>(psi, j0 & ~uint64_t(1), a, b);
+      const DFC p0 = dfc_of((x & 1) ? b : a), p1 = dfc_of((x & 1) ? a : b);
+      DF2Acc f0, f1;
+      bool first = true;
+      do {
+        const float2 ch = make_float2(g.fre[t], g.fim[t]), cl = make_float2(g.lre[t], g.lim[t]);
+        const float2 nh = make_float2(-ch.x, -ch.y), nl = make_float2(-cl.x, -cl.y);
+        const bool s0 = __popcll(j0 & g.z[t]) & 1;
+        const bool s1 = s0 ^ bool(g.z[t] & 1);
+        if (first) {
+          f0 = DF2Acc{s0 ? nh : ch, s0 ? nl : cl};
+          f1 = DF2Acc{s1 ? nh : ch, s1 ? nl : cl};
+          first = false;
+        } else {
+          df2_add(f0, s0 ? nh : ch, s0 ? nl : cl);
+          df2_add(f1, s1 ? nh : ch, s1 ? nl : cl);
+        }
+      } while (++t < g.nt && g.x[t] == x);
+      const DF2 c0 = df2_result(f0), c1 = df2_result(f1);
+      // o += c p: lanes (c.re, c.re) (p.re, p.im) + (-c.im, c.im) (p.im, p.re)
+      df2_mac(o0, make_float2(c0.hi.x, c0.hi.x), make_float2(-c0.hi.x, -c0.hi.x), make_float2(c0.lo.x, c0.lo.x), dfc_x(p0));
+      df2_mac(o0, make_float2(-c0.hi.y, c0.hi.y), make_float2(c0.hi.y, -c0.hi.y), make_float2(-c0.lo.y, c0.lo.y), dfc_sw(p0));
+      df2_mac(o1, make_float2(c1.hi.x, c1.hi.x), make_float2(-c1.hi.x, -c1.hi.x), make_float2(c1.lo.x, c1.lo.x), dfc_x(p1));
+      df2_mac(o1, make_float2(-c1.hi.y, c1.hi.y), make_float2(c1.hi.y, -c1.hi.y), make_float2(-c1.lo.y, c1.lo.y), dfc_sw(p1));
+    }
+    const DF2 r0 = df2_result(o0), r1 = df2_result(o1);
+    st_amp2<double>(lam, k, Cplx<double>{df_join(r0.hi.x, r0.lo.x), df_join(r0.hi.y, r0.lo.y)},
+                    Cplx<double>{df_join(r1.hi.x, r1.lo.x), df_join(r1.hi.y, r1.lo.y)});
   }
 }
 
@@ -360,8 +415,14 @@ static qc_status adjoint_impl(const qc_circuit* c, const double* params, int npa
         hg.cim[j] = ny == 1 ? cf : ny == 3 ? -cf : 0.0;
         hg.fre[j] = float(hg.cre[j]);
         hg.fim[j] = float(hg.cim[j]);
+        hg.lre[j] = float(hg.cre[j] - double(hg.fre[j]));
+        hg.lim[j] = float(hg.cim[j] - double(hg.fim[j]));
       }
-      QC_COUNT(), k_apply_hsum<R><<<g2, B, 0, stream>>>(reinterpret_cast<const R*>(s.amps), lam, N, hg);
+      if (sizeof(R) == 8 && n >= kDfMinQubits)
+        QC_COUNT(), k_apply_hsum_df<<<g2, B, 0, stream>>>(reinterpret_cast<const double*>(s.amps),
+                                                          reinterpret_cast<double*>(lam), N, hg);
+      else
+        QC_COUNT(), k_apply_hsum<R><<<g2, B, 0, stream>>>(reinterpret_cast<const R*>(s.amps), lam, N, hg);
     }
     if (first) {  // empty Hamiltonian
       cudaMemsetAsync(lam, 0, sbytes, stream);

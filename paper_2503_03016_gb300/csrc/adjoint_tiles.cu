@@ -321,15 +321,6 @@ __global__ void __launch_bounds__(NT, 1) k_adj_pass(R* __restrict__ psi, R* __re
 // ---------------------------------------------------------------------------
 // complex128 in double-float arithmetic (states of 2^kDfMinQubits amplitudes or more)
 // ---------------------------------------------------------------------------
-// (hi, lo) scalar sums
-__device__ __forceinline__ float2 dfs_add(float2 a, float2 b) {
-  const float s = __fadd_rn(a.x, b.x);
-  const float bb = __fsub_rn(s, a.x);
-  float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
-  e = __fadd_rn(e, __fadd_rn(a.y, b.y));
-  const float hi = __fadd_rn(s, e);
-  return make_float2(hi, __fsub_rn(e, __fsub_rn(hi, s)));
-}
 // the sum of the two lanes of a packed double-float result
 __device__ __forceinline__ float2 df_lane_total(const DF2& r) {
   return dfs_add(make_float2(r.hi.x, r.lo.x), make_float2(r.hi.y, r.lo.y));

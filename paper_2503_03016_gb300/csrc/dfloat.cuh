@@ -148,6 +148,21 @@ __device__ __forceinline__ double df_join(float hi, float lo) {
   return df_join_general(hi, lo);
 }
 
+// scalar double-float sums: a = (hi, lo).  dfs_add renormalises its result; dfs_acc
+// (a += b without renormalising: TwoSum of the hi parts, the lo parts and the error
+// added into lo) serves chains whose result is renormalised once at the end.
+__device__ __forceinline__ float2 dfs_renorm(float2 a) {
+  const float hi = __fadd_rn(a.x, a.y);
+  return make_float2(hi, __fsub_rn(a.y, __fsub_rn(hi, a.x)));
+}
+__device__ __forceinline__ float2 dfs_acc(float2 a, float2 b) {
+  const float s = __fadd_rn(a.x, b.x);
+  const float bb = __fsub_rn(s, a.x);
+  const float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+  return make_float2(s, __fadd_rn(e, __fadd_rn(a.y, b.y)));
+}
+__device__ __forceinline__ float2 dfs_add(float2 a, float2 b) { return dfs_renorm(dfs_acc(a, b)); }
+
 // ---------------------------------------------------------------------------
 // packed pairs: lane x and lane y are two independent double-floats
 // ---------------------------------------------------------------------------
@@ -189,6 +204,16 @@ __device__ __forceinline__ void df2_mac(DF2Acc& a, float2 xh, float2 nxh, float2
   const float2 err = __fadd2_rn(df2_sub(a.s, df2_sub(s, bb)), df2_sub(p, bb));
   a.s = s;
   a.c = __fadd2_rn(c, err);
+}
+
+// a += h + l for a double-float pair (h, l): TwoSum of the running sum and h, the error
+// and l into the error sum
+__device__ __forceinline__ void df2_add(DF2Acc& a, float2 h, float2 l) {
+  const float2 s = __fadd2_rn(a.s, h);
+  const float2 bb = df2_sub(s, a.s);
+  const float2 err = __fadd2_rn(df2_sub(a.s, df2_sub(s, bb)), df2_sub(h, bb));
+  a.s = s;
+  a.c = __fadd2_rn(a.c, __fadd2_rn(err, l));
 }
 
 // s + c renormalised by TwoSum: hi = fl(s + c) and lo its exact error

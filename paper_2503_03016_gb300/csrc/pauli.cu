@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "dfloat.cuh"
 #include "kernels.cuh"
 
 namespace qcgb {
@@ -189,6 +190,73 @@ __global__ void __launch_bounds__(kZBlock) k_pauli_z(const R* __restrict__ amps,
   }
 }
 
+// The same Z strings for complex128 states of 2^kDfMinQubits amplitudes or more in
+// double-float arithmetic: p_l = re^2 + im^2 from the FP32 pairs of the amplitude (the
+// squares of the hi parts exact by TwoProduct, the cross terms 2 hi lo rounded, lo^2
+// left out), the Walsh-Hadamard transform and the per-thread term sums as (hi, lo) pairs
+// with TwoSum; block and cross-block sums in FP64 as for the other kernels.
+__global__ void __launch_bounds__(kZBlock) k_pauli_z_df(const double* __restrict__ amps, uint64_t N, ZGroup g,
+                                                        double* __restrict__ partials) {
+  __shared__ float2 S[32][kZBlock];
+  float2 acc[kMaxZTerms];
+#pragma unroll
+  for (int t = 0; t < kMaxZTerms; ++t) acc[t] = make_float2(0.0f, 0.0f);
+  const int h = g.hshift;
+  const uint64_t nchunk = N >> 5;
+  const uint64_t nvb = uint64_t(1) << (g.kbits_base - 7);
+  for (uint64_t vb = blockIdx.x; vb < nvb; vb += gridDim.x) {
+    const uint64_t gt = vb * kZBlock + threadIdx.x;
+    if (gt >= nchunk) continue;
+    uint32_t sign = 0;
+#pragma unroll
+    for (int t = 0; t < kMaxZTerms; ++t)
+      if (t < g.nt) sign |= uint32_t(__popcll(gt & g.z[t]) & 1) << t;
+    const uint64_t nk = uint64_t(1) << g.kbits;
+    for (uint64_t j = 0; j < nk; ++j) {
+      const uint64_t k = j ^ (j >> 1);  // Gray code
+      const uint64_t c = gt + (k << g.kbits_base);
+      float2 w[32];
+#pragma unroll
+      for (int l = 0; l < 32; ++l) {
+        const Cplx<double> x = ld_amp<double>(amps, (uint64_t(l) << h) | c);
+        float rh, rl, ih, il;
+        df_split(x.re, rh, rl);
+        df_split(x.im, ih, il);
+        const float pr = __fmul_rn(rh, rh), pi = __fmul_rn(ih, ih);
+        float er = __fmaf_rn(rh, rh, -pr), ei = __fmaf_rn(ih, ih, -pi);
+        er = __fmaf_rn(__fadd_rn(rh, rh), rl, er);
+        ei = __fmaf_rn(__fadd_rn(ih, ih), il, ei);
+        w[l] = dfs_acc(make_float2(pr, er), make_float2(pi, ei));
+      }
+      // in-place Walsh-Hadamard transform over the 5 top bits
+#pragma unroll
+      for (int hb = 1; hb < 32; hb <<= 1)
+#pragma unroll
+        for (int l = 0; l < 32; ++l)
+          if (!(l & hb)) {
+            const float2 a = w[l], b = w[l | hb];
+            w[l] = dfs_acc(a, b);
+            w[l | hb] = dfs_acc(a, make_float2(-b.x, -b.y));
+          }
+#pragma unroll
+      for (int l = 0; l < 32; ++l) S[l][threadIdx.x] = dfs_renorm(w[l]);
+#pragma unroll
+      for (int t = 0; t < kMaxZTerms; ++t) {
+        if (t >= g.nt) break;
+        const float2 v = S[g.z[t] >> h][threadIdx.x];
+        acc[t] = dfs_acc(acc[t], ((sign >> t) & 1u) ? make_float2(-v.x, -v.y) : v);
+      }
+      if (j + 1 < nk) sign ^= g.flip[__ffsll((long long)(j + 1)) - 1];
+    }
+  }
+#pragma unroll
+  for (int t = 0; t < kMaxZTerms; ++t) {
+    if (t >= g.nt) break;
+    const double v = block_sum(double(acc[t].x) + double(acc[t].y));
+    if (threadIdx.x == 0) partials[size_t(blockIdx.x) * kMaxZTerms + t] = v;
+  }
+}
+
 // Cross-block sums, one block per term (grid = number of terms): each block adds its
 // term's block partials in a fixed order.
 __global__ void __launch_bounds__(256) k_sum_zterms(const double* partials, int nblocks, ZGroup g, double* out) {
@@ -234,20 +302,23 @@ qc_status parse_pauli(int n, const char* str, ParsedTerm* out) {
   return QC_OK;
 }
 
-// Resident k_pauli_z blocks per SM (1..32), queried once per (dtype, device).
-static int z_blocks_per_sm(bool c64, int device) {
+// Resident k_pauli_z blocks per SM (1..32), queried once per (kernel, device): kind 0
+// complex64, 1 complex128 in FP64, 2 complex128 in double-float.
+static int z_blocks_per_sm(int kind, int device) {
   static std::mutex mu;
-  static std::map<std::pair<bool, int>, int> cache;
+  static std::map<std::pair<int, int>, int> cache;
   std::lock_guard<std::mutex> lock(mu);
-  auto it = cache.find({c64, device});
+  auto it = cache.find({kind, device});
   if (it != cache.end()) return it->second;
   int per_sm = 0;
-  if (c64)
+  if (kind == 0)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pauli_z<float>, kZBlock, 0);
-  else
+  else if (kind == 1)
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pauli_z<double>, kZBlock, 0);
+  else
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pauli_z_df, kZBlock, 0);
   per_sm = std::min(std::max(per_sm, 1), 32);
-  cache[{c64, device}] = per_sm;
+  cache[{kind, device}] = per_sm;
   return per_sm;
 }
 
@@ -260,7 +331,7 @@ static void launch_z_strings(qc_state* s, const uint64_t* z, const int* slot, in
   const uint64_t N = state_len(s);
   const int cbits = s->n - 5;  // log2 of the chunk count
   const int K = std::max(7, std::min(cbits, kZMaxThreadBits));
-  const int per_sm = z_blocks_per_sm(s->dtype == QC_C64, s->device);
+  const int per_sm = z_blocks_per_sm(s->dtype == QC_C64 ? 0 : s->n >= kDfMinQubits ? 2 : 1, s->device);
   uint64_t gz = std::min<uint64_t>(uint64_t(1) << (K - 7), uint64_t(per_sm) * device_sm_count());
   gz = std::max<uint64_t>(1, std::min<uint64_t>(gz, max_blocks));
   for (int beg = 0; beg < nt; beg += kMaxZTerms) {
@@ -278,6 +349,9 @@ static void launch_z_strings(qc_state* s, const uint64_t* z, const int* slot, in
     if (s->dtype == QC_C64)
       QC_COUNT(), k_pauli_z<float><<<unsigned(gz), kZBlock, 0, s->stream>>>(reinterpret_cast<const float*>(s->amps),
                                                                           N, zg, part);
+    else if (s->n >= kDfMinQubits)
+      QC_COUNT(), k_pauli_z_df<<<unsigned(gz), kZBlock, 0, s->stream>>>(reinterpret_cast<const double*>(s->amps), N,
+                                                                       zg, part);
     else
       QC_COUNT(), k_pauli_z<double><<<unsigned(gz), kZBlock, 0, s->stream>>>(reinterpret_cast<const double*>(s->amps),
                                                                            N, zg, part);

@@ -24,6 +24,13 @@ __device__ __forceinline__ DFC dfc_slots(const double* s) {
   const float4 t = *reinterpret_cast<const float4*>(s);  // re_hi, re_lo, im_hi, im_lo
   return DFC{make_float2(t.x, t.z), make_float2(t.y, t.w)};
 }
+// a binary64 complex value split into a double-float one
+__device__ __forceinline__ DFC dfc_of(const Cplx<double>& z) {
+  float rh, rl, ih, il;
+  df_split(z.re, rh, rl);
+  df_split(z.im, ih, il);
+  return DFC{make_float2(rh, ih), make_float2(rl, il)};
+}
 // a real value from one slot: (hi, lo)
 __device__ __forceinline__ float2 dfr_slot(const double* s) { return *reinterpret_cast<const float2*>(s); }
 
