@@ -700,10 +700,12 @@ void emit_pass(const BuiltPass& bp0, const std::vector<PlanOp>& pops0, int n, in
     TileStage st = recs[si];
     st.op0 = int(hp.ops.size()) - P.op0;
     const size_t j = take.size();
-    // a CZ: the phase pi on b_t b_c keyed on its target t (no constant, no tag)
+    // a CZ: the phase pi (or -pi: the same factor -1, e.g. a daggered CZ whose matrix
+    // carries -0 imaginary parts) on b_t b_c keyed on its target t (no constant, no tag)
     auto is_cz = [&](const PlanOp& o) {
-      return o.phase && o.grad < 0 && o.c == 0.0 && o.beta.size() == 1 && o.beta[0].second == M_PI &&
-             o.cmask == o.cval && __builtin_popcountll(o.cmask) == 1;
+      return o.phase && o.grad < 0 && o.c == 0.0 && o.beta.size() == 1 &&
+             (o.beta[0].second == M_PI || o.beta[0].second == -M_PI) && o.cmask == o.cval &&
+             __builtin_popcountll(o.cmask) == 1;
     };
     // code of one end of a CZ pair in this stage: 0x80 | slot, a lane bit (< 16), or
     // 0x40 | global bit for a bit fixed by the tile number
