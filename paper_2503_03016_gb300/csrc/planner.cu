@@ -63,6 +63,8 @@ __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const
   TileStage* sst = reinterpret_cast<TileStage*>(tnt + kTileNumberTab);
   TileOp* sop = reinterpret_cast<TileOp*>(sst + P.nstages);
   R* smat = reinterpret_cast<R*>(sop + P.nops);
+  // the pass's phase tables (16-byte aligned after the matrices), when they fit
+  R* spool = reinterpret_cast<R*>(smat + ((P.nmat + 3) & ~3));
   // the tile's bit positions in shared memory (a dynamically indexed kernel parameter
   // array would be copied to local memory)
   __shared__ int8_t sbits[16], srbit[16];
@@ -99,9 +101,13 @@ __global__ void __launch_bounds__(NT, 1) k_tile_pass(R* __restrict__ amps, const
   for (int i = threadIdx.x; i < P.nstages; i += blockDim.x) sst[i] = stages[P.stage0 + i];
   for (int i = threadIdx.x; i < P.nops; i += blockDim.x) sop[i] = ops[P.op0 + i];
   for (int i = threadIdx.x; i < P.nmat; i += blockDim.x) smat[i] = mats[P.mat0 + i];
+  if (P.spool)
+    for (int i = threadIdx.x; i < P.npool; i += blockDim.x) spool[i] = pool[P.pool0 + i];
   __syncthreads();
   const uint32_t lowmask = (1u << L) - 1;
-  const Cplx<R>* cpool = reinterpret_cast<const Cplx<R>*>(pool);
+  // table offsets (op.tab) count complex entries from the start of the pool
+  const Cplx<R>* cpool = P.spool ? reinterpret_cast<const Cplx<R>*>(spool) - P.pool0 / 2
+                                 : reinterpret_cast<const Cplx<R>*>(pool);
   uint64_t t = blockIdx.x;
   if (t < P.ntiles) prefetch_tile<R>(bufs, amps, tile_base(t, tnt), hioff, L, T);
   cp_async_commit();
@@ -681,6 +687,8 @@ void emit_pass(const BuiltPass& bp0, const std::vector<PlanOp>& pops0, int n, in
   P.stage0 = int(hp.stages.size());
   P.op0 = int(hp.ops.size());
   P.mat0 = int(hp.mats.size());
+  while (hp.pool.size() % 2) hp.pool.push_back(R(0));
+  P.pool0 = int(hp.pool.size());
   int local_of[64];
   for (int b = 0; b < 64; ++b) local_of[b] = -1;
   for (int i = 0; i < m; ++i) local_of[bp.B[i]] = i;
@@ -957,6 +965,7 @@ void emit_pass(const BuiltPass& bp0, const std::vector<PlanOp>& pops0, int n, in
   P.nstages = int(hp.stages.size()) - P.stage0;
   P.nops = int(hp.ops.size()) - P.op0;
   P.nmat = int(hp.mats.size()) - P.mat0;
+  P.npool = int(hp.pool.size()) - P.pool0;
   hp.passes.push_back(P);
 }
 
@@ -1051,11 +1060,19 @@ static qc_status run_tiles(qc_state* s, const std::vector<ResolvedOp>& rops, int
   const R* dpool = reinterpret_cast<const R*>(base + sb + ob);
   const R* dmats = reinterpret_cast<const R*>(base + sb + ob + pb);
   const int threads = 1 << (m - SB);
+  const size_t fixed_smem = 2 * sizeof(Cplx<R>) * (size_t(1) << m) +
+                            (sizeof(uint64_t) + sizeof(uint32_t)) * (size_t(1) << (m - L)) +
+                            sizeof(uint64_t) * kTileNumberTab;
+  // a pass's phase tables go to shared memory where they fit beside the tiles (the
+  // tiles' copies stream through L1 and would evict them there)
   size_t plan_max = 0;
-  for (const TilePass& P : hp.passes)
-    plan_max = std::max(plan_max, P.nstages * sizeof(TileStage) + P.nops * sizeof(TileOp) + P.nmat * sizeof(R));
-  const size_t smem = 2 * sizeof(Cplx<R>) * (size_t(1) << m) + (sizeof(uint64_t) + sizeof(uint32_t)) * (size_t(1) << (m - L)) +
-                      sizeof(uint64_t) * kTileNumberTab + plan_max;
+  for (TilePass& P : hp.passes) {
+    const size_t plan = P.nstages * sizeof(TileStage) + P.nops * sizeof(TileOp) + ((P.nmat + 3) & ~3) * sizeof(R);
+    const size_t with_pool = plan + size_t(P.npool) * sizeof(R);
+    P.spool = P.npool > 0 && fixed_smem + with_pool <= kTileSmemBudget ? 1 : 0;
+    plan_max = std::max(plan_max, P.spool ? with_pool : plan);
+  }
+  const size_t smem = fixed_smem + plan_max;
   constexpr int NT = TileShape<R>::NT;
   bool extops = false;
   for (const TileOp& op : hp.ops)
