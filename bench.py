@@ -411,7 +411,7 @@ def run_ours(args):
                 "traffic": traffic, "traffic_note": "per pass, ncu at 26 qubits scaled by 2^(n-26)",
                 "algorithmic_bytes_per_pass": 2 * sbytes, "hbm_gbs_over_passes": passes * 2 * sbytes / (circ_ms * 1e-3) / 1e9,
                 "peak_source": "152 SMs x 128 FP32 lanes x 2 flops x %.0f MHz" % sm_mhz,
-                "kernel": "k_tile_pass<float,256,5>", "passes": passes}
+                "kernel": "k_tile_pass<float,512,4>", "passes": passes}
     else:
         algo_bytes = len(ops) * 2 * sbytes
         achieved = algo_bytes / (circ_ms * 1e-3) / 1e9

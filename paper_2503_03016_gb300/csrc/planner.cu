@@ -14,8 +14,8 @@
 // the same condition are merged into one phase op exp(i (c + sum_p beta_p b_p)).
 //
 // Inside a pass the gates are split into stages; in a stage every thread holds 2^SB
-// amplitudes spanning SB of the tile's bits in registers (SB = 5 for complex64, 4 for
-// complex128) and applies all of the stage's gates to them before writing back to
+// amplitudes spanning SB of the tile's bits in registers (SB = 4 for both precisions;
+// 3 for the double-float complex128 passes) and applies all of the stage's gates to them before writing back to
 // shared memory.  Shared memory is
 // addressed through an XOR swizzle so that the strided accesses of a stage do not
 // collide in the same bank.
@@ -1007,7 +1007,10 @@ template <typename R>
 struct TileShape;
 template <>
 struct TileShape<float> {
-  static constexpr int SB = 5, NT = 256;
+  // 2^4 amplitudes per thread with 512 threads (108 registers, 16 warps per SM): the
+  // QFT-32 passes 259 -> 240 ms against 2^5 with 256 threads (230 registers, 8 warps),
+  // the Haar brickwork and the adjoint's forward passes unchanged
+  static constexpr int SB = 4, NT = 512;
 };
 template <>
 struct TileShape<double> {

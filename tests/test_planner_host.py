@@ -34,6 +34,7 @@ def test_controlled_swap_is_not_a_relabeling():
 
 
 def test_brickwork_plan_is_stable():
-    """The 28-qubit Haar brickwork: 24 passes, 105 register stages, 540 ops (complex64)."""
+    """The 28-qubit Haar brickwork: 24 passes, 153 register stages of 4 bits, 540 ops
+    (complex64)."""
     import paper_2503_03016_gb300 as P
-    assert plan(28, W.brickwork(28, 40, 2), P.QC_C64) == (24, 105, 540)
+    assert plan(28, W.brickwork(28, 40, 2), P.QC_C64) == (24, 153, 540)
