@@ -404,9 +404,9 @@ def run_ours(args):
         sm_mhz = (clk.get("sm_mhz") or 2070.0) if isinstance(clk, dict) else 2070.0
         peak = torch.cuda.get_device_properties(0).multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
         achieved = flops / (circ_ms * 1e-3) / 1e12
-        # DRAM bytes of one tile pass in an ncu capture at 26 qubits (1012.94 MB), scaled
-        # by the larger state (a pass moves the state once each way)
-        traffic = 1012.936448e6 * (1 << (N_QUBITS - 26))
+        # DRAM bytes of one tile pass in an ncu capture at 26 qubits (537.43 + 476.53 MB),
+        # scaled by the larger state (a pass moves the state once each way)
+        traffic = 1013.959168e6 * (1 << (N_QUBITS - 26))
         roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "traffic_note": "per pass, ncu at 26 qubits scaled by 2^(n-26)",
                 "algorithmic_bytes_per_pass": 2 * sbytes, "hbm_gbs_over_passes": passes * 2 * sbytes / (circ_ms * 1e-3) / 1e9,
