@@ -536,9 +536,10 @@ def run_batch_general_bench(args):
 
 
 def run_block_bench(args):
-    """Opt-in secondary measurement: one dense 5-qubit block (Haar 32x32) and one dense
-    6-qubit block (Haar 64x64) on a 28-qubit complex64 state, CUDA-core FMA (k_kq_native)
-    vs tensor cores (TF32x3: k_block_tc, k_block_tc6)."""
+    """Opt-in secondary measurement: a dense 5-qubit block (Haar 32x32) on spread qubits
+    and on index bits 10..14, and a dense 6-qubit block (Haar 64x64), on a 28-qubit
+    complex64 state, CUDA-core FMA (k_kq_native) vs tensor cores (TF32x3: the one-stage
+    tile pass with box copies where the block's tile allows, else k_block_tc; k_block_tc6)."""
     import torch
 
     import paper_2503_03016_gb300 as P
@@ -549,7 +550,11 @@ def run_block_bench(args):
     st = P.State(n, "c64").init_gaussian(7)
     stream = torch.cuda.current_stream()
     res = {}
-    for k, qs in ((5, [3, 9, 14, 20, n - 2]), (6, [3, 9, 14, 20, 23, n - 2])):
+    # spread qubits (index bits 24, 18, 13, 7, 1 at 28 qubits) and a block on index bits
+    # 10..14
+    cases = (("k5", 5, [3, 9, 14, 20, n - 2]), ("k5_mid", 5, [n - 15 + j for j in range(5)]),
+             ("k6", 6, [3, 9, 14, 20, 23, n - 2]))
+    for label, k, qs in cases:
         U = W.haar_unitaries(1, 1 << k, 11)[0]
         for name, prec in (("native", P.QC_PREC_NATIVE), ("tf32x3", P.QC_PREC_TF32X3)):
             for _ in range(max(args.warmup, 1)):
@@ -569,7 +574,7 @@ def run_block_bench(args):
                 r["frac_tf32"] = tf / tf32_pk
             else:
                 r["frac_alu"] = tf / ALU_PEAK_TF
-            res["k%d_%s" % (k, name)] = r
+            res["%s_%s" % (label, name)] = r
     print(json.dumps({"metric": "fused 5- and 6-qubit blocks on %d qubits" % n, "results": res,
                       "peaks": {"hbm_gbs": hbm, "tf32_tflops": tf32_pk, "alu_tflops": ALU_PEAK_TF,
                                 "tf32_source": TF32_PEAK_SRC}}))

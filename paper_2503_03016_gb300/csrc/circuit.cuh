@@ -41,5 +41,10 @@ qc_status run_fused(qc_state* s, const qc_circuit* c, const double* params, qc_p
 qc_status run_tiles_tc(qc_state* s, const std::vector<ResolvedOp>& rops, bool* handled);
 qc_status apply_kq_native(qc_state* s, const int* bits, int k, const double* U);
 qc_status apply_kq_tf32x3(qc_state* s, const int* bits, int k, const double* U);
+// a dense block of k <= 5 qubits (bits[0] the most significant bit of U's index) as one
+// tensor-core tile pass of a single stage whose tiles move as boxes; *handled is false
+// (nothing applied) where it does not apply (complex128, fewer than 12 qubits, a tile
+// of more than 5 runs of index bits)
+qc_status apply_block_tile_tc(qc_state* s, const int* bits, int k, const double* U, bool* handled);
 
 }  // namespace qcgb

@@ -420,6 +420,9 @@ qc_status apply_kq_tf32x3(qc_state* s, const int* bits, int k, const double* U) 
     set_error("TF32x3 blocks need complex64, k <= %d and n >= %d", kTcK, kTcK + 7);
     return QC_ERR_UNSUPPORTED;
   }
+  bool handled = false;
+  if (qc_status st = apply_block_tile_tc(s, bits, k, U, &handled)) return st;
+  if (handled) return QC_OK;
   // pad with the lowest bits not in the block: U5 = U (x) I on (bits..., extra...)
   int b5[kTcK];
   for (int j = 0; j < k; ++j) b5[j] = bits[j];

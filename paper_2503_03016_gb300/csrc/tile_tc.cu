@@ -667,6 +667,60 @@ static float tf32_rne_host(float v) {
   return r;
 }
 
+// One stage's record and B image from its 32 x 32 block U (U[row * 32 + col], row and
+// column bit k = slot k) and its layout rec.
+static void tc_stage_record(const std::vector<cd>& U, const TileStage& rec, bool tma, std::vector<TcStage>& out,
+                            std::vector<float>& imgs) {
+  constexpr int D = 1 << kTtSB;
+  // B image: Bt[n][k] (n = output column, k = input column) of the real form,
+  // y_d = sum_c U[d][c] x_c; hi region then lo region, each in the swizzled layout
+  TcStage ts{};
+  ts.img = int32_t(imgs.size() / kTtImgFloats);
+  const size_t o0 = imgs.size();
+  imgs.resize(o0 + kTtImgFloats, 0.0f);
+  float* hi = imgs.data() + o0;
+  float* lo = hi + kTtImgFloats / 2;
+  for (int d = 0; d < D; ++d)
+    for (int c = 0; c < D; ++c) {
+      const double ur = U[d * D + c].real(), ui = U[d * D + c].imag();
+      const double vals[4] = {ur, -ui, ui, ur};
+      const int ns[4] = {2 * d, 2 * d, 2 * d + 1, 2 * d + 1};
+      const int ks[4] = {2 * c, 2 * c + 1, 2 * c, 2 * c + 1};
+      for (int e = 0; e < 4; ++e) {
+        const float v = float(vals[e]), h = tf32_rne_host(v);
+        const uint32_t off = sw128_offset(ns[e], ks[e], kTtCols) / 4;
+        hi[off] = h;
+        lo[off] = tf32_rne_host(v - h);
+      }
+    }
+  for (int k = 0; k < kTtSB; ++k)
+    ts.swz[k] = tma ? tma_swz_bytes(1u << rec.slot_bit[k]) : tile_swz_host(1u << rec.slot_bit[k]) * 8u;
+  for (int k = 0; k < kTtM - kTtSB; ++k) ts.lane_bit[k] = rec.lane_bit[k];
+  if (tma) {
+    // With the 128-byte swizzle, local bit p moves an 8-byte access to bank slot bit
+    // (p = 0: 0; 1..3: p; 4..6: p - 3; 7 and up: none).  Rows are a warp's lanes, so
+    // the first four row bits take one bit of each of these classes where the
+    // stage's slots leave one (a half warp then reads 16 distinct slots).
+    int8_t order[kTtM - kTtSB];
+    bool used[kTtM - kTtSB] = {false};
+    int no = 0;
+    for (int cls = 0; cls < 4; ++cls)
+      for (int k = 0; k < kTtM - kTtSB; ++k) {
+        const int p = rec.lane_bit[k];
+        const int c = p == 0 ? 0 : p <= 3 ? p : p <= 6 ? p - 3 : -1;
+        if (!used[k] && c == cls) {
+          used[k] = true;
+          order[no++] = int8_t(p);
+          break;
+        }
+      }
+    for (int k = 0; k < kTtM - kTtSB; ++k)
+      if (!used[k]) order[no++] = rec.lane_bit[k];
+    for (int k = 0; k < kTtM - kTtSB; ++k) ts.lane_bit[k] = order[k];
+  }
+  out.push_back(ts);
+}
+
 // The stages of one pass as 32 x 32 blocks and their B images; false if an op of a
 // stage depends on a bit outside the stage's slots (a control or a phase bit elsewhere).
 static bool tc_pass_blocks(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, bool tma,
@@ -739,53 +793,7 @@ static bool tc_pass_blocks(const BuiltPass& bp, const std::vector<PlanOp>& pops,
         }
       }
     }
-    // B image: Bt[n][k] (n = output column, k = input column) of the real form,
-    // y_d = sum_c U[d][c] x_c; hi region then lo region, each in the swizzled layout
-    TcStage ts{};
-    ts.img = int32_t(imgs.size() / kTtImgFloats);
-    const size_t o0 = imgs.size();
-    imgs.resize(o0 + kTtImgFloats, 0.0f);
-    float* hi = imgs.data() + o0;
-    float* lo = hi + kTtImgFloats / 2;
-    for (int d = 0; d < D; ++d)
-      for (int c = 0; c < D; ++c) {
-        const double ur = U[d * D + c].real(), ui = U[d * D + c].imag();
-        const double vals[4] = {ur, -ui, ui, ur};
-        const int ns[4] = {2 * d, 2 * d, 2 * d + 1, 2 * d + 1};
-        const int ks[4] = {2 * c, 2 * c + 1, 2 * c, 2 * c + 1};
-        for (int e = 0; e < 4; ++e) {
-          const float v = float(vals[e]), h = tf32_rne_host(v);
-          const uint32_t off = sw128_offset(ns[e], ks[e], kTtCols) / 4;
-          hi[off] = h;
-          lo[off] = tf32_rne_host(v - h);
-        }
-      }
-    for (int k = 0; k < kTtSB; ++k)
-      ts.swz[k] = tma ? tma_swz_bytes(1u << recs[si].slot_bit[k]) : tile_swz_host(1u << recs[si].slot_bit[k]) * 8u;
-    for (int k = 0; k < kTtM - kTtSB; ++k) ts.lane_bit[k] = recs[si].lane_bit[k];
-    if (tma) {
-      // With the 128-byte swizzle, local bit p moves an 8-byte access to bank slot bit
-      // (p = 0: 0; 1..3: p; 4..6: p - 3; 7 and up: none).  Rows are a warp's lanes, so
-      // the first four row bits take one bit of each of these classes where the
-      // stage's slots leave one (a half warp then reads 16 distinct slots).
-      int8_t order[kTtM - kTtSB];
-      bool used[kTtM - kTtSB] = {false};
-      int no = 0;
-      for (int cls = 0; cls < 4; ++cls)
-        for (int k = 0; k < kTtM - kTtSB; ++k) {
-          const int p = recs[si].lane_bit[k];
-          const int c = p == 0 ? 0 : p <= 3 ? p : p <= 6 ? p - 3 : -1;
-          if (!used[k] && c == cls) {
-            used[k] = true;
-            order[no++] = int8_t(p);
-            break;
-          }
-        }
-      for (int k = 0; k < kTtM - kTtSB; ++k)
-        if (!used[k]) order[no++] = recs[si].lane_bit[k];
-      for (int k = 0; k < kTtM - kTtSB; ++k) ts.lane_bit[k] = order[k];
-    }
-    out.push_back(ts);
+    tc_stage_record(U, recs[si], tma, out, imgs);
   }
   return true;
 }
@@ -964,6 +972,33 @@ static qc_status tc_plan(qc_state* s, const std::vector<ResolvedOp>& rops, int d
   return QC_OK;
 }
 
+// the shared-memory opt-in of both pass kernels
+static qc_status tc_pass_smem() {
+  for (auto kern : {k_tile_pass_tc<false>, k_tile_pass_tc<true>})
+    if (qc_status st = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       int(kTtSmem)),
+                                  "tensor-core tile pass shared memory"))
+      return st;
+  return QC_OK;
+}
+
+// one pass on s's stream: box copies with a tensor map of this state where tm.tma
+static qc_status launch_tc_pass(qc_state* s, const TilePass& P, const TcTma& tm, const TcStage* dst, const float* dimg,
+                                int* status, const TcNorm& nm, unsigned grid) {
+  alignas(64) CUtensorMap map;
+  memset(&map, 0, sizeof(map));
+  if (tm.tma && !encode_tile_map(&map, tm, s->amps, s->n)) {
+    set_error("tensor-core tile pass: tensor map encoding failed");
+    return QC_ERR_CUDA;
+  }
+  float* a = reinterpret_cast<float*>(s->amps);
+  if (tm.tma)
+    QC_COUNT(), k_tile_pass_tc<true><<<grid, kTtThreads, kTtSmem, s->stream>>>(a, P, dst, dimg, status, map, tm, nm);
+  else
+    QC_COUNT(), k_tile_pass_tc<false><<<grid, kTtThreads, kTtSmem, s->stream>>>(a, P, dst, dimg, status, map, tm, nm);
+  return QC_OK;
+}
+
 qc_status run_tiles_tc(qc_state* s, const std::vector<ResolvedOp>& rops, bool* handled) {
   *handled = false;
   const int n = s->n;
@@ -990,23 +1025,11 @@ qc_status run_tiles_tc(qc_state* s, const std::vector<ResolvedOp>& rops, bool* h
   const TcStage* dst = static_cast<const TcStage*>(g_tc.dev);
   const float* dimg = reinterpret_cast<const float*>(static_cast<char*>(g_tc.dev) + g_tc.stage_bytes);
   if (qc_status st = check_cuda(cudaMemsetAsync(status, 0, sizeof(int), s->stream), "status reset")) return st;
-  for (auto kern : {k_tile_pass_tc<false>, k_tile_pass_tc<true>})
-    if (qc_status st = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                       int(kTtSmem)),
-                                  "tensor-core tile pass shared memory"))
-      return st;
+  if (qc_status st = tc_pass_smem()) return st;
   const uint64_t ntiles = uint64_t(1) << (n - kTtM);
   // one CTA per SM, two tiles in flight per CTA
   const unsigned grid = unsigned(std::min<uint64_t>((ntiles + 1) / 2, uint64_t(device_sm_count())));
-  float* a = reinterpret_cast<float*>(s->amps);
   for (size_t i = 0; i < g_tc.passes.size(); ++i) {
-    alignas(64) CUtensorMap map;
-    memset(&map, 0, sizeof(map));
-    const TcTma& tm = g_tc.tmas[i];
-    if (tm.tma && !encode_tile_map(&map, tm, s->amps, n)) {
-      set_error("tensor-core tile pass: tensor map encoding failed");
-      return QC_ERR_CUDA;
-    }
     TcNorm nm{};
     nm.first = i == 0 ? 1 : 0;
     nm.apply = restore && i > 0 ? 1 : 0;
@@ -1014,12 +1037,7 @@ qc_status run_tiles_tc(qc_state* s, const std::vector<ResolvedOp>& rops, bool* h
     nm.in_part = norm_in;
     nm.out_prev = norm_out[(i + 1) & 1];
     nm.out_cur = norm_out[i & 1];
-    if (tm.tma)
-      QC_COUNT(), k_tile_pass_tc<true><<<grid, kTtThreads, kTtSmem, s->stream>>>(a, g_tc.passes[i], dst, dimg, status,
-                                                                              map, tm, nm);
-    else
-      QC_COUNT(), k_tile_pass_tc<false><<<grid, kTtThreads, kTtSmem, s->stream>>>(a, g_tc.passes[i], dst, dimg,
-                                                                               status, map, tm, nm);
+    if (qc_status st = launch_tc_pass(s, g_tc.passes[i], g_tc.tmas[i], dst, dimg, status, nm, grid)) return st;
   }
   if (qc_status st = check_launch("tensor-core tile pass")) return st;
   if (qc_status st = check_cuda(cudaEventRecord(g_tc.done, s->stream), "plan event")) return st;
@@ -1035,6 +1053,153 @@ qc_status run_tiles_tc(qc_state* s, const std::vector<ResolvedOp>& rops, bool* h
   g_last_stage_count = g_tc.nstages;
   *handled = true;
   return QC_OK;
+}
+
+// The tile bit set of a one-block pass: index bits 0..3, the block's bits and fillers up
+// to kTtM bits, chosen so that the tile forms as few box dimensions as possible: whole
+// gaps between the tile's runs first (the most dimensions removed, the smallest gap on
+// ties), then bits that extend a run without splitting a gap.  Ascending.
+static std::vector<int> block_tile_bits(const int* bits, int k, int n) {
+  bool in[64] = {false};
+  int cnt = 0;
+  auto add = [&](int b) {
+    if (!in[b]) {
+      in[b] = true;
+      ++cnt;
+    }
+  };
+  for (int b = 0; b < kTtL; ++b) add(b);
+  for (int j = 0; j < k; ++j) add(bits[j]);
+  auto dims = [&]() {
+    int nd = 1;
+    for (int b = kTtL; b < n;) {
+      const bool t = in[b];
+      while (b < n && in[b] == t) ++b;
+      ++nd;
+    }
+    return nd;
+  };
+  while (cnt < kTtM) {
+    const int d0 = dims();
+    int best_a = -1, best_e = -1, best_save = 0;
+    for (int b = kTtL; b < n;) {
+      if (in[b]) {
+        ++b;
+        continue;
+      }
+      const int a = b;
+      while (b < n && !in[b]) ++b;
+      if (b - a > kTtM - cnt) continue;
+      for (int x = a; x < b; ++x) in[x] = true;
+      const int save = d0 - dims();
+      for (int x = a; x < b; ++x) in[x] = false;
+      if (save > best_save || (save == best_save && save > 0 && b - a < best_e - best_a)) {
+        best_save = save;
+        best_a = a;
+        best_e = b;
+      }
+    }
+    if (best_save <= 0) break;
+    for (int x = best_a; x < best_e; ++x) add(x);
+  }
+  while (cnt < kTtM) {
+    const int d0 = dims();
+    int pick = -1;
+    for (int b = kTtL; b < n && pick < 0; ++b) {
+      if (in[b]) continue;
+      in[b] = true;
+      if (dims() <= d0) pick = b;
+      in[b] = false;
+    }
+    if (pick < 0)
+      for (int b = kTtL; b < n && pick < 0; ++b)
+        if (!in[b]) pick = b;
+    add(pick);
+  }
+  std::vector<int> B;
+  for (int b = 0; b < n; ++b)
+    if (in[b]) B.push_back(b);
+  return B;
+}
+
+qc_status apply_block_tile_tc(qc_state* s, const int* bits, int k, const double* U, bool* handled) {
+  *handled = false;
+  const int n = s->n;
+  if (s->dtype != QC_C64 || n < kTtM || k < 1 || k > kTtSB) return QC_OK;
+  const std::vector<int> B = block_tile_bits(bits, k, n);
+  int local_of[64];
+  for (int b = 0; b < 64; ++b) local_of[b] = -1;
+  for (int i = 0; i < kTtM; ++i) local_of[B[i]] = i;
+  std::vector<std::vector<int>> acts(1);
+  for (int j = 0; j < k; ++j) acts[0].push_back(local_of[bits[j]]);
+  const TileStage rec = stage_layouts(acts, kTtM, kTtSB, 4)[0];  // slot j = bits[j] for j < k
+  // only as box copies: with per-amplitude copies the gathering block kernel is faster
+  // (1.08 against 1.22 ms for a spread 5-qubit block at 28 qubits)
+  const TcTma tm = tma_runs(B, n);
+  if (!tm.tma) return QC_OK;
+  {
+    alignas(64) CUtensorMap probe;
+    if (!encode_tile_map(&probe, tm, s->amps, n)) return QC_OK;
+  }
+  // the 32 x 32 block: U on slots 0..k-1 (bits[0] the most significant bit of U's
+  // index), the identity on the padding slots
+  constexpr int D = 1 << kTtSB;
+  const int Dk = 1 << k;
+  auto urow = [&](int d) {
+    int r = 0;
+    for (int j = 0; j < k; ++j) r |= ((d >> j) & 1) << (k - 1 - j);
+    return r;
+  };
+  std::vector<cd> U32(D * D, cd(0.0, 0.0));
+  for (int d = 0; d < D; ++d)
+    for (int c = 0; c < D; ++c)
+      if ((d >> k) == (c >> k)) {
+        const int e = urow(d) * Dk + urow(c);
+        U32[d * D + c] = cd(U[2 * e], U[2 * e + 1]);
+      }
+  std::vector<TcStage> recs;
+  std::vector<float> img;
+  tc_stage_record(U32, rec, true, recs, img);
+  TilePass P{};
+  P.m = kTtM;
+  P.L = kTtL;
+  for (int i = 0; i < kTtM; ++i) P.bits[i] = int8_t(B[i]);
+  P.ntiles = uint64_t(1) << (n - kTtM);
+  P.stage0 = 0;
+  P.nstages = 1;
+  const unsigned grid = unsigned(std::min<uint64_t>((P.ntiles + 1) / 2, uint64_t(device_sm_count())));
+  // scratch: status word, norm sums (written, not used: one pass), stage record, B image
+  const size_t o_norm = 256, o_rec = (o_norm + sizeof(double) * grid + 255) & ~size_t(255);
+  const size_t o_img = o_rec + 256, total = o_img + img.size() * sizeof(float);
+  void* scr = nullptr;
+  if (qc_status st = state_scratch(s, total, &scr)) return st;
+  char* base = static_cast<char*>(scr);
+  int* status = reinterpret_cast<int*>(base);
+  double* norms = reinterpret_cast<double*>(base + o_norm);
+  std::vector<char> up(total - o_rec, 0);
+  memcpy(up.data(), recs.data(), sizeof(TcStage));
+  memcpy(up.data() + (o_img - o_rec), img.data(), img.size() * sizeof(float));
+  if (qc_status st = check_cuda(cudaMemsetAsync(status, 0, sizeof(int), s->stream), "status reset")) return st;
+  if (qc_status st = check_cuda(cudaMemcpyAsync(base + o_rec, up.data(), up.size(), cudaMemcpyHostToDevice, s->stream),
+                                "block upload"))
+    return st;
+  if (qc_status st = tc_pass_smem()) return st;
+  TcNorm nm{};
+  nm.nblocks = int(grid);
+  nm.in_part = norms;
+  nm.out_prev = norms;
+  nm.out_cur = norms;
+  if (qc_status st = launch_tc_pass(s, P, tm, reinterpret_cast<const TcStage*>(base + o_rec),
+                                    reinterpret_cast<const float*>(base + o_img), status, nm, grid))
+    return st;
+  if (qc_status st = check_launch("tensor-core block pass")) return st;
+  int h = 0;
+  if (qc_status st = check_cuda(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s->stream), "status"))
+    return st;
+  // the host staging buffer `up` is read by the copy above before the stream is done
+  if (qc_status st = check_cuda(cudaStreamSynchronize(s->stream), "tensor-core block pass")) return st;
+  *handled = true;
+  return device_status(h, "tensor-core block pass");
 }
 
 }  // namespace qcgb
