@@ -539,7 +539,8 @@ def run_block_bench(args):
     """Opt-in secondary measurement: a dense 5-qubit block (Haar 32x32) on spread qubits
     and on index bits 10..14, and a dense 6-qubit block (Haar 64x64), on a 28-qubit
     complex64 state, CUDA-core FMA (k_kq_native) vs tensor cores (TF32x3: the one-stage
-    tile pass with box copies where the block's tile allows, else k_block_tc; k_block_tc6)."""
+    tile pass with box copies where the block's tile has a box plan, else k_block_tc;
+    k_block_tc6)."""
     import torch
 
     import paper_2503_03016_gb300 as P

@@ -44,7 +44,7 @@ qc_status apply_kq_tf32x3(qc_state* s, const int* bits, int k, const double* U);
 // a dense block of k <= 5 qubits (bits[0] the most significant bit of U's index) as one
 // tensor-core tile pass of a single stage whose tiles move as boxes; *handled is false
 // (nothing applied) where it does not apply (complex128, fewer than 12 qubits, a tile
-// of more than 5 runs of index bits)
+// that no box plan covers)
 qc_status apply_block_tile_tc(qc_state* s, const int* bits, int k, const double* U, bool* handled);
 
 }  // namespace qcgb

@@ -96,18 +96,27 @@ constexpr size_t kTtSmem = 1024 /* alignment slack */ + 2 * kTtBimg + 2 * kTtGro
                            kTtHi * sizeof(uint64_t) + kTileNumberTab * sizeof(uint64_t) +
                            kTtMaxStages * sizeof(TcStage) + 256;
 
-// A pass whose tile is one box of the state for the tensor memory accelerator: the
-// state's index bits as at most 5 runs (dimension 0: bits 0..3, 16 amplitudes = 128
-// bytes; then alternating runs of bits in and out of the tile), box = the whole of the
-// tile's runs and one element of the others.  The box lands in shared memory with the
-// 128-byte swizzle (16-byte chunk c of 128-byte row r at chunk c ^ (r & 7)).
+// A pass whose tile moves as boxes of the state for the tensor memory accelerator: the
+// state's index bits grouped into at most 5 dimensions of consecutive bits (dimension
+// 0: bits 0..3, 16 amplitudes = 128 bytes); a dimension whose bits all lie in the tile
+// is copied whole, any other one element at a time.  Tile bits inside such a
+// dimension are box coordinates: the tile is 2^nc boxes (at least 1 KiB each), box j
+// at byte j * (tile bytes >> nc) with the coordinate bits of j, so the tile's local
+// bits are dimension 0, the whole dimensions' bits in ascending order, then the
+// coordinate bits.  Boxes land in shared memory with the 128-byte swizzle (16-byte
+// chunk c of 128-byte row r at chunk c ^ (r & 7)).
 struct TcTma {
   int32_t tma;         // 1: tiles move by cp.async.bulk.tensor, 0: by cp.async
   int8_t start[5];     // first index bit of dimension d
   int8_t len[5];       // its bits (0: a padding dimension of size 1)
-  int8_t tile[5];      // 1: dimension d is in the tile (coordinate 0)
-  int8_t pad;
+  int8_t tile[5];      // 1: dimension d is copied whole (coordinate 0)
+  int8_t nc;           // tile bits taken as box coordinates (at most kTtMaxCoordBits)
+  int8_t cdim[5];      // dimension of coordinate bit q
+  int8_t coff[5];      // its bit within that dimension
 };
+// Boxes of at least 8 KiB: with 16 boxes of 2 KiB per tile the one pass of the 28-qubit
+// brickwork that took them ran slower than with per-amplitude copies
+constexpr int kTtMaxCoordBits = 2;
 
 // Norm restoration across the passes of a circuit.  The tensor cores truncate their
 // FP32 accumulator toward zero, so every stage shrinks the amplitudes slightly (a
@@ -231,23 +240,50 @@ __device__ __forceinline__ void tma_coords(uint64_t base, const TcTma& tm, int32
     c[d] = tm.tile[d] || tm.len[d] == 0 ? 0 : int32_t((base >> tm.start[d]) & ((uint64_t(1) << tm.len[d]) - 1));
 }
 
-__device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap* map, const int32_t (&c)[5],
-                                              uint32_t bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(uint32_t(kTtTileBytes))
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5, "
-      "%6}], [%7];\n" ::"r"(dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(bar)
-      : "memory");
+// the coordinates of box j of a tile whose first box is at c (every index static, so
+// that cj stays in registers)
+__device__ __forceinline__ void tma_box_coords(const TcTma& tm, const int32_t (&c)[5], uint32_t j, int32_t (&cj)[5]) {
+#pragma unroll
+  for (int d = 0; d < 5; ++d) cj[d] = c[d];
+#pragma unroll
+  for (int q = 0; q < kTtMaxCoordBits; ++q)
+    if (q < tm.nc && ((j >> q) & 1u)) {
+#pragma unroll
+      for (int d = 0; d < 5; ++d)
+        if (tm.cdim[q] == d) cj[d] += int32_t(1) << tm.coff[q];
+    }
 }
 
-__device__ __forceinline__ void tma_store_tile(uint32_t src, const CUtensorMap* map, const int32_t (&c)[5]) {
-  asm volatile(
-      "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];\n" ::"l"(
-          reinterpret_cast<uint64_t>(map)),
-      "r"(c[0]), "r"(c[1]), "r"(c[2]), "r"(c[3]), "r"(c[4]), "r"(src)
-      : "memory");
+// the tile's boxes -> shared memory at dst, completion counted in bytes on `bar`
+__device__ __forceinline__ void tma_load_tile(uint32_t dst, const CUtensorMap* map, const int32_t (&c)[5],
+                                              uint32_t bar, const TcTma& tm) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(bar), "r"(uint32_t(kTtTileBytes))
+               : "memory");
+  const uint32_t nb = 1u << tm.nc, bytes = uint32_t(kTtTileBytes) >> tm.nc;
+  for (uint32_t j = 0; j < nb; ++j) {
+    int32_t cj[5];
+    tma_box_coords(tm, c, j, cj);
+    asm volatile(
+        "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+        "%5, %6}], [%7];\n" ::"r"(dst + j * bytes),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(cj[0]), "r"(cj[1]), "r"(cj[2]), "r"(cj[3]), "r"(cj[4]), "r"(bar)
+        : "memory");
+  }
+}
+
+// the tile's boxes from shared memory at src -> the state, as one bulk group
+__device__ __forceinline__ void tma_store_tile(uint32_t src, const CUtensorMap* map, const int32_t (&c)[5],
+                                               const TcTma& tm) {
+  const uint32_t nb = 1u << tm.nc, bytes = uint32_t(kTtTileBytes) >> tm.nc;
+  for (uint32_t j = 0; j < nb; ++j) {
+    int32_t cj[5];
+    tma_box_coords(tm, c, j, cj);
+    asm volatile(
+        "cp.async.bulk.tensor.5d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3, %4, %5}], [%6];\n" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(cj[0]), "r"(cj[1]), "r"(cj[2]), "r"(cj[3]), "r"(cj[4]), "r"(src + j * bytes)
+        : "memory");
+  }
   asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
 }
 
@@ -274,7 +310,7 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
   uint64_t* bars = reinterpret_cast<uint64_t*>(sst + kTtMaxStages);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 13);
   volatile int* abort_word = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  __shared__ int8_t sbits[16];
+  __shared__ int8_t sbits[16], ssorted[16];  // the tile's bits in local order / ascending
   __shared__ float s_fac;                                 // this pass's input scale
   __shared__ double s_norm[2][kTtGroups * kTtGroupThreads];  // per-thread norm sums
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -284,7 +320,13 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
 
   if (tid == 0) {
 #pragma unroll
-    for (int k = 0; k < 16; ++k) sbits[k] = P.bits[k];
+    for (int k = 0; k < 16; ++k) sbits[k] = ssorted[k] = P.bits[k];
+    for (int k = 1; k < m; ++k)  // insertion sort of the m tile bits
+      for (int j = k; j > 0 && ssorted[j - 1] > ssorted[j]; --j) {
+        const int8_t x = ssorted[j];
+        ssorted[j] = ssorted[j - 1];
+        ssorted[j - 1] = x;
+      }
     for (int b = 0; b < 13; ++b) {
       const uint32_t cnt = b < 4 ? uint32_t(kTtGroupThreads) : 1u;
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bars + b)), "r"(cnt) : "memory");
@@ -316,7 +358,7 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
       if ((h >> k) & 1) o |= uint64_t(1) << sbits[L + k];
     hioff[h] = o;
   }
-  build_tile_number_tables(tnt, sbits, m, __ffsll(static_cast<long long>(P.ntiles)) - 1);
+  build_tile_number_tables(tnt, ssorted, m, __ffsll(static_cast<long long>(P.ntiles)) - 1);
   asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
@@ -460,7 +502,7 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
       } else if (elect) {
         int32_t c[5];
         tma_coords(tile_base(t0, tnt), tm, c);
-        tma_load_tile(smem_u32(buf0), &tmap, c, tload);
+        tma_load_tile(smem_u32(buf0), &tmap, c, tload, tm);
         ++nload;
       }
     }
@@ -496,7 +538,7 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
           asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory");
           int32_t c[5];
           tma_coords(tile_base(t + G2, tnt), tm, c);
-          tma_load_tile(smem_u32(other), &tmap, c, tload);
+          tma_load_tile(smem_u32(other), &tmap, c, tload, tm);
           ++nload;
         }
         loaded = true;
@@ -595,7 +637,7 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
         if (elect) {
           int32_t c[5];
           tma_coords(tile_base(t, tnt), tm, c);
-          tma_store_tile(smem_u32(cur), &tmap, c);
+          tma_store_tile(smem_u32(cur), &tmap, c, tm);
         }
         if (!loaded) tma_next();
         continue;
@@ -798,33 +840,89 @@ static bool tc_pass_blocks(const BuiltPass& bp, const std::vector<PlanOp>& pops,
   return true;
 }
 
-// The runs of a pass's tile for a box copy (at most 5 dimensions), or tma = 0.
-static TcTma tma_runs(const std::vector<int>& B, int n) {
-  TcTma tm{};
+// The box plan of a pass's tile (bit set B, index bits 0..3 among them): dimension 0 =
+// bits 0..3; the runs of bits above (alternately in and out of the tile) grouped into
+// at most 4 dimensions of consecutive bits so that as few tile bits as possible fall in
+// dimensions that are not copied whole (those become box coordinates; at most
+// kTtMaxCoordBits); tma = 0 if no grouping fits.  Bloc receives the
+// tile's bits in the boxes' local order.
+static TcTma tma_plan(const std::vector<int>& B, int n, std::vector<int>& Bloc) {
   bool in[64] = {false};
   for (int b : B) in[b] = true;
-  int nd = 0;
-  auto add = [&](int start, int len, bool tile) {
-    if (nd < 5) {
-      tm.start[nd] = int8_t(start);
-      tm.len[nd] = int8_t(len);
-      tm.tile[nd] = tile ? 1 : 0;
-    }
-    ++nd;
-  };
-  add(0, kTtL, true);
+  for (int b = 0; b < kTtL; ++b)
+    if (!in[b]) return TcTma{};
+  std::vector<int> rs, rl;
+  std::vector<char> rin;
   for (int b = kTtL; b < n;) {
-    const int start = b;
+    const int st = b;
     const bool t = in[b];
     while (b < n && in[b] == t) ++b;
-    add(start, b - start, t);
+    rs.push_back(st);
+    rl.push_back(b - st);
+    rin.push_back(t ? 1 : 0);
   }
-  if (nd > 5) return TcTma{};
-  for (int d = nd; d < 5; ++d) {  // padding dimensions of size 1 above the state
+  const int R = int(rs.size());
+  constexpr int kGroups = 4, kInf = 1 << 20;
+  // a group of runs [i, j): copied whole if it is one run, else its tile bits are
+  // coordinates
+  auto cost = [&](int i, int j) {
+    if (j - i == 1) return 0;
+    int c = 0;
+    for (int x = i; x < j; ++x)
+      if (rin[x]) c += rl[x];
+    return c;
+  };
+  std::vector<std::vector<int>> best(kGroups + 1, std::vector<int>(R + 1, kInf)), from = best;
+  best[0][0] = 0;
+  for (int g = 1; g <= kGroups; ++g)
+    for (int j = 1; j <= R; ++j)
+      for (int i = g - 1; i < j; ++i)
+        if (best[g - 1][i] < kInf && best[g - 1][i] + cost(i, j) < best[g][j]) {
+          best[g][j] = best[g - 1][i] + cost(i, j);
+          from[g][j] = i;
+        }
+  int G = 0;
+  for (int g = 1; g <= kGroups; ++g)
+    if (best[g][R] < (G ? best[G][R] : kInf)) G = g;
+  if (G == 0 || best[G][R] > kTtMaxCoordBits) return TcTma{};
+  std::vector<std::pair<int, int>> groups(G);  // runs [first, last)
+  for (int g = G, j = R; g >= 1; --g) {
+    groups[g - 1] = {from[g][j], j};
+    j = from[g][j];
+  }
+  TcTma tm{};
+  tm.start[0] = 0;
+  tm.len[0] = int8_t(kTtL);
+  tm.tile[0] = 1;
+  Bloc.clear();
+  for (int b = 0; b < kTtL; ++b) Bloc.push_back(b);
+  std::vector<int> coords;
+  for (int g = 0; g < G; ++g) {
+    const int i = groups[g].first, j = groups[g].second, d = g + 1;
+    tm.start[d] = int8_t(rs[i]);
+    tm.len[d] = int8_t(rs[j - 1] + rl[j - 1] - rs[i]);
+    tm.tile[d] = (j - i == 1 && rin[i]) ? 1 : 0;
+    for (int x = i; x < j; ++x) {
+      if (!rin[x]) continue;
+      for (int b = rs[x]; b < rs[x] + rl[x]; ++b) {
+        if (tm.tile[d]) {
+          Bloc.push_back(b);
+        } else {
+          tm.cdim[coords.size()] = int8_t(d);
+          tm.coff[coords.size()] = int8_t(b - rs[i]);
+          coords.push_back(b);
+        }
+      }
+    }
+  }
+  for (int d = G + 1; d < 5; ++d) {  // padding dimensions of size 1 above the state
     tm.start[d] = int8_t(n);
     tm.len[d] = 0;
     tm.tile[d] = 0;
   }
+  tm.nc = int8_t(coords.size());
+  for (int b : coords) Bloc.push_back(b);
+  if (int(Bloc.size()) != kTtM) return TcTma{};
   tm.tma = 1;
   return tm;
 }
@@ -911,18 +1009,21 @@ static qc_status tc_plan(qc_state* s, const std::vector<ResolvedOp>& rops, int d
   std::vector<float> imgs;
   bool tc = true;
   for (const BuiltPass& bp : bps) {
-    TcTma tm = tma_runs(bp.B, n);
+    std::vector<int> Bloc;
+    TcTma tm = tma_plan(bp.B, n, Bloc);
     if (tm.tma) {  // a trial encoding with this state's address
       alignas(64) CUtensorMap probe;
       if (!encode_tile_map(&probe, tm, s->amps, n)) tm = TcTma{};
     }
+    BuiltPass bl = bp;  // the tile's bits in the local order of its boxes
+    if (tm.tma) bl.B = Bloc;
     TilePass P{};
     P.m = kTtM;
     P.L = kTtL;
-    for (int i = 0; i < kTtM; ++i) P.bits[i] = int8_t(bp.B[i]);
+    for (int i = 0; i < kTtM; ++i) P.bits[i] = int8_t(bl.B[i]);
     P.ntiles = uint64_t(1) << (n - kTtM);
     P.stage0 = int(stages.size());
-    if (!tc_pass_blocks(bp, pops, n, tm.tma != 0, stages, imgs)) {  // the CUDA-core passes take it
+    if (!tc_pass_blocks(bl, pops, n, tm.tma != 0, stages, imgs)) {  // the CUDA-core passes take it
       tc = false;
       break;
     }
@@ -1055,92 +1156,86 @@ qc_status run_tiles_tc(qc_state* s, const std::vector<ResolvedOp>& rops, bool* h
   return QC_OK;
 }
 
-// The tile bit set of a one-block pass: index bits 0..3, the block's bits and fillers up
-// to kTtM bits, chosen so that the tile forms as few box dimensions as possible: whole
-// gaps between the tile's runs first (the most dimensions removed, the smallest gap on
-// ties), then bits that extend a run without splitting a gap.  Ascending.
-static std::vector<int> block_tile_bits(const int* bits, int k, int n) {
-  bool in[64] = {false};
-  int cnt = 0;
-  auto add = [&](int b) {
-    if (!in[b]) {
-      in[b] = true;
-      ++cnt;
+// The tile of a one-block pass: index bits 0..3, the block's bits and fillers up to kTtM
+// bits.  Every subset of the gaps between the tile's runs that the fillers can close is
+// tried (at most 2^(k + 1)); the remaining fillers extend runs without splitting a gap
+// (lowest bits first, or highest first); the tile whose box plan has the fewest
+// coordinate bits, then the fewest dimensions, wins.  Bloc receives its bits in the
+// boxes' local order; tma = 0 if no candidate has a box plan.
+static TcTma block_tile_plan(const int* bits, int k, int n, std::vector<int>& Bloc) {
+  bool base[64] = {false};
+  for (int b = 0; b < kTtL; ++b) base[b] = true;
+  for (int j = 0; j < k; ++j) base[bits[j]] = true;
+  std::vector<std::pair<int, int>> gaps;  // [first, end) of each run of bits outside
+  for (int b = kTtL; b < n;) {
+    if (base[b]) {
+      ++b;
+      continue;
     }
-  };
-  for (int b = 0; b < kTtL; ++b) add(b);
-  for (int j = 0; j < k; ++j) add(bits[j]);
-  auto dims = [&]() {
-    int nd = 1;
-    for (int b = kTtL; b < n;) {
-      const bool t = in[b];
-      while (b < n && in[b] == t) ++b;
-      ++nd;
-    }
-    return nd;
-  };
-  while (cnt < kTtM) {
-    const int d0 = dims();
-    int best_a = -1, best_e = -1, best_save = 0;
-    for (int b = kTtL; b < n;) {
-      if (in[b]) {
-        ++b;
-        continue;
-      }
-      const int a = b;
-      while (b < n && !in[b]) ++b;
-      if (b - a > kTtM - cnt) continue;
-      for (int x = a; x < b; ++x) in[x] = true;
-      const int save = d0 - dims();
-      for (int x = a; x < b; ++x) in[x] = false;
-      if (save > best_save || (save == best_save && save > 0 && b - a < best_e - best_a)) {
-        best_save = save;
-        best_a = a;
-        best_e = b;
-      }
-    }
-    if (best_save <= 0) break;
-    for (int x = best_a; x < best_e; ++x) add(x);
+    const int a = b;
+    while (b < n && !base[b]) ++b;
+    gaps.push_back({a, b});
   }
-  while (cnt < kTtM) {
-    const int d0 = dims();
-    int pick = -1;
-    for (int b = kTtL; b < n && pick < 0; ++b) {
-      if (in[b]) continue;
-      in[b] = true;
-      if (dims() <= d0) pick = b;
-      in[b] = false;
+  TcTma best{};
+  int best_nc = 1 << 20, best_nd = 1 << 20;
+  const int ng = std::min(int(gaps.size()), 16);
+  for (uint32_t sub = 0; sub < (1u << ng); ++sub)
+    for (int dir = 0; dir < 2; ++dir) {
+      bool in[64];
+      memcpy(in, base, sizeof(in));
+      for (int g = 0; g < ng; ++g)
+        if ((sub >> g) & 1)
+          for (int x = gaps[g].first; x < gaps[g].second; ++x) in[x] = true;
+      int cnt = 0;
+      for (int b = 0; b < n; ++b) cnt += in[b] ? 1 : 0;
+      if (cnt > kTtM) continue;
+      while (cnt < kTtM) {
+        int pick = -1;
+        for (int i = 0; i < n - kTtL && pick < 0; ++i) {
+          const int b = dir ? n - 1 - i : kTtL + i;
+          if (!in[b] && ((b + 1 < n && in[b + 1]) || (b - 1 >= kTtL && in[b - 1]))) pick = b;
+        }
+        for (int b = kTtL; b < n && pick < 0; ++b)
+          if (!in[b]) pick = b;
+        in[pick] = true;
+        ++cnt;
+      }
+      std::vector<int> B, bl;
+      for (int b = 0; b < n; ++b)
+        if (in[b]) B.push_back(b);
+      const TcTma tm = tma_plan(B, n, bl);
+      if (!tm.tma) continue;
+      int nd = 0;
+      for (int d = 0; d < 5; ++d) nd += tm.len[d] > 0 ? 1 : 0;
+      if (tm.nc < best_nc || (tm.nc == best_nc && nd < best_nd)) {
+        best = tm;
+        best_nc = tm.nc;
+        best_nd = nd;
+        Bloc = bl;
+      }
     }
-    if (pick < 0)
-      for (int b = kTtL; b < n && pick < 0; ++b)
-        if (!in[b]) pick = b;
-    add(pick);
-  }
-  std::vector<int> B;
-  for (int b = 0; b < n; ++b)
-    if (in[b]) B.push_back(b);
-  return B;
+  return best;
 }
 
 qc_status apply_block_tile_tc(qc_state* s, const int* bits, int k, const double* U, bool* handled) {
   *handled = false;
   const int n = s->n;
   if (s->dtype != QC_C64 || n < kTtM || k < 1 || k > kTtSB) return QC_OK;
-  const std::vector<int> B = block_tile_bits(bits, k, n);
+  std::vector<int> B;  // the tile's bits in the local order of its boxes
+  const TcTma tm = block_tile_plan(bits, k, n, B);
+  // only as box copies: with per-amplitude copies the gathering block kernel is faster
+  // (1.08 against 1.22 ms for a spread 5-qubit block at 28 qubits)
+  if (!tm.tma) return QC_OK;
+  {
+    alignas(64) CUtensorMap probe;
+    if (!encode_tile_map(&probe, tm, s->amps, n)) return QC_OK;
+  }
   int local_of[64];
   for (int b = 0; b < 64; ++b) local_of[b] = -1;
   for (int i = 0; i < kTtM; ++i) local_of[B[i]] = i;
   std::vector<std::vector<int>> acts(1);
   for (int j = 0; j < k; ++j) acts[0].push_back(local_of[bits[j]]);
   const TileStage rec = stage_layouts(acts, kTtM, kTtSB, 4)[0];  // slot j = bits[j] for j < k
-  // only as box copies: with per-amplitude copies the gathering block kernel is faster
-  // (1.08 against 1.22 ms for a spread 5-qubit block at 28 qubits)
-  const TcTma tm = tma_runs(B, n);
-  if (!tm.tma) return QC_OK;
-  {
-    alignas(64) CUtensorMap probe;
-    if (!encode_tile_map(&probe, tm, s->amps, n)) return QC_OK;
-  }
   // the 32 x 32 block: U on slots 0..k-1 (bits[0] the most significant bit of U's
   // index), the identity on the padding slots
   constexpr int D = 1 << kTtSB;

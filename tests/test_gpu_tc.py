@@ -80,22 +80,21 @@ def test_tc_rejects_unsupported():
         P.qc_apply_fused_k(st.handle, [0, 1, 2, 3, 4, 5], np.eye(64), P.QC_PREC_TF32X3)
 
 
-@pytest.mark.parametrize("k", [4, 5])
-def test_tc_block_box_and_gather_layouts(k):
-    """At 20 qubits: a block on index bits 9.. whose tile (index bits 0..3, the block's
-    bits and fillers) forms 4 box dimensions (a one-stage tensor-core tile pass with box
-    copies) and a block spread over the register (6 or 7: the gathering block kernel),
-    both against the oracle."""
+@pytest.mark.parametrize("n,bits", [(20, (9, 10, 11, 12)), (20, (9, 10, 11, 12, 13)), (20, (2, 7, 12, 17)),
+                                    (20, (1, 6, 11, 15, 18)), (22, (6, 9, 12, 15, 19))])
+def test_tc_block_box_and_gather_layouts(n, bits):
+    """Blocks on the given index bits, against the oracle: a tile (index bits 0..3, the
+    block's bits, fillers) that is one box (bits 9..), one that is two boxes (the two
+    spread layouts at 20 qubits: one tile bit is a box coordinate), and one with no box
+    plan of at most two coordinate bits (22 qubits: the gathering block kernel)."""
     import paper_2503_03016_gb300 as P
-    n = 20
-    layouts = {"runs": [n - 1 - b for b in range(9, 9 + k)],          # index bits 9..
-               "spread": [n - 1 - b for b in ((2, 7, 12, 17) if k == 4 else (1, 6, 11, 15, 18))]}
-    for name, qs in layouts.items():
-        U = W.haar_unitaries(1, 1 << k, 40 + k)[0]
-        psi = W.random_state(n, 5 + k)
-        st = gpu_state(psi, "c64")
-        P.qc_apply_fused_k(st.handle, qs, U, P.QC_PREC_TF32X3)
-        want = psi.copy()
-        oracle.apply_kq(want, qs, U)
-        err = rel_l2(st.numpy(), want)
-        assert err <= 1e-5, (name, qs, err)
+    k = len(bits)
+    qs = [n - 1 - b for b in bits]
+    U = W.haar_unitaries(1, 1 << k, 40 + k + n)[0]
+    psi = W.random_state(n, 5 + k)
+    st = gpu_state(psi, "c64")
+    P.qc_apply_fused_k(st.handle, qs, U, P.QC_PREC_TF32X3)
+    want = psi.copy()
+    oracle.apply_kq(want, qs, U)
+    err = rel_l2(st.numpy(), want)
+    assert err <= 1e-5, (bits, err)
