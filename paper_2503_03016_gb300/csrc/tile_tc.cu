@@ -20,7 +20,7 @@
 // never passes through shared memory as an operand (the tensor cores read only B
 // there), and arrives on the group's mbarrier of that half of the columns: the MMA warp
 // starts the K steps of the first half while the second half is being gathered.  The MMA warp
-// issues the stage's 24 products (A from TMEM, B from shared memory) into two FP32
+// issues the stage's 16 products (A from TMEM, B from shared memory) into two FP32
 // accumulators and commits them to the group's mbarrier.  The group reads its rows of
 // D back (tcgen05.ld), adds the two partial sums, writes the outputs into the tile at
 // this stage's positions (the transposition between stages' row and slot bits) and,
@@ -31,11 +31,15 @@
 // during stage 0, the load of its next tile (cp.async into the buffer just written
 // back) during the following stages.
 //
-// Accumulation: the tensor cores truncate the FP32 accumulator toward zero after each
-// product step, which a circuit's stages compound into a norm loss when large partial
-// sums are accumulated many times.  Each accumulator takes half of the K steps, its
-// small products (a_hi b_lo, a_lo b_hi) first and the four a_hi b_hi products last, and
-// the two halves are added on the CUDA cores with round-to-nearest.
+// Products and accumulation: per K step, a_hi [b_hi | b_lo] is one product of N = 128
+// (the image holds each K slice as B_hi's rows followed by B_lo's, one 128-row operand),
+// whose first 64 columns accumulate the large products a_hi b_hi and the other 64 the
+// small products a_hi b_lo, and a_lo b_hi (N = 64) adds into the second accumulator: 16
+// products per stage instead of 24 of N = 64, which the tensor cores run at half the
+// rate of N = 128.  The tensor cores truncate the FP32 accumulator toward zero after each
+// product step, which a circuit's stages compound into a norm loss; the large and small
+// products are kept apart and added on the CUDA cores with round-to-nearest, and the
+// passes restore the register's norm (below).
 //
 // B images (host-built, already in the K-major 128-byte-swizzled layout, 32 KiB per
 // stage) stream through two shared-memory buffers by bulk copies with mbarrier
@@ -74,8 +78,10 @@ constexpr int kTtGroupThreads = kTtRows;        // one thread per row
 constexpr int kTtThreads = kTtGroups * kTtGroupThreads + 32;  // + the MMA warp
 constexpr int kTtMmaWarp = kTtGroups * kTtGroupThreads / 32;
 constexpr int kTtCols = 2 << kTtSB;             // 64 real columns (K = N)
-constexpr int kTtBregion = kTtCols * 128;       // one 32-column K slice of B: 8 KiB
-constexpr int kTtBimg = 2 * 2 * kTtBregion;     // B_hi + B_lo of one stage: 32 KiB
+constexpr int kTtBregion = kTtCols * 128;       // one 32-column K slice of B_hi or B_lo: 8 KiB
+// B image of one stage, 32 KiB: per K slice s, B_hi's 64 rows then B_lo's 64 rows (16 KiB
+// at s * 16 KiB), so that the slice is also one 128-row operand [B_hi; B_lo]
+constexpr int kTtBimg = 2 * 2 * kTtBregion;
 constexpr int kTtImgFloats = kTtBimg / 4;
 constexpr int kTtTileBytes = (1 << kTtM) * 8;   // complex64 tile: 32 KiB
 constexpr int kTtMaxStages = kMaxPassOps;
@@ -370,7 +376,7 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
   if (warp == kTtMmaWarp) {
     // ------------------------------------------------------------------ MMA warp
     if (lane == 0) {
-      constexpr uint32_t idesc = tf32_idesc(kTtRows, kTtCols);
+      constexpr uint32_t idesc = tf32_idesc(kTtRows, kTtCols), idesc2 = tf32_idesc(kTtRows, 2 * kTtCols);
       const bool resident = S <= 2;
       uint32_t bpar = 0, inflight = 0;
       uint32_t fpar_b = 0, freeing = 0;  // bfree[b]: parity of its next phase; a commit not yet waited for
@@ -395,7 +401,7 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
             bpar ^= 1u << b;
             inflight &= ~(1u << b);
           }
-          const uint32_t bh = smem_u32(bbuf + b * kTtBimg), bl = bh + 2 * kTtBregion;
+          const uint32_t bimg = smem_u32(bbuf + b * kTtBimg);
           for (int g = 0; g < kTtGroups; ++g) {
             if (k >= (g ? K1 : K0)) continue;
             const uint32_t gb = tmem + uint32_t(g * kTmemPerGroup);
@@ -405,16 +411,12 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
               ok = mbar_wait_ab(full0 + 8u * (2 * g + h), (fpar >> g) & 1u, abort_word);
               if (!ok) break;
               asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-              const uint32_t d = gb + 128u + uint32_t(64 * h);
-              // the small products first, then the a_hi b_hi products
+              // per K step: a_hi [b_hi | b_lo] as one N = 128 product (columns 128..191
+              // take a_hi b_hi, 192..255 a_hi b_lo), then a_lo b_hi into 192..255
               for (int ks = 4 * h; ks < 4 * h + 4; ++ks) {
-                const uint32_t boff = uint32_t((ks >> 2) * kTtBregion + (ks & 3) * 32);
-                tc_mma_ts(d, gb + uint32_t(8 * ks), sw128_desc(bl + boff, kTcAtom), idesc, ks == 4 * h ? 0u : 1u);
-                tc_mma_ts(d, gb + 64u + uint32_t(8 * ks), sw128_desc(bh + boff, kTcAtom), idesc, 1u);
-              }
-              for (int ks = 4 * h; ks < 4 * h + 4; ++ks) {
-                const uint32_t boff = uint32_t((ks >> 2) * kTtBregion + (ks & 3) * 32);
-                tc_mma_ts(d, gb + uint32_t(8 * ks), sw128_desc(bh + boff, kTcAtom), idesc, 1u);
+                const uint64_t bd = sw128_desc(bimg + uint32_t(h * 2 * kTtBregion + (ks & 3) * 32), kTcAtom);
+                tc_mma_ts(gb + 128u, gb + uint32_t(8 * ks), bd, idesc2, ks == 0 ? 0u : 1u);
+                tc_mma_ts(gb + 192u, gb + 64u + uint32_t(8 * ks), bd, idesc, 1u);
               }
             }
             if (!ok) break;
@@ -715,13 +717,13 @@ static void tc_stage_record(const std::vector<cd>& U, const TileStage& rec, bool
                             std::vector<float>& imgs) {
   constexpr int D = 1 << kTtSB;
   // B image: Bt[n][k] (n = output column, k = input column) of the real form,
-  // y_d = sum_c U[d][c] x_c; hi region then lo region, each in the swizzled layout
+  // y_d = sum_c U[d][c] x_c; per K slice, the hi rows then the lo rows, each in the
+  // swizzled layout
   TcStage ts{};
   ts.img = int32_t(imgs.size() / kTtImgFloats);
   const size_t o0 = imgs.size();
   imgs.resize(o0 + kTtImgFloats, 0.0f);
-  float* hi = imgs.data() + o0;
-  float* lo = hi + kTtImgFloats / 2;
+  float* img = imgs.data() + o0;
   for (int d = 0; d < D; ++d)
     for (int c = 0; c < D; ++c) {
       const double ur = U[d * D + c].real(), ui = U[d * D + c].imag();
@@ -730,9 +732,9 @@ static void tc_stage_record(const std::vector<cd>& U, const TileStage& rec, bool
       const int ks[4] = {2 * c, 2 * c + 1, 2 * c, 2 * c + 1};
       for (int e = 0; e < 4; ++e) {
         const float v = float(vals[e]), h = tf32_rne_host(v);
-        const uint32_t off = sw128_offset(ns[e], ks[e], kTtCols) / 4;
-        hi[off] = h;
-        lo[off] = tf32_rne_host(v - h);
+        const uint32_t off = ((ks[e] >> 5) * 2 * kTtBregion + sw128_offset(ns[e], ks[e] & 31, kTtCols)) / 4;
+        img[off] = h;
+        img[off + kTtBregion / 4] = tf32_rne_host(v - h);
       }
     }
   for (int k = 0; k < kTtSB; ++k)
