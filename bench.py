@@ -600,23 +600,29 @@ def run_qft_bench(args):
     for dt in ("c64", "c128"):
         st = P.State(n, dt).init_gaussian(3)
         sbytes = (1 << n) * (8 if dt == "c64" else 16)
-        for mode_name, mode in (("fused", P.QC_RUN_FUSED), ("per_gate", P.QC_RUN_PER_GATE)):
+        runs = [("fused", P.QC_RUN_FUSED, P.QC_PREC_NATIVE)]
+        if dt == "c64":  # tensor-core stage passes (TF32x3)
+            runs.append(("fused_tf32x3", P.QC_RUN_FUSED, P.QC_PREC_TF32X3))
+        runs.append(("per_gate", P.QC_RUN_PER_GATE, P.QC_PREC_NATIVE))
+        for mode_name, mode, prec in runs:
             if dt == "c128" and mode_name == "per_gate" and args.steps > 1:
                 reps = 1
             else:
                 reps = args.steps
-            P.qc_run_circuit(st.handle, circ, None, mode, P.QC_PREC_NATIVE)  # warm-up
+            P.qc_run_circuit(st.handle, circ, None, mode, prec)  # warm-up
             torch.cuda.synchronize()
             t = StreamTimer(stream)
             t.start()
             for _ in range(reps):
-                P.qc_run_circuit(st.handle, circ, None, mode, P.QC_PREC_NATIVE)
+                P.qc_run_circuit(st.handle, circ, None, mode, prec)
             ms = t.stop() / reps
             passes = P.qc_last_pass_count() if mode == P.QC_RUN_FUSED else None
             alg = 2 * sbytes * (passes if passes else per_gate_sweeps)
             gbs = alg / (ms * 1e-3) / 1e9
             res["%s_%s" % (dt, mode_name)] = {"ms": ms, "passes": passes, "algorithmic_gb": alg / 1e9,
                                               "gbs": gbs, "frac_hbm": gbs / hbm}
+            if mode == P.QC_RUN_FUSED:
+                res["%s_%s" % (dt, mode_name)]["path"] = P.qc_last_fused_path()
         st.free()
         torch.cuda.empty_cache()
     print(json.dumps({"metric": "QFT on %d qubits (%d gates)" % (n, len(ops)), "results": res,

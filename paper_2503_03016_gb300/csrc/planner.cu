@@ -325,7 +325,8 @@ void to_plan_ops(const std::vector<ResolvedOp>& in, std::vector<PlanOp>& out, co
 // bits with the targets of the first ops that need them.  An op is taken unless it
 // meets a skipped op it may not commute with (shared bits; two diagonal ops commute).
 static void greedy_pass(const std::vector<PlanOp>& ops, const std::vector<int>& remaining, int m, uint64_t B0,
-                        bool fixed, BuiltPass* bp, std::vector<int>* excluded, uint64_t* Bout, double* score) {
+                        bool fixed, bool cond_in_tile, BuiltPass* bp, std::vector<int>* excluded, uint64_t* Bout,
+                        double* score) {
   uint64_t Bmask = B0;
   int Bcount = __builtin_popcountll(B0);
   uint64_t blocked_all = 0;   // bits of skipped non-diagonal ops
@@ -335,9 +336,10 @@ static void greedy_pass(const std::vector<PlanOp>& ops, const std::vector<int>& 
     const PlanOp& p = ops[idx];
     bool ok = (p.touched & blocked_all) == 0 && int(bp->ops.size()) < kMaxPassOps;
     if (ok && !p.phase) ok = (p.touched & blocked_diag) == 0;
-    if (ok && !p.phase) {
-      uint64_t need = 0;
-      for (int k = 0; k < p.nt; ++k) need |= uint64_t(1) << p.tb[k];
+    if (ok && (!p.phase || (cond_in_tile && p.cmask))) {
+      uint64_t need = cond_in_tile ? p.cmask : 0;
+      if (!p.phase)
+        for (int k = 0; k < p.nt; ++k) need |= uint64_t(1) << p.tb[k];
       need &= ~Bmask;
       const int add = __builtin_popcountll(need);
       if (add == 0) {
@@ -363,7 +365,8 @@ static void greedy_pass(const std::vector<PlanOp>& ops, const std::vector<int>& 
   *score = sc;
 }
 
-static std::vector<BuiltPass> build_passes_uncached(const std::vector<PlanOp>& ops, int n, int m, int L) {
+static std::vector<BuiltPass> build_passes_uncached(const std::vector<PlanOp>& ops, int n, int m, int L,
+                                                    bool cond_in_tile) {
   std::vector<int> remaining(ops.size());
   for (size_t i = 0; i < ops.size(); ++i) remaining[i] = int(i);
   std::vector<BuiltPass> passes;
@@ -382,10 +385,10 @@ static std::vector<BuiltPass> build_passes_uncached(const std::vector<PlanOp>& o
       uint64_t Bm = 0;
       double sc = 0.0;
       if (cand < 0) {
-        greedy_pass(ops, remaining, m, low, false, &bp, &ex, &Bm, &sc);
+        greedy_pass(ops, remaining, m, low, false, cond_in_tile, &bp, &ex, &Bm, &sc);
       } else {
         const uint64_t win = ((uint64_t(1) << w) - 1) << (L + cand);
-        greedy_pass(ops, remaining, m, low | win, true, &bp, &ex, &Bm, &sc);
+        greedy_pass(ops, remaining, m, low | win, true, cond_in_tile, &bp, &ex, &Bm, &sc);
       }
       if (sc > best_score + 1e-9) {
         best_score = sc;
@@ -420,17 +423,19 @@ static std::mutex g_pass_cache_mu;
 static std::vector<PassCacheEntry> g_pass_cache;  // most recent last
 constexpr size_t kPassCacheEntries = 8;
 
-std::vector<BuiltPass> build_passes(const std::vector<PlanOp>& ops, int n, int m, int L) {
+std::vector<BuiltPass> build_passes(const std::vector<PlanOp>& ops, int n, int m, int L, bool cond_in_tile) {
   std::vector<int64_t> key;
-  key.reserve(3 + 5 * ops.size());
+  key.reserve(4 + 5 * ops.size());
   key.push_back(n);
   key.push_back(m);
   key.push_back(L);
+  key.push_back(cond_in_tile ? 1 : 0);
   for (const PlanOp& p : ops) {
     key.push_back(p.phase ? -1 : p.nt);
     key.push_back(p.phase ? 0 : p.tb[0]);
     key.push_back(!p.phase && p.nt == 2 ? p.tb[1] : 0);
     key.push_back(int64_t(p.touched));
+    if (cond_in_tile) key.push_back(int64_t(p.cmask));
   }
   {
     std::lock_guard<std::mutex> lock(g_pass_cache_mu);
@@ -442,7 +447,7 @@ std::vector<BuiltPass> build_passes(const std::vector<PlanOp>& ops, int n, int m
         return g_pass_cache.back().passes;
       }
   }
-  std::vector<BuiltPass> passes = build_passes_uncached(ops, n, m, L);
+  std::vector<BuiltPass> passes = build_passes_uncached(ops, n, m, L, cond_in_tile);
   std::lock_guard<std::mutex> lock(g_pass_cache_mu);
   if (g_pass_cache.size() >= kPassCacheEntries) g_pass_cache.erase(g_pass_cache.begin());
   g_pass_cache.push_back(PassCacheEntry{std::move(key), passes});
@@ -469,7 +474,7 @@ std::vector<BuiltPass> build_passes(const std::vector<PlanOp>& ops, int n, int m
 // stage's set without exceeding sb bits (with `fixed` >= 0: stay inside that set of
 // local bits) and no skipped op it fails to commute with precedes it.
 static void stage_sweep(const std::vector<int>& rest, const std::vector<PlanOp>& pops, const int* local_of, int sb,
-                        bool whole_ops, int64_t fixed, std::vector<int>& take, std::vector<int>& skip,
+                        int whole_ops, int64_t fixed, std::vector<int>& take, std::vector<int>& skip,
                         std::vector<int>& act) {
   take.clear();
   skip.clear();
@@ -493,7 +498,10 @@ static void stage_sweep(const std::vector<int>& rest, const std::vector<PlanOp>&
       if (whole_ops) {
         for (int b = 0; b < 64; ++b)
           if ((p.cmask >> b) & 1) add(b);
-        for (const auto& be : p.beta) add(be.first);
+        // mode 2: the phase bits of an op conditioned on at most one bit need no slot
+        // (that part of the op is deferred to the end of the stage)
+        if (whole_ops == 1 || !p.phase || __builtin_popcountll(p.cmask) >= 2)
+          for (const auto& be : p.beta) add(be.first);
       }
       if (outside || int(nw.size()) > sb)
         ok = false;
@@ -513,7 +521,7 @@ static void stage_sweep(const std::vector<int>& rest, const std::vector<PlanOp>&
 }
 
 void split_stages(const BuiltPass& bp, const std::vector<PlanOp>& pops, const int* local_of, int sb,
-                  std::vector<std::vector<int>>& takes, std::vector<std::vector<int>>& acts, bool whole_ops) {
+                  std::vector<std::vector<int>>& takes, std::vector<std::vector<int>>& acts, int whole_ops) {
   int m = 0;
   for (int b = 0; b < 64; ++b) m = std::max(m, local_of[b] + 1);
   std::vector<int> rest = bp.ops;
@@ -615,7 +623,7 @@ std::vector<TileStage> stage_layouts(const std::vector<std::vector<int>>& acts, 
 }
 
 // exactly the SWAP permutation (rows 0, 2, 1, 3 of the identity), no condition
-static bool is_exact_swap(const PlanOp& p) {
+bool is_exact_swap(const PlanOp& p) {
   if (p.phase || p.nt != 2 || p.cmask != 0 || p.grad >= 0) return false;
   for (int e = 0; e < 16; ++e) {
     const int r = e >> 2, c = e & 3;

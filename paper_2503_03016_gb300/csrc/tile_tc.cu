@@ -85,6 +85,15 @@ constexpr int kTtBimg = 2 * 2 * kTtBregion;
 constexpr int kTtImgFloats = kTtBimg / 4;
 constexpr int kTtTileBytes = (1 << kTtM) * 8;   // complex64 tile: 32 KiB
 constexpr int kTtMaxStages = kMaxPassOps;
+// Deferred phase factors.  The non-slot part of a phase op conditioned on at most one
+// slot bit -- exp(i sum beta_b b_b) over row and tile-number bits, applied where the
+// slot bit has its value -- commutes with the rest of its stage when no later op of
+// the stage acts densely on that slot, so it is applied after the stage's product: per
+// output (row r, block index c) one factor F(r, c) = F0(r) prod_k G_k,c_k(r), each
+// factor a row table (128 entries) times a per-tile value from three tile-number chunk
+// tables (3 x 256 entries), all FP64-built on the host and rounded to FP32.
+constexpr int kTtMaxDefStage = 11;  // factors per stage: unconditioned + 5 slots x 2 values
+constexpr int kTtMaxDefPass = 64;   // factors per pass (per-tile values in shared memory)
 constexpr int kTtHi = 1 << (kTtM - kTtL);       // 128-byte runs per tile
 // TMEM columns of a group: A_hi [0, 64), A_lo [64, 128), accumulators [128, 256)
 constexpr int kTmemPerGroup = 256;
@@ -94,9 +103,12 @@ struct TcStage {
   int32_t img;          // index of the stage's B image
   uint32_t swz[5];      // byte offset in the swizzled tile of block-index bit k
   int8_t lane_bit[7];   // local bit receiving bit k of the row index
+  int8_t ndef;          // deferred phase factors of the stage (0: none)
+  int32_t def0;         // global index of its first factor (row and tile-number tables)
+  int8_t dkey[kTtMaxDefStage];  // per factor: -1 unconditioned, else 2 slot + slot value
   int8_t pad;
 };
-static_assert(sizeof(TcStage) == 32, "TcStage must be 32 bytes");
+static_assert(sizeof(TcStage) == 48, "TcStage must be 48 bytes");
 
 constexpr size_t kTtSmem = 1024 /* alignment slack */ + 2 * kTtBimg + 2 * kTtGroups * kTtTileBytes +
                            kTtHi * sizeof(uint64_t) + kTileNumberTab * sizeof(uint64_t) +
@@ -293,13 +305,21 @@ __device__ __forceinline__ void tma_store_tile(uint32_t src, const CUtensorMap* 
   asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
 }
 
-template <bool TMA>
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// DEFER: the pass has stages with deferred phase factors (rowtab, gtab; the pass's
+// factors are global indices [P.pool0, P.pool0 + P.npool))
+template <bool TMA, bool DEFER>
 __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restrict__ amps, const TilePass P,
                                                                  const TcStage* __restrict__ stages,
                                                                  const float* __restrict__ imgs,
                                                                  int* __restrict__ status,
                                                                  const __grid_constant__ CUtensorMap tmap,
-                                                                 const TcTma tm, const TcNorm nrm) {
+                                                                 const TcTma tm, const TcNorm nrm,
+                                                                 const float2* __restrict__ rowtab,
+                                                                 const float2* __restrict__ gtab) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* base =
       reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -319,6 +339,7 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
   __shared__ int8_t sbits[16], ssorted[16];  // the tile's bits in local order / ascending
   __shared__ float s_fac;                                 // this pass's input scale
   __shared__ double s_norm[2][kTtGroups * kTtGroupThreads];  // per-thread norm sums
+  __shared__ float2 s_gfac[DEFER ? kTtGroups : 1][DEFER ? kTtMaxDefPass : 1];  // per-tile factor values
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   constexpr int m = kTtM, L = kTtL;
   constexpr uint32_t T = 1u << m;
@@ -520,6 +541,14 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
       const uint64_t t = t0 + k * G2;
       const bool next = k + 1 < Kg;
       const int nparts = S >= 3 ? 2 : 1;  // load windows: stages 1 .. nparts
+      if constexpr (DEFER) {
+        // this tile's values of the pass's deferred factors (the previous tile's last
+        // stage ended with a group barrier; the barrier below publishes these)
+        for (int i = row; i < P.npool; i += kTtGroupThreads) {
+          const float2* gt = gtab + size_t(P.pool0 + i) * 768;
+          s_gfac[g][i] = cmulf(cmulf(gt[t & 255], gt[256 + ((t >> 8) & 255)]), gt[512 + ((t >> 16) & 255)]);
+        }
+      }
       if (tma) {
         if (!mbar_wait_ab(tload, k & 1u, abort_word))
           failed = true;
@@ -607,6 +636,30 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        // deferred phase factors of this stage: F(c) = A[c & 7] B[c >> 3]
+        float2 fa[8], fb[4];
+        bool defer = false;
+        if constexpr (DEFER) {
+          if (st.ndef > 0) {
+            defer = true;
+            float2 f0 = make_float2(1.0f, 0.0f), gk[5][2];
+#pragma unroll
+            for (int b = 0; b < 5; ++b) gk[b][0] = gk[b][1] = f0;
+            for (int d = 0; d < st.ndef; ++d) {
+              const int src = st.def0 + d;
+              const float2 f = cmulf(rowtab[size_t(src) * kTtRows + row], s_gfac[g][src - P.pool0]);
+              const int key = st.dkey[d];
+              if (key < 0) f0 = cmulf(f0, f);
+#pragma unroll
+              for (int kv = 0; kv < 10; ++kv)
+                if (key == kv) gk[kv >> 1][kv & 1] = cmulf(gk[kv >> 1][kv & 1], f);
+            }
+#pragma unroll
+            for (int c = 0; c < 8; ++c) fa[c] = cmulf(cmulf(cmulf(f0, gk[0][c & 1]), gk[1][(c >> 1) & 1]), gk[2][c >> 2]);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) fb[c] = cmulf(gk[3][c & 1], gk[4][c >> 1]);
+          }
+        }
         // the row of D: the two partial sums added, written into the tile at this
         // stage's positions (for the next stage's gather, or the write-back)
         off[0] = off0;
@@ -622,8 +675,14 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
 #pragma unroll
           for (int i = 16 * q; i < 16 * q + 16; ++i) {
             const int c = (i ^ (i >> 1)) - 16 * q;
-            const float2 y = make_float2(__uint_as_float(d0[2 * c]) + __uint_as_float(d1[2 * c]),
-                                         __uint_as_float(d0[2 * c + 1]) + __uint_as_float(d1[2 * c + 1]));
+            float2 y = make_float2(__uint_as_float(d0[2 * c]) + __uint_as_float(d1[2 * c]),
+                                   __uint_as_float(d0[2 * c + 1]) + __uint_as_float(d1[2 * c + 1]));
+            if constexpr (DEFER) {
+              if (defer) {
+                const int cf = i ^ (i >> 1);
+                y = cmulf(y, cmulf(fa[cf & 7], fb[cf >> 3]));
+              }
+            }
             sout = fmaf(y.x, y.x, fmaf(y.y, y.y, sout));
             sts2(curs + off[i], y);
           }
@@ -765,17 +824,38 @@ static void tc_stage_record(const std::vector<cd>& U, const TileStage& rec, bool
   out.push_back(ts);
 }
 
-// The stages of one pass as 32 x 32 blocks and their B images; false if an op of a
-// stage depends on a bit outside the stage's slots (a control or a phase bit elsewhere).
-static bool tc_pass_blocks(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, bool tma,
-                           std::vector<TcStage>& out, std::vector<float>& imgs) {
+// Deferred phase factors of a circuit plan, host side: per factor a row table (128
+// complex values indexed by the stage's row number) and three tile-number chunk tables
+// (3 x 256), products formed in FP64 and rounded to FP32.
+struct TcDeferTabs {
+  std::vector<float> row;   // 2 x 128 floats per factor
+  std::vector<float> glob;  // 2 x 768 floats per factor
+  int count = 0;
+};
+
+// The stages of one pass as 32 x 32 blocks and their B images.  mode 1: every control
+// and phase bit of an op is a slot of its stage; false if an op depends on a bit outside
+// them.  mode 2: the phase bits of a phase op conditioned on at most one slot need no
+// slot; that part of the op is deferred to the end of the stage (its tables go into
+// tabs); false if a later op of the stage acts densely on the condition's slot, or the
+// factors exceed a stage's or a pass's share.  The pass's factors: global indices
+// [*pass_def0, *pass_def0 + *pass_ndef).
+static bool tc_pass_blocks(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, bool tma, int mode,
+                           std::vector<TcStage>& out, std::vector<float>& imgs, TcDeferTabs& tabs, int* pass_def0,
+                           int* pass_ndef) {
   int local_of[64];
   for (int b = 0; b < 64; ++b) local_of[b] = -1;
   for (int i = 0; i < kTtM; ++i) local_of[bp.B[i]] = i;
+  std::vector<int> tnbits;  // bit i of a tile number sits at global bit tnbits[i]
+  for (int b = 0; b < n; ++b)
+    if (local_of[b] < 0) tnbits.push_back(b);
+  if (mode == 2 && tnbits.size() > 24) return false;
   std::vector<std::vector<int>> takes, acts;
-  split_stages(bp, pops, local_of, kTtSB, takes, acts, /*whole_ops=*/true);
+  split_stages(bp, pops, local_of, kTtSB, takes, acts, mode);
   const std::vector<TileStage> recs = stage_layouts(acts, kTtM, kTtSB, 4);
   constexpr int D = 1 << kTtSB;
+  *pass_def0 = tabs.count;
+  *pass_ndef = 0;
   for (size_t si = 0; si < takes.size(); ++si) {
     int slot_of_local[16];
     for (int k = 0; k < 16; ++k) slot_of_local[k] = -1;
@@ -783,8 +863,13 @@ static bool tc_pass_blocks(const BuiltPass& bp, const std::vector<PlanOp>& pops,
     auto slot_of = [&](int gbit) { return local_of[gbit] < 0 ? -1 : slot_of_local[local_of[gbit]]; };
     std::vector<cd> U(D * D, cd(0.0, 0.0));  // U[row * D + col]
     for (int d = 0; d < D; ++d) U[d * D + d] = 1.0;
-    for (int idx : takes[si]) {
-      const PlanOp& p = pops[idx];
+    // deferred factors of the stage: key (-1, or 2 slot + value) and their angles on
+    // the tile's local bits and on the global bits
+    std::vector<int> dkeys;
+    std::vector<std::vector<double>> dloc, dglob;
+    const std::vector<int>& tk = takes[si];
+    for (size_t oi = 0; oi < tk.size(); ++oi) {
+      const PlanOp& p = pops[tk[oi]];
       uint32_t cm = 0, cv = 0;
       for (int b = 0; b < n; ++b) {
         if (!((p.cmask >> b) & 1)) continue;
@@ -794,11 +879,48 @@ static bool tc_pass_blocks(const BuiltPass& bp, const std::vector<PlanOp>& pops,
         if ((p.cval >> b) & 1) cv |= 1u << k;
       }
       if (p.phase) {
-        std::vector<std::pair<int, double>> bs;
+        std::vector<std::pair<int, double>> bs, rest;
         for (const auto& be : p.beta) {
           const int k = slot_of(be.first);
-          if (k < 0) return false;
-          bs.push_back({k, be.second});
+          if (k >= 0)
+            bs.push_back({k, be.second});
+          else if (mode == 2)
+            rest.push_back(be);
+          else
+            return false;
+        }
+        if (!rest.empty()) {
+          if (__builtin_popcount(cm) >= 2) return false;
+          int key = -1;
+          if (cm) {
+            // the factor moves past the stage's later ops: none may act densely on its
+            // slot, except an exact SWAP, which moves the factor to the other slot
+            const int k0 = __builtin_ctz(cm);
+            int k = k0;
+            for (size_t oj = oi + 1; oj < tk.size(); ++oj) {
+              const PlanOp& q = pops[tk[oj]];
+              if (q.phase) continue;
+              bool hit = false;
+              for (int t = 0; t < q.nt; ++t) hit |= slot_of(q.tb[t]) == k;
+              if (!hit) continue;
+              if (!is_exact_swap(q)) return false;
+              const int a = slot_of(q.tb[0]), b = slot_of(q.tb[1]);
+              k = a == k ? b : a;
+            }
+            key = 2 * k + int((cv >> k0) & 1u);
+          }
+          int f = int(std::find(dkeys.begin(), dkeys.end(), key) - dkeys.begin());
+          if (f == int(dkeys.size())) {
+            dkeys.push_back(key);
+            dloc.push_back(std::vector<double>(kTtM, 0.0));
+            dglob.push_back(std::vector<double>(n, 0.0));
+          }
+          for (const auto& be : rest) {
+            if (local_of[be.first] >= 0)
+              dloc[f][local_of[be.first]] += be.second;
+            else
+              dglob[f][be.first] += be.second;
+          }
         }
         for (int d = 0; d < D; ++d) {
           if ((uint32_t(d) & cm) != cv) continue;
@@ -838,6 +960,33 @@ static bool tc_pass_blocks(const BuiltPass& bp, const std::vector<PlanOp>& pops,
       }
     }
     tc_stage_record(U, recs[si], tma, out, imgs);
+    if (!dkeys.empty()) {
+      const int nd = int(dkeys.size());
+      if (nd > kTtMaxDefStage || *pass_ndef + nd > kTtMaxDefPass) return false;
+      TcStage& ts = out.back();
+      ts.ndef = int8_t(nd);
+      ts.def0 = tabs.count;
+      for (int f = 0; f < nd; ++f) {
+        ts.dkey[f] = int8_t(dkeys[f]);
+        for (int r = 0; r < kTtRows; ++r) {  // row bit b sits at local bit lane_bit[b]
+          double ang = 0.0;
+          for (int b = 0; b < kTtM - kTtSB; ++b)
+            if ((r >> b) & 1) ang += dloc[f][ts.lane_bit[b]];
+          tabs.row.push_back(float(std::cos(ang)));
+          tabs.row.push_back(float(std::sin(ang)));
+        }
+        for (int c = 0; c < 3; ++c)
+          for (int v = 0; v < 256; ++v) {
+            double ang = 0.0;
+            for (int i = 0; i < 8; ++i)
+              if (((v >> i) & 1) && 8 * c + i < int(tnbits.size())) ang += dglob[f][tnbits[8 * c + i]];
+            tabs.glob.push_back(float(std::cos(ang)));
+            tabs.glob.push_back(float(std::sin(ang)));
+          }
+        ++tabs.count;
+      }
+      *pass_ndef += nd;
+    }
   }
   return true;
 }
@@ -974,11 +1123,13 @@ struct TcPlanCache {
   bool tc = false;  // false: an op depends on a bit outside its stage (CUDA-core passes)
   std::vector<TilePass> passes;
   std::vector<TcTma> tmas;  // per pass: box copies or cp.async
+  std::vector<char> defer;  // per pass: stages with deferred phase factors
   int nstages = 0;
   std::vector<char> host;  // staging of the upload (kept until the next rebuild)
   void* dev = nullptr;
   size_t dev_bytes = 0;
   size_t stage_bytes = 0;
+  size_t row_off = 0, glob_off = 0;  // byte offsets of the factor tables in `dev`
   cudaEvent_t done = nullptr;  // recorded after the launches that read `dev`
   bool pending = false;
 };
@@ -1004,11 +1155,13 @@ static qc_status tc_plan(qc_state* s, const std::vector<ResolvedOp>& rops, int d
   g_tc.valid = false;
   std::vector<PlanOp> pops;
   to_plan_ops(rops, pops);
-  const std::vector<BuiltPass> bps = build_passes(pops, n, kTtM, kTtL);
+  const std::vector<BuiltPass> bps = build_passes(pops, n, kTtM, kTtL, /*cond_in_tile=*/true);
   std::vector<TilePass> passes;
   std::vector<TcTma> tmas;
+  std::vector<char> defer;
   std::vector<TcStage> stages;
   std::vector<float> imgs;
+  TcDeferTabs tabs;
   bool tc = true;
   for (const BuiltPass& bp : bps) {
     std::vector<int> Bloc;
@@ -1025,10 +1178,36 @@ static qc_status tc_plan(qc_state* s, const std::vector<ResolvedOp>& rops, int d
     for (int i = 0; i < kTtM; ++i) P.bits[i] = int8_t(bl.B[i]);
     P.ntiles = uint64_t(1) << (n - kTtM);
     P.stage0 = int(stages.size());
-    if (!tc_pass_blocks(bl, pops, n, tm.tma != 0, stages, imgs)) {  // the CUDA-core passes take it
+    // every phase bit a slot (mode 1), or phase bits off the slots deferred (mode 2):
+    // the fewer stages win (mode 1 on ties); neither: the CUDA-core passes take the
+    // circuit
+    int def0 = 0, ndef = 0;
+    const size_t i0 = imgs.size(), r0 = tabs.row.size(), g0 = tabs.glob.size();
+    const int c0 = tabs.count;
+    auto reset = [&]() {
+      stages.resize(size_t(P.stage0));
+      imgs.resize(i0);
+      tabs.row.resize(r0);
+      tabs.glob.resize(g0);
+      tabs.count = c0;
+    };
+    int nst[3] = {0, -1, -1};
+    for (int mode = 1; mode <= 2; ++mode) {
+      reset();
+      if (tc_pass_blocks(bl, pops, n, tm.tma != 0, mode, stages, imgs, tabs, &def0, &ndef))
+        nst[mode] = int(stages.size()) - P.stage0;
+    }
+    const int pick = nst[1] >= 0 && (nst[2] < 0 || nst[1] <= nst[2]) ? 1 : nst[2] >= 0 ? 2 : 0;
+    if (pick == 0) {
       tc = false;
       break;
     }
+    if (pick == 1) {  // (mode 2's tables are the last written: plan mode 1 again)
+      reset();
+      tc_pass_blocks(bl, pops, n, tm.tma != 0, 1, stages, imgs, tabs, &def0, &ndef);
+    }
+    P.pool0 = def0;  // the pass's deferred factors (global indices)
+    P.npool = ndef;
     P.nstages = int(stages.size()) - P.stage0;
     if (P.nstages > kTtMaxStages) {
       tc = false;
@@ -1036,6 +1215,7 @@ static qc_status tc_plan(qc_state* s, const std::vector<ResolvedOp>& rops, int d
     }
     passes.push_back(P);
     tmas.push_back(tm);
+    defer.push_back(ndef > 0 ? 1 : 0);
   }
   g_tc.device = dev;
   g_tc.n = n;
@@ -1045,24 +1225,28 @@ static qc_status tc_plan(qc_state* s, const std::vector<ResolvedOp>& rops, int d
   if (!tc) return QC_OK;
   auto al = [](size_t b) { return (b + 255) & ~size_t(255); };
   const size_t sb = al(stages.size() * sizeof(TcStage) + 1);
-  const size_t ib = imgs.size() * sizeof(float);
-  g_tc.host.assign(sb + ib, 0);
+  const size_t ib = al(imgs.size() * sizeof(float));
+  const size_t rb = al(tabs.row.size() * sizeof(float)), gb = tabs.glob.size() * sizeof(float);
+  const size_t total = sb + ib + rb + gb;
+  g_tc.host.assign(total, 0);
   if (!stages.empty()) memcpy(g_tc.host.data(), stages.data(), stages.size() * sizeof(TcStage));
-  if (ib) memcpy(g_tc.host.data() + sb, imgs.data(), ib);
+  if (!imgs.empty()) memcpy(g_tc.host.data() + sb, imgs.data(), imgs.size() * sizeof(float));
+  if (!tabs.row.empty()) memcpy(g_tc.host.data() + sb + ib, tabs.row.data(), tabs.row.size() * sizeof(float));
+  if (gb) memcpy(g_tc.host.data() + sb + ib + rb, tabs.glob.data(), gb);
   // the previous plan's launches are done with the buffer before it is overwritten
   if (g_tc.pending) cudaEventSynchronize(g_tc.done);
   g_tc.pending = false;
-  if (g_tc.dev_bytes < sb + ib) {
+  if (g_tc.dev_bytes < total) {
     if (g_tc.dev) cudaFree(g_tc.dev);
     g_tc.dev = nullptr;
     g_tc.dev_bytes = 0;
-    if (qc_status st = check_cuda(cudaMalloc(&g_tc.dev, sb + ib), "tensor-core plan buffer")) {
+    if (qc_status st = check_cuda(cudaMalloc(&g_tc.dev, total), "tensor-core plan buffer")) {
       g_tc.valid = false;
       return st;
     }
-    g_tc.dev_bytes = sb + ib;
+    g_tc.dev_bytes = total;
   }
-  if (qc_status st = check_cuda(cudaMemcpyAsync(g_tc.dev, g_tc.host.data(), sb + ib, cudaMemcpyHostToDevice,
+  if (qc_status st = check_cuda(cudaMemcpyAsync(g_tc.dev, g_tc.host.data(), total, cudaMemcpyHostToDevice,
                                                 s->stream),
                                 "tensor-core plan upload")) {
     g_tc.valid = false;
@@ -1070,14 +1254,18 @@ static qc_status tc_plan(qc_state* s, const std::vector<ResolvedOp>& rops, int d
   }
   g_tc.passes = passes;
   g_tc.tmas = tmas;
+  g_tc.defer = defer;
   g_tc.nstages = int(stages.size());
   g_tc.stage_bytes = sb;
+  g_tc.row_off = sb + ib;
+  g_tc.glob_off = sb + ib + rb;
   return QC_OK;
 }
 
 // the shared-memory opt-in of both pass kernels
 static qc_status tc_pass_smem() {
-  for (auto kern : {k_tile_pass_tc<false>, k_tile_pass_tc<true>})
+  for (auto kern : {k_tile_pass_tc<false, false>, k_tile_pass_tc<true, false>, k_tile_pass_tc<false, true>,
+                    k_tile_pass_tc<true, true>})
     if (qc_status st = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                        int(kTtSmem)),
                                   "tensor-core tile pass shared memory"))
@@ -1085,9 +1273,11 @@ static qc_status tc_pass_smem() {
   return QC_OK;
 }
 
-// one pass on s's stream: box copies with a tensor map of this state where tm.tma
-static qc_status launch_tc_pass(qc_state* s, const TilePass& P, const TcTma& tm, const TcStage* dst, const float* dimg,
-                                int* status, const TcNorm& nm, unsigned grid) {
+// one pass on s's stream: box copies with a tensor map of this state where tm.tma;
+// defer: the pass's stages have deferred phase factors (tables rowtab, gtab)
+static qc_status launch_tc_pass(qc_state* s, const TilePass& P, const TcTma& tm, bool defer, const TcStage* dst,
+                                const float* dimg, int* status, const TcNorm& nm, unsigned grid,
+                                const float2* rowtab = nullptr, const float2* gtab = nullptr) {
   alignas(64) CUtensorMap map;
   memset(&map, 0, sizeof(map));
   if (tm.tma && !encode_tile_map(&map, tm, s->amps, s->n)) {
@@ -1095,10 +1285,9 @@ static qc_status launch_tc_pass(qc_state* s, const TilePass& P, const TcTma& tm,
     return QC_ERR_CUDA;
   }
   float* a = reinterpret_cast<float*>(s->amps);
-  if (tm.tma)
-    QC_COUNT(), k_tile_pass_tc<true><<<grid, kTtThreads, kTtSmem, s->stream>>>(a, P, dst, dimg, status, map, tm, nm);
-  else
-    QC_COUNT(), k_tile_pass_tc<false><<<grid, kTtThreads, kTtSmem, s->stream>>>(a, P, dst, dimg, status, map, tm, nm);
+  auto kern = tm.tma ? (defer ? k_tile_pass_tc<true, true> : k_tile_pass_tc<true, false>)
+                     : (defer ? k_tile_pass_tc<false, true> : k_tile_pass_tc<false, false>);
+  QC_COUNT(), kern<<<grid, kTtThreads, kTtSmem, s->stream>>>(a, P, dst, dimg, status, map, tm, nm, rowtab, gtab);
   return QC_OK;
 }
 
@@ -1127,6 +1316,8 @@ qc_status run_tiles_tc(qc_state* s, const std::vector<ResolvedOp>& rops, bool* h
   for (const TilePass& P : g_tc.passes) restore &= P.nstages > 0;
   const TcStage* dst = static_cast<const TcStage*>(g_tc.dev);
   const float* dimg = reinterpret_cast<const float*>(static_cast<char*>(g_tc.dev) + g_tc.stage_bytes);
+  const float2* drow = reinterpret_cast<const float2*>(static_cast<char*>(g_tc.dev) + g_tc.row_off);
+  const float2* dglob = reinterpret_cast<const float2*>(static_cast<char*>(g_tc.dev) + g_tc.glob_off);
   if (qc_status st = check_cuda(cudaMemsetAsync(status, 0, sizeof(int), s->stream), "status reset")) return st;
   if (qc_status st = tc_pass_smem()) return st;
   const uint64_t ntiles = uint64_t(1) << (n - kTtM);
@@ -1140,7 +1331,9 @@ qc_status run_tiles_tc(qc_state* s, const std::vector<ResolvedOp>& rops, bool* h
     nm.in_part = norm_in;
     nm.out_prev = norm_out[(i + 1) & 1];
     nm.out_cur = norm_out[i & 1];
-    if (qc_status st = launch_tc_pass(s, g_tc.passes[i], g_tc.tmas[i], dst, dimg, status, nm, grid)) return st;
+    if (qc_status st = launch_tc_pass(s, g_tc.passes[i], g_tc.tmas[i], g_tc.defer[i] != 0, dst, dimg, status, nm,
+                                      grid, drow, dglob))
+      return st;
   }
   if (qc_status st = check_launch("tensor-core tile pass")) return st;
   if (qc_status st = check_cuda(cudaEventRecord(g_tc.done, s->stream), "plan event")) return st;
@@ -1286,7 +1479,7 @@ qc_status apply_block_tile_tc(qc_state* s, const int* bits, int k, const double*
   nm.in_part = norms;
   nm.out_prev = norms;
   nm.out_cur = norms;
-  if (qc_status st = launch_tc_pass(s, P, tm, reinterpret_cast<const TcStage*>(base + o_rec),
+  if (qc_status st = launch_tc_pass(s, P, tm, false, reinterpret_cast<const TcStage*>(base + o_rec),
                                     reinterpret_cast<const float*>(base + o_img), status, nm, grid))
     return st;
   if (qc_status st = check_launch("tensor-core block pass")) return st;

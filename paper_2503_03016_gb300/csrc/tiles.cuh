@@ -566,10 +566,14 @@ extern thread_local int g_last_stage_count;
 // rotations stay dense, Z rotations become phase ops)
 void to_plan_ops(const std::vector<ResolvedOp>& in, std::vector<PlanOp>& out, const std::vector<int>* grad = nullptr,
                  const std::vector<int>* gen = nullptr);
+// exactly the SWAP permutation of its two target bits, with no condition
+bool is_exact_swap(const PlanOp& p);
 // sets the constant of every unconditioned phase op to 0 (a global phase)
 void drop_global_phases(std::vector<PlanOp>& pops);
-// plan ops -> passes of tile bit sets B (m bits, the L lowest always included)
-std::vector<BuiltPass> build_passes(const std::vector<PlanOp>& ops, int n, int m, int L);
+// plan ops -> passes of tile bit sets B (m bits, the L lowest always included); with
+// cond_in_tile every condition bit of an op (a control, a phase op's condition) is a
+// tile bit of the pass that takes it, as the tensor-core stages need
+std::vector<BuiltPass> build_passes(const std::vector<PlanOp>& ops, int n, int m, int L, bool cond_in_tile = false);
 // one pass -> its register stages, tile ops and matrices (sb: stage width); with
 // swap_ops, an exact SWAP becomes a register permutation (TOP_SWAP) instead of a dense
 // 4x4 (kernels that hold two states per thread keep the dense form: fewer registers);
@@ -586,9 +590,10 @@ void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int 
                bool bfly_ops = false, bool real1_ops = false);
 // a pass's ops -> register stages (local_of: local bit of each global bit, -1 outside
 // the tile); takes[s] = the ops of stage s, acts[s] = the local bits their targets use
-// (whole_ops: control and phase bits in the tile count as active bits too)
+// (whole_ops 1: control and phase bits in the tile count as active bits too; 2: as 1,
+// except the phase bits of a phase op conditioned on at most one bit)
 void split_stages(const BuiltPass& bp, const std::vector<PlanOp>& pops, const int* local_of, int sb,
-                  std::vector<std::vector<int>>& takes, std::vector<std::vector<int>>& acts, bool whole_ops = false);
+                  std::vector<std::vector<int>>& takes, std::vector<std::vector<int>>& acts, int whole_ops = 0);
 // slot bits (acts[s] padded to sb) and thread-index bits of each stage (m - sb of them,
 // the first ones one per residue mod nres); warp bits kept over runs of stages
 std::vector<TileStage> stage_layouts(const std::vector<std::vector<int>>& acts, int m, int sb, int nres);

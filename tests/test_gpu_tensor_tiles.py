@@ -95,15 +95,50 @@ def test_tc_one_qubit_controlled_and_diagonal_ops():
     assert rel_l2(got, want) <= TOL["c64"]
 
 
-@pytest.mark.parametrize("n", [14, 16])
-def test_tc_falls_back_when_a_control_leaves_the_stage(n):
-    """QFT on more qubits than a tile holds: the controlled-phase ladders reach bits
-    outside the tile, so the circuit runs on the CUDA-core passes; the result is the
-    same."""
+@pytest.mark.parametrize("n", [14, 16, 20])
+def test_tc_qft_defers_phase_bits(n):
+    """QFT on more qubits than a tile holds: the controlled-phase ladders reach row bits
+    and bits outside the tile.  Each ladder is keyed on its target (a stage slot); the
+    part of its phases on the other bits commutes with the rest of the stage and is
+    applied per output after the stage's product, so the circuit runs on the tensor
+    cores."""
     ops = W.qft(n)
     x = W.gaussian_state(n, 3)
     got, want, path = run_tc(n, ops, psi=x)
-    assert path == 1
+    assert path == 2
+    assert rel_l2(got, want) <= TOL["c64"]
+
+
+def test_tc_inverse_qft_and_open_control_phases():
+    """The inverse QFT (negative ladders, the swaps first) and controlled phases on far
+    qubits with open and closed controls, interleaved with Hadamards and T gates."""
+    n = 18
+    ops = W.circuit_inverse(W.qft(n))
+    rng = np.random.default_rng(8)
+    for i in range(40):
+        a, b = (int(v) for v in rng.choice(n, 2, replace=False))
+        ph = float(rng.uniform(0, 6.3))
+        if i % 3 == 0:
+            ops.append(Op("cp", (a, b), (ph,)))
+        elif i % 3 == 1:
+            ops.append(Op("ctrl", (a, b), matrix=np.diag([1.0, np.exp(1j * ph)]), ctrl_states=(0,)))
+        else:
+            ops += [Op("h", (a,)), Op("t", (b,))]
+    x = W.gaussian_state(n, 5)
+    got, want, path = run_tc(n, ops, psi=x)
+    assert path in (1, 2)
+    assert rel_l2(got, want) <= TOL["c64"]
+
+
+def test_tc_falls_back_for_a_doubly_controlled_phase_outside_the_tile():
+    """A phase conditioned on two far qubits whose phase bit lies elsewhere cannot be
+    deferred (its condition spans two slots); the result is the same either way."""
+    n = 16
+    ops = [Op("h", (q,)) for q in range(n)]
+    ops.append(Op("ctrl", (0, n - 1, n // 2), matrix=np.diag([1.0, np.exp(0.7j)])))
+    ops += [Op("h", (q,)) for q in range(0, n, 3)]
+    got, want, path = run_tc(n, ops)
+    assert path in (1, 2)
     assert rel_l2(got, want) <= TOL["c64"]
 
 
