@@ -623,6 +623,7 @@ def run_qft_bench(args):
                                               "gbs": gbs, "frac_hbm": gbs / hbm}
             if mode == P.QC_RUN_FUSED:
                 res["%s_%s" % (dt, mode_name)]["path"] = P.qc_last_fused_path()
+                res["%s_%s" % (dt, mode_name)]["stages"] = P.qc_last_stage_count()
         st.free()
         torch.cuda.empty_cache()
     print(json.dumps({"metric": "QFT on %d qubits (%d gates)" % (n, len(ops)), "results": res,

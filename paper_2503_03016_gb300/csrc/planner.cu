@@ -634,7 +634,7 @@ bool is_exact_swap(const PlanOp& p) {
 }
 
 // an op with its global bits renamed: bit b -> ren[b]
-static PlanOp renamed(const PlanOp& p, const int* ren) {
+PlanOp renamed(const PlanOp& p, const int* ren) {
   PlanOp q = p;
   for (int k = 0; k < p.nt && !p.phase; ++k) q.tb[k] = ren[p.tb[k]];
   auto map_mask = [&](uint64_t mk) {

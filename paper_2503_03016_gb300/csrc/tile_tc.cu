@@ -337,6 +337,7 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 13);
   volatile int* abort_word = reinterpret_cast<volatile int*>(tmem_slot + 1);
   __shared__ int8_t sbits[16], ssorted[16];  // the tile's bits in local order / ascending
+  __shared__ int8_t srbit[16];                // relabeled SWAPs: see TilePass::rbit
   __shared__ float s_fac;                                 // this pass's input scale
   __shared__ double s_norm[2][kTtGroups * kTtGroupThreads];  // per-thread norm sums
   __shared__ float2 s_gfac[DEFER ? kTtGroups : 1][DEFER ? kTtMaxDefPass : 1];  // per-tile factor values
@@ -347,7 +348,10 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
 
   if (tid == 0) {
 #pragma unroll
-    for (int k = 0; k < 16; ++k) sbits[k] = ssorted[k] = P.bits[k];
+    for (int k = 0; k < 16; ++k) {
+      sbits[k] = ssorted[k] = P.bits[k];
+      srbit[k] = P.rbit[k];
+    }
     for (int k = 1; k < m; ++k)  // insertion sort of the m tile bits
       for (int j = k; j > 0 && ssorted[j - 1] > ssorted[j]; --j) {
         const int8_t x = ssorted[j];
@@ -694,6 +698,33 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
         group_sync(g);  // the tile is complete before the next stage gathers
       }
       if (failed) break;
+      if (P.permuted) {
+        // the pass's exact SWAPs, taken as a relabeling: output u (the thread's row in
+        // its low 7 bits, c above) takes the value at the tile position whose bit
+        // rbit[k] is bit k of u; both offsets are XOR-linear in u
+        auto perm = [&](uint32_t u) {
+          uint32_t v = 0;
+          for (int kb = 0; kb < m; ++kb) v |= ((u >> kb) & 1u) << srbit[kb];
+          return v;
+        };
+        auto swz = [&](uint32_t u) { return tma ? tma_swz_bytes(u) : tile_swz(u) * 8u; };
+        uint32_t pb[5];
+#pragma unroll
+        for (int b = 0; b < 5; ++b) pb[b] = swz(perm(1u << (7 + b)));
+        uint32_t o = swz(perm(uint32_t(row)));
+        float2 pv[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {  // Gray order: c = i ^ (i >> 1)
+          if (i) o ^= pb[__ffs(i) - 1];
+          pv[i ^ (i >> 1)] = lds2(curs + o);
+        }
+        group_sync(g);
+        const uint32_t d0 = swz(uint32_t(row));
+#pragma unroll
+        for (int c = 0; c < 32; ++c) sts2(curs + (d0 ^ swz(uint32_t(c) << 7)), pv[c]);
+        if (tma) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        group_sync(g);
+      }
       if (tma) {
         if (elect) {
           int32_t c[5];
@@ -1178,9 +1209,36 @@ static qc_status tc_plan(qc_state* s, const std::vector<ResolvedOp>& rops, int d
     for (int i = 0; i < kTtM; ++i) P.bits[i] = int8_t(bl.B[i]);
     P.ntiles = uint64_t(1) << (n - kTtM);
     P.stage0 = int(stages.size());
-    // every phase bit a slot (mode 1), or phase bits off the slots deferred (mode 2):
-    // the fewer stages win (mode 1 on ties); neither: the CUDA-core passes take the
-    // circuit
+    // The pass's exact SWAPs of two tile bits, either as ops of the stages or as a
+    // relabeling (the later ops renamed, the tile permuted before its write-back:
+    // rbit[k] = the local bit where the data of local bit k sits).
+    std::vector<PlanOp> rpops;
+    BuiltPass br;
+    br.B = bl.B;
+    int8_t rbit[16];
+    bool permuted = false;
+    {
+      int ren[64], loc[64];
+      for (int b = 0; b < 64; ++b) {
+        ren[b] = b;
+        loc[b] = -1;
+      }
+      for (int i = 0; i < kTtM; ++i) loc[bl.B[i]] = i;
+      for (int idx : bl.ops) {
+        const PlanOp& p = pops[idx];
+        if (is_exact_swap(p) && loc[ren[p.tb[0]]] >= 0 && loc[ren[p.tb[1]]] >= 0) {
+          std::swap(ren[p.tb[0]], ren[p.tb[1]]);
+          permuted = true;
+          continue;
+        }
+        br.ops.push_back(int(rpops.size()));
+        rpops.push_back(renamed(p, ren));
+      }
+      for (int k = 0; k < 16; ++k) rbit[k] = int8_t(k < kTtM && permuted ? loc[ren[bl.B[k]]] : k);
+    }
+    // every phase bit a slot (mode 1), or phase bits off the slots deferred (mode 2);
+    // SWAPs as ops or relabeled: the fewest stages win (a relabeling counts half a
+    // stage; the earlier variant on ties); none: the CUDA-core passes take the circuit
     int def0 = 0, ndef = 0;
     const size_t i0 = imgs.size(), r0 = tabs.row.size(), g0 = tabs.glob.size();
     const int c0 = tabs.count;
@@ -1191,20 +1249,33 @@ static qc_status tc_plan(qc_state* s, const std::vector<ResolvedOp>& rops, int d
       tabs.glob.resize(g0);
       tabs.count = c0;
     };
-    int nst[3] = {0, -1, -1};
-    for (int mode = 1; mode <= 2; ++mode) {
+    auto plan = [&](int v) {  // v: 2 relabel + (mode - 1)
+      const bool rl = v >= 2;
+      return tc_pass_blocks(rl ? br : bl, rl ? rpops : pops, n, tm.tma != 0, 1 + (v & 1), stages, imgs, tabs,
+                            &def0, &ndef);
+    };
+    int pick = -1;
+    double best = 1e30;
+    for (int v = 0; v < (permuted ? 4 : 2); ++v) {
       reset();
-      if (tc_pass_blocks(bl, pops, n, tm.tma != 0, mode, stages, imgs, tabs, &def0, &ndef))
-        nst[mode] = int(stages.size()) - P.stage0;
+      if (!plan(v)) continue;
+      const double score = double(stages.size() - size_t(P.stage0)) + (v >= 2 ? 0.5 : 0.0);
+      if (score < best) {
+        best = score;
+        pick = v;
+      }
     }
-    const int pick = nst[1] >= 0 && (nst[2] < 0 || nst[1] <= nst[2]) ? 1 : nst[2] >= 0 ? 2 : 0;
-    if (pick == 0) {
+    if (pick < 0) {
       tc = false;
       break;
     }
-    if (pick == 1) {  // (mode 2's tables are the last written: plan mode 1 again)
-      reset();
-      tc_pass_blocks(bl, pops, n, tm.tma != 0, 1, stages, imgs, tabs, &def0, &ndef);
+    reset();
+    plan(pick);
+    if (pick >= 2) {
+      P.permuted = 1;
+      for (int k = 0; k < 16; ++k) P.rbit[k] = rbit[k];
+    } else {
+      for (int k = 0; k < 16; ++k) P.rbit[k] = int8_t(k);
     }
     P.pool0 = def0;  // the pass's deferred factors (global indices)
     P.npool = ndef;

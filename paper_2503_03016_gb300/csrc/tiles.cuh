@@ -568,6 +568,8 @@ void to_plan_ops(const std::vector<ResolvedOp>& in, std::vector<PlanOp>& out, co
                  const std::vector<int>* gen = nullptr);
 // exactly the SWAP permutation of its two target bits, with no condition
 bool is_exact_swap(const PlanOp& p);
+// an op with its global bits renamed: bit b -> ren[b]
+PlanOp renamed(const PlanOp& p, const int* ren);
 // sets the constant of every unconditioned phase op to 0 (a global phase)
 void drop_global_phases(std::vector<PlanOp>& pops);
 // plan ops -> passes of tile bit sets B (m bits, the L lowest always included); with

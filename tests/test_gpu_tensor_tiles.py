@@ -197,3 +197,23 @@ def test_bf16x3_is_rejected():
     with pytest.raises(P.QCError) as e:
         st.run(W.brickwork(12, 2, 1), mode=P.QC_RUN_FUSED, prec=P.QC_PREC_BF16X3)
     assert e.value.status == 4
+
+
+@pytest.mark.parametrize("n", [13, 17])
+def test_tc_swaps_as_relabelings(n):
+    """SWAPs between random qubits among dense two-qubit gates and a final bit
+    reversal: a pass may take its SWAPs as a relabeling (the tile permuted before its
+    write-back) instead of stage ops; the result matches the oracle either way."""
+    rng = np.random.default_rng(n)
+    U = W.haar_unitaries(60, 4, 3 * n)
+    ops = []
+    for i in range(60):
+        a = int(rng.integers(0, n - 1))
+        ops.append(Op("u2q", (a, a + 1), matrix=U[i]))
+        if i % 4 == 3:
+            b, c = (int(v) for v in rng.choice(n, 2, replace=False))
+            ops.append(Op("swap", (b, c)))
+    ops += [Op("swap", (j, n - 1 - j)) for j in range(n // 2)]
+    got, want, path = run_tc(n, ops)
+    assert path == 2
+    assert rel_l2(got, want) <= TOL["c64"]
