@@ -1110,6 +1110,28 @@ static qc_status run_tiles(qc_state* s, const std::vector<ResolvedOp>& rops, int
   return check_launch("tile pass");
 }
 
+qc_status launch_copy_pass(qc_state* s, const TilePass& P0) {
+  TilePass P = P0;  // no stages, ops or tables: the tiles are copied through the relabeling
+  P.stage0 = P.nstages = P.op0 = P.nops = P.mat0 = P.nmat = P.pool0 = P.npool = P.spool = 0;
+  const int m = P.m, L = P.L;
+  const size_t smem = 2 * sizeof(Cplx<float>) * (size_t(1) << m) +
+                      (sizeof(uint64_t) + sizeof(uint32_t)) * (size_t(1) << (m - L)) +
+                      sizeof(uint64_t) * kTileNumberTab;
+  constexpr int NT = TileShape<float>::NT, SBK = TileShape<float>::SB;
+  auto kern = k_tile_pass<float, NT, SBK, true>;
+  if (qc_status st = check_cuda(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)),
+                                "copy pass shared memory"))
+    return st;
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem);
+  if (per_sm < 1) per_sm = 1;
+  const uint64_t cap = uint64_t(device_sm_count()) * per_sm;
+  const unsigned grid = unsigned(P.ntiles < cap ? P.ntiles : cap);
+  QC_COUNT(), kern<<<grid, NT, smem, s->stream>>>(reinterpret_cast<float*>(s->amps), P, nullptr, nullptr, nullptr,
+                                                  nullptr);
+  return check_launch("copy pass");
+}
+
 int tile_bits_for(const qc_state* s) {
   const int want = s->dtype == QC_C64 ? 13 : 12;
   return std::min(want, s->n);

@@ -1154,7 +1154,7 @@ struct TcPlanCache {
   bool tc = false;  // false: an op depends on a bit outside its stage (CUDA-core passes)
   std::vector<TilePass> passes;
   std::vector<TcTma> tmas;  // per pass: box copies or cp.async
-  std::vector<char> defer;  // per pass: stages with deferred phase factors
+  std::vector<char> defer;  // per pass: 1 stages with deferred phase factors, 2 a copy pass
   int nstages = 0;
   std::vector<char> host;  // staging of the upload (kept until the next rebuild)
   void* dev = nullptr;
@@ -1271,9 +1271,30 @@ static qc_status tc_plan(qc_state* s, const std::vector<ResolvedOp>& rops, int d
     }
     reset();
     plan(pick);
+    bool copy = false;
     if (pick >= 2) {
       P.permuted = 1;
       for (int k = 0; k < 16; ++k) P.rbit[k] = rbit[k];
+      if (int(stages.size()) == P.stage0) {
+        // nothing but the relabeling: the CUDA-core pass copies the tiles (bits in
+        // ascending order, the relabeling in that order)
+        copy = true;
+        int ren[64], loc[64];
+        for (int b = 0; b < 64; ++b) {
+          ren[b] = b;
+          loc[b] = -1;
+        }
+        for (int i = 0; i < kTtM; ++i) loc[bp.B[i]] = i;
+        for (int idx : bp.ops) {
+          const PlanOp& p = pops[idx];
+          if (is_exact_swap(p) && loc[ren[p.tb[0]]] >= 0 && loc[ren[p.tb[1]]] >= 0)
+            std::swap(ren[p.tb[0]], ren[p.tb[1]]);
+        }
+        for (int k = 0; k < 16; ++k) {
+          P.bits[k] = int8_t(k < kTtM ? bp.B[k] : 0);
+          P.rbit[k] = int8_t(k < kTtM ? loc[ren[bp.B[k]]] : k);
+        }
+      }
     } else {
       for (int k = 0; k < 16; ++k) P.rbit[k] = int8_t(k);
     }
@@ -1286,7 +1307,7 @@ static qc_status tc_plan(qc_state* s, const std::vector<ResolvedOp>& rops, int d
     }
     passes.push_back(P);
     tmas.push_back(tm);
-    defer.push_back(ndef > 0 ? 1 : 0);
+    defer.push_back(copy ? 2 : ndef > 0 ? 1 : 0);
   }
   g_tc.device = dev;
   g_tc.n = n;
@@ -1402,6 +1423,10 @@ qc_status run_tiles_tc(qc_state* s, const std::vector<ResolvedOp>& rops, bool* h
     nm.in_part = norm_in;
     nm.out_prev = norm_out[(i + 1) & 1];
     nm.out_cur = norm_out[i & 1];
+    if (g_tc.defer[i] == 2) {
+      if (qc_status st = launch_copy_pass(s, g_tc.passes[i])) return st;
+      continue;
+    }
     if (qc_status st = launch_tc_pass(s, g_tc.passes[i], g_tc.tmas[i], g_tc.defer[i] != 0, dst, dimg, status, nm,
                                       grid, drow, dglob))
       return st;

@@ -566,6 +566,9 @@ extern thread_local int g_last_stage_count;
 // rotations stay dense, Z rotations become phase ops)
 void to_plan_ops(const std::vector<ResolvedOp>& in, std::vector<PlanOp>& out, const std::vector<int>* grad = nullptr,
                  const std::vector<int>* gen = nullptr);
+// a complex64 pass with no stages whose SWAPs are a relabeling (P.permuted, P.rbit; P.bits
+// ascending): each tile copied through the permutation by the CUDA-core tile pass
+qc_status launch_copy_pass(qc_state* s, const TilePass& P);
 // exactly the SWAP permutation of its two target bits, with no condition
 bool is_exact_swap(const PlanOp& p);
 // an op with its global bits renamed: bit b -> ren[b]

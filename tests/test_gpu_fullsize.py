@@ -28,7 +28,10 @@ def _free_gb():
     return free / 2 ** 30
 
 
-def test_qft32_c64_gaussian_sampled_outputs():
+@pytest.mark.parametrize("prec", ["native", "tf32x3"])
+def test_qft32_c64_gaussian_sampled_outputs(prec):
+    """The fused QFT-32 on the CUDA-core passes and on the tensor-core passes (deferred
+    phase factors, relabeled SWAPs), sampled outputs against the DFT."""
     import torch
 
     import paper_2503_03016_gb300 as P
@@ -36,7 +39,8 @@ def test_qft32_c64_gaussian_sampled_outputs():
     if _free_gb() < 40:
         pytest.skip("needs ~34 GiB of device memory")
     st = P.State(n, "c64").init_gaussian(3)
-    st.run(W.qft(n), mode=P.QC_RUN_FUSED)
+    st.run(W.qft(n), mode=P.QC_RUN_FUSED, prec=P.QC_PREC_TF32X3 if prec == "tf32x3" else P.QC_PREC_NATIVE)
+    assert P.qc_last_fused_path() == (2 if prec == "tf32x3" else 1)
     ks = [0, 0x9E3779B9, (1 << 32) - 1]
     got = np.array([complex(st.tensor[k].item()) for k in ks])
     want = oracle.dft_gaussian_samples(n, 3, ks, round_c64=True)
@@ -49,12 +53,14 @@ def test_qft32_c64_gaussian_sampled_outputs():
     torch.cuda.empty_cache()
 
 
-@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("dtype", ["c64", "c128", "c64_tf32x3"])
 def test_qft32_sparse_closed_form(dtype):
     import torch
 
     import paper_2503_03016_gb300 as P
     n = 32
+    prec = P.QC_PREC_TF32X3 if dtype == "c64_tf32x3" else P.QC_PREC_NATIVE
+    dtype = dtype[:3] if dtype == "c64_tf32x3" else dtype
     need = 34 if dtype == "c64" else 66
     if _free_gb() < need + 4:
         pytest.skip("needs %d GiB of device memory" % need)
@@ -67,7 +73,7 @@ def test_qft32_sparse_closed_form(dtype):
     for x, c in zip(xs, cs):
         st.tensor[x] = complex(c)
     torch.cuda.synchronize()
-    st.run(W.qft(n), mode=P.QC_RUN_FUSED)
+    st.run(W.qft(n), mode=P.QC_RUN_FUSED, prec=prec)
     ks = [int(v) for v in rng.integers(0, 1 << n, 64)] + [0, 1, (1 << n) - 1]
     got = np.array([complex(st.tensor[k].item()) for k in ks])
     N = float(1 << n)
