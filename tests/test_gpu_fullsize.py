@@ -12,7 +12,7 @@ import pytest
 import oracle
 import workloads as W
 
-from gpu_util import need_gpu
+from gpu_util import need_gpu, record
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -46,6 +46,7 @@ def test_qft32_c64_gaussian_sampled_outputs(prec):
     want = oracle.dft_gaussian_samples(n, 3, ks, round_c64=True)
     # the complex64 target is 1e-5 relative L2, i.e. an RMS error of 1e-5 * 2^-16 per
     # output (outputs have RMS magnitude 2^-16); allow 3 sigma on a sampled output
+    record("qft32_c64_gaussian_sampled", prec=prec, max_err_over_rms=float(np.abs(got - want).max() / 2.0 ** -16))
     assert np.abs(got - want).max() <= 3e-5 * 2.0 ** -16, (got, want)
     nrm = torch.linalg.vector_norm(st.tensor.to(torch.complex128)).item()
     assert abs(nrm - 1) < 1e-5
@@ -82,6 +83,7 @@ def test_qft32_sparse_closed_form(dtype):
     # relative L2 targets (1e-12 / 1e-5) as an RMS error per output of RMS size 2^-16,
     # 3 sigma for a sampled output
     tol = 3 * (1e-12 if dtype == "c128" else 1e-5) * 2.0 ** -16
+    record("qft32_fused_sparse", dtype=dtype, prec=int(prec), max_err_over_rms=float(np.abs(got - want).max() / 2.0 ** -16))
     assert np.abs(got - want).max() <= tol, np.abs(got - want).max()
     st.free()
     torch.cuda.empty_cache()

@@ -6,7 +6,7 @@ import pytest
 import oracle
 import workloads as W
 
-from gpu_util import gpu_state, need_gpu, rel_l2
+from gpu_util import gpu_state, need_gpu, record, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -97,4 +97,5 @@ def test_tc_block_box_and_gather_layouts(n, bits):
     want = psi.copy()
     oracle.apply_kq(want, qs, U)
     err = rel_l2(st.numpy(), want)
+    record("tc_block_layout", n=n, bits=list(bits), rel_l2=err)
     assert err <= 1e-5, (bits, err)

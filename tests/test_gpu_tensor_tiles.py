@@ -8,7 +8,7 @@ import oracle
 import workloads as W
 from workloads import Op
 
-from gpu_util import TOL, gpu_state, need_gpu, rel_l2
+from gpu_util import TOL, gpu_state, need_gpu, record, rel_l2
 
 pytestmark = pytest.mark.gpu
 
@@ -106,6 +106,7 @@ def test_tc_qft_defers_phase_bits(n):
     x = W.gaussian_state(n, 3)
     got, want, path = run_tc(n, ops, psi=x)
     assert path == 2
+    record("tc_qft_deferred", n=n, rel_l2=rel_l2(got, want))
     assert rel_l2(got, want) <= TOL["c64"]
 
 
@@ -127,6 +128,7 @@ def test_tc_inverse_qft_and_open_control_phases():
     x = W.gaussian_state(n, 5)
     got, want, path = run_tc(n, ops, psi=x)
     assert path in (1, 2)
+    record("tc_inverse_qft_phases", n=n, path=path, rel_l2=rel_l2(got, want))
     assert rel_l2(got, want) <= TOL["c64"]
 
 
@@ -216,4 +218,5 @@ def test_tc_swaps_as_relabelings(n):
     ops += [Op("swap", (j, n - 1 - j)) for j in range(n // 2)]
     got, want, path = run_tc(n, ops)
     assert path == 2
+    record("tc_swaps_relabeled", n=n, rel_l2=rel_l2(got, want))
     assert rel_l2(got, want) <= TOL["c64"]
