@@ -480,10 +480,16 @@ static void stage_sweep(const std::vector<int>& rest, const std::vector<PlanOp>&
   skip.clear();
   act.clear();
   uint64_t blocked_all = 0, blocked_diag = 0;
+  // mode 2: condition bits of phase ops whose other bits may be deferred past the stage;
+  // a dense op on one of them would not commute with that deferred part
+  uint64_t dblock = 0;
   for (int idx : rest) {
     const PlanOp& p = pops[idx];
     bool ok = (p.touched & blocked_all) == 0;
     if (ok && !p.phase) ok = (p.touched & blocked_diag) == 0;
+    if (ok && !p.phase && whole_ops == 2)
+      for (int k = 0; k < p.nt; ++k)
+        if ((dblock >> p.tb[k]) & 1) ok = false;
     if (ok && (whole_ops || !p.phase)) {
       std::vector<int> nw = act;
       bool outside = false;
@@ -507,6 +513,11 @@ static void stage_sweep(const std::vector<int>& rest, const std::vector<PlanOp>&
         ok = false;
       else
         act = nw;
+      if (ok && whole_ops == 2 && p.phase && __builtin_popcountll(p.cmask) == 1)
+        for (const auto& be : p.beta) {
+          const int lb = local_of[be.first];
+          if (lb < 0 || std::find(act.begin(), act.end(), lb) == act.end()) dblock |= p.cmask;
+        }
     }
     if (ok) {
       take.push_back(idx);

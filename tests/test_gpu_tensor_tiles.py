@@ -220,3 +220,17 @@ def test_tc_swaps_as_relabelings(n):
     assert path == 2
     record("tc_swaps_relabeled", n=n, rel_l2=rel_l2(got, want))
     assert rel_l2(got, want) <= TOL["c64"]
+
+
+@pytest.mark.parametrize("n", [14, 18])
+def test_tc_ansatz_ring(n):
+    """The adjoint benchmark's ansatz (RY RZ on every qubit, a CZ ring) on the
+    tensor-core passes: a CZ to a qubit outside the stage's slots is deferred, and the
+    stage cut keeps the next layer's rotations of that qubit out of the stage."""
+    layers = 4
+    ops = W.ansatz(n, layers, True)
+    params = np.random.default_rng(n).uniform(0, 2 * np.pi, layers * 2 * n)
+    got, want, path = run_tc(n, ops, params=params)
+    assert path == 2
+    record("tc_ansatz_ring", n=n, rel_l2=rel_l2(got, want))
+    assert rel_l2(got, want) <= TOL["c64"]
