@@ -177,8 +177,10 @@ qc_status qc_apply_ctrl(qc_state* s, const int* ctrls, const int* ctrl_states, i
 
 /* A dense 2^k x 2^k block on qubits[0..k-1] (qubits[0] = MSB of the block index),
  * 1 <= k <= 7 (QC_PREC_TF32X3: 2 <= k <= 6, complex64, n >= k_eff + 7 where k_eff = 5
- * for k <= 5 (padded with identity qubits) and 6 for k = 6).  The product of consecutive gates that
- * act on at most k qubits (gate fusion). */
+ * for k <= 5 (padded with identity qubits) and 6 for k = 6; a block of k <= 5 runs as a
+ * one-stage tensor-core tile pass where its tile moves as at most four boxes, else as a
+ * gathering block kernel).  The product of consecutive gates that act on at most k
+ * qubits (gate fusion). */
 qc_status qc_apply_fused_k(qc_state* s, const int* qubits, int k, const double* U, qc_prec prec);
 
 /* ---------------------------------------------------------------------------
@@ -336,10 +338,13 @@ typedef enum {
  * complex64 state of n >= 12 qubits, the tile passes (2^12 amplitudes) run each stage --
  * the ops on 5 of the tile's bits, controls and phase bits included -- as one 32 x 32
  * block on the tensor cores (host FP64 product of the stage's gates; TF32 split with
- * round-to-nearest, eight FP32 partial accumulators per output added on the CUDA cores;
- * synchronising: a bounded-wait timeout returns QC_ERR_TIMEOUT, after which the state's
- * amplitudes are undefined).  A circuit with an op whose control or phase bit lies
- * outside its stage runs on the CUDA-core passes.  With QC_PREC_AUTO the first run of a
+ * round-to-nearest, the large and the small products in two FP32 accumulators added on
+ * the CUDA cores; synchronising: a bounded-wait timeout returns QC_ERR_TIMEOUT, after
+ * which the state's amplitudes are undefined).  Every control of an op is a slot of its
+ * stage; a phase op conditioned on at most one qubit may have phase bits elsewhere (that
+ * part is applied per output after the stage's product), and exact SWAPs may be taken as
+ * a relabeling of the tile.  A circuit that does not fit these stages runs on the
+ * CUDA-core passes.  With QC_PREC_AUTO the first run of a
  * circuit structure (gate kinds, qubits and controls; not the angles or matrices) on a
  * device times both kinds of pass on a scratch state of the same size (allocated and
  * freed by the call; if that allocation fails, the tensor-core passes are taken) and

@@ -53,7 +53,9 @@ struct TilePass {
   int32_t stage0, nstages;
   int32_t op0, nops;    // the pass's ops (staged in shared memory)
   int32_t mat0, nmat;   // the pass's dense matrices and phase slot tables (R values)
-  int32_t pool0, npool; // the pass's other phase tables (R values in the pool; pool0 even)
+  int32_t pool0, npool; // the pass's other phase tables (R values in the pool; pool0 even);
+                        // tensor-core passes: the pass's deferred phase factors (global
+                        // indices [pool0, pool0 + npool))
   int32_t spool;        // 1: the kernel stages those tables in shared memory
   int8_t bits[16];   // B ascending (global bit positions); bits[0..L) = 0..L-1
   int32_t c0, c1;    // local phase-table chunks: local bits [0,c0) and [c0,m)
