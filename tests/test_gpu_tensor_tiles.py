@@ -112,22 +112,27 @@ def test_tc_qft_defers_phase_bits(n):
 
 def test_tc_inverse_qft_and_open_control_phases():
     """The inverse QFT (negative ladders, the swaps first) and controlled phases on far
-    qubits with open and closed controls, interleaved with Hadamards and T gates."""
+    qubits with open and closed controls -- among them controlled Z rotations with an
+    open control, whose deferred part is conditioned on the control reading 0 --
+    interleaved with Hadamards and T gates, all on the tensor-core passes."""
     n = 18
     ops = W.circuit_inverse(W.qft(n))
     rng = np.random.default_rng(8)
-    for i in range(40):
+    for i in range(48):
         a, b = (int(v) for v in rng.choice(n, 2, replace=False))
         ph = float(rng.uniform(0, 6.3))
-        if i % 3 == 0:
+        if i % 4 == 0:
             ops.append(Op("cp", (a, b), (ph,)))
-        elif i % 3 == 1:
+        elif i % 4 == 1:
             ops.append(Op("ctrl", (a, b), matrix=np.diag([1.0, np.exp(1j * ph)]), ctrl_states=(0,)))
+        elif i % 4 == 2:
+            ops.append(Op("ctrl", (a, b), matrix=np.diag([np.exp(-0.5j * ph), np.exp(0.5j * ph)]),
+                          ctrl_states=(0,)))
         else:
             ops += [Op("h", (a,)), Op("t", (b,))]
     x = W.gaussian_state(n, 5)
     got, want, path = run_tc(n, ops, psi=x)
-    assert path in (1, 2)
+    assert path == 2
     record("tc_inverse_qft_phases", n=n, path=path, rel_l2=rel_l2(got, want))
     assert rel_l2(got, want) <= TOL["c64"]
 
