@@ -32,6 +32,9 @@
 
 namespace qcgb {
 
+// complex64 reverse passes: record shares kept pending per thread before their warp sums
+constexpr int kAdjPend = 8;
+
 // running per-warp sum of a recorded rotation's shares
 template <typename R>
 struct GradAcc;
@@ -133,6 +136,40 @@ __device__ __forceinline__ R grad_pairs_at(int s0, const Cplx<R> (&v)[1 << SB], 
   }
 }
 
+// The warp's sums of its kAdjPend pending record shares (this thread's share of record
+// k at pend[k * NT + thread]; record k's slot among the pass's records in slots[k]; the
+// first cnt are valid), added into the warp's running sums acc[slot].  A transposing
+// reduction: at offset 16 each lane keeps the half of the records its lane bit 4 names
+// and adds its partner's copy of that half, then at 8 and 4 the same on the halves left,
+// and the single record a lane then holds (k = lane / 4) is summed over offsets 2 and 1.
+template <int NT>
+__device__ __forceinline__ void flush_records_impl(const float* pend, const int16_t* slots, int cnt, int lane,
+                                                   float2* acc) {
+  __syncwarp();
+  const int tid = threadIdx.x;
+  float x[kAdjPend];
+#pragma unroll
+  for (int k = 0; k < kAdjPend; ++k) x[k] = k < cnt ? pend[k * NT + tid] : 0.0f;
+  const bool b4 = (lane & 16) != 0, b3 = (lane & 8) != 0, b2 = (lane & 4) != 0;
+  float y[4], z[2];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float keep = b4 ? x[4 + i] : x[i], send = b4 ? x[i] : x[4 + i];
+    y[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i) {
+    const float keep = b3 ? y[2 + i] : y[i], send = b3 ? y[i] : y[2 + i];
+    z[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+  }
+  float u = (b2 ? z[1] : z[0]) + __shfl_xor_sync(0xffffffffu, b2 ? z[0] : z[1], 4);
+  u += __shfl_xor_sync(0xffffffffu, u, 2);
+  u += __shfl_xor_sync(0xffffffffu, u, 1);
+  const int k = lane >> 2;
+  if ((lane & 3) == 0 && k < cnt) GradAcc<float>::add(acc[slots[k]], u);
+  __syncwarp();
+}
+
 template <typename R, int NT, int SB>
 __global__ void __launch_bounds__(NT, 1) k_adj_pass(R* __restrict__ psi, R* __restrict__ lam, const TilePass P,
                                                     const TileStage* __restrict__ stages,
@@ -152,6 +189,11 @@ __global__ void __launch_bounds__(NT, 1) k_adj_pass(R* __restrict__ psi, R* __re
   R* smat = reinterpret_cast<R*>(sop + P.nops);
   using GA = GradAcc<R>;
   typename GA::T* sacc = reinterpret_cast<typename GA::T*>(smat + ((P.nmat + 1) & ~1));  // NW x ngrad
+  // complex64: each thread's shares of up to kAdjPend records, summed over the warp
+  // together (a transposing reduction: 9 shuffles for 8 records instead of 40)
+  float* pend = reinterpret_cast<float*>(sacc + NW * P.ngrad);  // kAdjPend x NT
+  __shared__ int16_t pslot[NW][kAdjPend];
+  int npend = 0;  // warp-uniform: every thread of a warp takes the same records
   __shared__ int8_t sbits[16];
   if (threadIdx.x == 0) {
 #pragma unroll
@@ -238,11 +280,20 @@ __global__ void __launch_bounds__(NT, 1) k_adj_pass(R* __restrict__ psi, R* __re
           } else {
             share = grad_pairs_at<R, SB>(op.s0, v, w, op.gen);
           }
-          // warp sum at the state's precision (32 shares), then one update of the
-          // warp's running sum
+          if constexpr (sizeof(R) == 4) {
+            pend[npend * NT + threadIdx.x] = share;
+            if (lane == 0) pslot[warp][npend] = int16_t(op.gslot);
+            if (++npend == kAdjPend) {
+              flush_records_impl<NT>(pend, pslot[warp], npend, lane, reinterpret_cast<float2*>(sacc + warp * P.ngrad));
+              npend = 0;
+            }
+          } else {
+            // warp sum at the state's precision (32 shares), then one update of the
+            // warp's running sum
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) share += __shfl_xor_sync(0xffffffffu, share, o);
-          if (lane == 0) GA::add(sacc[warp * P.ngrad + op.gslot], share);
+            for (int o = 16; o > 0; o >>= 1) share += __shfl_xor_sync(0xffffffffu, share, o);
+            if (lane == 0) GA::add(sacc[warp * P.ngrad + op.gslot], share);
+          }
         }
         if ((base & op.gmask) != op.gval) continue;  // condition on bits outside the tile
         if ((r0 & op.lmask) != op.lval) continue;    // ... on the thread's lane bits
@@ -305,6 +356,10 @@ __global__ void __launch_bounds__(NT, 1) k_adj_pass(R* __restrict__ psi, R* __re
       st_amp2<R>(lam, gi, tl[p], tl[p ^ 1u]);
     }
     __syncthreads();  // this buffer is refilled two iterations later
+  }
+  if constexpr (sizeof(R) == 4) {
+    if (npend > 0)
+      flush_records_impl<NT>(pend, pslot[warp], npend, lane, reinterpret_cast<float2*>(sacc + warp * P.ngrad));
   }
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
@@ -685,7 +740,8 @@ qc_status adjoint_reverse_tiles(int n, const std::vector<ResolvedOp>& rev, const
   size_t plan_max = 0;
   for (const TilePass& P : hp.passes)
     plan_max = std::max(plan_max, P.nstages * sizeof(TileStage) + P.nops * sizeof(TileOp) +
-                                      ((P.nmat + 1) & ~1) * sizeof(R) + size_t(ntw / 32) * P.ngrad * sizeof(double));
+                                      ((P.nmat + 1) & ~1) * sizeof(R) + size_t(ntw / 32) * P.ngrad * sizeof(double) +
+                                      (sizeof(R) == 4 ? size_t(kAdjPend) * ntw * sizeof(float) : 0));
   const size_t smem = 4 * sizeof(Cplx<R>) * (size_t(1) << m) + sizeof(uint64_t) * (size_t(1) << (m - L)) +
                       sizeof(uint64_t) * kTileNumberTab + plan_max;
   auto kern = k_adj_pass<R, S::NT, S::SB>;
