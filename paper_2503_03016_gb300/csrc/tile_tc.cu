@@ -658,8 +658,13 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
               for (int kv = 0; kv < 10; ++kv)
                 if (key == kv) gk[kv >> 1][kv & 1] = cmulf(gk[kv >> 1][kv & 1], f);
             }
+            float2 t01[4], f2[2];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) fa[c] = cmulf(cmulf(cmulf(f0, gk[0][c & 1]), gk[1][(c >> 1) & 1]), gk[2][c >> 2]);
+            for (int c = 0; c < 4; ++c) t01[c] = cmulf(gk[0][c & 1], gk[1][c >> 1]);
+#pragma unroll
+            for (int c = 0; c < 2; ++c) f2[c] = cmulf(f0, gk[2][c]);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) fa[c] = cmulf(t01[c & 3], f2[c >> 2]);
 #pragma unroll
             for (int c = 0; c < 4; ++c) fb[c] = cmulf(gk[3][c & 1], gk[4][c >> 1]);
           }
