@@ -109,6 +109,21 @@ int qc_last_stage_count(void);
 struct qc_circuit;
 qc_status qc_plan_info(const struct qc_circuit* c, const double* params, qc_dtype dtype, int* passes,
                        int* stages, int* ops);
+/* The box plan the tensor-core tile passes use to move a tile of 12 index bits
+ * (`tile_bits`: 12 distinct bits below n, index bits 0..3 among them, any order) by
+ * cp.async.bulk.tensor; host only.  Outputs (caller-owned): local_bits[12] = the tile's
+ * bits in the local order of its boxes; dims[15] = per box dimension d = 0..4 its first
+ * index bit, its number of bits and 1 if it is copied whole (0: one element at a time);
+ * coords[5] = the number c of tile bits taken as box coordinates (the tile is 2^c boxes)
+ * and for each its dimension and its bit within that dimension (-1 if unused).
+ * QC_ERR_UNSUPPORTED: no plan with at most 2 coordinate bits (such a pass copies per
+ * amplitude). */
+qc_status qc_tc_box_plan(int n, const int* tile_bits, int* local_bits, int* dims, int* coords);
+/* The tile and box plan of a dense block of k <= 5 qubits run as a one-stage
+ * tensor-core tile pass (qc_apply_fused_k with QC_PREC_TF32X3): outputs as for
+ * qc_tc_box_plan; QC_ERR_UNSUPPORTED: no tile of the block has a box plan (the block
+ * then runs in the gathering block kernel).  Host only. */
+qc_status qc_tc_block_plan(int n, const int* qubits, int k, int* local_bits, int* dims, int* coords);
 
 /* ---------------------------------------------------------------------------
  * State handles (QCLAB Sec. 3.1 "Initialization")

@@ -77,6 +77,8 @@ _SIGS = {
     "qc_last_fused_path": (ctypes.c_int, []),
     "qc_last_stage_count": (ctypes.c_int, []),
     "qc_plan_info": (ctypes.c_int, [ctypes.c_void_p, _D, ctypes.c_int, _I, _I, _I]),
+    "qc_tc_box_plan": (ctypes.c_int, [ctypes.c_int, _I, _I, _I, _I]),
+    "qc_tc_block_plan": (ctypes.c_int, [ctypes.c_int, _I, ctypes.c_int, _I, _I, _I]),
     "qc_state_alloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(_P)]),
     "qc_state_wrap": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, ctypes.POINTER(_P)]),
     "qc_state_free": (ctypes.c_int, [_P]),
@@ -412,6 +414,31 @@ def qc_plan_info(circuit: Circuit, params=None, dtype: int = QC_C64):
     a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _call("qc_plan_info", ctypes.addressof(circuit.c), p, dtype, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
     return a.value, b.value, c.value
+
+
+def _box_plan_result(local, dims, coords):
+    return ([int(v) for v in local], [tuple(int(v) for v in dims[3 * d:3 * d + 3]) for d in range(5)],
+            [(int(coords[1 + 2 * q]), int(coords[2 + 2 * q])) for q in range(int(coords[0]))])
+
+
+def qc_tc_box_plan(n: int, tile_bits):
+    """(local bits, [(first bit, bits, whole)] x 5, [(dimension, bit)] per coordinate bit)
+    of the tensor-core passes' box plan for a tile; host only."""
+    tb = np.ascontiguousarray(tile_bits, dtype=np.int32)
+    local, dims, coords = (np.zeros(k, dtype=np.int32) for k in (12, 15, 5))
+    _call("qc_tc_box_plan", int(n), tb.ctypes.data_as(_I), local.ctypes.data_as(_I), dims.ctypes.data_as(_I),
+          coords.ctypes.data_as(_I))
+    return _box_plan_result(local, dims, coords)
+
+
+def qc_tc_block_plan(n: int, qubits):
+    """The one-stage tensor-core block pass's tile and box plan for a block on `qubits`
+    (as :func:`qc_tc_box_plan`); host only."""
+    qs = np.ascontiguousarray(qubits, dtype=np.int32)
+    local, dims, coords = (np.zeros(k, dtype=np.int32) for k in (12, 15, 5))
+    _call("qc_tc_block_plan", int(n), qs.ctypes.data_as(_I), len(qs), local.ctypes.data_as(_I),
+          dims.ctypes.data_as(_I), coords.ctypes.data_as(_I))
+    return _box_plan_result(local, dims, coords)
 
 
 def qc_run_circuit(h: int, circuit: Circuit, params=None, mode: int = QC_RUN_PER_GATE,

@@ -1593,4 +1593,79 @@ qc_status apply_block_tile_tc(qc_state* s, const int* bits, int k, const double*
   return device_status(h, "tensor-core block pass");
 }
 
+// the box plan's fields as plain integers: dims[3 d + {0, 1, 2}] = first bit, bits, copied
+// whole; coords[0] = coordinate bits, coords[1 + 2 q + {0, 1}] = dimension, bit in it
+static void box_plan_out(const TcTma& tm, const std::vector<int>& Bloc, int* local_bits, int* dims, int* coords) {
+  for (int i = 0; i < kTtM; ++i) local_bits[i] = Bloc[i];
+  for (int d = 0; d < 5; ++d) {
+    dims[3 * d] = tm.start[d];
+    dims[3 * d + 1] = tm.len[d];
+    dims[3 * d + 2] = tm.tile[d];
+  }
+  coords[0] = tm.nc;
+  for (int q = 0; q < kTtMaxCoordBits; ++q) {
+    coords[1 + 2 * q] = q < tm.nc ? tm.cdim[q] : -1;
+    coords[2 + 2 * q] = q < tm.nc ? tm.coff[q] : -1;
+  }
+}
+
 }  // namespace qcgb
+
+using namespace qcgb;
+
+extern "C" qc_status qc_tc_box_plan(int n, const int* tile_bits, int* local_bits, int* dims, int* coords) {
+  clear_error();
+  if (n < kTtM || n > 34 || !tile_bits || !local_bits || !dims || !coords) {
+    set_error("qc_tc_box_plan: invalid arguments");
+    return QC_ERR_INVALID_ARG;
+  }
+  std::vector<int> B;
+  uint64_t seen = 0;
+  for (int i = 0; i < kTtM; ++i) {
+    const int b = tile_bits[i];
+    if (b < 0 || b >= n || ((seen >> b) & 1)) {
+      set_error("qc_tc_box_plan: tile bits must be %d distinct bits below n", kTtM);
+      return QC_ERR_INVALID_ARG;
+    }
+    seen |= uint64_t(1) << b;
+  }
+  for (int b = 0; b < n; ++b)
+    if ((seen >> b) & 1) B.push_back(b);
+  std::vector<int> Bloc;
+  const TcTma tm = tma_plan(B, n, Bloc);
+  if (!tm.tma) {
+    set_error("qc_tc_box_plan: no box plan with at most %d coordinate bits", kTtMaxCoordBits);
+    return QC_ERR_UNSUPPORTED;
+  }
+  box_plan_out(tm, Bloc, local_bits, dims, coords);
+  return QC_OK;
+}
+
+extern "C" qc_status qc_tc_block_plan(int n, const int* qubits, int k, int* local_bits, int* dims, int* coords) {
+  clear_error();
+  if (n < kTtM || n > 34 || !qubits || k < 1 || k > kTtSB || !local_bits || !dims || !coords) {
+    set_error("qc_tc_block_plan: invalid arguments");
+    return QC_ERR_INVALID_ARG;
+  }
+  int bits[kTtSB];
+  for (int j = 0; j < k; ++j) {
+    if (qubits[j] < 0 || qubits[j] >= n) {
+      set_error("qc_tc_block_plan: qubit %d out of range", qubits[j]);
+      return QC_ERR_INVALID_ARG;
+    }
+    bits[j] = n - 1 - qubits[j];
+    for (int i = 0; i < j; ++i)
+      if (bits[i] == bits[j]) {
+        set_error("qc_tc_block_plan: repeated qubit %d", qubits[j]);
+        return QC_ERR_INVALID_ARG;
+      }
+  }
+  std::vector<int> Bloc;
+  const TcTma tm = block_tile_plan(bits, k, n, Bloc);
+  if (!tm.tma) {
+    set_error("qc_tc_block_plan: no tile of the block has a box plan");
+    return QC_ERR_UNSUPPORTED;
+  }
+  box_plan_out(tm, Bloc, local_bits, dims, coords);
+  return QC_OK;
+}
