@@ -609,7 +609,11 @@ __global__ void __launch_bounds__(kTtThreads, 1) k_tile_pass_tc(float* __restric
               v.x *= fac;
               v.y *= fac;
             }
-            const float hr = tf32_rna(v.x), hm = tf32_rna(v.y);
+            // round to the nearest TF32 value, ties away from zero, in integer arithmetic
+            // (the same value as cvt.rna.tf32 for every finite input; amplitudes are far
+            // below the overflow range)
+            const float hr = __uint_as_float((__float_as_uint(v.x) + 0x1000u) & 0xFFFFE000u);
+            const float hm = __uint_as_float((__float_as_uint(v.y) + 0x1000u) & 0xFFFFE000u);
             hi[2 * c] = __float_as_uint(hr);
             hi[2 * c + 1] = __float_as_uint(hm);
             lo[2 * c] = __float_as_uint(v.x - hr);
