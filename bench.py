@@ -391,7 +391,7 @@ def run_ours(args):
         # DRAM bytes of one tensor-core tile pass (box copies) in an ncu capture at 26
         # qubits (537.35 MB read + 480.32 MB written), scaled by the larger state
         roof = {"bound": "tensor", "achieved": achieved, "peak": tf32_pk, "unit": "TFLOP/s",
-                "frac": achieved / tf32_pk, "traffic": 1013.605632e6 * (1 << (N_QUBITS - 26)),
+                "frac": achieved / tf32_pk, "traffic": 1013.80352e6 * (1 << (N_QUBITS - 26)),
                 "traffic_note": "per pass, ncu at 26 qubits scaled by 2^(n-26)",
                 "peak_source": TF32_PEAK_SRC,
                 "kernel": "k_tile_pass_tc", "passes": passes, "stages": stages,
