@@ -124,6 +124,13 @@ qc_status qc_tc_box_plan(int n, const int* tile_bits, int* local_bits, int* dims
  * qc_tc_box_plan; QC_ERR_UNSUPPORTED: no tile of the block has a box plan (the block
  * then runs in the gathering block kernel).  Host only. */
 qc_status qc_tc_block_plan(int n, const int* qubits, int k, int* local_bits, int* dims, int* coords);
+/* Applies circuit `c` (12 <= c->n <= 26) to `state` (host, 2^n interleaved complex128
+ * values, modified in place) the way the tensor-core tile passes would -- the same
+ * passes, stage blocks (their FP64 products, not the TF32 split), deferred phase factors
+ * (the FP32 tables the kernel reads), relabelings and copy passes -- on the host: a
+ * check of the plan's logic, not of the arithmetic.  QC_ERR_UNSUPPORTED: the circuit does
+ * not fit the tensor-core stages (QC_RUN_FUSED would take the CUDA-core passes). */
+qc_status qc_tc_emulate(const struct qc_circuit* c, const double* params, double* state);
 
 /* ---------------------------------------------------------------------------
  * State handles (QCLAB Sec. 3.1 "Initialization")

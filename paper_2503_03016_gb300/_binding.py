@@ -79,6 +79,7 @@ _SIGS = {
     "qc_plan_info": (ctypes.c_int, [ctypes.c_void_p, _D, ctypes.c_int, _I, _I, _I]),
     "qc_tc_box_plan": (ctypes.c_int, [ctypes.c_int, _I, _I, _I, _I]),
     "qc_tc_block_plan": (ctypes.c_int, [ctypes.c_int, _I, ctypes.c_int, _I, _I, _I]),
+    "qc_tc_emulate": (ctypes.c_int, [ctypes.c_void_p, _D, _D]),
     "qc_state_alloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(_P)]),
     "qc_state_wrap": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, ctypes.POINTER(_P)]),
     "qc_state_free": (ctypes.c_int, [_P]),
@@ -439,6 +440,18 @@ def qc_tc_block_plan(n: int, qubits):
     _call("qc_tc_block_plan", int(n), qs.ctypes.data_as(_I), len(qs), local.ctypes.data_as(_I),
           dims.ctypes.data_as(_I), coords.ctypes.data_as(_I))
     return _box_plan_result(local, dims, coords)
+
+
+def qc_tc_emulate(circuit: Circuit, state, params=None) -> np.ndarray:
+    """The tensor-core passes' plan applied on the host to a copy of `state` (complex128,
+    2^n values); host only."""
+    out = np.ascontiguousarray(state, dtype=np.complex128).copy()
+    p = None
+    if params is not None:
+        params = np.ascontiguousarray(params, dtype=np.float64)
+        p = params.ctypes.data_as(_D)
+    _call("qc_tc_emulate", ctypes.addressof(circuit.c), p, out.ctypes.data_as(_D))
+    return out
 
 
 def qc_run_circuit(h: int, circuit: Circuit, params=None, mode: int = QC_RUN_PER_GATE,

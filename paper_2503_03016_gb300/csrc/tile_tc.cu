@@ -57,6 +57,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <array>
 #include <complex>
 #include <mutex>
 #include <vector>
@@ -882,7 +883,8 @@ struct TcDeferTabs {
 // [*pass_def0, *pass_def0 + *pass_ndef).
 static bool tc_pass_blocks(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, bool tma, int mode,
                            std::vector<TcStage>& out, std::vector<float>& imgs, TcDeferTabs& tabs, int* pass_def0,
-                           int* pass_ndef) {
+                           int* pass_ndef, std::vector<std::vector<cd>>* blocks_out = nullptr,
+                           std::vector<std::array<int8_t, 5>>* slots_out = nullptr) {
   int local_of[64];
   for (int b = 0; b < 64; ++b) local_of[b] = -1;
   for (int i = 0; i < kTtM; ++i) local_of[bp.B[i]] = i;
@@ -1000,6 +1002,12 @@ static bool tc_pass_blocks(const BuiltPass& bp, const std::vector<PlanOp>& pops,
       }
     }
     tc_stage_record(U, recs[si], tma, out, imgs);
+    if (blocks_out) blocks_out->push_back(U);
+    if (slots_out) {
+      std::array<int8_t, 5> sl;
+      for (int k = 0; k < kTtSB; ++k) sl[k] = recs[si].slot_bit[k];
+      slots_out->push_back(sl);
+    }
     if (!dkeys.empty()) {
       const int nd = int(dkeys.size());
       if (nd > kTtMaxDefStage || *pass_ndef + nd > kTtMaxDefPass) return false;
@@ -1190,25 +1198,38 @@ static bool same_ops(const std::vector<ResolvedOp>& a, const std::vector<Resolve
 }
 
 // plans `rops` into the cache (host stage blocks, B images, upload)
-static qc_status tc_plan(qc_state* s, const std::vector<ResolvedOp>& rops, int dev) {
-  const int n = s->n;
-  g_tc.valid = false;
-  std::vector<PlanOp> pops;
-  to_plan_ops(rops, pops);
-  const std::vector<BuiltPass> bps = build_passes(pops, n, kTtM, kTtL, /*cond_in_tile=*/true);
+// A circuit's tensor-core plan on the host: passes, their box plans and kinds (defer: 0
+// plain, 1 with deferred phase factors, 2 a relabeling copied by the CUDA-core pass),
+// stage records, B images and factor tables; optionally each stage's FP64 block and slot
+// bits (for a host emulation).  amps: the state whose address the box plans are tried
+// with (nullptr: no trial encoding).  False: the circuit does not fit the stages.
+struct TcHostPlan {
   std::vector<TilePass> passes;
   std::vector<TcTma> tmas;
   std::vector<char> defer;
   std::vector<TcStage> stages;
   std::vector<float> imgs;
   TcDeferTabs tabs;
-  bool tc = true;
+  std::vector<std::vector<cd>>* blocks = nullptr;
+  std::vector<std::array<int8_t, 5>>* slots = nullptr;
+};
+
+static bool tc_build(int n, const std::vector<ResolvedOp>& rops, void* amps, TcHostPlan& hp) {
+  std::vector<PlanOp> pops;
+  to_plan_ops(rops, pops);
+  const std::vector<BuiltPass> bps = build_passes(pops, n, kTtM, kTtL, /*cond_in_tile=*/true);
+  std::vector<TilePass>& passes = hp.passes;
+  std::vector<TcTma>& tmas = hp.tmas;
+  std::vector<char>& defer = hp.defer;
+  std::vector<TcStage>& stages = hp.stages;
+  std::vector<float>& imgs = hp.imgs;
+  TcDeferTabs& tabs = hp.tabs;
   for (const BuiltPass& bp : bps) {
     std::vector<int> Bloc;
     TcTma tm = tma_plan(bp.B, n, Bloc);
-    if (tm.tma) {  // a trial encoding with this state's address
+    if (tm.tma && amps) {  // a trial encoding with this state's address
       alignas(64) CUtensorMap probe;
-      if (!encode_tile_map(&probe, tm, s->amps, n)) tm = TcTma{};
+      if (!encode_tile_map(&probe, tm, amps, n)) tm = TcTma{};
     }
     BuiltPass bl = bp;  // the tile's bits in the local order of its boxes
     if (tm.tma) bl.B = Bloc;
@@ -1257,11 +1278,13 @@ static qc_status tc_plan(qc_state* s, const std::vector<ResolvedOp>& rops, int d
       tabs.row.resize(r0);
       tabs.glob.resize(g0);
       tabs.count = c0;
+      if (hp.blocks) hp.blocks->resize(size_t(P.stage0));
+      if (hp.slots) hp.slots->resize(size_t(P.stage0));
     };
     auto plan = [&](int v) {  // v: 2 relabel + (mode - 1)
       const bool rl = v >= 2;
       return tc_pass_blocks(rl ? br : bl, rl ? rpops : pops, n, tm.tma != 0, 1 + (v & 1), stages, imgs, tabs,
-                            &def0, &ndef);
+                            &def0, &ndef, hp.blocks, hp.slots);
     };
     int pick = -1;
     double best = 1e30;
@@ -1274,10 +1297,7 @@ static qc_status tc_plan(qc_state* s, const std::vector<ResolvedOp>& rops, int d
         pick = v;
       }
     }
-    if (pick < 0) {
-      tc = false;
-      break;
-    }
+    if (pick < 0) return false;
     reset();
     plan(pick);
     bool copy = false;
@@ -1310,14 +1330,25 @@ static qc_status tc_plan(qc_state* s, const std::vector<ResolvedOp>& rops, int d
     P.pool0 = def0;  // the pass's deferred factors (global indices)
     P.npool = ndef;
     P.nstages = int(stages.size()) - P.stage0;
-    if (P.nstages > kTtMaxStages) {
-      tc = false;
-      break;
-    }
+    if (P.nstages > kTtMaxStages) return false;
     passes.push_back(P);
     tmas.push_back(tm);
     defer.push_back(copy ? 2 : ndef > 0 ? 1 : 0);
   }
+  return true;
+}
+
+static qc_status tc_plan(qc_state* s, const std::vector<ResolvedOp>& rops, int dev) {
+  const int n = s->n;
+  g_tc.valid = false;
+  TcHostPlan hp;
+  const bool tc = tc_build(n, rops, s->amps, hp);
+  std::vector<TilePass>& passes = hp.passes;
+  std::vector<TcTma>& tmas = hp.tmas;
+  std::vector<char>& defer = hp.defer;
+  std::vector<TcStage>& stages = hp.stages;
+  std::vector<float>& imgs = hp.imgs;
+  TcDeferTabs& tabs = hp.tabs;
   g_tc.device = dev;
   g_tc.n = n;
   g_tc.rops = rops;
@@ -1671,5 +1702,97 @@ extern "C" qc_status qc_tc_block_plan(int n, const int* qubits, int k, int* loca
     return QC_ERR_UNSUPPORTED;
   }
   box_plan_out(tm, Bloc, local_bits, dims, coords);
+  return QC_OK;
+}
+
+extern "C" qc_status qc_tc_emulate(const qc_circuit* c, const double* params, double* state) {
+  clear_error();
+  if (!c || !state || c->n < kTtM || c->n > 26 || (c->nops > 0 && !c->ops)) {
+    set_error("qc_tc_emulate: invalid arguments (%d <= n <= 26)", kTtM);
+    return QC_ERR_INVALID_ARG;
+  }
+  const int n = c->n;
+  std::vector<ResolvedOp> rops(size_t(c->nops));
+  for (int i = 0; i < c->nops; ++i)
+    if (qc_status st = resolve_op(c, c->ops[i], params, &rops[size_t(i)])) return st;
+  std::vector<std::vector<cd>> blocks;
+  std::vector<std::array<int8_t, 5>> slots;
+  TcHostPlan hp;
+  hp.blocks = &blocks;
+  hp.slots = &slots;
+  if (!tc_build(n, rops, nullptr, hp)) {
+    set_error("qc_tc_emulate: the circuit does not fit the tensor-core stages");
+    return QC_ERR_UNSUPPORTED;
+  }
+  cd* a = reinterpret_cast<cd*>(state);
+  constexpr uint32_t T = 1u << kTtM;
+  const uint64_t ntiles = uint64_t(1) << (n - kTtM);
+  std::vector<cd> tile(T), tmp(T);
+  for (const TilePass& P : hp.passes) {
+    bool in[64] = {false};
+    for (int k = 0; k < kTtM; ++k) in[P.bits[k]] = true;
+    std::vector<int> tnb;  // bit i of a tile number sits at global bit tnb[i]
+    for (int b = 0; b < n; ++b)
+      if (!in[b]) tnb.push_back(b);
+    for (uint64_t t = 0; t < ntiles; ++t) {
+      uint64_t base = 0;
+      for (size_t i = 0; i < tnb.size(); ++i)
+        if ((t >> i) & 1) base |= uint64_t(1) << tnb[i];
+      auto addr = [&](uint32_t u) {
+        uint64_t g = base;
+        for (int k = 0; k < kTtM; ++k)
+          if ((u >> k) & 1) g |= uint64_t(1) << P.bits[k];
+        return g;
+      };
+      for (uint32_t u = 0; u < T; ++u) tile[u] = a[addr(u)];
+      for (int si = P.stage0; si < P.stage0 + P.nstages; ++si) {
+        const TcStage& ts = hp.stages[size_t(si)];
+        const std::vector<cd>& U = blocks[size_t(si)];
+        const std::array<int8_t, 5>& sl = slots[size_t(si)];
+        for (int r = 0; r < kTtRows; ++r) {
+          uint32_t rb = 0;
+          for (int b = 0; b < kTtM - kTtSB; ++b)
+            if ((r >> b) & 1) rb |= 1u << ts.lane_bit[b];
+          uint32_t pos[32];
+          cd x[32], y[32];
+          for (int cc = 0; cc < 32; ++cc) {
+            uint32_t u = rb;
+            for (int k = 0; k < kTtSB; ++k)
+              if ((cc >> k) & 1) u |= 1u << sl[size_t(k)];
+            pos[cc] = u;
+            x[cc] = tile[u];
+          }
+          for (int d = 0; d < 32; ++d) {
+            cd acc = 0.0;
+            for (int cc = 0; cc < 32; ++cc) acc += U[size_t(d * 32 + cc)] * x[cc];
+            y[d] = acc;
+          }
+          for (int f = 0; f < ts.ndef; ++f) {  // deferred factors: row table times the tile's value
+            const size_t src = size_t(ts.def0 + f);
+            const float* rt = &hp.tabs.row[src * 256 + size_t(2 * r)];
+            const float* gt = &hp.tabs.glob[src * 1536];
+            cd fac(rt[0], rt[1]);
+            for (int ch = 0; ch < 3; ++ch) {
+              const size_t v = size_t((t >> (8 * ch)) & 255);
+              fac *= cd(gt[2 * (ch * 256 + v)], gt[2 * (ch * 256 + v) + 1]);
+            }
+            const int key = ts.dkey[f];
+            for (int d = 0; d < 32; ++d)
+              if (key < 0 || ((d >> (key >> 1)) & 1) == (key & 1)) y[d] *= fac;
+          }
+          for (int d = 0; d < 32; ++d) tile[pos[d]] = y[d];
+        }
+      }
+      if (P.permuted) {  // output u from the position whose bit rbit[k] is bit k of u
+        for (uint32_t u = 0; u < T; ++u) {
+          uint32_t v = 0;
+          for (int k = 0; k < kTtM; ++k) v |= ((u >> k) & 1u) << P.rbit[k];
+          tmp[u] = tile[v];
+        }
+        tile.swap(tmp);
+      }
+      for (uint32_t u = 0; u < T; ++u) a[addr(u)] = tile[u];
+    }
+  }
   return QC_OK;
 }

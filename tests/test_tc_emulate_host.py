@@ -1,0 +1,84 @@
+"""Host-only check of the tensor-core passes' plan logic (qc_tc_emulate; no GPU needed):
+the planner's passes, stage blocks (their FP64 products), deferred phase factors (the
+FP32 tables the kernel reads), SWAP relabelings and copy passes applied on the host in
+the kernel's order, against the oracle.
+
+Circuits whose deferred factors are all +-1 (CZ rings) or that have none come out at
+FP64 rounding; circuits with deferred phases carry the tables' FP32 rounding (a few
+units of 1e-8 per factor).  A planning mistake -- a factor moved past an op it does not
+commute with, a wrong slot or row bit, a misread relabeling -- gives errors of order 1."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from workloads import Op
+
+
+def emulate(n, ops, psi, params=None):
+    import paper_2503_03016_gb300 as P
+    got = P.qc_tc_emulate(P.Circuit(n, ops), psi, params)
+    want = oracle.run(psi.copy(), ops, params)
+    return np.linalg.norm(got - want) / np.linalg.norm(want)
+
+
+@pytest.mark.parametrize("n", [13, 14, 16])
+def test_qft_with_deferred_ladders(n):
+    assert emulate(n, W.qft(n), W.gaussian_state(n, 3)) <= 1e-6
+
+
+def test_inverse_qft_with_far_and_open_control_phases():
+    n = 16
+    ops = W.circuit_inverse(W.qft(n))
+    rng = np.random.default_rng(8)
+    for i in range(48):
+        a, b = (int(v) for v in rng.choice(n, 2, replace=False))
+        ph = float(rng.uniform(0, 6.3))
+        if i % 4 == 0:
+            ops.append(Op("cp", (a, b), (ph,)))
+        elif i % 4 == 1:
+            ops.append(Op("ctrl", (a, b), matrix=np.diag([1.0, np.exp(1j * ph)]), ctrl_states=(0,)))
+        elif i % 4 == 2:
+            ops.append(Op("ctrl", (a, b), matrix=np.diag([np.exp(-0.5j * ph), np.exp(0.5j * ph)]),
+                          ctrl_states=(0,)))
+        else:
+            ops += [Op("h", (a,)), Op("t", (b,))]
+    assert emulate(n, ops, W.gaussian_state(n, 5)) <= 1e-6
+
+
+@pytest.mark.parametrize("n", [13, 15])
+def test_brickwork_and_ansatz_ring_exact(n):
+    assert emulate(n, W.brickwork(n, 12, 7), W.random_state(n, 1)) <= 1e-12
+    layers = 4
+    params = np.random.default_rng(n).uniform(0, 2 * np.pi, layers * 2 * n)
+    assert emulate(n, W.ansatz(n, layers, True), W.random_state(n, 2), params) <= 1e-12
+
+
+def test_swaps_relabelings_and_copy_passes():
+    n = 15
+    rng = np.random.default_rng(n)
+    U = W.haar_unitaries(60, 4, 3 * n)
+    ops = []
+    for i in range(60):
+        a = int(rng.integers(0, n - 1))
+        ops.append(Op("u2q", (a, a + 1), matrix=U[i]))
+        if i % 4 == 3:
+            b, c = (int(v) for v in rng.choice(n, 2, replace=False))
+            ops.append(Op("swap", (b, c)))
+    ops += [Op("swap", (j, n - 1 - j)) for j in range(n // 2)]  # a bit reversal at the end
+    assert emulate(n, ops, W.random_state(n, 3)) <= 1e-12
+
+
+def test_rejects_circuits_outside_the_stages_and_small_registers():
+    import paper_2503_03016_gb300 as P
+    n = 16
+    ops = [Op("h", (q,)) for q in range(n)]
+    ops.append(Op("ctrl", (0, n - 1, n // 2), matrix=np.diag([1.0, np.exp(0.7j)])))
+    psi = W.random_state(n, 4)
+    try:
+        err = emulate(n, ops, psi)
+        assert err <= 1e-6  # planned onto the stages after all: still exact
+    except P.QCError as e:
+        assert e.status == 4
+    with pytest.raises(P.QCError):
+        P.qc_tc_emulate(P.Circuit(10, W.qft(10)), W.random_state(10, 1))
