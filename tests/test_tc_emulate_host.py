@@ -82,3 +82,59 @@ def test_rejects_circuits_outside_the_stages_and_small_registers():
         assert e.status == 4
     with pytest.raises(P.QCError):
         P.qc_tc_emulate(P.Circuit(10, W.qft(10)), W.random_state(10, 1))
+
+
+def _mixed(n, seed, count=120):
+    """Every gate kind: 1-qubit gates and rotations, CNOT, CZ, CP, SWAP, Haar and
+    diagonal two-qubit matrices, multi-controlled X and controlled 2x2 gates with open
+    and closed controls, on random qubits."""
+    rng = np.random.default_rng(seed)
+    ops = []
+    kinds1 = ["h", "x", "y", "z", "s", "sdg", "t", "tdg"]
+    for i in range(count):
+        c = int(rng.integers(0, 11))
+        qs = [int(x) for x in rng.permutation(n)[:4]]
+        ang = float(rng.uniform(0, 6.3))
+        if c == 0:
+            ops.append(Op(kinds1[int(rng.integers(0, len(kinds1)))], (qs[0],)))
+        elif c == 1:
+            ops.append(Op(["rx", "ry", "rz"][int(rng.integers(0, 3))], (qs[0],), (ang,)))
+        elif c == 2:
+            ops.append(Op("u3", (qs[0],), tuple(float(a) for a in rng.uniform(0, 6.3, 3))))
+        elif c == 3:
+            ops.append(Op("cnot", (qs[0], qs[1])))
+        elif c == 4:
+            ops.append(Op("cz", (qs[0], qs[1])))
+        elif c == 5:
+            ops.append(Op("cp", (qs[0], qs[1]), (ang,)))
+        elif c == 6:
+            ops.append(Op("swap", (qs[0], qs[1])))
+        elif c == 7:
+            ops.append(Op("u2q", (qs[0], qs[1]), matrix=W.haar_unitaries(1, 4, seed * 1000 + i)[0]))
+        elif c == 8:
+            ops.append(Op("mcx", (qs[0], qs[1], qs[2]), ctrl_states=(int(rng.integers(0, 2)), int(rng.integers(0, 2)))))
+        elif c == 9:
+            ops.append(Op("ctrl", (qs[0], qs[1]), matrix=np.diag(np.exp(1j * rng.uniform(0, 6.3, 2))),
+                          ctrl_states=(int(rng.integers(0, 2)),)))
+        else:
+            ops.append(Op("u2q", (qs[0], qs[1]), matrix=np.diag(np.exp(1j * rng.uniform(0, 6.3, 4)))))
+    return ops
+
+
+def test_random_mixed_circuits():
+    """Seeded circuits of every gate kind on 12 to 15 qubits: where the tensor-core
+    planner takes the circuit, its plan applied on the host equals the oracle (FP32
+    phase tables: 1e-6); most of them fit the stages."""
+    import paper_2503_03016_gb300 as P
+    fit = 0
+    cases = [(n, seed) for n in (12, 13, 15) for seed in range(1, 7)]
+    for n, seed in cases:
+        ops = _mixed(n, seed)
+        try:
+            err = emulate(n, ops, W.random_state(n, seed))
+        except P.QCError as e:
+            assert e.status == 4
+            continue
+        fit += 1
+        assert err <= 1e-6, (n, seed, err)
+    assert fit >= len(cases) // 2, fit
