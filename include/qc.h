@@ -131,6 +131,11 @@ qc_status qc_tc_block_plan(int n, const int* qubits, int k, int* local_bits, int
  * check of the plan's logic, not of the arithmetic.  QC_ERR_UNSUPPORTED: the circuit does
  * not fit the tensor-core stages (QC_RUN_FUSED would take the CUDA-core passes). */
 qc_status qc_tc_emulate(const struct qc_circuit* c, const double* params, double* state);
+/* The tensor-core plan of circuit `c` (12 <= c->n <= 34): passes, stage blocks, deferred
+ * phase factors and passes that are only a relabeling (copied by the CUDA-core pass);
+ * host only.  QC_ERR_UNSUPPORTED: the circuit does not fit the tensor-core stages. */
+qc_status qc_tc_plan_info(const struct qc_circuit* c, const double* params, int* passes, int* stages, int* factors,
+                          int* copy_passes);
 
 /* ---------------------------------------------------------------------------
  * State handles (QCLAB Sec. 3.1 "Initialization")

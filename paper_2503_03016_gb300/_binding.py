@@ -80,6 +80,7 @@ _SIGS = {
     "qc_tc_box_plan": (ctypes.c_int, [ctypes.c_int, _I, _I, _I, _I]),
     "qc_tc_block_plan": (ctypes.c_int, [ctypes.c_int, _I, ctypes.c_int, _I, _I, _I]),
     "qc_tc_emulate": (ctypes.c_int, [ctypes.c_void_p, _D, _D]),
+    "qc_tc_plan_info": (ctypes.c_int, [ctypes.c_void_p, _D, _I, _I, _I, _I]),
     "qc_state_alloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(_P)]),
     "qc_state_wrap": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, ctypes.POINTER(_P)]),
     "qc_state_free": (ctypes.c_int, [_P]),
@@ -452,6 +453,18 @@ def qc_tc_emulate(circuit: Circuit, state, params=None) -> np.ndarray:
         p = params.ctypes.data_as(_D)
     _call("qc_tc_emulate", ctypes.addressof(circuit.c), p, out.ctypes.data_as(_D))
     return out
+
+
+def qc_tc_plan_info(circuit: Circuit, params=None):
+    """(passes, stage blocks, deferred factors, relabeling-only passes) of the
+    tensor-core plan; host only."""
+    p = None
+    if params is not None:
+        params = np.ascontiguousarray(params, dtype=np.float64)
+        p = params.ctypes.data_as(_D)
+    v = [ctypes.c_int() for _ in range(4)]
+    _call("qc_tc_plan_info", ctypes.addressof(circuit.c), p, *[ctypes.byref(x) for x in v])
+    return tuple(x.value for x in v)
 
 
 def qc_run_circuit(h: int, circuit: Circuit, params=None, mode: int = QC_RUN_PER_GATE,

@@ -1796,3 +1796,28 @@ extern "C" qc_status qc_tc_emulate(const qc_circuit* c, const double* params, do
   }
   return QC_OK;
 }
+
+extern "C" qc_status qc_tc_plan_info(const qc_circuit* c, const double* params, int* passes, int* stages,
+                                     int* factors, int* copy_passes) {
+  clear_error();
+  if (!c || c->n < kTtM || c->n > 34 || (c->nops > 0 && !c->ops) || !passes || !stages || !factors ||
+      !copy_passes) {
+    set_error("qc_tc_plan_info: invalid arguments (%d <= n <= 34)", kTtM);
+    return QC_ERR_INVALID_ARG;
+  }
+  std::vector<ResolvedOp> rops(size_t(c->nops));
+  for (int i = 0; i < c->nops; ++i)
+    if (qc_status st = resolve_op(c, c->ops[i], params, &rops[size_t(i)])) return st;
+  TcHostPlan hp;
+  if (!tc_build(c->n, rops, nullptr, hp)) {
+    set_error("qc_tc_plan_info: the circuit does not fit the tensor-core stages");
+    return QC_ERR_UNSUPPORTED;
+  }
+  *passes = int(hp.passes.size());
+  *stages = int(hp.stages.size());
+  *factors = hp.tabs.count;
+  int cp = 0;
+  for (char d : hp.defer) cp += d == 2 ? 1 : 0;
+  *copy_passes = cp;
+  return QC_OK;
+}
