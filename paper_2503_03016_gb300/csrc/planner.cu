@@ -555,6 +555,82 @@ void split_stages(const BuiltPass& bp, const std::vector<PlanOp>& pops, const in
   }
 }
 
+// The candidate stages over `rest` (the growing first-fit set and every window of sb
+// neighbouring local bits), without repeats
+struct StageCand {
+  std::vector<int> take, skip, act;
+};
+static std::vector<StageCand> stage_candidates(const std::vector<int>& rest, const std::vector<PlanOp>& pops,
+                                               const int* local_of, int sb, int whole_ops, int m) {
+  std::vector<StageCand> out;
+  auto push = [&](int64_t fixed) {
+    StageCand c;
+    stage_sweep(rest, pops, local_of, sb, whole_ops, fixed, c.take, c.skip, c.act);
+    if (c.take.empty()) return;
+    for (const StageCand& o : out)
+      if (o.take == c.take) return;
+    out.push_back(std::move(c));
+  };
+  push(-1);
+  for (int w = 0; w + sb <= m; ++w) push(((int64_t(1) << sb) - 1) << w);
+  return out;
+}
+
+// stages the greedy cut (most ops per stage) needs for `rest`
+static int greedy_stage_count(std::vector<int> rest, const std::vector<PlanOp>& pops, const int* local_of, int sb,
+                              int whole_ops, int m) {
+  int k = 0;
+  while (!rest.empty()) {
+    std::vector<StageCand> cs = stage_candidates(rest, pops, local_of, sb, whole_ops, m);
+    if (cs.empty()) return 1 << 20;
+    size_t best = 0;
+    for (size_t i = 1; i < cs.size(); ++i)
+      if (cs[i].take.size() > cs[best].take.size()) best = i;
+    rest = cs[best].skip;
+    ++k;
+  }
+  return k;
+}
+
+// stages needed for `rest` when the next `depth` stages are chosen by search and the
+// rest greedily
+static int lookahead_stage_count(const std::vector<int>& rest, const std::vector<PlanOp>& pops, const int* local_of,
+                                 int sb, int whole_ops, int m, int depth) {
+  if (rest.empty()) return 0;
+  if (depth == 0) return greedy_stage_count(rest, pops, local_of, sb, whole_ops, m);
+  int best = 1 << 20;
+  for (const StageCand& c : stage_candidates(rest, pops, local_of, sb, whole_ops, m))
+    best = std::min(best, 1 + lookahead_stage_count(c.skip, pops, local_of, sb, whole_ops, m, depth - 1));
+  return best;
+}
+
+void split_stages_lookahead(const BuiltPass& bp, const std::vector<PlanOp>& pops, const int* local_of, int sb,
+                            std::vector<std::vector<int>>& takes, std::vector<std::vector<int>>& acts, int whole_ops,
+                            int depth) {
+  int m = 0;
+  for (int b = 0; b < 64; ++b) m = std::max(m, local_of[b] + 1);
+  std::vector<int> rest = bp.ops;
+  while (!rest.empty()) {
+    std::vector<StageCand> cs = stage_candidates(rest, pops, local_of, sb, whole_ops, m);
+    if (cs.empty()) {  // (no op fits: leave them to the caller's checks, as the greedy cut does)
+      split_stages(BuiltPass{bp.B, rest}, pops, local_of, sb, takes, acts, whole_ops);
+      return;
+    }
+    size_t best = 0;
+    int best_n = 1 << 20;
+    for (size_t i = 0; i < cs.size(); ++i) {
+      const int nst = 1 + lookahead_stage_count(cs[i].skip, pops, local_of, sb, whole_ops, m, depth - 1);
+      if (nst < best_n || (nst == best_n && cs[i].take.size() > cs[best].take.size())) {
+        best_n = nst;
+        best = i;
+      }
+    }
+    takes.push_back(cs[best].take);
+    acts.push_back(cs[best].act);
+    rest = cs[best].skip;
+  }
+}
+
 std::vector<TileStage> stage_layouts(const std::vector<std::vector<int>>& acts, int m, int sb, int nres) {
   const int nthr = m - sb;
   const int nl = std::min(nthr, 5), nw = nthr - nl;

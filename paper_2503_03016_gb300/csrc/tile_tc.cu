@@ -95,6 +95,9 @@ constexpr int kTtMaxStages = kMaxPassOps;
 // tables (3 x 256 entries), all FP64-built on the host and rounded to FP32.
 constexpr int kTtMaxDefStage = 11;  // factors per stage: unconditioned + 5 slots x 2 values
 constexpr int kTtMaxDefPass = 64;   // factors per pass (per-tile values in shared memory)
+// stage cuts searched this many stages ahead (each stage block costs a full round of
+// transposition and products, so fewer blocks pay more than the host search costs)
+constexpr int kTtStageLookahead = 2;
 constexpr int kTtHi = 1 << (kTtM - kTtL);       // 128-byte runs per tile
 // TMEM columns of a group: A_hi [0, 64), A_lo [64, 128), accumulators [128, 256)
 constexpr int kTmemPerGroup = 256;
@@ -893,7 +896,7 @@ static bool tc_pass_blocks(const BuiltPass& bp, const std::vector<PlanOp>& pops,
     if (local_of[b] < 0) tnbits.push_back(b);
   if (mode == 2 && tnbits.size() > 24) return false;
   std::vector<std::vector<int>> takes, acts;
-  split_stages(bp, pops, local_of, kTtSB, takes, acts, mode);
+  split_stages_lookahead(bp, pops, local_of, kTtSB, takes, acts, mode, kTtStageLookahead);
   const std::vector<TileStage> recs = stage_layouts(acts, kTtM, kTtSB, 4);
   constexpr int D = 1 << kTtSB;
   *pass_def0 = tabs.count;

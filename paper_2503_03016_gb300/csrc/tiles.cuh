@@ -601,6 +601,11 @@ void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int 
 // except the phase bits of a phase op conditioned on at most one bit)
 void split_stages(const BuiltPass& bp, const std::vector<PlanOp>& pops, const int* local_of, int sb,
                   std::vector<std::vector<int>>& takes, std::vector<std::vector<int>>& acts, int whole_ops = 0);
+// as split_stages, each stage chosen among the same candidates by the fewest stages for
+// the pass when the next `depth` stages are searched and the rest cut greedily
+void split_stages_lookahead(const BuiltPass& bp, const std::vector<PlanOp>& pops, const int* local_of, int sb,
+                            std::vector<std::vector<int>>& takes, std::vector<std::vector<int>>& acts, int whole_ops,
+                            int depth);
 // slot bits (acts[s] padded to sb) and thread-index bits of each stage (m - sb of them,
 // the first ones one per residue mod nres); warp bits kept over runs of stages
 std::vector<TileStage> stage_layouts(const std::vector<std::vector<int>>& acts, int m, int sb, int nres);
