@@ -1201,6 +1201,36 @@ static bool same_ops(const std::vector<ResolvedOp>& a, const std::vector<Resolve
 }
 
 // plans `rops` into the cache (host stage blocks, B images, upload)
+// A pass's exact SWAPs of two tile bits taken as a relabeling: the other ops renamed
+// into rpops (br: the pass over them, the same tile bits), rbit[k] = the local bit (in
+// the order of bp.B) where the data of local bit k sits when the pass ends; false (rbit
+// the identity) if the pass has no such SWAP.
+static bool relabel_swaps(const BuiltPass& bp, const std::vector<PlanOp>& pops, std::vector<PlanOp>& rpops,
+                          BuiltPass& br, int8_t* rbit) {
+  int ren[64], loc[64];
+  for (int b = 0; b < 64; ++b) {
+    ren[b] = b;
+    loc[b] = -1;
+  }
+  for (int i = 0; i < kTtM; ++i) loc[bp.B[i]] = i;
+  br.B = bp.B;
+  br.ops.clear();
+  rpops.clear();
+  bool permuted = false;
+  for (int idx : bp.ops) {
+    const PlanOp& p = pops[idx];
+    if (is_exact_swap(p) && loc[ren[p.tb[0]]] >= 0 && loc[ren[p.tb[1]]] >= 0) {
+      std::swap(ren[p.tb[0]], ren[p.tb[1]]);
+      permuted = true;
+      continue;
+    }
+    br.ops.push_back(int(rpops.size()));
+    rpops.push_back(renamed(p, ren));
+  }
+  for (int k = 0; k < 16; ++k) rbit[k] = int8_t(k < kTtM && permuted ? loc[ren[bp.B[k]]] : k);
+  return permuted;
+}
+
 // A circuit's tensor-core plan on the host: passes, their box plans and kinds (defer: 0
 // plain, 1 with deferred phase factors, 2 a relabeling copied by the CUDA-core pass),
 // stage records, B images and factor tables; optionally each stage's FP64 block and slot
@@ -1243,32 +1273,11 @@ static bool tc_build(int n, const std::vector<ResolvedOp>& rops, void* amps, TcH
     P.ntiles = uint64_t(1) << (n - kTtM);
     P.stage0 = int(stages.size());
     // The pass's exact SWAPs of two tile bits, either as ops of the stages or as a
-    // relabeling (the later ops renamed, the tile permuted before its write-back:
-    // rbit[k] = the local bit where the data of local bit k sits).
+    // relabeling (the later ops renamed, the tile permuted before its write-back)
     std::vector<PlanOp> rpops;
     BuiltPass br;
-    br.B = bl.B;
     int8_t rbit[16];
-    bool permuted = false;
-    {
-      int ren[64], loc[64];
-      for (int b = 0; b < 64; ++b) {
-        ren[b] = b;
-        loc[b] = -1;
-      }
-      for (int i = 0; i < kTtM; ++i) loc[bl.B[i]] = i;
-      for (int idx : bl.ops) {
-        const PlanOp& p = pops[idx];
-        if (is_exact_swap(p) && loc[ren[p.tb[0]]] >= 0 && loc[ren[p.tb[1]]] >= 0) {
-          std::swap(ren[p.tb[0]], ren[p.tb[1]]);
-          permuted = true;
-          continue;
-        }
-        br.ops.push_back(int(rpops.size()));
-        rpops.push_back(renamed(p, ren));
-      }
-      for (int k = 0; k < 16; ++k) rbit[k] = int8_t(k < kTtM && permuted ? loc[ren[bl.B[k]]] : k);
-    }
+    const bool permuted = relabel_swaps(bl, pops, rpops, br, rbit);
     // every phase bit a slot (mode 1), or phase bits off the slots deferred (mode 2);
     // SWAPs as ops or relabeled: the fewest stages win (a relabeling counts half a
     // stage; the earlier variant on ties); none: the CUDA-core passes take the circuit
@@ -1311,21 +1320,10 @@ static bool tc_build(int n, const std::vector<ResolvedOp>& rops, void* amps, TcH
         // nothing but the relabeling: the CUDA-core pass copies the tiles (bits in
         // ascending order, the relabeling in that order)
         copy = true;
-        int ren[64], loc[64];
-        for (int b = 0; b < 64; ++b) {
-          ren[b] = b;
-          loc[b] = -1;
-        }
-        for (int i = 0; i < kTtM; ++i) loc[bp.B[i]] = i;
-        for (int idx : bp.ops) {
-          const PlanOp& p = pops[idx];
-          if (is_exact_swap(p) && loc[ren[p.tb[0]]] >= 0 && loc[ren[p.tb[1]]] >= 0)
-            std::swap(ren[p.tb[0]], ren[p.tb[1]]);
-        }
-        for (int k = 0; k < 16; ++k) {
-          P.bits[k] = int8_t(k < kTtM ? bp.B[k] : 0);
-          P.rbit[k] = int8_t(k < kTtM ? loc[ren[bp.B[k]]] : k);
-        }
+        std::vector<PlanOp> cpops;
+        BuiltPass cb;
+        relabel_swaps(bp, pops, cpops, cb, P.rbit);
+        for (int k = 0; k < 16; ++k) P.bits[k] = int8_t(k < kTtM ? bp.B[k] : 0);
       }
     } else {
       for (int k = 0; k < 16; ++k) P.rbit[k] = int8_t(k);

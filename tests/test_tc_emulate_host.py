@@ -22,8 +22,12 @@ def emulate(n, ops, psi, params=None):
     return np.linalg.norm(got - want) / np.linalg.norm(want)
 
 
-@pytest.mark.parametrize("n", [13, 14, 16])
+@pytest.mark.parametrize("n", [13, 14, 16, 17])
 def test_qft_with_deferred_ladders(n):
+    """(16 and 17 qubits: one and two passes that are only the final swaps' relabeling)"""
+    import paper_2503_03016_gb300 as P
+    if n >= 16:
+        assert P.qc_tc_plan_info(P.Circuit(n, W.qft(n)))[3] == n - 15
     assert emulate(n, W.qft(n), W.gaussian_state(n, 3)) <= 1e-6
 
 
