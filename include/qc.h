@@ -131,6 +131,12 @@ qc_status qc_tc_block_plan(int n, const int* qubits, int k, int* local_bits, int
  * check of the plan's logic, not of the arithmetic.  QC_ERR_UNSUPPORTED: the circuit does
  * not fit the tensor-core stages (QC_RUN_FUSED would take the CUDA-core passes). */
 qc_status qc_tc_emulate(const struct qc_circuit* c, const double* params, double* state);
+/* Applies circuit `c` (10 <= c->n <= 24) to `state` (host, 2^n interleaved complex128
+ * values, modified in place) through the CUDA-core tile-pass plan QC_RUN_FUSED builds for
+ * a state of `dtype` -- its passes, register stages, tile ops with their conditions,
+ * matrices, phase tables, CZ code words and relabeled SWAPs -- interpreted on the host in
+ * FP64 in the kernel's order: a check of the planner's logic.  Host only. */
+qc_status qc_tile_emulate(const struct qc_circuit* c, const double* params, qc_dtype dtype, double* state);
 /* The tensor-core plan of circuit `c` (12 <= c->n <= 34): passes, stage blocks, deferred
  * phase factors and passes that are only a relabeling (copied by the CUDA-core pass);
  * host only.  QC_ERR_UNSUPPORTED: the circuit does not fit the tensor-core stages. */

@@ -81,6 +81,7 @@ _SIGS = {
     "qc_tc_block_plan": (ctypes.c_int, [ctypes.c_int, _I, ctypes.c_int, _I, _I, _I]),
     "qc_tc_emulate": (ctypes.c_int, [ctypes.c_void_p, _D, _D]),
     "qc_tc_plan_info": (ctypes.c_int, [ctypes.c_void_p, _D, _I, _I, _I, _I]),
+    "qc_tile_emulate": (ctypes.c_int, [ctypes.c_void_p, _D, ctypes.c_int, _D]),
     "qc_state_alloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(_P)]),
     "qc_state_wrap": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, ctypes.POINTER(_P)]),
     "qc_state_free": (ctypes.c_int, [_P]),
@@ -452,6 +453,18 @@ def qc_tc_emulate(circuit: Circuit, state, params=None) -> np.ndarray:
         params = np.ascontiguousarray(params, dtype=np.float64)
         p = params.ctypes.data_as(_D)
     _call("qc_tc_emulate", ctypes.addressof(circuit.c), p, out.ctypes.data_as(_D))
+    return out
+
+
+def qc_tile_emulate(circuit: Circuit, state, params=None, dtype: int = QC_C64) -> np.ndarray:
+    """The CUDA-core tile-pass plan for a state of `dtype` applied on the host, in FP64, to
+    a copy of `state` (complex128, 2^n values); host only."""
+    out = np.ascontiguousarray(state, dtype=np.complex128).copy()
+    p = None
+    if params is not None:
+        params = np.ascontiguousarray(params, dtype=np.float64)
+        p = params.ctypes.data_as(_D)
+    _call("qc_tile_emulate", ctypes.addressof(circuit.c), p, int(dtype), out.ctypes.data_as(_D))
     return out
 
 

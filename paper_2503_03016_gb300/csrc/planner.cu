@@ -1408,3 +1408,174 @@ extern "C" qc_status qc_plan_info(const qc_circuit* c, const double* params, qc_
     plan_stats<double>(c->n, rops, m, passes, stages, ops);
   return QC_OK;
 }
+
+// ---------------------------------------------------------------------------
+// host emulation of the CUDA-core tile passes (a check of the plan's logic)
+// ---------------------------------------------------------------------------
+namespace qcgb {
+
+// `state` (2^n complex128) through the plan QC_RUN_FUSED builds for a state of `dtype` --
+// its passes, register stages, tile ops with their conditions, matrices, phase tables,
+// CZ code words and relabeled SWAPs -- in FP64 and in the kernel's order (the complex64
+// plan's structure with the complex128 plan's value format)
+static void emulate_tile_plan(int n, const std::vector<ResolvedOp>& rops, qc_dtype dtype, cd* a) {
+  const bool c64 = dtype == QC_C64;
+  const int m = std::min(c64 ? 13 : 12, n);
+  const int L = c64 ? 4 : 3;
+  const int SB = c64 ? TileShape<float>::SB : (n >= kDfMinQubits ? kDfTileSB : TileShape<double>::SB);
+  std::vector<PlanOp> pops;
+  to_plan_ops(rops, pops);
+  const std::vector<BuiltPass> bps = build_passes(pops, n, m, L);
+  HostPlan<double> hp;
+  for (const BuiltPass& bp : bps)
+    emit_pass<double>(bp, pops, n, m, L, SB, hp, /*swap_ops=*/!c64, /*phase1_ops=*/true, /*relabel_swaps=*/true,
+                      /*bfly_ops=*/!c64, /*real1_ops=*/!c64);
+  const uint32_t T = 1u << m, NA = 1u << SB;
+  const uint64_t ntiles = uint64_t(1) << (n - m);
+  std::vector<cd> tile(T), out(T);
+  const cd* cpool = reinterpret_cast<const cd*>(hp.pool.data());
+  for (const TilePass& P : hp.passes) {
+    bool in[64] = {false};
+    for (int k = 0; k < m; ++k) in[P.bits[k]] = true;
+    std::vector<int> tnb;  // bit i of a tile number sits at global bit tnb[i]
+    for (int b = 0; b < n; ++b)
+      if (!in[b]) tnb.push_back(b);
+    const double* mats = hp.mats.data() + P.mat0;
+    for (uint64_t t = 0; t < ntiles; ++t) {
+      uint64_t base = 0;
+      for (size_t i = 0; i < tnb.size(); ++i)
+        if ((t >> i) & 1) base |= uint64_t(1) << tnb[i];
+      auto addr = [&](uint32_t u) {
+        uint64_t g = base;
+        for (int k = 0; k < m; ++k)
+          if ((u >> k) & 1) g |= uint64_t(1) << P.bits[k];
+        return g;
+      };
+      for (uint32_t u = 0; u < T; ++u) tile[u] = a[addr(u)];
+      for (int s = 0; s < P.nstages; ++s) {
+        const TileStage& st = hp.stages[size_t(P.stage0 + s)];
+        for (uint32_t th = 0; th < (1u << (m - SB)); ++th) {
+          uint32_t r0 = 0;
+          for (int k = 0; k < m - SB; ++k) r0 |= ((th >> k) & 1u) << st.lane_bit[k];
+          std::vector<uint32_t> pos(NA);
+          std::vector<cd> v(NA);
+          for (uint32_t j = 0; j < NA; ++j) {
+            uint32_t u = r0;
+            for (int k = 0; k < SB; ++k)
+              if ((j >> k) & 1) u |= 1u << st.slot_bit[k];
+            pos[j] = u;
+            v[j] = tile[u];
+          }
+          for (int q = 0; q < st.nops; ++q) {
+            const TileOp& op = hp.ops[size_t(P.op0 + st.op0 + q)];
+            if ((base & op.gmask) != op.gval) continue;
+            if ((r0 & op.lmask) != op.lval) continue;
+            const double* mm = mats + op.mat;
+            auto pairs = [&](int s0, auto f) {
+              for (uint32_t j = 0; j < NA; ++j)
+                if (!((j >> s0) & 1) && ((op.jmask >> j) & 1u)) f(j, j | (1u << s0));
+            };
+            if (op.type == TOP_DENSE1) {
+              const cd u00(mm[0], mm[1]), u01(mm[2], mm[3]), u10(mm[4], mm[5]), u11(mm[6], mm[7]);
+              pairs(op.s0, [&](uint32_t j, uint32_t j1) {
+                const cd x = v[j], y = v[j1];
+                v[j] = u00 * x + u01 * y;
+                v[j1] = u10 * x + u11 * y;
+              });
+            } else if (op.type == TOP_DENSE2) {
+              const uint32_t b0 = 1u << op.s0, b1 = 1u << op.s1;
+              for (uint32_t j = 0; j < NA; ++j) {
+                if (j & (b0 | b1)) continue;
+                const uint32_t ix[4] = {j, j | b1, j | b0, j | b0 | b1};
+                cd x[4], o[4];
+                for (int c = 0; c < 4; ++c) x[c] = v[ix[c]];
+                for (int r = 0; r < 4; ++r) {
+                  o[r] = 0.0;
+                  for (int c = 0; c < 4; ++c) o[r] += cd(mm[8 * r + 2 * c], mm[8 * r + 2 * c + 1]) * x[c];
+                }
+                for (int r = 0; r < 4; ++r) v[ix[r]] = o[r];
+              }
+            } else if (op.type == TOP_SWAP) {
+              const uint32_t b0 = 1u << op.s0, b1 = 1u << op.s1;
+              for (uint32_t j = 0; j < NA; ++j)
+                if (!(j & (b0 | b1))) std::swap(v[j | b0], v[j | b1]);
+            } else if (op.type == TOP_CZSET) {
+              // code words: per pair, bytes 0 and 1 = 0x80 | slot, a lane bit, or 0x40 | global bit
+              for (uint32_t j = 0; j < NA; ++j) {
+                int parity = 0;
+                for (int e = 0; e < op.s0; ++e) {
+                  uint32_t code;
+                  memcpy(&code, mm + e, sizeof(code));
+                  int bit[2];
+                  for (int h = 0; h < 2; ++h) {
+                    const uint32_t c = (code >> (8 * h)) & 0xFFu;
+                    bit[h] = (c & 0x80u) ? int((j >> (c & 7u)) & 1u)
+                                         : (c & 0x40u) ? int((base >> (c & 63u)) & 1u) : int((r0 >> c) & 1u);
+                  }
+                  parity ^= bit[0] & bit[1];
+                }
+                if (parity) v[j] = -v[j];
+              }
+            } else if (op.type == TOP_BFLY) {
+              const double sp = mm[0];
+              pairs(op.s0, [&](uint32_t j, uint32_t j1) {
+                const cd x0 = v[j], x1 = v[j1];
+                v[j] = sp * x0 + sp * x1;
+                v[j1] = sp * x0 - sp * x1;
+              });
+            } else if (op.type == TOP_REAL1) {
+              const double ra = mm[0], rb = mm[1], rc = mm[2], rd = mm[3];
+              pairs(op.s0, [&](uint32_t j, uint32_t j1) {
+                const cd x0 = v[j], x1 = v[j1];
+                v[j] = ra * x0 + rb * x1;
+                v[j1] = rc * x0 + rd * x1;
+              });
+            } else if (op.type == TOP_PHASE1) {
+              const cd z0(mm[0], mm[1]), z1(mm[2], mm[3]);
+              const uint32_t fixed =
+                  op.s0 >= 0 ? 0u : op.zloc >= 0 ? (r0 >> op.zloc) & 1u : uint32_t((base >> op.zglob) & 1u);
+              for (uint32_t j = 0; j < NA; ++j) {
+                if (!((op.jmask >> j) & 1u)) continue;
+                const uint32_t b = op.s0 >= 0 ? (j >> op.s0) & 1u : fixed;
+                v[j] *= b ? z1 : z0;
+              }
+            } else {  // TOP_PHASE: tile-number chunks, the thread's two local chunks, slot table
+              const cd* l0 = cpool + op.tab;
+              const cd* l1 = l0 + (1 << P.c0);
+              const cd* g0 = l1 + (1 << (m - P.c0));
+              const uint64_t gn = uint64_t(1) << P.cg, gm = gn - 1;
+              const cd w = g0[t & gm] * g0[gn + ((t >> P.cg) & gm)] * g0[2 * gn + ((t >> (2 * P.cg)) & gm)] *
+                           l0[r0 & ((1u << P.c0) - 1)] * l1[r0 >> P.c0];
+              for (uint32_t j = 0; j < NA; ++j)
+                if ((op.jmask >> j) & 1u) v[j] *= w * cd(mm[2 * j], mm[2 * j + 1]);
+            }
+          }
+          for (uint32_t j = 0; j < NA; ++j) tile[pos[j]] = v[j];
+        }
+      }
+      // write-out through the relabeling: output u from the position whose bit rbit[k]
+      // is bit k of u
+      for (uint32_t u = 0; u < T; ++u) {
+        uint32_t src = 0;
+        for (int k = 0; k < m; ++k) src |= ((u >> k) & 1u) << P.rbit[k];
+        out[u] = tile[src];
+      }
+      for (uint32_t u = 0; u < T; ++u) a[addr(u)] = out[u];
+    }
+  }
+}
+
+}  // namespace qcgb
+
+extern "C" qc_status qc_tile_emulate(const qc_circuit* c, const double* params, qc_dtype dtype, double* state) {
+  clear_error();
+  if (!c || !state || c->n < 10 || c->n > 24 || (c->nops > 0 && !c->ops) || (dtype != QC_C64 && dtype != QC_C128)) {
+    set_error("qc_tile_emulate: invalid arguments (10 <= n <= 24)");
+    return QC_ERR_INVALID_ARG;
+  }
+  std::vector<ResolvedOp> rops(size_t(c->nops));
+  for (int i = 0; i < c->nops; ++i)
+    if (qc_status st = resolve_op(c, c->ops[i], params, &rops[size_t(i)])) return st;
+  emulate_tile_plan(c->n, rops, dtype, reinterpret_cast<std::complex<double>*>(state));
+  return QC_OK;
+}
