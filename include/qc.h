@@ -137,6 +137,14 @@ qc_status qc_tc_emulate(const struct qc_circuit* c, const double* params, double
  * matrices, phase tables, CZ code words and relabeled SWAPs -- interpreted on the host in
  * FP64 in the kernel's order: a check of the planner's logic.  Host only. */
 qc_status qc_tile_emulate(const struct qc_circuit* c, const double* params, qc_dtype dtype, double* state);
+/* The fused adjoint reverse sweep's plan for circuit `c` (12 <= c->n <= 24; its RX, RY,
+ * RZ with a parameter are the recorded rotations) applied on the host in FP64 to `psi`
+ * (the circuit's output state) and `lam` (H psi) -- both host, 2^n interleaved complex128,
+ * modified in place -- with the sweep's record of each rotation, Im <lambda|G|psi> just
+ * before it is undone, written to records[0 .. rotations) in circuit order: the plan the
+ * gradient launches for a state of `dtype`, a check of its logic.  Host only. */
+qc_status qc_adjoint_emulate(const struct qc_circuit* c, const double* params, qc_dtype dtype, double* psi,
+                             double* lam, double* records, int nrec);
 /* The tensor-core plan of circuit `c` (12 <= c->n <= 34): passes, stage blocks, deferred
  * phase factors and passes that are only a relabeling (copied by the CUDA-core pass);
  * host only.  QC_ERR_UNSUPPORTED: the circuit does not fit the tensor-core stages. */

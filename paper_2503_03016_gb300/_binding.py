@@ -82,6 +82,7 @@ _SIGS = {
     "qc_tc_emulate": (ctypes.c_int, [ctypes.c_void_p, _D, _D]),
     "qc_tc_plan_info": (ctypes.c_int, [ctypes.c_void_p, _D, _I, _I, _I, _I]),
     "qc_tile_emulate": (ctypes.c_int, [ctypes.c_void_p, _D, ctypes.c_int, _D]),
+    "qc_adjoint_emulate": (ctypes.c_int, [ctypes.c_void_p, _D, ctypes.c_int, _D, _D, _D, ctypes.c_int]),
     "qc_state_alloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, ctypes.POINTER(_P)]),
     "qc_state_wrap": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _P, _P, ctypes.POINTER(_P)]),
     "qc_state_free": (ctypes.c_int, [_P]),
@@ -466,6 +467,19 @@ def qc_tile_emulate(circuit: Circuit, state, params=None, dtype: int = QC_C64) -
         p = params.ctypes.data_as(_D)
     _call("qc_tile_emulate", ctypes.addressof(circuit.c), p, int(dtype), out.ctypes.data_as(_D))
     return out
+
+
+def qc_adjoint_emulate(circuit: Circuit, params, psi, lam, dtype: int = QC_C64) -> np.ndarray:
+    """The records (Im <lambda|G|psi> per rotation, circuit order) of the fused reverse
+    sweep's plan applied on the host to copies of psi and lam = H psi; host only."""
+    ps = np.ascontiguousarray(psi, dtype=np.complex128).copy()
+    ls = np.ascontiguousarray(lam, dtype=np.complex128).copy()
+    params = np.ascontiguousarray(params, dtype=np.float64)
+    nrot = sum(1 for i in range(circuit.c.nops) if circuit._ops[i].param >= 0)
+    rec = np.zeros(max(1, nrot))
+    _call("qc_adjoint_emulate", ctypes.addressof(circuit.c), params.ctypes.data_as(_D), int(dtype),
+          ps.ctypes.data_as(_D), ls.ctypes.data_as(_D), rec.ctypes.data_as(_D), len(rec))
+    return rec[:nrot]
 
 
 def qc_tc_plan_info(circuit: Circuit, params=None):

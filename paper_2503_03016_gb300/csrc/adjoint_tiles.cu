@@ -772,3 +772,172 @@ template qc_status adjoint_reverse_tiles<double>(int, const std::vector<Resolved
                                                  AdjPlanBuf*, double*, int*);
 
 }  // namespace qcgb
+
+// ---------------------------------------------------------------------------
+// host emulation of the fused reverse sweep's plan (a check of its logic)
+// ---------------------------------------------------------------------------
+namespace qcgb {
+
+// The reverse sweep's plan for `rev` (the daggered gates in reverse order; grad/gen: the
+// rotation recorded just before each op, or -1) applied on the host in FP64 to psi and
+// lambda, each record's shares summed into rec[grad]: the plan adjoint_reverse_tiles
+// launches, the same passes, stages, op conditions and record positions
+template <typename R>
+static void emulate_reverse(int n, const std::vector<ResolvedOp>& rev, const std::vector<int>& grad,
+                            const std::vector<int>& gen, std::complex<double>* psi, std::complex<double>* lam,
+                            double* rec) {
+  using cd = std::complex<double>;
+  using S = AdjShape<R>;
+  const int m = S::M, L = S::L;
+  const bool df = sizeof(R) == 8 && n >= kDfMinQubits;
+  const int sb = df ? kAdjDfSB : S::SB;
+  std::vector<PlanOp> pops;
+  to_plan_ops(rev, pops, &grad, &gen);
+  drop_global_phases(pops);
+  const std::vector<BuiltPass> bps = build_passes(pops, n, m, L);
+  HostPlan<double> hp;
+  for (const BuiltPass& bp : bps)
+    emit_pass<double>(bp, pops, n, m, L, sb, hp, /*swap_ops=*/false, /*phase1_ops=*/true, /*relabel_swaps=*/false,
+                      /*bfly_ops=*/false, /*real1_ops=*/true);
+  const uint32_t T = 1u << m, NA = 1u << sb;
+  const uint64_t ntiles = uint64_t(1) << (n - m);
+  const cd* cpool = reinterpret_cast<const cd*>(hp.pool.data());
+  std::vector<cd> tp(T), tl(T), v(NA), w(NA);
+  std::vector<uint32_t> pos(NA);
+  for (const TilePass& P : hp.passes) {
+    bool in[64] = {false};
+    for (int k = 0; k < m; ++k) in[P.bits[k]] = true;
+    std::vector<int> tnb;
+    for (int b = 0; b < n; ++b)
+      if (!in[b]) tnb.push_back(b);
+    const double* mats = hp.mats.data() + P.mat0;
+    for (uint64_t t = 0; t < ntiles; ++t) {
+      uint64_t base = 0;
+      for (size_t i = 0; i < tnb.size(); ++i)
+        if ((t >> i) & 1) base |= uint64_t(1) << tnb[i];
+      auto addr = [&](uint32_t u) {
+        uint64_t g = base;
+        for (int k = 0; k < m; ++k)
+          if ((u >> k) & 1) g |= uint64_t(1) << P.bits[k];
+        return g;
+      };
+      for (uint32_t u = 0; u < T; ++u) {
+        tp[u] = psi[addr(u)];
+        tl[u] = lam[addr(u)];
+      }
+      for (int s = 0; s < P.nstages; ++s) {
+        const TileStage& st = hp.stages[size_t(P.stage0 + s)];
+        for (uint32_t th = 0; th < (1u << (m - sb)); ++th) {
+          uint32_t r0 = 0;
+          for (int k = 0; k < m - sb; ++k) r0 |= ((th >> k) & 1u) << st.lane_bit[k];
+          for (uint32_t j = 0; j < NA; ++j) {
+            uint32_t u = r0;
+            for (int k = 0; k < sb; ++k)
+              if ((j >> k) & 1) u |= 1u << st.slot_bit[k];
+            pos[j] = u;
+            v[j] = tp[u];
+            w[j] = tl[u];
+          }
+          for (int q = 0; q < st.nops; ++q) {
+            const TileOp& op = hp.ops[size_t(P.op0 + st.op0 + q)];
+            if (op.grad >= 0) {  // the record: Im <lambda|G|psi> over this thread's amplitudes
+              double share = 0.0;
+              if (op.gen == 2) {
+                int ks = -1;
+                for (int k = 0; k < sb; ++k)
+                  if (st.slot_bit[k] == op.zloc) ks = k;
+                const uint32_t fixed =
+                    op.zloc >= 0 ? ((r0 >> op.zloc) & 1u) : uint32_t((base >> op.zglob) & 1u);
+                for (uint32_t j = 0; j < NA; ++j) {
+                  const uint32_t b = ks >= 0 ? (j >> ks) & 1u : fixed;
+                  const double x = std::imag(std::conj(w[j]) * v[j]);
+                  share += b ? -x : x;
+                }
+              } else {  // X or Y on slot s0
+                for (uint32_t j = 0; j < NA; ++j) {
+                  if ((j >> op.s0) & 1) continue;
+                  const uint32_t j1 = j | (1u << op.s0);
+                  const cd g0 = op.gen == 0 ? v[j1] : cd(0.0, -1.0) * v[j1];
+                  const cd g1 = op.gen == 0 ? v[j] : cd(0.0, 1.0) * v[j];
+                  share += std::imag(std::conj(w[j]) * g0) + std::imag(std::conj(w[j1]) * g1);
+                }
+              }
+              rec[op.grad] += share;
+            }
+            if ((base & op.gmask) != op.gval) continue;
+            if ((r0 & op.lmask) != op.lval) continue;
+            emulate_tile_op(op, mats, P, cpool, m, t, base, r0, v);
+            emulate_tile_op(op, mats, P, cpool, m, t, base, r0, w);
+          }
+          for (uint32_t j = 0; j < NA; ++j) {
+            tp[pos[j]] = v[j];
+            tl[pos[j]] = w[j];
+          }
+        }
+      }
+      for (uint32_t u = 0; u < T; ++u) {
+        psi[addr(u)] = tp[u];
+        lam[addr(u)] = tl[u];
+      }
+    }
+  }
+}
+
+}  // namespace qcgb
+
+extern "C" qc_status qc_adjoint_emulate(const qc_circuit* c, const double* params, qc_dtype dtype, double* psi,
+                                        double* lam, double* records, int nrec) {
+  using namespace qcgb;
+  clear_error();
+  if (!c || !psi || !lam || !records || c->n < AdjShape<float>::M || c->n > 24 || (c->nops > 0 && !c->ops) ||
+      (dtype != QC_C64 && dtype != QC_C128)) {
+    set_error("qc_adjoint_emulate: invalid arguments (%d <= n <= 24)", AdjShape<float>::M);
+    return QC_ERR_INVALID_ARG;
+  }
+  // the rotations in order (RX, RY, RZ with a parameter) and the reverse circuit with its
+  // records, as the gradient builds them
+  std::vector<ResolvedOp> rops(size_t(c->nops));
+  std::vector<int> gen(size_t(c->nops), -1);
+  int nrot = 0;
+  for (int i = 0; i < c->nops; ++i) {
+    const qc_op& op = c->ops[i];
+    if (qc_status st = resolve_op(c, op, params, &rops[size_t(i)])) return st;
+    if (op.param >= 0) {
+      if (op.kind != QC_GATE_RX && op.kind != QC_GATE_RY && op.kind != QC_GATE_RZ) {
+        set_error("qc_adjoint_emulate: parameterised op %d must be RX, RY or RZ", i);
+        return QC_ERR_UNSUPPORTED;
+      }
+      gen[size_t(i)] = op.kind == QC_GATE_RX ? 0 : op.kind == QC_GATE_RY ? 1 : 2;
+      ++nrot;
+    }
+  }
+  if (nrec < nrot) {
+    set_error("qc_adjoint_emulate: %d records needed", nrot);
+    return QC_ERR_INVALID_ARG;
+  }
+  std::vector<ResolvedOp> rev;
+  std::vector<int> rgrad, rgen;
+  int r = nrot;
+  for (int i = c->nops - 1; i >= 0; --i) {
+    ResolvedOp ud = rops[size_t(i)];
+    const int dim = ud.form == FORM_2Q ? 4 : 2;
+    double t[32];
+    for (int a = 0; a < dim; ++a)
+      for (int b = 0; b < dim; ++b) {
+        t[2 * (a * dim + b)] = ud.m[2 * (b * dim + a)];
+        t[2 * (a * dim + b) + 1] = -ud.m[2 * (b * dim + a) + 1];
+      }
+    memcpy(ud.m, t, sizeof(double) * 2 * dim * dim);
+    rev.push_back(ud);
+    rgrad.push_back(gen[size_t(i)] >= 0 ? --r : -1);
+    rgen.push_back(gen[size_t(i)]);
+  }
+  for (int k = 0; k < nrot; ++k) records[k] = 0.0;
+  auto* ps = reinterpret_cast<std::complex<double>*>(psi);
+  auto* ls = reinterpret_cast<std::complex<double>*>(lam);
+  if (dtype == QC_C64)
+    emulate_reverse<float>(c->n, rev, rgrad, rgen, ps, ls, records);
+  else
+    emulate_reverse<double>(c->n, rev, rgrad, rgen, ps, ls, records);
+  return QC_OK;
+}

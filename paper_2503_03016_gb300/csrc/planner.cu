@@ -1414,6 +1414,92 @@ extern "C" qc_status qc_plan_info(const qc_circuit* c, const double* params, qc_
 // ---------------------------------------------------------------------------
 namespace qcgb {
 
+// One tile op of a CUDA-core plan on a thread's 2^SB amplitudes v (slot combination j at
+// v[j]), interpreted in FP64 (conditions checked by the caller)
+void emulate_tile_op(const TileOp& op, const double* mats, const TilePass& P, const std::complex<double>* cpool,
+                     int m, uint64_t t, uint64_t base, uint32_t r0, std::vector<std::complex<double>>& v) {
+  const uint32_t NA = uint32_t(v.size());
+  const double* mm = mats + op.mat;
+  auto pairs = [&](int s0, auto f) {
+    for (uint32_t j = 0; j < NA; ++j)
+      if (!((j >> s0) & 1) && ((op.jmask >> j) & 1u)) f(j, j | (1u << s0));
+  };
+  if (op.type == TOP_DENSE1) {
+    const cd u00(mm[0], mm[1]), u01(mm[2], mm[3]), u10(mm[4], mm[5]), u11(mm[6], mm[7]);
+    pairs(op.s0, [&](uint32_t j, uint32_t j1) {
+      const cd x = v[j], y = v[j1];
+      v[j] = u00 * x + u01 * y;
+      v[j1] = u10 * x + u11 * y;
+    });
+  } else if (op.type == TOP_DENSE2) {
+    const uint32_t b0 = 1u << op.s0, b1 = 1u << op.s1;
+    for (uint32_t j = 0; j < NA; ++j) {
+      if (j & (b0 | b1)) continue;
+      const uint32_t ix[4] = {j, j | b1, j | b0, j | b0 | b1};
+      cd x[4], o[4];
+      for (int c = 0; c < 4; ++c) x[c] = v[ix[c]];
+      for (int r = 0; r < 4; ++r) {
+        o[r] = 0.0;
+        for (int c = 0; c < 4; ++c) o[r] += cd(mm[8 * r + 2 * c], mm[8 * r + 2 * c + 1]) * x[c];
+      }
+      for (int r = 0; r < 4; ++r) v[ix[r]] = o[r];
+    }
+  } else if (op.type == TOP_SWAP) {
+    const uint32_t b0 = 1u << op.s0, b1 = 1u << op.s1;
+    for (uint32_t j = 0; j < NA; ++j)
+      if (!(j & (b0 | b1))) std::swap(v[j | b0], v[j | b1]);
+  } else if (op.type == TOP_CZSET) {
+    // code words: per pair, bytes 0 and 1 = 0x80 | slot, a lane bit, or 0x40 | global bit
+    for (uint32_t j = 0; j < NA; ++j) {
+      int parity = 0;
+      for (int e = 0; e < op.s0; ++e) {
+        uint32_t code;
+        memcpy(&code, mm + e, sizeof(code));
+        int bit[2];
+        for (int h = 0; h < 2; ++h) {
+          const uint32_t c = (code >> (8 * h)) & 0xFFu;
+          bit[h] = (c & 0x80u) ? int((j >> (c & 7u)) & 1u)
+                               : (c & 0x40u) ? int((base >> (c & 63u)) & 1u) : int((r0 >> c) & 1u);
+        }
+        parity ^= bit[0] & bit[1];
+      }
+      if (parity) v[j] = -v[j];
+    }
+  } else if (op.type == TOP_BFLY) {
+    const double sp = mm[0];
+    pairs(op.s0, [&](uint32_t j, uint32_t j1) {
+      const cd x0 = v[j], x1 = v[j1];
+      v[j] = sp * x0 + sp * x1;
+      v[j1] = sp * x0 - sp * x1;
+    });
+  } else if (op.type == TOP_REAL1) {
+    const double ra = mm[0], rb = mm[1], rc = mm[2], rd = mm[3];
+    pairs(op.s0, [&](uint32_t j, uint32_t j1) {
+      const cd x0 = v[j], x1 = v[j1];
+      v[j] = ra * x0 + rb * x1;
+      v[j1] = rc * x0 + rd * x1;
+    });
+  } else if (op.type == TOP_PHASE1) {
+    const cd z0(mm[0], mm[1]), z1(mm[2], mm[3]);
+    const uint32_t fixed =
+        op.s0 >= 0 ? 0u : op.zloc >= 0 ? (r0 >> op.zloc) & 1u : uint32_t((base >> op.zglob) & 1u);
+    for (uint32_t j = 0; j < NA; ++j) {
+      if (!((op.jmask >> j) & 1u)) continue;
+      const uint32_t b = op.s0 >= 0 ? (j >> op.s0) & 1u : fixed;
+      v[j] *= b ? z1 : z0;
+    }
+  } else {  // TOP_PHASE: tile-number chunks, the thread's two local chunks, slot table
+    const cd* l0 = cpool + op.tab;
+    const cd* l1 = l0 + (1 << P.c0);
+    const cd* g0 = l1 + (1 << (m - P.c0));
+    const uint64_t gn = uint64_t(1) << P.cg, gm = gn - 1;
+    const cd w = g0[t & gm] * g0[gn + ((t >> P.cg) & gm)] * g0[2 * gn + ((t >> (2 * P.cg)) & gm)] *
+                 l0[r0 & ((1u << P.c0) - 1)] * l1[r0 >> P.c0];
+    for (uint32_t j = 0; j < NA; ++j)
+      if ((op.jmask >> j) & 1u) v[j] *= w * cd(mm[2 * j], mm[2 * j + 1]);
+  }
+}
+
 // `state` (2^n complex128) through the plan QC_RUN_FUSED builds for a state of `dtype` --
 // its passes, register stages, tile ops with their conditions, matrices, phase tables,
 // CZ code words and relabeled SWAPs -- in FP64 and in the kernel's order (the complex64
@@ -1470,85 +1556,7 @@ static void emulate_tile_plan(int n, const std::vector<ResolvedOp>& rops, qc_dty
             const TileOp& op = hp.ops[size_t(P.op0 + st.op0 + q)];
             if ((base & op.gmask) != op.gval) continue;
             if ((r0 & op.lmask) != op.lval) continue;
-            const double* mm = mats + op.mat;
-            auto pairs = [&](int s0, auto f) {
-              for (uint32_t j = 0; j < NA; ++j)
-                if (!((j >> s0) & 1) && ((op.jmask >> j) & 1u)) f(j, j | (1u << s0));
-            };
-            if (op.type == TOP_DENSE1) {
-              const cd u00(mm[0], mm[1]), u01(mm[2], mm[3]), u10(mm[4], mm[5]), u11(mm[6], mm[7]);
-              pairs(op.s0, [&](uint32_t j, uint32_t j1) {
-                const cd x = v[j], y = v[j1];
-                v[j] = u00 * x + u01 * y;
-                v[j1] = u10 * x + u11 * y;
-              });
-            } else if (op.type == TOP_DENSE2) {
-              const uint32_t b0 = 1u << op.s0, b1 = 1u << op.s1;
-              for (uint32_t j = 0; j < NA; ++j) {
-                if (j & (b0 | b1)) continue;
-                const uint32_t ix[4] = {j, j | b1, j | b0, j | b0 | b1};
-                cd x[4], o[4];
-                for (int c = 0; c < 4; ++c) x[c] = v[ix[c]];
-                for (int r = 0; r < 4; ++r) {
-                  o[r] = 0.0;
-                  for (int c = 0; c < 4; ++c) o[r] += cd(mm[8 * r + 2 * c], mm[8 * r + 2 * c + 1]) * x[c];
-                }
-                for (int r = 0; r < 4; ++r) v[ix[r]] = o[r];
-              }
-            } else if (op.type == TOP_SWAP) {
-              const uint32_t b0 = 1u << op.s0, b1 = 1u << op.s1;
-              for (uint32_t j = 0; j < NA; ++j)
-                if (!(j & (b0 | b1))) std::swap(v[j | b0], v[j | b1]);
-            } else if (op.type == TOP_CZSET) {
-              // code words: per pair, bytes 0 and 1 = 0x80 | slot, a lane bit, or 0x40 | global bit
-              for (uint32_t j = 0; j < NA; ++j) {
-                int parity = 0;
-                for (int e = 0; e < op.s0; ++e) {
-                  uint32_t code;
-                  memcpy(&code, mm + e, sizeof(code));
-                  int bit[2];
-                  for (int h = 0; h < 2; ++h) {
-                    const uint32_t c = (code >> (8 * h)) & 0xFFu;
-                    bit[h] = (c & 0x80u) ? int((j >> (c & 7u)) & 1u)
-                                         : (c & 0x40u) ? int((base >> (c & 63u)) & 1u) : int((r0 >> c) & 1u);
-                  }
-                  parity ^= bit[0] & bit[1];
-                }
-                if (parity) v[j] = -v[j];
-              }
-            } else if (op.type == TOP_BFLY) {
-              const double sp = mm[0];
-              pairs(op.s0, [&](uint32_t j, uint32_t j1) {
-                const cd x0 = v[j], x1 = v[j1];
-                v[j] = sp * x0 + sp * x1;
-                v[j1] = sp * x0 - sp * x1;
-              });
-            } else if (op.type == TOP_REAL1) {
-              const double ra = mm[0], rb = mm[1], rc = mm[2], rd = mm[3];
-              pairs(op.s0, [&](uint32_t j, uint32_t j1) {
-                const cd x0 = v[j], x1 = v[j1];
-                v[j] = ra * x0 + rb * x1;
-                v[j1] = rc * x0 + rd * x1;
-              });
-            } else if (op.type == TOP_PHASE1) {
-              const cd z0(mm[0], mm[1]), z1(mm[2], mm[3]);
-              const uint32_t fixed =
-                  op.s0 >= 0 ? 0u : op.zloc >= 0 ? (r0 >> op.zloc) & 1u : uint32_t((base >> op.zglob) & 1u);
-              for (uint32_t j = 0; j < NA; ++j) {
-                if (!((op.jmask >> j) & 1u)) continue;
-                const uint32_t b = op.s0 >= 0 ? (j >> op.s0) & 1u : fixed;
-                v[j] *= b ? z1 : z0;
-              }
-            } else {  // TOP_PHASE: tile-number chunks, the thread's two local chunks, slot table
-              const cd* l0 = cpool + op.tab;
-              const cd* l1 = l0 + (1 << P.c0);
-              const cd* g0 = l1 + (1 << (m - P.c0));
-              const uint64_t gn = uint64_t(1) << P.cg, gm = gn - 1;
-              const cd w = g0[t & gm] * g0[gn + ((t >> P.cg) & gm)] * g0[2 * gn + ((t >> (2 * P.cg)) & gm)] *
-                           l0[r0 & ((1u << P.c0) - 1)] * l1[r0 >> P.c0];
-              for (uint32_t j = 0; j < NA; ++j)
-                if ((op.jmask >> j) & 1u) v[j] *= w * cd(mm[2 * j], mm[2 * j + 1]);
-            }
+            emulate_tile_op(op, mats, P, cpool, m, t, base, r0, v);
           }
           for (uint32_t j = 0; j < NA; ++j) tile[pos[j]] = v[j];
         }

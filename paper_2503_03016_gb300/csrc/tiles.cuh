@@ -571,6 +571,11 @@ void to_plan_ops(const std::vector<ResolvedOp>& in, std::vector<PlanOp>& out, co
 // a complex64 pass with no stages whose SWAPs are a relabeling (P.permuted, P.rbit; P.bits
 // ascending): each tile copied through the permutation by the CUDA-core tile pass
 qc_status launch_copy_pass(qc_state* s, const TilePass& P);
+// host emulation: one tile op of a CUDA-core plan (complex128 value format) on a thread's
+// 2^SB amplitudes v, in FP64 (the op's conditions checked by the caller); mats: the
+// pass's matrix block, cpool: the plan's phase tables as complex values
+void emulate_tile_op(const TileOp& op, const double* mats, const TilePass& P, const std::complex<double>* cpool,
+                     int m, uint64_t t, uint64_t base, uint32_t r0, std::vector<std::complex<double>>& v);
 // exactly the SWAP permutation of its two target bits, with no condition
 bool is_exact_swap(const PlanOp& p);
 // an op with its global bits renamed: bit b -> ren[b]
