@@ -604,9 +604,77 @@ static int lookahead_stage_count(const std::vector<int>& rest, const std::vector
   return best;
 }
 
+void split_stages_search(const BuiltPass& bp, const std::vector<PlanOp>& pops, const int* local_of, int sb,
+                         std::vector<std::vector<int>>& takes, std::vector<std::vector<int>>& acts, int whole_ops,
+                         int depth);
+
+// The searched cuts depend only on the pass's structure -- each op's kind, bits, condition
+// and phase bits, the tile's local bits -- not on matrices or angles, so they are kept
+// for reuse when a circuit runs again with other parameters (a training loop): the
+// search costs far more than the rest of the plan.  Cuts are stored as positions in
+// bp.ops; a bounded number of recent ones are kept.
+struct StageCutEntry {
+  std::vector<int64_t> key;
+  std::vector<std::vector<int>> takes, acts;  // takes: positions in bp.ops
+};
+static std::mutex g_cut_mu;
+static std::vector<StageCutEntry> g_cuts;  // most recent last
+constexpr size_t kStageCutEntries = 512;
+
+static std::vector<int64_t> stage_cut_key(const BuiltPass& bp, const std::vector<PlanOp>& pops, const int* local_of,
+                                          int sb, int whole_ops, int depth) {
+  std::vector<int64_t> key = {sb, whole_ops, depth};
+  for (int b : bp.B) key.push_back(int64_t(b) * 64 + local_of[b]);
+  for (int idx : bp.ops) {
+    const PlanOp& p = pops[size_t(idx)];
+    key.push_back(p.phase ? -1 : p.nt);
+    key.push_back(p.phase ? 0 : int64_t(p.tb[0]) * 64 + (p.nt == 2 ? p.tb[1] : 0));
+    key.push_back(int64_t(p.touched));
+    key.push_back(int64_t(p.cmask));
+    key.push_back(int64_t(p.cval));
+    uint64_t bb = 0;
+    for (const auto& be : p.beta) bb |= uint64_t(1) << be.first;
+    key.push_back(int64_t(bb));
+  }
+  return key;
+}
+
 void split_stages_lookahead(const BuiltPass& bp, const std::vector<PlanOp>& pops, const int* local_of, int sb,
                             std::vector<std::vector<int>>& takes, std::vector<std::vector<int>>& acts, int whole_ops,
                             int depth) {
+  const std::vector<int64_t> key = stage_cut_key(bp, pops, local_of, sb, whole_ops, depth);
+  {
+    std::lock_guard<std::mutex> lock(g_cut_mu);
+    for (size_t e = 0; e < g_cuts.size(); ++e)
+      if (g_cuts[e].key == key) {
+        for (const std::vector<int>& t : g_cuts[e].takes) {
+          takes.emplace_back();
+          for (int pos : t) takes.back().push_back(bp.ops[size_t(pos)]);
+        }
+        for (const std::vector<int>& a : g_cuts[e].acts) acts.push_back(a);
+        return;
+      }
+  }
+  const size_t t0 = takes.size(), a0 = acts.size();
+  split_stages_search(bp, pops, local_of, sb, takes, acts, whole_ops, depth);
+  StageCutEntry ent;
+  ent.key = key;
+  for (size_t i = t0; i < takes.size(); ++i) {
+    ent.takes.emplace_back();
+    for (int idx : takes[i]) {
+      const auto it = std::find(bp.ops.begin(), bp.ops.end(), idx);
+      ent.takes.back().push_back(int(it - bp.ops.begin()));
+    }
+  }
+  for (size_t i = a0; i < acts.size(); ++i) ent.acts.push_back(acts[i]);
+  std::lock_guard<std::mutex> lock(g_cut_mu);
+  if (g_cuts.size() >= kStageCutEntries) g_cuts.erase(g_cuts.begin());
+  g_cuts.push_back(std::move(ent));
+}
+
+void split_stages_search(const BuiltPass& bp, const std::vector<PlanOp>& pops, const int* local_of, int sb,
+                         std::vector<std::vector<int>>& takes, std::vector<std::vector<int>>& acts, int whole_ops,
+                         int depth) {
   int m = 0;
   for (int b = 0; b < 64; ++b) m = std::max(m, local_of[b] + 1);
   std::vector<int> rest = bp.ops;

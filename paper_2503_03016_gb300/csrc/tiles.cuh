@@ -607,7 +607,8 @@ void emit_pass(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, int 
 void split_stages(const BuiltPass& bp, const std::vector<PlanOp>& pops, const int* local_of, int sb,
                   std::vector<std::vector<int>>& takes, std::vector<std::vector<int>>& acts, int whole_ops = 0);
 // as split_stages, each stage chosen among the same candidates by the fewest stages for
-// the pass when the next `depth` stages are searched and the rest cut greedily
+// the pass when the next `depth` stages are searched and the rest cut greedily; cuts are
+// kept by the pass's structure and reused (matrices and angles do not enter them)
 void split_stages_lookahead(const BuiltPass& bp, const std::vector<PlanOp>& pops, const int* local_of, int sb,
                             std::vector<std::vector<int>>& takes, std::vector<std::vector<int>>& acts, int whole_ops,
                             int depth);
