@@ -1231,6 +1231,41 @@ static bool relabel_swaps(const BuiltPass& bp, const std::vector<PlanOp>& pops, 
   return permuted;
 }
 
+// The variant a pass's plan takes (every phase bit a slot or deferred factors; SWAPs as
+// ops or relabeled) depends only on the pass's structure: op kinds, bits, conditions,
+// phase bits and which ops are exact SWAPs, the tile's bits and its copy kind.  Recent
+// choices are kept (-1: none fits; -2: not known).
+static std::vector<int64_t> variant_key(const BuiltPass& bp, const std::vector<PlanOp>& pops, int n, bool tma) {
+  std::vector<int64_t> key = {n, tma ? 1 : 0};
+  for (int b : bp.B) key.push_back(b);
+  for (int idx : bp.ops) {
+    const PlanOp& p = pops[size_t(idx)];
+    key.push_back(p.phase ? -1 : p.nt);
+    key.push_back(p.phase ? 0 : int64_t(p.tb[0]) * 64 + (p.nt == 2 ? p.tb[1] : 0));
+    key.push_back(int64_t(p.touched));
+    key.push_back(int64_t(p.cmask));
+    key.push_back(int64_t(p.cval));
+    uint64_t bb = 0;
+    for (const auto& be : p.beta) bb |= uint64_t(1) << be.first;
+    key.push_back(int64_t(bb));
+    key.push_back(is_exact_swap(p) ? 1 : 0);
+  }
+  return key;
+}
+static std::mutex g_variant_mu;
+static std::vector<std::pair<std::vector<int64_t>, int>> g_variants;  // most recent last
+static int cached_variant(const std::vector<int64_t>& key) {
+  std::lock_guard<std::mutex> lock(g_variant_mu);
+  for (const auto& e : g_variants)
+    if (e.first == key) return e.second;
+  return -2;
+}
+static void keep_variant(const std::vector<int64_t>& key, int pick) {
+  std::lock_guard<std::mutex> lock(g_variant_mu);
+  if (g_variants.size() >= 512) g_variants.erase(g_variants.begin());
+  g_variants.push_back({key, pick});
+}
+
 // A circuit's tensor-core plan on the host: passes, their box plans and kinds (defer: 0
 // plain, 1 with deferred phase factors, 2 a relabeling copied by the CUDA-core pass),
 // stage records, B images and factor tables; optionally each stage's FP64 block and slot
@@ -1298,20 +1333,31 @@ static bool tc_build(int n, const std::vector<ResolvedOp>& rops, void* amps, TcH
       return tc_pass_blocks(rl ? br : bl, rl ? rpops : pops, n, tm.tma != 0, 1 + (v & 1), stages, imgs, tabs,
                             &def0, &ndef, hp.blocks, hp.slots);
     };
-    int pick = -1;
-    double best = 1e30;
-    for (int v = 0; v < (permuted ? 4 : 2); ++v) {
+    // (the choice depends on the pass's structure only: kept and reused when the circuit
+    // runs again with other values)
+    const std::vector<int64_t> vkey = variant_key(bl, pops, n, tm.tma != 0);
+    int pick = cached_variant(vkey);
+    if (pick >= 0) {  // re-planned below; should it no longer fit, every variant is tried
       reset();
-      if (!plan(v)) continue;
-      const double score = double(stages.size() - size_t(P.stage0)) + (v >= 2 ? 0.5 : 0.0);
-      if (score < best) {
-        best = score;
-        pick = v;
+      if (!plan(pick)) pick = -2;
+    }
+    if (pick == -2) {
+      pick = -1;
+      double best = 1e30;
+      for (int v = 0; v < (permuted ? 4 : 2); ++v) {
+        reset();
+        if (!plan(v)) continue;
+        const double score = double(stages.size() - size_t(P.stage0)) + (v >= 2 ? 0.5 : 0.0);
+        if (score < best) {
+          best = score;
+          pick = v;
+        }
       }
+      keep_variant(vkey, pick);
     }
     if (pick < 0) return false;
     reset();
-    plan(pick);
+    if (!plan(pick)) return false;
     bool copy = false;
     if (pick >= 2) {
       P.permuted = 1;

@@ -155,3 +155,26 @@ def test_plan_statistics_pinned():
     assert P.qc_tc_plan_info(P.Circuit(32, W.qft(32))) == (8, 9, 30, 3)
     ops, params, _, _ = W.adjoint_workload(24, 10, 5)
     assert P.qc_tc_plan_info(P.Circuit(24, ops), params)[:2] == (8, 38)
+
+
+def test_replanning_with_new_values_reuses_the_structure():
+    """The same circuit with other rotation angles (a training loop) re-plans with the
+    variants kept from the first plan (the same passes and stages for generic angles);
+    the plan stays exact for every set of values, including angles that make rotations
+    diagonal or the identity (a new structure: its own search)."""
+    import paper_2503_03016_gb300 as P
+    n, layers = 15, 4
+    ops = W.ansatz(n, layers, True)
+    psi = W.random_state(n, 6)
+    rng = np.random.default_rng(11)
+    info = None
+    for trial in range(4):
+        params = rng.uniform(0, 2 * np.pi, layers * 2 * n)
+        if trial == 3:
+            params[::3] = 0.0  # identity rotations
+            params[1::3] = np.pi
+        got = P.qc_tc_plan_info(P.Circuit(n, ops), params)
+        info = got if info is None else info
+        if trial < 3:
+            assert got[:2] == info[:2]
+        assert emulate(n, ops, psi, params) <= 1e-12, trial
