@@ -1337,9 +1337,11 @@ static bool tc_build(int n, const std::vector<ResolvedOp>& rops, void* amps, TcH
     // runs again with other values)
     const std::vector<int64_t> vkey = variant_key(bl, pops, n, tm.tma != 0);
     int pick = cached_variant(vkey);
-    if (pick >= 0) {  // re-planned below; should it no longer fit, every variant is tried
+    bool planned = false;
+    if (pick >= 0) {  // should it no longer fit, every variant is tried
       reset();
-      if (!plan(pick)) pick = -2;
+      planned = plan(pick);
+      if (!planned) pick = -2;
     }
     if (pick == -2) {
       pick = -1;
@@ -1356,8 +1358,10 @@ static bool tc_build(int n, const std::vector<ResolvedOp>& rops, void* amps, TcH
       keep_variant(vkey, pick);
     }
     if (pick < 0) return false;
-    reset();
-    if (!plan(pick)) return false;
+    if (!planned) {
+      reset();
+      if (!plan(pick)) return false;
+    }
     bool copy = false;
     if (pick >= 2) {
       P.permuted = 1;
