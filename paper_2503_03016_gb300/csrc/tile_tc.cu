@@ -1282,6 +1282,25 @@ struct TcHostPlan {
   std::vector<std::array<int8_t, 5>>* slots = nullptr;
 };
 
+// An empty host plan whose vectors keep their capacity from this thread's earlier plans:
+// re-planning a circuit (new parameter values) then writes its 2-4 MB of stage images
+// into memory already mapped instead of growing a new vector page by page.  Valid until
+// the thread's next call.
+static TcHostPlan& tc_scratch_plan() {
+  thread_local TcHostPlan hp;
+  hp.passes.clear();
+  hp.tmas.clear();
+  hp.defer.clear();
+  hp.stages.clear();
+  hp.imgs.clear();
+  hp.tabs.row.clear();
+  hp.tabs.glob.clear();
+  hp.tabs.count = 0;
+  hp.blocks = nullptr;
+  hp.slots = nullptr;
+  return hp;
+}
+
 static bool tc_build(int n, const std::vector<ResolvedOp>& rops, void* amps, TcHostPlan& hp) {
   std::vector<PlanOp> pops;
   to_plan_ops(rops, pops);
@@ -1392,7 +1411,7 @@ static bool tc_build(int n, const std::vector<ResolvedOp>& rops, void* amps, TcH
 static qc_status tc_plan(qc_state* s, const std::vector<ResolvedOp>& rops, int dev) {
   const int n = s->n;
   g_tc.valid = false;
-  TcHostPlan hp;
+  TcHostPlan& hp = tc_scratch_plan();
   const bool tc = tc_build(n, rops, s->amps, hp);
   std::vector<TilePass>& passes = hp.passes;
   std::vector<TcTma>& tmas = hp.tmas;
@@ -1859,7 +1878,7 @@ extern "C" qc_status qc_tc_plan_info(const qc_circuit* c, const double* params, 
   std::vector<ResolvedOp> rops(size_t(c->nops));
   for (int i = 0; i < c->nops; ++i)
     if (qc_status st = resolve_op(c, c->ops[i], params, &rops[size_t(i)])) return st;
-  TcHostPlan hp;
+  TcHostPlan& hp = tc_scratch_plan();
   if (!tc_build(c->n, rops, nullptr, hp)) {
     set_error("qc_tc_plan_info: the circuit does not fit the tensor-core stages");
     return QC_ERR_UNSUPPORTED;
