@@ -178,3 +178,19 @@ def test_replanning_with_new_values_reuses_the_structure():
         if trial < 3:
             assert got[:2] == info[:2]
         assert emulate(n, ops, psi, params) <= 1e-12, trial
+
+
+def test_plans_do_not_carry_over_between_circuits():
+    """The host plan's vectors are reused from one plan to the next on a thread: a plan
+    made after a larger one (more passes, stage images and factor tables) and after a
+    smaller one is the same plan, and the circuit still emulates exactly."""
+    import paper_2503_03016_gb300 as P
+    n = 16
+    small = P.Circuit(13, W.brickwork(13, 6, 3))
+    large = P.Circuit(18, W.qft(18))
+    ops = W.circuit_inverse(W.qft(n))
+    first = P.qc_tc_plan_info(P.Circuit(n, ops))
+    for other in (large, small, large):
+        P.qc_tc_plan_info(other)
+        assert P.qc_tc_plan_info(P.Circuit(n, ops)) == first
+    assert emulate(n, ops, W.gaussian_state(n, 9)) <= 1e-6
