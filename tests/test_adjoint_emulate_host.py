@@ -72,3 +72,41 @@ def test_mixed_generators_shared_parameters_and_fixed_gates(dtype):
     coeffs = np.linspace(0.5, 1.5, len(terms))
     g = emulated_grad(n, ops, params, terms, coeffs, dtype)
     np.testing.assert_allclose(g, oracle.param_shift_grad(n, ops, params, terms, coeffs), atol=1e-12, rtol=0)
+
+
+@pytest.mark.parametrize("dtype", ["c64", "c128"])
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_swaps_haar_gates_and_random_pauli_sums(dtype, seed):
+    """Rotations between SWAPs, Haar two-qubit gates, CNOT, CZ and controlled phases on
+    random qubits; H a sum of random 1- to 3-qubit X/Y/Z strings with signed weights."""
+    n = 13
+    rng = np.random.default_rng(seed)
+    npar = 9
+    ops = []
+    for i in range(100):
+        c = int(rng.integers(0, 9))
+        a, b = (int(v) for v in rng.choice(n, 2, replace=False))
+        if c < 3:
+            ops.append(Op(["rx", "ry", "rz"][c], (a,), param_index=int(rng.integers(0, npar))))
+        elif c == 3:
+            ops.append(Op("swap", (a, b)))
+        elif c == 4:
+            ops.append(Op("u2q", (a, b), matrix=W.haar_unitaries(1, 4, 100 * seed + i)[0]))
+        elif c == 5:
+            ops.append(Op("cnot", (a, b)))
+        elif c == 6:
+            ops.append(Op("cz", (a, b)))
+        elif c == 7:
+            ops.append(Op("cp", (a, b), (float(rng.uniform(0, 6.3)),)))
+        else:
+            ops.append(Op("h", (a,)))
+    params = rng.uniform(0, 2 * np.pi, npar)
+    terms = []
+    for _ in range(5):
+        s = ["I"] * n
+        for q in rng.choice(n, int(rng.integers(1, 4)), replace=False):
+            s[int(q)] = "XYZ"[int(rng.integers(0, 3))]
+        terms.append("".join(s))
+    coeffs = rng.uniform(-1, 1, len(terms))
+    g = emulated_grad(n, ops, params, terms, coeffs, dtype)
+    np.testing.assert_allclose(g, oracle.param_shift_grad(n, ops, params, terms, coeffs), atol=1e-12, rtol=0)
