@@ -194,3 +194,68 @@ def test_plans_do_not_carry_over_between_circuits():
         P.qc_tc_plan_info(other)
         assert P.qc_tc_plan_info(P.Circuit(n, ops)) == first
     assert emulate(n, ops, W.gaussian_state(n, 9)) <= 1e-6
+
+
+# gate-kind weights of _weighted: 1q fixed, rotation, U3, CNOT, CZ, CP, SWAP, Haar 2q on
+# random qubits, MCX, controlled diagonal, diagonal 2q, controlled Haar 2x2, Haar 2q on
+# neighbours
+MIXES = {
+    "phase_heavy": [1, 2, 0.5, 0.5, 3, 3, 0.5, 0.3, 0.2, 2, 2, 0.3, 0.5],
+    "swap_heavy": [1, 1, 0.5, 1, 1, 1, 4, 1, 0.3, 0.5, 0.5, 0.5, 1],
+    "dense": [1, 1, 1, 1, 0.2, 0.2, 0.2, 3, 0.3, 0.2, 0.2, 1, 3],
+}
+
+
+def _weighted(n, seed, count, weights):
+    rng = np.random.default_rng(seed)
+    w = np.asarray(weights, float) / np.sum(weights)
+    kinds1 = ["h", "x", "y", "z", "s", "sdg", "t", "tdg"]
+    ops = []
+    for i in range(count):
+        c = int(rng.choice(len(w), p=w))
+        q = [int(x) for x in rng.permutation(n)[:3]]
+        ang = float(rng.uniform(0, 6.3))
+        if c == 0:
+            ops.append(Op(kinds1[int(rng.integers(0, 8))], (q[0],)))
+        elif c == 1:
+            ops.append(Op(["rx", "ry", "rz"][int(rng.integers(0, 3))], (q[0],), (ang,)))
+        elif c == 2:
+            ops.append(Op("u3", (q[0],), tuple(float(a) for a in rng.uniform(0, 6.3, 3))))
+        elif c in (3, 4, 6):
+            ops.append(Op({3: "cnot", 4: "cz", 6: "swap"}[c], (q[0], q[1])))
+        elif c == 5:
+            ops.append(Op("cp", (q[0], q[1]), (ang,)))
+        elif c == 7:
+            ops.append(Op("u2q", (q[0], q[1]), matrix=W.haar_unitaries(1, 4, 1000 * seed + i)[0]))
+        elif c == 8:
+            ops.append(Op("mcx", tuple(q), ctrl_states=tuple(int(v) for v in rng.integers(0, 2, 2))))
+        elif c == 9:
+            ops.append(Op("ctrl", (q[0], q[1]), matrix=np.diag(np.exp(1j * rng.uniform(0, 6.3, 2))),
+                          ctrl_states=(int(rng.integers(0, 2)),)))
+        elif c == 10:
+            ops.append(Op("u2q", (q[0], q[1]), matrix=np.diag(np.exp(1j * rng.uniform(0, 6.3, 4)))))
+        elif c == 11:
+            ops.append(Op("ctrl", (q[0], q[1]), matrix=W.haar_unitaries(1, 2, 7 * seed + i)[0],
+                          ctrl_states=(int(rng.integers(0, 2)),)))
+        else:
+            a = int(rng.integers(0, n - 1))
+            ops.append(Op("u2q", (a, a + 1), matrix=W.haar_unitaries(1, 4, 3 * seed + i)[0]))
+    return ops
+
+
+@pytest.mark.parametrize("mix", sorted(MIXES))
+def test_weighted_random_circuits(mix):
+    """Seeded circuits of 20-200 gates, weighted towards phases (deferred factors),
+    SWAPs (relabelings) or dense gates, on 12 to 18 qubits; the planner's caches of
+    stage cuts and variants are shared across them, as in one process of the library."""
+    import paper_2503_03016_gb300 as P
+    for n in (12, 14, 16, 18):
+        for seed in range(2):
+            count = int(np.random.default_rng(seed + 99).integers(20, 200))
+            ops = _weighted(n, 1000 * n + seed, count, MIXES[mix])
+            try:
+                err = emulate(n, ops, W.random_state(n, seed + 5))
+            except P.QCError as e:
+                assert e.status == 4
+                continue
+            assert err <= 1e-6, (n, seed, err)

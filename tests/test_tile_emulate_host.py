@@ -13,7 +13,7 @@ import oracle
 import workloads as W
 from workloads import Op
 
-from test_tc_emulate_host import _mixed
+from test_tc_emulate_host import MIXES, _mixed, _weighted
 
 DTYPES = ["c64", "c128"]
 
@@ -65,6 +65,17 @@ def test_cz_runs_and_swaps(dtype):
         ops.append(Op("swap", (a, b)))
     ops += [Op("swap", (j, n - 1 - j)) for j in range(n // 2)]
     assert emulate(n, ops, dtype) <= 1e-12
+
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("mix", sorted(MIXES))
+def test_weighted_random_circuits(dtype, mix):
+    """Seeded circuits weighted towards phases, SWAPs or dense gates (12 to 18 qubits)."""
+    for n in (12, 15, 18):
+        for seed in range(2):
+            count = int(np.random.default_rng(seed + 7).integers(20, 200))
+            ops = _weighted(n, 1000 * n + seed, count, MIXES[mix])
+            assert emulate(n, ops, dtype) <= 1e-12, (n, seed)
 
 
 def test_rejects_invalid_arguments():
