@@ -27,6 +27,7 @@
 #include <mutex>
 #include <map>
 #include <string>
+#include <unordered_map>
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -478,7 +479,11 @@ static void stage_sweep(const std::vector<int>& rest, const std::vector<PlanOp>&
                         std::vector<int>& act) {
   take.clear();
   skip.clear();
-  act.clear();
+  // the stage's local bits in the order they joined (av) and as a mask; an op's trial set
+  // is built in nv / nmask and kept if it fits
+  int av[64], nv[64];
+  int na = 0;
+  uint64_t amask = 0;
   uint64_t blocked_all = 0, blocked_diag = 0;
   // mode 2: condition bits of phase ops whose other bits may be deferred past the stage;
   // a dense op on one of them would not commute with that deferred part
@@ -491,32 +496,39 @@ static void stage_sweep(const std::vector<int>& rest, const std::vector<PlanOp>&
       for (int k = 0; k < p.nt; ++k)
         if ((dblock >> p.tb[k]) & 1) ok = false;
     if (ok && (whole_ops || !p.phase)) {
-      std::vector<int> nw = act;
+      int nn = na;
+      uint64_t nmask = amask;
+      for (int i = 0; i < na; ++i) nv[i] = av[i];
       bool outside = false;
       auto add = [&](int gbit) {
         const int lb = local_of[gbit];
         if (lb < 0) return;
         if (fixed >= 0 && !((fixed >> lb) & 1)) outside = true;
-        if (std::find(nw.begin(), nw.end(), lb) == nw.end()) nw.push_back(lb);
+        if (!((nmask >> lb) & 1)) {
+          nmask |= uint64_t(1) << lb;
+          nv[nn++] = lb;
+        }
       };
       if (!p.phase)
         for (int k = 0; k < p.nt; ++k) add(p.tb[k]);
       if (whole_ops) {
-        for (int b = 0; b < 64; ++b)
-          if ((p.cmask >> b) & 1) add(b);
+        for (uint64_t cm = p.cmask; cm; cm &= cm - 1) add(__builtin_ctzll(cm));
         // mode 2: the phase bits of an op conditioned on at most one bit need no slot
         // (that part of the op is deferred to the end of the stage)
         if (whole_ops == 1 || !p.phase || __builtin_popcountll(p.cmask) >= 2)
           for (const auto& be : p.beta) add(be.first);
       }
-      if (outside || int(nw.size()) > sb)
+      if (outside || nn > sb) {
         ok = false;
-      else
-        act = nw;
+      } else {
+        for (int i = na; i < nn; ++i) av[i] = nv[i];
+        na = nn;
+        amask = nmask;
+      }
       if (ok && whole_ops == 2 && p.phase && __builtin_popcountll(p.cmask) == 1)
         for (const auto& be : p.beta) {
           const int lb = local_of[be.first];
-          if (lb < 0 || std::find(act.begin(), act.end(), lb) == act.end()) dblock |= p.cmask;
+          if (lb < 0 || !((amask >> lb) & 1)) dblock |= p.cmask;
         }
     }
     if (ok) {
@@ -529,6 +541,7 @@ static void stage_sweep(const std::vector<int>& rest, const std::vector<PlanOp>&
         blocked_all |= p.touched;
     }
   }
+  act.assign(av, av + na);
 }
 
 void split_stages(const BuiltPass& bp, const std::vector<PlanOp>& pops, const int* local_of, int sb,
@@ -576,31 +589,67 @@ static std::vector<StageCand> stage_candidates(const std::vector<int>& rest, con
   return out;
 }
 
-// stages the greedy cut (most ops per stage) needs for `rest`
-static int greedy_stage_count(std::vector<int> rest, const std::vector<PlanOp>& pops, const int* local_of, int sb,
-                              int whole_ops, int m) {
-  int k = 0;
-  while (!rest.empty()) {
-    std::vector<StageCand> cs = stage_candidates(rest, pops, local_of, sb, whole_ops, m);
-    if (cs.empty()) return 1 << 20;
+// Greedy stage counts of op sets met during one search: the greedy cuts from different
+// branches run into the same remaining sets, so each set is cut once
+struct OpSetHash {
+  size_t operator()(const std::vector<int>& v) const {
+    uint64_t h = 1469598103934665603ull;  // FNV-1a over the op indices
+    for (int x : v) {
+      h ^= uint32_t(x);
+      h *= 1099511628211ull;
+    }
+    return size_t(h);
+  }
+};
+using GreedyMemo = std::unordered_map<std::vector<int>, int, OpSetHash>;
+constexpr int kNoCut = 1 << 20;  // some op fits no stage
+
+// stages the greedy cut (most ops per stage; the first such candidate) needs for `rest`;
+// kNoCut if it reaches ops that fit no stage
+static int greedy_stage_count(const std::vector<int>& rest, const std::vector<PlanOp>& pops, const int* local_of,
+                              int sb, int whole_ops, int m, GreedyMemo& memo) {
+  std::vector<std::vector<int>> chain;  // the sets the cut walks through, not yet known
+  std::vector<int> cur = rest;
+  int tail;
+  while (true) {
+    if (cur.empty()) {
+      tail = 0;
+      break;
+    }
+    const auto it = memo.find(cur);
+    if (it != memo.end()) {
+      tail = it->second;
+      break;
+    }
+    std::vector<StageCand> cs = stage_candidates(cur, pops, local_of, sb, whole_ops, m);
+    if (cs.empty()) {
+      memo.emplace(cur, kNoCut);
+      tail = kNoCut;
+      break;
+    }
     size_t best = 0;
     for (size_t i = 1; i < cs.size(); ++i)
       if (cs[i].take.size() > cs[best].take.size()) best = i;
-    rest = cs[best].skip;
-    ++k;
+    chain.push_back(std::move(cur));
+    cur = std::move(cs[best].skip);
   }
-  return k;
+  int v = tail;
+  for (size_t i = chain.size(); i-- > 0;) {
+    v = v == kNoCut ? kNoCut : v + 1;
+    memo.emplace(std::move(chain[i]), v);
+  }
+  return v;
 }
 
 // stages needed for `rest` when the next `depth` stages are chosen by search and the
 // rest greedily
 static int lookahead_stage_count(const std::vector<int>& rest, const std::vector<PlanOp>& pops, const int* local_of,
-                                 int sb, int whole_ops, int m, int depth) {
+                                 int sb, int whole_ops, int m, int depth, GreedyMemo& memo) {
   if (rest.empty()) return 0;
-  if (depth == 0) return greedy_stage_count(rest, pops, local_of, sb, whole_ops, m);
-  int best = 1 << 20;
+  if (depth == 0) return greedy_stage_count(rest, pops, local_of, sb, whole_ops, m, memo);
+  int best = kNoCut;
   for (const StageCand& c : stage_candidates(rest, pops, local_of, sb, whole_ops, m))
-    best = std::min(best, 1 + lookahead_stage_count(c.skip, pops, local_of, sb, whole_ops, m, depth - 1));
+    best = std::min(best, 1 + lookahead_stage_count(c.skip, pops, local_of, sb, whole_ops, m, depth - 1, memo));
   return best;
 }
 
@@ -678,6 +727,7 @@ void split_stages_search(const BuiltPass& bp, const std::vector<PlanOp>& pops, c
   int m = 0;
   for (int b = 0; b < 64; ++b) m = std::max(m, local_of[b] + 1);
   std::vector<int> rest = bp.ops;
+  GreedyMemo memo;
   while (!rest.empty()) {
     std::vector<StageCand> cs = stage_candidates(rest, pops, local_of, sb, whole_ops, m);
     if (cs.empty()) {  // (no op fits: leave them to the caller's checks, as the greedy cut does)
@@ -685,9 +735,9 @@ void split_stages_search(const BuiltPass& bp, const std::vector<PlanOp>& pops, c
       return;
     }
     size_t best = 0;
-    int best_n = 1 << 20;
+    int best_n = kNoCut;
     for (size_t i = 0; i < cs.size(); ++i) {
-      const int nst = 1 + lookahead_stage_count(cs[i].skip, pops, local_of, sb, whole_ops, m, depth - 1);
+      const int nst = 1 + lookahead_stage_count(cs[i].skip, pops, local_of, sb, whole_ops, m, depth - 1, memo);
       if (nst < best_n || (nst == best_n && cs[i].take.size() > cs[best].take.size())) {
         best_n = nst;
         best = i;
