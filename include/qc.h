@@ -390,7 +390,12 @@ typedef enum {
  * device times both kinds of pass on a scratch state of the same size (allocated and
  * freed by the call; if that allocation fails, the tensor-core passes are taken) and
  * keeps the faster for later runs; with the environment variable QC_AUTOTUNE_CACHE
- * naming a file, choices are appended to it and read back by later processes. */
+ * naming a file, choices are appended to it and read back by later processes.  Host
+ * planning: the tensor-core plan of the last circuit run is kept (with its device copy,
+ * library-owned) and reused while the circuit and its values are unchanged; the stage
+ * cuts and plan variants found for a circuit structure are kept process-wide (the 512
+ * most recent of each, under a lock), so the same structure with new values re-plans in
+ * milliseconds; the plan is built in memory the calling thread keeps for its next plan. */
 qc_status qc_run_circuit(qc_state* s, const qc_circuit* c, const double* params, qc_run_mode mode,
                          qc_prec prec);
 
