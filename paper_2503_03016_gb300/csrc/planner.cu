@@ -593,7 +593,7 @@ static std::vector<StageCand> stage_candidates(const std::vector<int>& rest, con
 // branches run into the same remaining sets, so each set is cut once
 struct OpSetHash {
   size_t operator()(const std::vector<int>& v) const {
-    uint64_t h = 1469598103934665603ull;  // FNV-1a over the op indices
+    uint64_t h = 1469598103934665603ull;  // FNV-style: one 32-bit index per step
     for (int x : v) {
       h ^= uint32_t(x);
       h *= 1099511628211ull;
